@@ -1,0 +1,261 @@
+"""ctypes wrapper of the FP64 CPU oracle (``pic_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` are the only users.  The GPU library and its binding never import this module.
+
+The oracle follows the PIC Monte Carlo cycle of the paper (Sec. 2) in plain FP64 loops; see the
+header comment of ``pic_oracle.c`` for the readings R1..R13 it implements.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_HDR = os.path.join(_HERE, "pic_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+COLL_EL, COLL_EX, COLL_IZ, COLL_CX = 1, 2, 4, 8
+FIELD_SELF, FIELD_EXTERNAL, FIELD_ZERO = 0, 1, 2
+LOAD_UNIFORM, LOAD_EXP, LOAD_QUIET_SINE = 0, 1, 2
+SOURCE_NONE, SOURCE_PAIRS = 0, 1
+CH_INIT, CH_COLL, CH_SCAT, CH_CHILD, CH_SOURCE = 1, 2, 3, 4, 5
+
+
+class OrcConfig(C.Structure):
+    _fields_ = [
+        ("ncells", C.c_int32), ("ppc", C.c_int32 * 2), ("load_profile", C.c_int32),
+        ("profile_mode", C.c_int32), ("source_mode", C.c_int32), ("sort_interval", C.c_int32),
+        ("coll_mask", C.c_uint32), ("field_mode", C.c_uint32), ("frozen_mask", C.c_uint32),
+        ("L", C.c_double), ("dt", C.c_double), ("mass", C.c_double * 2),
+        ("charge", C.c_double * 2), ("T", C.c_double * 2), ("Tg", C.c_double),
+        ("m_gas", C.c_double), ("B", C.c_double), ("B_angle_deg", C.c_double),
+        ("V_left", C.c_double), ("V_right", C.c_double), ("n_gas", C.c_double),
+        ("sigma_el", C.c_double), ("sigma_ex", C.c_double), ("E_ex", C.c_double),
+        ("sigma_iz", C.c_double), ("E_iz", C.c_double), ("sigma_cx", C.c_double),
+        ("E_cap", C.c_double), ("E_ext", C.c_double), ("profile_scale", C.c_double),
+        ("source_x1", C.c_double), ("seed", C.c_uint64),
+    ]
+
+
+class OrcDiag(C.Structure):
+    _fields_ = [
+        ("step", C.c_uint64), ("n", C.c_uint64 * 2), ("wall_hits", (C.c_uint64 * 2) * 2),
+        ("coll", C.c_uint64 * 5), ("near_threshold", C.c_uint64 * 2),
+        ("nu_max_violations", C.c_uint64 * 2), ("births", C.c_uint64 * 2),
+        ("source_pairs", C.c_uint64), ("dropped", C.c_uint64),
+        ("net_charge_units", C.c_int64), ("wall_charge", C.c_int64), ("ke", C.c_double * 2),
+        ("field_energy", C.c_double), ("wall_energy", C.c_double * 2),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (OpenMP on, no FMA contraction)."""
+    with _lock:
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+            return _LIB
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-fopenmp", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P = C.POINTER
+        L.orc_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+        L.orc_philox_batch.argtypes = [C.c_size_t, P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+        L.orc_poisson_thomas.argtypes = [C.c_int32, C.c_double, P(C.c_double), C.c_double,
+                                         C.c_double, P(C.c_double)]
+        L.orc_efield.argtypes = [C.c_int32, C.c_double, P(C.c_double), P(C.c_double),
+                                 P(C.c_double)]
+        L.orc_efield.restype = None
+        L.orc_boris.argtypes = [C.c_double, C.c_double, P(C.c_double), P(C.c_double),
+                                P(C.c_double)]
+        L.orc_boris.restype = None
+        L.orc_nu_max.argtypes = [P(OrcConfig), P(C.c_float), P(C.c_float)]
+        L.orc_nu_max.restype = None
+        L.orc_create.argtypes = [P(OrcConfig), P(C.c_int)]
+        L.orc_create.restype = C.c_void_p
+        L.orc_free.argtypes = [C.c_void_p]
+        L.orc_free.restype = None
+        L.orc_step.argtypes = [C.c_void_p, C.c_int32]
+        L.orc_diag.argtypes = [C.c_void_p, P(OrcDiag)]
+        L.orc_fields.argtypes = [C.c_void_p, P(C.c_int64), P(C.c_double), P(C.c_double),
+                                 P(C.c_double)]
+        L.orc_count.argtypes = [C.c_void_p, C.c_int]
+        L.orc_count.restype = C.c_uint64
+        L.orc_particles.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double),
+                                    P(C.c_uint64)]
+        L.orc_snapshot.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, P(C.c_size_t)]
+        L.orc_restore.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+        L.orc_config_hash.argtypes = [P(OrcConfig)]
+        L.orc_config_hash.restype = C.c_uint64
+        L.orc_set_threads.argtypes = [C.c_int]
+        _lib = L
+    return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def make_config(p: dict) -> OrcConfig:
+    """Fill an ``orc_config`` from a workload parameter dict."""
+    c = OrcConfig()
+    for name, _ in OrcConfig._fields_:
+        if name not in p:
+            continue
+        val = p[name]
+        if name in ("ppc", "mass", "charge", "T"):
+            arr = getattr(c, name)
+            arr[0], arr[1] = val[0], val[1]
+        else:
+            setattr(c, name, val)
+    return c
+
+
+# ------------------------------------------------------------------------------------------------
+def philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    """Philox4x32-10 of n counters (n x 4 uint32) under n keys (n x 2 uint32)."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.empty_like(ctr)
+    lib().orc_philox_batch(ctr.shape[0], _ptr(ctr, C.c_uint32), _ptr(key, C.c_uint32),
+                           _ptr(out, C.c_uint32))
+    return out
+
+
+def poisson_thomas(rho: np.ndarray, dx: float, V_L: float, V_R: float) -> np.ndarray:
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    phi = np.empty_like(rho)
+    rc = lib().orc_poisson_thomas(rho.size - 1, dx, _ptr(rho, C.c_double), V_L, V_R,
+                                  _ptr(phi, C.c_double))
+    if rc != 0:
+        raise ValueError(f"orc_poisson_thomas failed ({rc})")
+    return phi
+
+
+def efield(phi: np.ndarray, rho: np.ndarray, dx: float) -> np.ndarray:
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    E = np.empty_like(phi)
+    lib().orc_efield(phi.size - 1, dx, _ptr(phi, C.c_double), _ptr(rho, C.c_double),
+                     _ptr(E, C.c_double))
+    return E
+
+
+def boris(qm: float, dt: float, E, B, v) -> np.ndarray:
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    lib().orc_boris(qm, dt, _ptr(E, C.c_double), _ptr(B, C.c_double), _ptr(v, C.c_double))
+    return v
+
+
+def nu_max(params: dict):
+    c = make_config(params)
+    nm = (C.c_float * 2)()
+    pn = (C.c_float * 2)()
+    lib().orc_nu_max(C.byref(c), nm, pn)
+    return np.array(list(nm), np.float32), np.array(list(pn), np.float32)
+
+
+def config_hash(params: dict) -> int:
+    c = make_config(params)
+    return int(lib().orc_config_hash(C.byref(c)))
+
+
+def set_threads(n: int) -> int:
+    return int(lib().orc_set_threads(int(n)))
+
+
+def _diag_dict(d: OrcDiag) -> dict:
+    return {
+        "step": d.step, "n": [d.n[0], d.n[1]],
+        "wall_hits": [[d.wall_hits[s][k] for k in range(2)] for s in range(2)],
+        "coll": list(d.coll), "near_threshold": list(d.near_threshold),
+        "nu_max_violations": list(d.nu_max_violations), "births": list(d.births),
+        "source_pairs": d.source_pairs, "dropped": d.dropped,
+        "net_charge_units": d.net_charge_units, "wall_charge": d.wall_charge,
+        "ke": [d.ke[0], d.ke[1]], "field_energy": d.field_energy,
+        "wall_energy": [d.wall_energy[0], d.wall_energy[1]],
+    }
+
+
+class OracleSim:
+    """One oracle simulation (FP64, CPU)."""
+
+    def __init__(self, params: dict, threads: int = 1):
+        self.params = dict(params)
+        self.N = int(params["ncells"])
+        set_threads(threads)
+        self._cfg = make_config(params)
+        err = C.c_int(0)
+        h = lib().orc_create(C.byref(self._cfg), C.byref(err))
+        if not h:
+            raise ValueError(f"orc_create failed ({err.value})")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().orc_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, n: int = 1):
+        rc = lib().orc_step(self._h, int(n))
+        if rc != 0:
+            raise RuntimeError(f"orc_step failed ({rc})")
+
+    def diag(self) -> dict:
+        d = OrcDiag()
+        lib().orc_diag(self._h, C.byref(d))
+        return _diag_dict(d)
+
+    def fields(self) -> dict:
+        n1 = self.N + 1
+        R = np.empty(2 * n1, np.int64)
+        rho, phi, E = (np.empty(n1) for _ in range(3))
+        lib().orc_fields(self._h, _ptr(R, C.c_int64), _ptr(rho, C.c_double),
+                         _ptr(phi, C.c_double), _ptr(E, C.c_double))
+        return {"R": R.reshape(2, n1), "rho": rho, "phi": phi, "E": E}
+
+    def count(self, s: int) -> int:
+        return int(lib().orc_count(self._h, s))
+
+    def particles(self, s: int):
+        n = self.count(s)
+        x = np.empty(n)
+        v = np.empty((n, 3))
+        ids = np.empty(n, np.uint64)
+        lib().orc_particles(self._h, s, _ptr(x, C.c_double), _ptr(v, C.c_double),
+                            _ptr(ids, C.c_uint64))
+        return x, v, ids
+
+    def snapshot(self) -> bytes:
+        need = C.c_size_t(0)
+        lib().orc_snapshot(self._h, None, 0, C.byref(need))
+        buf = C.create_string_buffer(need.value)
+        rc = lib().orc_snapshot(self._h, buf, need.value, C.byref(need))
+        if rc != 0:
+            raise RuntimeError(f"orc_snapshot failed ({rc})")
+        return buf.raw[: need.value]
+
+    def restore(self, blob: bytes) -> int:
+        return int(lib().orc_restore(self._h, blob, len(blob)))

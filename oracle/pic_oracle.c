@@ -1,0 +1,1004 @@
+/*
+ * pic_oracle.c -- plain FP64 CPU oracle of the 1D3V electrostatic PIC Monte Carlo step.
+ *
+ * TEST INFRASTRUCTURE ONLY (see pic_oracle.h).  Slow and plain on purpose: one loop per stage of
+ * the PIC cycle in the order the paper lists it (Sec. 2), FP64 throughout, the Poisson problem
+ * solved by the Thomas algorithm, sorting as a textbook stable counting sort.
+ *
+ * Readings of points the paper leaves open (the paper prints no formulas; its method statement is
+ * the PIC MC cycle of Sec. 2 and the BIT1 lineage, XPDP1 with "natural sorting"):
+ *   R1  leapfrog start: loaded velocities are v^{-1/2}; no backward half push.
+ *   R2  step order: gather -> Boris push -> wall test -> MCC on survivors -> deposit (births
+ *       included) -> source -> Poisson -> sort when step % sort_interval == 0 -> step += 1.
+ *   R3  absorbed iff x < 0 or x >= L.
+ *   R4  wall nodes use half-cell volume; wall field from Gauss's law over the half cell.
+ *   R7  cross sections: constant elastic and CX; excitation/ionization linear above threshold,
+ *       saturating at twice the threshold.
+ *   R8  null-collision bound nu_max = n_g * sum(sigma_max) * v_cap, v_cap = sqrt(2 E_cap'/m),
+ *       E_cap' = E_cap + |V_L - V_R|; rounded to FP32 and shared by both codes by value.
+ *   R9  Philox4x32-10 keyed by (particle id ^ seed), counter (step lo, step hi, channel, index);
+ *       uniform u = (word >> 8) * 2^-24.
+ *   R10 isotropic scattering; elastic energy loss 2m/M (1 - cos chi); excitation loses E_ex;
+ *       ionization splits E - E_iz uniformly; new ion and CX ion Maxwellian at T_g.
+ *   R11 child ids are Philox words of (parent id, step, CHILD channel).
+ *   R12 CIC deposit in int64 fixed point: W_r = rint(f 2^32), W_l = 2^32 - W_r.
+ *   R13 source: one (e, ion) pair per ion absorbed this step, uniform in [0, x1), Maxwellian.
+ */
+#include "pic_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define TWO32 4294967296.0
+#define ORC_PI 3.14159265358979323846
+#define MAX_THREADS 256
+
+static int g_threads = 1;
+
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n < 1) n = 1;
+  if (n > MAX_THREADS) n = MAX_THREADS;
+  g_threads = n;
+#else
+  (void)n;
+  g_threads = 1;
+#endif
+  return g_threads;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Philox4x32-10: ten rounds of two 32x32->64 multiplies, with the key bumped by the Weyl
+ * constants between rounds (Salmon et al., SC'11, Sec. 4).                                      */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+void orc_philox_batch(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  for (size_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
+/* uniform in [0,1) with 24 bits: exact in both FP32 and FP64 (R9) */
+static double u01(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+static void draw(uint64_t id, uint64_t seed, uint64_t step, uint32_t channel, uint32_t index,
+                 uint32_t w[4]) {
+  uint64_t k = id ^ seed;
+  uint32_t key[2] = {(uint32_t)k, (uint32_t)(k >> 32)};
+  uint32_t ctr[4] = {(uint32_t)step, (uint32_t)(step >> 32), channel, index};
+  orc_philox4x32_10(ctr, key, w);
+}
+
+/* Box-Muller: two standard normals from two uniforms. */
+static void box_muller(uint32_t wa, uint32_t wb, double* n0, double* n1) {
+  double r = sqrt(-2.0 * log(1.0 - u01(wa)));
+  double th = 2.0 * ORC_PI * u01(wb);
+  *n0 = r * cos(th);
+  *n1 = r * sin(th);
+}
+
+/* direction uniform on the unit sphere: cos(theta) = 1 - 2u, phi = 2 pi u' (R10) */
+static void iso_dir(uint32_t wa, uint32_t wb, double d[3]) {
+  double ua = u01(wa), ub = u01(wb);
+  double ct = 1.0 - 2.0 * ua;
+  double st = 2.0 * sqrt(ua * (1.0 - ua));
+  double ph = 2.0 * ORC_PI * ub;
+  d[0] = st * cos(ph);
+  d[1] = st * sin(ph);
+  d[2] = ct;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Field solve (Sec. 2 "field solver"; BIT1's native Poisson solver, Sec. 2).                    */
+int orc_poisson_thomas(int32_t N, double dx, const double* rho, double V_L, double V_R,
+                       double* phi) {
+  if (N < 2) return ORC_EINVAL;
+  int32_t m = N - 1; /* unknowns phi_1 .. phi_{N-1} */
+  double* cp = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  double* dp = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  if (!cp || !dp) {
+    free(cp);
+    free(dp);
+    return ORC_ENOMEM;
+  }
+  /* a_j = -1, b_j = 2, c_j = -1; right-hand side with the Dirichlet values moved over */
+  for (int32_t j = 1; j <= m; ++j) {
+    double d = dx * dx * rho[j]; /* eps0 = 1 */
+    if (j == 1) d += V_L;
+    if (j == m) d += V_R;
+    if (j == 1) {
+      cp[j] = -1.0 / 2.0;
+      dp[j] = d / 2.0;
+    } else {
+      double den = 2.0 - (-1.0) * cp[j - 1];
+      cp[j] = -1.0 / den;
+      dp[j] = (d - (-1.0) * dp[j - 1]) / den;
+    }
+  }
+  phi[0] = V_L;
+  phi[N] = V_R;
+  phi[m] = dp[m];
+  for (int32_t j = m - 1; j >= 1; --j) phi[j] = dp[j] - cp[j] * phi[j + 1];
+  free(cp);
+  free(dp);
+  return ORC_OK;
+}
+
+void orc_efield(int32_t N, double dx, const double* phi, const double* rho, double* E) {
+  for (int32_t j = 1; j < N; ++j) E[j] = (phi[j - 1] - phi[j + 1]) / (2.0 * dx);
+  /* Gauss over [0, dx/2] and [L - dx/2, L] (R4) */
+  E[0] = (phi[0] - phi[1]) / dx - rho[0] * dx / 2.0;
+  E[N] = (phi[N - 1] - phi[N]) / dx + rho[N] * dx / 2.0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Boris rotation for a uniform B (the magnetised mover; Sec. 5.1 names it moveb).              */
+void orc_boris(double qm, double dt, const double E[3], const double B[3], double v[3]) {
+  double h = 0.5 * qm * dt;
+  double vm[3] = {v[0] + h * E[0], v[1] + h * E[1], v[2] + h * E[2]};
+  double t[3] = {h * B[0], h * B[1], h * B[2]};
+  double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  double s[3] = {2.0 * t[0] / (1.0 + t2), 2.0 * t[1] / (1.0 + t2), 2.0 * t[2] / (1.0 + t2)};
+  double vp[3] = {vm[0] + (vm[1] * t[2] - vm[2] * t[1]), vm[1] + (vm[2] * t[0] - vm[0] * t[2]),
+                  vm[2] + (vm[0] * t[1] - vm[1] * t[0])};
+  double vq[3] = {vm[0] + (vp[1] * s[2] - vp[2] * s[1]), vm[1] + (vp[2] * s[0] - vp[0] * s[2]),
+                  vm[2] + (vp[0] * s[1] - vp[1] * s[0])};
+  v[0] = vq[0] + h * E[0];
+  v[1] = vq[1] + h * E[1];
+  v[2] = vq[2] + h * E[2];
+}
+
+/* ------------------------------------------------------------------------------------------ */
+void orc_nu_max(const orc_config* c, float nu_max[2], float p_null[2]) {
+  double Ecap = c->E_cap + fabs(c->V_left - c->V_right);
+  double smax[2];
+  smax[0] = ((c->coll_mask & ORC_COLL_EL) ? c->sigma_el : 0.0) +
+            ((c->coll_mask & ORC_COLL_EX) ? c->sigma_ex : 0.0) +
+            ((c->coll_mask & ORC_COLL_IZ) ? c->sigma_iz : 0.0);
+  smax[1] = (c->coll_mask & ORC_COLL_CX) ? c->sigma_cx : 0.0;
+  for (int s = 0; s < 2; ++s) {
+    double vcap = sqrt(2.0 * Ecap / c->mass[s]);
+    nu_max[s] = (float)(c->n_gas * smax[s] * vcap);
+    p_null[s] = (float)(1.0 - exp(-(double)nu_max[s] * c->dt));
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  double *x, *vx, *vy, *vz;
+  uint64_t* id;
+  size_t n, cap;
+} orc_species;
+
+typedef struct {
+  uint64_t wall_hits[2];
+  uint64_t coll[5];
+  uint64_t near, viol;
+} orc_tcount;
+
+typedef struct {
+  double x, v[3];
+  uint64_t id;
+} orc_newp;
+
+typedef struct {
+  orc_newp* p;
+  size_t n, cap;
+} orc_plist;
+
+struct orc_sim {
+  orc_config cfg;
+  int32_t N;
+  double dx, w[2], qm[2], Bv[3];
+  float nu_max[2], p_null[2];
+  orc_species sp[2];
+  int64_t* R[2];
+  double *rho, *phi, *E;
+  uint64_t step;
+  uint64_t wall_hits[2][2], coll[5], near[2], viol[2], births[2], source_pairs;
+  int64_t wall_charge;
+  double wall_energy[2];
+};
+
+static int sp_reserve(orc_species* s, size_t cap) {
+  if (cap <= s->cap) return ORC_OK;
+  size_t nc = s->cap ? s->cap : 16;
+  while (nc < cap) nc *= 2;
+  double* x = (double*)realloc(s->x, nc * sizeof(double));
+  if (x) s->x = x;
+  double* a = (double*)realloc(s->vx, nc * sizeof(double));
+  if (a) s->vx = a;
+  double* b = (double*)realloc(s->vy, nc * sizeof(double));
+  if (b) s->vy = b;
+  double* c = (double*)realloc(s->vz, nc * sizeof(double));
+  if (c) s->vz = c;
+  uint64_t* d = (uint64_t*)realloc(s->id, nc * sizeof(uint64_t));
+  if (d) s->id = d;
+  if (!x || !a || !b || !c || !d) return ORC_ENOMEM;
+  s->cap = nc;
+  return ORC_OK;
+}
+
+static int sp_push_back(orc_species* s, double x, const double v[3], uint64_t id) {
+  if (s->n == s->cap && sp_reserve(s, s->n + 1) != ORC_OK) return ORC_ENOMEM;
+  s->x[s->n] = x;
+  s->vx[s->n] = v[0];
+  s->vy[s->n] = v[1];
+  s->vz[s->n] = v[2];
+  s->id[s->n] = id;
+  s->n++;
+  return ORC_OK;
+}
+
+static int plist_add(orc_plist* l, double x, const double v[3], uint64_t id) {
+  if (l->n == l->cap) {
+    size_t nc = l->cap ? 2 * l->cap : 64;
+    orc_newp* p = (orc_newp*)realloc(l->p, nc * sizeof(orc_newp));
+    if (!p) return ORC_ENOMEM;
+    l->p = p;
+    l->cap = nc;
+  }
+  l->p[l->n].x = x;
+  l->p[l->n].v[0] = v[0];
+  l->p[l->n].v[1] = v[1];
+  l->p[l->n].v[2] = v[2];
+  l->p[l->n].id = id;
+  l->n++;
+  return ORC_OK;
+}
+
+static int valid_config(const orc_config* c) {
+  if (c->ncells < 2 || !(c->L > 0) || !(c->dt > 0)) return 0;
+  for (int s = 0; s < 2; ++s) {
+    if (c->ppc[s] < 1 || !(c->mass[s] > 0) || c->T[s] < 0) return 0;
+    if (c->charge[s] == 0) return 0;
+  }
+  if (c->sort_interval < 1) return 0;
+  if (c->field_mode > ORC_FIELD_ZERO) return 0;
+  if (c->load_profile < 0 || c->load_profile > ORC_LOAD_QUIET_SINE) return 0;
+  if (c->load_profile == ORC_LOAD_EXP && !(c->profile_scale > 0)) return 0;
+  if (c->source_mode < 0 || c->source_mode > ORC_SOURCE_PAIRS) return 0;
+  if (c->source_mode == ORC_SOURCE_PAIRS && !(c->source_x1 > 0 && c->source_x1 <= c->ncells))
+    return 0;
+  if (c->n_gas < 0 || c->Tg < 0 || !(c->m_gas > 0)) return 0;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Deposit (Sec. 2 "deposition to the grid"): CIC in int64 fixed point (R12), then the node
+ * charge density, half-cell volume at the walls (R4), then Poisson and the node field.        */
+static void deposit_and_solve(orc_sim* s) {
+  int32_t N = s->N;
+  for (int sp = 0; sp < 2; ++sp) {
+    int64_t* R = s->R[sp];
+    memset(R, 0, sizeof(int64_t) * (size_t)(N + 1));
+    orc_species* p = &s->sp[sp];
+    for (size_t i = 0; i < p->n; ++i) {
+      double xh = p->x[i];
+      int32_t c = (int32_t)floor(xh);
+      double f = xh - (double)c;
+      int64_t Wr = (int64_t)rint(f * TWO32);
+      int64_t Wl = (int64_t)TWO32 - Wr;
+      R[c] += Wl;
+      R[c + 1] += Wr;
+    }
+  }
+  for (int32_t j = 0; j <= N; ++j) {
+    double vol = (j == 0 || j == N) ? 0.5 * s->dx : s->dx;
+    double q = 0.0;
+    for (int sp = 0; sp < 2; ++sp) q += s->cfg.charge[sp] * s->w[sp] * ((double)s->R[sp][j] / TWO32);
+    s->rho[j] = q / vol;
+  }
+  orc_poisson_thomas(N, s->dx, s->rho, s->cfg.V_left, s->cfg.V_right, s->phi);
+  orc_efield(N, s->dx, s->phi, s->rho, s->E);
+}
+
+/* Stable counting sort of one species by cell (the "natural sorting" arranger, Sec. 2).       */
+static int sort_species(orc_species* p, int32_t N) {
+  size_t n = p->n;
+  if (n == 0) return ORC_OK;
+  size_t* cnt = (size_t*)calloc((size_t)N + 1, sizeof(size_t));
+  size_t* perm = (size_t*)malloc(n * sizeof(size_t));
+  double* tmp = (double*)malloc(n * sizeof(double));
+  uint64_t* tid = (uint64_t*)malloc(n * sizeof(uint64_t));
+  if (!cnt || !perm || !tmp || !tid) {
+    free(cnt);
+    free(perm);
+    free(tmp);
+    free(tid);
+    return ORC_ENOMEM;
+  }
+  for (size_t i = 0; i < n; ++i) cnt[(size_t)floor(p->x[i]) + 1]++;
+  for (int32_t c = 0; c < N; ++c) cnt[c + 1] += cnt[c];
+  for (size_t i = 0; i < n; ++i) perm[cnt[(size_t)floor(p->x[i])]++] = i;
+  double* arrs[4] = {p->x, p->vx, p->vy, p->vz};
+  for (int a = 0; a < 4; ++a) {
+    for (size_t k = 0; k < n; ++k) tmp[k] = arrs[a][perm[k]];
+    memcpy(arrs[a], tmp, n * sizeof(double));
+  }
+  for (size_t k = 0; k < n; ++k) tid[k] = p->id[perm[k]];
+  memcpy(p->id, tid, n * sizeof(uint64_t));
+  free(cnt);
+  free(perm);
+  free(tmp);
+  free(tid);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Initial load (Sec. 2 "particle load"): positions per profile, Maxwellian velocities.       */
+static int load(orc_sim* s) {
+  const orc_config* c = &s->cfg;
+  int32_t N = s->N;
+  for (int sp = 0; sp < 2; ++sp) {
+    size_t np = (size_t)c->ppc[sp] * (size_t)N;
+    if (sp_reserve(&s->sp[sp], np) != ORC_OK) return ORC_ENOMEM;
+    orc_species* p = &s->sp[sp];
+    double vth = sqrt(c->T[sp] / c->mass[sp]);
+    for (size_t i = 0; i < np; ++i) {
+      uint64_t id = (sp == 0) ? (uint64_t)i : ((1ull << 62) | (uint64_t)i);
+      uint32_t w[4];
+      double x;
+      if (c->load_profile == ORC_LOAD_UNIFORM) {
+        draw(id, c->seed, 0, ORC_CH_INIT, 0, w);
+        x = (double)(i / (size_t)c->ppc[sp]) + u01(w[0]);
+      } else if (c->load_profile == ORC_LOAD_EXP) {
+        draw(id, c->seed, 0, ORC_CH_INIT, 0, w);
+        double lam = c->profile_scale;
+        x = -lam * log(1.0 - u01(w[0]) * (1.0 - exp(-(double)N / lam)));
+      } else {
+        double x0 = ((double)i + 0.5) * (double)N / (double)np;
+        x = x0;
+        if (sp == 0)
+          x = x0 + c->profile_scale * sin(2.0 * ORC_PI * (double)c->profile_mode * x0 / (double)N);
+      }
+      if (x < 0.0) x = 0.0;
+      if (x >= (double)N) x = nextafter((double)N, 0.0);
+      draw(id, c->seed, 0, ORC_CH_INIT, 1, w);
+      double n0, n1, n2, n3;
+      box_muller(w[0], w[1], &n0, &n1);
+      box_muller(w[2], w[3], &n2, &n3);
+      p->x[i] = x;
+      p->vx[i] = vth * n0;
+      p->vy[i] = vth * n1;
+      p->vz[i] = vth * n2;
+      p->id[i] = id;
+    }
+    p->n = np;
+  }
+  return ORC_OK;
+}
+
+static void derive(orc_sim* s) {
+  const orc_config* c = &s->cfg;
+  s->N = c->ncells;
+  s->dx = c->L / (double)c->ncells;
+  for (int sp = 0; sp < 2; ++sp) {
+    s->w[sp] = s->dx / (double)c->ppc[sp]; /* n0 = 1 */
+    s->qm[sp] = c->charge[sp] / c->mass[sp];
+  }
+  double th = c->B_angle_deg * ORC_PI / 180.0;
+  s->Bv[0] = c->B * cos(th);
+  s->Bv[1] = c->B * sin(th);
+  s->Bv[2] = 0.0;
+  orc_nu_max(c, s->nu_max, s->p_null);
+}
+
+orc_sim* orc_create(const orc_config* cfg, int* err) {
+  int e = ORC_OK;
+  orc_sim* s = NULL;
+  if (!cfg || !valid_config(cfg)) {
+    e = ORC_EINVAL;
+    goto out;
+  }
+  s = (orc_sim*)calloc(1, sizeof(orc_sim));
+  if (!s) {
+    e = ORC_ENOMEM;
+    goto out;
+  }
+  s->cfg = *cfg;
+  derive(s);
+  for (int sp = 0; sp < 2; ++sp) s->R[sp] = (int64_t*)calloc((size_t)s->N + 1, sizeof(int64_t));
+  s->rho = (double*)calloc((size_t)s->N + 1, sizeof(double));
+  s->phi = (double*)calloc((size_t)s->N + 1, sizeof(double));
+  s->E = (double*)calloc((size_t)s->N + 1, sizeof(double));
+  if (!s->R[0] || !s->R[1] || !s->rho || !s->phi || !s->E) {
+    e = ORC_ENOMEM;
+    goto out;
+  }
+  e = load(s);
+  if (e != ORC_OK) goto out;
+  for (int sp = 0; sp < 2; ++sp) sort_species(&s->sp[sp], s->N);
+  deposit_and_solve(s);
+out:
+  if (e != ORC_OK && s) {
+    orc_free(s);
+    s = NULL;
+  }
+  if (err) *err = e;
+  return s;
+}
+
+void orc_free(orc_sim* s) {
+  if (!s) return;
+  for (int sp = 0; sp < 2; ++sp) {
+    free(s->sp[sp].x);
+    free(s->sp[sp].vx);
+    free(s->sp[sp].vy);
+    free(s->sp[sp].vz);
+    free(s->sp[sp].id);
+    free(s->R[sp]);
+  }
+  free(s->rho);
+  free(s->phi);
+  free(s->E);
+  free(s);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Monte Carlo collision of one electron (null-collision method; Sec. 2 "MC collision
+ * handling").  Returns 1 when an ionization produced a pair (written to e_new / i_new).       */
+static int collide_electron(const orc_sim* s, uint64_t id, uint64_t step, double x, double v[3],
+                            orc_tcount* tc, orc_newp* e_new, orc_newp* i_new) {
+  const orc_config* c = &s->cfg;
+  uint32_t w[4];
+  draw(id, c->seed, step, ORC_CH_COLL, 0, w);
+  if (!(u01(w[0]) < (double)s->p_null[0])) return 0;
+  tc->coll[4]++;
+  double m = c->mass[0];
+  double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  double speed = sqrt(v2);
+  double En = 0.5 * m * v2;
+  double nu_el = (c->coll_mask & ORC_COLL_EL) ? c->n_gas * c->sigma_el * speed : 0.0;
+  double nu_ex = 0.0, nu_iz = 0.0;
+  if ((c->coll_mask & ORC_COLL_EX) && En > c->E_ex)
+    nu_ex = c->n_gas * c->sigma_ex * fmin((En - c->E_ex) / c->E_ex, 1.0) * speed;
+  if ((c->coll_mask & ORC_COLL_IZ) && En > c->E_iz)
+    nu_iz = c->n_gas * c->sigma_iz * fmin((En - c->E_iz) / c->E_iz, 1.0) * speed;
+  double numax = (double)s->nu_max[0];
+  double b1 = nu_el, b2 = b1 + nu_ex, b3 = b2 + nu_iz;
+  if (b3 > numax) tc->viol++;
+  double r = u01(w[1]) * numax;
+  double tol = 1e-5 * numax;
+  int near = fabs(r - b1) < tol || fabs(r - b2) < tol || fabs(r - b3) < tol;
+  if ((c->coll_mask & ORC_COLL_EX) && fabs(En - c->E_ex) < 1e-5 * c->E_ex) near = 1;
+  if ((c->coll_mask & ORC_COLL_IZ) && fabs(En - c->E_iz) < 1e-5 * c->E_iz) near = 1;
+  if (near) tc->near++;
+  double d[3];
+  iso_dir(w[2], w[3], d);
+  if (r < b1) { /* elastic: energy loss 2m/M (1 - cos chi) */
+    double cchi = (v[0] * d[0] + v[1] * d[1] + v[2] * d[2]) / speed;
+    double sp2 = speed * sqrt(1.0 - 2.0 * m / c->m_gas * (1.0 - cchi));
+    v[0] = sp2 * d[0];
+    v[1] = sp2 * d[1];
+    v[2] = sp2 * d[2];
+    tc->coll[0]++;
+    return 0;
+  }
+  if (r < b2) { /* excitation: loses E_ex */
+    double sp2 = sqrt(2.0 * (En - c->E_ex) / m);
+    v[0] = sp2 * d[0];
+    v[1] = sp2 * d[1];
+    v[2] = sp2 * d[2];
+    tc->coll[1]++;
+    return 0;
+  }
+  if (r < b3) { /* ionization: E - E_iz split uniformly between the two electrons */
+    uint32_t a[4], b[4], k[4];
+    draw(id, c->seed, step, ORC_CH_SCAT, 0, a);
+    draw(id, c->seed, step, ORC_CH_SCAT, 1, b);
+    draw(id, c->seed, step, ORC_CH_CHILD, 0, k);
+    double Er = En - c->E_iz;
+    double Es = u01(a[0]) * Er;
+    double Ep = Er - Es;
+    double spp = sqrt(2.0 * Ep / m), sps = sqrt(2.0 * Es / m);
+    v[0] = spp * d[0];
+    v[1] = spp * d[1];
+    v[2] = spp * d[2];
+    double d2[3];
+    iso_dir(a[1], a[2], d2);
+    e_new->x = x;
+    e_new->v[0] = sps * d2[0];
+    e_new->v[1] = sps * d2[1];
+    e_new->v[2] = sps * d2[2];
+    e_new->id = (uint64_t)k[0] | ((uint64_t)k[1] << 32);
+    double n0, n1, n2, n3, vt = sqrt(c->Tg / c->mass[1]);
+    box_muller(b[0], b[1], &n0, &n1);
+    box_muller(b[2], b[3], &n2, &n3);
+    i_new->x = x;
+    i_new->v[0] = vt * n0;
+    i_new->v[1] = vt * n1;
+    i_new->v[2] = vt * n2;
+    i_new->id = (uint64_t)k[2] | ((uint64_t)k[3] << 32);
+    tc->coll[2]++;
+    return 1;
+  }
+  return 0;
+}
+
+/* Charge exchange of one ion: the ion leaves with a Maxwellian velocity at T_g.               */
+static void collide_ion(const orc_sim* s, uint64_t id, uint64_t step, double v[3],
+                        orc_tcount* tc) {
+  const orc_config* c = &s->cfg;
+  uint32_t w[4];
+  draw(id, c->seed, step, ORC_CH_COLL, 0, w);
+  if (!(u01(w[0]) < (double)s->p_null[1])) return;
+  tc->coll[4]++;
+  double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  double numax = (double)s->nu_max[1];
+  double b1 = c->n_gas * c->sigma_cx * speed;
+  if (b1 > numax) tc->viol++;
+  double r = u01(w[1]) * numax;
+  if (fabs(r - b1) < 1e-5 * numax) tc->near++;
+  if (r < b1) {
+    uint32_t a[4];
+    draw(id, c->seed, step, ORC_CH_SCAT, 0, a);
+    double n0, n1, n2, n3, vt = sqrt(c->Tg / c->mass[1]);
+    box_muller(w[2], w[3], &n0, &n1);
+    box_muller(a[0], a[1], &n2, &n3);
+    v[0] = vt * n0;
+    v[1] = vt * n1;
+    v[2] = vt * n2;
+    tc->coll[3]++;
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* One full step (R2).                                                                         */
+static int step_once(orc_sim* s) {
+  const orc_config* c = &s->cfg;
+  const int32_t N = s->N;
+  const uint64_t step = s->step;
+  int nth = g_threads;
+  orc_tcount tcs[2][MAX_THREADS];
+  orc_plist born[2][MAX_THREADS];
+  memset(tcs, 0, sizeof(tcs));
+  memset(born, 0, sizeof(born));
+  int err = ORC_OK;
+
+  for (int sp = 0; sp < 2; ++sp) {
+    if (c->frozen_mask & (1u << sp)) continue;
+    orc_species* p = &s->sp[sp];
+    unsigned char* alive = (unsigned char*)malloc(p->n ? p->n : 1);
+    double* eabs = (double*)malloc((p->n ? p->n : 1) * sizeof(double));
+    if (!alive || !eabs) {
+      free(alive);
+      free(eabs);
+      return ORC_ENOMEM;
+    }
+    int do_mcc = (sp == 0) ? ((c->coll_mask & (ORC_COLL_EL | ORC_COLL_EX | ORC_COLL_IZ)) != 0)
+                           : ((c->coll_mask & ORC_COLL_CX) != 0);
+    long long n = (long long)p->n;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nth) schedule(static)
+#endif
+    for (long long i = 0; i < n; ++i) {
+      int t = 0;
+#ifdef _OPENMP
+      t = omp_get_thread_num();
+#endif
+      orc_tcount* tc = &tcs[sp][t];
+      double xh = p->x[i];
+      /* gather: CIC interpolation of the node field (Sec. 2 "interpolating fields back") */
+      double Ex = 0.0;
+      if (c->field_mode == ORC_FIELD_SELF) {
+        int32_t cc = (int32_t)floor(xh);
+        double f = xh - (double)cc;
+        Ex = (1.0 - f) * s->E[cc] + f * s->E[cc + 1];
+      } else if (c->field_mode == ORC_FIELD_EXTERNAL) {
+        Ex = c->E_ext;
+      }
+      /* push (Sec. 2 "particle mover") */
+      double Ev[3] = {Ex, 0.0, 0.0};
+      double v[3] = {p->vx[i], p->vy[i], p->vz[i]};
+      orc_boris(s->qm[sp], c->dt, Ev, s->Bv, v);
+      xh += v[0] * c->dt / s->dx;
+      /* walls (Table 3: plasma absorbed at the walls) */
+      if (xh < 0.0 || xh >= (double)N) {
+        tc->wall_hits[xh < 0.0 ? 0 : 1]++;
+        eabs[i] = 0.5 * c->mass[sp] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * s->w[sp];
+        alive[i] = 0;
+        p->x[i] = xh;
+        p->vx[i] = v[0];
+        p->vy[i] = v[1];
+        p->vz[i] = v[2];
+        continue;
+      }
+      alive[i] = 1;
+      /* Monte Carlo collisions on survivors */
+      if (do_mcc) {
+        if (sp == 0) {
+          orc_newp e_new, i_new;
+          if (collide_electron(s, p->id[i], step, xh, v, tc, &e_new, &i_new)) {
+            if (plist_add(&born[0][t], e_new.x, e_new.v, e_new.id) != ORC_OK ||
+                plist_add(&born[1][t], i_new.x, i_new.v, i_new.id) != ORC_OK)
+              err = ORC_ENOMEM;
+          }
+        } else {
+          collide_ion(s, p->id[i], step, v, tc);
+        }
+      }
+      p->x[i] = xh;
+      p->vx[i] = v[0];
+      p->vy[i] = v[1];
+      p->vz[i] = v[2];
+    }
+    /* stable compaction of the survivors; absorbed energy summed in particle order so that the
+     * result does not depend on the thread count */
+    size_t k = 0;
+    for (size_t i = 0; i < p->n; ++i) {
+      if (!alive[i]) {
+        s->wall_energy[sp] += eabs[i];
+        continue;
+      }
+      p->x[k] = p->x[i];
+      p->vx[k] = p->vx[i];
+      p->vy[k] = p->vy[i];
+      p->vz[k] = p->vz[i];
+      p->id[k] = p->id[i];
+      ++k;
+    }
+    p->n = k;
+    free(alive);
+    free(eabs);
+  }
+  if (err != ORC_OK) return err;
+
+  /* merge the per-thread counters and append the births, in thread order */
+  uint64_t ion_losses = 0;
+  for (int sp = 0; sp < 2; ++sp) {
+    for (int t = 0; t < MAX_THREADS; ++t) {
+      orc_tcount* tc = &tcs[sp][t];
+      for (int side = 0; side < 2; ++side) {
+        s->wall_hits[sp][side] += tc->wall_hits[side];
+        s->wall_charge += (c->charge[sp] > 0 ? 1 : -1) * (int64_t)tc->wall_hits[side];
+      }
+      for (int k = 0; k < 5; ++k) s->coll[k] += tc->coll[k];
+      s->near[sp] += tc->near;
+      s->viol[sp] += tc->viol;
+      if (sp == 1) ion_losses += tc->wall_hits[0] + tc->wall_hits[1];
+    }
+  }
+  for (int sp = 0; sp < 2; ++sp) {
+    for (int t = 0; t < MAX_THREADS; ++t) {
+      orc_plist* l = &born[sp][t];
+      for (size_t k = 0; k < l->n; ++k) {
+        if (sp_push_back(&s->sp[sp], l->p[k].x, l->p[k].v, l->p[k].id) != ORC_OK) err = ORC_ENOMEM;
+      }
+      s->births[sp] += l->n;
+      free(l->p);
+    }
+  }
+  if (err != ORC_OK) return err;
+
+  /* source (R13): one pair per ion absorbed in this step */
+  if (c->source_mode == ORC_SOURCE_PAIRS) {
+    for (uint64_t k = 0; k < ion_losses; ++k) {
+      uint64_t ide = (1ull << 63) | ((step & 0x7FFFFFFFull) << 32) | (2 * k);
+      uint32_t w[4];
+      draw(ide, c->seed, step, ORC_CH_SOURCE, 0, w);
+      double x = c->source_x1 * u01(w[0]);
+      for (int sp = 0; sp < 2; ++sp) {
+        uint64_t id = ide + (uint64_t)sp;
+        double vt = sqrt(c->T[sp] / c->mass[sp]);
+        double n0, n1, n2, n3;
+        draw(id, c->seed, step, ORC_CH_SOURCE, 1, w);
+        box_muller(w[0], w[1], &n0, &n1);
+        box_muller(w[2], w[3], &n2, &n3);
+        double v[3] = {vt * n0, vt * n1, vt * n2};
+        if (sp_push_back(&s->sp[sp], x, v, id) != ORC_OK) return ORC_ENOMEM;
+      }
+    }
+    s->source_pairs += ion_losses;
+  }
+
+  /* deposit + Poisson + field */
+  deposit_and_solve(s);
+
+  /* arranger: sort + compaction every sort_interval steps */
+  if (step % (uint64_t)c->sort_interval == 0) {
+    for (int sp = 0; sp < 2; ++sp)
+      if (sort_species(&s->sp[sp], N) != ORC_OK) return ORC_ENOMEM;
+  }
+  s->step = step + 1;
+  return ORC_OK;
+}
+
+int orc_step(orc_sim* s, int32_t nsteps) {
+  if (!s || nsteps < 0) return ORC_EINVAL;
+  for (int32_t k = 0; k < nsteps; ++k) {
+    int e = step_once(s);
+    if (e != ORC_OK) return e;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return (x > y) - (x < y);
+}
+
+int orc_diag(orc_sim* s, orc_diag_t* d) {
+  if (!s || !d) return ORC_EINVAL;
+  memset(d, 0, sizeof(*d));
+  d->step = s->step;
+  for (int sp = 0; sp < 2; ++sp) {
+    d->n[sp] = s->sp[sp].n;
+    d->wall_hits[sp][0] = s->wall_hits[sp][0];
+    d->wall_hits[sp][1] = s->wall_hits[sp][1];
+    d->near_threshold[sp] = s->near[sp];
+    d->nu_max_violations[sp] = s->viol[sp];
+    d->births[sp] = s->births[sp];
+    d->wall_energy[sp] = s->wall_energy[sp];
+    /* kinetic energy summed in ascending order of the terms: independent of storage order */
+    orc_species* p = &s->sp[sp];
+    double* e = (double*)malloc((p->n ? p->n : 1) * sizeof(double));
+    if (!e) return ORC_ENOMEM;
+    for (size_t i = 0; i < p->n; ++i)
+      e[i] = 0.5 * s->cfg.mass[sp] * (p->vx[i] * p->vx[i] + p->vy[i] * p->vy[i] + p->vz[i] * p->vz[i]);
+    qsort(e, p->n, sizeof(double), cmp_double);
+    double ke = 0.0;
+    for (size_t i = 0; i < p->n; ++i) ke += e[i];
+    free(e);
+    d->ke[sp] = ke * s->w[sp];
+  }
+  for (int k = 0; k < 5; ++k) d->coll[k] = s->coll[k];
+  d->source_pairs = s->source_pairs;
+  d->wall_charge = s->wall_charge;
+  int64_t q = 0;
+  for (int32_t j = 0; j <= s->N; ++j)
+    for (int sp = 0; sp < 2; ++sp) q += (s->cfg.charge[sp] > 0 ? 1 : -1) * s->R[sp][j];
+  d->net_charge_units = q;
+  double fe = 0.0;
+  for (int32_t j = 0; j <= s->N; ++j) {
+    double wgt = (j == 0 || j == s->N) ? 0.5 : 1.0;
+    fe += wgt * 0.5 * s->E[j] * s->E[j] * s->dx;
+  }
+  d->field_energy = fe;
+  return ORC_OK;
+}
+
+int orc_fields(orc_sim* s, int64_t* R, double* rho, double* phi, double* E) {
+  if (!s) return ORC_EINVAL;
+  size_t nn = (size_t)s->N + 1;
+  if (R) {
+    memcpy(R, s->R[0], nn * sizeof(int64_t));
+    memcpy(R + nn, s->R[1], nn * sizeof(int64_t));
+  }
+  if (rho) memcpy(rho, s->rho, nn * sizeof(double));
+  if (phi) memcpy(phi, s->phi, nn * sizeof(double));
+  if (E) memcpy(E, s->E, nn * sizeof(double));
+  return ORC_OK;
+}
+
+uint64_t orc_count(orc_sim* s, int species) {
+  if (!s || species < 0 || species > 1) return 0;
+  return s->sp[species].n;
+}
+
+int orc_particles(orc_sim* s, int species, double* x, double* v, uint64_t* id) {
+  if (!s || species < 0 || species > 1) return ORC_EINVAL;
+  orc_species* p = &s->sp[species];
+  for (size_t i = 0; i < p->n; ++i) {
+    if (x) x[i] = p->x[i];
+    if (v) {
+      v[3 * i] = p->vx[i];
+      v[3 * i + 1] = p->vy[i];
+      v[3 * i + 2] = p->vz[i];
+    }
+    if (id) id[i] = p->id[i];
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Snapshot blob, version 1, little-endian, no padding:
+ *   "PICMCSN1" | u32 version | u32 0 | u64 config hash | u64 step | u64 n[2] |
+ *   u64 wall_hits[2][2] | u64 coll[5] | u64 near[2] | u64 viol[2] | u64 births[2] |
+ *   u64 source_pairs | u64 dropped | i64 wall_charge | f64 wall_energy[2] |
+ *   per species: i32 cell[n] | f64 frac[n] | f64 vx[n] | f64 vy[n] | f64 vz[n] | u64 id[n] |
+ *   u32 CRC-32 (IEEE 802.3, reflected, as zlib) of everything before it.
+ * Particles are written in ascending id order within a species (canonical order), so two runs
+ * that hold the same particle set write the same bytes.  This mirrors the checkpoint semantics
+ * of Sec. 4.1 (per-species particle records; restart rebuilds positions and velocities).      */
+#define SNAP_MAGIC "PICMCSN1"
+#define SNAP_HDR (8 + 4 + 4 + 8 + 8 + 16 + 17 * 8 + 8 + 16)
+
+static uint32_t crc32_ieee(const unsigned char* p, size_t n) {
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) {
+    c ^= p[i];
+    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+  }
+  return c ^ 0xFFFFFFFFu;
+}
+
+static void fnv_bytes(uint64_t* h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    *h ^= b[i];
+    *h *= 0x100000001b3ull;
+  }
+}
+
+uint64_t orc_config_hash(const orc_config* c) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  int32_t iv[6] = {c->ncells, c->ppc[0], c->ppc[1], c->load_profile, c->profile_mode,
+                   c->source_mode};
+  uint32_t uv[3] = {c->coll_mask, c->field_mode, c->frozen_mask};
+  double dv[25] = {c->L,        c->dt,          c->mass[0],  c->mass[1],  c->charge[0],
+                   c->charge[1], c->T[0],       c->T[1],     c->Tg,       c->m_gas,
+                   c->B,        c->B_angle_deg, c->V_left,   c->V_right,  c->n_gas,
+                   c->sigma_el, c->sigma_ex,    c->E_ex,     c->sigma_iz, c->E_iz,
+                   c->sigma_cx, c->E_cap,       c->E_ext,    c->profile_scale,
+                   c->source_x1};
+  fnv_bytes(&h, iv, sizeof(iv));
+  fnv_bytes(&h, uv, sizeof(uv));
+  fnv_bytes(&h, dv, sizeof(dv));
+  fnv_bytes(&h, &c->seed, sizeof(uint64_t));
+  return h;
+}
+
+typedef struct {
+  const uint64_t* id;
+  size_t i;
+} idx_key;
+
+static int cmp_key(const void* a, const void* b) {
+  const idx_key* x = (const idx_key*)a;
+  const idx_key* y = (const idx_key*)b;
+  uint64_t u = x->id[x->i], v = y->id[y->i];
+  return (u > v) - (u < v);
+}
+
+static void put(unsigned char** q, const void* src, size_t n) {
+  memcpy(*q, src, n);
+  *q += n;
+}
+
+int orc_snapshot(orc_sim* s, void* buf, size_t cap, size_t* needed) {
+  if (!s) return ORC_EINVAL;
+  size_t need = SNAP_HDR + 4;
+  for (int sp = 0; sp < 2; ++sp) need += s->sp[sp].n * 44;
+  if (needed) *needed = need;
+  if (!buf) return ORC_OK;
+  if (cap < need) return ORC_EINVAL;
+  unsigned char* q = (unsigned char*)buf;
+  uint32_t ver = 1, zero = 0;
+  uint64_t h = orc_config_hash(&s->cfg), dropped = 0;
+  put(&q, SNAP_MAGIC, 8);
+  put(&q, &ver, 4);
+  put(&q, &zero, 4);
+  put(&q, &h, 8);
+  put(&q, &s->step, 8);
+  for (int sp = 0; sp < 2; ++sp) {
+    uint64_t n = s->sp[sp].n;
+    put(&q, &n, 8);
+  }
+  put(&q, s->wall_hits, 32);
+  put(&q, s->coll, 40);
+  put(&q, s->near, 16);
+  put(&q, s->viol, 16);
+  put(&q, s->births, 16);
+  put(&q, &s->source_pairs, 8);
+  put(&q, &dropped, 8);
+  put(&q, &s->wall_charge, 8);
+  put(&q, s->wall_energy, 16);
+  for (int sp = 0; sp < 2; ++sp) {
+    orc_species* p = &s->sp[sp];
+    size_t n = p->n;
+    idx_key* ord = (idx_key*)malloc((n ? n : 1) * sizeof(idx_key));
+    if (!ord) return ORC_ENOMEM;
+    for (size_t i = 0; i < n; ++i) {
+      ord[i].id = p->id;
+      ord[i].i = i;
+    }
+    qsort(ord, n, sizeof(idx_key), cmp_key);
+    for (size_t k = 0; k < n; ++k) {
+      int32_t cc = (int32_t)floor(p->x[ord[k].i]);
+      put(&q, &cc, 4);
+    }
+    for (size_t k = 0; k < n; ++k) {
+      double xh = p->x[ord[k].i];
+      double f = xh - floor(xh);
+      put(&q, &f, 8);
+    }
+    double* arrs[3] = {p->vx, p->vy, p->vz};
+    for (int a = 0; a < 3; ++a)
+      for (size_t k = 0; k < n; ++k) put(&q, &arrs[a][ord[k].i], 8);
+    for (size_t k = 0; k < n; ++k) put(&q, &p->id[ord[k].i], 8);
+    free(ord);
+  }
+  uint32_t crc = crc32_ieee((const unsigned char*)buf, (size_t)(q - (unsigned char*)buf));
+  put(&q, &crc, 4);
+  return ORC_OK;
+}
+
+static void get(const unsigned char** q, void* dst, size_t n) {
+  memcpy(dst, *q, n);
+  *q += n;
+}
+
+int orc_restore(orc_sim* s, const void* buf, size_t len) {
+  if (!s || !buf) return ORC_EINVAL;
+  const unsigned char* b = (const unsigned char*)buf;
+  if (len < SNAP_HDR + 4 || memcmp(b, SNAP_MAGIC, 8) != 0) return ORC_ECORRUPT;
+  uint32_t crc;
+  memcpy(&crc, b + len - 4, 4);
+  if (crc != crc32_ieee(b, len - 4)) return ORC_ECORRUPT;
+  const unsigned char* q = b + 8;
+  uint32_t ver, zero;
+  uint64_t h, step, n[2], dropped;
+  get(&q, &ver, 4);
+  get(&q, &zero, 4);
+  get(&q, &h, 8);
+  if (ver != 1 || h != orc_config_hash(&s->cfg)) return ORC_ECORRUPT;
+  get(&q, &step, 8);
+  get(&q, &n[0], 8);
+  get(&q, &n[1], 8);
+  if (len != SNAP_HDR + 4 + 44 * (n[0] + n[1])) return ORC_ECORRUPT;
+  get(&q, s->wall_hits, 32);
+  get(&q, s->coll, 40);
+  get(&q, s->near, 16);
+  get(&q, s->viol, 16);
+  get(&q, s->births, 16);
+  get(&q, &s->source_pairs, 8);
+  get(&q, &dropped, 8);
+  get(&q, &s->wall_charge, 8);
+  get(&q, s->wall_energy, 16);
+  s->step = step;
+  for (int sp = 0; sp < 2; ++sp) {
+    orc_species* p = &s->sp[sp];
+    if (sp_reserve(p, n[sp]) != ORC_OK) return ORC_ENOMEM;
+    const unsigned char* cell = q;
+    const unsigned char* frac = cell + 4 * n[sp];
+    const unsigned char* vx = frac + 8 * n[sp];
+    const unsigned char* vy = vx + 8 * n[sp];
+    const unsigned char* vz = vy + 8 * n[sp];
+    const unsigned char* id = vz + 8 * n[sp];
+    for (size_t i = 0; i < n[sp]; ++i) {
+      int32_t cc;
+      double f;
+      memcpy(&cc, cell + 4 * i, 4);
+      memcpy(&f, frac + 8 * i, 8);
+      if (cc < 0 || cc >= s->N || !(f >= 0.0 && f < 1.0)) return ORC_ECORRUPT;
+      p->x[i] = (double)cc + f;
+      if (p->x[i] >= (double)cc + 1.0) p->x[i] = nextafter((double)cc + 1.0, 0.0);
+      memcpy(&p->vx[i], vx + 8 * i, 8);
+      memcpy(&p->vy[i], vy + 8 * i, 8);
+      memcpy(&p->vz[i], vz + 8 * i, 8);
+      memcpy(&p->id[i], id + 8 * i, 8);
+    }
+    p->n = n[sp];
+    q = id + 8 * n[sp];
+  }
+  for (int sp = 0; sp < 2; ++sp) sort_species(&s->sp[sp], s->N);
+  deposit_and_solve(s);
+  return ORC_OK;
+}

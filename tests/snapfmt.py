@@ -1,0 +1,95 @@
+"""Reader/writer of the version-1 snapshot blob, for building test inputs.
+
+Format (little-endian, no padding): "PICMCSN1" | u32 version | u32 0 | u64 config hash |
+u64 step | u64 n[2] | u64 counters[17] | i64 wall_charge | f64 wall_energy[2] | per species:
+i32 cell[n], f64 frac[n], f64 vx[n], f64 vy[n], f64 vz[n], u64 id[n] | u32 CRC-32 (zlib).
+Counters: wall_hits[2][2], coll[5], near[2], viol[2], births[2], source_pairs, dropped.
+
+This is input plumbing only: it splices particle arrays into a header taken from an existing
+blob and recomputes the checksum.  It holds none of the method's arithmetic.
+"""
+from __future__ import annotations
+
+import struct
+import zlib
+
+import numpy as np
+
+HDR = 8 + 4 + 4 + 8 + 8 + 16 + 17 * 8 + 8 + 16
+
+
+def parse(blob: bytes) -> dict:
+    assert blob[:8] == b"PICMCSN1"
+    ver, _z, h, step, n0, n1 = struct.unpack_from("<IIQQQQ", blob, 8)
+    counters = np.frombuffer(blob, np.uint64, 17, 48).copy()
+    wall_charge = struct.unpack_from("<q", blob, 48 + 17 * 8)[0]
+    wall_energy = np.frombuffer(blob, np.float64, 2, 48 + 17 * 8 + 8).copy()
+    off = HDR
+    sp = []
+    for n in (n0, n1):
+        cell = np.frombuffer(blob, np.int32, n, off).copy(); off += 4 * n
+        frac = np.frombuffer(blob, np.float64, n, off).copy(); off += 8 * n
+        v = np.stack([np.frombuffer(blob, np.float64, n, off + 8 * n * k) for k in range(3)], 1)
+        off += 24 * n
+        ids = np.frombuffer(blob, np.uint64, n, off).copy(); off += 8 * n
+        sp.append({"cell": cell, "frac": frac, "v": v.copy(), "id": ids})
+    crc = struct.unpack_from("<I", blob, off)[0]
+    assert off + 4 == len(blob)
+    return {"version": ver, "hash": h, "step": step, "counters": counters,
+            "wall_charge": wall_charge, "wall_energy": wall_energy, "species": sp, "crc": crc}
+
+
+def build(d: dict) -> bytes:
+    """Inverse of ``parse``; particles are written in ascending id order (canonical)."""
+    sp = d["species"]
+    out = bytearray(b"PICMCSN1")
+    out += struct.pack("<IIQQQQ", 1, 0, d["hash"], d["step"], len(sp[0]["id"]), len(sp[1]["id"]))
+    out += np.asarray(d["counters"], np.uint64).tobytes()
+    out += struct.pack("<q", int(d["wall_charge"]))
+    out += np.asarray(d["wall_energy"], np.float64).tobytes()
+    for s in sp:
+        o = np.argsort(np.asarray(s["id"], np.uint64), kind="stable")
+        out += np.asarray(s["cell"], np.int32)[o].tobytes()
+        out += np.asarray(s["frac"], np.float64)[o].tobytes()
+        v = np.asarray(s["v"], np.float64)[o]
+        for k in range(3):
+            out += np.ascontiguousarray(v[:, k]).tobytes()
+        out += np.asarray(s["id"], np.uint64)[o].tobytes()
+    out += struct.pack("<I", zlib.crc32(bytes(out)) & 0xFFFFFFFF)
+    return bytes(out)
+
+
+def with_particles(blob: bytes, species: list, step: int | None = None) -> bytes:
+    """Replace the particles of ``blob``; ``species[s]`` has x (dx units), v (n x 3), id."""
+    d = parse(blob)
+    d["counters"] = np.zeros(17, np.uint64)
+    d["wall_charge"] = 0
+    d["wall_energy"] = np.zeros(2)
+    if step is not None:
+        d["step"] = step
+    new = []
+    for s in species:
+        x = np.asarray(s["x"], np.float64)
+        cell = np.floor(x).astype(np.int32)
+        new.append({"cell": cell, "frac": x - cell, "v": np.asarray(s["v"], np.float64).reshape(-1, 3),
+                    "id": np.asarray(s["id"], np.uint64)})
+    d["species"] = new
+    return build(d)
+
+
+def round_to_fp32(blob: bytes) -> bytes:
+    """Round positions (within the cell) and velocities to FP32-representable values."""
+    d = parse(blob)
+    for s in d["species"]:
+        f32 = s["frac"].astype(np.float32)
+        wrap = f32 >= np.float32(1.0)
+        f32[wrap] = 0.0
+        s["cell"] = s["cell"] + wrap.astype(np.int32)
+        s["frac"] = f32.astype(np.float64)
+        s["v"] = s["v"].astype(np.float32).astype(np.float64)
+    return build(d)
+
+
+def canonical_particles(blob: bytes):
+    """(cell, frac, v, id) per species in id order, as parsed."""
+    return parse(blob)["species"]
