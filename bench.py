@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Throughput of the 1D3V PIC Monte Carlo step on GB300: particle-steps/s and HBM roofline.
+
+Default workload: the non-uniform-load case (65536 cells, 100,007,936 particles, density
+~ exp(-x/(L/8)), pair source, B = 0.5 at 30 degrees, all four collision processes, per-cell
+counting sort every 10 steps), FP32 particle path with int64 fixed-point deposit.  A "step" is one
+full PIC MC step (gather, push, walls, MCC, deposit, source, Poisson, and the sort on every tenth
+step).  Inputs (2.8 GB of particles) are larger than L2, so no flush is needed between steps.
+
+Lines printed (rank 0): one JSON object.  ``--impl reference`` times the plain FP64 CPU oracle
+(the reference of this build) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2606_28534_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s & HBM roofline %, FP32/batched vs plain FP64 grid, 1 GB300"
+BYTES_STEP_KERNEL = 48  # algorithmic bytes per particle per step kernel: 28 read + 20 written
+BYTES_SORT = 56         # per particle per sort: 28 read + 28 written
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.idx)], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [t.strip() for t in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------------
+def cpu_baseline(params: dict, seconds: float) -> dict:
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample of the workload."""
+    from oracle import oracle as O
+
+    cores = len(os.sched_getaffinity(0))
+    sample = W.variant(params, ppc=(max(1, params["ppc"][0] // 64), max(1, params["ppc"][1] // 64)))
+    sim = O.OracleSim(sample, threads=cores)
+    sim.step(1)  # warm-up (first touch)
+    ps = 0
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 2 or time.perf_counter() - t0 < seconds:
+        ps += sim.count(0) + sim.count(1)  # live particles at the start of the step
+        sim.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    sim.close()
+    return {"value": ps / dt, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+            "sample": (f"same workload with ppc/64 ({sample['ppc'][0] * sample['ncells'] * 2:,} "
+                       f"particles, {sample['ncells']} cells), {steps} steps, {dt:.1f} s, "
+                       f"{cores} OpenMP threads")}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    params = W.CONFIGS[args.workload]
+    per_step = []
+    total_ps, total_t = 0, 0.0
+    from oracle import oracle as O
+
+    cores = len(os.sched_getaffinity(0))
+    sample = W.variant(params, ppc=(max(1, params["ppc"][0] // 64), max(1, params["ppc"][1] // 64)))
+    sim = O.OracleSim(sample, threads=cores)
+    sim.step(max(1, min(args.warmup, 3)))
+    for _ in range(args.steps):
+        ps = sim.count(0) + sim.count(1)  # live particles at the start of the step
+        t0 = time.perf_counter()
+        sim.step(1)
+        dt = time.perf_counter() - t0
+        per_step.append(dt)
+        total_ps += ps
+        total_t += dt
+    value = total_ps / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {W_DESC[args.workload]}",
+                   "sample": f"ppc/64 of the workload, {args.steps} steps"},
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"same workload with ppc/64, {args.steps} timed steps"},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+W_DESC = {
+    "c1": "plain PIC MC, 256 cells, 51,200 particles",
+    "c2": "uniform load, 4096 cells, 8,192,000 particles, B 0.5 @ 30 deg, 4 processes",
+    "c3": "non-uniform load, 65536 cells, 100,007,936 particles, exp(-x/(L/8)) + pair source, "
+          "B 0.5 @ 30 deg, 4 processes, sort every 10 steps",
+    "c5": "collisionless, 1024 cells, 409,600 particles",
+}
+
+
+# ------------------------------------------------------------------------------------------------
+def timed_run(sim, torch, steps: int, profile: bool):
+    """K steps on the device between two events on the library's stream (bracketed by syncs)."""
+    ps0 = sim.diag()["particle_steps"]
+    torch.cuda.synchronize()
+    if profile:
+        sim.profile(True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(sim.stream)
+    sim.step(steps)
+    b.record(sim.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    kt = None
+    if profile:
+        kt = sim.kernel_times()
+        sim.profile(False)
+    ps = sim.diag()["particle_steps"] - ps0
+    return ms, ps, kt
+
+
+def run_ours(args, rank: int, world: int, local: int) -> None:
+    import torch
+
+    from paper_2606_28534_gb300 import build, pic
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allmax(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def allsum(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t)
+        return float(t.item())
+
+    # replicas: every rank advances its own simulation (seed + rank); no data-path collective
+    params = W.variant(W.CONFIGS[args.workload], seed=W.CONFIGS[args.workload]["seed"] + 1000 * rank)
+    sim = pic.Simulation(params)
+    sim.step(args.warmup)
+    sim.sync()
+
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ms, ps, kt = timed_run(sim, torch, args.steps, profile=True)
+    barrier()
+    clk = clocks.stop() if clocks else None
+    ms_max = allmax(ms)
+    ps_all = allsum(ps)
+    value = ps_all / (ms_max / 1000.0)
+
+    peak, peak_kind = _peaks()
+    step_ms = kt["step"]["ms"] / max(1, kt["step"]["launches"])
+    bytes_per_launch = BYTES_STEP_KERNEL * ps / max(1, kt["step"]["launches"])
+    achieved = bytes_per_launch / (step_ms / 1000.0) / 1e9
+    kernel_shares = {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in kt.values())), 4)
+                     for k, v in kt.items() if v["launches"]}
+
+    # plain FP64 path on the same workload (the baseline the FP32 path is compared with)
+    plain = None
+    if not args.no_plain:
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        pp = W.variant(params, precision=W.PRECISION_FP64_PLAIN)
+        ps_sim = pic.Simulation(pp)
+        ps_sim.step(min(args.warmup, 5))
+        ksteps = max(3, min(args.steps, args.plain_steps))
+        pms, pps, _ = timed_run(ps_sim, torch, ksteps, profile=False)
+        plain = {"value": allsum(pps) / (allmax(pms) / 1000.0), "unit": "particle-steps/s",
+                 "ms_per_step": pms / ksteps, "steps": ksteps, "dtype": "f64"}
+        ps_sim.close()
+        del ps_sim
+        torch.cuda.empty_cache()
+        sim = None
+
+    # end to end through the public API: restart from a host checkpoint blob (pinned memory),
+    # then steps with a device-to-host read of the diagnostics after every step
+    e2e = None
+    if not args.no_e2e:
+        src = pic.Simulation(params)
+        src.step(args.warmup)
+        blob = src.snapshot()
+        src.close()
+        del src
+        pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
+        pinned.numpy()[:] = memoryview(blob)
+        del blob
+        ek = max(3, min(args.steps, args.e2e_steps))
+        sim2 = pic.Simulation(params)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = pic.lib().pic_restore(sim2._h, pinned.data_ptr(), pinned.numel())
+        if rc != 0:
+            raise RuntimeError(f"pic_restore failed: {rc}")
+        dsum = 0
+        for _ in range(ek):
+            sim2.step(1)
+            dsum = sim2.diag()["particle_steps"]
+        torch.cuda.synchronize()
+        et = time.perf_counter() - t0
+        barrier()
+        et = allmax(et)
+        diag_bytes = 8 * 3 * (params["ncells"] + 1) + 512
+        e2e = {"value": allsum(dsum) / et, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(pinned.numel() / ek), "d2h_bytes_per_step": diag_bytes,
+               "steps": ek, "what": "pic_restore from a pinned host checkpoint + per step "
+                                    "pic_step(1) and pic_diag (device-to-host read)"}
+        sim2.close()
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {W_DESC[args.workload]}",
+                   "precision": "FP32 particles/field, int64 fixed-point deposit, FP64 Poisson",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (2.8 GB of particles); no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_step32",
+                     "peak_kind": peak_kind,
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": step_ms},
+        "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in kt.items()
+                    if v["launches"]},
+        "kernel_shares": kernel_shares,
+        "gpu_launches": int(sum(v["launches"] for v in kt.values())),
+        "clocks": clk,
+        "fp64_plain": plain,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(W.CONFIGS[args.workload], args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(W.CONFIGS), default="c3")
+    ap.add_argument("--plain-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

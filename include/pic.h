@@ -1,0 +1,200 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) 1D3V electrostatic particle-in-cell Monte Carlo step.
+ *
+ * The operation is the PIC MC cycle of the paper (Sec. 2, "Background"): particle mover,
+ * deposition of charge to the grid, field solve, interpolation of the field back to the
+ * particles, and Monte Carlo collisions, for the bounded high-density sheath model of Table 3
+ * (a magnetised plasma between two absorbing walls with a neutral background), advanced by
+ * BIT1-style "natural sorting" of particles per cell (Sec. 2).  Checkpoint/restart semantics
+ * (per-species particle records from which the run resumes exactly) follow Sec. 4.1.
+ *
+ * Conventions for every call:
+ *  - Return value: PIC_OK (0) or one of the PIC_E* codes below; pic_strerror() names it.
+ *  - A handle owns all device state of one simulation.  The caller owns every host buffer it
+ *    passes.  No call is thread-safe on one handle; distinct handles are independent.
+ *  - Work is enqueued on the CUDA stream given to pic_init (NULL = the legacy default stream).
+ *    pic_step returns without waiting; device-side errors (capacity overflow, a bounded wait
+ *    that gave up, a bounds check) surface at the next synchronising call: pic_diag,
+ *    pic_snapshot, pic_get_field or pic_sync.
+ *  - Units: lengths in Debye lengths, time in 1/omega_pe, m_e = e = eps0 = n0 = T_e = 1.
+ *    Positions are kept cell-local: an int32 cell index and a fraction in [0, 1).
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_ABI_VERSION 1u
+
+/* status codes */
+#define PIC_OK 0
+#define PIC_EINVAL 1    /* invalid argument or configuration */
+#define PIC_ENOMEM 2    /* device or host allocation failed, or workspace too small */
+#define PIC_ECUDA 3     /* a CUDA runtime call failed */
+#define PIC_EOVERFLOW 4 /* particle capacity exceeded (particles were dropped) */
+#define PIC_ECORRUPT 5  /* snapshot blob: bad magic, version, checksum, size or config hash */
+#define PIC_ETIMEOUT 6  /* a bounded device-side wait gave up */
+#define PIC_EDEVICE 7   /* a device-side check failed (error flag set by a kernel) */
+
+/* arithmetic of the particle path */
+#define PIC_FP32 0u       /* FP32 particles and field, int64 fixed-point deposit, sorted */
+#define PIC_FP64_PLAIN 1u /* FP64 particles, FP64 atomic deposit, unsorted (the plain baseline) */
+
+/* collision processes (bit mask), Sec. 2 "MC collision handling" */
+#define PIC_COLL_EL 1u /* electron-neutral elastic, constant cross section */
+#define PIC_COLL_EX 2u /* electron-neutral excitation, linear above E_ex, saturating at 2 E_ex */
+#define PIC_COLL_IZ 4u /* electron-impact ionization, linear above E_iz, saturating at 2 E_iz */
+#define PIC_COLL_CX 8u /* ion-neutral charge exchange, constant cross section */
+
+/* field modes */
+#define PIC_FIELD_SELF 0u     /* self-consistent Poisson field */
+#define PIC_FIELD_EXTERNAL 1u /* particles see a uniform E_x = E_ext (Poisson still solved) */
+#define PIC_FIELD_ZERO 2u     /* particles see no electric field */
+
+/* load profiles */
+#define PIC_LOAD_UNIFORM 0    /* ppc particles per cell, uniformly random inside the cell */
+#define PIC_LOAD_EXP 1        /* density ~ exp(-x/lambda), lambda = profile_scale (cells) */
+#define PIC_LOAD_QUIET_SINE 2 /* evenly spaced; species 0 displaced by A sin(2 pi m x / L) */
+
+/* particle sources */
+#define PIC_SOURCE_NONE 0
+#define PIC_SOURCE_PAIRS 1 /* each step, one (e, ion) pair per ion absorbed in that step,
+                              uniform in [0, source_x1), Maxwellian at T[0], T[1] */
+
+/* Configuration.  Plain old data; abi_version must be PIC_ABI_VERSION.  Species 0 are the
+ * electrons (the only species that ionize, excite and scatter elastically); species 1 are the
+ * ions (charge exchange).  Weight of a macro-particle: w_s = dx / ppc_s (n0 = 1). */
+typedef struct pic_config {
+  uint32_t abi_version;
+  uint32_t precision;     /* PIC_FP32 or PIC_FP64_PLAIN */
+  int32_t ncells;         /* N >= 2 cells, N + 1 nodes; PIC_FP32 needs N <= 262143 */
+  int32_t ppc[2];         /* mean particles per cell per species (>= 1) */
+  int32_t load_profile;   /* PIC_LOAD_* */
+  int32_t profile_mode;   /* mode number m of PIC_LOAD_QUIET_SINE */
+  int32_t source_mode;    /* PIC_SOURCE_* */
+  int32_t sort_interval;  /* sort + compact after steps with step % sort_interval == 0 */
+  uint32_t coll_mask;     /* PIC_COLL_* */
+  uint32_t field_mode;    /* PIC_FIELD_* */
+  uint32_t frozen_mask;   /* bit s set: species s is neither pushed nor collided */
+  double L;               /* domain length; dx = L / N */
+  double dt;              /* time step */
+  double mass[2];         /* species masses */
+  double charge[2];       /* species charges (nonzero) */
+  double T[2];            /* initial temperatures */
+  double Tg;              /* neutral gas temperature (new ions, charge exchange) */
+  double m_gas;           /* neutral mass (elastic energy transfer 2 m / m_gas) */
+  double B;               /* |B|, in units where the electron cyclotron frequency is |B| */
+  double B_angle_deg;     /* angle of B to the wall normal x, B in the x-y plane */
+  double V_left, V_right; /* wall potentials */
+  double n_gas;           /* neutral density */
+  double sigma_el;        /* elastic cross section */
+  double sigma_ex, E_ex;  /* excitation cross-section scale and threshold */
+  double sigma_iz, E_iz;  /* ionization cross-section scale and threshold */
+  double sigma_cx;        /* charge-exchange cross section */
+  double E_cap;           /* null-collision bound uses E_cap + |V_left - V_right| */
+  double E_ext;           /* uniform field of PIC_FIELD_EXTERNAL */
+  double profile_scale;   /* PIC_LOAD_EXP scale length / PIC_LOAD_QUIET_SINE amplitude (cells) */
+  double source_x1;       /* end of the source region (cells), 0 < source_x1 <= N */
+  double capacity_factor; /* particle buffer capacity per species = factor * ppc * N (>= 1) */
+  uint64_t seed;          /* XORed into every particle's random-number key */
+} pic_config;
+
+/* Diagnostics (cumulative since pic_init unless stated). */
+typedef struct pic_diag {
+  uint64_t step;                 /* steps taken */
+  uint64_t n[2];                 /* live particles per species (exact) */
+  uint64_t wall_hits[2][2];      /* [species][0 = left, 1 = right] absorbed particles */
+  uint64_t coll[5];              /* e elastic, e excitation, e ionization, ion CX, candidates */
+  uint64_t near_threshold[2];    /* candidate draws within 1e-5 relative of a process boundary */
+  uint64_t nu_max_violations[2]; /* candidates whose total collision frequency exceeded nu_max */
+  uint64_t births[2];            /* particles created by ionization */
+  uint64_t source_pairs;         /* pairs injected by the source */
+  uint64_t dropped;              /* particles lost because a buffer was full */
+  int64_t net_charge_units;      /* sum over nodes and species of sign(q) R, 2^-32 particle units */
+  int64_t wall_charge;           /* sum over absorbed particles of sign(q) */
+  double ke[2];                  /* sum of 0.5 m v^2 w over live particles (half step) */
+  double field_energy;           /* sum_j 0.5 E_j^2 dx, half weight at the two walls */
+  double wall_energy[2];         /* sum of 0.5 m v^2 w over absorbed particles */
+  uint64_t particle_steps;       /* sum over steps of the live particles at the start of each
+                                    step, since pic_init / pic_restore (the throughput unit) */
+} pic_diag_t;
+
+typedef struct pic_handle pic_handle;
+
+/* Bytes of device workspace that pic_init needs for cfg (capacity, sort buffers, grids). */
+int pic_workspace_size(const pic_config* cfg, size_t* bytes);
+
+/* Create a simulation: validate cfg, carve the caller's device workspace (256-byte aligned,
+ * >= pic_workspace_size bytes; it must outlive the handle) or, when workspace is NULL, allocate
+ * it with cudaMalloc (freed by pic_free).  Loads the particles (Philox keyed by particle id),
+ * deposits, solves the field and sorts.  cuda_stream is a cudaStream_t (NULL = default).
+ * On success *out owns the state; on failure *out is NULL. */
+int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, void* cuda_stream,
+             pic_handle** out);
+
+/* Enqueue n >= 0 steps (gather, Boris push, walls, null-collision MC, deposit, source,
+ * Poisson, and the per-cell counting sort + compaction on steps with step % sort_interval
+ * == 0).  Asynchronous on the handle's stream. */
+int pic_step(pic_handle* h, int32_t n);
+
+/* Wait for the stream and report device-side errors (PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_EDEVICE). */
+int pic_sync(pic_handle* h);
+
+/* Serialise the state into buf (host memory, cap bytes).  buf == NULL: only *needed is set.
+ * Version-1 blob, little-endian: "PICMCSN1", u32 version, u32 0, u64 config hash, u64 step,
+ * u64 n[2], u64 counters[17], i64 wall_charge, f64 wall_energy[2], then per species
+ * i32 cell[n], f64 frac[n], f64 vx[n], f64 vy[n], f64 vz[n], u64 id[n] in ascending id order,
+ * then the CRC-32 (IEEE, as zlib) of all preceding bytes.  Synchronises the stream. */
+int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed);
+
+/* Replace the state by a blob from pic_snapshot (or any writer of the same format) made with
+ * the same physics configuration (config hash), then redeposit and re-solve the field.
+ * PIC_ECORRUPT on any format error; PIC_EOVERFLOW if a species exceeds the capacity.
+ * Positions and velocities are rounded to FP32 under PIC_FP32.  Synchronises the stream. */
+int pic_restore(pic_handle* h, const void* buf, size_t len);
+
+/* Diagnostics; synchronises the stream and reduces on the device. */
+int pic_diag(pic_handle* h, pic_diag_t* out);
+
+/* Copy the grid to host buffers of nnodes = N + 1 entries each (any may be NULL):
+ * R: 2 x (N+1) int64 deposits (2^-32 particle units), rho, phi: FP64, E: FP32 node field as
+ * seen by the particles.  Synchronises the stream. */
+int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E, size_t nnodes);
+
+/* Per-kernel device time via CUDA events on the handle's stream.  enable != 0 starts recording
+ * (adds two event records per launch); pic_kernel_times synchronises and returns, for up to
+ * nkinds kernel kinds, total milliseconds, launch counts and names. */
+#define PIC_KERNEL_KINDS 8
+int pic_profile(pic_handle* h, int enable);
+int pic_kernel_times(pic_handle* h, double* ms, uint64_t* launches, const char** names,
+                     int32_t nkinds);
+
+/* Destroy the handle (synchronises; frees what pic_init allocated). */
+void pic_free(pic_handle* h);
+
+const char* pic_strerror(int status);
+
+/* ---- single operations, on caller-owned device buffers ------------------------------------ */
+
+/* Philox4x32-10 (Salmon et al., SC'11; the generator of the MC draws): out[4i..4i+3] =
+ * Philox(ctr[4i..4i+3], key[2i..2i+1]) for i < n.  Device pointers; asynchronous on stream. */
+int pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
+               void* cuda_stream);
+
+/* Field solve of the PIC cycle (Sec. 2 "field solver"): the interior problem
+ * -phi_{j-1} + 2 phi_j - phi_{j+1} = dx^2 rho_j, phi_0 = V_L, phi_N = V_R, solved exactly by
+ * the discrete Green's function (two prefix scans in FP64), then E_j = (phi_{j-1}-phi_{j+1})/2dx
+ * inside and Gauss's law over the half cell at each wall.  rho, phi, E: N + 1 FP64 device
+ * values.  Needs no workspace; 2 <= N <= 262143.  Asynchronous on stream. */
+int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double V_R,
+                double* phi, double* E, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

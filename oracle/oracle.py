@@ -53,6 +53,7 @@ class OrcDiag(C.Structure):
         ("source_pairs", C.c_uint64), ("dropped", C.c_uint64),
         ("net_charge_units", C.c_int64), ("wall_charge", C.c_int64), ("ke", C.c_double * 2),
         ("field_energy", C.c_double), ("wall_energy", C.c_double * 2),
+        ("particle_steps", C.c_uint64),
     ]
 
 
@@ -105,6 +106,9 @@ def lib():
         L.orc_config_hash.argtypes = [P(OrcConfig)]
         L.orc_config_hash.restype = C.c_uint64
         L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_load_particle.argtypes = [P(OrcConfig), C.c_int, C.c_uint64, P(C.c_double),
+                                        P(C.c_double), P(C.c_uint64)]
+        L.orc_load_particle.restype = None
         _lib = L
     return _lib
 
@@ -179,6 +183,21 @@ def config_hash(params: dict) -> int:
     return int(lib().orc_config_hash(C.byref(c)))
 
 
+def load_particles(params: dict, species: int, indices) -> tuple:
+    """Initial (x, v, id) of the given particle indices of one species, one by one."""
+    c = make_config(params)
+    idx = np.asarray(indices, np.uint64)
+    x = np.empty(len(idx))
+    v = np.empty((len(idx), 3))
+    ids = np.empty(len(idx), np.uint64)
+    xx, vv, ii = C.c_double(), (C.c_double * 3)(), C.c_uint64()
+    L = lib()
+    for k, i in enumerate(idx):
+        L.orc_load_particle(C.byref(c), species, int(i), C.byref(xx), vv, C.byref(ii))
+        x[k], v[k], ids[k] = xx.value, list(vv), ii.value
+    return x, v, ids
+
+
 def set_threads(n: int) -> int:
     return int(lib().orc_set_threads(int(n)))
 
@@ -193,6 +212,7 @@ def _diag_dict(d: OrcDiag) -> dict:
         "net_charge_units": d.net_charge_units, "wall_charge": d.wall_charge,
         "ke": [d.ke[0], d.ke[1]], "field_energy": d.field_energy,
         "wall_energy": [d.wall_energy[0], d.wall_energy[1]],
+        "particle_steps": d.particle_steps,
     }
 
 

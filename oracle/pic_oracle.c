@@ -223,6 +223,7 @@ struct orc_sim {
   uint64_t wall_hits[2][2], coll[5], near[2], viol[2], births[2], source_pairs;
   int64_t wall_charge;
   double wall_energy[2];
+  uint64_t particle_steps;
 };
 
 static int sp_reserve(orc_species* s, size_t cap) {
@@ -351,43 +352,52 @@ static int sort_species(orc_species* p, int32_t N) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* Initial load (Sec. 2 "particle load"): positions per profile, Maxwellian velocities.       */
+/* Initial load (Sec. 2 "particle load"): positions per profile, Maxwellian velocities.  Particle
+ * i of species s has id i (electrons) or 2^62 | i (ions) and draws from its own Philox stream. */
+void orc_load_particle(const orc_config* c, int sp, uint64_t i, double* xo, double v[3], uint64_t* ido) {
+  const int32_t N = c->ncells;
+  const size_t np = (size_t)c->ppc[sp] * (size_t)N;
+  const double vth = sqrt(c->T[sp] / c->mass[sp]);
+  uint64_t id = (sp == 0) ? i : ((1ull << 62) | i);
+  uint32_t w[4];
+  double x;
+  if (c->load_profile == ORC_LOAD_UNIFORM) {
+    draw(id, c->seed, 0, ORC_CH_INIT, 0, w);
+    x = (double)(i / (uint64_t)c->ppc[sp]) + u01(w[0]);
+  } else if (c->load_profile == ORC_LOAD_EXP) {
+    draw(id, c->seed, 0, ORC_CH_INIT, 0, w);
+    double lam = c->profile_scale;
+    x = -lam * log(1.0 - u01(w[0]) * (1.0 - exp(-(double)N / lam)));
+  } else {
+    double x0 = ((double)i + 0.5) * (double)N / (double)np;
+    x = x0;
+    if (sp == 0) x = x0 + c->profile_scale * sin(2.0 * ORC_PI * (double)c->profile_mode * x0 / (double)N);
+  }
+  if (x < 0.0) x = 0.0;
+  if (x >= (double)N) x = nextafter((double)N, 0.0);
+  draw(id, c->seed, 0, ORC_CH_INIT, 1, w);
+  double n0, n1, n2, n3;
+  box_muller(w[0], w[1], &n0, &n1);
+  box_muller(w[2], w[3], &n2, &n3);
+  *xo = x;
+  v[0] = vth * n0;
+  v[1] = vth * n1;
+  v[2] = vth * n2;
+  *ido = id;
+}
+
 static int load(orc_sim* s) {
   const orc_config* c = &s->cfg;
-  int32_t N = s->N;
   for (int sp = 0; sp < 2; ++sp) {
-    size_t np = (size_t)c->ppc[sp] * (size_t)N;
+    size_t np = (size_t)c->ppc[sp] * (size_t)s->N;
     if (sp_reserve(&s->sp[sp], np) != ORC_OK) return ORC_ENOMEM;
     orc_species* p = &s->sp[sp];
-    double vth = sqrt(c->T[sp] / c->mass[sp]);
     for (size_t i = 0; i < np; ++i) {
-      uint64_t id = (sp == 0) ? (uint64_t)i : ((1ull << 62) | (uint64_t)i);
-      uint32_t w[4];
-      double x;
-      if (c->load_profile == ORC_LOAD_UNIFORM) {
-        draw(id, c->seed, 0, ORC_CH_INIT, 0, w);
-        x = (double)(i / (size_t)c->ppc[sp]) + u01(w[0]);
-      } else if (c->load_profile == ORC_LOAD_EXP) {
-        draw(id, c->seed, 0, ORC_CH_INIT, 0, w);
-        double lam = c->profile_scale;
-        x = -lam * log(1.0 - u01(w[0]) * (1.0 - exp(-(double)N / lam)));
-      } else {
-        double x0 = ((double)i + 0.5) * (double)N / (double)np;
-        x = x0;
-        if (sp == 0)
-          x = x0 + c->profile_scale * sin(2.0 * ORC_PI * (double)c->profile_mode * x0 / (double)N);
-      }
-      if (x < 0.0) x = 0.0;
-      if (x >= (double)N) x = nextafter((double)N, 0.0);
-      draw(id, c->seed, 0, ORC_CH_INIT, 1, w);
-      double n0, n1, n2, n3;
-      box_muller(w[0], w[1], &n0, &n1);
-      box_muller(w[2], w[3], &n2, &n3);
-      p->x[i] = x;
-      p->vx[i] = vth * n0;
-      p->vy[i] = vth * n1;
-      p->vz[i] = vth * n2;
-      p->id[i] = id;
+      double v[3];
+      orc_load_particle(c, sp, (uint64_t)i, &p->x[i], v, &p->id[i]);
+      p->vx[i] = v[0];
+      p->vy[i] = v[1];
+      p->vz[i] = v[2];
     }
     p->n = np;
   }
@@ -575,6 +585,7 @@ static int step_once(orc_sim* s) {
   const int32_t N = s->N;
   const uint64_t step = s->step;
   int nth = g_threads;
+  s->particle_steps += s->sp[0].n + s->sp[1].n;
   orc_tcount tcs[2][MAX_THREADS];
   orc_plist born[2][MAX_THREADS];
   memset(tcs, 0, sizeof(tcs));
@@ -781,6 +792,7 @@ int orc_diag(orc_sim* s, orc_diag_t* d) {
     fe += wgt * 0.5 * s->E[j] * s->E[j] * s->dx;
   }
   d->field_energy = fe;
+  d->particle_steps = s->particle_steps;
   return ORC_OK;
 }
 
@@ -973,6 +985,7 @@ int orc_restore(orc_sim* s, const void* buf, size_t len) {
   get(&q, &s->wall_charge, 8);
   get(&q, s->wall_energy, 16);
   s->step = step;
+  s->particle_steps = 0;
   for (int sp = 0; sp < 2; ++sp) {
     orc_species* p = &s->sp[sp];
     if (sp_reserve(p, n[sp]) != ORC_OK) return ORC_ENOMEM;

@@ -103,6 +103,7 @@ typedef struct {
   double ke[2];                  /* sum 0.5 m v^2 w (at the half step) */
   double field_energy;           /* sum_j 0.5 eps0 E_j^2 dx, half weight at the walls */
   double wall_energy[2];         /* sum over absorbed particles of 0.5 m v^2 w */
+  uint64_t particle_steps;       /* sum over steps of the live particles at step start */
 } orc_diag_t;
 
 typedef struct orc_sim orc_sim;
@@ -124,6 +125,9 @@ void orc_boris(double qm, double dt, const double E[3], const double B[3], doubl
 
 /* Null-collision bound per species (R8), already rounded to FP32. */
 void orc_nu_max(const orc_config* cfg, float nu_max[2], float p_null[2]);
+
+/* Initial state of particle i of species sp (x in dx units, v, id) as the load creates it. */
+void orc_load_particle(const orc_config* cfg, int sp, uint64_t i, double* x, double v[3], uint64_t* id);
 
 /* Simulation object. */
 orc_sim* orc_create(const orc_config* cfg, int* err);

@@ -1,0 +1,949 @@
+// api.cu -- the C ABI of include/pic.h: configuration checks, device workspace layout, the
+// per-step launch sequence, snapshot/restore (checkpoint/restart semantics of the paper's
+// Sec. 4.1), diagnostics and kernel timing.  All device work is in the k_*.cu kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_internal.cuh"
+
+int occupancy_step32();
+int occupancy_step64();
+
+namespace {
+
+enum Kind { K_STEP = 0, K_SOURCE, K_FIELD, K_SORT, K_LOAD, K_DIAG, K_KINDS };
+const char* kKindNames[PIC_KERNEL_KINDS] = {"step", "source", "field", "sort", "load", "diag", "", ""};
+
+struct EvPair {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct pic_handle {
+  pic_config cfg;
+  cudaStream_t st = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool owns_ws = false;
+  int N = 0;
+  bool plain = false;
+  unsigned long long cap[2] = {0, 0};
+  Species32 a32[2][2];  // [buffer][species]
+  int cur = 0;
+  Species64 a64[2];
+  unsigned int* cnt[2] = {nullptr, nullptr};
+  unsigned long long* S[2] = {nullptr, nullptr};
+  unsigned int* cursor[2] = {nullptr, nullptr};
+  double* acc[2] = {nullptr, nullptr};
+  long long* R[2] = {nullptr, nullptr};
+  double *rho = nullptr, *phi = nullptr, *E = nullptr;
+  float2* E2 = nullptr;
+  Ctl* ctl = nullptr;
+  Phys ph;
+  unsigned long long step = 0;
+  int grid_step = 0, grid_sort = 0, grid_diag = 0;
+  bool prof = false;
+  std::vector<EvPair> ev;
+  double ms[PIC_KERNEL_KINDS] = {0};
+  uint64_t launches[PIC_KERNEL_KINDS] = {0};
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+bool valid(const pic_config* c) {
+  if (!c || c->abi_version != PIC_ABI_VERSION) return false;
+  if (c->precision > PIC_FP64_PLAIN) return false;
+  if (c->ncells < 2 || c->ncells > PIC_MAX_CELLS_FP32) return false;
+  if (!(c->L > 0) || !(c->dt > 0) || !std::isfinite(c->L) || !std::isfinite(c->dt)) return false;
+  for (int s = 0; s < 2; ++s) {
+    if (c->ppc[s] < 1 || !(c->mass[s] > 0) || !(c->T[s] >= 0) || c->charge[s] == 0) return false;
+  }
+  if (c->sort_interval < 1 || c->field_mode > PIC_FIELD_ZERO) return false;
+  if (c->load_profile < 0 || c->load_profile > PIC_LOAD_QUIET_SINE) return false;
+  if (c->load_profile == PIC_LOAD_EXP && !(c->profile_scale > 0)) return false;
+  if (c->source_mode < 0 || c->source_mode > PIC_SOURCE_PAIRS) return false;
+  if (c->source_mode == PIC_SOURCE_PAIRS && !(c->source_x1 > 0 && c->source_x1 <= c->ncells)) return false;
+  if (!(c->n_gas >= 0) || !(c->Tg >= 0) || !(c->m_gas > 0)) return false;
+  if (!(c->capacity_factor >= 1.0) || !(c->capacity_factor <= 64.0)) return false;
+  if ((c->coll_mask & PIC_COLL_EX) && !(c->E_ex > 0)) return false;
+  if ((c->coll_mask & PIC_COLL_IZ) && !(c->E_iz > 0)) return false;
+  const double n = (double)c->ppc[0] * c->ncells * c->capacity_factor;
+  const double m = (double)c->ppc[1] * c->ncells * c->capacity_factor;
+  if (n > 2.0e9 || m > 2.0e9) return false;  // u32 cell cursors
+  return true;
+}
+
+unsigned long long capacity(const pic_config* c, int s) {
+  double n = std::ceil((double)c->ppc[s] * (double)c->ncells * c->capacity_factor);
+  unsigned long long v = (unsigned long long)n + 4ull;
+  return (v + 1023ull) & ~1023ull;
+}
+
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * count;
+    return p;
+  }
+};
+
+void layout(pic_handle* h, char* base, size_t* total) {
+  Carve cv{base};
+  const int N = h->N;
+  h->ctl = cv.take<Ctl>(1);
+  if (!h->plain) {
+    for (int b = 0; b < 2; ++b)
+      for (int s = 0; s < 2; ++s) {
+        Species32& a = h->a32[b][s];
+        a.cell = cv.take<int>(h->cap[s]);
+        a.frac = cv.take<float>(h->cap[s]);
+        a.vx = cv.take<float>(h->cap[s]);
+        a.vy = cv.take<float>(h->cap[s]);
+        a.vz = cv.take<float>(h->cap[s]);
+        a.id = cv.take<unsigned long long>(h->cap[s]);
+      }
+    for (int s = 0; s < 2; ++s) {
+      h->cnt[s] = cv.take<unsigned int>(N);
+      h->S[s] = cv.take<unsigned long long>(N);
+      h->cursor[s] = cv.take<unsigned int>(N);
+    }
+    h->E2 = cv.take<float2>(N);
+  } else {
+    for (int s = 0; s < 2; ++s) {
+      Species64& a = h->a64[s];
+      a.x = cv.take<double>(h->cap[s]);
+      a.vx = cv.take<double>(h->cap[s]);
+      a.vy = cv.take<double>(h->cap[s]);
+      a.vz = cv.take<double>(h->cap[s]);
+      a.id = cv.take<unsigned long long>(h->cap[s]);
+    }
+    for (int s = 0; s < 2; ++s) h->acc[s] = cv.take<double>(N + 1);
+  }
+  for (int s = 0; s < 2; ++s) h->R[s] = cv.take<long long>(N + 1);
+  h->rho = cv.take<double>(N + 1);
+  h->phi = cv.take<double>(N + 1);
+  h->E = cv.take<double>(N + 1);
+  *total = cv.off + 256;
+}
+
+// Physics constants (host, FP64), rounded once to FP32 for the FP32 path.  The null-collision
+// bound nu_max = n_g * sum(sigma_max) * v_cap, v_cap = sqrt(2 (E_cap + |V_L - V_R|) / m), is rounded to
+// FP32 first and P_null = 1 - exp(-nu_max dt) is computed from that FP32 value.
+void derive(pic_handle* h) {
+  const pic_config& c = h->cfg;
+  Phys& p = h->ph;
+  std::memset(&p, 0, sizeof(p));
+  const double dx = c.L / c.ncells;
+  const double th = c.B_angle_deg * 3.14159265358979323846 / 180.0;
+  const double Bv[3] = {c.B * std::cos(th), c.B * std::sin(th), 0.0};
+  const double Ecap = c.E_cap + std::fabs(c.V_left - c.V_right);
+  double smax[2];
+  smax[0] = ((c.coll_mask & PIC_COLL_EL) ? c.sigma_el : 0.0) + ((c.coll_mask & PIC_COLL_EX) ? c.sigma_ex : 0.0) +
+            ((c.coll_mask & PIC_COLL_IZ) ? c.sigma_iz : 0.0);
+  smax[1] = (c.coll_mask & PIC_COLL_CX) ? c.sigma_cx : 0.0;
+  for (int s = 0; s < 2; ++s) {
+    SpConst& k = p.sp[s];
+    const double h2 = 0.5 * (c.charge[s] / c.mass[s]) * c.dt;
+    double t[3], tt = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      t[i] = h2 * Bv[i];
+      tt += t[i] * t[i];
+    }
+    for (int i = 0; i < 3; ++i) {
+      k.t_d[i] = t[i];
+      k.s_d[i] = 2.0 * t[i] / (1.0 + tt);
+      k.t[i] = (float)k.t_d[i];
+      k.s[i] = (float)k.s_d[i];
+    }
+    k.qmdt2_d = h2;
+    k.qmdt2 = (float)h2;
+    k.mass_d = c.mass[s];
+    k.mass = (float)c.mass[s];
+    k.vt_d = std::sqrt(c.T[s] / c.mass[s]);
+    k.vt = (float)k.vt_d;
+    k.w = (float)(dx / c.ppc[s]);
+    k.qsign = c.charge[s] > 0 ? 1 : -1;
+    const double vcap = std::sqrt(2.0 * Ecap / c.mass[s]);
+    k.nu_max = (float)(c.n_gas * smax[s] * vcap);
+    k.p_null = (float)(1.0 - std::exp(-(double)k.nu_max * c.dt));
+  }
+  p.dtdx_d = c.dt / dx;
+  p.dtdx = (float)p.dtdx_d;
+  p.ngs_el_d = c.n_gas * c.sigma_el;
+  p.ngs_ex_d = c.n_gas * c.sigma_ex;
+  p.ngs_iz_d = c.n_gas * c.sigma_iz;
+  p.ngs_cx_d = c.n_gas * c.sigma_cx;
+  p.ngs_el = (float)p.ngs_el_d;
+  p.ngs_ex = (float)p.ngs_ex_d;
+  p.ngs_iz = (float)p.ngs_iz_d;
+  p.ngs_cx = (float)p.ngs_cx_d;
+  p.E_ex_d = c.E_ex;
+  p.E_iz_d = c.E_iz;
+  p.E_ex = (float)c.E_ex;
+  p.E_iz = (float)c.E_iz;
+  p.inv_E_ex = c.E_ex > 0 ? (float)(1.0 / c.E_ex) : 0.f;
+  p.inv_E_iz = c.E_iz > 0 ? (float)(1.0 / c.E_iz) : 0.f;
+  p.two_m_over_M_d = 2.0 * c.mass[0] / c.m_gas;
+  p.two_m_over_M = (float)p.two_m_over_M_d;
+  p.vt_gas_d = std::sqrt(c.Tg / c.mass[1]);
+  p.vt_gas = (float)p.vt_gas_d;
+  p.E_ext_d = c.E_ext;
+  p.E_ext = (float)c.E_ext;
+  p.src_x1_d = c.source_x1;
+  p.src_x1 = (float)c.source_x1;
+  p.coll_mask = c.coll_mask;
+  p.field_mode = c.field_mode;
+  p.push_mask = 3u & ~c.frozen_mask;
+  p.has_B = c.B != 0.0 ? 1u : 0u;
+  p.N = c.ncells;
+  p.seed = c.seed;
+}
+
+// ---------------------------------------------------------------------------------------------
+void prof_begin(pic_handle* h, int kind, EvPair* e) {
+  e->kind = kind;
+  e->a = e->b = nullptr;
+  if (!h->prof) return;
+  cudaEventCreate(&e->a);
+  cudaEventCreate(&e->b);
+  cudaEventRecord(e->a, h->st);
+}
+
+void prof_end(pic_handle* h, EvPair* e) {
+  if (!h->prof || !e->a) return;
+  cudaEventRecord(e->b, h->st);
+  h->ev.push_back(*e);
+}
+
+void prof_harvest(pic_handle* h) {
+  for (EvPair& e : h->ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      h->ms[e.kind] += ms;
+      h->launches[e.kind] += 1;
+    }
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  h->ev.clear();
+}
+
+StepParams32 params32(pic_handle* h) {
+  StepParams32 P;
+  for (int s = 0; s < 2; ++s) {
+    P.sp[s] = h->a32[h->cur][s];
+    P.cap[s] = h->cap[s];
+    P.cnt[s] = h->cnt[s];
+    P.S[s] = h->S[s];
+  }
+  P.E2 = h->E2;
+  P.ctl = h->ctl;
+  P.ph = h->ph;
+  P.step = h->step;
+  return P;
+}
+
+StepParams64 params64(pic_handle* h) {
+  StepParams64 P;
+  for (int s = 0; s < 2; ++s) {
+    P.sp[s] = h->a64[s];
+    P.cap[s] = h->cap[s];
+    P.acc[s] = h->acc[s];
+  }
+  P.E = h->E;
+  P.ctl = h->ctl;
+  P.ph = h->ph;
+  P.step = h->step;
+  return P;
+}
+
+PoissonParams field_params(pic_handle* h, bool keep_counts, bool count_step) {
+  PoissonParams F;
+  std::memset(&F, 0, sizeof(F));
+  const double dx = h->cfg.L / h->cfg.ncells;
+  for (int s = 0; s < 2; ++s) {
+    F.cnt[s] = h->cnt[s];
+    F.S[s] = h->S[s];
+    F.acc[s] = h->acc[s];
+    F.qw[s] = h->cfg.charge[s] * (dx / h->cfg.ppc[s]);
+    F.R[s] = h->R[s];
+    F.cap[s] = h->cap[s];
+    if (!h->plain) F.pad32[s] = h->a32[h->cur][s];
+    F.pad64[s] = h->a64[s];
+  }
+  F.mode = h->plain ? 1 : 0;
+  F.keep_counts = keep_counts ? 1 : 0;
+  F.count_step = count_step ? 1 : 0;
+  F.N = h->N;
+  F.dx = dx;
+  F.V_L = h->cfg.V_left;
+  F.V_R = h->cfg.V_right;
+  F.rho = h->rho;
+  F.phi = h->phi;
+  F.E = h->E;
+  F.E2 = h->E2;
+  F.ctl = h->ctl;
+  F.plain = h->plain ? 1 : 0;
+  return F;
+}
+
+#define CK(x)                                \
+  do {                                       \
+    cudaError_t e__ = (x);                   \
+    if (e__ != cudaSuccess) return PIC_ECUDA; \
+  } while (0)
+
+// Deposit of the current particles without moving them, field solve, and (FP32) the sort.
+int refresh_field(pic_handle* h) {
+  EvPair e;
+  Phys saved = h->ph;
+  h->ph.push_mask = 0u;
+  h->ph.coll_mask = 0u;
+  prof_begin(h, K_STEP, &e);
+  cudaError_t err = h->plain ? launch_step64(params64(h), h->grid_step, h->st)
+                             : launch_step32(params32(h), h->grid_step, h->st);
+  prof_end(h, &e);
+  h->ph = saved;
+  CK(err);
+  prof_begin(h, K_FIELD, &e);
+  CK(launch_field(field_params(h, !h->plain, false), h->st));
+  prof_end(h, &e);
+  if (!h->plain) {
+    prof_begin(h, K_SORT, &e);
+    Species32 src[2] = {h->a32[h->cur][0], h->a32[h->cur][1]};
+    Species32 dst[2] = {h->a32[1 - h->cur][0], h->a32[1 - h->cur][1]};
+    CK(launch_sort32(src, dst, h->cnt, h->cursor, h->cap, h->ctl, h->N, h->grid_sort, h->st));
+    prof_end(h, &e);
+    h->cur = 1 - h->cur;
+  }
+  return PIC_OK;
+}
+
+int check_errors(pic_handle* h) {
+  CK(cudaStreamSynchronize(h->st));
+  unsigned int err = 0;
+  CK(cudaMemcpy(&err, &h->ctl->error, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err & ERR_OVERFLOW) return PIC_EOVERFLOW;
+  if (err & ERR_TIMEOUT) return PIC_ETIMEOUT;
+  if (err & ERR_DEVICE) return PIC_EDEVICE;
+  return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Snapshot format helpers (CRC-32 IEEE 802.3 reflected; FNV-1a 64 of the canonical config).
+uint32_t crc32_ieee(const unsigned char* p, size_t n) {
+  static uint32_t table[256];
+  static bool init = false;
+  if (!init) {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : (c >> 1);
+      table[i] = c;
+    }
+    init = true;
+  }
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) c = table[(c ^ p[i]) & 0xFFu] ^ (c >> 8);
+  return c ^ 0xFFFFFFFFu;
+}
+
+struct Fnv {
+  uint64_t h = 0xcbf29ce484222325ull;
+  void add(const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 0x100000001b3ull;
+    }
+  }
+};
+
+// Canonical physics fields (precision, sort interval and capacity excluded): int32 ncells,
+// ppc[2], load_profile, profile_mode, source_mode; uint32 coll_mask, field_mode, frozen_mask;
+// f64 L, dt, mass[2], charge[2], T[2], Tg, m_gas, B, B_angle_deg, V_left, V_right, n_gas,
+// sigma_el, sigma_ex, E_ex, sigma_iz, E_iz, sigma_cx, E_cap, E_ext, profile_scale, source_x1;
+// u64 seed; all little-endian.
+uint64_t config_hash(const pic_config& c) {
+  Fnv f;
+  const int32_t iv[6] = {c.ncells, c.ppc[0], c.ppc[1], c.load_profile, c.profile_mode, c.source_mode};
+  const uint32_t uv[3] = {c.coll_mask, c.field_mode, c.frozen_mask};
+  const double dv[25] = {c.L,        c.dt,          c.mass[0], c.mass[1],  c.charge[0], c.charge[1], c.T[0],
+                         c.T[1],     c.Tg,          c.m_gas,   c.B,        c.B_angle_deg, c.V_left,   c.V_right,
+                         c.n_gas,    c.sigma_el,    c.sigma_ex, c.E_ex,    c.sigma_iz,  c.E_iz,      c.sigma_cx,
+                         c.E_cap,    c.E_ext,       c.profile_scale,       c.source_x1};
+  f.add(iv, sizeof(iv));
+  f.add(uv, sizeof(uv));
+  f.add(dv, sizeof(dv));
+  f.add(&c.seed, sizeof(c.seed));
+  return f.h;
+}
+
+const size_t kHdr = 8 + 4 + 4 + 8 + 8 + 16 + 17 * 8 + 8 + 16;
+
+struct HostParticles {
+  std::vector<int32_t> cell;
+  std::vector<double> frac, vx, vy, vz;
+  std::vector<uint64_t> id;
+};
+
+int fetch_particles(pic_handle* h, HostParticles out[2], Ctl* ctl) {
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemcpy(ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  for (int s = 0; s < 2; ++s) {
+    const size_t n = (size_t)ctl->n_cur[s];
+    HostParticles& o = out[s];
+    std::vector<uint64_t> id(n);
+    std::vector<double> vx(n), vy(n), vz(n), x(n);
+    std::vector<int32_t> cell(n);
+    std::vector<float> f32(n);
+    if (!h->plain) {
+      const Species32& a = h->a32[h->cur][s];
+      CK(cudaMemcpy(cell.data(), a.cell, n * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(f32.data(), a.frac, n * 4, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < n; ++i) x[i] = f32[i];
+      CK(cudaMemcpy(f32.data(), a.vx, n * 4, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < n; ++i) vx[i] = f32[i];
+      CK(cudaMemcpy(f32.data(), a.vy, n * 4, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < n; ++i) vy[i] = f32[i];
+      CK(cudaMemcpy(f32.data(), a.vz, n * 4, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < n; ++i) vz[i] = f32[i];
+      CK(cudaMemcpy(id.data(), a.id, n * 8, cudaMemcpyDeviceToHost));
+    } else {
+      const Species64& a = h->a64[s];
+      CK(cudaMemcpy(x.data(), a.x, n * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(vx.data(), a.vx, n * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(vy.data(), a.vy, n * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(vz.data(), a.vz, n * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(id.data(), a.id, n * 8, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < n; ++i) {
+        if (x[i] < 0.0) {
+          cell[i] = PIC_DEAD_CELL;
+          continue;
+        }
+        double c = std::floor(x[i]);
+        cell[i] = (int32_t)c;
+        x[i] = x[i] - c;
+      }
+    }
+    std::vector<size_t> live;
+    live.reserve(n);
+    for (size_t i = 0; i < n; ++i)
+      if (cell[i] != PIC_DEAD_CELL) live.push_back(i);
+    std::sort(live.begin(), live.end(), [&](size_t a, size_t b) { return id[a] < id[b]; });
+    const size_t m = live.size();
+    o.cell.resize(m);
+    o.frac.resize(m);
+    o.vx.resize(m);
+    o.vy.resize(m);
+    o.vz.resize(m);
+    o.id.resize(m);
+    for (size_t k = 0; k < m; ++k) {
+      const size_t i = live[k];
+      o.cell[k] = cell[i];
+      o.frac[k] = x[i];
+      o.vx[k] = vx[i];
+      o.vy[k] = vy[i];
+      o.vz[k] = vz[i];
+      o.id[k] = id[i];
+    }
+  }
+  return PIC_OK;
+}
+
+template <class T>
+void put(std::vector<unsigned char>& b, const T& v) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+  b.insert(b.end(), p, p + sizeof(T));
+}
+
+template <class T>
+void put_arr(std::vector<unsigned char>& b, const std::vector<T>& v) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(v.data());
+  b.insert(b.end(), p, p + sizeof(T) * v.size());
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+const char* pic_strerror(int status) {
+  switch (status) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument or configuration";
+    case PIC_ENOMEM: return "out of memory or workspace too small";
+    case PIC_ECUDA: return "CUDA runtime error";
+    case PIC_EOVERFLOW: return "particle capacity exceeded";
+    case PIC_ECORRUPT: return "corrupt or mismatched snapshot";
+    case PIC_ETIMEOUT: return "device wait timed out";
+    case PIC_EDEVICE: return "device-side check failed";
+    default: return "unknown status";
+  }
+}
+
+int pic_workspace_size(const pic_config* cfg, size_t* bytes) {
+  if (!valid(cfg) || !bytes) return PIC_EINVAL;
+  pic_handle tmp;
+  tmp.cfg = *cfg;
+  tmp.N = cfg->ncells;
+  tmp.plain = cfg->precision == PIC_FP64_PLAIN;
+  for (int s = 0; s < 2; ++s) tmp.cap[s] = capacity(cfg, s);
+  layout(&tmp, nullptr, bytes);
+  return PIC_OK;
+}
+
+int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, void* cuda_stream, pic_handle** out) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  if (!valid(cfg)) return PIC_EINVAL;
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return PIC_EINVAL;
+  pic_handle* h = new (std::nothrow) pic_handle();
+  if (!h) return PIC_ENOMEM;
+  h->cfg = *cfg;
+  h->st = static_cast<cudaStream_t>(cuda_stream);
+  h->N = cfg->ncells;
+  h->plain = cfg->precision == PIC_FP64_PLAIN;
+  for (int s = 0; s < 2; ++s) h->cap[s] = capacity(cfg, s);
+  size_t need = 0;
+  layout(h, nullptr, &need);
+  if (workspace) {
+    if (workspace_bytes < need) {
+      delete h;
+      return PIC_ENOMEM;
+    }
+    h->ws = workspace;
+  } else {
+    if (cudaMalloc(&h->ws, need) != cudaSuccess) {
+      delete h;
+      return PIC_ENOMEM;
+    }
+    h->owns_ws = true;
+  }
+  h->ws_bytes = need;
+  layout(h, static_cast<char*>(h->ws), &need);
+  derive(h);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
+  h->grid_step = sms * (h->plain ? occupancy_step64() : occupancy_step32());
+  h->grid_sort = sms * 4;
+  h->grid_diag = sms * 8;
+  *out = h;
+
+  int rc = PIC_OK;
+  // zero the grid arrays and the control block (particle arrays are written by the load)
+  const char* grid_begin = reinterpret_cast<const char*>(h->plain ? (void*)h->acc[0] : (void*)h->cnt[0]);
+  size_t grid_off = (size_t)(grid_begin - static_cast<char*>(h->ws));
+  if (cudaMemsetAsync(static_cast<char*>(h->ws) + grid_off, 0, need - 256 - grid_off, h->st) != cudaSuccess ||
+      cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st) != cudaSuccess) {
+    rc = PIC_ECUDA;
+  }
+  unsigned long long n[2];
+  for (int s = 0; s < 2; ++s) n[s] = (unsigned long long)cfg->ppc[s] * (unsigned long long)cfg->ncells;
+  if (rc == PIC_OK) {
+    EvPair e;
+    prof_begin(h, K_LOAD, &e);
+    cudaError_t err = h->plain ? launch_load64(params64(h), n, cfg->load_profile, cfg->ppc[0], cfg->ppc[1],
+                                               cfg->profile_scale, cfg->profile_mode, h->st)
+                               : launch_load32(params32(h), n, cfg->load_profile, cfg->ppc[0], cfg->ppc[1],
+                                               cfg->profile_scale, cfg->profile_mode, h->st);
+    prof_end(h, &e);
+    if (err != cudaSuccess) rc = PIC_ECUDA;
+  }
+  if (rc == PIC_OK) {
+    // extents, padding slots, live counts
+    Ctl c0;
+    std::memset(&c0, 0, sizeof(c0));
+    for (int s = 0; s < 2; ++s) {
+      c0.n_cur[s] = round_up4(n[s]);
+      c0.n_live[s] = n[s];
+      const unsigned long long pad = c0.n_cur[s] - n[s];
+      if (pad) {
+        if (!h->plain) {
+          int dead[4] = {PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL};
+          if (cudaMemcpyAsync(h->a32[0][s].cell + n[s], dead, pad * 4, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            rc = PIC_ECUDA;
+        } else {
+          double dead[4] = {-1.0, -1.0, -1.0, -1.0};
+          if (cudaMemcpyAsync(h->a64[s].x + n[s], dead, pad * 8, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            rc = PIC_ECUDA;
+        }
+      }
+    }
+    if (rc == PIC_OK && cudaMemcpyAsync(h->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+      rc = PIC_ECUDA;
+    if (rc == PIC_OK) rc = refresh_field(h);
+    if (rc == PIC_OK) rc = check_errors(h);
+  }
+  if (rc != PIC_OK) {
+    pic_free(h);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+int pic_step(pic_handle* h, int32_t n) {
+  if (!h || n < 0) return PIC_EINVAL;
+  for (int32_t k = 0; k < n; ++k) {
+    const bool sort_now = !h->plain && (h->step % (unsigned long long)h->cfg.sort_interval) == 0ull;
+    EvPair e;
+    if (!h->plain) {
+      const StepParams32 P = params32(h);
+      prof_begin(h, K_STEP, &e);
+      CK(launch_step32(P, h->grid_step, h->st));
+      prof_end(h, &e);
+      if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
+        prof_begin(h, K_SOURCE, &e);
+        CK(launch_source32(P, h->st));
+        prof_end(h, &e);
+      }
+    } else {
+      const StepParams64 P = params64(h);
+      prof_begin(h, K_STEP, &e);
+      CK(launch_step64(P, h->grid_step, h->st));
+      prof_end(h, &e);
+      if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
+        prof_begin(h, K_SOURCE, &e);
+        CK(launch_source64(P, h->st));
+        prof_end(h, &e);
+      }
+    }
+    prof_begin(h, K_FIELD, &e);
+    CK(launch_field(field_params(h, sort_now, true), h->st));
+    prof_end(h, &e);
+    if (sort_now) {
+      prof_begin(h, K_SORT, &e);
+      Species32 src[2] = {h->a32[h->cur][0], h->a32[h->cur][1]};
+      Species32 dst[2] = {h->a32[1 - h->cur][0], h->a32[1 - h->cur][1]};
+      CK(launch_sort32(src, dst, h->cnt, h->cursor, h->cap, h->ctl, h->N, h->grid_sort, h->st));
+      prof_end(h, &e);
+      h->cur = 1 - h->cur;
+    }
+    h->step += 1;
+  }
+  return PIC_OK;
+}
+
+int pic_sync(pic_handle* h) {
+  if (!h) return PIC_EINVAL;
+  return check_errors(h);
+}
+
+int pic_diag(pic_handle* h, pic_diag_t* d) {
+  if (!h || !d) return PIC_EINVAL;
+  int rc = check_errors(h);
+  if (rc != PIC_OK) return rc;
+  CK(cudaMemsetAsync(h->ctl->ke_fx, 0, sizeof(h->ctl->ke_fx), h->st));
+  EvPair e;
+  prof_begin(h, K_DIAG, &e);
+  CK(h->plain ? launch_diag64(params64(h), h->grid_diag, h->st) : launch_diag32(params32(h), h->grid_diag, h->st));
+  prof_end(h, &e);
+  CK(cudaStreamSynchronize(h->st));
+  Ctl c;
+  CK(cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const int N = h->N;
+  std::vector<long long> R(2 * (size_t)(N + 1));
+  std::vector<double> E(N + 1);
+  CK(cudaMemcpy(R.data(), h->R[0], sizeof(long long) * (N + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(R.data() + N + 1, h->R[1], sizeof(long long) * (N + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(E.data(), h->E, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost));
+  std::memset(d, 0, sizeof(*d));
+  const double dx = h->cfg.L / N;
+  d->step = h->step;
+  for (int s = 0; s < 2; ++s) {
+    const double w = dx / h->cfg.ppc[s];
+    d->n[s] = c.n_live[s];
+    d->wall_hits[s][0] = c.wall_hits[s][0];
+    d->wall_hits[s][1] = c.wall_hits[s][1];
+    d->near_threshold[s] = c.near_thr[s];
+    d->nu_max_violations[s] = c.viol[s];
+    d->births[s] = c.births[s];
+    d->ke[s] = (double)c.ke_fx[s] * (1.0 / 16777216.0) * w;
+    d->wall_energy[s] = (double)c.wall_energy_fx[s] * (1.0 / 16777216.0) * w;
+  }
+  for (int k = 0; k < 5; ++k) d->coll[k] = c.coll[k];
+  d->source_pairs = c.source_pairs;
+  d->dropped = c.dropped;
+  d->wall_charge = c.wall_charge;
+  long long q = 0;
+  for (int s = 0; s < 2; ++s) {
+    const long long sg = h->cfg.charge[s] > 0 ? 1 : -1;
+    for (int j = 0; j <= N; ++j) q += sg * R[(size_t)s * (N + 1) + j];
+  }
+  d->net_charge_units = q;
+  double fe = 0.0;
+  for (int j = 0; j <= N; ++j) fe += ((j == 0 || j == N) ? 0.5 : 1.0) * 0.5 * E[j] * E[j] * dx;
+  d->field_energy = fe;
+  d->particle_steps = c.particle_steps;
+  return PIC_OK;
+}
+
+int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E, size_t nnodes) {
+  if (!h || nnodes != (size_t)h->N + 1) return PIC_EINVAL;
+  int rc = check_errors(h);
+  if (rc != PIC_OK) return rc;
+  if (R) {
+    CK(cudaMemcpy(R, h->R[0], sizeof(int64_t) * nnodes, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(R + nnodes, h->R[1], sizeof(int64_t) * nnodes, cudaMemcpyDeviceToHost));
+  }
+  if (rho) CK(cudaMemcpy(rho, h->rho, sizeof(double) * nnodes, cudaMemcpyDeviceToHost));
+  if (phi) CK(cudaMemcpy(phi, h->phi, sizeof(double) * nnodes, cudaMemcpyDeviceToHost));
+  if (E) {
+    std::vector<double> e(nnodes);
+    CK(cudaMemcpy(e.data(), h->E, sizeof(double) * nnodes, cudaMemcpyDeviceToHost));
+    for (size_t j = 0; j < nnodes; ++j) E[j] = (float)e[j];
+  }
+  return PIC_OK;
+}
+
+int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
+  if (!h) return PIC_EINVAL;
+  int rc = check_errors(h);
+  if (rc != PIC_OK && rc != PIC_EOVERFLOW) return rc;
+  HostParticles P[2];
+  Ctl c;
+  rc = fetch_particles(h, P, &c);
+  if (rc != PIC_OK) return rc;
+  const size_t need = kHdr + 4 + 44 * (P[0].id.size() + P[1].id.size());
+  if (needed) *needed = need;
+  if (!buf) return PIC_OK;
+  if (cap < need) return PIC_EINVAL;
+  std::vector<unsigned char> b;
+  b.reserve(need);
+  b.insert(b.end(), "PICMCSN1", "PICMCSN1" + 8);
+  put(b, (uint32_t)1);
+  put(b, (uint32_t)0);
+  put(b, config_hash(h->cfg));
+  put(b, (uint64_t)h->step);
+  put(b, (uint64_t)P[0].id.size());
+  put(b, (uint64_t)P[1].id.size());
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < 2; ++k) put(b, (uint64_t)c.wall_hits[s][k]);
+  for (int k = 0; k < 5; ++k) put(b, (uint64_t)c.coll[k]);
+  for (int s = 0; s < 2; ++s) put(b, (uint64_t)c.near_thr[s]);
+  for (int s = 0; s < 2; ++s) put(b, (uint64_t)c.viol[s]);
+  for (int s = 0; s < 2; ++s) put(b, (uint64_t)c.births[s]);
+  put(b, (uint64_t)c.source_pairs);
+  put(b, (uint64_t)c.dropped);
+  put(b, (int64_t)c.wall_charge);
+  const double dx = h->cfg.L / h->N;
+  for (int s = 0; s < 2; ++s) put(b, (double)c.wall_energy_fx[s] * (1.0 / 16777216.0) * (dx / h->cfg.ppc[s]));
+  for (int s = 0; s < 2; ++s) {
+    put_arr(b, P[s].cell);
+    put_arr(b, P[s].frac);
+    put_arr(b, P[s].vx);
+    put_arr(b, P[s].vy);
+    put_arr(b, P[s].vz);
+    put_arr(b, P[s].id);
+  }
+  put(b, crc32_ieee(b.data(), b.size()));
+  std::memcpy(buf, b.data(), b.size());
+  return PIC_OK;
+}
+
+int pic_restore(pic_handle* h, const void* buf, size_t len) {
+  if (!h || !buf) return PIC_EINVAL;
+  const unsigned char* b = static_cast<const unsigned char*>(buf);
+  if (len < kHdr + 4 || std::memcmp(b, "PICMCSN1", 8) != 0) return PIC_ECORRUPT;
+  uint32_t crc;
+  std::memcpy(&crc, b + len - 4, 4);
+  if (crc != crc32_ieee(b, len - 4)) return PIC_ECORRUPT;
+  uint32_t ver;
+  uint64_t hash, step, n[2];
+  std::memcpy(&ver, b + 8, 4);
+  std::memcpy(&hash, b + 16, 8);
+  std::memcpy(&step, b + 24, 8);
+  std::memcpy(n, b + 32, 16);
+  if (ver != 1 || hash != config_hash(h->cfg)) return PIC_ECORRUPT;
+  if (n[0] > (1ull << 40) || n[1] > (1ull << 40) || len != kHdr + 4 + 44 * (n[0] + n[1])) return PIC_ECORRUPT;
+  for (int s = 0; s < 2; ++s)
+    if (round_up4(n[s]) > h->cap[s]) return PIC_EOVERFLOW;
+  CK(cudaStreamSynchronize(h->st));
+  uint64_t cnt[17];
+  int64_t wall_charge;
+  double wall_energy[2];
+  std::memcpy(cnt, b + 48, sizeof(cnt));
+  std::memcpy(&wall_charge, b + 48 + 136, 8);
+  std::memcpy(wall_energy, b + 48 + 144, 16);
+  const int N = h->N;
+  const double dx = h->cfg.L / N;
+  size_t off = kHdr;
+  h->cur = 0;
+  for (int s = 0; s < 2; ++s) {
+    const size_t m = (size_t)n[s];
+    std::vector<int32_t> cell(m);
+    std::vector<double> frac(m), vx(m), vy(m), vz(m);
+    std::vector<uint64_t> id(m);
+    std::memcpy(cell.data(), b + off, 4 * m);
+    off += 4 * m;
+    std::memcpy(frac.data(), b + off, 8 * m);
+    off += 8 * m;
+    std::memcpy(vx.data(), b + off, 8 * m);
+    off += 8 * m;
+    std::memcpy(vy.data(), b + off, 8 * m);
+    off += 8 * m;
+    std::memcpy(vz.data(), b + off, 8 * m);
+    off += 8 * m;
+    std::memcpy(id.data(), b + off, 8 * m);
+    off += 8 * m;
+    for (size_t i = 0; i < m; ++i)
+      if (cell[i] < 0 || cell[i] >= N || !(frac[i] >= 0.0 && frac[i] < 1.0)) return PIC_ECORRUPT;
+    const size_t mp = (size_t)round_up4(m);
+    if (!h->plain) {
+      std::vector<int32_t> c32(mp, PIC_DEAD_CELL);
+      std::vector<float> f32(mp, 0.f), x32(mp, 0.f), y32(mp, 0.f), z32(mp, 0.f);
+      std::vector<uint64_t> id2(mp, 0ull);
+      for (size_t i = 0; i < m; ++i) {
+        int c = cell[i];
+        float f = (float)frac[i];
+        if (f >= 1.f) {
+          f = 0.f;
+          c += 1;
+          if (c >= N) {
+            c = N - 1;
+            f = 0.99999994f;
+          }
+        }
+        c32[i] = c;
+        f32[i] = f;
+        x32[i] = (float)vx[i];
+        y32[i] = (float)vy[i];
+        z32[i] = (float)vz[i];
+        id2[i] = id[i];
+      }
+      const Species32& a = h->a32[0][s];
+      CK(cudaMemcpy(a.cell, c32.data(), 4 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.frac, f32.data(), 4 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.vx, x32.data(), 4 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.vy, y32.data(), 4 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.vz, z32.data(), 4 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.id, id2.data(), 8 * mp, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<double> x(mp, -1.0), a1(mp, 0.0), a2(mp, 0.0), a3(mp, 0.0);
+      std::vector<uint64_t> id2(mp, 0ull);
+      for (size_t i = 0; i < m; ++i) {
+        double xx = (double)cell[i] + frac[i];
+        if (xx >= (double)cell[i] + 1.0) xx = std::nextafter((double)cell[i] + 1.0, 0.0);
+        x[i] = xx;
+        a1[i] = vx[i];
+        a2[i] = vy[i];
+        a3[i] = vz[i];
+        id2[i] = id[i];
+      }
+      const Species64& a = h->a64[s];
+      CK(cudaMemcpy(a.x, x.data(), 8 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.vx, a1.data(), 8 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.vy, a2.data(), 8 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.vz, a3.data(), 8 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.id, id2.data(), 8 * mp, cudaMemcpyHostToDevice));
+    }
+  }
+  Ctl c;
+  std::memset(&c, 0, sizeof(c));
+  for (int s = 0; s < 2; ++s) {
+    c.n_cur[s] = round_up4(n[s]);
+    c.n_live[s] = n[s];
+  }
+  int k = 0;
+  for (int s = 0; s < 2; ++s)
+    for (int side = 0; side < 2; ++side) c.wall_hits[s][side] = cnt[k++];
+  for (int i = 0; i < 5; ++i) c.coll[i] = cnt[k++];
+  for (int s = 0; s < 2; ++s) c.near_thr[s] = cnt[k++];
+  for (int s = 0; s < 2; ++s) c.viol[s] = cnt[k++];
+  for (int s = 0; s < 2; ++s) c.births[s] = cnt[k++];
+  c.source_pairs = cnt[k++];
+  c.dropped = cnt[k++];
+  c.wall_charge = wall_charge;
+  for (int s = 0; s < 2; ++s) {
+    const double w = dx / h->cfg.ppc[s];
+    c.wall_energy_fx[s] = (unsigned long long)std::llrint(wall_energy[s] / w * 16777216.0);
+  }
+  CK(cudaMemcpy(h->ctl, &c, sizeof(c), cudaMemcpyHostToDevice));
+  // clear the grid accumulators (a previous step may have left counts for a sort)
+  if (!h->plain) {
+    for (int s = 0; s < 2; ++s) {
+      CK(cudaMemsetAsync(h->cnt[s], 0, sizeof(unsigned int) * N, h->st));
+      CK(cudaMemsetAsync(h->S[s], 0, sizeof(unsigned long long) * N, h->st));
+    }
+  } else {
+    for (int s = 0; s < 2; ++s) CK(cudaMemsetAsync(h->acc[s], 0, sizeof(double) * (N + 1), h->st));
+  }
+  h->step = step;
+  int rc = refresh_field(h);
+  if (rc != PIC_OK) return rc;
+  return check_errors(h);
+}
+
+int pic_profile(pic_handle* h, int enable) {
+  if (!h) return PIC_EINVAL;
+  if (!enable && h->prof) {
+    cudaStreamSynchronize(h->st);
+    prof_harvest(h);
+  }
+  h->prof = enable != 0;
+  return PIC_OK;
+}
+
+int pic_kernel_times(pic_handle* h, double* ms, uint64_t* launches, const char** names, int32_t nkinds) {
+  if (!h || nkinds < 0) return PIC_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  prof_harvest(h);
+  for (int k = 0; k < nkinds && k < PIC_KERNEL_KINDS; ++k) {
+    if (ms) ms[k] = h->ms[k];
+    if (launches) launches[k] = h->launches[k];
+    if (names) names[k] = kKindNames[k];
+  }
+  for (int k = 0; k < PIC_KERNEL_KINDS; ++k) {
+    h->ms[k] = 0.0;
+    h->launches[k] = 0;
+  }
+  return PIC_OK;
+}
+
+void pic_free(pic_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  prof_harvest(h);
+  if (h->owns_ws && h->ws) cudaFree(h->ws);
+  delete h;
+}
+
+int pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n, void* cuda_stream) {
+  if (n && (!ctr || !key || !out)) return PIC_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(ctr) & 15u) || (reinterpret_cast<uintptr_t>(out) & 15u) ||
+      (reinterpret_cast<uintptr_t>(key) & 7u))
+    return PIC_EINVAL;
+  return launch_philox(ctr, key, out, n, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double V_R, double* phi, double* E,
+                void* cuda_stream) {
+  if (!rho || !phi || !E || ncells < 2 || ncells > PIC_MAX_CELLS_FP32 || !(dx > 0)) return PIC_EINVAL;
+  PoissonParams F;
+  std::memset(&F, 0, sizeof(F));
+  F.rho_in = rho;
+  F.mode = 2;
+  F.N = ncells;
+  F.dx = dx;
+  F.V_L = V_L;
+  F.V_R = V_R;
+  F.phi = phi;
+  F.E = E;
+  return launch_field(F, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+}  // extern "C"

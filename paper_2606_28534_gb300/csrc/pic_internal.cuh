@@ -1,0 +1,198 @@
+// pic_internal.cuh -- device-side data layout and helpers of the GB300 PIC MC library.
+//
+// Layout in HBM (one handle):
+//   per species s, two particle buffers (A/B, swapped by the counting sort), SoA:
+//     cell int32[cap] | frac f32[cap] | vx f32[cap] | vy f32[cap] | vz f32[cap] | id u64[cap]
+//   (PIC_FP64_PLAIN: one buffer, x f64[cap] (cell units) | vx, vy, vz f64[cap] | id u64[cap])
+//   grid: cnt_s u32[N], S_s u64[N] (per-cell particle count and sum of right CIC weights),
+//         R_s i64[N+1], rho f64[N+1], phi f64[N+1], E f64[N+1], E2 float2[N] = (E_c, E_{c+1}),
+//         cursor_s u32[N] (sort), plain path rho_acc_s f64[N+1]
+//   control block Ctl (counters and array extents), 256-byte aligned.
+// Extents n_cur are kept a multiple of 4 so that every particle load/store is a 128-bit access;
+// slots past the last particle carry cell = DEAD_CELL.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PIC_TPB 256
+#define PIC_PPT 4
+#define PIC_TILE (PIC_TPB * PIC_PPT)
+#define PIC_WCAP 2048
+#define PIC_DEAD_CELL ((int)0x80000000)
+#define PIC_FIELD_CTAS 8
+#define PIC_FIELD_TPB 1024
+#define PIC_FIELD_MAX_ITEMS 32
+#define PIC_MAX_CELLS_FP32 (PIC_FIELD_CTAS * PIC_FIELD_TPB * PIC_FIELD_MAX_ITEMS - 1)
+
+// Philox counter word 2: the stream of a draw
+#define CH_INIT 1u
+#define CH_COLL 2u
+#define CH_SCAT 3u
+#define CH_CHILD 4u
+#define CH_SOURCE 5u
+
+// error bits of Ctl::error
+#define ERR_OVERFLOW 1u
+#define ERR_TIMEOUT 2u
+#define ERR_DEVICE 4u
+
+struct Ctl {
+  unsigned long long n_cur[2];   // array extent (multiple of 4, includes dead slots)
+  unsigned long long n_born[2];  // slots claimed past n_cur in the current step
+  unsigned long long n_live[2];  // live particles
+  unsigned long long wall_hits[2][2];
+  unsigned long long coll[5];
+  unsigned long long near_thr[2];
+  unsigned long long viol[2];
+  unsigned long long births[2];
+  unsigned long long source_pairs;
+  unsigned long long dropped;
+  long long wall_charge;
+  unsigned long long wall_energy_fx[2];  // sum of 0.5 m v^2 of absorbed particles, 2^-24 units
+  unsigned long long src_K;              // ions absorbed in the current step
+  unsigned long long sort_total[2];
+  unsigned int sort_done;                // blocks of the scatter that finished
+  unsigned int error;
+  unsigned long long ke_fx[2];           // diag scratch: sum 0.5 m v^2, 2^-24 units
+  unsigned long long particle_steps;     // sum over steps of the live particles at step start
+  unsigned long long live_mark;          // live particles at the start of the next step
+};
+
+struct Species32 {
+  int* cell;
+  float* frac;
+  float* vx;
+  float* vy;
+  float* vz;
+  unsigned long long* id;
+};
+
+struct Species64 {
+  double* x;
+  double* vx;
+  double* vy;
+  double* vz;
+  unsigned long long* id;
+};
+
+// Physics constants of one species, rounded once on the host.
+struct SpConst {
+  float qmdt2;      // (q/m) dt / 2
+  float t[3], s[3]; // Boris rotation vectors
+  float p_null;     // 1 - exp(-nu_max dt), FP32
+  float nu_max;     // FP32
+  float mass;
+  float vt;         // sqrt(T/m) (source, load)
+  float w;          // weight dx/ppc
+  int qsign;        // sign of the charge
+  double qmdt2_d, t_d[3], s_d[3], mass_d, vt_d;
+};
+
+struct Phys {
+  SpConst sp[2];
+  float dtdx;
+  float ngs_el, ngs_ex, ngs_iz, ngs_cx;  // n_gas * sigma
+  float E_ex, E_iz, inv_E_ex, inv_E_iz;
+  float two_m_over_M;
+  float vt_gas;  // sqrt(Tg / m_ion)
+  float E_ext;
+  float src_x1;
+  double dtdx_d, ngs_el_d, ngs_ex_d, ngs_iz_d, ngs_cx_d, E_ex_d, E_iz_d, two_m_over_M_d,
+      vt_gas_d, E_ext_d, src_x1_d;
+  unsigned int coll_mask, field_mode, push_mask, has_B;
+  int N;
+  unsigned long long seed;
+};
+
+struct StepParams32 {
+  Species32 sp[2];
+  unsigned long long cap[2];
+  const float2* E2;
+  unsigned int* cnt[2];
+  unsigned long long* S[2];
+  Ctl* ctl;
+  Phys ph;
+  unsigned long long step;
+};
+
+struct StepParams64 {
+  Species64 sp[2];
+  unsigned long long cap[2];
+  const double* E;
+  double* acc[2];  // rho accumulators (particle units) at N + 1 nodes
+  Ctl* ctl;
+  Phys ph;
+  unsigned long long step;
+};
+
+// --------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round forms the two
+// 32x32 -> 64-bit products of counter words 0 and 2 with the round multipliers and mixes their
+// halves with words 1, 3 and the key; the key advances by the two Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ k.x, (unsigned)p1, (unsigned)(p0 >> 32) ^ c.w ^ k.y,
+                   (unsigned)p0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 draw4(unsigned long long id, unsigned long long seed,
+                                       unsigned long long step, unsigned ch, unsigned idx) {
+  unsigned long long k = id ^ seed;
+  return philox10(make_uint4((unsigned)step, (unsigned)(step >> 32), ch, idx),
+                  make_uint2((unsigned)k, (unsigned)(k >> 32)));
+}
+
+// 24-bit uniform in [0, 1): exact in FP32 and FP64
+__device__ __forceinline__ float u01f(unsigned w) { return (float)(w >> 8) * 5.9604644775390625e-08f; }
+__device__ __forceinline__ double u01d(unsigned w) { return (double)(w >> 8) * 5.9604644775390625e-08; }
+
+__host__ __device__ inline unsigned long long round_up4(unsigned long long n) { return (n + 3ull) & ~3ull; }
+
+// launchers (each file owns its kernels)
+struct PoissonParams {
+  // input: either fixed-point counts (cnt/S) or FP64 accumulators (acc) or a plain rho
+  const unsigned int* cnt[2];
+  unsigned long long* S[2];
+  double* acc[2];
+  const double* rho_in;
+  double qw[2];     // q_s * w_s
+  int mode;         // 0: fixed point, 1: FP64 accumulators, 2: plain rho
+  int keep_counts;  // fixed point: leave cnt for the sort
+  int N;
+  double dx, V_L, V_R;
+  long long* R[2];  // out (fixed point mode)
+  double* rho;      // out (modes 0, 1)
+  double* phi;
+  double* E;
+  float2* E2;       // out, may be null
+  Ctl* ctl;         // bookkeeping, may be null
+  int count_step;   // add the live particles at the start of this step to particle_steps
+  Species32 pad32[2];
+  Species64 pad64[2];
+  unsigned long long cap[2];
+  int plain;
+};
+
+cudaError_t launch_field(const PoissonParams& p, cudaStream_t st);
+cudaError_t launch_step32(const StepParams32& p, int grid, cudaStream_t st);
+cudaError_t launch_step64(const StepParams64& p, int grid, cudaStream_t st);
+cudaError_t launch_source32(const StepParams32& p, cudaStream_t st);
+cudaError_t launch_source64(const StepParams64& p, cudaStream_t st);
+cudaError_t launch_load32(const StepParams32& p, const unsigned long long n[2], int profile,
+                          int ppc0, int ppc1, double scale, int mode, cudaStream_t st);
+cudaError_t launch_load64(const StepParams64& p, const unsigned long long n[2], int profile,
+                          int ppc0, int ppc1, double scale, int mode, cudaStream_t st);
+cudaError_t launch_sort32(Species32 src[2], Species32 dst[2], unsigned int* cnt[2],
+                          unsigned int* cursor[2], const unsigned long long cap[2], Ctl* ctl, int N,
+                          int grid, cudaStream_t st);
+cudaError_t launch_diag32(const StepParams32& p, int grid, cudaStream_t st);
+cudaError_t launch_diag64(const StepParams64& p, int grid, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
+                          cudaStream_t st);

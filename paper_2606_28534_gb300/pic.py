@@ -1,0 +1,247 @@
+"""Python binding of the C ABI in ``include/pic.h`` (argument marshalling only).
+
+Every step of the PIC MC cycle runs in the CUDA kernels of ``libpicgb.so``; this module fills the
+``pic_config`` struct, hands over device memory and the CUDA stream owned by PyTorch, and converts
+results to Python objects.  There is no CPU fallback: without the built library and a CUDA device
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpicgb.so")
+_lib = None
+
+PIC_ABI_VERSION = 1
+PIC_KERNEL_KINDS = 8
+STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_EOVERFLOW",
+          5: "PIC_ECORRUPT", 6: "PIC_ETIMEOUT", 7: "PIC_EDEVICE"}
+
+
+class PicError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({lib().pic_strerror(status).decode()})")
+        self.status = status
+
+
+class PicConfig(C.Structure):
+    _fields_ = [
+        ("abi_version", C.c_uint32), ("precision", C.c_uint32), ("ncells", C.c_int32),
+        ("ppc", C.c_int32 * 2), ("load_profile", C.c_int32), ("profile_mode", C.c_int32),
+        ("source_mode", C.c_int32), ("sort_interval", C.c_int32), ("coll_mask", C.c_uint32),
+        ("field_mode", C.c_uint32), ("frozen_mask", C.c_uint32), ("L", C.c_double),
+        ("dt", C.c_double), ("mass", C.c_double * 2), ("charge", C.c_double * 2),
+        ("T", C.c_double * 2), ("Tg", C.c_double), ("m_gas", C.c_double), ("B", C.c_double),
+        ("B_angle_deg", C.c_double), ("V_left", C.c_double), ("V_right", C.c_double),
+        ("n_gas", C.c_double), ("sigma_el", C.c_double), ("sigma_ex", C.c_double),
+        ("E_ex", C.c_double), ("sigma_iz", C.c_double), ("E_iz", C.c_double),
+        ("sigma_cx", C.c_double), ("E_cap", C.c_double), ("E_ext", C.c_double),
+        ("profile_scale", C.c_double), ("source_x1", C.c_double), ("capacity_factor", C.c_double),
+        ("seed", C.c_uint64),
+    ]
+
+
+class PicDiag(C.Structure):
+    _fields_ = [
+        ("step", C.c_uint64), ("n", C.c_uint64 * 2), ("wall_hits", (C.c_uint64 * 2) * 2),
+        ("coll", C.c_uint64 * 5), ("near_threshold", C.c_uint64 * 2),
+        ("nu_max_violations", C.c_uint64 * 2), ("births", C.c_uint64 * 2),
+        ("source_pairs", C.c_uint64), ("dropped", C.c_uint64),
+        ("net_charge_units", C.c_int64), ("wall_charge", C.c_int64), ("ke", C.c_double * 2),
+        ("field_energy", C.c_double), ("wall_energy", C.c_double * 2),
+        ("particle_steps", C.c_uint64),
+    ]
+
+
+#: every entry point of include/pic.h
+SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapshot", "pic_restore",
+           "pic_diag", "pic_get_field", "pic_profile", "pic_kernel_times", "pic_free",
+           "pic_strerror", "pic_philox", "pic_poisson")
+
+
+def lib():
+    """Load ``libpicgb.so`` (built by ``build.py``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2606_28534_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        P, V = C.POINTER, C.c_void_p
+        L.pic_workspace_size.argtypes = [P(PicConfig), P(C.c_size_t)]
+        L.pic_init.argtypes = [P(PicConfig), V, C.c_size_t, V, P(V)]
+        L.pic_step.argtypes = [V, C.c_int32]
+        L.pic_sync.argtypes = [V]
+        L.pic_snapshot.argtypes = [V, V, C.c_size_t, P(C.c_size_t)]
+        L.pic_restore.argtypes = [V, V, C.c_size_t]
+        L.pic_diag.argtypes = [V, P(PicDiag)]
+        L.pic_get_field.argtypes = [V, P(C.c_int64), P(C.c_double), P(C.c_double), P(C.c_float),
+                                    C.c_size_t]
+        L.pic_profile.argtypes = [V, C.c_int]
+        L.pic_kernel_times.argtypes = [V, P(C.c_double), P(C.c_uint64), P(C.c_char_p), C.c_int32]
+        L.pic_free.argtypes = [V]
+        L.pic_free.restype = None
+        L.pic_strerror.argtypes = [C.c_int]
+        L.pic_strerror.restype = C.c_char_p
+        L.pic_philox.argtypes = [V, V, V, C.c_size_t, V]
+        L.pic_poisson.argtypes = [V, C.c_int32, C.c_double, C.c_double, C.c_double, V, V, V]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise PicError(rc, what)
+
+
+def make_config(p: dict) -> PicConfig:
+    """Fill a ``pic_config`` from a workload dict (see ``workloads.py``)."""
+    c = PicConfig()
+    c.abi_version = PIC_ABI_VERSION
+    for name, _ in PicConfig._fields_:
+        if name == "abi_version" or name not in p:
+            continue
+        v = p[name]
+        if name in ("ppc", "mass", "charge", "T"):
+            a = getattr(c, name)
+            a[0], a[1] = v[0], v[1]
+        else:
+            setattr(c, name, v)
+    return c
+
+
+def workspace_size(params: dict) -> int:
+    c = make_config(params)
+    n = C.c_size_t(0)
+    _check(lib().pic_workspace_size(C.byref(c), C.byref(n)), "pic_workspace_size")
+    return n.value
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required (no CPU fallback)")
+    return torch
+
+
+def _diag_dict(d: PicDiag) -> dict:
+    return {
+        "step": d.step, "n": [d.n[0], d.n[1]],
+        "wall_hits": [[d.wall_hits[s][k] for k in range(2)] for s in range(2)],
+        "coll": list(d.coll), "near_threshold": list(d.near_threshold),
+        "nu_max_violations": list(d.nu_max_violations), "births": list(d.births),
+        "source_pairs": d.source_pairs, "dropped": d.dropped,
+        "net_charge_units": d.net_charge_units, "wall_charge": d.wall_charge,
+        "ke": [d.ke[0], d.ke[1]], "field_energy": d.field_energy,
+        "wall_energy": [d.wall_energy[0], d.wall_energy[1]],
+        "particle_steps": d.particle_steps,
+    }
+
+
+class Simulation:
+    """One simulation on one GPU; device memory is a torch uint8 workspace tensor."""
+
+    def __init__(self, params: dict, device=None, stream=None):
+        torch = _torch()
+        self.params = dict(params)
+        self.N = int(params["ncells"])
+        self.device = torch.device(device if device is not None else "cuda")
+        self._cfg = make_config(params)
+        nbytes = workspace_size(params)
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().pic_init(C.byref(self._cfg), C.c_void_p(self._ws.data_ptr()), nbytes,
+                                C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        _check(rc, "pic_init")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_free(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        _check(lib().pic_step(self._h, int(n)), "pic_step")
+
+    def sync(self):
+        _check(lib().pic_sync(self._h), "pic_sync")
+
+    def diag(self) -> dict:
+        d = PicDiag()
+        _check(lib().pic_diag(self._h, C.byref(d)), "pic_diag")
+        return _diag_dict(d)
+
+    def fields(self) -> dict:
+        n1 = self.N + 1
+        R = np.empty(2 * n1, np.int64)
+        rho, phi = np.empty(n1), np.empty(n1)
+        E = np.empty(n1, np.float32)
+        _check(lib().pic_get_field(self._h, R.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   rho.ctypes.data_as(C.POINTER(C.c_double)),
+                                   phi.ctypes.data_as(C.POINTER(C.c_double)),
+                                   E.ctypes.data_as(C.POINTER(C.c_float)), n1), "pic_get_field")
+        return {"R": R.reshape(2, n1), "rho": rho, "phi": phi, "E": E}
+
+    def snapshot(self) -> bytes:
+        need = C.c_size_t(0)
+        _check(lib().pic_snapshot(self._h, None, 0, C.byref(need)), "pic_snapshot")
+        buf = C.create_string_buffer(need.value)
+        _check(lib().pic_snapshot(self._h, buf, need.value, C.byref(need)), "pic_snapshot")
+        return buf.raw[: need.value]
+
+    def restore(self, blob: bytes) -> int:
+        """Returns the status (0 = ok) instead of raising, so that tests can check error codes."""
+        return int(lib().pic_restore(self._h, blob, len(blob)))
+
+    def profile(self, enable: bool):
+        _check(lib().pic_profile(self._h, 1 if enable else 0), "pic_profile")
+
+    def kernel_times(self) -> dict:
+        ms = (C.c_double * PIC_KERNEL_KINDS)()
+        ln = (C.c_uint64 * PIC_KERNEL_KINDS)()
+        names = (C.c_char_p * PIC_KERNEL_KINDS)()
+        _check(lib().pic_kernel_times(self._h, ms, ln, names, PIC_KERNEL_KINDS), "pic_kernel_times")
+        return {names[k].decode(): {"ms": ms[k], "launches": int(ln[k])}
+                for k in range(PIC_KERNEL_KINDS) if names[k] and names[k].decode()}
+
+
+def philox(ctr, key, stream=None):
+    """Philox4x32-10 on the GPU: ctr (n, 4) and key (n, 2) int32/uint32 CUDA tensors -> (n, 4)."""
+    torch = _torch()
+    n = ctr.shape[0]
+    out = torch.empty((n, 4), dtype=ctr.dtype, device=ctr.device)
+    st = stream if stream is not None else torch.cuda.current_stream(ctr.device)
+    _check(lib().pic_philox(C.c_void_p(ctr.data_ptr()), C.c_void_p(key.data_ptr()),
+                            C.c_void_p(out.data_ptr()), n, C.c_void_p(st.cuda_stream)), "pic_philox")
+    return out
+
+
+def poisson(rho, dx: float, V_L: float, V_R: float, stream=None):
+    """Field solve on the GPU: rho (N+1,) float64 CUDA tensor -> (phi, E)."""
+    torch = _torch()
+    N = rho.shape[0] - 1
+    phi = torch.empty_like(rho)
+    E = torch.empty_like(rho)
+    st = stream if stream is not None else torch.cuda.current_stream(rho.device)
+    _check(lib().pic_poisson(C.c_void_p(rho.data_ptr()), N, dx, V_L, V_R, C.c_void_p(phi.data_ptr()),
+                             C.c_void_p(E.data_ptr()), C.c_void_p(st.cuda_stream)), "pic_poisson")
+    return phi, E
+
+
+__all__ = ["Simulation", "philox", "poisson", "make_config", "workspace_size", "lib", "PicError",
+           "SYMBOLS", "W"]
