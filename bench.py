@@ -159,6 +159,7 @@ W_DESC = {
     "c3": "non-uniform load, 65536 cells, 100,007,936 particles, exp(-x/(L/8)) + pair source, "
           "B 0.5 @ 30 deg, 4 processes, sort every 10 steps",
     "c5": "collisionless, 1024 cells, 409,600 particles",
+    "c3p": "non-uniform load profiling case, 65536 cells, 12,582,912 particles",
 }
 
 

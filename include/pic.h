@@ -72,7 +72,7 @@ extern "C" {
 typedef struct pic_config {
   uint32_t abi_version;
   uint32_t precision;     /* PIC_FP32 or PIC_FP64_PLAIN */
-  int32_t ncells;         /* N >= 2 cells, N + 1 nodes; PIC_FP32 needs N <= 262143 */
+  int32_t ncells;         /* N >= 2 cells, N + 1 nodes; N <= 196607 */
   int32_t ppc[2];         /* mean particles per cell per species (>= 1) */
   int32_t load_profile;   /* PIC_LOAD_* */
   int32_t profile_mode;   /* mode number m of PIC_LOAD_QUIET_SINE */
@@ -101,7 +101,7 @@ typedef struct pic_config {
   double profile_scale;   /* PIC_LOAD_EXP scale length / PIC_LOAD_QUIET_SINE amplitude (cells) */
   double source_x1;       /* end of the source region (cells), 0 < source_x1 <= N */
   double capacity_factor; /* particle buffer capacity per species = factor * ppc * N (>= 1) */
-  uint64_t seed;          /* XORed into every particle's random-number key */
+  uint64_t seed;          /* run seed (enters every Philox key and counter) */
 } pic_config;
 
 /* Diagnostics (cumulative since pic_init unless stated). */
@@ -190,7 +190,7 @@ int pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n
  * -phi_{j-1} + 2 phi_j - phi_{j+1} = dx^2 rho_j, phi_0 = V_L, phi_N = V_R, solved exactly by
  * the discrete Green's function (two prefix scans in FP64), then E_j = (phi_{j-1}-phi_{j+1})/2dx
  * inside and Gauss's law over the half cell at each wall.  rho, phi, E: N + 1 FP64 device
- * values.  Needs no workspace; 2 <= N <= 262143.  Asynchronous on stream. */
+ * values.  Needs no workspace; 2 <= N <= 196607.  Asynchronous on stream. */
 int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double V_R,
                 double* phi, double* E, void* cuda_stream);
 

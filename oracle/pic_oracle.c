@@ -16,8 +16,8 @@
  *       saturating at twice the threshold.
  *   R8  null-collision bound nu_max = n_g * sum(sigma_max) * v_cap, v_cap = sqrt(2 E_cap'/m),
  *       E_cap' = E_cap + |V_L - V_R|; rounded to FP32 and shared by both codes by value.
- *   R9  Philox4x32-10 keyed by (particle id ^ seed), counter (step lo, step hi, channel, index);
- *       uniform u = (word >> 8) * 2^-24.
+ *   R9  Philox4x32-10: key (step lo, seed lo), counter (id lo, id hi, channel | step hi << 8,
+ *       index ^ seed hi); uniform u = (word >> 8) * 2^-24.
  *   R10 isotropic scattering; elastic energy loss 2m/M (1 - cos chi); excitation loses E_ex;
  *       ionization splits E - E_iz uniformly; new ion and CX ion Maxwellian at T_g.
  *   R11 child ids are Philox words of (parent id, step, CHILD channel).
@@ -86,11 +86,14 @@ void orc_philox_batch(size_t n, const uint32_t* ctr, const uint32_t* key, uint32
 /* uniform in [0,1) with 24 bits: exact in both FP32 and FP64 (R9) */
 static double u01(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
 
+/* One Philox block for (particle id, step, channel, index) under the run's seed (R9): the key is
+ * (step, seed) and the counter (id, channel, index), with the high halves of step and seed folded
+ * into the counter, so that distinct (id, step, channel, index) give distinct (key, counter). */
 static void draw(uint64_t id, uint64_t seed, uint64_t step, uint32_t channel, uint32_t index,
                  uint32_t w[4]) {
-  uint64_t k = id ^ seed;
-  uint32_t key[2] = {(uint32_t)k, (uint32_t)(k >> 32)};
-  uint32_t ctr[4] = {(uint32_t)step, (uint32_t)(step >> 32), channel, index};
+  uint32_t key[2] = {(uint32_t)step, (uint32_t)seed};
+  uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), channel | ((uint32_t)(step >> 32) << 8),
+                     index ^ (uint32_t)(seed >> 32)};
   orc_philox4x32_10(ctr, key, w);
 }
 

@@ -85,7 +85,7 @@ typedef struct {
   double E_ext;           /* ORC_FIELD_EXTERNAL field */
   double profile_scale;   /* EXP: scale length (dx units); QUIET_SINE: amplitude (dx units) */
   double source_x1;       /* source region [0, source_x1) (dx units) */
-  uint64_t seed;          /* XORed into every particle key */
+  uint64_t seed;          /* run seed: part of every Philox key and counter */
 } orc_config;
 
 typedef struct {

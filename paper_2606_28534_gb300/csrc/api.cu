@@ -179,6 +179,7 @@ void derive(pic_handle* h) {
     const double vcap = std::sqrt(2.0 * Ecap / c.mass[s]);
     k.nu_max = (float)(c.n_gas * smax[s] * vcap);
     k.p_null = (float)(1.0 - std::exp(-(double)k.nu_max * c.dt));
+    k.p_null_u24 = (unsigned)std::ceil((double)k.p_null * 16777216.0);
   }
   p.dtdx_d = c.dt / dx;
   p.dtdx = (float)p.dtdx_d;
@@ -270,6 +271,30 @@ StepParams64 params64(pic_handle* h) {
   return P;
 }
 
+// Integer-exact field (k_field_exact) when both charges are small integers: the net deposit
+// r = m_0 R_0 + m_1 R_1 with m_s = q_s ppc_{1-s} / g (g = gcd of the ppc) is an exact integer and
+// f = kappa r with kappa = dx^2 2^-32 g / (ppc_0 ppc_1).
+void exact_coefficients(pic_handle* h, PoissonParams* F) {
+  const pic_config& c = h->cfg;
+  F->exact = 0;
+  if (h->plain) return;
+  long long g = std::gcd((long long)c.ppc[0], (long long)c.ppc[1]);
+  for (int s = 0; s < 2; ++s) {
+    const double q = c.charge[s];
+    if (q != std::floor(q) || std::fabs(q) > 64.0) return;
+    const long long other = (long long)c.ppc[1 - s] / g;
+    if (other > 1024) return;
+    F->m[s] = (long long)q * other;
+  }
+  const int N = c.ncells;
+  const double dx = c.L / N;
+  const double kappa = dx * dx * 2.3283064365386963e-10 * (double)g / ((double)c.ppc[0] * (double)c.ppc[1]);
+  F->e_in = kappa / (2.0 * N * dx);
+  F->e_wall = kappa / ((double)N * dx);
+  F->e_bias = (c.V_left - c.V_right) / ((double)N * dx);
+  F->exact = 1;
+}
+
 PoissonParams field_params(pic_handle* h, bool keep_counts, bool count_step) {
   PoissonParams F;
   std::memset(&F, 0, sizeof(F));
@@ -285,6 +310,8 @@ PoissonParams field_params(pic_handle* h, bool keep_counts, bool count_step) {
     F.pad64[s] = h->a64[s];
   }
   F.mode = h->plain ? 1 : 0;
+  F.inv_dx = 1.0 / dx;
+  exact_coefficients(h, &F);
   F.keep_counts = keep_counts ? 1 : 0;
   F.count_step = count_step ? 1 : 0;
   F.N = h->N;
@@ -329,6 +356,19 @@ int refresh_field(pic_handle* h) {
     prof_end(h, &e);
     h->cur = 1 - h->cur;
   }
+  return PIC_OK;
+}
+
+// rho and phi of the current deposit, from the stored node deposits (FP64 Green's function);
+// the node field the particles use is left as the step computed it.
+int field_diagnostics(pic_handle* h) {
+  PoissonParams F = field_params(h, true, false);
+  F.mode = 3;
+  F.ctl = nullptr;
+  F.E = nullptr;
+  F.E2 = nullptr;
+  if (h->plain) return PIC_OK;  // the plain path's solve already produced rho and phi
+  CK(launch_field(F, h->st));
   return PIC_OK;
 }
 
@@ -648,6 +688,8 @@ int pic_diag(pic_handle* h, pic_diag_t* d) {
   int rc = check_errors(h);
   if (rc != PIC_OK) return rc;
   CK(cudaMemsetAsync(h->ctl->ke_fx, 0, sizeof(h->ctl->ke_fx), h->st));
+  rc = field_diagnostics(h);
+  if (rc != PIC_OK) return rc;
   EvPair e;
   prof_begin(h, K_DIAG, &e);
   CK(h->plain ? launch_diag64(params64(h), h->grid_diag, h->st) : launch_diag32(params32(h), h->grid_diag, h->st));
@@ -696,6 +738,9 @@ int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E,
   if (!h || nnodes != (size_t)h->N + 1) return PIC_EINVAL;
   int rc = check_errors(h);
   if (rc != PIC_OK) return rc;
+  rc = field_diagnostics(h);
+  if (rc != PIC_OK) return rc;
+  CK(cudaStreamSynchronize(h->st));
   if (R) {
     CK(cudaMemcpy(R, h->R[0], sizeof(int64_t) * nnodes, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(R + nnodes, h->R[1], sizeof(int64_t) * nnodes, cudaMemcpyDeviceToHost));
@@ -937,6 +982,7 @@ int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double
   std::memset(&F, 0, sizeof(F));
   F.rho_in = rho;
   F.mode = 2;
+  F.inv_dx = 1.0 / dx;
   F.N = ncells;
   F.dx = dx;
   F.V_L = V_L;

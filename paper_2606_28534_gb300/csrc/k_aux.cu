@@ -2,7 +2,7 @@
 //
 // Load (paper Sec. 2: "initialization of the simulation domain, particle load"): particle i of
 // species s has id i (electrons) or 2^62 | i (ions); its position and velocity come from the
-// Philox blocks (id ^ seed; step 0, INIT, 0) and (id ^ seed; 0, INIT, 1), evaluated in FP64 and
+// Philox blocks (id, step 0, INIT, 0) and (id, step 0, INIT, 1), evaluated in FP64 and
 // rounded once to the storage precision.  Profiles: uniform (ppc per cell, random in the cell),
 // exponential (inverse CDF of exp(-x/lambda) truncated to [0, L)), quiet sine (evenly spaced,
 // species 0 displaced by A sin(2 pi m x / L)).

@@ -1,20 +1,32 @@
 // k_field.cu -- deposit finalisation, field solve and node field of the PIC cycle (paper Sec. 2:
 // "deposition to the grid" and "field solver"; BIT1's native Poisson solver).
 //
-// One thread-block cluster of PIC_FIELD_CTAS CTAs handles the whole grid (N + 1 nodes; each
-// thread a run of consecutive nodes):
-//   1. node deposits R_sj from the per-cell counts and right-weight sums written by the particle
-//      step (R_j = 2^32 cnt_j - S_j + S_{j-1}, exact int64), node density
-//      rho_j = sum_s q_s w_s R_sj 2^-32 / vol_j (vol = dx inside, dx/2 at the walls);
-//   2. the interior problem -phi_{j-1} + 2 phi_j - phi_{j+1} = f_j = dx^2 rho_j (eps0 = 1),
-//      phi_0 = V_L, phi_N = V_R, solved by its exact inverse (the discrete Green's function
-//      G_jk = min(j,k) (N - max(j,k)) / N):
-//        phi_j = [ (N-j) A_j + j B_j ] / N + V_L (N-j)/N + V_R j/N,
-//        A_j = sum_{k<=j} k f_k,   B_j = sum_{k>j} (N-k) f_k,
-//      i.e. two FP64 prefix scans; the CTA totals are exchanged through distributed shared memory;
-//   3. E_j = (phi_{j-1} - phi_{j+1}) / (2 dx) inside, Gauss's law over the half cell at the
-//      walls, stored as FP64 and as the node pairs (E_c, E_{c+1}) in FP32 that the particles read.
-// The CTA count is fixed, so the summation order, and hence every bit of phi, is reproducible.
+// The interior problem -phi_{j-1} + 2 phi_j - phi_{j+1} = f_j = dx^2 rho_j (eps0 = 1),
+// phi_0 = V_L, phi_N = V_R, has the exact inverse (discrete Green's function)
+//   G_jk = min(j,k) (N - max(j,k)) / N,
+//   phi_j = [ (N-j) A_j + j B_j ] / N + V_L (N-j)/N + V_R j/N,
+//   A_j = sum_{k<=j} k f_k,  B_j = sum_{k>j} (N-k) f_k,
+// and the node field is E_j = (phi_{j-1} - phi_{j+1}) / (2 dx) inside, Gauss's law over the half
+// cell at the walls: E_0 = (phi_0 - phi_1)/dx - rho_0 dx/2, E_N = (phi_{N-1} - phi_N)/dx + rho_N dx/2.
+//
+// Two implementations, each one thread-block cluster of PIC_FIELD_CTAS CTAs; a CTA stages its
+// contiguous segment of the N + 1 nodes in shared memory with coalesced loads, each thread scans a
+// run of consecutive nodes, and CTA totals travel through distributed shared memory.  The CTA
+// count is fixed, so every bit of the result is reproducible.
+//
+// k_field_exact (FP32 path, integer species charges; the per-step solve).  FP64 runs at a small
+// fraction of the FP32/INT32 rate on this GPU, and the deposit is already exact int64, so the
+// solve stays in integers: with r_j = m_0 R_0j + m_1 R_1j (m_s = q_s ppc_{1-s}, so that
+// f_j = kappa r_j with kappa = dx^2 2^-32 / (ppc_0 ppc_1)), the cumulative charge Q_j = sum_{k<=j}
+// r_k over interior nodes, and T = N Q_N - sum_k k r_k, the Green's-function formula reduces to
+//   E_j = kappa / (2 N dx) * [ N (Q_j + Q_{j-1}) - 2 T ] + (V_L - V_R) / (N dx)       (0 < j < N)
+//   E_0 = -kappa / (N dx) * [ T + N r_0 ] + (V_L - V_R) / (N dx),
+//   E_N =  kappa / (N dx) * [ sum_k k r_k + N r_N ] + (V_L - V_R) / (N dx),
+// (r_0, r_N: the wall-node deposits), with the brackets exact in int128 and one FP64 rounding per
+// node.  phi and rho are needed only by the diagnostics and come from k_field_fp64 on demand.
+//
+// k_field_fp64 (plain FP64 path, the pic_poisson operation, diagnostics, non-integer charges):
+// the Green's-function formula above in FP64 with two prefix scans.
 #include <cooperative_groups.h>
 
 #include "pic_internal.cuh"
@@ -41,83 +53,268 @@ __device__ __forceinline__ Pair warp_incl_scan(Pair v) {
   return v;
 }
 
+__device__ __forceinline__ __int128 shfl_up_i128(__int128 v, int o) {
+  long long lo = (long long)(unsigned long long)v;
+  long long hi = (long long)(v >> 64);
+  lo = __shfl_up_sync(0xFFFFFFFFu, lo, o);
+  hi = __shfl_up_sync(0xFFFFFFFFu, hi, o);
+  return ((__int128)hi << 64) | (__int128)(unsigned long long)lo;
+}
+
+__device__ __forceinline__ double i128_to_double(__int128 x) {
+  const long long hi = (long long)(x >> 64);
+  const unsigned long long lo = (unsigned long long)x;
+  if ((hi == 0 && (long long)lo >= 0) || (hi == -1 && (long long)lo < 0)) return (double)(long long)lo;
+  return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+// node deposit R_sj from the per-cell counts and right-weight sums: R_j = 2^32 cnt_j - S_j + S_{j-1}
+__device__ __forceinline__ long long node_R(const PoissonParams& P, int s, int j) {
+  unsigned long long r = 0ull;
+  if (j < P.N) r += ((unsigned long long)P.cnt[s][j] << 32) - P.S[s][j];
+  if (j > 0) r += P.S[s][j - 1];
+  return (long long)r;
+}
+
+// particle-array bookkeeping after the deposits of a step (one thread)
+__device__ void bookkeeping(const PoissonParams& P) {
+  Ctl* g = P.ctl;
+  const unsigned long long c0 = g->n_cur[0], c1 = g->n_cur[1], b0 = g->n_born[0], b1 = g->n_born[1];
+  const unsigned long long l0 = g->n_live[0], l1 = g->n_live[1], mark = g->live_mark;
+  if (P.count_step) g->particle_steps += mark;
+  g->live_mark = l0 + l1;
+  for (int s = 0; s < 2; ++s) {
+    unsigned long long n = (s ? c1 + b1 : c0 + b0);
+    if (n > P.cap[s]) n = P.cap[s];
+    const unsigned long long pad = round_up4(n);
+    for (unsigned long long i = n; i < pad; ++i) {
+      if (P.plain)
+        P.pad64[s].x[i] = -1.0;
+      else
+        P.pad32[s].cell[i] = PIC_DEAD_CELL;
+    }
+    g->n_cur[s] = pad;
+    g->n_born[s] = 0ull;
+  }
+  g->src_K = 0ull;
+}
+
+// =============================================================================================
+__global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIELD_TPB, 1)
+    k_field_exact(const __grid_constant__ PoissonParams P) {
+  extern __shared__ long long Rn[];  // r_j of this CTA's segment, then E_j (as double bits)
+  __shared__ __int128 warp_q[PIC_FIELD_TPB / 32], warp_p[PIC_FIELD_TPB / 32];
+  __shared__ __int128 cta_q, cta_p;  // read by the other CTAs of the cluster
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int rank = (int)cluster.block_rank();
+  const int N = P.N;
+  const int M = N + 1;
+  const int seg = (M + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
+  const int a = rank * seg;
+  const int len = max(0, min(seg, M - a));
+
+  if (P.ctl && rank == 0 && tid == 0) bookkeeping(P);
+
+  // ---- pass 1 (coalesced): node deposits, net integer charge ------------------------------------
+  for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+    const int j = a + i;
+    const long long R0 = node_R(P, 0, j), R1 = node_R(P, 1, j);
+    P.R[0][j] = R0;
+    P.R[1][j] = R1;
+    const __int128 rn = (__int128)P.m[0] * R0 + (__int128)P.m[1] * R1;
+    if (rn > (__int128)0x7FFFFFFFFFFFFFFFll || rn < -(__int128)0x7FFFFFFFFFFFFFFFll) {
+      atomicOr(&P.ctl->error, ERR_DEVICE);  // net deposit beyond int64: report, never wrap silently
+    }
+    Rn[i] = (long long)rn;
+  }
+  __syncthreads();
+
+  // ---- per-thread runs: Q (cumulative interior charge) and sum of k r_k -------------------------
+  const int items = (len + PIC_FIELD_TPB - 1) / PIC_FIELD_TPB;
+  const int i0 = tid * items;
+  __int128 oq = 0, op = 0;
+  for (int k = 0; k < items; ++k) {
+    const int i = i0 + k;
+    if (i >= len) break;
+    const int j = a + i;
+    if (j >= 1 && j <= N - 1) {
+      oq += (__int128)Rn[i];
+      op += (__int128)Rn[i] * j;
+    }
+  }
+  __int128 iq = oq, ip = op;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const __int128 uq = shfl_up_i128(iq, o), up = shfl_up_i128(ip, o);
+    if (lane >= o) {
+      iq += uq;
+      ip += up;
+    }
+  }
+  if (lane == 31) {
+    warp_q[w] = iq;
+    warp_p[w] = ip;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    __int128 vq = warp_q[tid], vp = warp_p[tid];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const __int128 uq = shfl_up_i128(vq, o), up = shfl_up_i128(vp, o);
+      if (lane >= o) {
+        vq += uq;
+        vp += up;
+      }
+    }
+    warp_q[tid] = vq;
+    warp_p[tid] = vp;
+    if (tid == 31) {
+      cta_q = vq;
+      cta_p = vp;
+    }
+  }
+  __syncthreads();
+  __int128 q = (w ? warp_q[w - 1] : (__int128)0) + iq - oq;  // exclusive prefix within the CTA
+  cluster.sync();  // CTA totals visible; every input of pass 1 has been read
+  __int128 Qtot = 0, Ptot = 0;
+#pragma unroll
+  for (int r = 0; r < PIC_FIELD_CTAS; ++r) {
+    const __int128 vq = *cluster.map_shared_rank(&cta_q, r);
+    const __int128 vp = *cluster.map_shared_rank(&cta_p, r);
+    if (r < rank) q += vq;
+    Qtot += vq;
+    Ptot += vp;
+  }
+  // clear the deposit accumulators for the next step (coalesced)
+  for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+    const int j = a + i;
+    if (j < N) {
+      P.S[0][j] = 0ull;
+      P.S[1][j] = 0ull;
+      if (!P.keep_counts) {
+        const_cast<unsigned int*>(P.cnt[0])[j] = 0u;
+        const_cast<unsigned int*>(P.cnt[1])[j] = 0u;
+      }
+    }
+  }
+
+  // ---- pass 2: node field in place --------------------------------------------------------------
+  const __int128 T = (__int128)N * Qtot - Ptot;
+  for (int k = 0; k < items; ++k) {
+    const int i = i0 + k;
+    if (i >= len) break;
+    const int j = a + i;
+    const __int128 r = Rn[i];
+    double E;
+    if (j == 0) {
+      E = -P.e_wall * i128_to_double(T + (__int128)N * r) + P.e_bias;
+    } else if (j == N) {
+      E = P.e_wall * i128_to_double(Ptot + (__int128)N * r) + P.e_bias;
+    } else {
+      const __int128 qprev = q;
+      q += r;
+      E = P.e_in * i128_to_double((__int128)N * (q + qprev) - 2 * T) + P.e_bias;
+    }
+    Rn[i] = __double_as_longlong(E);
+  }
+  __syncthreads();
+  for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+    const int j = a + i;
+    const double E = __longlong_as_double(Rn[i]);
+    P.E[j] = E;
+    if (j < N) P.E2[j].x = (float)E;
+    if (j > 0) P.E2[j - 1].y = (float)E;
+  }
+  cluster.sync();  // keep the shared totals alive until every CTA has read them
+}
+
+// =============================================================================================
+// FP64 Green's function.  MODE 0: from the per-cell counts (non-integer charges), 1: from the
+// FP64 accumulators of the plain path, 2: from a given rho (pic_poisson), 3: from the stored R
+// (diagnostics: rho and phi, and E only when asked for).
 template <int MODE>
 __device__ __forceinline__ double node_rho(const PoissonParams& P, int j) {
-  const int N = P.N;
-  const double vol = (j == 0 || j == N) ? 0.5 * P.dx : P.dx;
+  const double inv_vol = (j == 0 || j == P.N) ? 2.0 * P.inv_dx : P.inv_dx;
   if (MODE == 0) {
-    long long R[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      unsigned long long r = 0ull;
-      if (j < N) r += ((unsigned long long)P.cnt[s][j] << 32) - P.S[s][j];
-      if (j > 0) r += P.S[s][j - 1];
-      R[s] = (long long)r;
-      P.R[s][j] = R[s];
-    }
-    return (P.qw[0] * (double)R[0] + P.qw[1] * (double)R[1]) * 2.3283064365386963e-10 / vol;
+    const long long R0 = node_R(P, 0, j), R1 = node_R(P, 1, j);
+    P.R[0][j] = R0;
+    P.R[1][j] = R1;
+    return (P.qw[0] * (double)R0 + P.qw[1] * (double)R1) * 2.3283064365386963e-10 * inv_vol;
   } else if (MODE == 1) {
-    double a0 = P.acc[0][j], a1 = P.acc[1][j];
+    const double a0 = P.acc[0][j], a1 = P.acc[1][j];
     P.R[0][j] = __double2ll_rn(a0 * 4294967296.0);
     P.R[1][j] = __double2ll_rn(a1 * 4294967296.0);
-    return (P.qw[0] * a0 + P.qw[1] * a1) / vol;
-  } else {
+    return (P.qw[0] * a0 + P.qw[1] * a1) * inv_vol;
+  } else if (MODE == 2) {
     return P.rho_in[j];
+  } else {
+    return (P.qw[0] * (double)P.R[0][j] + P.qw[1] * (double)P.R[1][j]) * 2.3283064365386963e-10 * inv_vol;
   }
 }
 
 template <int MODE>
 __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIELD_TPB, 1)
-    k_field(const PoissonParams P) {
-  cg::cluster_group cluster = cg::this_cluster();
+    k_field_fp64(const __grid_constant__ PoissonParams P) {
+  extern __shared__ double F[];  // this CTA's segment: f_j = dx^2 rho_j, then phi_j
   __shared__ Pair warp_tot[PIC_FIELD_TPB / 32];
   __shared__ Pair cta_tot;  // read by the other CTAs of the cluster
+  cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x;
   const int rank = (int)cluster.block_rank();
   const int N = P.N;
   const int M = N + 1;
-  const int items = (M + PIC_FIELD_CTAS * PIC_FIELD_TPB - 1) / (PIC_FIELD_CTAS * PIC_FIELD_TPB);
-  const int j0 = (rank * PIC_FIELD_TPB + tid) * items;
+  const int seg = (M + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
+  const int a = rank * seg;
+  const int len = max(0, min(seg, M - a));
   const double dx2 = P.dx * P.dx;
 
-  // ---- pass 1: density, and per-thread sums of k f_k and (N - k) f_k ---------------------------
+  if ((MODE == 0 || MODE == 1) && P.ctl && rank == 0 && tid == 0) bookkeeping(P);
+
+  // ---- pass 1 (coalesced): node density -> shared f_j ---------------------------------------
+  for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+    const int j = a + i;
+    const double r = node_rho<MODE>(P, j);
+    if (MODE != 2) P.rho[j] = r;
+    F[i] = (j >= 1 && j <= N - 1) ? dx2 * r : 0.0;
+  }
+  __syncthreads();
+
+  // ---- per-thread runs of consecutive nodes: sums of k f_k and (N - k) f_k ----------------------
+  const int items = (len + PIC_FIELD_TPB - 1) / PIC_FIELD_TPB;
+  const int i0 = tid * items;
   Pair own = {0.0, 0.0};
   for (int k = 0; k < items; ++k) {
-    const int j = j0 + k;
-    if (j > N) break;
-    double r = node_rho<MODE>(P, j);
-    if (MODE != 2) P.rho[j] = r;
-    if (j >= 1 && j <= N - 1) {
-      double f = dx2 * r;
-      own.a += (double)j * f;
-      own.c += (double)(N - j) * f;
-    }
+    const int i = i0 + k;
+    if (i >= len) break;
+    const double f = F[i];
+    const int j = a + i;
+    own.a += (double)j * f;
+    own.c += (double)(N - j) * f;
   }
-  // ---- block scan, then cluster scan of the CTA totals ------------------------------------------
   Pair incl = warp_incl_scan(own);
   if ((tid & 31) == 31) warp_tot[tid >> 5] = incl;
   __syncthreads();
   if (tid < 32) {
-    Pair w = warp_tot[tid];
-    Pair wi = warp_incl_scan(w);
+    Pair wi = warp_incl_scan(warp_tot[tid]);
     warp_tot[tid] = wi;  // inclusive over warps
     if (tid == 31) cta_tot = wi;
   }
   __syncthreads();
-  Pair excl;  // exclusive prefix of this thread within the CTA
+  Pair excl;
   {
     const int w = tid >> 5, lane = tid & 31;
-    double pa = __shfl_up_sync(0xFFFFFFFFu, incl.a, 1);
-    double pc = __shfl_up_sync(0xFFFFFFFFu, incl.c, 1);
-    Pair before = w ? warp_tot[w - 1] : Pair{0.0, 0.0};
+    const double pa = __shfl_up_sync(0xFFFFFFFFu, incl.a, 1);
+    const double pc = __shfl_up_sync(0xFFFFFFFFu, incl.c, 1);
+    const Pair before = w ? warp_tot[w - 1] : Pair{0.0, 0.0};
     excl.a = before.a + (lane ? pa : 0.0);
     excl.c = before.c + (lane ? pc : 0.0);
   }
-  cluster.sync();
+  cluster.sync();  // CTA totals visible; every input of pass 1 has been read
   Pair off = {0.0, 0.0}, tot = {0.0, 0.0};
+#pragma unroll
   for (int r = 0; r < PIC_FIELD_CTAS; ++r) {
-    const Pair* t = cluster.map_shared_rank(&cta_tot, r);
-    Pair v = *t;
+    const Pair v = *cluster.map_shared_rank(&cta_tot, r);
     if (r < rank) {
       off.a += v.a;
       off.c += v.c;
@@ -125,35 +322,36 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
     tot.a += v.a;
     tot.c += v.c;
   }
-  // inputs are consumed: clear the accumulators for the next step
-  for (int k = 0; k < items; ++k) {
-    const int j = j0 + k;
-    if (j > N) break;
-    if (MODE == 0 && j < N) {
-      P.S[0][j] = 0ull;
-      P.S[1][j] = 0ull;
-      if (!P.keep_counts) {
-        const_cast<unsigned int*>(P.cnt[0])[j] = 0u;
-        const_cast<unsigned int*>(P.cnt[1])[j] = 0u;
+  // clear the accumulators of the deposit for the next step (coalesced)
+  if (MODE == 0) {
+    for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+      const int j = a + i;
+      if (j < N) {
+        P.S[0][j] = 0ull;
+        P.S[1][j] = 0ull;
+        if (!P.keep_counts) {
+          const_cast<unsigned int*>(P.cnt[0])[j] = 0u;
+          const_cast<unsigned int*>(P.cnt[1])[j] = 0u;
+        }
       }
-    } else if (MODE == 1) {
-      P.acc[0][j] = 0.0;
-      P.acc[1][j] = 0.0;
+    }
+  } else if (MODE == 1) {
+    for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+      P.acc[0][a + i] = 0.0;
+      P.acc[1][a + i] = 0.0;
     }
   }
 
-  // ---- pass 2: potential --------------------------------------------------------------------
+  // ---- pass 2: potential, in place --------------------------------------------------------------
   double A = off.a + excl.a, Cc = off.c + excl.c;
   const double invN = 1.0 / (double)N;
   for (int k = 0; k < items; ++k) {
-    const int j = j0 + k;
-    if (j > N) break;
-    if (j >= 1 && j <= N - 1) {
-      double r = MODE == 2 ? P.rho_in[j] : P.rho[j];
-      double f = dx2 * r;
-      A += (double)j * f;
-      Cc += (double)(N - j) * f;
-    }
+    const int i = i0 + k;
+    if (i >= len) break;
+    const int j = a + i;
+    const double f = F[i];
+    A += (double)j * f;
+    Cc += (double)(N - j) * f;
     double phi;
     if (j == 0) {
       phi = P.V_L;
@@ -164,62 +362,67 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
       phi = ((double)(N - j) * A + (double)j * B) * invN + P.V_L * ((double)(N - j) * invN) +
             P.V_R * ((double)j * invN);
     }
+    F[i] = phi;
     P.phi[j] = phi;
   }
-  cluster.sync();  // phi of the whole grid is visible to every CTA of the cluster
+  cluster.sync();  // phi of the whole grid is written (shared here, global for the neighbours)
 
-  // ---- pass 3: node field -----------------------------------------------------------------------
-  const double* phi = P.phi;
-  const double* rho = MODE == 2 ? P.rho_in : P.rho;
-  for (int k = 0; k <= items; ++k) {
-    const int j = j0 + k;
-    if (j > N) break;
-    double E;
-    if (j == 0)
-      E = (phi[0] - phi[1]) / P.dx - rho[0] * P.dx * 0.5;
-    else if (j == N)
-      E = (phi[N - 1] - phi[N]) / P.dx + rho[N] * P.dx * 0.5;
-    else
-      E = (phi[j - 1] - phi[j + 1]) / (2.0 * P.dx);
-    if (k < items) P.E[j] = E;
-    if (P.E2) {
-      // node pair of cell j (left node) and of cell j-1 (right node)
-      if (k < items && j < N) P.E2[j].x = (float)E;
-      if (k > 0 && j >= 1) P.E2[j - 1].y = (float)E;
-    }
-  }
-
-  // ---- bookkeeping of the particle arrays (one thread) ------------------------------------------
-  if (P.ctl && rank == 0 && tid == 0) {
-    Ctl* g = P.ctl;
-    if (P.count_step) g->particle_steps += g->live_mark;
-    g->live_mark = g->n_live[0] + g->n_live[1];
-    for (int s = 0; s < 2; ++s) {
-      unsigned long long n = g->n_cur[s] + g->n_born[s];
-      if (n > P.cap[s]) n = P.cap[s];
-      unsigned long long pad = round_up4(n);
-      for (unsigned long long i = n; i < pad; ++i) {
-        if (P.plain)
-          P.pad64[s].x[i] = -1.0;
-        else
-          P.pad32[s].cell[i] = PIC_DEAD_CELL;
+  // ---- pass 3 (coalesced): node field ------------------------------------------------------------
+  if (P.E) {
+    const double* rho = MODE == 2 ? P.rho_in : P.rho;
+    for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+      const int j = a + i;
+      const double pm = j == 0 ? 0.0 : (i > 0 ? F[i - 1] : P.phi[j - 1]);
+      const double pp = j == N ? 0.0 : (i + 1 < len ? F[i + 1] : P.phi[j + 1]);
+      double E;
+      if (j == 0)
+        E = (F[i] - pp) * P.inv_dx - rho[0] * P.dx * 0.5;
+      else if (j == N)
+        E = (pm - F[i]) * P.inv_dx + rho[N] * P.dx * 0.5;
+      else
+        E = (pm - pp) * (0.5 * P.inv_dx);
+      P.E[j] = E;
+      if (P.E2) {
+        if (j < N) P.E2[j].x = (float)E;
+        if (j > 0) P.E2[j - 1].y = (float)E;
       }
-      g->n_cur[s] = pad;
-      g->n_born[s] = 0ull;
     }
-    g->src_K = 0ull;
   }
+  cluster.sync();  // keep the shared totals alive until every CTA has read them
+}
+
+template <class K>
+void set_smem(K kernel, int bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace
 
 cudaError_t launch_field(const PoissonParams& p, cudaStream_t st) {
   if (p.N < 2 || p.N > PIC_MAX_CELLS_FP32) return cudaErrorInvalidValue;
-  if (p.mode == 0)
-    k_field<0><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, 0, st>>>(p);
-  else if (p.mode == 1)
-    k_field<1><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, 0, st>>>(p);
-  else
-    k_field<2><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, 0, st>>>(p);
+  const int seg = (p.N + 1 + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
+  const size_t smem = sizeof(double) * (size_t)seg;
+  static bool attr_set = false;
+  if (!attr_set) {
+    const int maxs = (int)(sizeof(double) * PIC_FIELD_SEG_MAX);
+    set_smem(k_field_exact, maxs);
+    set_smem(k_field_fp64<0>, maxs);
+    set_smem(k_field_fp64<1>, maxs);
+    set_smem(k_field_fp64<2>, maxs);
+    set_smem(k_field_fp64<3>, maxs);
+    attr_set = true;
+  }
+  switch (p.mode) {
+    case 0:
+      if (p.exact)
+        k_field_exact<<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p);
+      else
+        k_field_fp64<0><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p);
+      break;
+    case 1: k_field_fp64<1><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
+    case 2: k_field_fp64<2><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
+    case 3: k_field_fp64<3><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }

@@ -4,7 +4,8 @@
 // The per-cell particle counts come for free from the deposit of the step that precedes the
 // sort (every live particle, births and source pairs included, was counted in its cell), so the
 // sort is two launches:
-//   k_sort_scan     one CTA per species: exclusive scan of the counts -> per-cell write cursors;
+//   k_sort_scan     one 8-CTA cluster per species: exclusive scan of the counts -> per-cell write
+//                   cursors;
 //                   records the old extent, sets the new one, pads the destination with DEAD
 //                   cells and clears the counts;
 //   k_sort_scatter  persistent tiles over the old arrays (both species): every live particle
@@ -14,7 +15,11 @@
 // The order inside a cell follows the atomic claims and is not reproducible; every per-particle
 // result of the method depends only on the particle itself, the step and the field, so the state
 // as a set of particles is reproducible, and snapshots are written in id order.
+#include <cooperative_groups.h>
+
 #include "pic_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -27,19 +32,35 @@ struct SortParams {
   int N;
 };
 
-__global__ void __launch_bounds__(1024) k_sort_scan(const SortParams P) {
+// One cluster of PIC_FIELD_CTAS CTAs per species: each CTA stages a contiguous segment of the
+// counts in shared memory (coalesced), scans runs of consecutive cells per thread, and takes its
+// offset from the CTA totals of the lower ranks through distributed shared memory.
+__global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(1024, 1)
+    k_sort_scan(const __grid_constant__ SortParams P) {
+  extern __shared__ unsigned int cs[];
   __shared__ unsigned long long warp_tot[32];
-  const int s = blockIdx.x;
+  __shared__ unsigned long long cta_tot;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int s = (int)(blockIdx.x / PIC_FIELD_CTAS);
+  const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int N = P.N;
   unsigned int* cnt = s ? P.cnt[1] : P.cnt[0];
   unsigned int* cur = s ? P.cursor[1] : P.cursor[0];
-  const int items = (N + 1023) / 1024;
-  const int c0 = tid * items;
+  const int seg = (N + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
+  const int a = rank * seg;
+  const int len = max(0, min(seg, N - a));
+  for (int i = tid; i < len; i += 1024) {
+    cs[i] = cnt[a + i];
+    cnt[a + i] = 0u;
+  }
+  __syncthreads();
+  const int items = (len + 1023) / 1024;
+  const int i0 = tid * items;
   unsigned long long own = 0ull;
   for (int k = 0; k < items; ++k) {
-    const int c = c0 + k;
-    if (c < N) own += cnt[c];
+    const int i = i0 + k;
+    if (i < len) own += cs[i];
   }
   unsigned long long incl = own;
 #pragma unroll
@@ -57,19 +78,29 @@ __global__ void __launch_bounds__(1024) k_sort_scan(const SortParams P) {
       if (lane >= o) v += u;
     }
     warp_tot[tid] = v;
+    if (tid == 31) cta_tot = v;
   }
   __syncthreads();
-  unsigned long long run = (w ? warp_tot[w - 1] : 0ull) + incl - own;
-  const unsigned long long total = warp_tot[31];
+  cluster.sync();
+  unsigned long long off = 0ull, total = 0ull;
+#pragma unroll
+  for (int r = 0; r < PIC_FIELD_CTAS; ++r) {
+    const unsigned long long v = *cluster.map_shared_rank(&cta_tot, r);
+    if (r < rank) off += v;
+    total += v;
+  }
+  unsigned long long run = off + (w ? warp_tot[w - 1] : 0ull) + incl - own;
   for (int k = 0; k < items; ++k) {
-    const int c = c0 + k;
-    if (c < N) {
-      cur[c] = (unsigned int)run;
-      run += cnt[c];
-      cnt[c] = 0u;
+    const int i = i0 + k;
+    if (i < len) {
+      const unsigned int c = cs[i];
+      cs[i] = (unsigned int)run;
+      run += c;
     }
   }
-  if (tid == 0) {
+  __syncthreads();
+  for (int i = tid; i < len; i += 1024) cur[a + i] = cs[i];
+  if (rank == 0 && tid == 0) {
     Ctl* g = P.ctl;
     g->sort_total[s] = g->n_cur[s];  // old extent, read by the scatter
     if (total != g->n_live[s]) atomicOr(&g->error, ERR_DEVICE);
@@ -83,6 +114,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan(const SortParams P) {
     for (unsigned long long i = total; i < pad; ++i) dcell[i] = PIC_DEAD_CELL;
     g->n_cur[s] = pad;
   }
+  cluster.sync();  // keep the CTA totals alive until every rank has read them
 }
 
 template <int s>
@@ -113,28 +145,30 @@ __device__ __forceinline__ void scatter_tile(const SortParams& P, unsigned long 
   }
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
+  // claim the slots of all four particles first (four atomics in flight), then copy
+  unsigned peers[PIC_PPT], base[PIC_PPT];
 #pragma unroll
   for (int k = 0; k < PIC_PPT; ++k) {
     const bool live = c[k] != PIC_DEAD_CELL;
-    const int key = live ? c[k] : -1;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
-    const int leader = __ffs(peers) - 1;
-    unsigned base = 0u;
-    if (live && lane == leader) base = atomicAdd(cur + c[k], (unsigned)__popc(peers));
-    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (live) {
-      const unsigned long long slot = base + (unsigned)__popc(peers & below);
-      if (slot >= P.cap[s]) {  // only reachable if the counts disagree with the arrays
-        atomicOr(&P.ctl->error, ERR_DEVICE);
-        continue;
-      }
-      D.cell[slot] = c[k];
-      D.frac[slot] = f[k];
-      D.vx[slot] = vx[k];
-      D.vy[slot] = vy[k];
-      D.vz[slot] = vz[k];
-      D.id[slot] = id[k];
+    peers[k] = __match_any_sync(0xFFFFFFFFu, live ? c[k] : -1);
+    base[k] = 0u;
+    if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(cur + c[k], (unsigned)__popc(peers[k]));
+  }
+#pragma unroll
+  for (int k = 0; k < PIC_PPT; ++k) {
+    const unsigned b = __shfl_sync(0xFFFFFFFFu, base[k], __ffs(peers[k]) - 1);
+    if (c[k] == PIC_DEAD_CELL) continue;
+    const unsigned long long slot = b + (unsigned)__popc(peers[k] & below);
+    if (slot >= P.cap[s]) {  // only reachable if the counts disagree with the arrays
+      atomicOr(&P.ctl->error, ERR_DEVICE);
+      continue;
     }
+    D.cell[slot] = c[k];
+    D.frac[slot] = f[k];
+    D.vx[slot] = vx[k];
+    D.vy[slot] = vy[k];
+    D.vz[slot] = vz[k];
+    D.id[slot] = id[k];
   }
 }
 
@@ -168,7 +202,14 @@ cudaError_t launch_sort32(Species32 src[2], Species32 dst[2], unsigned int* cnt[
   }
   P.ctl = ctl;
   P.N = N;
-  k_sort_scan<<<2, 1024, 0, st>>>(P);
+  const int seg = (N + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_sort_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(unsigned int) * PIC_FIELD_SEG_MAX));
+    attr_set = true;
+  }
+  k_sort_scan<<<2 * PIC_FIELD_CTAS, 1024, sizeof(unsigned int) * (size_t)seg, st>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sort_scatter<<<grid, PIC_TPB, 0, st>>>(P);

@@ -14,15 +14,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#define PIC_TPB 256
-#define PIC_PPT 4
+#ifndef PIC_TPB
+#define PIC_TPB 256  // threads per CTA of the particle kernels
+#endif
+#define PIC_PPT 4  // particles per thread (one 128-bit access per array)
+#ifndef PIC_STEP_MINB
+#define PIC_STEP_MINB 3  // resident CTAs per SM the step kernel is compiled for
+#endif
 #define PIC_TILE (PIC_TPB * PIC_PPT)
 #define PIC_WCAP 2048
 #define PIC_DEAD_CELL ((int)0x80000000)
 #define PIC_FIELD_CTAS 8
 #define PIC_FIELD_TPB 1024
-#define PIC_FIELD_MAX_ITEMS 32
-#define PIC_MAX_CELLS_FP32 (PIC_FIELD_CTAS * PIC_FIELD_TPB * PIC_FIELD_MAX_ITEMS - 1)
+#define PIC_FIELD_SEG_MAX 24576  // nodes per CTA of the field cluster (192 KB of shared memory)
+#define PIC_MAX_CELLS_FP32 (PIC_FIELD_CTAS * PIC_FIELD_SEG_MAX - 1)
 
 // Philox counter word 2: the stream of a draw
 #define CH_INIT 1u
@@ -80,6 +85,7 @@ struct SpConst {
   float qmdt2;      // (q/m) dt / 2
   float t[3], s[3]; // Boris rotation vectors
   float p_null;     // 1 - exp(-nu_max dt), FP32
+  unsigned p_null_u24;  // ceil(p_null 2^24): (w >> 8) < p_null_u24  <=>  u01(w) < p_null
   float nu_max;     // FP32
   float mass;
   float vt;         // sqrt(T/m) (source, load)
@@ -142,11 +148,14 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
   return c;
 }
 
+// The draw for (particle id, step, channel, index): key (step lo, seed lo) -- the same for every
+// particle of a step, so the key schedule is warp-uniform -- and counter (id lo, id hi,
+// channel | step hi << 8, index ^ seed hi).
 __device__ __forceinline__ uint4 draw4(unsigned long long id, unsigned long long seed,
                                        unsigned long long step, unsigned ch, unsigned idx) {
-  unsigned long long k = id ^ seed;
-  return philox10(make_uint4((unsigned)step, (unsigned)(step >> 32), ch, idx),
-                  make_uint2((unsigned)k, (unsigned)(k >> 32)));
+  return philox10(make_uint4((unsigned)id, (unsigned)(id >> 32), ch | ((unsigned)(step >> 32) << 8),
+                             idx ^ (unsigned)(seed >> 32)),
+                  make_uint2((unsigned)step, (unsigned)seed));
 }
 
 // 24-bit uniform in [0, 1): exact in FP32 and FP64
@@ -154,6 +163,50 @@ __device__ __forceinline__ float u01f(unsigned w) { return (float)(w >> 8) * 5.9
 __device__ __forceinline__ double u01d(unsigned w) { return (double)(w >> 8) * 5.9604644775390625e-08; }
 
 __host__ __device__ inline unsigned long long round_up4(unsigned long long n) { return (n + 3ull) & ~3ull; }
+
+// --------------------------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, 1D) and mbarriers, inline PTX for sm_90+.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Wait for a phase with an iteration cap; false when the cap ran out (the caller reports it).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Order this thread's earlier generic-proxy accesses of shared memory before later async-proxy
+// (TMA) accesses, so that a stage buffer is refilled only after it has been read.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Global -> shared bulk copy; completes tx bytes on the mbarrier.  Both addresses 16-byte aligned,
+// size a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 
 // launchers (each file owns its kernels)
 struct PoissonParams {
@@ -163,7 +216,11 @@ struct PoissonParams {
   double* acc[2];
   const double* rho_in;
   double qw[2];     // q_s * w_s
-  int mode;         // 0: fixed point, 1: FP64 accumulators, 2: plain rho
+  long long m[2];   // exact path: integer charge multipliers q_s ppc_{1-s} / gcd(ppc_0, ppc_1)
+  double e_in, e_wall, e_bias;  // exact path: E coefficients (see k_field.cu)
+  double inv_dx;
+  int exact;        // mode 0: integer-exact field (integer charges)
+  int mode;         // 0: fixed point, 1: FP64 accumulators, 2: plain rho, 3: from stored R
   int keep_counts;  // fixed point: leave cnt for the sort
   int N;
   double dx, V_L, V_R;

@@ -68,4 +68,8 @@ SMALL_C3 = variant(C3, ncells=512, L=512.0, ppc=(41, 41), profile_scale=64.0, so
 #: strongly collisional: every process fires often, to exercise the collision paths.
 SMALL_COLL = variant(SMALL_C2, n_gas=25.0, ncells=48, L=48.0, ppc=(61, 61))
 
-CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c5": C5}
+#: profiling case: config 3's physics and profile with 1/8 of the particles (12.5 M, 350 MB of
+#: particle data: larger than L2, small enough for multi-pass counter captures)
+C3_PROFILE = variant(C3, ppc=(96, 96))
+
+CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c5": C5, "c3p": C3_PROFILE}

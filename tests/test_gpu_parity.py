@@ -67,7 +67,7 @@ def test_philox_bit_exact_against_oracle():
     assert out[0].tolist() == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
 
 
-@pytest.mark.parametrize("N", [2, 3, 7, 100, 1023, 8191, 8192, 65536, 262143])
+@pytest.mark.parametrize("N", [2, 3, 7, 100, 1023, 8191, 8192, 65536, 196607])
 def test_poisson_matches_thomas(N):
     import torch
 
@@ -125,8 +125,31 @@ def test_restore_deposit_is_bit_exact():
         assert np.abs(fo["rho"] - fg["rho"]).max() <= 1e-15 * np.abs(fo["rho"]).max()
         scale = np.abs(fo["phi"]).max()
         assert np.abs(fo["phi"] - fg["phi"]).max() <= _cond_tol(p["ncells"]) * scale
+        # the field the particles see (FP32), against the oracle's Thomas solve and centred
+        # differences: FP32 rounding plus the conditioning bound of the solve
+        escale = np.abs(fo["E"]).max()
+        assert np.abs(fo["E"] - fg["E"]).max() <= 2.0**-23 * escale + _cond_tol(p["ncells"]) * scale
         # the snapshot round-trips byte for byte (format written independently on both sides)
         assert g.snapshot() == blob
+
+
+def test_non_integer_charges_use_the_fp64_solve():
+    # charges that are not small integers take the FP64 Green's function; same bar
+    p = W.variant(W.SMALL_C2, charge=(-1.0, 1.5), ppc=(53, 35))
+    blob = _oracle_blob_fp32(p)
+    o = O.OracleSim(p)
+    assert o.restore(blob) == 0
+    g = pic.Simulation(p)
+    assert g.restore(blob) == 0
+    fo, fg = o.fields(), g.fields()
+    assert np.array_equal(fo["R"], fg["R"])
+    scale = np.abs(fo["phi"]).max()
+    assert np.abs(fo["phi"] - fg["phi"]).max() <= _cond_tol(p["ncells"]) * scale
+    escale = np.abs(fo["E"]).max()
+    assert np.abs(fo["E"] - fg["E"]).max() <= 2.0**-23 * escale + _cond_tol(p["ncells"]) * scale
+    o.step(2)
+    g.step(2)
+    assert o.diag()["n"] == g.diag()["n"]
 
 
 @pytest.mark.parametrize("name", ["SMALL_C1", "SMALL_C2", "SMALL_C3", "SMALL_COLL"])
