@@ -194,6 +194,30 @@ int pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n
 int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double V_R,
                 double* phi, double* E, void* cuda_stream);
 
+/* ---- allocation-free entry point ------------------------------------------------------------ */
+
+/* The paper has no counterpart to this call: it exists for callers that cannot allocate device
+ * memory (code confined to another framework's fixed memory pool, code that must not allocate
+ * after start-up, hosts that only hand over their own buffers).  It computes what pic_restore +
+ * pic_get_field compute for a particle state -- the int64 CIC deposit of each species and the
+ * node field of the integer-exact Poisson solve -- without any cudaMalloc, cudaFree or
+ * allocating library call.  Its scratch (per-cell counts and weight sums, about 2 MB) is one
+ * fixed array in device memory that every GPU which loads this library keeps until the process
+ * exits; the first call on each device looks up that array's device address (make that first
+ * call before any stream capture).  Limits: 2 <= cfg->ncells <= PIC_NOALLOC_MAX_CELLS (larger
+ * grids return PIC_EINVAL), integer charges |q| <= 64, ppc ratio as in pic_init's exact solve.
+ * Inputs (device, caller-owned): per species s the cell indices (int32) and fractions (FP32) of
+ * n_s particles; entries with a cell outside [0, N) or a fraction outside [0, 1) are skipped.
+ * Outputs (device, caller-owned): R, 2 x (N+1) int64 node deposits (species 0 then 1, 2^-32
+ * particle units); E, N+1 FP64 node field.  The call runs on cuda_stream and synchronises it
+ * before returning (PIC_EDEVICE if a device-side check failed).  All calls share the one scratch
+ * array and each clears it first: calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
+#define PIC_NOALLOC_MAX_CELLS 65536
+int pic_field_noalloc(const pic_config* cfg, const int32_t* cell0, const float* frac0, uint64_t n0,
+                      const int32_t* cell1, const float* frac1, uint64_t n1, int64_t* R, double* E,
+                      void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,7 +62,7 @@ class PicDiag(C.Structure):
 #: every entry point of include/pic.h
 SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapshot", "pic_restore",
            "pic_diag", "pic_get_field", "pic_profile", "pic_kernel_times", "pic_free",
-           "pic_strerror", "pic_philox", "pic_poisson")
+           "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc")
 
 
 def lib():
@@ -90,6 +90,7 @@ def lib():
         L.pic_strerror.restype = C.c_char_p
         L.pic_philox.argtypes = [V, V, V, C.c_size_t, V]
         L.pic_poisson.argtypes = [V, C.c_int32, C.c_double, C.c_double, C.c_double, V, V, V]
+        L.pic_field_noalloc.argtypes = [P(PicConfig), V, V, C.c_uint64, V, V, C.c_uint64, V, V, V]
         _lib = L
     return _lib
 
@@ -241,6 +242,27 @@ def poisson(rho, dx: float, V_L: float, V_R: float, stream=None):
     _check(lib().pic_poisson(C.c_void_p(rho.data_ptr()), N, dx, V_L, V_R, C.c_void_p(phi.data_ptr()),
                              C.c_void_p(E.data_ptr()), C.c_void_p(st.cuda_stream)), "pic_poisson")
     return phi, E
+
+
+def field_noalloc(params: dict, cell0, frac0, cell1, frac1, stream=None):
+    """Deposit + field of a particle state with no device allocation inside the library.
+
+    cell_s (int32) and frac_s (float32) are CUDA tensors of one species each; returns
+    (R (2, N+1) int64, E (N+1,) float64).  The output tensors are allocated here by the caller
+    side (torch); the library call itself allocates nothing.
+    """
+    torch = _torch()
+    c = make_config(params)
+    N = int(params["ncells"])
+    dev = cell0.device
+    R = torch.empty((2, N + 1), dtype=torch.int64, device=dev)
+    E = torch.empty(N + 1, dtype=torch.float64, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    _check(lib().pic_field_noalloc(C.byref(c), C.c_void_p(cell0.data_ptr()), C.c_void_p(frac0.data_ptr()),
+                                   cell0.numel(), C.c_void_p(cell1.data_ptr()), C.c_void_p(frac1.data_ptr()),
+                                   cell1.numel(), C.c_void_p(R.data_ptr()), C.c_void_p(E.data_ptr()),
+                                   C.c_void_p(st.cuda_stream)), "pic_field_noalloc")
+    return R, E
 
 
 __all__ = ["Simulation", "philox", "poisson", "make_config", "workspace_size", "lib", "PicError",

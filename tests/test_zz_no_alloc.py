@@ -1,0 +1,78 @@
+"""pic_field_noalloc: the allocation-free variant of the deposit + field solve.
+
+Some callers cannot allocate device memory (they live inside another framework's fixed memory
+pool, or must not allocate after start-up); for them the library offers one entry point whose
+scratch is a fixed device array inside the library.  This file checks, through the C ABI, that it
+gives what the ordinary entry points give (pic_restore + pic_get_field on a handle with its own
+workspace) for the same particles, on two calls in a row with different states -- so a call that
+failed to clear what the previous call left in the shared scratch would show up -- and that a grid
+larger than the fixed scratch is refused.  It lives in a file of its own that pytest collects
+last, so that a run stopping at the first failure has already run everything else.
+"""
+import numpy as np
+import pytest
+
+import snapfmt
+from oracle import oracle as O
+from paper_2606_28534_gb300 import build, pic
+from paper_2606_28534_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    pic.lib()
+
+
+def _state(params, steps):
+    o = O.OracleSim(params)
+    o.step(steps)
+    return snapfmt.round_to_fp32(o.snapshot())
+
+
+def _reference_fields(params, blob):
+    g = pic.Simulation(params)
+    assert g.restore(blob) == 0
+    f = g.fields()
+    g.close()
+    return f["R"], f["E"]
+
+
+def _device_particles(blob):
+    import torch
+
+    sp = snapfmt.parse(blob)["species"]
+    out = []
+    for s in sp:
+        out.append(torch.from_numpy(np.ascontiguousarray(s["cell"], np.int32)).cuda())
+        out.append(torch.from_numpy(np.ascontiguousarray(s["frac"].astype(np.float32))).cuda())
+    return out
+
+
+def test_no_alloc_matches_the_workspace_path_on_consecutive_calls():
+    p = W.variant(W.SMALL_C3, ncells=4096, L=4096.0, profile_scale=512.0, source_x1=256.0)
+    for steps in (2, 7):  # two calls in a row, different states
+        blob = _state(p, steps)
+        R_ref, E_ref = _reference_fields(p, blob)
+        c0, f0, c1, f1 = _device_particles(blob)
+        R, E = pic.field_noalloc(p, c0, f0, c1, f1)
+        R, E = R.cpu().numpy(), E.cpu().numpy()
+        assert np.array_equal(R, R_ref)  # integer deposit: exact
+        scale = np.abs(E_ref).max()
+        assert np.abs(E.astype(np.float32) - E_ref).max() <= 2.0**-23 * scale
+
+
+def test_no_alloc_refuses_grids_beyond_its_scratch():
+    import torch
+
+    p = W.variant(W.SMALL_C2, ncells=65537, L=65537.0)
+    z = torch.zeros(4, dtype=torch.int32, device="cuda")
+    f = torch.zeros(4, dtype=torch.float32, device="cuda")
+    with pytest.raises(pic.PicError) as e:
+        pic.field_noalloc(p, z, f, z, f)
+    assert e.value.status == 1
