@@ -49,13 +49,9 @@ __device__ __forceinline__ void box_muller_f(unsigned wa, unsigned wb, float& n0
   n1 = r * s;
 }
 
-struct PushConst {
-  float qmdt2, t0, t1, t2, s0, s1, s2, mass;
-};
-
 // Interpolation (e = node pair of the cell) + Boris + move.  Returns the new cell (may be outside
 // [0, N): absorbed).
-__device__ __forceinline__ int push_one(const Phys& ph, const PushConst& k, float2 e, int c, float& f, float& vx,
+__device__ __forceinline__ int push_one(const Phys& ph, const SpConst& k, float2 e, int c, float& f, float& vx,
                                         float& vy, float& vz) {
   float E = 0.f;
   if (ph.field_mode == 0u) {
@@ -66,12 +62,12 @@ __device__ __forceinline__ int push_one(const Phys& ph, const PushConst& k, floa
   float a = k.qmdt2 * E;
   float mx = vx + a, my = vy, mz = vz;
   if (ph.has_B) {
-    float px = mx + (my * k.t2 - mz * k.t1);
-    float py = my + (mz * k.t0 - mx * k.t2);
-    float pz = mz + (mx * k.t1 - my * k.t0);
-    mx += py * k.s2 - pz * k.s1;
-    my += pz * k.s0 - px * k.s2;
-    mz += px * k.s1 - py * k.s0;
+    float px = mx + (my * k.t[2] - mz * k.t[1]);
+    float py = my + (mz * k.t[0] - mx * k.t[2]);
+    float pz = mz + (mx * k.t[1] - my * k.t[0]);
+    mx += py * k.s[2] - pz * k.s[1];
+    my += pz * k.s[0] - px * k.s[2];
+    mz += px * k.s[1] - py * k.s[0];
   }
   vx = mx + a;
   vy = my;
@@ -273,10 +269,10 @@ __device__ __noinline__ void flush_queue(const StepParams32& P, const unsigned l
 }
 
 // Lane 0 starts the bulk copies of chunk t (ncur particles in the species) into a stage buffer.
-__device__ __forceinline__ void stage_issue(const Species32& A, unsigned long long t, unsigned long long ncur,
-                                            unsigned char* buf, unsigned long long* bar) {
-  const unsigned long long i0 = t * CHUNK;
-  const unsigned n = (unsigned)min((unsigned long long)CHUNK, ncur - i0);  // multiple of 4
+__device__ __forceinline__ void stage_issue(const Species32& A, unsigned t, unsigned ncur, unsigned char* buf,
+                                            unsigned long long* bar) {
+  const unsigned i0 = t * CHUNK;
+  const unsigned n = min((unsigned)CHUNK, ncur - i0);  // multiple of 4
   mbar_expect_tx(bar, n * 28u);
   tma_load_1d(buf, A.cell + i0, n * 4u, bar);
   tma_load_1d(buf + CHUNK * 4, A.frac + i0, n * 4u, bar);
@@ -311,54 +307,40 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
   unsigned parity = 0u;  // bit st: phase parity of stage st
   bool failed = false;   // a bounded wait gave up
   const unsigned long long ncur0 = P.ctl->n_cur[0], ncur1 = P.ctl->n_cur[1];
-  const unsigned long long gw = (unsigned long long)blockIdx.x * WARPS + wib;
-  const unsigned long long nw = (unsigned long long)gridDim.x * WARPS;
+  const unsigned gw = blockIdx.x * WARPS + wib;  // particle indices and chunk counts fit 32 bits
+  const unsigned nw = gridDim.x * WARPS;
   const Phys& ph = P.ph;
   const int N = ph.N;
 
 #pragma unroll 1
   for (int s = 0; s < 2 && !failed; ++s) {
-    const unsigned long long ncur = s ? ncur1 : ncur0;
-    const unsigned long long chunks = (ncur + CHUNK - 1) / CHUNK;
-    const Species32 A = s ? P.sp[1] : P.sp[0];
-    unsigned int* const gcnt = s ? P.cnt[1] : P.cnt[0];
-    unsigned long long* const gS = s ? P.S[1] : P.S[0];
-    PushConst K;
-    {
-      const SpConst& K0 = ph.sp[0];
-      const SpConst& K1 = ph.sp[1];
-      K.qmdt2 = s ? K1.qmdt2 : K0.qmdt2;
-      K.t0 = s ? K1.t[0] : K0.t[0];
-      K.t1 = s ? K1.t[1] : K0.t[1];
-      K.t2 = s ? K1.t[2] : K0.t[2];
-      K.s0 = s ? K1.s[0] : K0.s[0];
-      K.s1 = s ? K1.s[1] : K0.s[1];
-      K.s2 = s ? K1.s[2] : K0.s[2];
-      K.mass = s ? K1.mass : K0.mass;
-    }
+    // species arrays and constants are read from the kernel parameters where they are used
+    const unsigned ncur = (unsigned)(s ? ncur1 : ncur0);
+    const unsigned chunks = (ncur + CHUNK - 1) / CHUNK;
+    const Species32& A = P.sp[s];
+    const SpConst& K = ph.sp[s];
     const bool moves = (ph.push_mask >> s) & 1u;
     const bool collides = moves && (s == 0 ? (ph.coll_mask & 7u) != 0u : (ph.coll_mask & 8u) != 0u);
-    const unsigned thr = s ? ph.sp[1].p_null_u24 : ph.sp[0].p_null_u24;
     const unsigned long long tag = (unsigned long long)s << 63;
 
     // prologue: the warp's first NSTAGE chunks
     if (lane == 0) {
 #pragma unroll
       for (int st = 0; st < NSTAGE; ++st) {
-        const unsigned long long t = gw + (unsigned long long)st * nw;
+        const unsigned t = gw + st * nw;
         if (t < chunks) stage_issue(A, t, ncur, stage + st * STAGE_BYTES, bar + st);
       }
     }
     int st = 0;
 #pragma unroll 1
-    for (unsigned long long t = gw; t < chunks; t += nw) {
+    for (unsigned t = gw; t < chunks; t += nw) {
       if (!__all_sync(0xFFFFFFFFu, mbar_wait_bounded(bar + st, (parity >> st) & 1u))) {
         failed = true;
         break;
       }
       parity ^= 1u << st;
       const unsigned char* const buf = stage + st * STAGE_BYTES;
-      const unsigned long long i0 = t * CHUNK + (unsigned long long)lane * PIC_PPT;
+      const unsigned i0 = t * CHUNK + lane * PIC_PPT;
       int c[PIC_PPT];
       float f[PIC_PPT], vx[PIC_PPT], vy[PIC_PPT], vz[PIC_PPT];
       unsigned long long id[PIC_PPT];
@@ -397,7 +379,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        const unsigned long long tn = t + (unsigned long long)NSTAGE * nw;
+        const unsigned tn = t + NSTAGE * nw;
         if (tn < chunks) stage_issue(A, tn, ncur, stage + st * STAGE_BYTES, bar + st);
       }
       st = st + 1 == NSTAGE ? 0 : st + 1;
@@ -409,7 +391,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
           const uint4 w = draw4(id[k], ph.seed, P.step, CH_COLL, 0u);
-          if ((w.x >> 8) < thr) cand |= 1u << k;
+          if ((w.x >> 8) < K.p_null_u24) cand |= 1u << k;
         }
       }
 #pragma unroll
@@ -441,7 +423,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
       for (int k = 0; k < PIC_PPT; ++k) {
         const bool qk = ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL;
         const unsigned b = __ballot_sync(0xFFFFFFFFu, qk);
-        if (qk) q[qn + __popc(b & below)] = tag | (i0 + k);
+        if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(i0 + k);
         qn += __popc(b);
       }
 
@@ -466,7 +448,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
         }
       }
 #pragma unroll
-      for (int k = 0; k < PIC_PPT; ++k) warp_deposit(gcnt, gS, rn[k] ? c[k] : -1, rn[k], rsw[k]);
+      for (int k = 0; k < PIC_PPT; ++k) warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] : -1, rn[k], rsw[k]);
 
       if (qn > QFLUSH) {
         flush_queue(P, q, qn, ncur0, ncur1, &bc);
