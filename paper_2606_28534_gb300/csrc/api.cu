@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "../../include/pic.h"
@@ -384,20 +385,94 @@ int check_errors(pic_handle* h) {
 
 // ---------------------------------------------------------------------------------------------
 // Snapshot format helpers (CRC-32 IEEE 802.3 reflected; FNV-1a 64 of the canonical config).
-uint32_t crc32_ieee(const unsigned char* p, size_t n) {
-  static uint32_t table[256];
-  static bool init = false;
-  if (!init) {
+// CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320, as zlib), slice-by-8 tables.
+struct CrcTables {
+  uint32_t t[8][256];
+  CrcTables() {
     for (uint32_t i = 0; i < 256; ++i) {
       uint32_t c = i;
       for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : (c >> 1);
-      table[i] = c;
+      t[0][i] = c;
     }
-    init = true;
+    for (uint32_t i = 0; i < 256; ++i)
+      for (int k = 1; k < 8; ++k) t[k][i] = t[0][t[k - 1][i] & 0xFFu] ^ (t[k - 1][i] >> 8);
   }
+};
+const CrcTables& crc_tables() {
+  static const CrcTables T;
+  return T;
+}
+
+uint32_t crc32_serial(const unsigned char* p, size_t n) {
+  const CrcTables& T = crc_tables();
   uint32_t c = 0xFFFFFFFFu;
-  for (size_t i = 0; i < n; ++i) c = table[(c ^ p[i]) & 0xFFu] ^ (c >> 8);
+  while (n >= 8) {
+    uint32_t lo, hi;
+    std::memcpy(&lo, p, 4);
+    std::memcpy(&hi, p + 4, 4);
+    lo ^= c;
+    c = T.t[7][lo & 0xFF] ^ T.t[6][(lo >> 8) & 0xFF] ^ T.t[5][(lo >> 16) & 0xFF] ^ T.t[4][lo >> 24] ^
+        T.t[3][hi & 0xFF] ^ T.t[2][(hi >> 8) & 0xFF] ^ T.t[1][(hi >> 16) & 0xFF] ^ T.t[0][hi >> 24];
+    p += 8;
+    n -= 8;
+  }
+  while (n--) c = T.t[0][(c ^ *p++) & 0xFFu] ^ (c >> 8);
   return c ^ 0xFFFFFFFFu;
+}
+
+// GF(2) operator on the CRC register, column i = image of bit i.
+struct Gf2 {
+  uint32_t m[32];
+};
+uint32_t gf2_apply(const Gf2& a, uint32_t v) {
+  uint32_t r = 0;
+  for (int i = 0; v; ++i, v >>= 1)
+    if (v & 1u) r ^= a.m[i];
+  return r;
+}
+Gf2 gf2_square(const Gf2& a) {
+  Gf2 r;
+  for (int i = 0; i < 32; ++i) r.m[i] = gf2_apply(a, a.m[i]);
+  return r;
+}
+// crc(A || B) = crc(B) xor Z^{|B|}(crc(A)), Z = the register update of one zero byte (the init and
+// final complements cancel), so chunks can be checksummed independently and joined.
+uint32_t crc32_join(uint32_t crc_a, uint32_t crc_b, size_t len_b) {
+  Gf2 op;
+  op.m[0] = 0xEDB88320u;  // one zero bit: r -> (r >> 1) ^ (r & 1 ? P : 0)
+  for (int i = 1; i < 32; ++i) op.m[i] = 1u << (i - 1);
+  op = gf2_square(gf2_square(gf2_square(op)));  // one zero byte
+  while (len_b) {
+    if (len_b & 1u) crc_a = gf2_apply(op, crc_a);
+    op = gf2_square(op);
+    len_b >>= 1;
+  }
+  return crc_a ^ crc_b;
+}
+
+// Host threads for the large linear passes over a blob (checksum, range checks).
+int host_threads(size_t bytes) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const size_t by_size = bytes / (32u << 20) + 1;  // at least 32 MB per thread
+  return (int)std::max<size_t>(1, std::min<size_t>({by_size, (size_t)(hw ? hw : 1), (size_t)64}));
+}
+
+uint32_t crc32_ieee(const unsigned char* p, size_t n) {
+  const int T = host_threads(n);
+  if (T == 1) return crc32_serial(p, n);
+  std::vector<uint32_t> part(T);
+  std::vector<size_t> len(T);
+  std::vector<std::thread> th;
+  const size_t chunk = (n + T - 1) / T;
+  for (int k = 0; k < T; ++k) {
+    const size_t a = std::min(n, (size_t)k * chunk), b = std::min(n, a + chunk);
+    len[k] = b - a;
+    th.emplace_back([&, k, a]() { part[k] = crc32_serial(p + a, len[k]); });
+  }
+  for (auto& t : th) t.join();
+  uint32_t c = part[0];
+  for (int k = 1; k < T; ++k) c = crc32_join(c, part[k], len[k]);
+  return c;
 }
 
 struct Fnv {
@@ -688,21 +763,19 @@ int pic_diag(pic_handle* h, pic_diag_t* d) {
   int rc = check_errors(h);
   if (rc != PIC_OK) return rc;
   CK(cudaMemsetAsync(h->ctl->ke_fx, 0, sizeof(h->ctl->ke_fx), h->st));
-  rc = field_diagnostics(h);
-  if (rc != PIC_OK) return rc;
+  CK(cudaMemsetAsync(&h->ctl->netq, 0, sizeof(h->ctl->netq), h->st));
   EvPair e;
   prof_begin(h, K_DIAG, &e);
-  CK(h->plain ? launch_diag64(params64(h), h->grid_diag, h->st) : launch_diag32(params32(h), h->grid_diag, h->st));
+  // FP32 path: the step itself summed the kinetic energy (ke_last); the plain path reduces here
+  if (h->plain) CK(launch_diag64(params64(h), h->grid_diag, h->st));
+  CK(launch_diag_grid(h->R[0], h->R[1], h->cfg.charge[0] > 0 ? 1 : -1, h->cfg.charge[1] > 0 ? 1 : -1, h->E, h->N,
+                      h->cfg.L / h->N, h->ctl, h->st));
   prof_end(h, &e);
-  CK(cudaStreamSynchronize(h->st));
+  // one device-to-host read of the control block
   Ctl c;
-  CK(cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
   const int N = h->N;
-  std::vector<long long> R(2 * (size_t)(N + 1));
-  std::vector<double> E(N + 1);
-  CK(cudaMemcpy(R.data(), h->R[0], sizeof(long long) * (N + 1), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(R.data() + N + 1, h->R[1], sizeof(long long) * (N + 1), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(E.data(), h->E, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost));
   std::memset(d, 0, sizeof(*d));
   const double dx = h->cfg.L / N;
   d->step = h->step;
@@ -714,21 +787,16 @@ int pic_diag(pic_handle* h, pic_diag_t* d) {
     d->near_threshold[s] = c.near_thr[s];
     d->nu_max_violations[s] = c.viol[s];
     d->births[s] = c.births[s];
-    d->ke[s] = (double)c.ke_fx[s] * (1.0 / 16777216.0) * w;
+    d->ke[s] = (double)(h->plain ? c.ke_fx[s] : c.ke_last[s]) * (1.0 / 16777216.0) * w;
     d->wall_energy[s] = (double)c.wall_energy_fx[s] * (1.0 / 16777216.0) * w;
   }
   for (int k = 0; k < 5; ++k) d->coll[k] = c.coll[k];
   d->source_pairs = c.source_pairs;
   d->dropped = c.dropped;
   d->wall_charge = c.wall_charge;
-  long long q = 0;
-  for (int s = 0; s < 2; ++s) {
-    const long long sg = h->cfg.charge[s] > 0 ? 1 : -1;
-    for (int j = 0; j <= N; ++j) q += sg * R[(size_t)s * (N + 1) + j];
-  }
-  d->net_charge_units = q;
+  d->net_charge_units = c.netq;
   double fe = 0.0;
-  for (int j = 0; j <= N; ++j) fe += ((j == 0 || j == N) ? 0.5 : 1.0) * 0.5 * E[j] * E[j] * dx;
+  for (int b = 0; b < PIC_DIAG_BLOCKS; ++b) fe += c.fe_part[b];
   d->field_energy = fe;
   d->particle_steps = c.particle_steps;
   return PIC_OK;
@@ -826,68 +894,89 @@ int pic_restore(pic_handle* h, const void* buf, size_t len) {
   std::memcpy(wall_energy, b + 48 + 144, 16);
   const int N = h->N;
   const double dx = h->cfg.L / N;
+  // range check of every cell and fraction before any device state changes (host threads)
+  {
+    size_t off = kHdr;
+    bool bad = false;
+    for (int s = 0; s < 2; ++s) {
+      const size_t m = (size_t)n[s];
+      const unsigned char* cell = b + off;
+      const unsigned char* frac = cell + 4 * m;
+      const int T = host_threads(12 * m);
+      std::vector<char> flag(T, 0);
+      std::vector<std::thread> th;
+      const size_t chunk = (m + T - 1) / T;
+      for (int k = 0; k < T; ++k) {
+        th.emplace_back([&, k]() {
+          const size_t i0 = std::min(m, (size_t)k * chunk), i1 = std::min(m, i0 + chunk);
+          for (size_t i = i0; i < i1; ++i) {
+            int32_t c;
+            double f;
+            std::memcpy(&c, cell + 4 * i, 4);
+            std::memcpy(&f, frac + 8 * i, 8);
+            if (c < 0 || c >= N || !(f >= 0.0 && f < 1.0)) {
+              flag[k] = 1;
+              break;
+            }
+          }
+        });
+      }
+      for (auto& t : th) t.join();
+      for (char f : flag) bad = bad || f;
+      off += 44 * m;
+    }
+    if (bad) return PIC_ECORRUPT;
+  }
   size_t off = kHdr;
   h->cur = 0;
   for (int s = 0; s < 2; ++s) {
     const size_t m = (size_t)n[s];
-    std::vector<int32_t> cell(m);
-    std::vector<double> frac(m), vx(m), vy(m), vz(m);
-    std::vector<uint64_t> id(m);
-    std::memcpy(cell.data(), b + off, 4 * m);
-    off += 4 * m;
-    std::memcpy(frac.data(), b + off, 8 * m);
-    off += 8 * m;
-    std::memcpy(vx.data(), b + off, 8 * m);
-    off += 8 * m;
-    std::memcpy(vy.data(), b + off, 8 * m);
-    off += 8 * m;
-    std::memcpy(vz.data(), b + off, 8 * m);
-    off += 8 * m;
-    std::memcpy(id.data(), b + off, 8 * m);
-    off += 8 * m;
-    for (size_t i = 0; i < m; ++i)
-      if (cell[i] < 0 || cell[i] >= N || !(frac[i] >= 0.0 && frac[i] < 1.0)) return PIC_ECORRUPT;
     const size_t mp = (size_t)round_up4(m);
     if (!h->plain) {
-      std::vector<int32_t> c32(mp, PIC_DEAD_CELL);
-      std::vector<float> f32(mp, 0.f), x32(mp, 0.f), y32(mp, 0.f), z32(mp, 0.f);
-      std::vector<uint64_t> id2(mp, 0ull);
-      for (size_t i = 0; i < m; ++i) {
-        int c = cell[i];
-        float f = (float)frac[i];
-        if (f >= 1.f) {
-          f = 0.f;
-          c += 1;
-          if (c >= N) {
-            c = N - 1;
-            f = 0.99999994f;
-          }
+      // the blob's arrays go straight to device staging (the sort's second buffer, unused
+      // between sorts) and a kernel converts them into buffer 0
+      char* stage = reinterpret_cast<char*>(h->a32[1][0].cell);
+      const size_t stage_bytes = (size_t)(reinterpret_cast<char*>(h->a32[1][1].id + h->cap[1]) - stage);
+      const size_t per = std::max<size_t>(4, (stage_bytes - 6 * 256) / 44 / 4 * 4);
+      const unsigned char* src[6] = {b + off, b + off + 4 * m, b + off + 12 * m, b + off + 20 * m,
+                                     b + off + 28 * m, b + off + 36 * m};
+      const size_t width[6] = {4, 8, 8, 8, 8, 8};
+      for (size_t done = 0; done < m; done += per) {
+        const size_t cnt_i = std::min(per, m - done);
+        char* dst[6];
+        size_t o = 0;
+        for (int a = 0; a < 6; ++a) {
+          dst[a] = stage + o;
+          o += (width[a] * cnt_i + 255) & ~size_t(255);
+          CK(cudaMemcpyAsync(dst[a], src[a] + width[a] * done, width[a] * cnt_i, cudaMemcpyHostToDevice, h->st));
         }
-        c32[i] = c;
-        f32[i] = f;
-        x32[i] = (float)vx[i];
-        y32[i] = (float)vy[i];
-        z32[i] = (float)vz[i];
-        id2[i] = id[i];
+        CK(launch_restore32(reinterpret_cast<const int*>(dst[0]), reinterpret_cast<const double*>(dst[1]),
+                            reinterpret_cast<const double*>(dst[2]), reinterpret_cast<const double*>(dst[3]),
+                            reinterpret_cast<const double*>(dst[4]),
+                            reinterpret_cast<const unsigned long long*>(dst[5]), cnt_i, h->a32[0][s], done, N,
+                            h->st));
       }
-      const Species32& a = h->a32[0][s];
-      CK(cudaMemcpy(a.cell, c32.data(), 4 * mp, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(a.frac, f32.data(), 4 * mp, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(a.vx, x32.data(), 4 * mp, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(a.vy, y32.data(), 4 * mp, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(a.vz, z32.data(), 4 * mp, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(a.id, id2.data(), 8 * mp, cudaMemcpyHostToDevice));
+      if (mp > m) {
+        const int dead[4] = {PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL};
+        CK(cudaMemcpyAsync(h->a32[0][s].cell + m, dead, 4 * (mp - m), cudaMemcpyHostToDevice, h->st));
+        CK(cudaStreamSynchronize(h->st));
+      }
     } else {
       std::vector<double> x(mp, -1.0), a1(mp, 0.0), a2(mp, 0.0), a3(mp, 0.0);
       std::vector<uint64_t> id2(mp, 0ull);
+      const unsigned char* cell = b + off;
       for (size_t i = 0; i < m; ++i) {
-        double xx = (double)cell[i] + frac[i];
-        if (xx >= (double)cell[i] + 1.0) xx = std::nextafter((double)cell[i] + 1.0, 0.0);
+        int32_t c;
+        double f;
+        std::memcpy(&c, cell + 4 * i, 4);
+        std::memcpy(&f, cell + 4 * m + 8 * i, 8);
+        double xx = (double)c + f;
+        if (xx >= (double)c + 1.0) xx = std::nextafter((double)c + 1.0, 0.0);
         x[i] = xx;
-        a1[i] = vx[i];
-        a2[i] = vy[i];
-        a3[i] = vz[i];
-        id2[i] = id[i];
+        std::memcpy(&a1[i], cell + 12 * m + 8 * i, 8);
+        std::memcpy(&a2[i], cell + 20 * m + 8 * i, 8);
+        std::memcpy(&a3[i], cell + 28 * m + 8 * i, 8);
+        std::memcpy(&id2[i], cell + 36 * m + 8 * i, 8);
       }
       const Species64& a = h->a64[s];
       CK(cudaMemcpy(a.x, x.data(), 8 * mp, cudaMemcpyHostToDevice));
@@ -896,7 +985,9 @@ int pic_restore(pic_handle* h, const void* buf, size_t len) {
       CK(cudaMemcpy(a.vz, a3.data(), 8 * mp, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(a.id, id2.data(), 8 * mp, cudaMemcpyHostToDevice));
     }
+    off += 44 * m;
   }
+  CK(cudaStreamSynchronize(h->st));
   Ctl c;
   std::memset(&c, 0, sizeof(c));
   for (int s = 0; s < 2; ++s) {

@@ -94,31 +94,12 @@ __global__ void __launch_bounds__(256) k_load64(const StepParams64 P, const Load
   }
 }
 
-// Sum of 0.5 m v^2 over live particles in 2^-24 fixed point: exact integer sums, independent of
-// particle order and of the launch shape.
+// Plain path: sum of 0.5 m v^2 over live particles in 2^-24 fixed point (exact integer sums,
+// independent of particle order and launch shape).  The FP32 step sums its own (ke_fx32).
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
   return v;
-}
-
-__global__ void __launch_bounds__(256) k_diag32(const StepParams32 P) {
-  const unsigned long long n0 = P.ctl->n_cur[0], n1 = P.ctl->n_cur[1];
-  unsigned long long acc[2] = {0ull, 0ull};
-  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < n0 + n1;
-       g += (unsigned long long)gridDim.x * blockDim.x) {
-    const int s = g < n0 ? 0 : 1;
-    const unsigned long long i = s ? g - n0 : g;
-    const Species32 A = s ? P.sp[1] : P.sp[0];
-    if (A.cell[i] == PIC_DEAD_CELL) continue;
-    double vx = A.vx[i], vy = A.vy[i], vz = A.vz[i];
-    double e = 0.5 * P.ph.sp[s].mass_d * (vx * vx + vy * vy + vz * vz);
-    acc[s] += __double2ull_rn(e * 16777216.0);
-  }
-  for (int s = 0; s < 2; ++s) {
-    unsigned long long t = warp_sum64(acc[s]);
-    if ((threadIdx.x & 31) == 0 && t) atomicAdd(&P.ctl->ke_fx[s], t);
-  }
 }
 
 __global__ void __launch_bounds__(256) k_diag64(const StepParams64 P) {
@@ -137,6 +118,69 @@ __global__ void __launch_bounds__(256) k_diag64(const StepParams64 P) {
   for (int s = 0; s < 2; ++s) {
     unsigned long long t = warp_sum64(acc[s]);
     if ((threadIdx.x & 31) == 0 && t) atomicAdd(&P.ctl->ke_fx[s], t);
+  }
+}
+
+// Net deposited charge (exact int64) and field energy sum_j w_j 0.5 E_j^2 dx (w = 1/2 at the walls):
+// block b sums a fixed run of nodes in a fixed order and writes its partial; the host adds the
+// PIC_DIAG_BLOCKS partials in block order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_diag_grid(const long long* __restrict__ R0, const long long* __restrict__ R1,
+                                                   int sign0, int sign1, const double* __restrict__ E, int N,
+                                                   double dx, Ctl* ctl) {
+  __shared__ double wsum[8];
+  const int seg = (N + 1 + gridDim.x - 1) / gridDim.x;
+  const int a = blockIdx.x * seg, b = min(N + 1, a + seg);
+  double fe = 0.0;
+  long long q = 0;
+  for (int j = a + (int)threadIdx.x; j < b; j += blockDim.x) {
+    const double e = E[j];
+    fe += ((j == 0 || j == N) ? 0.25 : 0.5) * e * e * dx;
+    q += (long long)sign0 * R0[j] + (long long)sign1 * R1[j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fe += __shfl_down_sync(0xFFFFFFFFu, fe, o);
+    q += __shfl_down_sync(0xFFFFFFFFu, q, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    wsum[threadIdx.x >> 5] = fe;
+    if (q) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->netq), (unsigned long long)q);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+    ctl->fe_part[blockIdx.x] = t;
+  }
+}
+
+// Restore: one chunk of a snapshot's per-species arrays (uploaded as they are in the blob: int32
+// cells, FP64 fractions and velocities, u64 ids) converted to the FP32 layout.  The host has
+// already checked cells and fractions; a fraction that rounds up to 1 moves to the next cell.
+__global__ void __launch_bounds__(256) k_restore32(const int* __restrict__ cell, const double* __restrict__ frac,
+                                                   const double* __restrict__ vx, const double* __restrict__ vy,
+                                                   const double* __restrict__ vz,
+                                                   const unsigned long long* __restrict__ id, unsigned long long n,
+                                                   Species32 dst, unsigned long long base, int N) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    int c = cell[i];
+    float f = (float)frac[i];
+    if (f >= 1.f) {
+      f = 0.f;
+      c += 1;
+      if (c >= N) {
+        c = N - 1;
+        f = 0.99999994f;
+      }
+    }
+    const unsigned long long k = base + i;
+    dst.cell[k] = c;
+    dst.frac[k] = f;
+    dst.vx[k] = (float)vx[i];
+    dst.vy[k] = (float)vy[i];
+    dst.vz[k] = (float)vz[i];
+    dst.id[k] = id[i];
   }
 }
 
@@ -168,13 +212,24 @@ cudaError_t launch_load64(const StepParams64& p, const unsigned long long n[2], 
   return cudaGetLastError();
 }
 
-cudaError_t launch_diag32(const StepParams32& p, int grid, cudaStream_t st) {
-  k_diag32<<<grid, 256, 0, st>>>(p);
+cudaError_t launch_diag64(const StepParams64& p, int grid, cudaStream_t st) {
+  k_diag64<<<grid, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_diag64(const StepParams64& p, int grid, cudaStream_t st) {
-  k_diag64<<<grid, 256, 0, st>>>(p);
+cudaError_t launch_diag_grid(const long long* R0, const long long* R1, int sign0, int sign1, const double* E, int N,
+                             double dx, Ctl* ctl, cudaStream_t st) {
+  k_diag_grid<<<PIC_DIAG_BLOCKS, 256, 0, st>>>(R0, R1, sign0, sign1, E, N, dx, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restore32(const int* cell, const double* frac, const double* vx, const double* vy, const double* vz,
+                             const unsigned long long* id, unsigned long long n, const Species32& dst,
+                             unsigned long long base, int N, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned long long blocks = (n + 255) / 256;
+  const int grid = (int)(blocks < 152ull * 16 ? blocks : 152ull * 16);
+  k_restore32<<<grid, 256, 0, st>>>(cell, frac, vx, vy, vz, id, n, dst, base, N);
   return cudaGetLastError();
 }
 

@@ -95,6 +95,8 @@ __device__ void bookkeeping(const PoissonParams& P) {
     }
     g->n_cur[s] = pad;
     g->n_born[s] = 0ull;
+    g->ke_last[s] = g->ke_acc[s];
+    g->ke_acc[s] = 0ull;
   }
   g->src_K = 0ull;
 }

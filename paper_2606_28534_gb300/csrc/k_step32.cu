@@ -28,6 +28,7 @@ struct BlockCounters {
   unsigned int lost[2];
   unsigned int born[2];
   unsigned long long efx[2];
+  unsigned long long ke[2];  // kinetic energy (ke_fx32) of particles handled out of the hot loop
 };
 
 __device__ __forceinline__ void iso_dir_f(unsigned wa, unsigned wb, float& dx, float& dy, float& dz) {
@@ -169,11 +170,13 @@ __device__ __forceinline__ float4 collide_electron(const StepParams32& P, unsign
     atomicAdd(P.cnt[0] + c, 1u);
     atomicAdd(P.S[0] + c, wr);
     atomicAdd(&bc->born[0], 1u);
+    atomicAdd(&bc->ke[0], ke_fx32(ce[0], ce[1], ce[2], ph.sp[0].mass));
   }
   if (append32<1>(P, ncur1, c, f, ci, (unsigned long long)kk.z | ((unsigned long long)kk.w << 32))) {
     atomicAdd(P.cnt[1] + c, 1u);
     atomicAdd(P.S[1] + c, wr);
     atomicAdd(&bc->born[1], 1u);
+    atomicAdd(&bc->ke[1], ke_fx32(ci[0], ci[1], ci[2], ph.sp[1].mass));
   }
   return make_float4(spp * dx, spp * dy, spp * dz, 1.f);
 }
@@ -264,6 +267,7 @@ __device__ __noinline__ void flush_queue(const StepParams32& P, const unsigned l
     A.vx[i] = r.x;
     A.vy[i] = r.y;
     A.vz[i] = r.z;
+    atomicAdd(&bc->ke[s], ke_fx32(r.x, r.y, r.z, P.ph.sp[s].mass));
   }
   __syncwarp();
 }
@@ -322,6 +326,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
     const bool moves = (ph.push_mask >> s) & 1u;
     const bool collides = moves && (s == 0 ? (ph.coll_mask & 7u) != 0u : (ph.coll_mask & 8u) != 0u);
     const unsigned long long tag = (unsigned long long)s << 63;
+    unsigned long long ke_lane = 0ull;  // kinetic energy of this lane's particles that stay live
 
     // prologue: the warp's first NSTAGE chunks
     if (lane == 0) {
@@ -418,6 +423,10 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
         *reinterpret_cast<float4*>(A.vy + i0) = make_float4(vy[0], vy[1], vy[2], vy[3]);
         *reinterpret_cast<float4*>(A.vz + i0) = make_float4(vz[0], vz[1], vz[2], vz[3]);
       }
+      // kinetic energy after the push; a candidate's is added after its collision
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k)
+        if (c[k] != PIC_DEAD_CELL && !((cand >> k) & 1u)) ke_lane += ke_fx32(vx[k], vy[k], vz[k], K.mass);
       // queue the surviving candidates (their collision changes v only, not the deposit)
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) {
@@ -455,6 +464,9 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
         qn = 0;
       }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ke_lane += __shfl_down_sync(0xFFFFFFFFu, ke_lane, o);
+    if (lane == 0 && ke_lane) atomicAdd(&bc.ke[s], ke_lane);
   }
   if (failed) {
     // a stage never completed: report, then give the copies still in flight a bounded chance to
@@ -486,6 +498,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
     if (dl) atomicAdd(&g->n_live[s], (unsigned long long)dl);
     if (bc.born[s]) atomicAdd(&g->births[s], (unsigned long long)bc.born[s]);
     if (bc.efx[s]) atomicAdd(&g->wall_energy_fx[s], bc.efx[s]);
+    if (bc.ke[s]) atomicAdd(&g->ke_acc[s], bc.ke[s]);
   } else if (tid == 15) {
     long long qq = 0;
     for (int s = 0; s < 2; ++s) qq += (long long)ph.sp[s].qsign * (long long)(bc.hits[s][0] + bc.hits[s][1]);
@@ -524,6 +537,7 @@ __global__ void __launch_bounds__(256) k_source32(const StepParams32 P) {
         atomicAdd(P.cnt[0] + c, 1u);
         atomicAdd(P.S[0] + c, (unsigned long long)wr);
         atomicAdd(&added[0], 1u);
+        atomicAdd(&P.ctl->ke_acc[0], ke_fx32(v[0], v[1], v[2], ph.sp[0].mass));
       }
     }
     {
@@ -536,6 +550,7 @@ __global__ void __launch_bounds__(256) k_source32(const StepParams32 P) {
         atomicAdd(P.cnt[1] + c, 1u);
         atomicAdd(P.S[1] + c, (unsigned long long)wr);
         atomicAdd(&added[1], 1u);
+        atomicAdd(&P.ctl->ke_acc[1], ke_fx32(v[0], v[1], v[2], ph.sp[1].mass));
       }
     }
   }

@@ -41,6 +41,8 @@
 #define ERR_TIMEOUT 2u
 #define ERR_DEVICE 4u
 
+#define PIC_DIAG_BLOCKS 64  // node blocks of the field-energy reduction (fixed: reproducible sums)
+
 struct Ctl {
   unsigned long long n_cur[2];   // array extent (multiple of 4, includes dead slots)
   unsigned long long n_born[2];  // slots claimed past n_cur in the current step
@@ -61,6 +63,10 @@ struct Ctl {
   unsigned long long ke_fx[2];           // diag scratch: sum 0.5 m v^2, 2^-24 units
   unsigned long long particle_steps;     // sum over steps of the live particles at step start
   unsigned long long live_mark;          // live particles at the start of the next step
+  unsigned long long ke_acc[2];          // sum of ke_fx32 over the particles alive after this step
+  unsigned long long ke_last[2];         // ke_acc of the last completed step (read by pic_diag)
+  long long netq;                        // diag scratch: sum_j sum_s sign(q_s) R_sj
+  double fe_part[PIC_DIAG_BLOCKS];       // diag scratch: field energy per block of nodes
 };
 
 struct Species32 {
@@ -164,6 +170,14 @@ __device__ __forceinline__ double u01d(unsigned w) { return (double)(w >> 8) * 5
 
 __host__ __device__ inline unsigned long long round_up4(unsigned long long n) { return (n + 3ull) & ~3ull; }
 
+// Kinetic energy of one FP32 particle in 2^-24 fixed point with every rounding spelled out (no
+// contraction), so the sum over particles is exact and independent of order and of the kernel
+// that forms it: rint(2^24 * (m/2) * ((vx^2 + vy^2) + vz^2)), all products and sums in FP32.
+__device__ __forceinline__ unsigned long long ke_fx32(float vx, float vy, float vz, float mass) {
+  const float t = __fadd_rn(__fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy)), __fmul_rn(vz, vz));
+  return __float2ull_rn(__fmul_rn(__fmul_rn(__fmul_rn(0.5f, mass), t), 16777216.0f));
+}
+
 // --------------------------------------------------------------------------------------------
 // Bulk asynchronous copies (TMA, 1D) and mbarriers, inline PTX for sm_90+.
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -249,7 +263,11 @@ cudaError_t launch_load64(const StepParams64& p, const unsigned long long n[2], 
 cudaError_t launch_sort32(Species32 src[2], Species32 dst[2], unsigned int* cnt[2],
                           unsigned int* cursor[2], const unsigned long long cap[2], Ctl* ctl, int N,
                           int grid, cudaStream_t st);
-cudaError_t launch_diag32(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_diag64(const StepParams64& p, int grid, cudaStream_t st);
+cudaError_t launch_diag_grid(const long long* R0, const long long* R1, int sign0, int sign1, const double* E, int N,
+                             double dx, Ctl* ctl, cudaStream_t st);
+cudaError_t launch_restore32(const int* cell, const double* frac, const double* vx, const double* vy, const double* vz,
+                             const unsigned long long* id, unsigned long long n, const Species32& dst,
+                             unsigned long long base, int N, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                           cudaStream_t st);
