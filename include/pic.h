@@ -194,6 +194,95 @@ int pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n
 int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double V_R,
                 double* phi, double* E, void* cuda_stream);
 
+/* ---- ensembles: many independent simulations advanced together ------------------------------
+ *
+ * A batch holds nsims independent simulations (a parameter scan, the seeds of one study) and
+ * advances all of them by one step with one persistent launch of the particle step over every
+ * simulation's particles -- their uneven particle counts split evenly over the GPU, as the
+ * particle load balancing of Sec. 4.1 ("Particle Load Balancing") splits uneven particle
+ * distributions over MPI ranks --
+ * one launch of the field solve (one thread-block cluster per simulation), and, on sort steps,
+ * one per-cell counting sort over all of them.  Repeated steps replay a captured CUDA graph of
+ * 2 * sort_interval steps.  Each simulation computes exactly what pic_init + pic_step compute for
+ * its own configuration: the same random draws, the same int64 deposit, the same field, the same
+ * particle set; the batch changes only how the work is laid out on the GPU.
+ *
+ * What may differ between the simulations of a batch: ncells (and L with it), ppc, the initial
+ * load (profile, T), the collision set and every collision parameter (n_gas, sigma_*, E_*, E_cap,
+ * Tg, m_gas), the wall potentials, capacity_factor and the seed.  What they must share: dt, the
+ * cell size L / ncells, B and its angle, the species masses and charges, frozen_mask, field_mode,
+ * E_ext and sort_interval.  Every simulation must use PIC_FP32, PIC_SOURCE_NONE and integer
+ * species charges (the integer-exact field solve); 1 <= nsims <= PIC_BATCH_MAX_SIMS; the
+ * particle capacities of each species together below 2^31.  Anything else: PIC_EINVAL.
+ *
+ * Conventions are those of the single-simulation calls: the caller owns host buffers, work runs on
+ * the stream given to pic_batch_init, device errors surface at the next synchronising call.
+ * Simulation k of a batch is addressed by its index 0 <= k < nsims. */
+#define PIC_BATCH_MAX_SIMS 4096
+
+typedef struct pic_batch pic_batch;
+
+/* Launch configuration of the batch step; results do not depend on it. */
+typedef struct pic_batch_tuning {
+  int32_t variant;          /* shape of the particle-step kernel, 0 .. pic_batch_variant_count()-1 */
+  int32_t ctas_per_sm;      /* resident CTAs per SM of the particle step; 0 = as many as fit */
+  int32_t sort_ctas_per_sm; /* CTAs per SM of the sort's scatter; 0 = 4 */
+  int32_t use_graph;        /* nonzero: replay CUDA graphs of 2 * sort_interval steps */
+} pic_batch_tuning;
+
+/* Number of compiled shapes of the batch particle-step kernel, and the name of shape v
+ * ("tpb<threads per CTA>_minb<CTAs per SM>_stages<TMA stages per warp>"; NULL if out of range). */
+int32_t pic_batch_variant_count(void);
+const char* pic_batch_variant_name(int32_t v);
+
+/* Bytes of device workspace that pic_batch_init needs for these configurations. */
+int pic_batch_workspace_size(const pic_config* cfgs, int32_t nsims, size_t* bytes);
+
+/* Create a batch from nsims configurations (host array; copied): as pic_workspace_size /
+ * pic_init, with workspace NULL meaning cudaMalloc.  Loads every simulation as pic_init would,
+ * then plans the first step.  The default tuning is shape 0, all CTAs that fit, graphs on. */
+int pic_batch_init(const pic_config* cfgs, int32_t nsims, void* workspace, size_t workspace_bytes,
+                   void* cuda_stream, pic_batch** out);
+
+/* Set / read the launch configuration (PIC_EINVAL for an unknown shape or a CTA count beyond
+ * what fits on an SM).  Setting drops captured graphs. */
+int pic_batch_set_tuning(pic_batch* b, const pic_batch_tuning* t);
+int pic_batch_get_tuning(pic_batch* b, pic_batch_tuning* t);
+
+/* Enqueue n >= 0 steps of every simulation (asynchronous on the batch's stream). */
+int pic_batch_step(pic_batch* b, int32_t n);
+
+/* Wait for the stream; report device-side errors of any simulation. */
+int pic_batch_sync(pic_batch* b);
+
+/* Diagnostics of simulations 0 .. nsims-1 into out[0 .. nsims-1] (as pic_diag). */
+int pic_batch_diag(pic_batch* b, pic_diag_t* out, int32_t nsims);
+
+/* Snapshot of simulation k, in pic_snapshot's format: the blob restores into a single handle made
+ * from the same configuration, and vice versa. */
+int pic_batch_snapshot(pic_batch* b, int32_t k, void* buf, size_t cap, size_t* needed);
+
+/* Replace the state of every simulation: blobs[k] (lens[k] bytes) for simulation k, each made
+ * with simulation k's configuration, all at the same step (which becomes the batch's step).
+ * Checks every blob before changing any state (PIC_ECORRUPT, PIC_EOVERFLOW as pic_restore). */
+int pic_batch_restore(pic_batch* b, const void* const* blobs, const size_t* lens);
+
+/* Back to the state pic_batch_init made (every simulation reloaded, step 0). */
+int pic_batch_reset(pic_batch* b);
+
+/* Grid of simulation k (as pic_get_field; nnodes = its ncells + 1). */
+int pic_batch_get_field(pic_batch* b, int32_t k, int64_t* R, double* rho, double* phi, float* E,
+                        size_t nnodes);
+
+/* Per-kernel device time (as pic_profile / pic_kernel_times; kinds "step", "field", "sort",
+ * "plan").  While profiling, steps are launched one by one (no graphs). */
+int pic_batch_profile(pic_batch* b, int enable);
+int pic_batch_kernel_times(pic_batch* b, double* ms, uint64_t* launches, const char** names,
+                           int32_t nkinds);
+
+/* Destroy the batch (synchronises; frees what pic_batch_init allocated). */
+void pic_batch_free(pic_batch* b);
+
 /* ---- allocation-free entry point ------------------------------------------------------------ */
 
 /* The paper has no counterpart to this call: it exists for callers that cannot allocate device

@@ -30,7 +30,7 @@ def _nvcc() -> str:
 def _headers_mtime() -> float:
     t = os.path.getmtime(os.path.join(INCLUDE, "pic.h"))
     for f in os.listdir(CSRC):
-        if f.endswith(".cuh"):
+        if f.endswith((".cuh", ".h")):
             t = max(t, os.path.getmtime(os.path.join(CSRC, f)))
     return t
 

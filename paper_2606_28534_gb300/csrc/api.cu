@@ -10,54 +10,12 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/pic.h"
-#include "pic_internal.cuh"
+#include "api_internal.h"
 
-int occupancy_step32();
-int occupancy_step64();
+namespace picx {
 
-namespace {
+const char* const kKindNames[PIC_KERNEL_KINDS] = {"step", "source", "field", "sort", "load", "diag", "plan", ""};
 
-enum Kind { K_STEP = 0, K_SOURCE, K_FIELD, K_SORT, K_LOAD, K_DIAG, K_KINDS };
-const char* kKindNames[PIC_KERNEL_KINDS] = {"step", "source", "field", "sort", "load", "diag", "", ""};
-
-struct EvPair {
-  int kind;
-  cudaEvent_t a, b;
-};
-
-}  // namespace
-
-struct pic_handle {
-  pic_config cfg;
-  cudaStream_t st = nullptr;
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  bool owns_ws = false;
-  int N = 0;
-  bool plain = false;
-  unsigned long long cap[2] = {0, 0};
-  Species32 a32[2][2];  // [buffer][species]
-  int cur = 0;
-  Species64 a64[2];
-  unsigned int* cnt[2] = {nullptr, nullptr};
-  unsigned long long* S[2] = {nullptr, nullptr};
-  unsigned int* cursor[2] = {nullptr, nullptr};
-  double* acc[2] = {nullptr, nullptr};
-  long long* R[2] = {nullptr, nullptr};
-  double *rho = nullptr, *phi = nullptr, *E = nullptr;
-  float2* E2 = nullptr;
-  Ctl* ctl = nullptr;
-  Phys ph;
-  unsigned long long step = 0;
-  int grid_step = 0, grid_sort = 0, grid_diag = 0;
-  bool prof = false;
-  std::vector<EvPair> ev;
-  double ms[PIC_KERNEL_KINDS] = {0};
-  uint64_t launches[PIC_KERNEL_KINDS] = {0};
-};
-
-namespace {
 
 // ---------------------------------------------------------------------------------------------
 bool valid(const pic_config* c) {
@@ -116,6 +74,8 @@ void layout(pic_handle* h, char* base, size_t* total) {
         a.vz = cv.take<float>(h->cap[s]);
         a.id = cv.take<unsigned long long>(h->cap[s]);
       }
+    h->stage = reinterpret_cast<char*>(h->a32[1][0].cell);
+    h->stage_bytes = h->stage ? (size_t)(reinterpret_cast<char*>(h->a32[1][1].id + h->cap[1]) - h->stage) : 0;
     for (int s = 0; s < 2; ++s) {
       h->cnt[s] = cv.take<unsigned int>(N);
       h->S[s] = cv.take<unsigned long long>(N);
@@ -275,10 +235,20 @@ StepParams64 params64(pic_handle* h) {
 // Integer-exact field (k_field_exact) when both charges are small integers: the net deposit
 // r = m_0 R_0 + m_1 R_1 with m_s = q_s ppc_{1-s} / g (g = gcd of the ppc) is an exact integer and
 // f = kappa r with kappa = dx^2 2^-32 g / (ppc_0 ppc_1).
+bool exact_possible(const pic_config& c) {
+  const long long g = std::gcd((long long)c.ppc[0], (long long)c.ppc[1]);
+  for (int s = 0; s < 2; ++s) {
+    const double q = c.charge[s];
+    if (q != std::floor(q) || std::fabs(q) > 64.0) return false;
+    if ((long long)c.ppc[1 - s] / g > 1024) return false;
+  }
+  return true;
+}
+
 void exact_coefficients(pic_handle* h, PoissonParams* F) {
   const pic_config& c = h->cfg;
   F->exact = 0;
-  if (h->plain) return;
+  if (h->plain || !exact_possible(c)) return;
   long long g = std::gcd((long long)c.ppc[0], (long long)c.ppc[1]);
   for (int s = 0; s < 2; ++s) {
     const double q = c.charge[s];
@@ -373,14 +343,63 @@ int field_diagnostics(pic_handle* h) {
   return PIC_OK;
 }
 
-int check_errors(pic_handle* h) {
-  CK(cudaStreamSynchronize(h->st));
-  unsigned int err = 0;
-  CK(cudaMemcpy(&err, &h->ctl->error, sizeof(err), cudaMemcpyDeviceToHost));
+int status_of(unsigned int err) {
   if (err & ERR_OVERFLOW) return PIC_EOVERFLOW;
   if (err & ERR_TIMEOUT) return PIC_ETIMEOUT;
   if (err & ERR_DEVICE) return PIC_EDEVICE;
   return PIC_OK;
+}
+
+int check_errors(pic_handle* h) {
+  CK(cudaStreamSynchronize(h->st));
+  unsigned int err = 0;
+  CK(cudaMemcpy(&err, &h->ctl->error, sizeof(err), cudaMemcpyDeviceToHost));
+  return status_of(err);
+}
+
+int load_initial(pic_handle* h) {
+  const pic_config& c = h->cfg;
+  int rc = PIC_OK;
+  h->cur = 0;
+  h->step = 0;
+  unsigned long long n[2];
+  for (int s = 0; s < 2; ++s) n[s] = (unsigned long long)c.ppc[s] * (unsigned long long)c.ncells;
+  {
+    EvPair e;
+    prof_begin(h, K_LOAD, &e);
+    cudaError_t err = h->plain ? launch_load64(params64(h), n, c.load_profile, c.ppc[0], c.ppc[1],
+                                               c.profile_scale, c.profile_mode, h->st)
+                               : launch_load32(params32(h), n, c.load_profile, c.ppc[0], c.ppc[1],
+                                               c.profile_scale, c.profile_mode, h->st);
+    prof_end(h, &e);
+    if (err != cudaSuccess) rc = PIC_ECUDA;
+  }
+  if (rc == PIC_OK) {
+    // extents, padding slots, live counts
+    Ctl c0;
+    std::memset(&c0, 0, sizeof(c0));
+    for (int s = 0; s < 2; ++s) {
+      c0.n_cur[s] = round_up4(n[s]);
+      c0.n_live[s] = n[s];
+      const unsigned long long pad = c0.n_cur[s] - n[s];
+      if (pad) {
+        if (!h->plain) {
+          int dead[4] = {PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL};
+          if (cudaMemcpyAsync(h->a32[0][s].cell + n[s], dead, pad * 4, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            rc = PIC_ECUDA;
+        } else {
+          double dead[4] = {-1.0, -1.0, -1.0, -1.0};
+          if (cudaMemcpyAsync(h->a64[s].x + n[s], dead, pad * 8, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            rc = PIC_ECUDA;
+        }
+      }
+    }
+    if (rc == PIC_OK && cudaMemcpyAsync(h->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+      rc = PIC_ECUDA;
+    if (rc == PIC_OK) rc = refresh_field(h);
+    if (rc == PIC_OK) rc = check_errors(h);
+  }
+  return rc;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -590,7 +609,185 @@ void put_arr(std::vector<unsigned char>& b, const std::vector<T>& v) {
   b.insert(b.end(), p, p + sizeof(T) * v.size());
 }
 
-}  // namespace
+int check_blob(const pic_handle* h, const void* buf, size_t len) {
+  if (!h || !buf) return PIC_EINVAL;
+  const unsigned char* b = static_cast<const unsigned char*>(buf);
+  if (len < kHdr + 4 || std::memcmp(b, "PICMCSN1", 8) != 0) return PIC_ECORRUPT;
+  uint32_t crc;
+  std::memcpy(&crc, b + len - 4, 4);
+  if (crc != crc32_ieee(b, len - 4)) return PIC_ECORRUPT;
+  uint32_t ver;
+  uint64_t hash, step, n[2];
+  std::memcpy(&ver, b + 8, 4);
+  std::memcpy(&hash, b + 16, 8);
+  std::memcpy(&step, b + 24, 8);
+  std::memcpy(n, b + 32, 16);
+  if (ver != 1 || hash != config_hash(h->cfg)) return PIC_ECORRUPT;
+  if (n[0] > (1ull << 40) || n[1] > (1ull << 40) || len != kHdr + 4 + 44 * (n[0] + n[1])) return PIC_ECORRUPT;
+  for (int s = 0; s < 2; ++s)
+    if (round_up4(n[s]) > h->cap[s]) return PIC_EOVERFLOW;
+  const int N = h->N;
+  // range of every cell and fraction (host threads)
+  {
+    size_t off = kHdr;
+    bool bad = false;
+    for (int s = 0; s < 2; ++s) {
+      const size_t m = (size_t)n[s];
+      const unsigned char* cell = b + off;
+      const unsigned char* frac = cell + 4 * m;
+      const int T = host_threads(12 * m);
+      std::vector<char> flag(T, 0);
+      std::vector<std::thread> th;
+      const size_t chunk = (m + T - 1) / T;
+      for (int k = 0; k < T; ++k) {
+        th.emplace_back([&, k]() {
+          const size_t i0 = std::min(m, (size_t)k * chunk), i1 = std::min(m, i0 + chunk);
+          for (size_t i = i0; i < i1; ++i) {
+            int32_t c;
+            double f;
+            std::memcpy(&c, cell + 4 * i, 4);
+            std::memcpy(&f, frac + 8 * i, 8);
+            if (c < 0 || c >= N || !(f >= 0.0 && f < 1.0)) {
+              flag[k] = 1;
+              break;
+            }
+          }
+        });
+      }
+      for (auto& t : th) t.join();
+      for (char f : flag) bad = bad || f;
+      off += 44 * m;
+    }
+    if (bad) return PIC_ECORRUPT;
+  }
+  return PIC_OK;
+}
+
+int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
+  if (!h || !buf) return PIC_EINVAL;
+  if (!checked) {
+    const int rc = check_blob(h, buf, len);
+    if (rc != PIC_OK) return rc;
+  }
+  const unsigned char* b = static_cast<const unsigned char*>(buf);
+  uint64_t step, n[2];
+  std::memcpy(&step, b + 24, 8);
+  std::memcpy(n, b + 32, 16);
+  CK(cudaStreamSynchronize(h->st));
+  uint64_t cnt[17];
+  int64_t wall_charge;
+  double wall_energy[2];
+  std::memcpy(cnt, b + 48, sizeof(cnt));
+  std::memcpy(&wall_charge, b + 48 + 136, 8);
+  std::memcpy(wall_energy, b + 48 + 144, 16);
+  const int N = h->N;
+  const double dx = h->cfg.L / N;
+  size_t off = kHdr;
+  h->cur = 0;
+  for (int s = 0; s < 2; ++s) {
+    const size_t m = (size_t)n[s];
+    const size_t mp = (size_t)round_up4(m);
+    if (!h->plain) {
+      // the blob's arrays go straight to device staging (the sort's second buffer, unused
+      // between sorts) and a kernel converts them into buffer 0
+      char* stage = h->stage;
+      const size_t stage_bytes = h->stage_bytes;
+      const size_t per = std::max<size_t>(4, (stage_bytes - 6 * 256) / 44 / 4 * 4);
+      const unsigned char* src[6] = {b + off, b + off + 4 * m, b + off + 12 * m, b + off + 20 * m,
+                                     b + off + 28 * m, b + off + 36 * m};
+      const size_t width[6] = {4, 8, 8, 8, 8, 8};
+      for (size_t done = 0; done < m; done += per) {
+        const size_t cnt_i = std::min(per, m - done);
+        char* dst[6];
+        size_t o = 0;
+        for (int a = 0; a < 6; ++a) {
+          dst[a] = stage + o;
+          o += (width[a] * cnt_i + 255) & ~size_t(255);
+          CK(cudaMemcpyAsync(dst[a], src[a] + width[a] * done, width[a] * cnt_i, cudaMemcpyHostToDevice, h->st));
+        }
+        CK(launch_restore32(reinterpret_cast<const int*>(dst[0]), reinterpret_cast<const double*>(dst[1]),
+                            reinterpret_cast<const double*>(dst[2]), reinterpret_cast<const double*>(dst[3]),
+                            reinterpret_cast<const double*>(dst[4]),
+                            reinterpret_cast<const unsigned long long*>(dst[5]), cnt_i, h->a32[0][s], done, N,
+                            h->st));
+      }
+      if (mp > m) {
+        const int dead[4] = {PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL};
+        CK(cudaMemcpyAsync(h->a32[0][s].cell + m, dead, 4 * (mp - m), cudaMemcpyHostToDevice, h->st));
+        CK(cudaStreamSynchronize(h->st));
+      }
+    } else {
+      std::vector<double> x(mp, -1.0), a1(mp, 0.0), a2(mp, 0.0), a3(mp, 0.0);
+      std::vector<uint64_t> id2(mp, 0ull);
+      const unsigned char* cell = b + off;
+      for (size_t i = 0; i < m; ++i) {
+        int32_t c;
+        double f;
+        std::memcpy(&c, cell + 4 * i, 4);
+        std::memcpy(&f, cell + 4 * m + 8 * i, 8);
+        double xx = (double)c + f;
+        if (xx >= (double)c + 1.0) xx = std::nextafter((double)c + 1.0, 0.0);
+        x[i] = xx;
+        std::memcpy(&a1[i], cell + 12 * m + 8 * i, 8);
+        std::memcpy(&a2[i], cell + 20 * m + 8 * i, 8);
+        std::memcpy(&a3[i], cell + 28 * m + 8 * i, 8);
+        std::memcpy(&id2[i], cell + 36 * m + 8 * i, 8);
+      }
+      const Species64& a = h->a64[s];
+      CK(cudaMemcpy(a.x, x.data(), 8 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.vx, a1.data(), 8 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.vy, a2.data(), 8 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.vz, a3.data(), 8 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.id, id2.data(), 8 * mp, cudaMemcpyHostToDevice));
+    }
+    off += 44 * m;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  Ctl c;
+  std::memset(&c, 0, sizeof(c));
+  for (int s = 0; s < 2; ++s) {
+    c.n_cur[s] = round_up4(n[s]);
+    c.n_live[s] = n[s];
+  }
+  int k = 0;
+  for (int s = 0; s < 2; ++s)
+    for (int side = 0; side < 2; ++side) c.wall_hits[s][side] = cnt[k++];
+  for (int i = 0; i < 5; ++i) c.coll[i] = cnt[k++];
+  for (int s = 0; s < 2; ++s) c.near_thr[s] = cnt[k++];
+  for (int s = 0; s < 2; ++s) c.viol[s] = cnt[k++];
+  for (int s = 0; s < 2; ++s) c.births[s] = cnt[k++];
+  c.source_pairs = cnt[k++];
+  c.dropped = cnt[k++];
+  c.wall_charge = wall_charge;
+  for (int s = 0; s < 2; ++s) {
+    const double w = dx / h->cfg.ppc[s];
+    c.wall_energy_fx[s] = (unsigned long long)std::llrint(wall_energy[s] / w * 16777216.0);
+  }
+  CK(cudaMemcpy(h->ctl, &c, sizeof(c), cudaMemcpyHostToDevice));
+  // clear the grid accumulators (a previous step may have left counts for a sort)
+  if (!h->plain) {
+    for (int s = 0; s < 2; ++s) {
+      CK(cudaMemsetAsync(h->cnt[s], 0, sizeof(unsigned int) * N, h->st));
+      CK(cudaMemsetAsync(h->S[s], 0, sizeof(unsigned long long) * N, h->st));
+    }
+  } else {
+    for (int s = 0; s < 2; ++s) CK(cudaMemsetAsync(h->acc[s], 0, sizeof(double) * (N + 1), h->st));
+  }
+  h->step = step;
+  return PIC_OK;
+}
+
+bool blob_step(const void* buf, size_t len, unsigned long long* step) {
+  if (!buf || len < kHdr + 4 || std::memcmp(buf, "PICMCSN1", 8) != 0) return false;
+  uint64_t v;
+  std::memcpy(&v, static_cast<const unsigned char*>(buf) + 24, 8);
+  *step = v;
+  return true;
+}
+
+}  // namespace picx
+
+using namespace picx;
 
 // =============================================================================================
 extern "C" {
@@ -667,43 +864,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
       cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st) != cudaSuccess) {
     rc = PIC_ECUDA;
   }
-  unsigned long long n[2];
-  for (int s = 0; s < 2; ++s) n[s] = (unsigned long long)cfg->ppc[s] * (unsigned long long)cfg->ncells;
-  if (rc == PIC_OK) {
-    EvPair e;
-    prof_begin(h, K_LOAD, &e);
-    cudaError_t err = h->plain ? launch_load64(params64(h), n, cfg->load_profile, cfg->ppc[0], cfg->ppc[1],
-                                               cfg->profile_scale, cfg->profile_mode, h->st)
-                               : launch_load32(params32(h), n, cfg->load_profile, cfg->ppc[0], cfg->ppc[1],
-                                               cfg->profile_scale, cfg->profile_mode, h->st);
-    prof_end(h, &e);
-    if (err != cudaSuccess) rc = PIC_ECUDA;
-  }
-  if (rc == PIC_OK) {
-    // extents, padding slots, live counts
-    Ctl c0;
-    std::memset(&c0, 0, sizeof(c0));
-    for (int s = 0; s < 2; ++s) {
-      c0.n_cur[s] = round_up4(n[s]);
-      c0.n_live[s] = n[s];
-      const unsigned long long pad = c0.n_cur[s] - n[s];
-      if (pad) {
-        if (!h->plain) {
-          int dead[4] = {PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL};
-          if (cudaMemcpyAsync(h->a32[0][s].cell + n[s], dead, pad * 4, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
-            rc = PIC_ECUDA;
-        } else {
-          double dead[4] = {-1.0, -1.0, -1.0, -1.0};
-          if (cudaMemcpyAsync(h->a64[s].x + n[s], dead, pad * 8, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
-            rc = PIC_ECUDA;
-        }
-      }
-    }
-    if (rc == PIC_OK && cudaMemcpyAsync(h->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
-      rc = PIC_ECUDA;
-    if (rc == PIC_OK) rc = refresh_field(h);
-    if (rc == PIC_OK) rc = check_errors(h);
-  }
+  if (rc == PIC_OK) rc = load_initial(h);
   if (rc != PIC_OK) {
     pic_free(h);
     *out = nullptr;
@@ -869,157 +1030,9 @@ int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
 }
 
 int pic_restore(pic_handle* h, const void* buf, size_t len) {
-  if (!h || !buf) return PIC_EINVAL;
-  const unsigned char* b = static_cast<const unsigned char*>(buf);
-  if (len < kHdr + 4 || std::memcmp(b, "PICMCSN1", 8) != 0) return PIC_ECORRUPT;
-  uint32_t crc;
-  std::memcpy(&crc, b + len - 4, 4);
-  if (crc != crc32_ieee(b, len - 4)) return PIC_ECORRUPT;
-  uint32_t ver;
-  uint64_t hash, step, n[2];
-  std::memcpy(&ver, b + 8, 4);
-  std::memcpy(&hash, b + 16, 8);
-  std::memcpy(&step, b + 24, 8);
-  std::memcpy(n, b + 32, 16);
-  if (ver != 1 || hash != config_hash(h->cfg)) return PIC_ECORRUPT;
-  if (n[0] > (1ull << 40) || n[1] > (1ull << 40) || len != kHdr + 4 + 44 * (n[0] + n[1])) return PIC_ECORRUPT;
-  for (int s = 0; s < 2; ++s)
-    if (round_up4(n[s]) > h->cap[s]) return PIC_EOVERFLOW;
-  CK(cudaStreamSynchronize(h->st));
-  uint64_t cnt[17];
-  int64_t wall_charge;
-  double wall_energy[2];
-  std::memcpy(cnt, b + 48, sizeof(cnt));
-  std::memcpy(&wall_charge, b + 48 + 136, 8);
-  std::memcpy(wall_energy, b + 48 + 144, 16);
-  const int N = h->N;
-  const double dx = h->cfg.L / N;
-  // range check of every cell and fraction before any device state changes (host threads)
-  {
-    size_t off = kHdr;
-    bool bad = false;
-    for (int s = 0; s < 2; ++s) {
-      const size_t m = (size_t)n[s];
-      const unsigned char* cell = b + off;
-      const unsigned char* frac = cell + 4 * m;
-      const int T = host_threads(12 * m);
-      std::vector<char> flag(T, 0);
-      std::vector<std::thread> th;
-      const size_t chunk = (m + T - 1) / T;
-      for (int k = 0; k < T; ++k) {
-        th.emplace_back([&, k]() {
-          const size_t i0 = std::min(m, (size_t)k * chunk), i1 = std::min(m, i0 + chunk);
-          for (size_t i = i0; i < i1; ++i) {
-            int32_t c;
-            double f;
-            std::memcpy(&c, cell + 4 * i, 4);
-            std::memcpy(&f, frac + 8 * i, 8);
-            if (c < 0 || c >= N || !(f >= 0.0 && f < 1.0)) {
-              flag[k] = 1;
-              break;
-            }
-          }
-        });
-      }
-      for (auto& t : th) t.join();
-      for (char f : flag) bad = bad || f;
-      off += 44 * m;
-    }
-    if (bad) return PIC_ECORRUPT;
-  }
-  size_t off = kHdr;
-  h->cur = 0;
-  for (int s = 0; s < 2; ++s) {
-    const size_t m = (size_t)n[s];
-    const size_t mp = (size_t)round_up4(m);
-    if (!h->plain) {
-      // the blob's arrays go straight to device staging (the sort's second buffer, unused
-      // between sorts) and a kernel converts them into buffer 0
-      char* stage = reinterpret_cast<char*>(h->a32[1][0].cell);
-      const size_t stage_bytes = (size_t)(reinterpret_cast<char*>(h->a32[1][1].id + h->cap[1]) - stage);
-      const size_t per = std::max<size_t>(4, (stage_bytes - 6 * 256) / 44 / 4 * 4);
-      const unsigned char* src[6] = {b + off, b + off + 4 * m, b + off + 12 * m, b + off + 20 * m,
-                                     b + off + 28 * m, b + off + 36 * m};
-      const size_t width[6] = {4, 8, 8, 8, 8, 8};
-      for (size_t done = 0; done < m; done += per) {
-        const size_t cnt_i = std::min(per, m - done);
-        char* dst[6];
-        size_t o = 0;
-        for (int a = 0; a < 6; ++a) {
-          dst[a] = stage + o;
-          o += (width[a] * cnt_i + 255) & ~size_t(255);
-          CK(cudaMemcpyAsync(dst[a], src[a] + width[a] * done, width[a] * cnt_i, cudaMemcpyHostToDevice, h->st));
-        }
-        CK(launch_restore32(reinterpret_cast<const int*>(dst[0]), reinterpret_cast<const double*>(dst[1]),
-                            reinterpret_cast<const double*>(dst[2]), reinterpret_cast<const double*>(dst[3]),
-                            reinterpret_cast<const double*>(dst[4]),
-                            reinterpret_cast<const unsigned long long*>(dst[5]), cnt_i, h->a32[0][s], done, N,
-                            h->st));
-      }
-      if (mp > m) {
-        const int dead[4] = {PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL};
-        CK(cudaMemcpyAsync(h->a32[0][s].cell + m, dead, 4 * (mp - m), cudaMemcpyHostToDevice, h->st));
-        CK(cudaStreamSynchronize(h->st));
-      }
-    } else {
-      std::vector<double> x(mp, -1.0), a1(mp, 0.0), a2(mp, 0.0), a3(mp, 0.0);
-      std::vector<uint64_t> id2(mp, 0ull);
-      const unsigned char* cell = b + off;
-      for (size_t i = 0; i < m; ++i) {
-        int32_t c;
-        double f;
-        std::memcpy(&c, cell + 4 * i, 4);
-        std::memcpy(&f, cell + 4 * m + 8 * i, 8);
-        double xx = (double)c + f;
-        if (xx >= (double)c + 1.0) xx = std::nextafter((double)c + 1.0, 0.0);
-        x[i] = xx;
-        std::memcpy(&a1[i], cell + 12 * m + 8 * i, 8);
-        std::memcpy(&a2[i], cell + 20 * m + 8 * i, 8);
-        std::memcpy(&a3[i], cell + 28 * m + 8 * i, 8);
-        std::memcpy(&id2[i], cell + 36 * m + 8 * i, 8);
-      }
-      const Species64& a = h->a64[s];
-      CK(cudaMemcpy(a.x, x.data(), 8 * mp, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(a.vx, a1.data(), 8 * mp, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(a.vy, a2.data(), 8 * mp, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(a.vz, a3.data(), 8 * mp, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(a.id, id2.data(), 8 * mp, cudaMemcpyHostToDevice));
-    }
-    off += 44 * m;
-  }
-  CK(cudaStreamSynchronize(h->st));
-  Ctl c;
-  std::memset(&c, 0, sizeof(c));
-  for (int s = 0; s < 2; ++s) {
-    c.n_cur[s] = round_up4(n[s]);
-    c.n_live[s] = n[s];
-  }
-  int k = 0;
-  for (int s = 0; s < 2; ++s)
-    for (int side = 0; side < 2; ++side) c.wall_hits[s][side] = cnt[k++];
-  for (int i = 0; i < 5; ++i) c.coll[i] = cnt[k++];
-  for (int s = 0; s < 2; ++s) c.near_thr[s] = cnt[k++];
-  for (int s = 0; s < 2; ++s) c.viol[s] = cnt[k++];
-  for (int s = 0; s < 2; ++s) c.births[s] = cnt[k++];
-  c.source_pairs = cnt[k++];
-  c.dropped = cnt[k++];
-  c.wall_charge = wall_charge;
-  for (int s = 0; s < 2; ++s) {
-    const double w = dx / h->cfg.ppc[s];
-    c.wall_energy_fx[s] = (unsigned long long)std::llrint(wall_energy[s] / w * 16777216.0);
-  }
-  CK(cudaMemcpy(h->ctl, &c, sizeof(c), cudaMemcpyHostToDevice));
-  // clear the grid accumulators (a previous step may have left counts for a sort)
-  if (!h->plain) {
-    for (int s = 0; s < 2; ++s) {
-      CK(cudaMemsetAsync(h->cnt[s], 0, sizeof(unsigned int) * N, h->st));
-      CK(cudaMemsetAsync(h->S[s], 0, sizeof(unsigned long long) * N, h->st));
-    }
-  } else {
-    for (int s = 0; s < 2; ++s) CK(cudaMemsetAsync(h->acc[s], 0, sizeof(double) * (N + 1), h->st));
-  }
-  h->step = step;
-  int rc = refresh_field(h);
+  int rc = restore_state(h, buf, len, false);
+  if (rc != PIC_OK) return rc;
+  rc = refresh_field(h);
   if (rc != PIC_OK) return rc;
   return check_errors(h);
 }

@@ -1,0 +1,464 @@
+// k_bstep32.cu -- the FP32 particle step (paper Sec. 2: interpolation, mover, MC collisions,
+// deposition) of an ensemble of independent simulations in one persistent launch, and the plan
+// kernel that lays out its work.
+//
+// Work list.  Species s of simulation k owns the chunks [pre_s[k], pre_s[k+1]) of one list over the
+// whole ensemble (chunks of 32 x PIC_PPT consecutive particles of its segment; pre_s is written by
+// k_bplan from the extents after the previous step).  Warp w of the grid takes the contiguous run
+// [w per, (w+1) per) of the list, so that a warp meets one or two simulations per species: it keeps
+// the simulation's constants (segment, cells, seed, P_null) in registers, its collision queue and
+// its counters, and hands the counters to the simulation's control block when it moves on.
+// Per particle the arithmetic is the single-run kernel's (k_step32.cu), with the simulation's cell
+// offset added for the field gather and the deposit; constants every simulation shares (push,
+// masses, field mode) are kernel parameters.
+//
+// Shapes.  The kernel is compiled for a few (CTA size, resident CTAs per SM, TMA stages per warp)
+// shapes; pic_batch_set_tuning picks one at run time (the autotuner times them).  Particles per
+// thread stay at PIC_PPT = 4: one 128-bit access per array.
+#include "step32_common.cuh"
+
+namespace {
+
+// The simulation a warp is in, as the particle loop reads it (shared memory, one per warp: read
+// where used instead of held in registers through the loop).
+struct WarpSim {
+  unsigned seg;    // first slot of the species segment
+  unsigned nk;     // extent of the species segment
+  unsigned pnull;  // null-collision probability, 0: no draw
+  int cbase;       // first cell
+  int N;           // cells
+  unsigned pad;
+  unsigned long long seed;
+};
+
+template <int TPB, int NST>
+struct BShape {
+  static constexpr int WARPS = TPB / 32;
+  static constexpr size_t SMEM = (size_t)WARPS * (NST * STAGE_BYTES + QCAP * 8 + NST * 8);
+};
+
+// Last k < nsims with pre[k] <= t, for t < pre[nsims]: the simulation that owns chunk t.
+__device__ __forceinline__ int owner(const unsigned* __restrict__ pre, int nsims, unsigned t) {
+  int lo = 0, hi = nsims;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= t)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Lane 0: bulk copies of local chunk lt of species s of simulation k into a stage buffer.
+__device__ __forceinline__ void issue_chunk(const BatchStep32& B, int s, int k, unsigned lt, unsigned char* buf,
+                                            unsigned long long* bar) {
+  const unsigned nk = B.ncur[s][k];
+  const unsigned i0 = lt * CHUNK;
+  const unsigned n = min((unsigned)CHUNK, nk - i0);  // multiple of 4
+  stage_issue_span(B.sp[s], B.hot[k].seg[s] + i0, n, buf, bar);
+}
+
+// The warp leaves simulation k: its queued collisions, the kinetic energy of its particles of
+// species s and its counters go to the simulation; the counters restart from zero.
+__device__ __forceinline__ void leave_sim(const BatchStep32& B, int k, int s, const unsigned long long* q, int qn,
+                                          BlockCounters& wc, unsigned long long ke, bool run_queue) {
+  const int lane = threadIdx.x & 31;
+  if (run_queue && qn) flush_queue(B.sims[k], q, qn, B.ncur[0][k], B.ncur[1][k], &wc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xFFFFFFFFu, ke, o);
+  if (lane == 0 && ke) atomicAdd(&wc.ke[s], ke);
+  __syncwarp();
+  if (lane < 16) counters_to_ctl(B.sims[k].ctl, B.ph, wc, lane);
+  __syncwarp();
+  if (lane < (int)(sizeof(BlockCounters) / 4)) reinterpret_cast<unsigned int*>(&wc)[lane] = 0u;
+  __syncwarp();
+}
+
+template <int TPB, int MINB, int NST>
+__global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ BatchStep32 B) {
+  constexpr int WARPS = TPB / 32;
+  static_assert(sizeof(BlockCounters) / 4 <= 32, "one word of the counters per lane");
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ BlockCounters wcs[WARPS];
+  __shared__ WarpSim wsm[WARPS];
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wib = tid >> 5;
+  unsigned char* const stage = dsm + (size_t)wib * NST * STAGE_BYTES;
+  unsigned long long* const q =
+      reinterpret_cast<unsigned long long*>(dsm + (size_t)WARPS * NST * STAGE_BYTES) + (size_t)wib * QCAP;
+  unsigned long long* const bar = reinterpret_cast<unsigned long long*>(
+                                      dsm + (size_t)WARPS * (NST * STAGE_BYTES + QCAP * 8)) + wib * NST;
+  BlockCounters& wc = wcs[wib];
+  if (lane < (int)(sizeof(BlockCounters) / 4)) reinterpret_cast<unsigned int*>(&wc)[lane] = 0u;
+  if (lane < NST) mbar_init(bar + lane, 1u);
+  mbar_init_fence();
+  __syncthreads();
+
+  const unsigned below = (1u << lane) - 1u;
+  const Phys& ph = B.ph;
+  const int nsims = B.nsims;
+  const unsigned long long step = B.dev->step;
+  const unsigned gw = blockIdx.x * WARPS + wib;
+  const unsigned nw = gridDim.x * WARPS;
+  int qn = 0;            // warp-uniform
+  unsigned parity = 0u;  // bit st: phase parity of stage st
+  bool failed = false;   // a bounded wait gave up
+
+#pragma unroll 1
+  for (int s = 0; s < 2 && !failed; ++s) {
+    const unsigned* __restrict__ pre = B.pre[s];
+    const unsigned total = pre[nsims];
+    const unsigned per = (total + nw - 1) / nw;
+    const unsigned t0 = min(total, gw * per);
+    const unsigned t1 = min(total, t0 + per);
+    if (t0 >= t1) continue;
+    const Species32& A = B.sp[s];
+    const SpConst& K = ph.sp[s];
+    const bool moves = (ph.push_mask >> s) & 1u;
+    const unsigned long long tag = (unsigned long long)s << 63;
+    const int kfirst = owner(pre, nsims, t0);
+
+    // prologue: the warp's first NST chunks
+    if (lane == 0) {
+      int ki = kfirst;
+#pragma unroll
+      for (int st = 0; st < NST; ++st) {
+        const unsigned t = t0 + st;
+        if (t < t1) {
+          while (pre[ki + 1] <= t) ++ki;
+          issue_chunk(B, s, ki, t - pre[ki], stage + st * STAGE_BYTES, bar + st);
+        }
+      }
+    }
+    // the simulation being processed (warp-uniform); kend == 0 until the first one is entered.
+    // pnull == 0: the species does not collide in this simulation (no draw is made).
+    int kc = kfirst;
+    unsigned kbeg = 0u, kend = 0u;
+    WarpSim& ws = wsm[wib];
+    unsigned long long ke_lane = 0ull;  // kinetic energy of this lane's particles that stay live
+    int st = 0;
+#pragma unroll 1
+    for (unsigned t = t0; t < t1; ++t) {
+      if (t >= kend) {  // first chunk of another simulation
+        if (kend) {
+          leave_sim(B, kc, s, q, qn, wc, ke_lane, true);
+          qn = 0;
+          ke_lane = 0ull;
+        }
+        while (pre[kc + 1] <= t) ++kc;
+        kbeg = pre[kc];
+        kend = pre[kc + 1];
+        if (lane == 0) {
+          const BSim& h = B.hot[kc];
+          ws.seg = h.seg[s];
+          ws.nk = B.ncur[s][kc];
+          ws.pnull = moves && ((h.collides >> s) & 1u) ? h.p_null_u24[s] : 0u;
+          ws.cbase = h.cbase;
+          ws.N = h.N;
+          ws.seed = h.seed;
+        }
+        __syncwarp();
+      }
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait_bounded(bar + st, (parity >> st) & 1u))) {
+        failed = true;
+        break;
+      }
+      parity ^= 1u << st;
+      const unsigned char* const buf = stage + st * STAGE_BYTES;
+      const unsigned i0 = (t - kbeg) * CHUNK + lane * PIC_PPT;  // index in the simulation's segment
+      int c[PIC_PPT];
+      float f[PIC_PPT], vx[PIC_PPT], vy[PIC_PPT], vz[PIC_PPT];
+      unsigned long long id[PIC_PPT];
+      const bool have = i0 < ws.nk;
+      {
+        const int4 c4 = reinterpret_cast<const int4*>(buf)[lane];
+        const float4 f4 = reinterpret_cast<const float4*>(buf + CHUNK * 4)[lane];
+        const float4 x4 = reinterpret_cast<const float4*>(buf + CHUNK * 8)[lane];
+        const float4 y4 = reinterpret_cast<const float4*>(buf + CHUNK * 12)[lane];
+        const float4 z4 = reinterpret_cast<const float4*>(buf + CHUNK * 16)[lane];
+        const ulonglong2 id01 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane];
+        const ulonglong2 id23 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane + 1];
+        c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+        f[0] = f4.x; f[1] = f4.y; f[2] = f4.z; f[3] = f4.w;
+        vx[0] = x4.x; vx[1] = x4.y; vx[2] = x4.z; vx[3] = x4.w;
+        vy[0] = y4.x; vy[1] = y4.y; vy[2] = y4.z; vy[3] = y4.w;
+        vz[0] = z4.x; vz[1] = z4.y; vz[2] = z4.z; vz[3] = z4.w;
+        id[0] = id01.x; id[1] = id01.y; id[2] = id23.x; id[3] = id23.y;
+      }
+      if (!have) {
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          c[k] = PIC_DEAD_CELL;
+          id[k] = 0ull;
+        }
+      }
+      float2 e2[PIC_PPT];
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k) {
+        e2[k] = make_float2(0.f, 0.f);
+        if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL) e2[k] = __ldg(B.E2 + (ws.cbase + c[k]));
+      }
+      // the stage is read: refill it with the chunk NST steps ahead
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        const unsigned tn = t + NST;
+        if (tn < t1) {
+          int ki = kc;  // owner of chunk tn: this simulation or a later one
+          while (pre[ki + 1] <= tn) ++ki;
+          issue_chunk(B, s, ki, tn - pre[ki], stage + st * STAGE_BYTES, bar + st);
+        }
+      }
+      st = st + 1 == NST ? 0 : st + 1;
+
+      unsigned cand = 0u;
+      const unsigned pnull = ws.pnull;
+      if (pnull) {
+        const unsigned long long seed = ws.seed;
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          const uint4 w = draw4(id[k], seed, step, CH_COLL, 0u);
+          if ((w.x >> 8) < pnull) cand |= 1u << k;
+        }
+      }
+      const int N = ws.N;
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k) {
+        if (c[k] == PIC_DEAD_CELL) continue;
+        if (moves) {
+          const int cn = push_one(ph, K, e2[k], c[k], f[k], vx[k], vy[k], vz[k]);
+          if ((unsigned)cn >= (unsigned)N) {  // absorbed at a wall
+            const int side = cn < 0 ? 0 : 1;
+            atomicAdd(&wc.hits[s][side], 1u);
+            atomicAdd(&wc.lost[s], 1u);
+            const float e = 0.5f * K.mass * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
+            atomicAdd(&wc.efx[s], (unsigned long long)__double2ull_rn((double)e * 16777216.0));
+            c[k] = PIC_DEAD_CELL;
+            continue;
+          }
+          c[k] = cn;
+        }
+      }
+      if (have && moves) {
+        const unsigned g = ws.seg + i0;
+        *reinterpret_cast<int4*>(A.cell + g) = make_int4(c[0], c[1], c[2], c[3]);
+        *reinterpret_cast<float4*>(A.frac + g) = make_float4(f[0], f[1], f[2], f[3]);
+        *reinterpret_cast<float4*>(A.vx + g) = make_float4(vx[0], vx[1], vx[2], vx[3]);
+        *reinterpret_cast<float4*>(A.vy + g) = make_float4(vy[0], vy[1], vy[2], vy[3]);
+        *reinterpret_cast<float4*>(A.vz + g) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+      }
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k)
+        if (c[k] != PIC_DEAD_CELL && !((cand >> k) & 1u)) ke_lane += ke_fx32(vx[k], vy[k], vz[k], K.mass);
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k) {
+        const bool qk = ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL;
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, qk);
+        if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(i0 + k);
+        qn += __popc(b);
+      }
+
+      unsigned rn[PIC_PPT];
+      unsigned long long rsw[PIC_PPT];
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k) {
+        const bool live = c[k] != PIC_DEAD_CELL;
+        rn[k] = live ? 1u : 0u;
+        rsw[k] = live ? (unsigned long long)wr_of(f[k]) : 0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k) {
+#pragma unroll
+        for (int j = k + 1; j < PIC_PPT; ++j) {
+          if (rn[k] && rn[j] && c[j] == c[k]) {
+            rn[k] += rn[j];
+            rsw[k] += rsw[j];
+            rn[j] = 0u;
+          }
+        }
+      }
+      const int cbase = ws.cbase;
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k)
+        warp_deposit(B.cnt[s], B.S[s], rn[k] ? cbase + c[k] : -1, rn[k], rsw[k]);
+
+      if (qn > QFLUSH) {
+        flush_queue(B.sims[kc], q, qn, B.ncur[0][kc], B.ncur[1][kc], &wc);
+        qn = 0;
+      }
+    }
+    if (failed) {
+      // a stage never completed: report, give the copies in flight a bounded chance to land
+      // before this CTA's shared memory is released, and hand over the counters (not the queue)
+      if (lane == 0) {
+        atomicOr(&B.dev->error, ERR_TIMEOUT);
+        atomicOr(&B.sims[kc].ctl->error, ERR_TIMEOUT);
+      }
+      for (int k = 0; k < NST; ++k) mbar_wait_bounded(bar + k, (parity >> k) & 1u);
+      if (kend) leave_sim(B, kc, s, q, 0, wc, 0ull, false);
+    } else if (kend) {
+      leave_sim(B, kc, s, q, qn, wc, ke_lane, true);
+      qn = 0;
+    }
+  }
+}
+
+// ---- plan: extents, chunk and tile prefixes, error bits, step counter (one CTA of 1024) ------
+constexpr int PLAN_TPB = 1024;
+
+__device__ __forceinline__ void block_excl_scan2(unsigned& a, unsigned& b, unsigned* wa, unsigned* wb,
+                                                 unsigned& tot_a, unsigned& tot_b) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  unsigned ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned ua = __shfl_up_sync(0xFFFFFFFFu, ia, o), ub = __shfl_up_sync(0xFFFFFFFFu, ib, o);
+    if (lane >= o) {
+      ia += ua;
+      ib += ub;
+    }
+  }
+  if (lane == 31) {
+    wa[w] = ia;
+    wb[w] = ib;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    unsigned va = wa[tid], vb = wb[tid];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned ua = __shfl_up_sync(0xFFFFFFFFu, va, o), ub = __shfl_up_sync(0xFFFFFFFFu, vb, o);
+      if (lane >= o) {
+        va += ua;
+        vb += ub;
+      }
+    }
+    wa[tid] = va;  // inclusive over warps
+    wb[tid] = vb;
+  }
+  __syncthreads();
+  const unsigned ea = (w ? wa[w - 1] : 0u) + ia - a, eb = (w ? wb[w - 1] : 0u) + ib - b;
+  tot_a = wa[31];
+  tot_b = wb[31];
+  __syncthreads();  // the warp totals are reused by the next scan
+  a = ea;
+  b = eb;
+}
+
+__global__ void __launch_bounds__(PLAN_TPB) k_bplan(const BatchPlan P) {
+  __shared__ unsigned wa[32], wb[32];
+  __shared__ unsigned err_s;
+  __shared__ unsigned long long step_s;
+  const int tid = threadIdx.x;
+  const int n = P.nsims;
+  const int per = (n + PLAN_TPB - 1) / PLAN_TPB;  // at most PIC_BATCH_MAX / PLAN_TPB = 4
+  const int k0 = tid * per;
+  if (tid == 0) {
+    err_s = 0u;
+    step_s = P.dev->step + (P.advance ? 1ull : 0ull);
+  }
+  __syncthreads();
+  unsigned err = 0u;
+#pragma unroll 1
+  for (int s = 0; s < 2; ++s) {
+    unsigned ext[PIC_BATCH_MAX / PLAN_TPB];
+    unsigned chunks = 0u, tiles = 0u;
+#pragma unroll
+    for (int i = 0; i < PIC_BATCH_MAX / PLAN_TPB; ++i) {
+      ext[i] = 0u;
+      const int k = k0 + i;
+      if (i < per && k < n) {
+        const Ctl* g = P.sims[0][k].ctl;
+        ext[i] = (unsigned)g->n_cur[s];
+        if (s == 0) err |= g->error;
+        chunks += (ext[i] + 32u * PIC_PPT - 1u) / (32u * PIC_PPT);
+        tiles += (ext[i] + PIC_TILE - 1u) / PIC_TILE;
+      }
+    }
+    unsigned tot_c, tot_t;
+    block_excl_scan2(chunks, tiles, wa, wb, tot_c, tot_t);
+#pragma unroll
+    for (int i = 0; i < PIC_BATCH_MAX / PLAN_TPB; ++i) {
+      const int k = k0 + i;
+      if (i < per && k < n) {
+        P.pre[s][k] = chunks;
+        P.tpre[s][k] = tiles;
+        P.ncur[s][k] = ext[i];
+        chunks += (ext[i] + 32u * PIC_PPT - 1u) / (32u * PIC_PPT);
+        tiles += (ext[i] + PIC_TILE - 1u) / PIC_TILE;
+      }
+    }
+    if (tid == 0) {
+      P.pre[s][n] = tot_c;
+      P.tpre[s][n] = tot_t;
+    }
+  }
+  if (err) atomicOr(&err_s, err);
+  for (int k = tid; k < n; k += PLAN_TPB) {
+    P.sims[0][k].step = step_s;
+    P.sims[1][k].step = step_s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    P.dev->step = step_s;
+    if (err_s) P.dev->error |= err_s;
+  }
+}
+
+template <int TPB, int MINB, int NST>
+cudaError_t launch_variant(const BatchStep32& p, int grid, cudaStream_t st) {
+  constexpr size_t smem = BShape<TPB, NST>::SMEM;
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done = true;
+  }
+  k_bstep32<TPB, MINB, NST><<<grid, TPB, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int TPB, int MINB, int NST>
+int occupancy_variant() {
+  constexpr size_t smem = BShape<TPB, NST>::SMEM;
+  cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bstep32<TPB, MINB, NST>, TPB, smem) != cudaSuccess || b < 1)
+    b = 1;
+  return b;
+}
+
+struct Variant {
+  const char* name;
+  cudaError_t (*launch)(const BatchStep32&, int, cudaStream_t);
+  int (*occupancy)();
+};
+
+// (threads per CTA, CTAs per SM the registers are budgeted for, TMA stages per warp)
+const Variant kVariants[] = {
+    {"tpb256_minb3_stages2", launch_variant<256, 3, 2>, occupancy_variant<256, 3, 2>},
+    {"tpb128_minb6_stages2", launch_variant<128, 6, 2>, occupancy_variant<128, 6, 2>},
+    {"tpb256_minb2_stages3", launch_variant<256, 2, 3>, occupancy_variant<256, 2, 3>},
+    {"tpb384_minb2_stages2", launch_variant<384, 2, 2>, occupancy_variant<384, 2, 2>},
+};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+
+}  // namespace
+
+int bstep32_variants() { return kNumVariants; }
+
+const char* bstep32_variant_name(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].name : nullptr; }
+
+int bstep32_occupancy(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].occupancy() : 0; }
+
+cudaError_t launch_bstep32(int v, const BatchStep32& p, int grid, cudaStream_t st) {
+  if (v < 0 || v >= kNumVariants || grid < 1) return cudaErrorInvalidValue;
+  return kVariants[v].launch(p, grid, st);
+}
+
+cudaError_t launch_bplan(const BatchPlan& p, cudaStream_t st) {
+  if (p.nsims < 1 || p.nsims > PIC_BATCH_MAX) return cudaErrorInvalidValue;
+  k_bplan<<<1, PLAN_TPB, 0, st>>>(p);
+  return cudaGetLastError();
+}

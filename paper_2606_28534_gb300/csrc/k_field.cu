@@ -29,6 +29,8 @@
 // the Green's-function formula above in FP64 with two prefix scans.
 #include <cooperative_groups.h>
 
+#include <cstring>
+
 #include "pic_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -102,8 +104,11 @@ __device__ void bookkeeping(const PoissonParams& P) {
 }
 
 // =============================================================================================
+// BATCH: cluster k of the grid solves simulation k of an ensemble, with the parameters tab[k].
+template <bool BATCH>
 __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIELD_TPB, 1)
-    k_field_exact(const __grid_constant__ PoissonParams P) {
+    k_field_exact(const __grid_constant__ PoissonParams P0, const PoissonParams* __restrict__ tab) {
+  const PoissonParams& P = BATCH ? tab[blockIdx.x / PIC_FIELD_CTAS] : P0;
   extern __shared__ long long Rn[];  // r_j of this CTA's segment, then E_j (as double bits)
   __shared__ __int128 warp_q[PIC_FIELD_TPB / 32], warp_p[PIC_FIELD_TPB / 32];
   __shared__ __int128 cta_q, cta_p;  // read by the other CTAs of the cluster
@@ -400,24 +405,29 @@ void set_smem(K kernel, int bytes) {
 
 }  // namespace
 
-cudaError_t launch_field(const PoissonParams& p, cudaStream_t st) {
-  if (p.N < 2 || p.N > PIC_MAX_CELLS_FP32) return cudaErrorInvalidValue;
-  const int seg = (p.N + 1 + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
-  const size_t smem = sizeof(double) * (size_t)seg;
+static void field_attrs() {
   static bool attr_set = false;
   if (!attr_set) {
     const int maxs = (int)(sizeof(double) * PIC_FIELD_SEG_MAX);
-    set_smem(k_field_exact, maxs);
+    set_smem(k_field_exact<false>, maxs);
+    set_smem(k_field_exact<true>, maxs);
     set_smem(k_field_fp64<0>, maxs);
     set_smem(k_field_fp64<1>, maxs);
     set_smem(k_field_fp64<2>, maxs);
     set_smem(k_field_fp64<3>, maxs);
     attr_set = true;
   }
+}
+
+cudaError_t launch_field(const PoissonParams& p, cudaStream_t st) {
+  if (p.N < 2 || p.N > PIC_MAX_CELLS_FP32) return cudaErrorInvalidValue;
+  const int seg = (p.N + 1 + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
+  const size_t smem = sizeof(double) * (size_t)seg;
+  field_attrs();
   switch (p.mode) {
     case 0:
       if (p.exact)
-        k_field_exact<<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p);
+        k_field_exact<false><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p, nullptr);
       else
         k_field_fp64<0><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p);
       break;
@@ -426,5 +436,17 @@ cudaError_t launch_field(const PoissonParams& p, cudaStream_t st) {
     case 3: k_field_fp64<3><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// Integer-exact field of every simulation of an ensemble: one cluster per simulation, parameters
+// tab[k] in device memory (their ctl, counts and arrays point into the batch's arrays).
+cudaError_t launch_field_batch(const PoissonParams* tab, int nsims, int maxN, cudaStream_t st) {
+  if (nsims < 1 || nsims > PIC_BATCH_MAX || maxN < 2 || maxN > PIC_MAX_CELLS_FP32) return cudaErrorInvalidValue;
+  const int seg = (maxN + 1 + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
+  field_attrs();
+  PoissonParams unused;
+  memset(&unused, 0, sizeof(unused));
+  k_field_exact<true><<<nsims * PIC_FIELD_CTAS, PIC_FIELD_TPB, sizeof(double) * (size_t)seg, st>>>(unused, tab);
   return cudaGetLastError();
 }

@@ -17,31 +17,28 @@
 // as a set of particles is reproducible, and snapshots are written in id order.
 #include <cooperative_groups.h>
 
+#include <cstring>
+
 #include "pic_internal.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace {
 
-struct SortParams {
-  Species32 src[2], dst[2];
-  unsigned int* cnt[2];
-  unsigned int* cursor[2];
-  unsigned long long cap[2];
-  Ctl* ctl;
-  int N;
-};
-
 // One cluster of PIC_FIELD_CTAS CTAs per species: each CTA stages a contiguous segment of the
 // counts in shared memory (coalesced), scans runs of consecutive cells per thread, and takes its
 // offset from the CTA totals of the lower ranks through distributed shared memory.
+// BATCH: clusters 2k and 2k + 1 scan species 0 and 1 of simulation k of an ensemble, with the
+// parameters tab[k].
+template <bool BATCH>
 __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(1024, 1)
-    k_sort_scan(const __grid_constant__ SortParams P) {
+    k_sort_scan(const __grid_constant__ SortParams P0, const SortParams* __restrict__ tab) {
   extern __shared__ unsigned int cs[];
   __shared__ unsigned long long warp_tot[32];
   __shared__ unsigned long long cta_tot;
   cg::cluster_group cluster = cg::this_cluster();
-  const int s = (int)(blockIdx.x / PIC_FIELD_CTAS);
+  const SortParams& P = BATCH ? tab[blockIdx.x / (2 * PIC_FIELD_CTAS)] : P0;
+  const int s = BATCH ? (int)((blockIdx.x / PIC_FIELD_CTAS) & 1u) : (int)(blockIdx.x / PIC_FIELD_CTAS);
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int N = P.N;
@@ -187,7 +184,64 @@ __global__ void __launch_bounds__(PIC_TPB) k_sort_scatter(const SortParams P) {
   }
 }
 
+// Scatter of an ensemble: the tiles of every simulation (tile prefix tpre_s over the simulations,
+// extents ncur_s as they were when the prefix was formed, which is the extent the scan recorded),
+// both species, strided over the grid.
+__global__ void __launch_bounds__(PIC_TPB) k_bsort_scatter(const SortParams* __restrict__ tab,
+                                                         const unsigned* __restrict__ tpre0,
+                                                         const unsigned* __restrict__ tpre1,
+                                                         const unsigned* __restrict__ ncur0,
+                                                         const unsigned* __restrict__ ncur1, int nsims) {
+  const unsigned tiles0 = tpre0[nsims];
+  const unsigned tiles = tiles0 + tpre1[nsims];
+  for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int s = t >= tiles0 ? 1 : 0;
+    const unsigned tt = s ? t - tiles0 : t;
+    const unsigned* pre = s ? tpre1 : tpre0;
+    int lo = 0, hi = nsims;  // last k with pre[k] <= tt (the first such k with a tile)
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pre[mid] <= tt) lo = mid; else hi = mid;
+    }
+    while (pre[lo + 1] <= tt) ++lo;  // skip simulations without particles
+    const SortParams& P = tab[lo];
+    const unsigned long long i0 =
+        (unsigned long long)(tt - pre[lo]) * PIC_TILE + (unsigned long long)threadIdx.x * PIC_PPT;
+    const unsigned n = s ? ncur1[lo] : ncur0[lo];
+    if (s == 0)
+      scatter_tile<0>(P, i0, i0 < n);
+    else
+      scatter_tile<1>(P, i0, i0 < n);
+  }
+}
+
+void scan_attrs() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_sort_scan<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(unsigned int) * PIC_FIELD_SEG_MAX));
+    cudaFuncSetAttribute(k_sort_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(unsigned int) * PIC_FIELD_SEG_MAX));
+    attr_set = true;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sort_batch(const SortParams* tab, const unsigned* tpre0, const unsigned* tpre1,
+                              const unsigned* ncur0, const unsigned* ncur1, int nsims, int maxN, int grid,
+                              cudaStream_t st) {
+  if (nsims < 1 || nsims > PIC_BATCH_MAX || maxN < 2 || maxN > PIC_MAX_CELLS_FP32) return cudaErrorInvalidValue;
+  scan_attrs();
+  const int seg = (maxN + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
+  SortParams unused;
+  memset(&unused, 0, sizeof(unused));
+  k_sort_scan<true><<<2 * nsims * PIC_FIELD_CTAS, 1024, sizeof(unsigned int) * (size_t)seg, st>>>(unused, tab);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_bsort_scatter<<<grid, PIC_TPB, 0, st>>>(tab, tpre0, tpre1, ncur0, ncur1, nsims);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sort32(Species32 src[2], Species32 dst[2], unsigned int* cnt[2],
                           unsigned int* cursor[2], const unsigned long long cap[2], Ctl* ctl, int N,
@@ -203,13 +257,8 @@ cudaError_t launch_sort32(Species32 src[2], Species32 dst[2], unsigned int* cnt[
   P.ctl = ctl;
   P.N = N;
   const int seg = (N + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_sort_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(unsigned int) * PIC_FIELD_SEG_MAX));
-    attr_set = true;
-  }
-  k_sort_scan<<<2 * PIC_FIELD_CTAS, 1024, sizeof(unsigned int) * (size_t)seg, st>>>(P);
+  scan_attrs();
+  k_sort_scan<false><<<2 * PIC_FIELD_CTAS, 1024, sizeof(unsigned int) * (size_t)seg, st>>>(P, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sort_scatter<<<grid, PIC_TPB, 0, st>>>(P);

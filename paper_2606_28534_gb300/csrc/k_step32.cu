@@ -16,275 +16,13 @@
 //            W_r, aggregated over the lanes of a warp that share a cell (redux.sync) and added
 //            to global memory with one reduction per (warp, cell).  Node deposits follow as
 //            R_j = 2^32 cnt_j - S_j + S_{j-1} in the field kernel.
-#include "pic_internal.cuh"
+#include "step32_common.cuh"
 
 namespace {
 
-struct BlockCounters {
-  unsigned int hits[2][2];
-  unsigned int coll[5];
-  unsigned int near_thr[2];
-  unsigned int viol[2];
-  unsigned int lost[2];
-  unsigned int born[2];
-  unsigned long long efx[2];
-  unsigned long long ke[2];  // kinetic energy (ke_fx32) of particles handled out of the hot loop
-};
-
-__device__ __forceinline__ void iso_dir_f(unsigned wa, unsigned wb, float& dx, float& dy, float& dz) {
-  float ua = u01f(wa), ub = u01f(wb);
-  float ct = 1.f - 2.f * ua;
-  float st = 2.f * sqrtf(ua * (1.f - ua));
-  float sp, cp;
-  sincospif(2.f * ub, &sp, &cp);
-  dx = st * cp;
-  dy = st * sp;
-  dz = ct;
-}
-
-__device__ __forceinline__ void box_muller_f(unsigned wa, unsigned wb, float& n0, float& n1) {
-  float r = sqrtf(-2.f * logf(1.f - u01f(wa)));
-  float s, c;
-  sincospif(2.f * u01f(wb), &s, &c);
-  n0 = r * c;
-  n1 = r * s;
-}
-
-// Interpolation (e = node pair of the cell) + Boris + move.  Returns the new cell (may be outside
-// [0, N): absorbed).
-__device__ __forceinline__ int push_one(const Phys& ph, const SpConst& k, float2 e, int c, float& f, float& vx,
-                                        float& vy, float& vz) {
-  float E = 0.f;
-  if (ph.field_mode == 0u) {
-    E = (1.f - f) * e.x + f * e.y;
-  } else if (ph.field_mode == 1u) {
-    E = ph.E_ext;
-  }
-  float a = k.qmdt2 * E;
-  float mx = vx + a, my = vy, mz = vz;
-  if (ph.has_B) {
-    float px = mx + (my * k.t[2] - mz * k.t[1]);
-    float py = my + (mz * k.t[0] - mx * k.t[2]);
-    float pz = mz + (mx * k.t[1] - my * k.t[0]);
-    mx += py * k.s[2] - pz * k.s[1];
-    my += pz * k.s[0] - px * k.s[2];
-    mz += px * k.s[1] - py * k.s[0];
-  }
-  vx = mx + a;
-  vy = my;
-  vz = mz;
-  float fn = f + vx * ph.dtdx;
-  float fl = floorf(fn);
-  f = fn - fl;
-  int cn = c + (int)fl;
-  if (f >= 1.f) {  // fn slightly below an integer: the fraction rounds up to 1
-    f = 0.f;
-    cn += 1;
-  }
-  return cn;
-}
-
-__device__ __forceinline__ unsigned wr_of(float f) {
-  // f in [0, 1): f * 2^32 is exact in FP32 and below 2^32 - 255
-  return __float2uint_rn(f * 4294967296.0f);
-}
-
-// Append one particle past the end of species s; returns false (and counts a drop) when full.
-template <int s>
-__device__ __forceinline__ bool append32(const StepParams32& P, unsigned long long ncur, int c, float f,
-                                         const float* v, unsigned long long id) {
-  unsigned long long slot = ncur + atomicAdd(&P.ctl->n_born[s], 1ull);
-  if (slot >= P.cap[s]) {
-    atomicAdd(&P.ctl->dropped, 1ull);
-    atomicOr(&P.ctl->error, ERR_OVERFLOW);
-    return false;
-  }
-  const Species32& a = P.sp[s];
-  a.cell[slot] = c;
-  a.frac[slot] = f;
-  a.vx[slot] = v[0];
-  a.vy[slot] = v[1];
-  a.vz[slot] = v[2];
-  a.id[slot] = id;
-  return true;
-}
-
-// Collision of a null-collision candidate electron (P_null test already passed): selects elastic,
-// excitation, ionization or null against u1 nu_max; ionization appends the new (e, ion) pair at
-// the parent's position and deposits it.  Returns the new velocity.
-__device__ __forceinline__ float4 collide_electron(const StepParams32& P, unsigned long long ncur0,
-                                                unsigned long long ncur1, unsigned long long id, int c,
-                                                float f, float vx, float vy, float vz, BlockCounters* bc) {
-  const Phys& ph = P.ph;
-  const SpConst& k = ph.sp[0];
-  const unsigned long long step = P.step;
-  uint4 w = draw4(id, ph.seed, step, CH_COLL, 0u);
-  atomicAdd(&bc->coll[4], 1u);
-  float v2 = vx * vx + vy * vy + vz * vz;
-  float speed = sqrtf(v2);
-  float En = 0.5f * k.mass * v2;
-  float nu_el = (ph.coll_mask & 1u) ? ph.ngs_el * speed : 0.f;
-  float nu_ex = 0.f, nu_iz = 0.f;
-  if ((ph.coll_mask & 2u) && En > ph.E_ex) nu_ex = ph.ngs_ex * fminf((En - ph.E_ex) * ph.inv_E_ex, 1.f) * speed;
-  if ((ph.coll_mask & 4u) && En > ph.E_iz) nu_iz = ph.ngs_iz * fminf((En - ph.E_iz) * ph.inv_E_iz, 1.f) * speed;
-  float b1 = nu_el, b2 = b1 + nu_ex, b3 = b2 + nu_iz;
-  if (b3 > k.nu_max) atomicAdd(&bc->viol[0], 1u);
-  float r = u01f(w.y) * k.nu_max;
-  float tol = 1e-5f * k.nu_max;
-  bool near = fabsf(r - b1) < tol || fabsf(r - b2) < tol || fabsf(r - b3) < tol;
-  if ((ph.coll_mask & 2u) && fabsf(En - ph.E_ex) < 1e-5f * ph.E_ex) near = true;
-  if ((ph.coll_mask & 4u) && fabsf(En - ph.E_iz) < 1e-5f * ph.E_iz) near = true;
-  if (near) atomicAdd(&bc->near_thr[0], 1u);
-  if (!(r < b3)) return make_float4(vx, vy, vz, 1.f);
-  float dx, dy, dz;
-  iso_dir_f(w.z, w.w, dx, dy, dz);
-  if (r < b1) {  // elastic, energy loss (2m/M)(1 - cos chi)
-    float cchi = (vx * dx + vy * dy + vz * dz) / speed;
-    float sp2 = speed * sqrtf(1.f - ph.two_m_over_M * (1.f - cchi));
-    atomicAdd(&bc->coll[0], 1u);
-    return make_float4(sp2 * dx, sp2 * dy, sp2 * dz, 1.f);
-  }
-  if (r < b2) {  // excitation, loses E_ex
-    float sp2 = sqrtf(2.f * (En - ph.E_ex) / k.mass);
-    atomicAdd(&bc->coll[1], 1u);
-    return make_float4(sp2 * dx, sp2 * dy, sp2 * dz, 1.f);
-  }
-  // ionization: E - E_iz split uniformly; new ion Maxwellian at T_g
-  uint4 a = draw4(id, ph.seed, step, CH_SCAT, 0u);
-  uint4 b = draw4(id, ph.seed, step, CH_SCAT, 1u);
-  uint4 kk = draw4(id, ph.seed, step, CH_CHILD, 0u);
-  float Er = En - ph.E_iz;
-  float Es = u01f(a.x) * Er;
-  float Ep = Er - Es;
-  float spp = sqrtf(2.f * Ep / k.mass), sps = sqrtf(2.f * Es / k.mass);
-  float d2x, d2y, d2z;
-  iso_dir_f(a.y, a.z, d2x, d2y, d2z);
-  float ce[3] = {sps * d2x, sps * d2y, sps * d2z};
-  float n0, n1, n2, n3;
-  box_muller_f(b.x, b.y, n0, n1);
-  box_muller_f(b.z, b.w, n2, n3);
-  float ci[3] = {ph.vt_gas * n0, ph.vt_gas * n1, ph.vt_gas * n2};
-  atomicAdd(&bc->coll[2], 1u);
-  const unsigned long long wr = wr_of(f);
-  if (append32<0>(P, ncur0, c, f, ce, (unsigned long long)kk.x | ((unsigned long long)kk.y << 32))) {
-    atomicAdd(P.cnt[0] + c, 1u);
-    atomicAdd(P.S[0] + c, wr);
-    atomicAdd(&bc->born[0], 1u);
-    atomicAdd(&bc->ke[0], ke_fx32(ce[0], ce[1], ce[2], ph.sp[0].mass));
-  }
-  if (append32<1>(P, ncur1, c, f, ci, (unsigned long long)kk.z | ((unsigned long long)kk.w << 32))) {
-    atomicAdd(P.cnt[1] + c, 1u);
-    atomicAdd(P.S[1] + c, wr);
-    atomicAdd(&bc->born[1], 1u);
-    atomicAdd(&bc->ke[1], ke_fx32(ci[0], ci[1], ci[2], ph.sp[1].mass));
-  }
-  return make_float4(spp * dx, spp * dy, spp * dz, 1.f);
-}
-
-// Charge exchange of a candidate ion: the ion leaves with a Maxwellian velocity at T_g.
-__device__ __forceinline__ float4 collide_ion(const Phys& ph, unsigned long long id, unsigned long long step,
-                                           float vx, float vy, float vz, BlockCounters* bc) {
-  const SpConst& k = ph.sp[1];
-  uint4 w = draw4(id, ph.seed, step, CH_COLL, 0u);
-  atomicAdd(&bc->coll[4], 1u);
-  float speed = sqrtf(vx * vx + vy * vy + vz * vz);
-  float b1 = ph.ngs_cx * speed;
-  if (b1 > k.nu_max) atomicAdd(&bc->viol[1], 1u);
-  float r = u01f(w.y) * k.nu_max;
-  if (fabsf(r - b1) < 1e-5f * k.nu_max) atomicAdd(&bc->near_thr[1], 1u);
-  if (r < b1) {
-    uint4 a = draw4(id, ph.seed, step, CH_SCAT, 0u);
-    float n0, n1, n2, n3;
-    box_muller_f(w.z, w.w, n0, n1);
-    box_muller_f(a.x, a.y, n2, n3);
-    atomicAdd(&bc->coll[3], 1u);
-    return make_float4(ph.vt_gas * n0, ph.vt_gas * n1, ph.vt_gas * n2, 1.f);
-  }
-  return make_float4(vx, vy, vz, 1.f);
-}
-
-// Deposit of one warp's runs of equal cells: lanes holding the same cell combine their counts
-// and right-weight sums with redux.sync, and one lane issues the global reduction.  Up to two
-// distinct cells per run slot are aggregated (a sorted warp spans one or two cells); remaining
-// lanes (sparse regions) reduce individually.  Sums stay exact: sw < 2^35, split at bit 20 so that
-// each 32-lane 32-bit sum cannot wrap.
-__device__ __forceinline__ void warp_deposit(unsigned int* __restrict__ gcnt, unsigned long long* __restrict__ gS,
-                                             int key, unsigned n, unsigned long long sw) {
-  const int lane = threadIdx.x & 31;
-  unsigned active = __ballot_sync(0xFFFFFFFFu, key >= 0);
-#pragma unroll 1
-  for (int it = 0; it < 2 && active; ++it) {
-    const int leader = __ffs(active) - 1;
-    const int kc = __shfl_sync(0xFFFFFFFFu, key, leader);
-    const bool mine = key == kc;
-    const unsigned n_sum = __reduce_add_sync(0xFFFFFFFFu, mine ? n : 0u);
-    const unsigned lo_sum = __reduce_add_sync(0xFFFFFFFFu, mine ? (unsigned)(sw & 0xFFFFFull) : 0u);
-    const unsigned hi_sum = __reduce_add_sync(0xFFFFFFFFu, mine ? (unsigned)(sw >> 20) : 0u);
-    if (lane == leader) {
-      atomicAdd(gcnt + kc, n_sum);
-      atomicAdd(gS + kc, ((unsigned long long)hi_sum << 20) + (unsigned long long)lo_sum);
-    }
-    if (mine) key = -1;
-    active = __ballot_sync(0xFFFFFFFFu, key >= 0);
-  }
-  if (key >= 0) {
-    atomicAdd(gcnt + key, n);
-    atomicAdd(gS + key, sw);
-  }
-}
-
-constexpr int QCAP = 160;   // per-warp queue of collision candidates
-constexpr int QFLUSH = 32;  // the warp processes its queue once it holds more than this (a
-                            // chunk adds at most 32 * PIC_PPT = 128 entries)
 constexpr int NSTAGE = 2;   // chunks in flight per warp (TMA double buffer)
-constexpr int CHUNK = 32 * PIC_PPT;
-// stage buffer of one chunk: cell | frac | vx | vy | vz (4 B each) | id (8 B)
-constexpr int STAGE_BYTES = CHUNK * (5 * 4 + 8);
 constexpr int WARPS = PIC_TPB / 32;
 constexpr size_t STEP_SMEM = (size_t)WARPS * (NSTAGE * STAGE_BYTES + QCAP * 8 + NSTAGE * 8);
-
-// Collisions of the queued candidates, one per lane: each lane reloads its particle (just written
-// by this warp, so from L2), applies the collision and stores the new velocity.  About one
-// particle in a hundred is a candidate, so this runs every few dozen chunks and keeps the rare
-// code out of the streaming loop.
-__device__ __noinline__ void flush_queue(const StepParams32& P, const unsigned long long* q, int qn,
-                                         unsigned long long ncur0, unsigned long long ncur1, BlockCounters* bc) {
-  __syncwarp();
-  const int lane = threadIdx.x & 31;
-  for (int base = 0; base < qn; base += 32) {
-    const int e = base + lane;
-    if (e >= qn) break;
-    const unsigned long long rec = q[e];
-    const int s = (int)(rec >> 63);
-    const unsigned long long i = rec & 0x7FFFFFFFFFFFFFFFull;
-    const Species32 A = s ? P.sp[1] : P.sp[0];
-    const int c = A.cell[i];
-    const float f = A.frac[i];
-    const unsigned long long id = A.id[i];
-    const float vx = A.vx[i], vy = A.vy[i], vz = A.vz[i];
-    const float4 r = s == 0 ? collide_electron(P, ncur0, ncur1, id, c, f, vx, vy, vz, bc)
-                            : collide_ion(P.ph, id, P.step, vx, vy, vz, bc);
-    A.vx[i] = r.x;
-    A.vy[i] = r.y;
-    A.vz[i] = r.z;
-    atomicAdd(&bc->ke[s], ke_fx32(r.x, r.y, r.z, P.ph.sp[s].mass));
-  }
-  __syncwarp();
-}
-
-// Lane 0 starts the bulk copies of chunk t (ncur particles in the species) into a stage buffer.
-__device__ __forceinline__ void stage_issue(const Species32& A, unsigned t, unsigned ncur, unsigned char* buf,
-                                            unsigned long long* bar) {
-  const unsigned i0 = t * CHUNK;
-  const unsigned n = min((unsigned)CHUNK, ncur - i0);  // multiple of 4
-  mbar_expect_tx(bar, n * 28u);
-  tma_load_1d(buf, A.cell + i0, n * 4u, bar);
-  tma_load_1d(buf + CHUNK * 4, A.frac + i0, n * 4u, bar);
-  tma_load_1d(buf + CHUNK * 8, A.vx + i0, n * 4u, bar);
-  tma_load_1d(buf + CHUNK * 12, A.vy + i0, n * 4u, bar);
-  tma_load_1d(buf + CHUNK * 16, A.vz + i0, n * 4u, bar);
-  tma_load_1d(buf + CHUNK * 20, A.id + i0, n * 8u, bar);
-}
 
 // One warp handles chunks of 32 x PIC_PPT consecutive particles of one species, strided over all
 // warps of the grid; the warp's next chunk is already streaming into shared memory (TMA bulk copy
@@ -479,33 +217,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
 
 // ---- flush the block counters ----------------------------------------------------------------
   __syncthreads();
-  Ctl* g = P.ctl;
-  if (tid < 4) {
-    unsigned v = bc.hits[tid >> 1][tid & 1];
-    if (v) atomicAdd(&g->wall_hits[tid >> 1][tid & 1], (unsigned long long)v);
-  } else if (tid < 9) {
-    unsigned v = bc.coll[tid - 4];
-    if (v) atomicAdd(&g->coll[tid - 4], (unsigned long long)v);
-  } else if (tid < 11) {
-    unsigned v = bc.near_thr[tid - 9];
-    if (v) atomicAdd(&g->near_thr[tid - 9], (unsigned long long)v);
-  } else if (tid < 13) {
-    unsigned v = bc.viol[tid - 11];
-    if (v) atomicAdd(&g->viol[tid - 11], (unsigned long long)v);
-  } else if (tid < 15) {
-    const int s = tid - 13;
-    long long dl = (long long)bc.born[s] - (long long)bc.lost[s];
-    if (dl) atomicAdd(&g->n_live[s], (unsigned long long)dl);
-    if (bc.born[s]) atomicAdd(&g->births[s], (unsigned long long)bc.born[s]);
-    if (bc.efx[s]) atomicAdd(&g->wall_energy_fx[s], bc.efx[s]);
-    if (bc.ke[s]) atomicAdd(&g->ke_acc[s], bc.ke[s]);
-  } else if (tid == 15) {
-    long long qq = 0;
-    for (int s = 0; s < 2; ++s) qq += (long long)ph.sp[s].qsign * (long long)(bc.hits[s][0] + bc.hits[s][1]);
-    if (qq) atomicAdd(reinterpret_cast<unsigned long long*>(&g->wall_charge), (unsigned long long)qq);
-    unsigned ion_lost = bc.hits[1][0] + bc.hits[1][1];
-    if (ion_lost) atomicAdd(&g->src_K, (unsigned long long)ion_lost);
-  }
+  if (tid < 16) counters_to_ctl(P.ctl, ph, bc, tid);
 }
 
 // Pair source (one pair per ion absorbed in this step), uniform in [0, x1), Maxwellian at T_s.

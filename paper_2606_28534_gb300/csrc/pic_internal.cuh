@@ -251,6 +251,65 @@ struct PoissonParams {
   int plain;
 };
 
+struct SortParams {
+  Species32 src[2], dst[2];
+  unsigned int* cnt[2];
+  unsigned int* cursor[2];
+  unsigned long long cap[2];
+  Ctl* ctl;
+  int N;
+};
+
+// ---- ensembles of simulations (one batch: many independent runs advanced together) ----------
+// Every simulation keeps the single-run layout -- its own control block, particle segments,
+// cells and nodes -- inside arrays shared by the batch: the particles of species s of
+// simulation k occupy slots [seg, seg + cap) of the batch's species arrays, its cells
+// [cbase, cbase + N) of the cell arrays and its nodes [nbase, nbase + N + 1) of the node arrays.
+// Cell indices stored with the particles are the simulation's own (0 .. N-1).
+#define PIC_BATCH_MAX 4096  // simulations per batch
+
+// What the batch step kernel needs of one simulation in its particle loop.
+struct BSim {
+  unsigned seg[2];          // first slot of each species segment in the batch arrays
+  int cbase;                // first cell in the batch cell arrays
+  int N;                    // cells
+  unsigned long long seed;  // run seed
+  unsigned p_null_u24[2];   // null-collision probability (see SpConst)
+  unsigned collides;        // bit s: species s takes the null-collision test
+  unsigned pad;
+};
+
+// Batch-level device words.
+struct BatchDev {
+  unsigned long long step;  // step the next particle step advances
+  unsigned int error;       // OR of the simulations' error bits (refreshed by the plan kernel)
+  unsigned int pad;
+};
+
+struct BatchStep32 {
+  Species32 sp[2];              // batch arrays of the current buffer
+  const float2* E2;             // batch cell arrays
+  unsigned int* cnt[2];
+  unsigned long long* S[2];
+  Phys ph;                      // constants every simulation of the batch shares (push, masses)
+  const StepParams32* sims;     // per simulation, pointers offset to its segment and cells
+  const BSim* hot;
+  const unsigned* pre[2];       // per species: chunk prefix over the simulations (nsims + 1)
+  const unsigned* ncur[2];      // per species: extent of each simulation at the step's start
+  BatchDev* dev;
+  int nsims;
+};
+
+struct BatchPlan {
+  StepParams32* sims[2];        // per-simulation parameters of both buffers (their step is set)
+  unsigned* pre[2];             // out: chunk prefix (chunks of 32 * PIC_PPT particles)
+  unsigned* tpre[2];            // out: tile prefix (tiles of PIC_TILE particles, the sort)
+  unsigned* ncur[2];            // out: extents
+  BatchDev* dev;
+  int nsims;
+  int advance;                  // 1: the step just completed (dev->step += 1)
+};
+
 cudaError_t launch_field(const PoissonParams& p, cudaStream_t st);
 cudaError_t launch_step32(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_step64(const StepParams64& p, int grid, cudaStream_t st);
@@ -271,3 +330,14 @@ cudaError_t launch_restore32(const int* cell, const double* frac, const double* 
                              unsigned long long base, int N, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                           cudaStream_t st);
+
+// ensembles
+int bstep32_variants();
+const char* bstep32_variant_name(int v);
+int bstep32_occupancy(int v);
+cudaError_t launch_bstep32(int v, const BatchStep32& p, int grid, cudaStream_t st);
+cudaError_t launch_bplan(const BatchPlan& p, cudaStream_t st);
+cudaError_t launch_field_batch(const PoissonParams* tab, int nsims, int maxN, cudaStream_t st);
+cudaError_t launch_sort_batch(const SortParams* tab, const unsigned* tpre0, const unsigned* tpre1,
+                              const unsigned* ncur0, const unsigned* ncur1, int nsims, int maxN, int grid,
+                              cudaStream_t st);

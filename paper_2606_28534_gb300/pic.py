@@ -62,7 +62,19 @@ class PicDiag(C.Structure):
 #: every entry point of include/pic.h
 SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapshot", "pic_restore",
            "pic_diag", "pic_get_field", "pic_profile", "pic_kernel_times", "pic_free",
-           "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc")
+           "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc",
+           "pic_batch_variant_count", "pic_batch_variant_name", "pic_batch_workspace_size",
+           "pic_batch_init", "pic_batch_set_tuning", "pic_batch_get_tuning", "pic_batch_step",
+           "pic_batch_sync", "pic_batch_diag", "pic_batch_snapshot", "pic_batch_restore",
+           "pic_batch_reset", "pic_batch_get_field", "pic_batch_profile", "pic_batch_kernel_times",
+           "pic_batch_free")
+
+PIC_BATCH_MAX_SIMS = 4096
+
+
+class PicBatchTuning(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("ctas_per_sm", C.c_int32), ("sort_ctas_per_sm", C.c_int32),
+                ("use_graph", C.c_int32)]
 
 
 def lib():
@@ -91,6 +103,26 @@ def lib():
         L.pic_philox.argtypes = [V, V, V, C.c_size_t, V]
         L.pic_poisson.argtypes = [V, C.c_int32, C.c_double, C.c_double, C.c_double, V, V, V]
         L.pic_field_noalloc.argtypes = [P(PicConfig), V, V, C.c_uint64, V, V, C.c_uint64, V, V, V]
+        L.pic_batch_variant_count.argtypes = []
+        L.pic_batch_variant_count.restype = C.c_int32
+        L.pic_batch_variant_name.argtypes = [C.c_int32]
+        L.pic_batch_variant_name.restype = C.c_char_p
+        L.pic_batch_workspace_size.argtypes = [P(PicConfig), C.c_int32, P(C.c_size_t)]
+        L.pic_batch_init.argtypes = [P(PicConfig), C.c_int32, V, C.c_size_t, V, P(V)]
+        L.pic_batch_set_tuning.argtypes = [V, P(PicBatchTuning)]
+        L.pic_batch_get_tuning.argtypes = [V, P(PicBatchTuning)]
+        L.pic_batch_step.argtypes = [V, C.c_int32]
+        L.pic_batch_sync.argtypes = [V]
+        L.pic_batch_diag.argtypes = [V, P(PicDiag), C.c_int32]
+        L.pic_batch_snapshot.argtypes = [V, C.c_int32, V, C.c_size_t, P(C.c_size_t)]
+        L.pic_batch_restore.argtypes = [V, P(V), P(C.c_size_t)]
+        L.pic_batch_reset.argtypes = [V]
+        L.pic_batch_get_field.argtypes = [V, C.c_int32, P(C.c_int64), P(C.c_double), P(C.c_double),
+                                          P(C.c_float), C.c_size_t]
+        L.pic_batch_profile.argtypes = [V, C.c_int]
+        L.pic_batch_kernel_times.argtypes = [V, P(C.c_double), P(C.c_uint64), P(C.c_char_p), C.c_int32]
+        L.pic_batch_free.argtypes = [V]
+        L.pic_batch_free.restype = None
         _lib = L
     return _lib
 
@@ -221,6 +253,121 @@ class Simulation:
                 for k in range(PIC_KERNEL_KINDS) if names[k] and names[k].decode()}
 
 
+def batch_variants() -> list:
+    """Names of the compiled shapes of the ensemble particle-step kernel."""
+    return [lib().pic_batch_variant_name(v).decode() for v in range(lib().pic_batch_variant_count())]
+
+
+def _config_array(params_list):
+    n = len(params_list)
+    arr = (PicConfig * n)()
+    for k, p in enumerate(params_list):
+        arr[k] = make_config(p)
+    return arr
+
+
+def batch_workspace_size(params_list) -> int:
+    arr = _config_array(params_list)
+    n = C.c_size_t(0)
+    _check(lib().pic_batch_workspace_size(arr, len(params_list), C.byref(n)), "pic_batch_workspace_size")
+    return n.value
+
+
+class Batch:
+    """An ensemble of independent simulations advanced together (pic_batch_* calls)."""
+
+    def __init__(self, params_list, device=None, stream=None):
+        torch = _torch()
+        self.params = [dict(p) for p in params_list]
+        self.n = len(self.params)
+        self.device = torch.device(device if device is not None else "cuda")
+        self._cfgs = _config_array(self.params)
+        nbytes = batch_workspace_size(self.params)
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().pic_batch_init(self._cfgs, self.n, C.c_void_p(self._ws.data_ptr()), nbytes,
+                                      C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        _check(rc, "pic_batch_init")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_batch_free(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, variant: int = 0, ctas_per_sm: int = 0, sort_ctas_per_sm: int = 0,
+                   use_graph: bool = True):
+        t = PicBatchTuning(int(variant), int(ctas_per_sm), int(sort_ctas_per_sm), 1 if use_graph else 0)
+        _check(lib().pic_batch_set_tuning(self._h, C.byref(t)), "pic_batch_set_tuning")
+
+    def tuning(self) -> dict:
+        t = PicBatchTuning()
+        _check(lib().pic_batch_get_tuning(self._h, C.byref(t)), "pic_batch_get_tuning")
+        return {"variant": t.variant, "ctas_per_sm": t.ctas_per_sm, "sort_ctas_per_sm": t.sort_ctas_per_sm,
+                "use_graph": bool(t.use_graph)}
+
+    def step(self, n: int = 1):
+        _check(lib().pic_batch_step(self._h, int(n)), "pic_batch_step")
+
+    def sync(self):
+        _check(lib().pic_batch_sync(self._h), "pic_batch_sync")
+
+    def diag(self) -> list:
+        d = (PicDiag * self.n)()
+        _check(lib().pic_batch_diag(self._h, d, self.n), "pic_batch_diag")
+        return [_diag_dict(d[k]) for k in range(self.n)]
+
+    def snapshot(self, k: int) -> bytes:
+        need = C.c_size_t(0)
+        _check(lib().pic_batch_snapshot(self._h, int(k), None, 0, C.byref(need)), "pic_batch_snapshot")
+        buf = C.create_string_buffer(need.value)
+        _check(lib().pic_batch_snapshot(self._h, int(k), buf, need.value, C.byref(need)), "pic_batch_snapshot")
+        return buf.raw[: need.value]
+
+    def restore(self, blobs) -> int:
+        """Returns the status (0 = ok) instead of raising, so that tests can check error codes."""
+        if len(blobs) != self.n:
+            raise ValueError("one blob per simulation")
+        keep = [C.create_string_buffer(b, len(b)) for b in blobs]
+        ptrs = (C.c_void_p * self.n)(*[C.cast(k, C.c_void_p) for k in keep])
+        lens = (C.c_size_t * self.n)(*[len(b) for b in blobs])
+        return int(lib().pic_batch_restore(self._h, ptrs, lens))
+
+    def reset(self):
+        _check(lib().pic_batch_reset(self._h), "pic_batch_reset")
+
+    def fields(self, k: int) -> dict:
+        n1 = int(self.params[k]["ncells"]) + 1
+        R = np.empty(2 * n1, np.int64)
+        rho, phi = np.empty(n1), np.empty(n1)
+        E = np.empty(n1, np.float32)
+        _check(lib().pic_batch_get_field(self._h, int(k), R.ctypes.data_as(C.POINTER(C.c_int64)),
+                                         rho.ctypes.data_as(C.POINTER(C.c_double)),
+                                         phi.ctypes.data_as(C.POINTER(C.c_double)),
+                                         E.ctypes.data_as(C.POINTER(C.c_float)), n1), "pic_batch_get_field")
+        return {"R": R.reshape(2, n1), "rho": rho, "phi": phi, "E": E}
+
+    def profile(self, enable: bool):
+        _check(lib().pic_batch_profile(self._h, 1 if enable else 0), "pic_batch_profile")
+
+    def kernel_times(self) -> dict:
+        ms = (C.c_double * PIC_KERNEL_KINDS)()
+        ln = (C.c_uint64 * PIC_KERNEL_KINDS)()
+        names = (C.c_char_p * PIC_KERNEL_KINDS)()
+        _check(lib().pic_batch_kernel_times(self._h, ms, ln, names, PIC_KERNEL_KINDS), "pic_batch_kernel_times")
+        return {names[k].decode(): {"ms": ms[k], "launches": int(ln[k])}
+                for k in range(PIC_KERNEL_KINDS) if names[k] and names[k].decode()}
+
+
 def philox(ctr, key, stream=None):
     """Philox4x32-10 on the GPU: ctr (n, 4) and key (n, 2) int32/uint32 CUDA tensors -> (n, 4)."""
     torch = _torch()
@@ -265,5 +412,5 @@ def field_noalloc(params: dict, cell0, frac0, cell1, frac1, stream=None):
     return R, E
 
 
-__all__ = ["Simulation", "philox", "poisson", "make_config", "workspace_size", "lib", "PicError",
-           "SYMBOLS", "W"]
+__all__ = ["Simulation", "Batch", "philox", "poisson", "make_config", "workspace_size",
+           "batch_workspace_size", "batch_variants", "lib", "PicError", "SYMBOLS", "W"]

@@ -56,6 +56,49 @@ C3 = variant(C2, ncells=65536, L=65536.0, ppc=(763, 763), load_profile=LOAD_EXP,
              capacity_factor=1.15, seed=SEED0 + 3)
 C3_STEPS = 100
 
+#: config 4: an ensemble of 256 independent runs of config 2's physics (B = 0.5 at 30 degrees, all
+#: four processes), each with its own size and plasma: cells uniform in [128, 8192] (dx = 1),
+#: particles per cell uniform in [50, 500] (both species), electron collisionality nu/omega_p =
+#: n_gas * sigma_el log-uniform in [0.001, 0.1], left-wall bias uniform in [-5, 0] T_e (right wall
+#: grounded), 500 steps; about 5.9e8 particles in all.
+C4_SIMS, C4_STEPS = 256, 500
+
+
+def ensemble(n: int = C4_SIMS, seed: int = SEED0 + 4, cells=(128, 8192), ppc=(50, 500),
+             nu=(1e-3, 1e-1), bias=(-5.0, 0.0), base: dict | None = None, **kw) -> list:
+    """Seeded draw of ``n`` run configurations (numpy PCG64, fixed seed); run k gets the run seed
+    ``seed * 4096 + k``.  Extra keyword arguments override fields of every run."""
+    import numpy as np
+
+    base = C2 if base is None else base
+    g = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        N = int(g.integers(cells[0], cells[1] + 1))
+        m = int(g.integers(ppc[0], ppc[1] + 1))
+        lnu = g.uniform(np.log(nu[0]), np.log(nu[1]))
+        V = float(g.uniform(bias[0], bias[1]))
+        out.append(variant(base, ncells=N, L=float(N), ppc=(m, m), n_gas=float(np.exp(lnu)) / base["sigma_el"],
+                           V_left=V, V_right=0.0, seed=seed * 4096 + k, **kw))
+    return out
+
+
+def c4() -> list:
+    return ensemble()
+
+
+#: a small heterogeneous ensemble the oracle finishes in seconds: sizes from 2 cells up, few
+#: particles per cell, collisionality up to strongly collisional
+def small_ensemble(n: int = 9, seed: int = SEED0 + 40) -> list:
+    runs = ensemble(n, seed=seed, cells=(24, 220), ppc=(5, 48), nu=(1e-3, 2.5e-1))
+    runs[0] = variant(runs[0], ncells=2, L=2.0, ppc=(7, 7))         # the smallest grid
+    runs[1] = variant(runs[1], coll_mask=0)                          # collisionless
+    runs[2] = variant(runs[2], coll_mask=COLL_CX, ppc=(9, 23))       # ions only collide; unequal ppc
+    runs[3] = variant(runs[3], n_gas=25.0)                           # every process fires often
+    runs[4] = variant(runs[4], load_profile=LOAD_EXP, profile_scale=16.0)
+    return runs
+
+
 #: config 5: collisionless adjoint case, 1024 cells x 200 ppc, 200 steps.
 C5 = variant(BASE, ncells=1024, L=1024.0, ppc=(200, 200), coll_mask=0, seed=SEED0 + 5)
 C5_STEPS = 200

@@ -64,3 +64,76 @@ def test_init_rejects_bad_arguments_before_any_device_work(L):
     assert L.pic_step(None, 1) == 1
     assert L.pic_diag(None, None) == 1
     assert L.pic_poisson(None, 8, 1.0, 0.0, 0.0, None, None, None) == 1
+
+
+# ---- ensembles --------------------------------------------------------------------------------
+def test_batch_shapes_are_listed(L):
+    names = pic.batch_variants()
+    assert len(names) >= 2 and all(re.fullmatch(r"tpb\d+_minb\d+_stages\d+", n) for n in names)
+    assert L.pic_batch_variant_name(len(names)) is None
+    assert L.pic_batch_variant_name(-1) is None
+
+
+def test_batch_workspace_is_the_sum_of_its_parts(L):
+    runs = W.small_ensemble()
+    total = pic.batch_workspace_size(runs)
+    assert total > 0
+    # one more simulation needs more room
+    assert pic.batch_workspace_size(runs + [runs[3]]) > total
+    # the C4 ensemble: about 5.9e8 particles, two SoA buffers of 28 bytes a slot with headroom
+    c4 = W.c4()
+    n = sum(2 * p["ncells"] * p["ppc"][0] for p in c4)
+    assert 5.0e8 < n < 6.5e8
+    assert 2 * 28 * n < pic.batch_workspace_size(c4) < 2 * 28 * n * 1.5
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dt=0.05),                       # time step shared by the batch
+    dict(L=200.0),                       # cell size shared (L / ncells)
+    dict(B=0.25),
+    dict(B_angle_deg=10.0),
+    dict(mass=(1.0, 1836.0)),
+    dict(charge=(-1.0, 2.0)),
+    dict(sort_interval=4),
+    dict(field_mode=W.FIELD_ZERO),
+    dict(frozen_mask=2),
+    dict(precision=W.PRECISION_FP64_PLAIN),  # the batch is the FP32 path
+    dict(source_mode=W.SOURCE_PAIRS, source_x1=4.0),
+])
+def test_batch_rejects_configurations_that_cannot_share_a_launch(L, bad):
+    runs = W.small_ensemble()
+    runs[5] = W.variant(runs[5], **bad)
+    with pytest.raises(pic.PicError) as e:
+        pic.batch_workspace_size(runs)
+    assert e.value.status == 1
+
+
+def test_batch_accepts_per_run_physics(L):
+    runs = W.small_ensemble()
+    runs[5] = W.variant(runs[5], V_left=-4.0, V_right=0.5, n_gas=3.0, sigma_cx=0.05, Tg=0.2,
+                        T=(2.0, 0.3), E_cap=40.0, capacity_factor=2.0, seed=5,
+                        load_profile=W.LOAD_QUIET_SINE, profile_scale=0.2, profile_mode=3)
+    assert pic.batch_workspace_size(runs) > 0
+
+
+def test_batch_init_rejects_bad_arguments_before_any_device_work(L):
+    runs = W.small_ensemble()
+    arr = (pic.PicConfig * len(runs))(*[pic.make_config(p) for p in runs])
+    h = C.c_void_p(1)
+    assert L.pic_batch_init(arr, 0, None, 0, None, C.byref(h)) == 1
+    assert h.value is None
+    assert L.pic_batch_init(arr, pic.PIC_BATCH_MAX_SIMS + 1, None, 0, None, C.byref(h)) == 1
+    assert L.pic_batch_init(None, 3, None, 0, None, C.byref(h)) == 1
+    # a workspace that is not 256-byte aligned
+    assert L.pic_batch_init(arr, len(runs), C.c_void_p(16), 1 << 30, None, C.byref(h)) == 1
+    n = C.c_size_t(0)
+    assert L.pic_batch_workspace_size(arr, len(runs), None) == 1
+    assert L.pic_batch_workspace_size(arr, len(runs), C.byref(n)) == 0 and n.value > 0
+    assert L.pic_batch_step(None, 1) == 1
+    assert L.pic_batch_sync(None) == 1
+    assert L.pic_batch_diag(None, None, 0) == 1
+    assert L.pic_batch_snapshot(None, 0, None, 0, None) == 1
+    assert L.pic_batch_restore(None, None, None) == 1
+    assert L.pic_batch_reset(None) == 1
+    assert L.pic_batch_set_tuning(None, None) == 1
+    L.pic_batch_free(None)

@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 import snapfmt
+import stepcheck
 from oracle import oracle as O
 from paper_2606_28534_gb300 import build, pic
 from paper_2606_28534_gb300 import workloads as W
@@ -162,39 +163,7 @@ def test_single_step_fp32_matches_oracle(name):
     assert g.restore(blob) == 0
     o.step(1)
     g.step(1)
-    do, dg = o.diag(), g.diag()
-    so = snapfmt.parse(o.snapshot())["species"]
-    sg = snapfmt.parse(g.snapshot())["species"]
-    d0 = snapfmt.parse(blob)
-    near = sum(do["near_threshold"]) - int(d0["counters"][9] + d0["counters"][10]) + \
-        sum(dg["near_threshold"]) - int(d0["counters"][9] + d0["counters"][10])
-    mismatched = 0
-    for s in range(2):
-        a, b = _by_id(sg[s]), _by_id(so[s])
-        common, ia, ib = np.intersect1d(a["id"], b["id"], return_indices=True)
-        only = len(a["id"]) + len(b["id"]) - 2 * len(common)
-        xa = a["cell"][ia] + a["frac"][ia]
-        xb = b["cell"][ib] + b["frac"][ib]
-        vt = math.sqrt(p["T"][s] / p["mass"][s])
-        dv = np.abs(a["v"][ia] - b["v"][ib]).max(axis=1)
-        okv = dv <= 1e-5 * np.abs(b["v"][ib]).max(axis=1) + 1e-6 * vt
-        okx = np.abs(xa - xb) <= 2e-6
-        bad = ~(okv & okx)
-        mismatched += int(bad.sum()) + only
-    # every disagreement is a near-threshold collision draw (each can add a particle pair)
-    assert mismatched <= 4 * near, (mismatched, near)
-    for s in range(2):
-        assert dg["wall_hits"][s] == do["wall_hits"][s]
-    for k in range(4):
-        assert abs(dg["coll"][k] - do["coll"][k]) <= near
-    assert dg["coll"][4] == do["coll"][4]  # the candidate test uses identical values
-    assert dg["net_charge_units"] == 2**32 * (dg["n"][1] - dg["n"][0])
-    fo, fg = o.fields(), g.fields()
-    scale = max(np.abs(fo["phi"]).max(), 1e-3)
-    assert np.abs(fo["phi"] - fg["phi"]).max() <= 1e-5 * scale + _cond_tol(p["ncells"]) * scale
-    # integer deposit: each particle's W_r differs by at most its FP32 position error 2^32 * 2e-6
-    count = np.abs(fo["R"]).max() / 2**32 + 1
-    assert np.abs(fo["R"] - fg["R"]).max() <= count * 2**32 * 2e-6 + 2**33 * mismatched
+    stepcheck.assert_one_step(p, blob, o.diag(), o.snapshot(), o.fields(), g.diag(), g.snapshot(), g.fields())
 
 
 @pytest.mark.parametrize("name", ["SMALL_C1", "SMALL_C2", "SMALL_C3"])
