@@ -186,6 +186,80 @@ def timed_run(sim, torch, steps: int, profile: bool):
     return ms, ps, kt
 
 
+def events_ms(torch, stream, fn) -> float:
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def batched(args, torch, pic, peak: float) -> dict:
+    """Config 4: 256 independent runs of uneven size in one batch (autotuned launch configuration,
+    CUDA graphs), against the same runs advanced one at a time through the single-run API."""
+    from paper_2606_28534_gb300 import autotune
+
+    runs = W.c4()
+    K = args.batch_steps
+    b = pic.Batch(runs)
+    tune = autotune.tune(b, cache_path=os.path.join(tempfile.gettempdir(), "pic_gb300_tuning.json"))
+    b.step(args.warmup)
+    b.sync()
+
+    def ps_total():
+        return sum(d["particle_steps"] for d in b.diag())
+
+    ps0 = ps_total()
+    ms = events_ms(torch, b.stream, lambda: b.step(K))
+    b.sync()
+    ps = ps_total() - ps0
+    # kernel times of whole sort cycles, launched one by one with events (no graphs)
+    cyc = 2 * runs[0]["sort_interval"]
+    q0 = ps_total()
+    b.profile(True)
+    b.step(cyc)
+    kt = b.kernel_times()
+    b.profile(False)
+    kps = ps_total() - q0
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    step_ms = kt["step"]["ms"] / max(1, kt["step"]["launches"])
+    bytes_per_launch = BYTES_STEP_KERNEL * kps / max(1, kt["step"]["launches"])
+    achieved = bytes_per_launch / (step_ms / 1000.0) / 1e9
+    # the same runs one at a time (same steps each; device time of the steps only)
+    one_ms, one_ps = 0.0, 0
+    for p in runs:
+        g = pic.Simulation(p)
+        g.step(args.warmup)
+        g.sync()
+        q = g.diag()["particle_steps"]
+        one_ms += events_ms(torch, g.stream, lambda: g.step(K))
+        one_ps += g.diag()["particle_steps"] - q
+        g.close()
+    value = ps / (ms / 1000.0)
+    one = one_ps / (one_ms / 1000.0)
+    return {
+        "workload": f"c4: {len(runs)} independent runs, cells U[128, 8192], ppc U[50, 500], "
+                    f"nu/omega_p log-U[0.001, 0.1], V_L U[-5, 0], config 2's physics; "
+                    f"{sum(2 * p['ncells'] * p['ppc'][0] for p in runs):,} particles",
+        "value": value, "unit": "particle-steps/s", "steps": K, "ms_per_step": ms / K,
+        "tuning": dict(tune["tuning"], shape=pic.batch_variants()[tune["tuning"]["variant"]],
+                       cached=tune["cached"], trials=len(tune["trials"])),
+        "one_at_a_time": {"value": one, "unit": "particle-steps/s", "ms_per_step": one_ms / K,
+                          "what": "each run alone through pic_init / pic_step, device time of its steps"},
+        "speedup_vs_one_at_a_time": value / one,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "kernel": "k_bstep32", "bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": step_ms, "traffic": None},
+        "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in kt.items()
+                    if v["launches"]},
+    }
+
+
 def run_ours(args, rank: int, world: int, local: int) -> None:
     import torch
 
@@ -296,6 +370,10 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
                        "pic_step(1) and pic_diag (device-to-host read of the control block)"}
         sim2.close()
 
+    batch = None
+    if not args.no_batch:
+        batch = batched(args, torch, pic, peak)
+
     if rank != 0:
         return
     line = {
@@ -317,6 +395,7 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         "gpu_launches": int(sum(v["launches"] for v in kt.values())),
         "clocks": clk,
         "fp64_plain": plain,
+        "batched": batch,
         "e2e": e2e,
     }
     if world == 1 and not args.no_cpu:
@@ -339,6 +418,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=W.C4_STEPS)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
