@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic_oracle.c")
+_SRC_ADJ = os.path.join(_HERE, "pic_adjoint.c")
 _HDR = os.path.join(_HERE, "pic_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
@@ -60,12 +61,12 @@ class OrcDiag(C.Structure):
 def build(force: bool = False) -> str:
     """Compile ``liboracle.so`` with gcc (OpenMP on, no FMA contraction)."""
     with _lock:
-        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_ADJ), os.path.getmtime(_HDR))
         if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
             return _LIB
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-fopenmp", "-shared",
-               _SRC, "-o", tmp, "-lm"]
+               _SRC, _SRC_ADJ, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
         return _LIB
@@ -109,6 +110,15 @@ def lib():
         L.orc_load_particle.argtypes = [P(OrcConfig), C.c_int, C.c_uint64, P(C.c_double),
                                         P(C.c_double), P(C.c_uint64)]
         L.orc_load_particle.restype = None
+        L.orc_field_apply.argtypes = [C.c_int32, C.c_double, P(C.c_double), P(C.c_double)]
+        L.orc_field_apply.restype = None
+        L.orc_field_adjoint.argtypes = [C.c_int32, C.c_double, P(C.c_double), P(C.c_double)]
+        L.orc_field_adjoint.restype = None
+        L.orc_adj_particles.argtypes = [P(OrcConfig)]
+        L.orc_adj_particles.restype = C.c_size_t
+        L.orc_adj_forward.argtypes = [P(OrcConfig), C.c_int32, C.c_int, P(C.c_int32), P(C.c_double)]
+        L.orc_adj_gradient.argtypes = [P(OrcConfig), C.c_int32, P(C.c_double), P(C.c_double),
+                                       P(C.c_double), P(C.c_int32)]
         _lib = L
     return _lib
 
@@ -279,3 +289,55 @@ class OracleSim:
 
     def restore(self, blob: bytes) -> int:
         return int(lib().orc_restore(self._h, blob, len(blob)))
+
+
+# ------------------------------------------------------------------------------------------------
+# Adjoint of the collisionless step (pic_adjoint.c): frozen absorption schedule, observables
+# J = (J_flux, J_fe), parameters (V_left, T[0]).
+ADJ_NEVER = 2**31 - 1
+
+
+def field_apply(rho: np.ndarray, dx: float) -> np.ndarray:
+    """E = G rho (node field of a charge density, walls grounded)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    E = np.empty_like(rho)
+    lib().orc_field_apply(len(rho) - 1, dx, _ptr(rho, C.c_double), _ptr(E, C.c_double))
+    return E
+
+
+def field_adjoint(mu: np.ndarray, dx: float) -> np.ndarray:
+    """rho_bar = G^T mu."""
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    rb = np.empty_like(mu)
+    lib().orc_field_adjoint(len(mu) - 1, dx, _ptr(mu, C.c_double), _ptr(rb, C.c_double))
+    return rb
+
+
+def adj_forward(params: dict, steps: int, absorb: np.ndarray | None = None):
+    """Forward of the adjoint model.  absorb None: records the schedule; else replays it.
+    Returns (J (2,), absorb)."""
+    c = make_config(params)
+    n = lib().orc_adj_particles(C.byref(c))
+    replay = absorb is not None
+    ab = np.ascontiguousarray(absorb, dtype=np.int32).copy() if replay else np.zeros(n, np.int32)
+    if len(ab) != n:
+        raise ValueError("schedule of the wrong length")
+    J = np.zeros(2)
+    rc = lib().orc_adj_forward(C.byref(c), steps, 1 if replay else 0, _ptr(ab, C.c_int32), _ptr(J, C.c_double))
+    if rc != 0:
+        raise RuntimeError(f"orc_adj_forward failed: {rc}")
+    return J, ab
+
+
+def adj_gradient(params: dict, steps: int, weights=(1.0, 0.0)):
+    """Discrete adjoint: (grad d(w . J)/d(V_left, T_e) (2,), J (2,), recorded schedule)."""
+    c = make_config(params)
+    n = lib().orc_adj_particles(C.byref(c))
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    g, J = np.zeros(2), np.zeros(2)
+    ab = np.zeros(n, np.int32)
+    rc = lib().orc_adj_gradient(C.byref(c), steps, _ptr(w, C.c_double), _ptr(g, C.c_double),
+                                _ptr(J, C.c_double), _ptr(ab, C.c_int32))
+    if rc != 0:
+        raise RuntimeError(f"orc_adj_gradient failed: {rc}")
+    return g, J, ab

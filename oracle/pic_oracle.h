@@ -146,6 +146,25 @@ uint64_t orc_config_hash(const orc_config* cfg);
 /* OpenMP threads used by orc_step (1 = serial); returns the count in effect. */
 int orc_set_threads(int n);
 
+/* ---- adjoint of the collisionless step (pic_adjoint.c) ----------------------------------------
+ * Frozen absorption schedule, observables J = (J_flux, J_fe) and parameters (V_left, T[0]) as the
+ * header comment of pic_adjoint.c states.  Configurations: coll_mask 0, no source, T[0] > 0. */
+#define ORC_ADJ_NEVER INT32_MAX
+/* Node field of a charge density without wall bias, E = G rho, and its transpose rho_bar = G^T mu
+ * (N + 1 nodes each). */
+void orc_field_apply(int32_t N, double dx, const double* rho, double* E);
+void orc_field_adjoint(int32_t N, double dx, const double* mu, double* rho_bar);
+/* Particles of the model: electrons then ions, in load order. */
+size_t orc_adj_particles(const orc_config* cfg);
+/* Forward of `steps` steps.  replay == 0: records absorb[p] (the step at which particle p left
+ * [0, N), ORC_ADJ_NEVER if it did not); replay != 0: absorbs particle p at step absorb[p].
+ * J[0] = J_flux, J[1] = J_fe. */
+int orc_adj_forward(const orc_config* cfg, int32_t steps, int replay, int32_t* absorb, double J[2]);
+/* Recording forward, then the discrete adjoint: grad = d(w[0] J_flux + w[1] J_fe) / d(V_left, T[0]).
+ * Also returns J and the recorded schedule. */
+int orc_adj_gradient(const orc_config* cfg, int32_t steps, const double w[2], double grad[2], double J[2],
+                     int32_t* absorb);
+
 #ifdef __cplusplus
 }
 #endif
