@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -260,6 +261,46 @@ def batched(args, torch, pic, peak: float) -> dict:
     }
 
 
+def adjoint_section(args, torch, pic) -> dict:
+    """Config 5: forward + reverse sweep of the collisionless adjoint (checkpoint every 20 steps),
+    timed on the device; its gradient against the FP64 oracle's on the host cores."""
+    p = W.variant(W.C5, V_left=-1.0)
+    steps = W.C5_STEPS
+    a = pic.Adjoint(p, steps, 20)
+    VL, Te = p["V_left"], p["T"][0]
+    a.forward(VL, Te)
+    a.gradient(1.0, 0.0)  # warm-up
+    fwd, rev = [], []
+    for _ in range(args.adj_reps):
+        J = a.forward(VL, Te)
+        g_flux = a.gradient(1.0, 0.0)
+        f_ms, r_ms = a.times()
+        fwd.append(f_ms)
+        rev.append(r_ms)
+    g_fe = a.gradient(0.0, 1.0)
+    a.close()
+    n = p["ncells"] * (p["ppc"][0] + p["ppc"][1])
+    f_ms, r_ms = statistics.median(fwd), statistics.median(rev)
+    out = {
+        "workload": f"c5: collisionless, {p['ncells']} cells, {n:,} particles, {steps} steps, "
+                    "checkpoint every 20 steps, parameters (V_left, T_e), observables (J_flux, J_fe)",
+        "forward_ms": f_ms, "gradient_ms": r_ms,
+        "value": n * steps / ((f_ms + r_ms) / 1000.0), "unit": "particle-steps/s (forward + one reverse sweep)",
+        "J": list(J), "grad_flux": list(g_flux), "grad_fe": list(g_fe),
+    }
+    if not args.no_cpu:
+        from oracle import oracle as O
+
+        t0 = time.perf_counter()
+        go_f, Jo, _ = O.adj_gradient(p, steps, (1.0, 0.0))
+        go_e, _, _ = O.adj_gradient(p, steps, (0.0, 1.0))
+        out["oracle"] = {"J": list(Jo), "grad_flux": list(go_f), "grad_fe": list(go_e),
+                         "seconds": round(time.perf_counter() - t0, 2),
+                         "rel_diff_flux": float(math.dist(g_flux, go_f) / math.hypot(*go_f)),
+                         "rel_diff_fe": float(math.dist(g_fe, go_e) / math.hypot(*go_e))}
+    return out
+
+
 def run_ours(args, rank: int, world: int, local: int) -> None:
     import torch
 
@@ -373,6 +414,9 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
     batch = None
     if not args.no_batch:
         batch = batched(args, torch, pic, peak)
+    adj = None
+    if not args.no_adjoint:
+        adj = adjoint_section(args, torch, pic)
 
     if rank != 0:
         return
@@ -396,6 +440,7 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         "clocks": clk,
         "fp64_plain": plain,
         "batched": batch,
+        "adjoint": adj,
         "e2e": e2e,
     }
     if world == 1 and not args.no_cpu:
@@ -419,6 +464,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adj-reps", type=int, default=5)
     ap.add_argument("--batch-steps", type=int, default=W.C4_STEPS)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -283,6 +283,55 @@ int pic_batch_kernel_times(pic_batch* b, double* ms, uint64_t* launches, const c
 /* Destroy the batch (synchronises; frees what pic_batch_init allocated). */
 void pic_batch_free(pic_batch* b);
 
+/* ---- gradients: the adjoint of the collisionless step -------------------------------------------
+ *
+ * The paper computes no gradients; these calls differentiate its collisionless step (Sec. 2:
+ * gather, Boris push, deposit, field solve; collisions off) by a hand-written discrete adjoint.
+ * Model (one handle = one configuration, `steps` steps; FP32 particles, signed int64 fixed-point
+ * deposit, FP64 field; the adjoint accumulates in FP64):
+ *  - absorption at the walls is taken as a fixed schedule: a recording forward absorbs a particle at
+ *    the first step its position leaves [0, L) and stores that step; a replaying forward absorbs
+ *    each particle at its recorded step whatever its position (until then a particle outside
+ *    [0, L) keeps the linear extension of its boundary cell's CIC weights), so that finite
+ *    differences of the replaying forward approximate what the adjoint differentiates;
+ *  - J[0] = J_flux = sum over steps n of dt * sum over electrons alive after step n of
+ *    w v_x S(x - (L - dx)), S(d) = max(0, 1 - |d|/dx): the CIC share of the last interior node, a
+ *    smooth measure of the electron flux into the right wall;
+ *    J[1] = J_fe = sum_j c_j E_j^2 dx / 2 of the final node field (c_j = 1/2 at the walls);
+ *  - parameters: V_left (the right wall keeps cfg->V_right) and the initial electron temperature
+ *    T_e, which scales the loaded electron velocities, v = sqrt(T_e / m) xi, with the draws xi fixed.
+ * The adjoint stores the particle state every `checkpoint_every` steps and the node field of every
+ * step during a recording forward, and recomputes each segment of checkpoint_every steps from its
+ * checkpoint during the reverse sweep (memory: about (steps / checkpoint_every + checkpoint_every)
+ * x 20 bytes per particle).  Configurations: coll_mask 0, PIC_SOURCE_NONE, T[0] > 0 (precision
+ * and sort_interval are ignored); 1 <= checkpoint_every <= steps.  Work runs on cuda_stream; the
+ * forward and gradient calls synchronise it. */
+typedef struct pic_adj pic_adj;
+
+int pic_adj_workspace_size(const pic_config* cfg, int32_t steps, int32_t checkpoint_every, size_t* bytes);
+
+/* Create the handle (workspace as pic_init: caller's, 256-byte aligned, or NULL = cudaMalloc). */
+int pic_adj_init(const pic_config* cfg, int32_t steps, int32_t checkpoint_every, void* workspace,
+                 size_t workspace_bytes, void* cuda_stream, pic_adj** out);
+
+/* Load with V_left and T_e, run the steps; J[0] = J_flux, J[1] = J_fe (host).  replay == 0 records
+ * the schedule and the checkpoints (the point pic_adj_gradient differentiates at); replay != 0
+ * reuses the last recorded schedule (PIC_EINVAL if there is none) and keeps the recording. */
+int pic_adj_forward(pic_adj* a, double V_left, double T_e, int32_t replay, double J[2]);
+
+/* grad = d(w[0] J_flux + w[1] J_fe) / d(V_left, T_e) at the last recording forward (host arrays):
+ * one reverse sweep per weight vector (a vector-Jacobian product). */
+int pic_adj_gradient(pic_adj* a, const double w[2], double grad[2]);
+
+/* The recorded schedule: absorb[p] = step at which particle p was absorbed (INT32_MAX: never),
+ * electrons then ions in load order; n must be the particle count. */
+int pic_adj_schedule(pic_adj* a, int32_t* absorb, size_t n);
+
+/* Device time of the last forward and the last gradient (CUDA events on the handle's stream). */
+int pic_adj_times(pic_adj* a, double* forward_ms, double* gradient_ms);
+
+void pic_adj_free(pic_adj* a);
+
 /* ---- allocation-free entry point ------------------------------------------------------------ */
 
 /* The paper has no counterpart to this call: it exists for callers that cannot allocate device

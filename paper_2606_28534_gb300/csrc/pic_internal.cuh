@@ -310,6 +310,58 @@ struct BatchPlan {
   int advance;                  // 1: the step just completed (dev->step += 1)
 };
 
+// ---- adjoint of the collisionless step ------------------------------------------------------
+struct AdjState {  // one particle state: all electrons, then all ions
+  int* cell;
+  float* frac;
+  float* vx;
+  float* vy;
+  float* vz;
+};
+
+struct AdjStep {
+  AdjState src, dst;               // state at step start / after the step (may be the same arrays)
+  int* absorb;                     // step at which each particle is absorbed (INT_MAX: never)
+  const double* E;                 // node field E^n (FP64, N + 1)
+  unsigned long long* R[2];        // signed int64 fixed-point node deposits (out)
+  unsigned long long* jflux_fx;    // J_flux, 2^-40 fixed point (accumulated)
+  unsigned long long n0, np;       // electrons [0, n0), ions [n0, np)
+  long long step;
+  int N;
+  int mode;                        // 0 record, 1 replay, 2 recompute (no deposit, no J_flux)
+  unsigned field_mode, frozen_mask, has_B;
+  float qmdt2[2], t[2][3], s[2][3];
+  float dtdx, E_ext;
+  double flux_dtw;                 // dt * w_electron
+};
+
+struct AdjRev {
+  AdjState s0, s1;                 // tape: state at the start and at the end of step n
+  const int* absorb;
+  const double* E;                 // E^n
+  const double* chi;               // A^{-1} psi of mu^{n+1}
+  const double* mu;                // mu^{n+1} (its wall entries)
+  double* mu_next;                 // mu^n (accumulated)
+  double *lx, *lvx, *lvy, *lvz;    // lambda (FP64)
+  unsigned long long n0, np;
+  long long step;
+  int N;
+  unsigned field_mode, frozen_mask;
+  double dx, dtdx;
+  double qw[2], h[2];              // q w, q dt / 2m
+  double M[2][9];                  // Boris rotation per species, row-major
+  double flux_dtw;                 // weight of J_flux * dt * w_electron
+};
+
+cudaError_t launch_adj_push(const AdjStep& p, int max_grid, cudaStream_t st);
+cudaError_t launch_adj_deposit0(const AdjState& s, unsigned long long n0, unsigned long long np,
+                                unsigned long long* R0, unsigned long long* R1, int max_grid, cudaStream_t st);
+cudaError_t launch_adj_fill(int* a, unsigned long long n, int v, cudaStream_t st);
+cudaError_t launch_adj_field_t(const double* mu, double* rhs, int N, double dx, double* gV, int with_rhs,
+                               cudaStream_t st);
+cudaError_t launch_adj_reverse(const AdjRev& p, int max_grid, cudaStream_t st);
+cudaError_t launch_adj_tgrad(const AdjRev& p, const AdjState& s0, double* partial, int blocks, cudaStream_t st);
+
 cudaError_t launch_field(const PoissonParams& p, cudaStream_t st);
 cudaError_t launch_step32(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_step64(const StepParams64& p, int grid, cudaStream_t st);

@@ -67,7 +67,8 @@ SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapsh
            "pic_batch_init", "pic_batch_set_tuning", "pic_batch_get_tuning", "pic_batch_step",
            "pic_batch_sync", "pic_batch_diag", "pic_batch_snapshot", "pic_batch_restore",
            "pic_batch_reset", "pic_batch_get_field", "pic_batch_profile", "pic_batch_kernel_times",
-           "pic_batch_free")
+           "pic_batch_free", "pic_adj_workspace_size", "pic_adj_init", "pic_adj_forward",
+           "pic_adj_gradient", "pic_adj_schedule", "pic_adj_times", "pic_adj_free")
 
 PIC_BATCH_MAX_SIMS = 4096
 
@@ -123,6 +124,14 @@ def lib():
         L.pic_batch_kernel_times.argtypes = [V, P(C.c_double), P(C.c_uint64), P(C.c_char_p), C.c_int32]
         L.pic_batch_free.argtypes = [V]
         L.pic_batch_free.restype = None
+        L.pic_adj_workspace_size.argtypes = [P(PicConfig), C.c_int32, C.c_int32, P(C.c_size_t)]
+        L.pic_adj_init.argtypes = [P(PicConfig), C.c_int32, C.c_int32, V, C.c_size_t, V, P(V)]
+        L.pic_adj_forward.argtypes = [V, C.c_double, C.c_double, C.c_int32, P(C.c_double)]
+        L.pic_adj_gradient.argtypes = [V, P(C.c_double), P(C.c_double)]
+        L.pic_adj_schedule.argtypes = [V, P(C.c_int32), C.c_size_t]
+        L.pic_adj_times.argtypes = [V, P(C.c_double), P(C.c_double)]
+        L.pic_adj_free.argtypes = [V]
+        L.pic_adj_free.restype = None
         _lib = L
     return _lib
 
@@ -368,6 +377,74 @@ class Batch:
                 for k in range(PIC_KERNEL_KINDS) if names[k] and names[k].decode()}
 
 
+def adj_workspace_size(params: dict, steps: int, checkpoint_every: int) -> int:
+    c = make_config(params)
+    n = C.c_size_t(0)
+    _check(lib().pic_adj_workspace_size(C.byref(c), int(steps), int(checkpoint_every), C.byref(n)),
+           "pic_adj_workspace_size")
+    return n.value
+
+
+class Adjoint:
+    """Collisionless forward with a recorded absorption schedule and its discrete adjoint
+    (pic_adj_* calls): observables (J_flux, J_fe), parameters (V_left, T_e)."""
+
+    def __init__(self, params: dict, steps: int, checkpoint_every: int = 20, device=None, stream=None):
+        torch = _torch()
+        self.params = dict(params)
+        self.steps = int(steps)
+        self.checkpoint_every = int(checkpoint_every)
+        self.n = int(params["ncells"]) * (int(params["ppc"][0]) + int(params["ppc"][1]))
+        self.device = torch.device(device if device is not None else "cuda")
+        self._cfg = make_config(params)
+        nbytes = adj_workspace_size(params, steps, checkpoint_every)
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().pic_adj_init(C.byref(self._cfg), self.steps, self.checkpoint_every,
+                                    C.c_void_p(self._ws.data_ptr()), nbytes, C.c_void_p(self.stream.cuda_stream),
+                                    C.byref(h))
+        _check(rc, "pic_adj_init")
+        self._h = h
+        self.recorded = None  # (V_left, T_e) of the last recording forward
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_adj_free(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, V_left: float, T_e: float, replay: bool = False):
+        J = (C.c_double * 2)()
+        _check(lib().pic_adj_forward(self._h, float(V_left), float(T_e), 1 if replay else 0, J), "pic_adj_forward")
+        if not replay:
+            self.recorded = (float(V_left), float(T_e))
+        return J[0], J[1]
+
+    def gradient(self, w_flux: float = 1.0, w_fe: float = 0.0):
+        w = (C.c_double * 2)(float(w_flux), float(w_fe))
+        g = (C.c_double * 2)()
+        _check(lib().pic_adj_gradient(self._h, w, g), "pic_adj_gradient")
+        return g[0], g[1]
+
+    def schedule(self) -> np.ndarray:
+        a = np.empty(self.n, np.int32)
+        _check(lib().pic_adj_schedule(self._h, a.ctypes.data_as(C.POINTER(C.c_int32)), self.n), "pic_adj_schedule")
+        return a
+
+    def times(self):
+        f, g = C.c_double(), C.c_double()
+        _check(lib().pic_adj_times(self._h, C.byref(f), C.byref(g)), "pic_adj_times")
+        return f.value, g.value
+
+
 def philox(ctr, key, stream=None):
     """Philox4x32-10 on the GPU: ctr (n, 4) and key (n, 2) int32/uint32 CUDA tensors -> (n, 4)."""
     torch = _torch()
@@ -412,5 +489,5 @@ def field_noalloc(params: dict, cell0, frac0, cell1, frac1, stream=None):
     return R, E
 
 
-__all__ = ["Simulation", "Batch", "philox", "poisson", "make_config", "workspace_size",
-           "batch_workspace_size", "batch_variants", "lib", "PicError", "SYMBOLS", "W"]
+__all__ = ["Simulation", "Batch", "Adjoint", "philox", "poisson", "make_config", "workspace_size",
+           "batch_workspace_size", "batch_variants", "adj_workspace_size", "lib", "PicError", "SYMBOLS", "W"]

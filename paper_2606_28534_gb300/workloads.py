@@ -91,11 +91,13 @@ def c4() -> list:
 #: particles per cell, collisionality up to strongly collisional
 def small_ensemble(n: int = 9, seed: int = SEED0 + 40) -> list:
     runs = ensemble(n, seed=seed, cells=(24, 220), ppc=(5, 48), nu=(1e-3, 2.5e-1))
-    runs[0] = variant(runs[0], ncells=2, L=2.0, ppc=(7, 7))         # the smallest grid
-    runs[1] = variant(runs[1], coll_mask=0)                          # collisionless
-    runs[2] = variant(runs[2], coll_mask=COLL_CX, ppc=(9, 23))       # ions only collide; unequal ppc
-    runs[3] = variant(runs[3], n_gas=25.0)                           # every process fires often
-    runs[4] = variant(runs[4], load_profile=LOAD_EXP, profile_scale=16.0)
+    special = [dict(ncells=2, L=2.0, ppc=(7, 7)),                    # the smallest grid
+               dict(coll_mask=0),                                    # collisionless
+               dict(coll_mask=COLL_CX, ppc=(9, 23)),                 # ions only collide; unequal ppc
+               dict(n_gas=25.0),                                     # every process fires often
+               dict(load_profile=LOAD_EXP, profile_scale=16.0)]
+    for k, kw in enumerate(special[:n]):
+        runs[k] = variant(runs[k], **kw)
     return runs
 
 
