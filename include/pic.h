@@ -142,6 +142,14 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
  * == 0).  Asynchronous on the handle's stream. */
 int pic_step(pic_handle* h, int32_t n);
 
+/* Kinetic-energy diagnostics (pic_diag_t.ke).  every > 0: the FP32 step kernel sums the kinetic
+ * energy of the particles it leaves alive on every every-th step (counted from pic_init /
+ * pic_restore), so that pic_diag right after such a step costs no extra pass; every == 0 (the
+ * default): pic_diag sums it with one pass over the particles when asked.  Both use the same exact
+ * 2^-24 fixed point and give the same bits.  The plain FP64 path always sums in pic_diag.
+ * PIC_EINVAL for every < 0. */
+int pic_set_diag_interval(pic_handle* h, int32_t every);
+
 /* Wait for the stream and report device-side errors (PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_EDEVICE). */
 int pic_sync(pic_handle* h);
 

@@ -215,6 +215,7 @@ StepParams32 params32(pic_handle* h) {
   P.ctl = h->ctl;
   P.ph = h->ph;
   P.step = h->step;
+  P.sum_ke = 0u;
   return P;
 }
 
@@ -311,10 +312,13 @@ int refresh_field(pic_handle* h) {
   h->ph.push_mask = 0u;
   h->ph.coll_mask = 0u;
   prof_begin(h, K_STEP, &e);
+  StepParams32 P32 = params32(h);
+  P32.sum_ke = 1u;
   cudaError_t err = h->plain ? launch_step64(params64(h), h->grid_step, h->st)
-                             : launch_step32(params32(h), h->grid_step, h->st);
+                             : launch_step32(P32, h->grid_step, h->st);
   prof_end(h, &e);
   h->ph = saved;
+  h->ke_valid = !h->plain;
   CK(err);
   prof_begin(h, K_FIELD, &e);
   CK(launch_field(field_params(h, !h->plain, false), h->st));
@@ -852,7 +856,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms <= 0) sms = 152;
   h->grid_step = sms * (h->plain ? occupancy_step64() : occupancy_step32());
-  h->grid_sort = sms * 4;
+  h->grid_sort = sms * 16;
   h->grid_diag = sms * 8;
   *out = h;
 
@@ -878,7 +882,10 @@ int pic_step(pic_handle* h, int32_t n) {
     const bool sort_now = !h->plain && (h->step % (unsigned long long)h->cfg.sort_interval) == 0ull;
     EvPair e;
     if (!h->plain) {
-      const StepParams32 P = params32(h);
+      StepParams32 P = params32(h);
+      const bool sum_ke = h->ke_every > 0 && ((h->step + 1) % (unsigned long long)h->ke_every) == 0ull;
+      P.sum_ke = sum_ke ? 1u : 0u;
+      h->ke_valid = sum_ke;
       prof_begin(h, K_STEP, &e);
       CK(launch_step32(P, h->grid_step, h->st));
       prof_end(h, &e);
@@ -914,6 +921,12 @@ int pic_step(pic_handle* h, int32_t n) {
   return PIC_OK;
 }
 
+int pic_set_diag_interval(pic_handle* h, int32_t every) {
+  if (!h || every < 0) return PIC_EINVAL;
+  h->ke_every = every;
+  return PIC_OK;
+}
+
 int pic_sync(pic_handle* h) {
   if (!h) return PIC_EINVAL;
   return check_errors(h);
@@ -927,8 +940,11 @@ int pic_diag(pic_handle* h, pic_diag_t* d) {
   CK(cudaMemsetAsync(&h->ctl->netq, 0, sizeof(h->ctl->netq), h->st));
   EvPair e;
   prof_begin(h, K_DIAG, &e);
-  // FP32 path: the step itself summed the kinetic energy (ke_last); the plain path reduces here
+  // kinetic energy: summed by the last step (FP32 path, when it was asked to: ke_last), else one
+  // reduction pass here (same fixed point, same bits)
+  const bool ke_from_step = !h->plain && h->ke_valid;
   if (h->plain) CK(launch_diag64(params64(h), h->grid_diag, h->st));
+  if (!h->plain && !ke_from_step) CK(launch_diag32(params32(h), h->grid_diag, h->st));
   CK(launch_diag_grid(h->R[0], h->R[1], h->cfg.charge[0] > 0 ? 1 : -1, h->cfg.charge[1] > 0 ? 1 : -1, h->E, h->N,
                       h->cfg.L / h->N, h->ctl, h->st));
   prof_end(h, &e);
@@ -948,7 +964,7 @@ int pic_diag(pic_handle* h, pic_diag_t* d) {
     d->near_threshold[s] = c.near_thr[s];
     d->nu_max_violations[s] = c.viol[s];
     d->births[s] = c.births[s];
-    d->ke[s] = (double)(h->plain ? c.ke_fx[s] : c.ke_last[s]) * (1.0 / 16777216.0) * w;
+    d->ke[s] = (double)(ke_from_step ? c.ke_last[s] : c.ke_fx[s]) * (1.0 / 16777216.0) * w;
     d->wall_energy[s] = (double)c.wall_energy_fx[s] * (1.0 / 16777216.0) * w;
   }
   for (int k = 0; k < 5; ++k) d->coll[k] = c.coll[k];

@@ -206,7 +206,7 @@ void make_view(pic_batch* b, int k, pic_handle* h) {
   h->stage_bytes = (size_t)(reinterpret_cast<char*>(b->arr[1][1].id + b->total_cap[1]) - h->stage);
   derive(h);
   h->grid_step = b->sms * occupancy_step32();
-  h->grid_sort = b->sms * 4;
+  h->grid_sort = b->sms * 16;
   h->grid_diag = b->sms * 8;
 }
 
@@ -416,11 +416,13 @@ int sync_errors(pic_batch* b) {
   return status_of(d.error);
 }
 
-// The view of simulation k, brought up to the batch's step and buffer.
+// The view of simulation k, brought up to the batch's step and buffer (the batch step sums the
+// kinetic energy every step).
 pic_handle* view(pic_batch* b, int k) {
   pic_handle* h = b->views[k];
   h->step = b->step;
   h->cur = b->cur;
+  h->ke_valid = true;
   return h;
 }
 

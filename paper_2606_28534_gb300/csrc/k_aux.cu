@@ -102,6 +102,25 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
   return v;
 }
 
+// Kinetic energy of the live FP32 particles, the same 2^-24 fixed point (ke_fx32) the step sums
+// when asked to: the two give the same bits.
+__global__ void __launch_bounds__(256) k_diag32(const StepParams32 P) {
+  const unsigned long long n0 = P.ctl->n_cur[0], n1 = P.ctl->n_cur[1];
+  unsigned long long acc[2] = {0ull, 0ull};
+  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < n0 + n1;
+       g += (unsigned long long)gridDim.x * blockDim.x) {
+    const int s = g < n0 ? 0 : 1;
+    const unsigned long long i = s ? g - n0 : g;
+    const Species32& A = s ? P.sp[1] : P.sp[0];
+    if (A.cell[i] == PIC_DEAD_CELL) continue;
+    acc[s] += ke_fx32(A.vx[i], A.vy[i], A.vz[i], P.ph.sp[s].mass);
+  }
+  for (int s = 0; s < 2; ++s) {
+    unsigned long long t = warp_sum64(acc[s]);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(&P.ctl->ke_fx[s], t);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_diag64(const StepParams64 P) {
   const unsigned long long n0 = P.ctl->n_cur[0], n1 = P.ctl->n_cur[1];
   unsigned long long acc[2] = {0ull, 0ull};
@@ -209,6 +228,11 @@ cudaError_t launch_load64(const StepParams64& p, const unsigned long long n[2], 
   int grid = (int)((tot + 255) / 256 < 152ull * 16 ? (tot + 255) / 256 : 152ull * 16);
   if (grid < 1) grid = 1;
   k_load64<<<grid, 256, 0, st>>>(p, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag32(const StepParams32& p, int grid, cudaStream_t st) {
+  k_diag32<<<grid, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 

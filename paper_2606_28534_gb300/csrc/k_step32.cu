@@ -161,10 +161,12 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
         *reinterpret_cast<float4*>(A.vy + i0) = make_float4(vy[0], vy[1], vy[2], vy[3]);
         *reinterpret_cast<float4*>(A.vz + i0) = make_float4(vz[0], vz[1], vz[2], vz[3]);
       }
-      // kinetic energy after the push; a candidate's is added after its collision
+      // kinetic energy after the push (steps that sum it); a candidate's is added after its collision
+      if (P.sum_ke) {
 #pragma unroll
-      for (int k = 0; k < PIC_PPT; ++k)
-        if (c[k] != PIC_DEAD_CELL && !((cand >> k) & 1u)) ke_lane += ke_fx32(vx[k], vy[k], vz[k], K.mass);
+        for (int k = 0; k < PIC_PPT; ++k)
+          if (c[k] != PIC_DEAD_CELL && !((cand >> k) & 1u)) ke_lane += ke_fx32(vx[k], vy[k], vz[k], K.mass);
+      }
       // queue the surviving candidates (their collision changes v only, not the deposit)
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) {

@@ -125,6 +125,7 @@ struct StepParams32 {
   Ctl* ctl;
   Phys ph;
   unsigned long long step;
+  unsigned int sum_ke;  // sum the kinetic energy of the particles alive after this step
 };
 
 struct StepParams64 {
@@ -375,6 +376,7 @@ cudaError_t launch_sort32(Species32 src[2], Species32 dst[2], unsigned int* cnt[
                           unsigned int* cursor[2], const unsigned long long cap[2], Ctl* ctl, int N,
                           int grid, cudaStream_t st);
 cudaError_t launch_diag64(const StepParams64& p, int grid, cudaStream_t st);
+cudaError_t launch_diag32(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_diag_grid(const long long* R0, const long long* R1, int sign0, int sign1, const double* E, int N,
                              double dx, Ctl* ctl, cudaStream_t st);
 cudaError_t launch_restore32(const int* cell, const double* frac, const double* vx, const double* vy, const double* vz,

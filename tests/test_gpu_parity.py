@@ -214,8 +214,9 @@ def test_step_kinetic_energy_is_the_exact_fixed_point_sum():
     # The FP32 step sums 0.5 m v^2 of every particle alive after the step (pushed, collided, born,
     # injected) in 2^-24 fixed point with each FP32 rounding spelled out; recomputing that sum
     # from the snapshot must give the same bits.
-    for p in (W.variant(W.SMALL_COLL), W.SMALL_C3):
+    for p, every in ((W.variant(W.SMALL_COLL), 1), (W.SMALL_C3, 1), (W.SMALL_C3, 0)):
         g = pic.Simulation(p)
+        g.set_diag_interval(every)  # 1: summed in the step; 0: summed by pic_diag
         g.step(7)
         d = g.diag()
         sp = snapfmt.parse(g.snapshot())["species"]
@@ -226,6 +227,22 @@ def test_step_kinetic_energy_is_the_exact_fixed_point_sum():
             fx = int(np.rint(e.astype(np.float64)).astype(np.uint64).sum(dtype=np.uint64))
             w = (p["L"] / p["ncells"]) / p["ppc"][s]
             assert d["ke"][s] == float(fx) * (1.0 / 16777216.0) * w
+
+
+def test_diag_interval_changes_no_bit_of_the_diagnostics():
+    p = W.variant(W.SMALL_COLL, sort_interval=4)
+    sims = [pic.Simulation(p) for _ in range(3)]
+    for g, every in zip(sims, (0, 1, 3)):
+        g.set_diag_interval(every)
+    for _ in range(9):
+        for g in sims:
+            g.step(1)
+        d = [g.diag() for g in sims]
+        assert d[0] == d[1] == d[2]
+    with pytest.raises(pic.PicError):
+        sims[0].set_diag_interval(-1)
+    for g in sims:
+        g.close()
 
 
 def test_charge_and_accounting_invariants_every_step():
