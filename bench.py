@@ -31,7 +31,6 @@ from paper_2606_28534_gb300 import workloads as W  # noqa: E402
 METRIC = "particle-steps/s & HBM roofline %, FP32/batched vs plain FP64 grid, 1 GB300"
 BYTES_STEP_KERNEL = 48  # algorithmic bytes per particle per step kernel: 28 read + 20 written
 BYTES_SORT = 56         # per particle per sort: 28 read + 28 written
-CTL_BYTES = 792         # device-to-host bytes of one pic_diag: the control block (counters, partial sums)
 
 
 def _peaks():
@@ -406,7 +405,8 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         barrier()
         et = allmax(t2 - t0)
         e2e = {"value": allsum(dsum) / et, "unit": "particle-steps/s",
-               "h2d_bytes_per_step": int(pinned.numel() / ek), "d2h_bytes_per_step": CTL_BYTES,
+               "h2d_bytes_per_step": int(pinned.numel() / ek),
+               "d2h_bytes_per_step": int(pic.lib().pic_diag_bytes()),
                "steps": ek, "restore_s": round(t1 - t0, 4), "ms_per_step": round(1e3 * (t2 - t1) / ek, 4),
                "what": "pic_restore from a checkpoint blob in pinned host memory, then per step "
                        "pic_step(1) and pic_diag (device-to-host read of the control block)"}

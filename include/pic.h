@@ -169,6 +169,10 @@ int pic_restore(pic_handle* h, const void* buf, size_t len);
 /* Diagnostics; synchronises the stream and reduces on the device. */
 int pic_diag(pic_handle* h, pic_diag_t* out);
 
+/* Bytes one pic_diag copies from the device to the host (the control block of counters and
+ * partial sums): the device-to-host traffic of reading the diagnostics. */
+size_t pic_diag_bytes(void);
+
 /* Copy the grid to host buffers of nnodes = N + 1 entries each (any may be NULL):
  * R: 2 x (N+1) int64 deposits (2^-32 particle units), rho, phi: FP64, E: FP32 node field as
  * seen by the particles.  Synchronises the stream. */

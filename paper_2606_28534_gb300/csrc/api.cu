@@ -216,6 +216,11 @@ StepParams32 params32(pic_handle* h) {
   P.ph = h->ph;
   P.step = h->step;
   P.sum_ke = 0u;
+  P.scatter = 0u;
+  for (int s = 0; s < 2; ++s) {
+    P.src[s] = P.sp[s];
+    P.cursor[s] = h->cursor[s];
+  }
   return P;
 }
 
@@ -319,6 +324,7 @@ int refresh_field(pic_handle* h) {
   prof_end(h, &e);
   h->ph = saved;
   h->ke_valid = !h->plain;
+  h->pending_scatter = false;  // the full sort below replaces any pending one
   CK(err);
   prof_begin(h, K_FIELD, &e);
   CK(launch_field(field_params(h, !h->plain, false), h->st));
@@ -880,19 +886,28 @@ int pic_step(pic_handle* h, int32_t n) {
   if (!h || n < 0) return PIC_EINVAL;
   for (int32_t k = 0; k < n; ++k) {
     const bool sort_now = !h->plain && (h->step % (unsigned long long)h->cfg.sort_interval) == 0ull;
+    const bool scatter = !h->plain && h->pending_scatter;
     EvPair e;
     if (!h->plain) {
       StepParams32 P = params32(h);
       const bool sum_ke = h->ke_every > 0 && ((h->step + 1) % (unsigned long long)h->ke_every) == 0ull;
       P.sum_ke = sum_ke ? 1u : 0u;
       h->ke_valid = sum_ke;
+      if (scatter) {  // the step after a sort: read buffer cur, fill buffer 1 - cur in sorted order
+        for (int s = 0; s < 2; ++s) P.sp[s] = h->a32[1 - h->cur][s];
+        P.scatter = 1u;
+      }
       prof_begin(h, K_STEP, &e);
-      CK(launch_step32(P, h->grid_step, h->st));
+      CK(scatter ? launch_step32_scatter(P, h->grid_step, h->st) : launch_step32(P, h->grid_step, h->st));
       prof_end(h, &e);
       if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
         prof_begin(h, K_SOURCE, &e);
         CK(launch_source32(P, h->st));
         prof_end(h, &e);
+      }
+      if (scatter) {
+        h->cur = 1 - h->cur;
+        h->pending_scatter = false;
       }
     } else {
       const StepParams64 P = params64(h);
@@ -906,20 +921,26 @@ int pic_step(pic_handle* h, int32_t n) {
       }
     }
     prof_begin(h, K_FIELD, &e);
-    CK(launch_field(field_params(h, sort_now, true), h->st));
+    PoissonParams F = field_params(h, sort_now, true);
+    F.scatter_step = scatter ? 1 : 0;
+    CK(launch_field(F, h->st));
     prof_end(h, &e);
     if (sort_now) {
+      // the counting sort: cursors from this step's counts now; the particles move during the next
+      // step (k_step32 in scatter mode), which saves a read and a write of every particle
       prof_begin(h, K_SORT, &e);
       Species32 src[2] = {h->a32[h->cur][0], h->a32[h->cur][1]};
       Species32 dst[2] = {h->a32[1 - h->cur][0], h->a32[1 - h->cur][1]};
-      CK(launch_sort32(src, dst, h->cnt, h->cursor, h->cap, h->ctl, h->N, h->grid_sort, h->st));
+      CK(launch_sort_scan32(src, dst, h->cnt, h->cursor, h->cap, h->ctl, h->N, h->st));
       prof_end(h, &e);
-      h->cur = 1 - h->cur;
+      h->pending_scatter = true;
     }
     h->step += 1;
   }
   return PIC_OK;
 }
+
+size_t pic_diag_bytes(void) { return sizeof(Ctl); }
 
 int pic_set_diag_interval(pic_handle* h, int32_t every) {
   if (!h || every < 0) return PIC_EINVAL;

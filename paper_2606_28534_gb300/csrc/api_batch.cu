@@ -233,6 +233,7 @@ int upload_tables(pic_batch* b) {
       }
       so.ctl = h->ctl;
       so.N = h->N;
+      so.defer = 0;
       h->cur = keep_cur;
     }
     CKB(cudaMemcpy(b->d_sims[p], sims.data(), sizeof(StepParams32) * n, cudaMemcpyHostToDevice));

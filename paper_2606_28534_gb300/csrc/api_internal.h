@@ -48,6 +48,7 @@ struct pic_handle {
   unsigned long long step = 0;
   int grid_step = 0, grid_sort = 0, grid_diag = 0;
   int ke_every = 0;       // the step sums the kinetic energy on every ke_every-th step (0: never)
+  bool pending_scatter = false;  // a sort scan ran: the next step moves the particles to buffer 1 - cur
   bool ke_valid = false;  // the last completed step (or refresh) summed it (ke_last holds it)
   bool prof = false;
   std::vector<picx::EvPair> ev;

@@ -81,7 +81,11 @@ __device__ __forceinline__ long long node_R(const PoissonParams& P, int s, int j
 // particle-array bookkeeping after the deposits of a step (one thread)
 __device__ void bookkeeping(const PoissonParams& P) {
   Ctl* g = P.ctl;
-  const unsigned long long c0 = g->n_cur[0], c1 = g->n_cur[1], b0 = g->n_born[0], b1 = g->n_born[1];
+  // after a scattering step the particles (and this step's births) are in the buffer the sort
+  // scan sized: its extent is sort_new
+  const unsigned long long c0 = P.scatter_step ? g->sort_new[0] : g->n_cur[0];
+  const unsigned long long c1 = P.scatter_step ? g->sort_new[1] : g->n_cur[1];
+  const unsigned long long b0 = g->n_born[0], b1 = g->n_born[1];
   const unsigned long long l0 = g->n_live[0], l1 = g->n_live[1], mark = g->live_mark;
   if (P.count_step) g->particle_steps += mark;
   g->live_mark = l0 + l1;

@@ -109,7 +109,10 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(1024, 1
     }
     int* dcell = s ? P.dst[1].cell : P.dst[0].cell;
     for (unsigned long long i = total; i < pad; ++i) dcell[i] = PIC_DEAD_CELL;
-    g->n_cur[s] = pad;
+    if (P.defer)
+      g->sort_new[s] = pad;
+    else
+      g->n_cur[s] = pad;
   }
   cluster.sync();  // keep the CTA totals alive until every rank has read them
 }
@@ -256,11 +259,31 @@ cudaError_t launch_sort32(Species32 src[2], Species32 dst[2], unsigned int* cnt[
   }
   P.ctl = ctl;
   P.N = N;
+  P.defer = 0;
   const int seg = (N + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
   scan_attrs();
   k_sort_scan<false><<<2 * PIC_FIELD_CTAS, 1024, sizeof(unsigned int) * (size_t)seg, st>>>(P, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sort_scatter<<<grid, PIC_TPB, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_scan32(Species32 src[2], Species32 dst[2], unsigned int* cnt[2], unsigned int* cursor[2],
+                               const unsigned long long cap[2], Ctl* ctl, int N, cudaStream_t st) {
+  SortParams P;
+  for (int s = 0; s < 2; ++s) {
+    P.cap[s] = cap[s];
+    P.src[s] = src[s];
+    P.dst[s] = dst[s];
+    P.cnt[s] = cnt[s];
+    P.cursor[s] = cursor[s];
+  }
+  P.ctl = ctl;
+  P.N = N;
+  P.defer = 1;
+  const int seg = (N + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
+  scan_attrs();
+  k_sort_scan<false><<<2 * PIC_FIELD_CTAS, 1024, sizeof(unsigned int) * (size_t)seg, st>>>(P, nullptr);
   return cudaGetLastError();
 }

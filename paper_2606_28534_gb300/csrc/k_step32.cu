@@ -28,6 +28,13 @@ constexpr size_t STEP_SMEM = (size_t)WARPS * (NSTAGE * STAGE_BYTES + QCAP * 8 + 
 // warps of the grid; the warp's next chunk is already streaming into shared memory (TMA bulk copy
 // completing on an mbarrier) while it computes the current one.  No block-wide barrier inside the
 // particle loop.
+// SCATTER: the step after a sort step.  The sort scan has turned the per-cell counts of the
+// previous deposit into write cursors; this step reads the particles from the buffer the sort step
+// left (P.src) and writes each one, pushed and collided, to its slot in the other buffer (P.sp):
+// slots of one cell are claimed with one atomic per (warp, cell) group, so that a warp's writes
+// stay contiguous.  A particle absorbed in this step leaves a dead slot; births are appended past
+// the filled buffer's extent (sort_new).  This replaces the separate scatter pass of the sort.
+template <bool SCATTER>
 __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_constant__ StepParams32 P) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ BlockCounters bc;
@@ -49,6 +56,9 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
   unsigned parity = 0u;  // bit st: phase parity of stage st
   bool failed = false;   // a bounded wait gave up
   const unsigned long long ncur0 = P.ctl->n_cur[0], ncur1 = P.ctl->n_cur[1];
+  // births go past the extent of the buffer being written
+  const unsigned long long nb0 = SCATTER ? P.ctl->sort_new[0] : ncur0;
+  const unsigned long long nb1 = SCATTER ? P.ctl->sort_new[1] : ncur1;
   const unsigned gw = blockIdx.x * WARPS + wib;  // particle indices and chunk counts fit 32 bits
   const unsigned nw = gridDim.x * WARPS;
   const Phys& ph = P.ph;
@@ -59,7 +69,8 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
     // species arrays and constants are read from the kernel parameters where they are used
     const unsigned ncur = (unsigned)(s ? ncur1 : ncur0);
     const unsigned chunks = (ncur + CHUNK - 1) / CHUNK;
-    const Species32& A = P.sp[s];
+    const Species32& A = P.sp[s];                   // written
+    const Species32& Asrc = SCATTER ? P.src[s] : P.sp[s];  // read
     const SpConst& K = ph.sp[s];
     const bool moves = (ph.push_mask >> s) & 1u;
     const bool collides = moves && (s == 0 ? (ph.coll_mask & 7u) != 0u : (ph.coll_mask & 8u) != 0u);
@@ -71,7 +82,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
 #pragma unroll
       for (int st = 0; st < NSTAGE; ++st) {
         const unsigned t = gw + st * nw;
-        if (t < chunks) stage_issue(A, t, ncur, stage + st * STAGE_BYTES, bar + st);
+        if (t < chunks) stage_issue(Asrc, t, ncur, stage + st * STAGE_BYTES, bar + st);
       }
     }
     int st = 0;
@@ -118,17 +129,35 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
         e2[k] = make_float2(0.f, 0.f);
         if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL) e2[k] = __ldg(P.E2 + c[k]);
       }
+      // scatter: claim each live particle's slot in its cell (four atomics in flight)
+      unsigned slot[PIC_PPT];
+      if (SCATTER) {
+        unsigned peers[PIC_PPT], base[PIC_PPT];
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          const bool live = c[k] != PIC_DEAD_CELL;
+          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? c[k] : -1);
+          base[k] = 0u;
+          if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(P.cursor[s] + c[k], (unsigned)__popc(peers[k]));
+        }
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k)
+          slot[k] = __shfl_sync(0xFFFFFFFFu, base[k], __ffs(peers[k]) - 1) + (unsigned)__popc(peers[k] & below);
+      }
       // the stage is read: refill it with the chunk NSTAGE steps ahead
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
         const unsigned tn = t + NSTAGE * nw;
-        if (tn < chunks) stage_issue(A, tn, ncur, stage + st * STAGE_BYTES, bar + st);
+        if (tn < chunks) stage_issue(Asrc, tn, ncur, stage + st * STAGE_BYTES, bar + st);
       }
       st = st + 1 == NSTAGE ? 0 : st + 1;
 
       // null-collision candidates: the draw depends only on (id, step), so the four Philox
       // blocks are independent instruction streams
+      unsigned live0 = 0u;  // live at the start of the step (scatter: owns a slot)
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k) live0 |= c[k] != PIC_DEAD_CELL ? (1u << k) : 0u;
       unsigned cand = 0u;
       if (collides) {
 #pragma unroll
@@ -154,7 +183,25 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
           c[k] = cn;
         }
       }
-      if (have && moves) {
+      if (SCATTER) {
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          if (!((live0 >> k) & 1u)) continue;
+          const unsigned j = slot[k];
+          if (j >= P.cap[s]) {  // only reachable if the counts disagree with the arrays
+            atomicOr(&P.ctl->error, ERR_DEVICE);
+            c[k] = PIC_DEAD_CELL;
+            continue;
+          }
+          A.cell[j] = c[k];
+          if (c[k] == PIC_DEAD_CELL) continue;  // absorbed in this step: a dead slot
+          A.frac[j] = f[k];
+          A.vx[j] = vx[k];
+          A.vy[j] = vy[k];
+          A.vz[j] = vz[k];
+          A.id[j] = id[k];
+        }
+      } else if (have && moves) {
         *reinterpret_cast<int4*>(A.cell + i0) = make_int4(c[0], c[1], c[2], c[3]);
         *reinterpret_cast<float4*>(A.frac + i0) = make_float4(f[0], f[1], f[2], f[3]);
         *reinterpret_cast<float4*>(A.vx + i0) = make_float4(vx[0], vx[1], vx[2], vx[3]);
@@ -172,7 +219,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
       for (int k = 0; k < PIC_PPT; ++k) {
         const bool qk = ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL;
         const unsigned b = __ballot_sync(0xFFFFFFFFu, qk);
-        if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(i0 + k);
+        if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(SCATTER ? slot[k] : i0 + k);
         qn += __popc(b);
       }
 
@@ -200,7 +247,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
       for (int k = 0; k < PIC_PPT; ++k) warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] : -1, rn[k], rsw[k]);
 
       if (qn > QFLUSH) {
-        flush_queue(P, q, qn, ncur0, ncur1, &bc);
+        flush_queue(P, q, qn, nb0, nb1, &bc);
         qn = 0;
       }
     }
@@ -214,7 +261,7 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
     if (lane == 0) atomicOr(&P.ctl->error, ERR_TIMEOUT);
     for (int k = 0; k < NSTAGE; ++k) mbar_wait_bounded(bar + k, (parity >> k) & 1u);
   } else if (qn) {
-    flush_queue(P, q, qn, ncur0, ncur1, &bc);
+    flush_queue(P, q, qn, nb0, nb1, &bc);
   }
 
 // ---- flush the block counters ----------------------------------------------------------------
@@ -227,7 +274,9 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
 __global__ void __launch_bounds__(256) k_source32(const StepParams32 P) {
   const Phys& ph = P.ph;
   const unsigned long long K = P.ctl->src_K;
-  const unsigned long long n0 = P.ctl->n_cur[0], n1 = P.ctl->n_cur[1];
+  // births go past the extent of the buffer the step filled
+  const unsigned long long n0 = P.scatter ? P.ctl->sort_new[0] : P.ctl->n_cur[0];
+  const unsigned long long n1 = P.scatter ? P.ctl->sort_new[1] : P.ctl->n_cur[1];
   __shared__ unsigned int added[2];
   if (threadIdx.x < 2) added[threadIdx.x] = 0u;
   __syncthreads();
@@ -279,22 +328,30 @@ static void step32_attrs();
 
 int occupancy_step32() {
   step32_attrs();
-  int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step32, PIC_TPB, STEP_SMEM) != cudaSuccess || b < 1) b = 1;
-  return b;
+  int b = 0, c = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step32<false>, PIC_TPB, STEP_SMEM) != cudaSuccess || b < 1) b = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_step32<true>, PIC_TPB, STEP_SMEM) != cudaSuccess || c < 1) c = 1;
+  return b < c ? b : c;
 }
 
 static void step32_attrs() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_step32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STEP_SMEM);
+    cudaFuncSetAttribute(k_step32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STEP_SMEM);
+    cudaFuncSetAttribute(k_step32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STEP_SMEM);
     done = true;
   }
 }
 
 cudaError_t launch_step32(const StepParams32& p, int grid, cudaStream_t st) {
   step32_attrs();
-  k_step32<<<grid, PIC_TPB, STEP_SMEM, st>>>(p);
+  k_step32<false><<<grid, PIC_TPB, STEP_SMEM, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step32_scatter(const StepParams32& p, int grid, cudaStream_t st) {
+  step32_attrs();
+  k_step32<true><<<grid, PIC_TPB, STEP_SMEM, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,7 @@ struct Ctl {
   unsigned long long wall_energy_fx[2];  // sum of 0.5 m v^2 of absorbed particles, 2^-24 units
   unsigned long long src_K;              // ions absorbed in the current step
   unsigned long long sort_total[2];
+  unsigned long long sort_new[2];        // deferred sort: extent of the buffer the next step fills
   unsigned int sort_done;                // blocks of the scatter that finished
   unsigned int error;
   unsigned long long ke_fx[2];           // diag scratch: sum 0.5 m v^2, 2^-24 units
@@ -125,7 +126,10 @@ struct StepParams32 {
   Ctl* ctl;
   Phys ph;
   unsigned long long step;
-  unsigned int sum_ke;  // sum the kinetic energy of the particles alive after this step
+  unsigned int sum_ke;   // sum the kinetic energy of the particles alive after this step
+  unsigned int scatter;  // the step after a sort: read src, write each particle to its sorted slot in sp
+  Species32 src[2];      // scatter: the buffer the sort step left (sp: the buffer being filled)
+  unsigned int* cursor[2];  // scatter: per-cell write cursors of the sort scan
 };
 
 struct StepParams64 {
@@ -250,6 +254,7 @@ struct PoissonParams {
   Species64 pad64[2];
   unsigned long long cap[2];
   int plain;
+  int scatter_step;  // bookkeeping after a scattering step: the extent of the filled buffer is sort_new
 };
 
 struct SortParams {
@@ -259,6 +264,7 @@ struct SortParams {
   unsigned long long cap[2];
   Ctl* ctl;
   int N;
+  int defer;  // 1: record the new extent in sort_new and leave n_cur (the next step scatters)
 };
 
 // ---- ensembles of simulations (one batch: many independent runs advanced together) ----------
@@ -375,6 +381,10 @@ cudaError_t launch_load64(const StepParams64& p, const unsigned long long n[2], 
 cudaError_t launch_sort32(Species32 src[2], Species32 dst[2], unsigned int* cnt[2],
                           unsigned int* cursor[2], const unsigned long long cap[2], Ctl* ctl, int N,
                           int grid, cudaStream_t st);
+// the scan alone, deferred: the next step kernel (scatter mode) moves the particles
+cudaError_t launch_sort_scan32(Species32 src[2], Species32 dst[2], unsigned int* cnt[2], unsigned int* cursor[2],
+                               const unsigned long long cap[2], Ctl* ctl, int N, cudaStream_t st);
+cudaError_t launch_step32_scatter(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_diag64(const StepParams64& p, int grid, cudaStream_t st);
 cudaError_t launch_diag32(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_diag_grid(const long long* R0, const long long* R1, int sign0, int sign1, const double* E, int N,

@@ -62,7 +62,7 @@ class PicDiag(C.Structure):
 #: every entry point of include/pic.h
 SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapshot", "pic_restore",
            "pic_diag", "pic_get_field", "pic_profile", "pic_kernel_times", "pic_free",
-           "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc", "pic_set_diag_interval",
+           "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc", "pic_set_diag_interval", "pic_diag_bytes",
            "pic_batch_variant_count", "pic_batch_variant_name", "pic_batch_workspace_size",
            "pic_batch_init", "pic_batch_set_tuning", "pic_batch_get_tuning", "pic_batch_step",
            "pic_batch_sync", "pic_batch_diag", "pic_batch_snapshot", "pic_batch_restore",
@@ -91,6 +91,8 @@ def lib():
         L.pic_step.argtypes = [V, C.c_int32]
         L.pic_sync.argtypes = [V]
         L.pic_set_diag_interval.argtypes = [V, C.c_int32]
+        L.pic_diag_bytes.argtypes = []
+        L.pic_diag_bytes.restype = C.c_size_t
         L.pic_snapshot.argtypes = [V, V, C.c_size_t, P(C.c_size_t)]
         L.pic_restore.argtypes = [V, V, C.c_size_t]
         L.pic_diag.argtypes = [V, P(PicDiag)]
