@@ -30,7 +30,11 @@ from paper_2606_28534_gb300 import workloads as W  # noqa: E402
 
 METRIC = "particle-steps/s & HBM roofline %, FP32/batched vs plain FP64 grid, 1 GB300"
 BYTES_STEP_KERNEL = 48  # algorithmic bytes per particle per step kernel: 28 read + 20 written
-BYTES_SORT = 56         # per particle per sort: 28 read + 28 written
+BYTES_SCATTER_EXTRA = 8  # the step after a sort writes each particle to a new slot: + its 8-byte id
+# DRAM bytes per particle of one launch, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of these kernels on the 12.6M-particle profiling case (c3p), scaled by
+# particles to a full launch: the ordinary step and the step after a sort
+TRAFFIC_STEP, TRAFFIC_SCATTER = 49.07, 57.06
 
 
 def _peaks():
@@ -350,9 +354,21 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
     value = ps_all / (ms_max / 1000.0)
 
     peak, peak_kind = _peaks()
+    # the dominant kernel: the ordinary step (48 B per particle); the step after each sort, which
+    # also moves every particle to its sorted slot (56 B per particle), is reported beside it
+    n_launch = kt["step"]["launches"] + kt["step_scatter"]["launches"]
+    per_launch_particles = ps / max(1, n_launch)
     step_ms = kt["step"]["ms"] / max(1, kt["step"]["launches"])
-    bytes_per_launch = BYTES_STEP_KERNEL * ps / max(1, kt["step"]["launches"])
+    bytes_per_launch = BYTES_STEP_KERNEL * per_launch_particles
+    traffic = TRAFFIC_STEP * per_launch_particles
     achieved = bytes_per_launch / (step_ms / 1000.0) / 1e9
+    sc_ms = kt["step_scatter"]["ms"] / max(1, kt["step_scatter"]["launches"])
+    sc_bytes = (BYTES_STEP_KERNEL + BYTES_SCATTER_EXTRA) * per_launch_particles
+    scatter_step = {"kernel": "k_step32 (scatter)", "launches": kt["step_scatter"]["launches"],
+                    "avg_launch_ms": sc_ms, "bytes_per_launch": sc_bytes,
+                    "achieved": sc_bytes / (sc_ms / 1000.0) / 1e9 if sc_ms else None,
+                    "frac": sc_bytes / (sc_ms / 1000.0) / 1e9 / peak if sc_ms else None,
+                    "traffic": TRAFFIC_SCATTER * per_launch_particles}
     kernel_shares = {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in kt.values())), 4)
                      for k, v in kt.items() if v["launches"]}
 
@@ -433,9 +449,10 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
                    "diagnostics": "kinetic energy summed by pic_diag on request (after the timed "
                                   "steps); e2e sums it inside every step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_step32",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_step32",
                      "peak_kind": peak_kind,
-                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": step_ms},
+                     "bytes_per_launch": bytes_per_launch, "bytes_per_particle": BYTES_STEP_KERNEL,
+                     "avg_launch_ms": step_ms, "scatter_step": scatter_step},
         "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in kt.items()
                     if v["launches"]},
         "kernel_shares": kernel_shares,

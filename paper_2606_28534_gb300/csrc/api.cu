@@ -14,7 +14,8 @@
 
 namespace picx {
 
-const char* const kKindNames[PIC_KERNEL_KINDS] = {"step", "source", "field", "sort", "load", "diag", "plan", ""};
+const char* const kKindNames[PIC_KERNEL_KINDS] = {"step", "source", "field", "sort", "load", "diag", "plan",
+                                                   "step_scatter"};
 
 
 // ---------------------------------------------------------------------------------------------
@@ -862,6 +863,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms <= 0) sms = 152;
   h->grid_step = sms * (h->plain ? occupancy_step64() : occupancy_step32());
+  h->grid_scatter = h->plain ? 0 : sms * occupancy_step32(true);
   h->grid_sort = sms * 16;
   h->grid_diag = sms * 8;
   *out = h;
@@ -897,8 +899,8 @@ int pic_step(pic_handle* h, int32_t n) {
         for (int s = 0; s < 2; ++s) P.sp[s] = h->a32[1 - h->cur][s];
         P.scatter = 1u;
       }
-      prof_begin(h, K_STEP, &e);
-      CK(scatter ? launch_step32_scatter(P, h->grid_step, h->st) : launch_step32(P, h->grid_step, h->st));
+      prof_begin(h, scatter ? K_STEP_SCATTER : K_STEP, &e);
+      CK(scatter ? launch_step32_scatter(P, h->grid_scatter, h->st) : launch_step32(P, h->grid_step, h->st));
       prof_end(h, &e);
       if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
         prof_begin(h, K_SOURCE, &e);

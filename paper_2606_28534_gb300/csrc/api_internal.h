@@ -7,12 +7,12 @@
 #include "../../include/pic.h"
 #include "pic_internal.cuh"
 
-int occupancy_step32();
+int occupancy_step32(bool scatter = false);
 int occupancy_step64();
 
 namespace picx {
 
-enum Kind { K_STEP = 0, K_SOURCE, K_FIELD, K_SORT, K_LOAD, K_DIAG, K_PLAN, K_KINDS };
+enum Kind { K_STEP = 0, K_SOURCE, K_FIELD, K_SORT, K_LOAD, K_DIAG, K_PLAN, K_STEP_SCATTER, K_KINDS };
 extern const char* const kKindNames[PIC_KERNEL_KINDS];
 
 struct EvPair {
@@ -46,7 +46,7 @@ struct pic_handle {
   size_t stage_bytes = 0;
   Phys ph;
   unsigned long long step = 0;
-  int grid_step = 0, grid_sort = 0, grid_diag = 0;
+  int grid_step = 0, grid_sort = 0, grid_diag = 0, grid_scatter = 0;
   int ke_every = 0;       // the step sums the kinetic energy on every ke_every-th step (0: never)
   bool pending_scatter = false;  // a sort scan ran: the next step moves the particles to buffer 1 - cur
   bool ke_valid = false;  // the last completed step (or refresh) summed it (ke_last holds it)

@@ -24,8 +24,9 @@ constexpr int NSTAGE = 2;   // chunks in flight per warp (TMA double buffer)
 constexpr int WARPS = PIC_TPB / 32;
 constexpr size_t STEP_SMEM = (size_t)WARPS * (NSTAGE * STAGE_BYTES + QCAP * 8 + NSTAGE * 8);
 
-// One warp handles chunks of 32 x PIC_PPT consecutive particles of one species, strided over all
-// warps of the grid; the warp's next chunk is already streaming into shared memory (TMA bulk copy
+// One warp handles chunks of 32 x PIC_PPT consecutive particles of one species (a contiguous run
+// of chunks per warp; strided over the warps of the grid in the step after a sort); the warp's next
+// chunk is already streaming into shared memory (TMA bulk copy
 // completing on an mbarrier) while it computes the current one.  No block-wide barrier inside the
 // particle loop.
 // SCATTER: the step after a sort step.  The sort scan has turned the per-cell counts of the
@@ -34,8 +35,13 @@ constexpr size_t STEP_SMEM = (size_t)WARPS * (NSTAGE * STAGE_BYTES + QCAP * 8 + 
 // slots of one cell are claimed with one atomic per (warp, cell) group, so that a warp's writes
 // stay contiguous.  A particle absorbed in this step leaves a dead slot; births are appended past
 // the filled buffer's extent (sort_new).  This replaces the separate scatter pass of the sort.
+#ifndef PIC_SCATTER_MINB
+#define PIC_SCATTER_MINB 2  // resident CTAs per SM of the step after a sort (120 registers: no spills)
+#endif
+
 template <bool SCATTER>
-__global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_constant__ StepParams32 P) {
+__global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP_MINB)
+    k_step32(const __grid_constant__ StepParams32 P) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ BlockCounters bc;
 
@@ -75,19 +81,28 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
     const bool moves = (ph.push_mask >> s) & 1u;
     const bool collides = moves && (s == 0 ? (ph.coll_mask & 7u) != 0u : (ph.coll_mask & 8u) != 0u);
     const unsigned long long tag = (unsigned long long)s << 63;
+    // Chunk schedule.  An ordinary step gives each warp a contiguous run of chunks: concurrent warps
+    // then work in different cells, so that the deposit's reductions from different warps rarely
+    // meet on one address (on the grid stride ~50 warps deposit into one dense cell at a time).  The
+    // step after a sort keeps the grid stride: its cursor claims return values, and many warps in
+    // one cell overlap their latencies.
+    const unsigned per = SCATTER ? 0u : (chunks + nw - 1) / nw;
+    const unsigned t_first = SCATTER ? gw : min(chunks, gw * per);
+    const unsigned t_end = SCATTER ? chunks : min(chunks, t_first + per);
+    const unsigned t_inc = SCATTER ? nw : 1u;
     unsigned long long ke_lane = 0ull;  // kinetic energy of this lane's particles that stay live
 
     // prologue: the warp's first NSTAGE chunks
     if (lane == 0) {
 #pragma unroll
       for (int st = 0; st < NSTAGE; ++st) {
-        const unsigned t = gw + st * nw;
-        if (t < chunks) stage_issue(Asrc, t, ncur, stage + st * STAGE_BYTES, bar + st);
+        const unsigned t = t_first + st * t_inc;
+        if (t < t_end) stage_issue(Asrc, t, ncur, stage + st * STAGE_BYTES, bar + st);
       }
     }
     int st = 0;
 #pragma unroll 1
-    for (unsigned t = gw; t < chunks; t += nw) {
+    for (unsigned t = t_first; t < t_end; t += t_inc) {
       if (!__all_sync(0xFFFFFFFFu, mbar_wait_bounded(bar + st, (parity >> st) & 1u))) {
         failed = true;
         break;
@@ -148,8 +163,8 @@ __global__ void __launch_bounds__(PIC_TPB, PIC_STEP_MINB) k_step32(const __grid_
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        const unsigned tn = t + NSTAGE * nw;
-        if (tn < chunks) stage_issue(Asrc, tn, ncur, stage + st * STAGE_BYTES, bar + st);
+        const unsigned tn = t + NSTAGE * t_inc;
+        if (tn < t_end) stage_issue(Asrc, tn, ncur, stage + st * STAGE_BYTES, bar + st);
       }
       st = st + 1 == NSTAGE ? 0 : st + 1;
 
@@ -326,12 +341,14 @@ __global__ void __launch_bounds__(256) k_source32(const StepParams32 P) {
 
 static void step32_attrs();
 
-int occupancy_step32() {
+int occupancy_step32(bool scatter) {
   step32_attrs();
-  int b = 0, c = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step32<false>, PIC_TPB, STEP_SMEM) != cudaSuccess || b < 1) b = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_step32<true>, PIC_TPB, STEP_SMEM) != cudaSuccess || c < 1) c = 1;
-  return b < c ? b : c;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, scatter ? k_step32<true> : k_step32<false>, PIC_TPB,
+                                                    STEP_SMEM) != cudaSuccess ||
+      b < 1)
+    b = 1;
+  return b;
 }
 
 static void step32_attrs() {
