@@ -377,3 +377,41 @@ def test_full_size_sampled_load_and_invariants(name):
         lost = d["wall_hits"][s][0] + d["wall_hits"][s][1]
         assert d["n"][s] == n0[s] + d["births"][s] - lost + d["source_pairs"]
     assert d["coll"][4] > 0 and d["coll"][0] > 0
+
+
+# ---- edge cases ---------------------------------------------------------------------------------
+def test_largest_grid_steps_and_matches_the_oracle():
+    # the largest grid the FP32 path takes (8 CTAs of the field cluster x 24576 nodes, minus one)
+    N = 8 * 24576 - 1
+    p = W.variant(W.SMALL_C2, ncells=N, L=float(N), ppc=(1, 1), sort_interval=2)
+    blob = _oracle_blob_fp32(p, steps=2)
+    o = O.OracleSim(p)
+    assert o.restore(blob) == 0
+    g = pic.Simulation(p)
+    assert g.restore(blob) == 0
+    o.step(1)
+    g.step(1)
+    stepcheck.assert_one_step(p, blob, o.diag(), o.snapshot(), o.fields(), g.diag(), g.snapshot(), g.fields())
+    g.step(5)  # across a sort and the step that moves the particles
+    d = g.diag()
+    assert d["net_charge_units"] == 2**32 * (d["n"][1] - d["n"][0])
+    with pytest.raises(pic.PicError):
+        pic.Simulation(W.variant(p, ncells=N + 1, L=float(N + 1)))
+
+
+def test_species_that_empty_out_keep_stepping():
+    # two cells, hot particles (seed chosen so that every particle reaches a wall within five
+    # steps): the run goes on with empty species (zero extents), through sorts, and agrees with the
+    # oracle throughout
+    p = W.variant(W.SMALL_C1, ncells=2, L=2.0, ppc=(3, 3), T=(1e4, 1e6), sort_interval=2, coll_mask=0,
+                  seed=3)
+    o = O.OracleSim(p)
+    g = pic.Simulation(p)
+    for _ in range(12):
+        o.step(1)
+        g.step(1)
+        do, dg = o.diag(), g.diag()
+        assert dg["n"] == do["n"] and dg["wall_hits"] == do["wall_hits"]
+        assert dg["net_charge_units"] == 2**32 * (dg["n"][1] - dg["n"][0])
+    assert dg["n"] == [0, 0]
+    assert g.snapshot() == snapfmt.round_to_fp32(o.snapshot())

@@ -1,0 +1,94 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake -- a dropped term, a wrong sign, a transposed operand, a wrong index
+or constant -- in a copy of the oracle's C sources, builds that copy, and runs the oracle's pin
+tests against it (PIC_ORACLE_LIB points the wrapper at the copy).  The case passes when a pin
+fails.  Nothing here touches the GPU or the oracle the other tests use.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+PINS_MAIN = ["tests/test_oracle_pins_numerics.py", "tests/test_oracle_pins_physics.py"]
+PINS_ADJ = ["tests/test_oracle_pins_adjoint.py"]
+
+# (name, file, text as written, text with the mistake, pin files expected to catch it)
+MUTATIONS = [
+    ("philox multiplier", "pic_oracle.c", "(uint64_t)0xD2511F53u * (uint64_t)c0",
+     "(uint64_t)0xD2511F55u * (uint64_t)c0", PINS_MAIN),
+    ("Thomas boundary sign", "pic_oracle.c", "if (j == 1) d += V_L;", "if (j == 1) d -= V_L;", PINS_MAIN),
+    ("Thomas elimination sign", "pic_oracle.c", "dp[j] = (d - (-1.0) * dp[j - 1]) / den;",
+     "dp[j] = (d + (-1.0) * dp[j - 1]) / den;", PINS_MAIN),
+    ("wall Gauss term sign", "pic_oracle.c", "E[0] = (phi[0] - phi[1]) / dx - rho[0] * dx / 2.0;",
+     "E[0] = (phi[0] - phi[1]) / dx + rho[0] * dx / 2.0;", PINS_MAIN),
+    ("Boris cross product transposed", "pic_oracle.c", "vm[0] + (vm[1] * t[2] - vm[2] * t[1])",
+     "vm[0] + (vm[2] * t[1] - vm[1] * t[2])", PINS_MAIN),
+    ("Boris second half kick dropped", "pic_oracle.c", "v[0] = vq[0] + h * E[0];", "v[0] = vq[0];",
+     PINS_MAIN),
+    ("null-collision probability linearised", "pic_oracle.c",
+     "p_null[s] = (float)(1.0 - exp(-(double)nu_max[s] * c->dt));",
+     "p_null[s] = (float)((double)nu_max[s] * c->dt);", PINS_MAIN),
+    ("CIC deposit weights swapped", "pic_oracle.c", "R[c] += Wl;\n      R[c + 1] += Wr;",
+     "R[c] += Wr;\n      R[c + 1] += Wl;", PINS_MAIN),
+    ("wall half-cell volume dropped", "pic_oracle.c",
+     "double vol = (j == 0 || j == N) ? 0.5 * s->dx : s->dx;", "double vol = s->dx;", PINS_MAIN),
+    ("gather weights swapped", "pic_oracle.c", "Ex = (1.0 - f) * s->E[cc] + f * s->E[cc + 1];",
+     "Ex = f * s->E[cc] + (1.0 - f) * s->E[cc + 1];", PINS_MAIN),
+    ("elastic angle term dropped", "pic_oracle.c", "sqrt(1.0 - 2.0 * m / c->m_gas * (1.0 - cchi))",
+     "sqrt(1.0 - 2.0 * m / c->m_gas)", PINS_MAIN),
+    ("excitation loss dropped", "pic_oracle.c", "double sp2 = sqrt(2.0 * (En - c->E_ex) / m);",
+     "double sp2 = sqrt(2.0 * En / m);", PINS_MAIN),
+    ("ionization threshold dropped", "pic_oracle.c", "double Er = En - c->E_iz;", "double Er = En;",
+     PINS_MAIN),
+    ("charge exchange without a new velocity", "pic_oracle.c",
+     "    v[0] = vt * n0;\n    v[1] = vt * n1;\n    v[2] = vt * n2;\n    tc->coll[3]++;",
+     "    tc->coll[3]++;", PINS_MAIN),
+    ("exponential load not truncated", "pic_oracle.c",
+     "x = -lam * log(1.0 - u01(w[0]) * (1.0 - exp(-(double)N / lam)));",
+     "x = -lam * log(1.0 - u01(w[0]));", PINS_MAIN),
+    ("adjoint: gather position term dropped", "pic_adjoint.c",
+     "lx[p] += ebar * (En[k0 + 1] - En[k0]);", "(void)En;", PINS_ADJ),
+    ("adjoint: rotation not transposed", "pic_adjoint.c",
+     "Lt[k] = m.M[s][0][k] * L[0] + m.M[s][1][k] * L[1] + m.M[s][2][k] * L[2];",
+     "Lt[k] = m.M[s][k][0] * L[0] + m.M[s][k][1] * L[1] + m.M[s][k][2] * L[2];", PINS_ADJ),
+    ("adjoint: flux share slope sign", "pic_adjoint.c", "(d > 0.0 ? -1.0 : (d < 0.0 ? 1.0 : 0.0))",
+     "(d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0))", PINS_ADJ),
+    ("adjoint: field transpose wall sign", "pic_adjoint.c", "if (k == 1) a -= mu[0] / dx;",
+     "if (k == 1) a += mu[0] / dx;", PINS_ADJ),
+    ("adjoint: initial field's bias term dropped", "pic_adjoint.c",
+     "    for (int32_t j = 0; j <= N; ++j) gV += mu[j] / ((double)N * m.dx);\n    double gT",
+     "    double gT", PINS_ADJ),
+    ("adjoint: temperature chain factor", "pic_adjoint.c", "grad[1] = gT / (2.0 * c->T[0]);",
+     "grad[1] = gT / c->T[0];", PINS_ADJ),
+    ("adjoint: position update without 1/dx", "pic_adjoint.c", "lv[3 * p] += lx[p] * c->dt / m.dx;",
+     "lv[3 * p] += lx[p] * c->dt;", PINS_ADJ),
+]
+
+
+def _build_copy(tmp, fname, old, new):
+    src = os.path.join(tmp, "src")
+    shutil.copytree(ORACLE, src, ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.py"))
+    path = os.path.join(src, fname)
+    text = open(path).read()
+    assert text.count(old) == 1, f"the text to change occurs {text.count(old)} times in {fname}"
+    open(path, "w").write(text.replace(old, new))
+    lib = os.path.join(tmp, "liboracle_mut.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-fopenmp", "-shared",
+                    os.path.join(src, "pic_oracle.c"), os.path.join(src, "pic_adjoint.c"), "-o", lib, "-lm"],
+                   check=True)
+    return lib
+
+
+@pytest.mark.parametrize("name,fname,old,new,pins", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(tmp_path, name, fname, old, new, pins):
+    lib = _build_copy(str(tmp_path), fname, old, new)
+    env = dict(os.environ, PIC_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    # exit 1: a test failed (the mistake was caught); 0: every pin passed with the mistake in place
+    assert r.returncode == 1, f"no pin caught '{name}' (pytest exit {r.returncode}):\n{r.stdout[-2000:]}"

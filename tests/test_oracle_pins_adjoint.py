@@ -43,10 +43,11 @@ def test_field_transpose_dot_product_and_matrix(N):
         assert np.abs(GT - G.T).max() <= 1e-12 * np.abs(G).max()
 
 
-@pytest.mark.parametrize("case", ["self", "magnetised", "external", "frozen_ions", "biased_right"])
+@pytest.mark.parametrize("case", ["self", "magnetised", "external", "frozen_ions", "biased_right", "half_cells"])
 def test_gradient_equals_central_differences(case):
     p = {
         "self": BASE,
+        "half_cells": W.variant(BASE, L=24.0),  # dx = 1/2: positions advance by v dt / dx
         "magnetised": W.variant(BASE, B=0.5, B_angle_deg=30.0),
         "external": W.variant(BASE, field_mode=W.FIELD_EXTERNAL, E_ext=0.02),
         "frozen_ions": W.variant(BASE, frozen_mask=2),

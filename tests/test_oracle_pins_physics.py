@@ -142,11 +142,14 @@ def _maxwell_mean_speed(T, m):
     return math.sqrt(8 * T / (math.pi * m))
 
 
-def test_elastic_rate_matches_n_sigma_mean_speed():
+@pytest.mark.parametrize("sigma_el", [0.1, 2.0])
+def test_elastic_rate_matches_n_sigma_mean_speed(sigma_el):
     # constant cross section: collisions per particle-step = P_null nu/nu_max; summed over a
-    # Maxwellian this is (1 - e^{-a})/a * n sigma <|v|> dt, a = nu_max dt.
+    # Maxwellian this is (1 - e^{-a})/a * n sigma <|v|> dt, a = nu_max dt (the chance that a
+    # Poisson process of rate nu_max has an event within dt is 1 - e^{-a}).  sigma_el = 2 makes
+    # a ~ 1.6, where that chance is far from its first-order value a.
     p = W.variant(W.BASE, ncells=200, L=200.0, ppc=(500, 1), coll_mask=W.COLL_EL,
-                  field_mode=W.FIELD_ZERO, sigma_el=0.1)
+                  field_mode=W.FIELD_ZERO, sigma_el=sigma_el)
     s = _sim(p)
     n = s.count(0)
     steps = 4
@@ -294,13 +297,27 @@ def test_loader_uniform_maxwellian():
         assert len(np.unique(ids)) == len(ids)
 
 
-def test_loader_exponential_profile():
-    p = W.variant(W.SMALL_C3)
+@pytest.mark.parametrize("scale", [None, 256.0])
+def test_loader_exponential_profile(scale):
+    # the density is exp(-x / lambda) truncated to [0, L): with lambda = L/2 the truncation holds
+    # back 13.5 % of an untruncated exponential's mass
+    p = W.variant(W.SMALL_C3) if scale is None else W.variant(W.SMALL_C3, profile_scale=scale)
     s = _sim(p)
     x, v, ids = s.particles(0)
     lam, L = p["profile_scale"], p["ncells"]
     cdf = lambda t: (1 - np.exp(-t / lam)) / (1 - np.exp(-L / lam))
     assert stats.kstest(x, cdf).pvalue > 1e-4
+
+
+def test_quiet_load_density_is_uniform_at_every_node():
+    # evenly spaced particles (quiet load, no displacement) fill every cell symmetrically: each
+    # interior node collects one cell's worth of charge over dx, each wall node half of it over the
+    # half cell dx/2, so the node density is the same everywhere.  Ions of charge 2 against
+    # electrons of charge -1 leave a net density of +1.
+    p = W.variant(W.BASE, ncells=24, L=24.0, ppc=(40, 40), charge=(-1.0, 2.0),
+                  load_profile=W.LOAD_QUIET_SINE, profile_scale=0.0, profile_mode=1)
+    rho = _sim(p).fields()["rho"]
+    assert np.abs(rho - 1.0).max() < 1e-9, rho
 
 
 def test_sort_orders_cells_and_keeps_the_set():
