@@ -212,10 +212,10 @@ int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double
  * advances all of them by one step with one persistent launch of the particle step over every
  * simulation's particles -- their uneven particle counts split evenly over the GPU, as the
  * particle load balancing of Sec. 4.1 ("Particle Load Balancing") splits uneven particle
- * distributions over MPI ranks --
- * one launch of the field solve (one thread-block cluster per simulation), and, on sort steps,
- * one per-cell counting sort over all of them.  Repeated steps replay a captured CUDA graph of
- * 2 * sort_interval steps.  Each simulation computes exactly what pic_init + pic_step compute for
+ * distributions over MPI ranks --, one launch of the field solve (one thread-block cluster per
+ * simulation) and, on sort steps, the per-cell counting sort's scans (the next step's launch moves
+ * the particles).  Repeated steps replay a captured CUDA graph of 2 * sort_interval steps.
+ * Each simulation computes exactly what pic_init + pic_step compute for
  * its own configuration: the same random draws, the same int64 deposit, the same field, the same
  * particle set; the batch changes only how the work is laid out on the GPU.
  *
@@ -238,7 +238,6 @@ typedef struct pic_batch pic_batch;
 typedef struct pic_batch_tuning {
   int32_t variant;          /* shape of the particle-step kernel, 0 .. pic_batch_variant_count()-1 */
   int32_t ctas_per_sm;      /* resident CTAs per SM of the particle step; 0 = as many as fit */
-  int32_t sort_ctas_per_sm; /* CTAs per SM of the sort's scatter; 0 = 4 */
   int32_t use_graph;        /* nonzero: replay CUDA graphs of 2 * sort_interval steps */
 } pic_batch_tuning;
 
@@ -260,6 +259,11 @@ int pic_batch_init(const pic_config* cfgs, int32_t nsims, void* workspace, size_
  * what fits on an SM).  Setting drops captured graphs. */
 int pic_batch_set_tuning(pic_batch* b, const pic_batch_tuning* t);
 int pic_batch_get_tuning(pic_batch* b, pic_batch_tuning* t);
+
+/* Kinetic-energy diagnostics of a batch: every == 1 sums them inside every batch step (pic_batch_diag
+ * after a step costs no extra pass); every == 0 (the default) sums them in pic_batch_diag, one pass
+ * per simulation.  Same bits either way.  Other values: PIC_EINVAL.  Drops captured graphs. */
+int pic_batch_set_diag_interval(pic_batch* b, int32_t every);
 
 /* Enqueue n >= 0 steps of every simulation (asynchronous on the batch's stream). */
 int pic_batch_step(pic_batch* b, int32_t n);

@@ -9,7 +9,7 @@ with CUDA events on the batch's stream:
 
 1. every compiled shape of the particle-step kernel, with as many CTAs per SM as fit;
 2. for the fastest shape, fewer CTAs per SM;
-3. for the fastest so far, the CTA count of the sort's scatter.
+3. for the fastest so far, launching the steps one by one instead of replaying a CUDA graph.
 
 It then sets the winner and returns the batch to its initial state (pic_batch_reset), since the
 trials advanced it.  The cache key holds the GPU's name and SM count, the compiled shapes, the
@@ -54,7 +54,7 @@ def _valid_entry(e, nvariants: int) -> bool:
     try:
         t = e["tuning"]
         return 0 <= int(t["variant"]) < nvariants and int(t["ctas_per_sm"]) >= 0 and \
-            int(t["sort_ctas_per_sm"]) >= 0 and isinstance(e["ms_per_step"], (int, float))
+            isinstance(t["use_graph"], bool) and isinstance(e["ms_per_step"], (int, float))
     except (KeyError, TypeError, ValueError):
         return False
 
@@ -81,7 +81,7 @@ def _device():
 
 
 def tune(batch, *, cache_path: str | None = None, force: bool = False, timer=None, device=None,
-         variants=None, max_ctas: int = 8, sort_options=(2, 4, 8, 16)) -> dict:
+         variants=None, max_ctas: int = 8) -> dict:
     """Pick and set the fastest launch configuration of ``batch`` (a ``pic.Batch`` or anything with
     its ``params``, ``set_tuning``, ``step``, ``sync`` and ``reset``).  Returns
     ``{"tuning": ..., "ms_per_step": ..., "cached": bool, "trials": [...], "key": ...}``."""
@@ -116,7 +116,7 @@ def tune(batch, *, cache_path: str | None = None, force: bool = False, timer=Non
         trials.append({"tuning": dict(t), "ms_per_step": ms})
         return ms
 
-    base = {"variant": 0, "ctas_per_sm": 0, "sort_ctas_per_sm": 0, "use_graph": True}
+    base = {"variant": 0, "ctas_per_sm": 0, "use_graph": True}
     best, best_ms = None, math.inf
     for v in range(len(variants)):
         t = dict(base, variant=v)
@@ -130,11 +130,10 @@ def tune(batch, *, cache_path: str | None = None, force: bool = False, timer=Non
         ms = trial(t)
         if ms is not None and ms < best_ms:
             best, best_ms = t, ms
-    for c in sort_options:
-        t = dict(best, sort_ctas_per_sm=c)
-        ms = trial(t)
-        if ms is not None and ms < best_ms:
-            best, best_ms = t, ms
+    t = dict(best, use_graph=False)
+    ms = trial(t)
+    if ms is not None and ms < best_ms:
+        best, best_ms = t, ms
     batch.set_tuning(**best)
     batch.reset()  # the trials advanced the batch
     cache[key] = {"tuning": best, "ms_per_step": best_ms, "variant_name": variants[best["variant"]]}

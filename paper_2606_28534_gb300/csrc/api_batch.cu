@@ -47,10 +47,10 @@ struct pic_batch {
   long long* R[2] = {nullptr, nullptr};
   double *rho = nullptr, *phi = nullptr, *E = nullptr;
   StepParams32* d_sims[2] = {nullptr, nullptr};                  // [buffer]
-  PoissonParams* d_field[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [buffer][sort step]
+  PoissonParams* d_field[2][2][2] = {};  // [buffer][sort step][step after a sort]
   SortParams* d_sort[2] = {nullptr, nullptr};                    // [source buffer]
   BSim* d_hot = nullptr;
-  unsigned *pre[2] = {nullptr, nullptr}, *tpre[2] = {nullptr, nullptr}, *ncur[2] = {nullptr, nullptr};
+  unsigned *pre[2] = {nullptr, nullptr}, *ncur[2] = {nullptr, nullptr};
   std::vector<unsigned long long> seg[2], cap_s[2];
   std::vector<long long> cbase, nbase;
   unsigned long long total_cap[2] = {0, 0};
@@ -62,8 +62,11 @@ struct pic_batch {
   int sort_interval = 1;
   int sms = 152;
   pic_batch_tuning tun;
-  int grid_step = 0, grid_sort = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by the buffer parity the graph starts from
+  int grid_step = 0;
+  cudaGraphExec_t graph[2][2] = {};  // by the buffer parity and pending scatter the graph starts from
+  bool pending = false;     // a sort scan ran: the next step moves the particles to buffer 1 - cur
+  int ke_every = 0;         // 1: the step sums the kinetic energy; 0: pic_batch_diag sums it
+  bool ke_valid = false;    // the last step (or load) summed it
   bool prof = false;
   std::vector<EvPair> ev;
   double ms[PIC_KERNEL_KINDS] = {0};
@@ -151,7 +154,6 @@ void layout(pic_batch* b, char* base, size_t* total) {
   b->E = cv.take<double>(M);
   for (int s = 0; s < 2; ++s) {
     b->pre[s] = cv.take<unsigned>((size_t)n + 1);
-    b->tpre[s] = cv.take<unsigned>((size_t)n + 1);
     b->ncur[s] = cv.take<unsigned>((size_t)n);
   }
   b->zero_bytes = (cv.off + 255) & ~size_t(255);
@@ -159,7 +161,8 @@ void layout(pic_batch* b, char* base, size_t* total) {
   for (int p = 0; p < 2; ++p) {
     b->d_sims[p] = cv.take<StepParams32>((size_t)n);
     b->d_sort[p] = cv.take<SortParams>((size_t)n);
-    for (int q = 0; q < 2; ++q) b->d_field[p][q] = cv.take<PoissonParams>((size_t)n);
+    for (int q = 0; q < 2; ++q)
+      for (int r = 0; r < 2; ++r) b->d_field[p][q][r] = cv.take<PoissonParams>((size_t)n);
   }
   b->d_hot = cv.take<BSim>((size_t)n);
   for (int p = 0; p < 2; ++p)
@@ -233,22 +236,24 @@ int upload_tables(pic_batch* b) {
       }
       so.ctl = h->ctl;
       so.N = h->N;
-      so.defer = 0;
+      so.defer = 1;  // the scan only: the next step moves the particles
       h->cur = keep_cur;
     }
     CKB(cudaMemcpy(b->d_sims[p], sims.data(), sizeof(StepParams32) * n, cudaMemcpyHostToDevice));
     CKB(cudaMemcpy(b->d_sort[p], sort.data(), sizeof(SortParams) * n, cudaMemcpyHostToDevice));
-    for (int q = 0; q < 2; ++q) {
-      for (int k = 0; k < n; ++k) {
-        pic_handle* h = b->views[k];
-        const int keep_cur = h->cur;
-        h->cur = p;
-        field[k] = field_params(h, q != 0, true);
-        h->cur = keep_cur;
-        if (!field[k].exact) return PIC_EINVAL;
+    for (int q = 0; q < 2; ++q)
+      for (int r = 0; r < 2; ++r) {
+        for (int k = 0; k < n; ++k) {
+          pic_handle* h = b->views[k];
+          const int keep_cur = h->cur;
+          h->cur = p;
+          field[k] = field_params(h, q != 0, true);
+          field[k].scatter_step = r;
+          h->cur = keep_cur;
+          if (!field[k].exact) return PIC_EINVAL;
+        }
+        CKB(cudaMemcpy(b->d_field[p][q][r], field.data(), sizeof(PoissonParams) * n, cudaMemcpyHostToDevice));
       }
-      CKB(cudaMemcpy(b->d_field[p][q], field.data(), sizeof(PoissonParams) * n, cudaMemcpyHostToDevice));
-    }
   }
   for (int k = 0; k < n; ++k) {
     const pic_handle* h = b->views[k];
@@ -262,6 +267,7 @@ int upload_tables(pic_batch* b) {
     x.N = h->N;
     x.seed = h->ph.seed;
     x.collides = ((h->ph.coll_mask & 7u) ? 1u : 0u) | ((h->ph.coll_mask & 8u) ? 2u : 0u);
+    for (int s = 0; s < 2; ++s) x.cap[s] = (unsigned)b->cap_s[s][k];
   }
   CKB(cudaMemcpy(b->d_hot, hot.data(), sizeof(BSim) * n, cudaMemcpyHostToDevice));
   return PIC_OK;
@@ -299,7 +305,6 @@ BatchPlan plan_params(pic_batch* b, int advance) {
   BatchPlan P;
   for (int s = 0; s < 2; ++s) {
     P.pre[s] = b->pre[s];
-    P.tpre[s] = b->tpre[s];
     P.ncur[s] = b->ncur[s];
     P.sims[s] = b->d_sims[s];
   }
@@ -309,10 +314,15 @@ BatchPlan plan_params(pic_batch* b, int advance) {
   return P;
 }
 
-BatchStep32 step_params(pic_batch* b) {
+// Parameters of the step kernel: in the step after a sort it reads buffer cur and fills buffer
+// 1 - cur (whose per-simulation tables then serve the collision queue and births).
+BatchStep32 step_params(pic_batch* b, bool scatter) {
   BatchStep32 P;
+  const int dst = scatter ? 1 - b->cur : b->cur;
   for (int s = 0; s < 2; ++s) {
-    P.sp[s] = b->arr[b->cur][s];
+    P.sp[s] = b->arr[dst][s];
+    P.src[s] = b->arr[b->cur][s];
+    P.cursor[s] = b->cursor[s];
     P.cnt[s] = b->cnt[s];
     P.S[s] = b->S[s];
     P.pre[s] = b->pre[s];
@@ -320,8 +330,9 @@ BatchStep32 step_params(pic_batch* b) {
   }
   P.E2 = b->E2;
   P.ph = b->views[0]->ph;  // the shared constants (push, masses, field mode) are equal in every view
-  P.sims = b->d_sims[b->cur];
+  P.sims = b->d_sims[dst];
   P.hot = b->d_hot;
+  P.sum_ke = b->ke_every == 1 ? 1u : 0u;
   P.dev = b->dev;
   P.nsims = b->n;
   return P;
@@ -330,40 +341,47 @@ BatchStep32 step_params(pic_batch* b) {
 // One step of every simulation on stream st (host bookkeeping of cur and step included).
 int enqueue_step(pic_batch* b, cudaStream_t st) {
   const bool sort_now = (b->step % (unsigned long long)b->sort_interval) == 0ull;
+  const bool scatter = b->pending;
   EvPair e;
-  bprof_begin(b, K_STEP, &e, st);
-  CKB(launch_bstep32(b->tun.variant, step_params(b), b->grid_step, st));
+  bprof_begin(b, scatter ? K_STEP_SCATTER : K_STEP, &e, st);
+  CKB(launch_bstep32(b->tun.variant, step_params(b, scatter), b->grid_step, scatter, st));
   bprof_end(b, &e, st);
+  if (scatter) {
+    b->cur = 1 - b->cur;
+    b->pending = false;
+  }
+  b->ke_valid = b->ke_every == 1;
   bprof_begin(b, K_FIELD, &e, st);
-  CKB(launch_field_batch(b->d_field[b->cur][sort_now ? 1 : 0], b->n, b->maxN, st));
+  CKB(launch_field_batch(b->d_field[b->cur][sort_now ? 1 : 0][scatter ? 1 : 0], b->n, b->maxN, st));
   bprof_end(b, &e, st);
   bprof_begin(b, K_PLAN, &e, st);
   CKB(launch_bplan(plan_params(b, 1), st));
   bprof_end(b, &e, st);
   if (sort_now) {
+    // the counting sort's scans: cursors now, the particles move during the next step (the extents
+    // the plan just read stay those of buffer cur until then)
     bprof_begin(b, K_SORT, &e, st);
-    CKB(launch_sort_batch(b->d_sort[b->cur], b->tpre[0], b->tpre[1], b->ncur[0], b->ncur[1], b->n, b->maxN,
-                          b->grid_sort, st));
+    CKB(launch_sort_scan_batch(b->d_sort[b->cur], b->n, b->maxN, st));
     bprof_end(b, &e, st);
-    b->cur = 1 - b->cur;
-    bprof_begin(b, K_PLAN, &e, st);
-    CKB(launch_bplan(plan_params(b, 0), st));
-    bprof_end(b, &e, st);
+    b->pending = true;
   }
   b->step += 1;
   return PIC_OK;
 }
 
 void drop_graphs(pic_batch* b) {
-  for (int p = 0; p < 2; ++p) {
-    if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
-    b->graph[p] = nullptr;
-  }
+  for (int p = 0; p < 2; ++p)
+    for (int q = 0; q < 2; ++q) {
+      if (b->graph[p][q]) cudaGraphExecDestroy(b->graph[p][q]);
+      b->graph[p][q] = nullptr;
+    }
 }
 
-// Graph of 2 * sort_interval steps starting at a sort step from buffer parity b->cur.
+// Graph of 2 * sort_interval steps starting at a sort step, from buffer parity b->cur and pending
+// state b->pending (both are back where they started after the two sorts).
 int capture_graph(pic_batch* b) {
   const int p = b->cur;
+  const bool pend = b->pending;
   const unsigned long long step0 = b->step;
   cudaGraph_t g = nullptr;
   CKB(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -371,6 +389,7 @@ int capture_graph(pic_batch* b) {
   for (int i = 0; i < 2 * b->sort_interval && rc == PIC_OK; ++i) rc = enqueue_step(b, b->cap);
   const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);
   b->cur = p;  // capture only recorded the launches
+  b->pending = pend;
   b->step = step0;
   if (rc != PIC_OK || ec != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
@@ -380,7 +399,7 @@ int capture_graph(pic_batch* b) {
   const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
   cudaGraphDestroy(g);
   if (ei != cudaSuccess) return PIC_ECUDA;
-  b->graph[p] = x;
+  b->graph[p][pend ? 1 : 0] = x;
   return PIC_OK;
 }
 
@@ -406,6 +425,8 @@ int load_all(pic_batch* b) {
   for (int k = 0; k < b->n; ++k)
     if (b->views[k]->cur != b->cur) return PIC_EDEVICE;
   b->step = 0;
+  b->pending = false;  // the load's full sort left every simulation sorted
+  b->ke_valid = true;  // and summed the kinetic energy
   return PIC_OK;
 }
 
@@ -417,13 +438,13 @@ int sync_errors(pic_batch* b) {
   return status_of(d.error);
 }
 
-// The view of simulation k, brought up to the batch's step and buffer (the batch step sums the
-// kinetic energy every step).
+// The view of simulation k, brought up to the batch's step and buffer (and whether the last step
+// summed the kinetic energy; if not, pic_diag sums it).
 pic_handle* view(pic_batch* b, int k) {
   pic_handle* h = b->views[k];
   h->step = b->step;
   h->cur = b->cur;
-  h->ke_valid = true;
+  h->ke_valid = b->ke_valid;
   return h;
 }
 
@@ -511,12 +532,20 @@ int pic_batch_set_tuning(pic_batch* b, const pic_batch_tuning* t) {
   if (t->variant < 0 || t->variant >= bstep32_variants()) return PIC_EINVAL;
   const int occ = bstep32_occupancy(t->variant);
   if (t->ctas_per_sm < 0 || t->ctas_per_sm > occ) return PIC_EINVAL;
-  if (t->sort_ctas_per_sm < 0 || t->sort_ctas_per_sm > 32) return PIC_EINVAL;
   if (b->cap) cudaStreamSynchronize(b->st);
   drop_graphs(b);
   b->tun = *t;
   b->grid_step = b->sms * (t->ctas_per_sm ? t->ctas_per_sm : occ);
-  b->grid_sort = b->sms * (t->sort_ctas_per_sm ? t->sort_ctas_per_sm : 4);
+  return PIC_OK;
+}
+
+int pic_batch_set_diag_interval(pic_batch* b, int32_t every) {
+  if (!b || every < 0 || every > 1) return PIC_EINVAL;
+  if (every != b->ke_every) {
+    cudaStreamSynchronize(b->st);
+    drop_graphs(b);  // the graphs hold the kernel parameters of the other choice
+  }
+  b->ke_every = every;
   return PIC_OK;
 }
 
@@ -533,12 +562,14 @@ int pic_batch_step(pic_batch* b, int32_t n) {
     const bool graphable = b->tun.use_graph && !b->prof && (b->step % (unsigned long long)b->sort_interval) == 0ull &&
                            (unsigned long long)n >= cycle;
     if (graphable) {
-      if (!b->graph[b->cur]) {
+      cudaGraphExec_t& g = b->graph[b->cur][b->pending ? 1 : 0];
+      if (!g) {
         const int rc = capture_graph(b);
         if (rc != PIC_OK) return rc;
       }
-      CKB(cudaGraphLaunch(b->graph[b->cur], b->st));
-      b->step += cycle;  // two sorts: the buffer parity is back where it started
+      CKB(cudaGraphLaunch(g, b->st));
+      b->step += cycle;  // two sorts: the buffer parity and the pending state are back where they started
+      b->ke_valid = b->ke_every == 1;
       n -= (int32_t)cycle;
     } else {
       const int rc = enqueue_step(b, b->st);
@@ -595,6 +626,8 @@ int pic_batch_restore(pic_batch* b, const void* const* blobs, const size_t* lens
   }
   b->cur = b->views[0]->cur;
   b->step = step;
+  b->pending = false;
+  b->ke_valid = true;
   const int rc = replan(b);
   if (rc != PIC_OK) return rc;
   return sync_errors(b);

@@ -27,7 +27,7 @@ struct WarpSim {
   unsigned pnull;  // null-collision probability, 0: no draw
   int cbase;       // first cell
   int N;           // cells
-  unsigned pad;
+  unsigned cap;    // capacity of the species segment
   unsigned long long seed;
 };
 
@@ -50,21 +50,28 @@ __device__ __forceinline__ int owner(const unsigned* __restrict__ pre, int nsims
   return lo;
 }
 
-// Lane 0: bulk copies of local chunk lt of species s of simulation k into a stage buffer.
-__device__ __forceinline__ void issue_chunk(const BatchStep32& B, int s, int k, unsigned lt, unsigned char* buf,
-                                            unsigned long long* bar) {
+// Lane 0: bulk copies of local chunk lt of species s of simulation k (arrays A) into a stage buffer.
+__device__ __forceinline__ void issue_chunk(const BatchStep32& B, const Species32& A, int s, int k, unsigned lt,
+                                            unsigned char* buf, unsigned long long* bar) {
   const unsigned nk = B.ncur[s][k];
   const unsigned i0 = lt * CHUNK;
   const unsigned n = min((unsigned)CHUNK, nk - i0);  // multiple of 4
-  stage_issue_span(B.sp[s], B.hot[k].seg[s] + i0, n, buf, bar);
+  stage_issue_span(A, B.hot[k].seg[s] + i0, n, buf, bar);
+}
+
+// Where births of simulation k go in species s: past the extent of the buffer being written (after
+// a sort, the extent the sort scan gave the filled buffer).
+__device__ __forceinline__ unsigned long long birth_base(const BatchStep32& B, int k, int s, bool scatter) {
+  return scatter ? B.sims[k].ctl->sort_new[s] : (unsigned long long)B.ncur[s][k];
 }
 
 // The warp leaves simulation k: its queued collisions, the kinetic energy of its particles of
 // species s and its counters go to the simulation; the counters restart from zero.
 __device__ __forceinline__ void leave_sim(const BatchStep32& B, int k, int s, const unsigned long long* q, int qn,
-                                          BlockCounters& wc, unsigned long long ke, bool run_queue) {
+                                          BlockCounters& wc, unsigned long long ke, bool run_queue, bool scatter) {
   const int lane = threadIdx.x & 31;
-  if (run_queue && qn) flush_queue(B.sims[k], q, qn, B.ncur[0][k], B.ncur[1][k], &wc);
+  if (run_queue && qn)
+    flush_queue(B.sims[k], q, qn, birth_base(B, k, 0, scatter), birth_base(B, k, 1, scatter), &wc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xFFFFFFFFu, ke, o);
   if (lane == 0 && ke) atomicAdd(&wc.ke[s], ke);
@@ -75,7 +82,10 @@ __device__ __forceinline__ void leave_sim(const BatchStep32& B, int k, int s, co
   __syncwarp();
 }
 
-template <int TPB, int MINB, int NST>
+// SCATTER: the step after a sort step (see k_step32.cu): read B.src, write each particle to its
+// sorted slot of its simulation's segment in B.sp (cursors: the sort scan's, at the simulation's
+// cell offset); B.sims then addresses the written buffer, for the collision queue and births.
+template <int TPB, int MINB, int NST, bool SCATTER>
 __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ BatchStep32 B) {
   constexpr int WARPS = TPB / 32;
   static_assert(sizeof(BlockCounters) / 4 <= 32, "one word of the counters per lane");
@@ -114,7 +124,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
     const unsigned t0 = min(total, gw * per);
     const unsigned t1 = min(total, t0 + per);
     if (t0 >= t1) continue;
-    const Species32& A = B.sp[s];
+    const Species32& A = B.sp[s];                          // written
+    const Species32& Asrc = SCATTER ? B.src[s] : B.sp[s];  // read
     const SpConst& K = ph.sp[s];
     const bool moves = (ph.push_mask >> s) & 1u;
     const unsigned long long tag = (unsigned long long)s << 63;
@@ -128,7 +139,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         const unsigned t = t0 + st;
         if (t < t1) {
           while (pre[ki + 1] <= t) ++ki;
-          issue_chunk(B, s, ki, t - pre[ki], stage + st * STAGE_BYTES, bar + st);
+          issue_chunk(B, Asrc, s, ki, t - pre[ki], stage + st * STAGE_BYTES, bar + st);
         }
       }
     }
@@ -143,7 +154,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
     for (unsigned t = t0; t < t1; ++t) {
       if (t >= kend) {  // first chunk of another simulation
         if (kend) {
-          leave_sim(B, kc, s, q, qn, wc, ke_lane, true);
+          leave_sim(B, kc, s, q, qn, wc, ke_lane, true, SCATTER);
           qn = 0;
           ke_lane = 0ull;
         }
@@ -157,6 +168,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
           ws.pnull = moves && ((h.collides >> s) & 1u) ? h.p_null_u24[s] : 0u;
           ws.cbase = h.cbase;
           ws.N = h.N;
+          ws.cap = h.cap[s];
           ws.seed = h.seed;
         }
         __syncwarp();
@@ -200,6 +212,26 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         e2[k] = make_float2(0.f, 0.f);
         if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL) e2[k] = __ldg(B.E2 + (ws.cbase + c[k]));
       }
+      // the step after a sort: claim each live particle's slot in its cell (four atomics in flight)
+      unsigned slot[PIC_PPT];
+      if (SCATTER) {
+        const int cb = ws.cbase;
+        unsigned peers[PIC_PPT], base[PIC_PPT];
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          const bool live = c[k] != PIC_DEAD_CELL;
+          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cb + c[k] : -1);
+          base[k] = 0u;
+          if (live && lane == __ffs(peers[k]) - 1)
+            base[k] = atomicAdd(B.cursor[s] + cb + c[k], (unsigned)__popc(peers[k]));
+        }
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k)
+          slot[k] = __shfl_sync(0xFFFFFFFFu, base[k], __ffs(peers[k]) - 1) + (unsigned)__popc(peers[k] & below);
+      }
+      unsigned live0 = 0u;  // live at the start of the step (the step after a sort: owns a slot)
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k) live0 |= c[k] != PIC_DEAD_CELL ? (1u << k) : 0u;
       // the stage is read: refill it with the chunk NST steps ahead
       fence_proxy_async_smem();
       __syncwarp();
@@ -208,7 +240,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         if (tn < t1) {
           int ki = kc;  // owner of chunk tn: this simulation or a later one
           while (pre[ki + 1] <= tn) ++ki;
-          issue_chunk(B, s, ki, tn - pre[ki], stage + st * STAGE_BYTES, bar + st);
+          issue_chunk(B, Asrc, s, ki, tn - pre[ki], stage + st * STAGE_BYTES, bar + st);
         }
       }
       st = st + 1 == NST ? 0 : st + 1;
@@ -241,7 +273,26 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
           c[k] = cn;
         }
       }
-      if (have && moves) {
+      if (SCATTER) {
+        const unsigned seg = ws.seg, cap = ws.cap;
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          if (!((live0 >> k) & 1u)) continue;
+          if (slot[k] >= cap) {  // only reachable if the counts disagree with the arrays
+            atomicOr(&B.sims[kc].ctl->error, ERR_DEVICE);
+            c[k] = PIC_DEAD_CELL;
+            continue;
+          }
+          const unsigned j = seg + slot[k];
+          A.cell[j] = c[k];
+          if (c[k] == PIC_DEAD_CELL) continue;  // absorbed in this step: a dead slot
+          A.frac[j] = f[k];
+          A.vx[j] = vx[k];
+          A.vy[j] = vy[k];
+          A.vz[j] = vz[k];
+          A.id[j] = id[k];
+        }
+      } else if (have && moves) {
         const unsigned g = ws.seg + i0;
         *reinterpret_cast<int4*>(A.cell + g) = make_int4(c[0], c[1], c[2], c[3]);
         *reinterpret_cast<float4*>(A.frac + g) = make_float4(f[0], f[1], f[2], f[3]);
@@ -249,14 +300,16 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         *reinterpret_cast<float4*>(A.vy + g) = make_float4(vy[0], vy[1], vy[2], vy[3]);
         *reinterpret_cast<float4*>(A.vz + g) = make_float4(vz[0], vz[1], vz[2], vz[3]);
       }
+      if (B.sum_ke) {
 #pragma unroll
-      for (int k = 0; k < PIC_PPT; ++k)
-        if (c[k] != PIC_DEAD_CELL && !((cand >> k) & 1u)) ke_lane += ke_fx32(vx[k], vy[k], vz[k], K.mass);
+        for (int k = 0; k < PIC_PPT; ++k)
+          if (c[k] != PIC_DEAD_CELL && !((cand >> k) & 1u)) ke_lane += ke_fx32(vx[k], vy[k], vz[k], K.mass);
+      }
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) {
         const bool qk = ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL;
         const unsigned b = __ballot_sync(0xFFFFFFFFu, qk);
-        if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(i0 + k);
+        if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(SCATTER ? slot[k] : i0 + k);
         qn += __popc(b);
       }
 
@@ -285,7 +338,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         warp_deposit(B.cnt[s], B.S[s], rn[k] ? cbase + c[k] : -1, rn[k], rsw[k]);
 
       if (qn > QFLUSH) {
-        flush_queue(B.sims[kc], q, qn, B.ncur[0][kc], B.ncur[1][kc], &wc);
+        flush_queue(B.sims[kc], q, qn, birth_base(B, kc, 0, SCATTER), birth_base(B, kc, 1, SCATTER), &wc);
         qn = 0;
       }
     }
@@ -297,9 +350,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         atomicOr(&B.sims[kc].ctl->error, ERR_TIMEOUT);
       }
       for (int k = 0; k < NST; ++k) mbar_wait_bounded(bar + k, (parity >> k) & 1u);
-      if (kend) leave_sim(B, kc, s, q, 0, wc, 0ull, false);
+      if (kend) leave_sim(B, kc, s, q, 0, wc, 0ull, false, SCATTER);
     } else if (kend) {
-      leave_sim(B, kc, s, q, qn, wc, ke_lane, true);
+      leave_sim(B, kc, s, q, qn, wc, ke_lane, true, SCATTER);
       qn = 0;
     }
   }
@@ -308,47 +361,35 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
 // ---- plan: extents, chunk and tile prefixes, error bits, step counter (one CTA of 1024) ------
 constexpr int PLAN_TPB = 1024;
 
-__device__ __forceinline__ void block_excl_scan2(unsigned& a, unsigned& b, unsigned* wa, unsigned* wb,
-                                                 unsigned& tot_a, unsigned& tot_b) {
+// Exclusive scan of one value per thread over the CTA; tot = the sum.
+__device__ __forceinline__ void block_excl_scan(unsigned& a, unsigned* wa, unsigned& tot) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  unsigned ia = a, ib = b;
+  unsigned ia = a;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const unsigned ua = __shfl_up_sync(0xFFFFFFFFu, ia, o), ub = __shfl_up_sync(0xFFFFFFFFu, ib, o);
-    if (lane >= o) {
-      ia += ua;
-      ib += ub;
-    }
+    const unsigned ua = __shfl_up_sync(0xFFFFFFFFu, ia, o);
+    if (lane >= o) ia += ua;
   }
-  if (lane == 31) {
-    wa[w] = ia;
-    wb[w] = ib;
-  }
+  if (lane == 31) wa[w] = ia;
   __syncthreads();
   if (tid < 32) {
-    unsigned va = wa[tid], vb = wb[tid];
+    unsigned va = wa[tid];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned ua = __shfl_up_sync(0xFFFFFFFFu, va, o), ub = __shfl_up_sync(0xFFFFFFFFu, vb, o);
-      if (lane >= o) {
-        va += ua;
-        vb += ub;
-      }
+      const unsigned ua = __shfl_up_sync(0xFFFFFFFFu, va, o);
+      if (lane >= o) va += ua;
     }
     wa[tid] = va;  // inclusive over warps
-    wb[tid] = vb;
   }
   __syncthreads();
-  const unsigned ea = (w ? wa[w - 1] : 0u) + ia - a, eb = (w ? wb[w - 1] : 0u) + ib - b;
-  tot_a = wa[31];
-  tot_b = wb[31];
+  const unsigned ea = (w ? wa[w - 1] : 0u) + ia - a;
+  tot = wa[31];
   __syncthreads();  // the warp totals are reused by the next scan
   a = ea;
-  b = eb;
 }
 
 __global__ void __launch_bounds__(PLAN_TPB) k_bplan(const BatchPlan P) {
-  __shared__ unsigned wa[32], wb[32];
+  __shared__ unsigned wa[32];
   __shared__ unsigned err_s;
   __shared__ unsigned long long step_s;
   const int tid = threadIdx.x;
@@ -364,7 +405,7 @@ __global__ void __launch_bounds__(PLAN_TPB) k_bplan(const BatchPlan P) {
 #pragma unroll 1
   for (int s = 0; s < 2; ++s) {
     unsigned ext[PIC_BATCH_MAX / PLAN_TPB];
-    unsigned chunks = 0u, tiles = 0u;
+    unsigned chunks = 0u;
 #pragma unroll
     for (int i = 0; i < PIC_BATCH_MAX / PLAN_TPB; ++i) {
       ext[i] = 0u;
@@ -374,26 +415,20 @@ __global__ void __launch_bounds__(PLAN_TPB) k_bplan(const BatchPlan P) {
         ext[i] = (unsigned)g->n_cur[s];
         if (s == 0) err |= g->error;
         chunks += (ext[i] + 32u * PIC_PPT - 1u) / (32u * PIC_PPT);
-        tiles += (ext[i] + PIC_TILE - 1u) / PIC_TILE;
       }
     }
-    unsigned tot_c, tot_t;
-    block_excl_scan2(chunks, tiles, wa, wb, tot_c, tot_t);
+    unsigned tot_c;
+    block_excl_scan(chunks, wa, tot_c);
 #pragma unroll
     for (int i = 0; i < PIC_BATCH_MAX / PLAN_TPB; ++i) {
       const int k = k0 + i;
       if (i < per && k < n) {
         P.pre[s][k] = chunks;
-        P.tpre[s][k] = tiles;
         P.ncur[s][k] = ext[i];
         chunks += (ext[i] + 32u * PIC_PPT - 1u) / (32u * PIC_PPT);
-        tiles += (ext[i] + PIC_TILE - 1u) / PIC_TILE;
       }
     }
-    if (tid == 0) {
-      P.pre[s][n] = tot_c;
-      P.tpre[s][n] = tot_t;
-    }
+    if (tid == 0) P.pre[s][n] = tot_c;
   }
   if (err) atomicOr(&err_s, err);
   for (int k = tid; k < n; k += PLAN_TPB) {
@@ -407,40 +442,48 @@ __global__ void __launch_bounds__(PLAN_TPB) k_bplan(const BatchPlan P) {
   }
 }
 
-template <int TPB, int MINB, int NST>
+template <int TPB, int MINB, int NST, bool SCATTER>
 cudaError_t launch_variant(const BatchStep32& p, int grid, cudaStream_t st) {
   constexpr size_t smem = BShape<TPB, NST>::SMEM;
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST, SCATTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     done = true;
   }
-  k_bstep32<TPB, MINB, NST><<<grid, TPB, smem, st>>>(p);
+  k_bstep32<TPB, MINB, NST, SCATTER><<<grid, TPB, smem, st>>>(p);
   return cudaGetLastError();
 }
 
 template <int TPB, int MINB, int NST>
 int occupancy_variant() {
   constexpr size_t smem = BShape<TPB, NST>::SMEM;
-  cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bstep32<TPB, MINB, NST>, TPB, smem) != cudaSuccess || b < 1)
-    b = 1;
-  return b;
+  int occ[2] = {0, 0};
+  cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_bstep32<TPB, MINB, NST, false>, TPB, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_bstep32<TPB, MINB, NST, true>, TPB, smem);
+  const int b = occ[0] < occ[1] ? occ[0] : occ[1];
+  return b < 1 ? 1 : b;
 }
 
 struct Variant {
   const char* name;
   cudaError_t (*launch)(const BatchStep32&, int, cudaStream_t);
+  cudaError_t (*launch_scatter)(const BatchStep32&, int, cudaStream_t);
   int (*occupancy)();
 };
 
+#define BSTEP32_VARIANT(T, M, S)                                                                  \
+  {"tpb" #T "_minb" #M "_stages" #S, launch_variant<T, M, S, false>, launch_variant<T, M, S, true>, \
+   occupancy_variant<T, M, S>}
+
 // (threads per CTA, CTAs per SM the registers are budgeted for, TMA stages per warp)
 const Variant kVariants[] = {
-    {"tpb256_minb3_stages2", launch_variant<256, 3, 2>, occupancy_variant<256, 3, 2>},
-    {"tpb128_minb6_stages2", launch_variant<128, 6, 2>, occupancy_variant<128, 6, 2>},
-    {"tpb256_minb2_stages3", launch_variant<256, 2, 3>, occupancy_variant<256, 2, 3>},
-    {"tpb384_minb2_stages2", launch_variant<384, 2, 2>, occupancy_variant<384, 2, 2>},
+    BSTEP32_VARIANT(256, 3, 2),
+    BSTEP32_VARIANT(128, 6, 2),
+    BSTEP32_VARIANT(256, 2, 3),
+    BSTEP32_VARIANT(384, 2, 2),
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -452,9 +495,9 @@ const char* bstep32_variant_name(int v) { return v >= 0 && v < kNumVariants ? kV
 
 int bstep32_occupancy(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].occupancy() : 0; }
 
-cudaError_t launch_bstep32(int v, const BatchStep32& p, int grid, cudaStream_t st) {
+cudaError_t launch_bstep32(int v, const BatchStep32& p, int grid, bool scatter, cudaStream_t st) {
   if (v < 0 || v >= kNumVariants || grid < 1) return cudaErrorInvalidValue;
-  return kVariants[v].launch(p, grid, st);
+  return scatter ? kVariants[v].launch_scatter(p, grid, st) : kVariants[v].launch(p, grid, st);
 }
 
 cudaError_t launch_bplan(const BatchPlan& p, cudaStream_t st) {

@@ -187,37 +187,6 @@ __global__ void __launch_bounds__(PIC_TPB) k_sort_scatter(const SortParams P) {
   }
 }
 
-// Scatter of an ensemble: the tiles of every simulation (tile prefix tpre_s over the simulations,
-// extents ncur_s as they were when the prefix was formed, which is the extent the scan recorded),
-// both species, strided over the grid.
-__global__ void __launch_bounds__(PIC_TPB) k_bsort_scatter(const SortParams* __restrict__ tab,
-                                                         const unsigned* __restrict__ tpre0,
-                                                         const unsigned* __restrict__ tpre1,
-                                                         const unsigned* __restrict__ ncur0,
-                                                         const unsigned* __restrict__ ncur1, int nsims) {
-  const unsigned tiles0 = tpre0[nsims];
-  const unsigned tiles = tiles0 + tpre1[nsims];
-  for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int s = t >= tiles0 ? 1 : 0;
-    const unsigned tt = s ? t - tiles0 : t;
-    const unsigned* pre = s ? tpre1 : tpre0;
-    int lo = 0, hi = nsims;  // last k with pre[k] <= tt (the first such k with a tile)
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (pre[mid] <= tt) lo = mid; else hi = mid;
-    }
-    while (pre[lo + 1] <= tt) ++lo;  // skip simulations without particles
-    const SortParams& P = tab[lo];
-    const unsigned long long i0 =
-        (unsigned long long)(tt - pre[lo]) * PIC_TILE + (unsigned long long)threadIdx.x * PIC_PPT;
-    const unsigned n = s ? ncur1[lo] : ncur0[lo];
-    if (s == 0)
-      scatter_tile<0>(P, i0, i0 < n);
-    else
-      scatter_tile<1>(P, i0, i0 < n);
-  }
-}
-
 void scan_attrs() {
   static bool attr_set = false;
   if (!attr_set) {
@@ -231,18 +200,13 @@ void scan_attrs() {
 
 }  // namespace
 
-cudaError_t launch_sort_batch(const SortParams* tab, const unsigned* tpre0, const unsigned* tpre1,
-                              const unsigned* ncur0, const unsigned* ncur1, int nsims, int maxN, int grid,
-                              cudaStream_t st) {
+cudaError_t launch_sort_scan_batch(const SortParams* tab, int nsims, int maxN, cudaStream_t st) {
   if (nsims < 1 || nsims > PIC_BATCH_MAX || maxN < 2 || maxN > PIC_MAX_CELLS_FP32) return cudaErrorInvalidValue;
   scan_attrs();
   const int seg = (maxN + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
   SortParams unused;
   memset(&unused, 0, sizeof(unused));
   k_sort_scan<true><<<2 * nsims * PIC_FIELD_CTAS, 1024, sizeof(unsigned int) * (size_t)seg, st>>>(unused, tab);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_bsort_scatter<<<grid, PIC_TPB, 0, st>>>(tab, tpre0, tpre1, ncur0, ncur1, nsims);
   return cudaGetLastError();
 }
 

@@ -283,6 +283,7 @@ struct BSim {
   unsigned long long seed;  // run seed
   unsigned p_null_u24[2];   // null-collision probability (see SpConst)
   unsigned collides;        // bit s: species s takes the null-collision test
+  unsigned cap[2];          // capacity of each species segment
   unsigned pad;
 };
 
@@ -294,7 +295,10 @@ struct BatchDev {
 };
 
 struct BatchStep32 {
-  Species32 sp[2];              // batch arrays of the current buffer
+  Species32 sp[2];              // batch arrays written (the current buffer; after a sort the other)
+  Species32 src[2];             // batch arrays read (the buffer the sort step left, else sp)
+  unsigned int* cursor[2];      // the step after a sort: per-cell write cursors (batch cell arrays)
+  unsigned int sum_ke;          // sum the kinetic energy of the particles alive after the step
   const float2* E2;             // batch cell arrays
   unsigned int* cnt[2];
   unsigned long long* S[2];
@@ -310,7 +314,6 @@ struct BatchStep32 {
 struct BatchPlan {
   StepParams32* sims[2];        // per-simulation parameters of both buffers (their step is set)
   unsigned* pre[2];             // out: chunk prefix (chunks of 32 * PIC_PPT particles)
-  unsigned* tpre[2];            // out: tile prefix (tiles of PIC_TILE particles, the sort)
   unsigned* ncur[2];            // out: extents
   BatchDev* dev;
   int nsims;
@@ -399,9 +402,8 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* ou
 int bstep32_variants();
 const char* bstep32_variant_name(int v);
 int bstep32_occupancy(int v);
-cudaError_t launch_bstep32(int v, const BatchStep32& p, int grid, cudaStream_t st);
+cudaError_t launch_bstep32(int v, const BatchStep32& p, int grid, bool scatter, cudaStream_t st);
 cudaError_t launch_bplan(const BatchPlan& p, cudaStream_t st);
 cudaError_t launch_field_batch(const PoissonParams* tab, int nsims, int maxN, cudaStream_t st);
-cudaError_t launch_sort_batch(const SortParams* tab, const unsigned* tpre0, const unsigned* tpre1,
-                              const unsigned* ncur0, const unsigned* ncur1, int nsims, int maxN, int grid,
-                              cudaStream_t st);
+// the sort scans of an ensemble (tables with defer = 1: the next step moves the particles)
+cudaError_t launch_sort_scan_batch(const SortParams* tab, int nsims, int maxN, cudaStream_t st);

@@ -64,7 +64,7 @@ SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapsh
            "pic_diag", "pic_get_field", "pic_profile", "pic_kernel_times", "pic_free",
            "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc", "pic_set_diag_interval", "pic_diag_bytes",
            "pic_batch_variant_count", "pic_batch_variant_name", "pic_batch_workspace_size",
-           "pic_batch_init", "pic_batch_set_tuning", "pic_batch_get_tuning", "pic_batch_step",
+           "pic_batch_init", "pic_batch_set_tuning", "pic_batch_set_diag_interval", "pic_batch_get_tuning", "pic_batch_step",
            "pic_batch_sync", "pic_batch_diag", "pic_batch_snapshot", "pic_batch_restore",
            "pic_batch_reset", "pic_batch_get_field", "pic_batch_profile", "pic_batch_kernel_times",
            "pic_batch_free", "pic_adj_workspace_size", "pic_adj_init", "pic_adj_forward",
@@ -74,7 +74,7 @@ PIC_BATCH_MAX_SIMS = 4096
 
 
 class PicBatchTuning(C.Structure):
-    _fields_ = [("variant", C.c_int32), ("ctas_per_sm", C.c_int32), ("sort_ctas_per_sm", C.c_int32),
+    _fields_ = [("variant", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("use_graph", C.c_int32)]
 
 
@@ -115,6 +115,7 @@ def lib():
         L.pic_batch_init.argtypes = [P(PicConfig), C.c_int32, V, C.c_size_t, V, P(V)]
         L.pic_batch_set_tuning.argtypes = [V, P(PicBatchTuning)]
         L.pic_batch_get_tuning.argtypes = [V, P(PicBatchTuning)]
+        L.pic_batch_set_diag_interval.argtypes = [V, C.c_int32]
         L.pic_batch_step.argtypes = [V, C.c_int32]
         L.pic_batch_sync.argtypes = [V]
         L.pic_batch_diag.argtypes = [V, P(PicDiag), C.c_int32]
@@ -320,15 +321,19 @@ class Batch:
         except Exception:
             pass
 
-    def set_tuning(self, variant: int = 0, ctas_per_sm: int = 0, sort_ctas_per_sm: int = 0,
+    def set_tuning(self, variant: int = 0, ctas_per_sm: int = 0,
                    use_graph: bool = True):
-        t = PicBatchTuning(int(variant), int(ctas_per_sm), int(sort_ctas_per_sm), 1 if use_graph else 0)
+        t = PicBatchTuning(int(variant), int(ctas_per_sm), 1 if use_graph else 0)
         _check(lib().pic_batch_set_tuning(self._h, C.byref(t)), "pic_batch_set_tuning")
+
+    def set_diag_interval(self, every: int):
+        """1: sum the kinetic energy inside every step; 0: only when diag() asks."""
+        _check(lib().pic_batch_set_diag_interval(self._h, int(every)), "pic_batch_set_diag_interval")
 
     def tuning(self) -> dict:
         t = PicBatchTuning()
         _check(lib().pic_batch_get_tuning(self._h, C.byref(t)), "pic_batch_get_tuning")
-        return {"variant": t.variant, "ctas_per_sm": t.ctas_per_sm, "sort_ctas_per_sm": t.sort_ctas_per_sm,
+        return {"variant": t.variant, "ctas_per_sm": t.ctas_per_sm,
                 "use_graph": bool(t.use_graph)}
 
     def step(self, n: int = 1):

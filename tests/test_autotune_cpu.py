@@ -25,14 +25,14 @@ class Batch:
 
     def __init__(self, params, times):
         self.params = params
-        self.times = times  # (variant, ctas, sort_ctas) -> ms per step
+        self.times = times  # (variant, ctas, use_graph) -> ms per step
         self.tuning = None
         self.calls = []
 
-    def set_tuning(self, variant, ctas_per_sm, sort_ctas_per_sm, use_graph):
+    def set_tuning(self, variant, ctas_per_sm, use_graph):
         if ctas_per_sm > OCC[variant]:
             raise _invalid()
-        self.tuning = (variant, ctas_per_sm, sort_ctas_per_sm, use_graph)
+        self.tuning = (variant, ctas_per_sm, use_graph)
         self.calls.append(("set", self.tuning))
 
     def step(self, n):
@@ -46,17 +46,17 @@ class Batch:
 
 
 def _timer(batch, steps):
-    v, c, sc, _ = batch.tuning
-    return batch.times(v, c, sc) * steps
+    v, c, g = batch.tuning
+    return batch.times(v, c, g) * steps
 
 
-def _times(v, c, sc):
-    # shape 1 is fastest; 4 CTAs per SM beat 6 for it; 8 scatter CTAs per SM are best
+def _times(v, c, g):
+    # shape 1 is fastest; 4 CTAs per SM beat 6 for it; graph replay saves a little
     t = {0: 10.0, 1: 9.0, 2: 9.5}[v]
     if v == 1 and c == 4:
         t -= 0.5
-    if sc == 8:
-        t -= 0.25
+    if not g:
+        t += 0.25
     return t
 
 
@@ -66,14 +66,14 @@ def test_tuner_picks_the_fastest_and_resets(tmp_path):
     path = str(tmp_path / "t.json")
     r = autotune.tune(b, cache_path=path, timer=_timer, device=("GB300", 152), variants=VARIANTS)
     assert not r["cached"]
-    assert r["tuning"] == {"variant": 1, "ctas_per_sm": 4, "sort_ctas_per_sm": 8, "use_graph": True}
-    assert r["ms_per_step"] == pytest.approx(9.0 - 0.5 - 0.25)
-    assert b.tuning == (1, 4, 8, True)
+    assert r["tuning"] == {"variant": 1, "ctas_per_sm": 4, "use_graph": True}
+    assert r["ms_per_step"] == pytest.approx(9.0 - 0.5)
+    assert b.tuning == (1, 4, True)
     # the winner is set, then the batch goes back to its initial state
     assert b.calls[-2][0] == "set" and b.calls[-1] == ("reset",)
     # every trial runs whole cycles of 2 * sort_interval steps
     assert all(c[1] == 2 * runs[0]["sort_interval"] for c in b.calls if c[0] == "step")
-    # shapes first, then CTA counts (only those that fit), then the scatter
+    # shapes first, then CTA counts (only those that fit), then graphs off
     tried = [t["tuning"] for t in r["trials"]]
     assert [t["variant"] for t in tried[:3]] == [0, 1, 2]
     assert [t["ctas_per_sm"] for t in tried[3:3 + OCC[1]]] == list(range(1, OCC[1] + 1))
@@ -89,7 +89,7 @@ def test_cache_hit_sets_without_trials_and_key_separates_shapes(tmp_path):
     r = autotune.tune(b2, cache_path=path, timer=_timer, device=("GB300", 152), variants=VARIANTS)
     assert r["cached"] and r["trials"] == []
     assert [c[0] for c in b2.calls] == ["set"]
-    assert b2.tuning == (1, 4, 8, True)
+    assert b2.tuning == (1, 4, True)
     # another GPU, another ensemble, or another set of compiled shapes: no hit
     k = autotune.shape_key(runs, "GB300", 152, VARIANTS)
     assert k != autotune.shape_key(runs, "GB300", 148, VARIANTS)
@@ -107,8 +107,8 @@ def test_corrupt_or_stale_cache_entries_are_ignored(tmp_path):
     runs = W.small_ensemble()
     path = tmp_path / "t.json"
     key = autotune.shape_key(runs, "GB300", 152, VARIANTS)
-    path.write_text(json.dumps({key: {"tuning": {"variant": 7, "ctas_per_sm": 0, "sort_ctas_per_sm": 0,
-                                                 "use_graph": True}, "ms_per_step": 1.0}}))
+    path.write_text(json.dumps({key: {"tuning": {"variant": 7, "ctas_per_sm": 0, "use_graph": True},
+                                      "ms_per_step": 1.0}}))
     r = autotune.tune(Batch(runs, _times), cache_path=str(path), timer=_timer, device=("GB300", 152),
                       variants=VARIANTS)
     assert not r["cached"]
