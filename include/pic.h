@@ -166,7 +166,8 @@ int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed);
  * Positions and velocities are rounded to FP32 under PIC_FP32.  Synchronises the stream. */
 int pic_restore(pic_handle* h, const void* buf, size_t len);
 
-/* Diagnostics; synchronises the stream and reduces on the device. */
+/* Diagnostics; reduces on the device, then one read of the control block and one wait on the
+ * stream.  *out is filled only when the call returns PIC_OK (otherwise: the device-side error). */
 int pic_diag(pic_handle* h, pic_diag_t* out);
 
 /* Bytes one pic_diag copies from the device to the host (the control block of counters and

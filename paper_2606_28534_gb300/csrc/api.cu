@@ -957,8 +957,6 @@ int pic_sync(pic_handle* h) {
 
 int pic_diag(pic_handle* h, pic_diag_t* d) {
   if (!h || !d) return PIC_EINVAL;
-  int rc = check_errors(h);
-  if (rc != PIC_OK) return rc;
   CK(cudaMemsetAsync(h->ctl->ke_fx, 0, sizeof(h->ctl->ke_fx), h->st));
   CK(cudaMemsetAsync(&h->ctl->netq, 0, sizeof(h->ctl->netq), h->st));
   EvPair e;
@@ -971,10 +969,12 @@ int pic_diag(pic_handle* h, pic_diag_t* d) {
   CK(launch_diag_grid(h->R[0], h->R[1], h->cfg.charge[0] > 0 ? 1 : -1, h->cfg.charge[1] > 0 ? 1 : -1, h->E, h->N,
                       h->cfg.L / h->N, h->ctl, h->st));
   prof_end(h, &e);
-  // one device-to-host read of the control block
+  // one device-to-host read of the control block (its error word included) and one wait
   Ctl c;
   CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  const int rc = status_of(c.error);
+  if (rc != PIC_OK) return rc;
   const int N = h->N;
   std::memset(d, 0, sizeof(*d));
   const double dx = h->cfg.L / N;
