@@ -304,6 +304,48 @@ def adjoint_section(args, torch, pic) -> dict:
     return out
 
 
+class Ranks:
+    """Barrier, max and sum over the ranks of a torch.distributed process group (one process per
+    GPU, NCCL on the GPUs, gloo on the CPU); a lone process when ``dist`` is None.  A value travels
+    as a one-element float64 tensor on ``device``."""
+
+    def __init__(self, dist, device: str):
+        self.dist, self.device = dist, device
+
+    def barrier(self) -> None:
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x: float, op) -> float:
+        if self.dist is None:
+            return float(x)
+        import torch
+
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+
+def replica_params(workload: str, rank: int) -> dict:
+    """The run rank ``rank`` advances: the workload itself, seeded seed + 1000 * rank, so that the
+    replicas draw independent particles and collisions while each does a full run's work."""
+    base = W.CONFIGS[workload]
+    return W.variant(base, seed=base["seed"] + 1000 * rank)
+
+
+def whole_job(units: float, ms: float, ranks: Ranks):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time.
+    Returns (units per second, the slowest rank's milliseconds)."""
+    ms_max = ranks.max(ms)
+    return ranks.sum(units) / (ms_max / 1000.0), ms_max
+
+
 def run_ours(args, rank: int, world: int, local: int) -> None:
     import torch
 
@@ -316,27 +358,10 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ranks = Ranks(dist, "cuda")
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def allmax(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def allsum(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t)
-        return float(t.item())
-
-    # replicas: every rank advances its own simulation (seed + rank); no data-path collective
-    params = W.variant(W.CONFIGS[args.workload], seed=W.CONFIGS[args.workload]["seed"] + 1000 * rank)
+    # replicas: every rank advances its own simulation; no data-path collective
+    params = replica_params(args.workload, rank)
     sim = pic.Simulation(params)
     sim.step(args.warmup)
     sim.sync()
@@ -344,14 +369,12 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
-    barrier()
+    ranks.barrier()
     torch.cuda.synchronize()
     ms, ps, kt = timed_run(sim, torch, args.steps, profile=True)
-    barrier()
+    ranks.barrier()
     clk = clocks.stop() if clocks else None
-    ms_max = allmax(ms)
-    ps_all = allsum(ps)
-    value = ps_all / (ms_max / 1000.0)
+    value, ms_max = whole_job(ps, ms, ranks)
 
     peak, peak_kind = _peaks()
     # the dominant kernel: the ordinary step (48 B per particle); the step after each sort, which
@@ -383,7 +406,7 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         ps_sim.step(min(args.warmup, 5))
         ksteps = max(3, min(args.steps, args.plain_steps))
         pms, pps, _ = timed_run(ps_sim, torch, ksteps, profile=False)
-        plain = {"value": allsum(pps) / (allmax(pms) / 1000.0), "unit": "particle-steps/s",
+        plain = {"value": whole_job(pps, pms, ranks)[0], "unit": "particle-steps/s",
                  "ms_per_step": pms / ksteps, "steps": ksteps, "dtype": "f64"}
         ps_sim.close()
         del ps_sim
@@ -405,7 +428,7 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         ek = max(3, min(args.steps, args.e2e_steps))
         sim2 = pic.Simulation(params)
         sim2.set_diag_interval(1)  # diagnostics read after every step: summed inside the step
-        barrier()
+        ranks.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rc = pic.lib().pic_restore(sim2._h, pinned.data_ptr(), pinned.numel())
@@ -418,9 +441,8 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
             dsum = sim2.diag()["particle_steps"]
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        barrier()
-        et = allmax(t2 - t0)
-        e2e = {"value": allsum(dsum) / et, "unit": "particle-steps/s",
+        ranks.barrier()
+        e2e = {"value": whole_job(dsum, 1e3 * (t2 - t0), ranks)[0], "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(pinned.numel() / ek),
                "d2h_bytes_per_step": int(pic.lib().pic_diag_bytes()),
                "steps": ek, "restore_s": round(t1 - t0, 4), "ms_per_step": round(1e3 * (t2 - t1) / ek, 4),
