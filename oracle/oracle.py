@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the CP
 ``bench.py`` are the only users.  The GPU library and its binding never import this module.
 
 The oracle follows the PIC Monte Carlo cycle of the paper (Sec. 2) in plain FP64 loops; see the
-header comment of ``pic_oracle.c`` for the readings R1..R13 it implements.
+header comment of ``pic_oracle.c`` for the readings R1..R13 and N1..N6 it implements.
 """
 from __future__ import annotations
 
@@ -27,7 +27,7 @@ COLL_EL, COLL_EX, COLL_IZ, COLL_CX = 1, 2, 4, 8
 FIELD_SELF, FIELD_EXTERNAL, FIELD_ZERO = 0, 1, 2
 LOAD_UNIFORM, LOAD_EXP, LOAD_QUIET_SINE = 0, 1, 2
 SOURCE_NONE, SOURCE_PAIRS = 0, 1
-CH_INIT, CH_COLL, CH_SCAT, CH_CHILD, CH_SOURCE = 1, 2, 3, 4, 5
+CH_INIT, CH_COLL, CH_SCAT, CH_CHILD, CH_SOURCE, CH_RECYCLE, CH_NIZ = 1, 2, 3, 4, 5, 6, 7
 
 
 class OrcConfig(C.Structure):
@@ -43,6 +43,17 @@ class OrcConfig(C.Structure):
         ("sigma_iz", C.c_double), ("E_iz", C.c_double), ("sigma_cx", C.c_double),
         ("E_cap", C.c_double), ("E_ext", C.c_double), ("profile_scale", C.c_double),
         ("source_x1", C.c_double), ("seed", C.c_uint64),
+        ("smooth_passes", C.c_int32), ("neutrals", C.c_uint32), ("neutral_ppc", C.c_int32),
+        ("reserved", C.c_uint32), ("recycle", C.c_double),
+        ("T_rec", C.c_double), ("K_iz", C.c_double), ("T_sec", C.c_double),
+    ]
+
+
+class OrcNDiag(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint64), ("recycled", C.c_uint64 * 2), ("lost", C.c_uint64 * 2),
+        ("ionized", C.c_uint64), ("near_threshold", C.c_uint64), ("particle_steps", C.c_uint64),
+        ("ke", C.c_double),
     ]
 
 
@@ -104,6 +115,9 @@ def lib():
         L.orc_diag.argtypes = [C.c_void_p, P(OrcDiag)]
         L.orc_fields.argtypes = [C.c_void_p, P(C.c_int64), P(C.c_double), P(C.c_double),
                                  P(C.c_double)]
+        L.orc_neutral_diag.argtypes = [C.c_void_p, P(OrcNDiag)]
+        L.orc_smooth.argtypes = [C.c_int32, C.c_int32, P(C.c_double)]
+        L.orc_smooth.restype = None
         L.orc_count.argtypes = [C.c_void_p, C.c_int]
         L.orc_count.restype = C.c_uint64
         L.orc_particles.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double),
@@ -214,6 +228,13 @@ def load_particles(params: dict, species: int, indices) -> tuple:
     return x, v, ids
 
 
+def smooth(rho: np.ndarray, passes: int) -> np.ndarray:
+    """The density filter (passes of the binomial (1, 2, 1)/4 stencil, (1, 1)/2 at the walls)."""
+    out = np.array(rho, dtype=np.float64, copy=True)
+    lib().orc_smooth(len(out) - 1, int(passes), _ptr(out, C.c_double))
+    return out
+
+
 def set_threads(n: int) -> int:
     return int(lib().orc_set_threads(int(n)))
 
@@ -263,6 +284,14 @@ class OracleSim:
         d = OrcDiag()
         lib().orc_diag(self._h, C.byref(d))
         return _diag_dict(d)
+
+    def neutral_diag(self) -> dict:
+        d = OrcNDiag()
+        rc = lib().orc_neutral_diag(self._h, C.byref(d))
+        if rc != 0:
+            raise RuntimeError(f"orc_neutral_diag failed ({rc})")
+        return {"n": d.n, "recycled": list(d.recycled), "lost": list(d.lost), "ionized": d.ionized,
+                "near_threshold": d.near_threshold, "particle_steps": d.particle_steps, "ke": d.ke}
 
     def fields(self) -> dict:
         n1 = self.N + 1

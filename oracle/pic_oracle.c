@@ -23,6 +23,24 @@
  *   R11 child ids are Philox words of (parent id, step, CHILD channel).
  *   R12 CIC deposit in int64 fixed point: W_r = rint(f 2^32), W_l = 2^32 - W_r.
  *   R13 source: one (e, ion) pair per ion absorbed this step, uniform in [0, x1), Maxwellian.
+ *
+ * The D+/e/D sheath physics (Table 3: D+ ions recycled into D neutrals at the walls; Sec. 2:
+ * density smoothing), all off unless the configuration asks for it:
+ *   N1  species 2 are tracked neutrals of the ion's mass and weight, charge 0; at t = 0 either
+ *       none or neutral_ppc per cell, loaded like a uniform species at T_rec (ids 3 << 61 | i).
+ *   N2  an ion absorbed at a wall returns as a neutral with probability `recycle`, at that wall
+ *       (x = 0, or x = N - 2^-24 cells), v_x inward from the flux-weighted half-Maxwellian at
+ *       T_rec (|v_x| = v_t sqrt(-2 ln(1 - u))), v_y, v_z Maxwellian; it moves from the next step.
+ *   N3  neutrals move ballistically and are lost at either wall (x < 0 or x >= L).
+ *   N4  a neutral left inside ionizes with P = 1 - exp(-K_iz n_e(x) dt), n_e(x) the CIC
+ *       interpolation of the node electron density of the start-of-step deposit (half volume at
+ *       the walls, not smoothed); it becomes an ion (same x, v, id) and an electron is born at x,
+ *       Maxwellian at T_sec.  No electron loses the ionization energy (test-particle reading).
+ *   N5  step order: charged species (R2; recycling at the ion wall test), then the neutrals alive
+ *       at the step start, then births are appended, source, deposit, smoothing, Poisson, sort.
+ *   N6  smoothing: passes of rho'_j = (rho_{j-1} + 2 rho_j + rho_{j+1}) / 4 inside and
+ *       rho'_0 = (rho_0 + rho_1) / 2, rho'_N = (rho_{N-1} + rho_N) / 2 at the walls (with the
+ *       half-cell wall volume this keeps the total charge and a uniform density).
  */
 #include "pic_oracle.h"
 
@@ -202,6 +220,7 @@ typedef struct {
   uint64_t wall_hits[2];
   uint64_t coll[5];
   uint64_t near, viol;
+  uint64_t recycled[2]; /* ions that returned as neutrals, per wall (N2) */
 } orc_tcount;
 
 typedef struct {
@@ -220,8 +239,11 @@ struct orc_sim {
   double dx, w[2], qm[2], Bv[3];
   float nu_max[2], p_null[2];
   orc_species sp[2];
+  orc_species nt; /* tracked neutrals (N1) */
   int64_t* R[2];
   double *rho, *phi, *E;
+  double* ne; /* node electron density of the last deposit (N4) */
+  uint64_t nt_recycled[2], nt_lost[2], nt_ionized, nt_near, nt_particle_steps;
   uint64_t step;
   uint64_t wall_hits[2][2], coll[5], near[2], viol[2], births[2], source_pairs;
   int64_t wall_charge;
@@ -290,7 +312,28 @@ static int valid_config(const orc_config* c) {
   if (c->source_mode == ORC_SOURCE_PAIRS && !(c->source_x1 > 0 && c->source_x1 <= c->ncells))
     return 0;
   if (c->n_gas < 0 || c->Tg < 0 || !(c->m_gas > 0)) return 0;
+  if (c->smooth_passes < 0 || c->smooth_passes > ORC_MAX_SMOOTH || c->neutrals > 1u) return 0;
+  if (c->neutrals && !(c->recycle >= 0.0 && c->recycle <= 1.0 && c->T_rec >= 0.0 && c->K_iz >= 0.0 &&
+                       c->T_sec >= 0.0 && c->neutral_ppc >= 0))
+    return 0;
+  if (!c->neutrals && c->neutral_ppc != 0) return 0;
   return 1;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Density smoothing (Sec. 2, BIT1's smoothing operators; reading N6): each pass replaces the node
+ * density by the binomial (1, 2, 1)/4 average inside and the (1, 1)/2 average at a wall node.      */
+void orc_smooth(int32_t N, int32_t passes, double* rho) {
+  if (passes <= 0) return;
+  double* old = (double*)malloc(((size_t)N + 1) * sizeof(double));
+  if (!old) return;
+  for (int32_t p = 0; p < passes; ++p) {
+    memcpy(old, rho, ((size_t)N + 1) * sizeof(double));
+    rho[0] = (old[0] + old[1]) / 2.0;
+    for (int32_t j = 1; j < N; ++j) rho[j] = (old[j - 1] + 2.0 * old[j] + old[j + 1]) / 4.0;
+    rho[N] = (old[N - 1] + old[N]) / 2.0;
+  }
+  free(old);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -317,7 +360,9 @@ static void deposit_and_solve(orc_sim* s) {
     double q = 0.0;
     for (int sp = 0; sp < 2; ++sp) q += s->cfg.charge[sp] * s->w[sp] * ((double)s->R[sp][j] / TWO32);
     s->rho[j] = q / vol;
+    s->ne[j] = s->w[0] * ((double)s->R[0][j] / TWO32) / vol;
   }
+  orc_smooth(N, s->cfg.smooth_passes, s->rho);
   orc_poisson_thomas(N, s->dx, s->rho, s->cfg.V_left, s->cfg.V_right, s->phi);
   orc_efield(N, s->dx, s->phi, s->rho, s->E);
 }
@@ -359,6 +404,24 @@ static int sort_species(orc_species* p, int32_t N) {
  * i of species s has id i (electrons) or 2^62 | i (ions) and draws from its own Philox stream. */
 void orc_load_particle(const orc_config* c, int sp, uint64_t i, double* xo, double v[3], uint64_t* ido) {
   const int32_t N = c->ncells;
+  if (sp == 2) { /* initial neutrals (N1): uniform in each cell, Maxwellian at T_rec */
+    const uint64_t id = (3ull << 61) | i;
+    const double vt = sqrt(c->T_rec / c->mass[1]);
+    uint32_t w[4];
+    draw(id, c->seed, 0, ORC_CH_INIT, 0, w);
+    double x = (double)(i / (uint64_t)c->neutral_ppc) + u01(w[0]);
+    if (x >= (double)N) x = nextafter((double)N, 0.0);
+    draw(id, c->seed, 0, ORC_CH_INIT, 1, w);
+    double n0, n1, n2, n3;
+    box_muller(w[0], w[1], &n0, &n1);
+    box_muller(w[2], w[3], &n2, &n3);
+    *xo = x;
+    v[0] = vt * n0;
+    v[1] = vt * n1;
+    v[2] = vt * n2;
+    *ido = id;
+    return;
+  }
   const size_t np = (size_t)c->ppc[sp] * (size_t)N;
   const double vth = sqrt(c->T[sp] / c->mass[sp]);
   uint64_t id = (sp == 0) ? i : ((1ull << 62) | i);
@@ -404,6 +467,19 @@ static int load(orc_sim* s) {
     }
     p->n = np;
   }
+  if (c->neutrals && c->neutral_ppc > 0) {
+    size_t np = (size_t)c->neutral_ppc * (size_t)s->N;
+    if (sp_reserve(&s->nt, np) != ORC_OK) return ORC_ENOMEM;
+    orc_species* p = &s->nt;
+    for (size_t i = 0; i < np; ++i) {
+      double v[3];
+      orc_load_particle(c, 2, (uint64_t)i, &p->x[i], v, &p->id[i]);
+      p->vx[i] = v[0];
+      p->vy[i] = v[1];
+      p->vz[i] = v[2];
+    }
+    p->n = np;
+  }
   return ORC_OK;
 }
 
@@ -440,13 +516,15 @@ orc_sim* orc_create(const orc_config* cfg, int* err) {
   s->rho = (double*)calloc((size_t)s->N + 1, sizeof(double));
   s->phi = (double*)calloc((size_t)s->N + 1, sizeof(double));
   s->E = (double*)calloc((size_t)s->N + 1, sizeof(double));
-  if (!s->R[0] || !s->R[1] || !s->rho || !s->phi || !s->E) {
+  s->ne = (double*)calloc((size_t)s->N + 1, sizeof(double));
+  if (!s->R[0] || !s->R[1] || !s->rho || !s->phi || !s->E || !s->ne) {
     e = ORC_ENOMEM;
     goto out;
   }
   e = load(s);
   if (e != ORC_OK) goto out;
   for (int sp = 0; sp < 2; ++sp) sort_species(&s->sp[sp], s->N);
+  sort_species(&s->nt, s->N);
   deposit_and_solve(s);
 out:
   if (e != ORC_OK && s) {
@@ -467,9 +545,15 @@ void orc_free(orc_sim* s) {
     free(s->sp[sp].id);
     free(s->R[sp]);
   }
+  free(s->nt.x);
+  free(s->nt.vx);
+  free(s->nt.vy);
+  free(s->nt.vz);
+  free(s->nt.id);
   free(s->rho);
   free(s->phi);
   free(s->E);
+  free(s->ne);
   free(s);
 }
 
@@ -582,6 +666,56 @@ static void collide_ion(const orc_sim* s, uint64_t id, uint64_t step, double v[3
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Recycling of an ion absorbed at wall `side` (0 left, 1 right) in step `step` (reading N2):
+ * returns 1 and the new neutral when the ion returns.                                          */
+static int recycle_ion(const orc_sim* s, uint64_t id, uint64_t step, int side, orc_newp* out) {
+  const orc_config* c = &s->cfg;
+  uint32_t w[4], k[4];
+  draw(id, c->seed, step, ORC_CH_RECYCLE, 0, w);
+  if (!(u01(w[0]) < c->recycle)) return 0;
+  draw(id, c->seed, step, ORC_CH_RECYCLE, 1, k);
+  double vt = sqrt(c->T_rec / c->mass[1]);
+  double vx = vt * sqrt(-2.0 * log(1.0 - u01(w[1]))); /* flux-weighted half-Maxwellian */
+  double n0, n1;
+  box_muller(w[2], w[3], &n0, &n1);
+  out->x = side == 0 ? 0.0 : (double)s->N - 1.0 / 16777216.0;
+  out->v[0] = side == 0 ? vx : -vx;
+  out->v[1] = vt * n0;
+  out->v[2] = vt * n1;
+  out->id = (uint64_t)k[0] | ((uint64_t)k[1] << 32);
+  return 1;
+}
+
+/* Electron-impact ionization of a neutral at x in step `step` (reading N4): returns 1 and the
+ * electron it creates when the neutral ionizes; counts a draw within 1e-5 P of P in *near.     */
+static int ionize_neutral(const orc_sim* s, uint64_t id, uint64_t step, double x, uint64_t* near,
+                          orc_newp* e_new) {
+  const orc_config* c = &s->cfg;
+  int32_t cc = (int32_t)floor(x);
+  double f = x - (double)cc;
+  double ne = (1.0 - f) * s->ne[cc] + f * s->ne[cc + 1];
+  double P = 1.0 - exp(-c->K_iz * ne * c->dt);
+  uint32_t w[4];
+  draw(id, c->seed, step, ORC_CH_NIZ, 0, w);
+  double u = u01(w[0]);
+  if (fabs(u - P) < 1e-5 * P) (*near)++;
+  if (!(u < P)) return 0;
+  uint32_t b[4], k[4];
+  draw(id, c->seed, step, ORC_CH_NIZ, 1, b);
+  draw(id, c->seed, step, ORC_CH_NIZ, 2, k);
+  double vt = sqrt(c->T_sec / c->mass[0]);
+  double n0, n1, n2, n3;
+  box_muller(b[0], b[1], &n0, &n1);
+  box_muller(b[2], b[3], &n2, &n3);
+  e_new->x = x;
+  e_new->v[0] = vt * n0;
+  e_new->v[1] = vt * n1;
+  e_new->v[2] = vt * n2;
+  e_new->id = (uint64_t)k[0] | ((uint64_t)k[1] << 32);
+  return 1;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* One full step (R2).                                                                         */
 static int step_once(orc_sim* s) {
   const orc_config* c = &s->cfg;
@@ -589,10 +723,15 @@ static int step_once(orc_sim* s) {
   const uint64_t step = s->step;
   int nth = g_threads;
   s->particle_steps += s->sp[0].n + s->sp[1].n;
+  s->nt_particle_steps += s->nt.n;
   orc_tcount tcs[2][MAX_THREADS];
   orc_plist born[2][MAX_THREADS];
+  orc_plist nz_born[2][MAX_THREADS]; /* (electron, ion) of each neutral's ionization */
+  orc_plist recycled[MAX_THREADS];
   memset(tcs, 0, sizeof(tcs));
   memset(born, 0, sizeof(born));
+  memset(nz_born, 0, sizeof(nz_born));
+  memset(recycled, 0, sizeof(recycled));
   int err = ORC_OK;
 
   for (int sp = 0; sp < 2; ++sp) {
@@ -634,7 +773,15 @@ static int step_once(orc_sim* s) {
       xh += v[0] * c->dt / s->dx;
       /* walls (Table 3: plasma absorbed at the walls) */
       if (xh < 0.0 || xh >= (double)N) {
-        tc->wall_hits[xh < 0.0 ? 0 : 1]++;
+        const int side = xh < 0.0 ? 0 : 1;
+        tc->wall_hits[side]++;
+        if (sp == 1 && c->neutrals) { /* N2 */
+          orc_newp q;
+          if (recycle_ion(s, p->id[i], step, side, &q)) {
+            tc->recycled[side]++;
+            if (plist_add(&recycled[t], q.x, q.v, q.id) != ORC_OK) err = ORC_ENOMEM;
+          }
+        }
         eabs[i] = 0.5 * c->mass[sp] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * s->w[sp];
         alive[i] = 0;
         p->x[i] = xh;
@@ -695,8 +842,69 @@ static int step_once(orc_sim* s) {
       for (int k = 0; k < 5; ++k) s->coll[k] += tc->coll[k];
       s->near[sp] += tc->near;
       s->viol[sp] += tc->viol;
+      s->nt_recycled[0] += tc->recycled[0];
+      s->nt_recycled[1] += tc->recycled[1];
       if (sp == 1) ion_losses += tc->wall_hits[0] + tc->wall_hits[1];
     }
+  }
+
+  /* tracked neutrals alive at the step start: ballistic move, walls, ionization (N3, N4) */
+  if (c->neutrals && s->nt.n) {
+    orc_species* p = &s->nt;
+    const long long n = (long long)p->n;
+    unsigned char* keep = (unsigned char*)malloc((size_t)n);
+    uint64_t(*cnt)[4] = (uint64_t(*)[4])calloc(MAX_THREADS, sizeof(*cnt)); /* lost L, R, ionized, near */
+    if (!keep || !cnt) {
+      free(keep);
+      free(cnt);
+      return ORC_ENOMEM;
+    }
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nth) schedule(static)
+#endif
+    for (long long i = 0; i < n; ++i) {
+      int t = 0;
+#ifdef _OPENMP
+      t = omp_get_thread_num();
+#endif
+      double xh = p->x[i] + p->vx[i] * c->dt / s->dx;
+      if (xh < 0.0 || xh >= (double)N) {
+        cnt[t][xh < 0.0 ? 0 : 1]++;
+        keep[i] = 0;
+        continue;
+      }
+      p->x[i] = xh;
+      orc_newp e_new;
+      if (ionize_neutral(s, p->id[i], step, xh, &cnt[t][3], &e_new)) {
+        const double v[3] = {p->vx[i], p->vy[i], p->vz[i]};
+        if (plist_add(&nz_born[0][t], e_new.x, e_new.v, e_new.id) != ORC_OK ||
+            plist_add(&nz_born[1][t], xh, v, p->id[i]) != ORC_OK)
+          err = ORC_ENOMEM;
+        cnt[t][2]++;
+        keep[i] = 0;
+        continue;
+      }
+      keep[i] = 1;
+    }
+    size_t k = 0;
+    for (size_t i = 0; i < p->n; ++i) {
+      if (!keep[i]) continue;
+      p->x[k] = p->x[i];
+      p->vx[k] = p->vx[i];
+      p->vy[k] = p->vy[i];
+      p->vz[k] = p->vz[i];
+      p->id[k] = p->id[i];
+      ++k;
+    }
+    p->n = k;
+    for (int t = 0; t < MAX_THREADS; ++t) {
+      s->nt_lost[0] += cnt[t][0];
+      s->nt_lost[1] += cnt[t][1];
+      s->nt_ionized += cnt[t][2];
+      s->nt_near += cnt[t][3];
+    }
+    free(keep);
+    free(cnt);
   }
   for (int sp = 0; sp < 2; ++sp) {
     for (int t = 0; t < MAX_THREADS; ++t) {
@@ -707,6 +915,20 @@ static int step_once(orc_sim* s) {
       s->births[sp] += l->n;
       free(l->p);
     }
+  }
+  for (int sp = 0; sp < 2; ++sp) {
+    for (int t = 0; t < MAX_THREADS; ++t) {
+      orc_plist* l = &nz_born[sp][t];
+      for (size_t k = 0; k < l->n; ++k)
+        if (sp_push_back(&s->sp[sp], l->p[k].x, l->p[k].v, l->p[k].id) != ORC_OK) err = ORC_ENOMEM;
+      free(l->p);
+    }
+  }
+  for (int t = 0; t < MAX_THREADS; ++t) {
+    orc_plist* l = &recycled[t];
+    for (size_t k = 0; k < l->n; ++k)
+      if (sp_push_back(&s->nt, l->p[k].x, l->p[k].v, l->p[k].id) != ORC_OK) err = ORC_ENOMEM;
+    free(l->p);
   }
   if (err != ORC_OK) return err;
 
@@ -738,6 +960,7 @@ static int step_once(orc_sim* s) {
   if (step % (uint64_t)c->sort_interval == 0) {
     for (int sp = 0; sp < 2; ++sp)
       if (sort_species(&s->sp[sp], N) != ORC_OK) return ORC_ENOMEM;
+    if (sort_species(&s->nt, N) != ORC_OK) return ORC_ENOMEM;
   }
   s->step = step + 1;
   return ORC_OK;
@@ -812,14 +1035,44 @@ int orc_fields(orc_sim* s, int64_t* R, double* rho, double* phi, double* E) {
   return ORC_OK;
 }
 
+static orc_species* species_of(orc_sim* s, int species) {
+  if (!s || species < 0 || species > 2) return NULL;
+  return species == 2 ? &s->nt : &s->sp[species];
+}
+
 uint64_t orc_count(orc_sim* s, int species) {
-  if (!s || species < 0 || species > 1) return 0;
-  return s->sp[species].n;
+  orc_species* p = species_of(s, species);
+  return p ? p->n : 0;
+}
+
+int orc_neutral_diag(orc_sim* s, orc_ndiag_t* d) {
+  if (!s || !d) return ORC_EINVAL;
+  memset(d, 0, sizeof(*d));
+  orc_species* p = &s->nt;
+  d->n = p->n;
+  for (int k = 0; k < 2; ++k) {
+    d->recycled[k] = s->nt_recycled[k];
+    d->lost[k] = s->nt_lost[k];
+  }
+  d->ionized = s->nt_ionized;
+  d->near_threshold = s->nt_near;
+  d->particle_steps = s->nt_particle_steps;
+  /* neutrals carry the ion's mass and weight (N1); terms summed in ascending order */
+  double* e = (double*)malloc((p->n ? p->n : 1) * sizeof(double));
+  if (!e) return ORC_ENOMEM;
+  for (size_t i = 0; i < p->n; ++i)
+    e[i] = 0.5 * s->cfg.mass[1] * (p->vx[i] * p->vx[i] + p->vy[i] * p->vy[i] + p->vz[i] * p->vz[i]);
+  qsort(e, p->n, sizeof(double), cmp_double);
+  double ke = 0.0;
+  for (size_t i = 0; i < p->n; ++i) ke += e[i];
+  free(e);
+  d->ke = ke * s->w[1];
+  return ORC_OK;
 }
 
 int orc_particles(orc_sim* s, int species, double* x, double* v, uint64_t* id) {
-  if (!s || species < 0 || species > 1) return ORC_EINVAL;
-  orc_species* p = &s->sp[species];
+  orc_species* p = species_of(s, species);
+  if (!p) return ORC_EINVAL;
   for (size_t i = 0; i < p->n; ++i) {
     if (x) x[i] = p->x[i];
     if (v) {
@@ -841,7 +1094,9 @@ int orc_particles(orc_sim* s, int species, double* x, double* v, uint64_t* id) {
  *   u32 CRC-32 (IEEE 802.3, reflected, as zlib) of everything before it.
  * Particles are written in ascending id order within a species (canonical order), so two runs
  * that hold the same particle set write the same bytes.  This mirrors the checkpoint semantics
- * of Sec. 4.1 (per-species particle records; restart rebuilds positions and velocities).      */
+ * of Sec. 4.1 (per-species particle records; restart rebuilds positions and velocities).
+ * Version 2 (configurations with tracked neutrals) inserts before the CRC: u64 n_neutral |
+ * u64 recycled[2] | u64 lost[2] | u64 ionized | u64 near | the neutral records as above.     */
 #define SNAP_MAGIC "PICMCSN1"
 #define SNAP_HDR (8 + 4 + 4 + 8 + 8 + 16 + 17 * 8 + 8 + 16)
 
@@ -877,6 +1132,12 @@ uint64_t orc_config_hash(const orc_config* c) {
   fnv_bytes(&h, uv, sizeof(uv));
   fnv_bytes(&h, dv, sizeof(dv));
   fnv_bytes(&h, &c->seed, sizeof(uint64_t));
+  if (c->smooth_passes || c->neutrals) { /* the sheath-physics fields, when any is in use */
+    int32_t iv2[3] = {c->smooth_passes, (int32_t)c->neutrals, c->neutral_ppc};
+    double dv2[4] = {c->recycle, c->T_rec, c->K_iz, c->T_sec};
+    fnv_bytes(&h, iv2, sizeof(iv2));
+    fnv_bytes(&h, dv2, sizeof(dv2));
+  }
   return h;
 }
 
@@ -897,15 +1158,45 @@ static void put(unsigned char** q, const void* src, size_t n) {
   *q += n;
 }
 
+/* One species' records in ascending id order. */
+static int put_species(unsigned char** q, const orc_species* p) {
+  size_t n = p->n;
+  idx_key* ord = (idx_key*)malloc((n ? n : 1) * sizeof(idx_key));
+  if (!ord) return ORC_ENOMEM;
+  for (size_t i = 0; i < n; ++i) {
+    ord[i].id = p->id;
+    ord[i].i = i;
+  }
+  qsort(ord, n, sizeof(idx_key), cmp_key);
+  for (size_t k = 0; k < n; ++k) {
+    int32_t cc = (int32_t)floor(p->x[ord[k].i]);
+    put(q, &cc, 4);
+  }
+  for (size_t k = 0; k < n; ++k) {
+    double xh = p->x[ord[k].i];
+    double f = xh - floor(xh);
+    put(q, &f, 8);
+  }
+  double* arrs[3] = {p->vx, p->vy, p->vz};
+  for (int a = 0; a < 3; ++a)
+    for (size_t k = 0; k < n; ++k) put(q, &arrs[a][ord[k].i], 8);
+  for (size_t k = 0; k < n; ++k) put(q, &p->id[ord[k].i], 8);
+  free(ord);
+  return ORC_OK;
+}
+
+#define SNAP_NT_HDR (8 + 6 * 8)
+
 int orc_snapshot(orc_sim* s, void* buf, size_t cap, size_t* needed) {
   if (!s) return ORC_EINVAL;
   size_t need = SNAP_HDR + 4;
   for (int sp = 0; sp < 2; ++sp) need += s->sp[sp].n * 44;
+  if (s->cfg.neutrals) need += SNAP_NT_HDR + s->nt.n * 44;
   if (needed) *needed = need;
   if (!buf) return ORC_OK;
   if (cap < need) return ORC_EINVAL;
   unsigned char* q = (unsigned char*)buf;
-  uint32_t ver = 1, zero = 0;
+  uint32_t ver = s->cfg.neutrals ? 2 : 1, zero = 0;
   uint64_t h = orc_config_hash(&s->cfg), dropped = 0;
   put(&q, SNAP_MAGIC, 8);
   put(&q, &ver, 4);
@@ -925,30 +1216,16 @@ int orc_snapshot(orc_sim* s, void* buf, size_t cap, size_t* needed) {
   put(&q, &dropped, 8);
   put(&q, &s->wall_charge, 8);
   put(&q, s->wall_energy, 16);
-  for (int sp = 0; sp < 2; ++sp) {
-    orc_species* p = &s->sp[sp];
-    size_t n = p->n;
-    idx_key* ord = (idx_key*)malloc((n ? n : 1) * sizeof(idx_key));
-    if (!ord) return ORC_ENOMEM;
-    for (size_t i = 0; i < n; ++i) {
-      ord[i].id = p->id;
-      ord[i].i = i;
-    }
-    qsort(ord, n, sizeof(idx_key), cmp_key);
-    for (size_t k = 0; k < n; ++k) {
-      int32_t cc = (int32_t)floor(p->x[ord[k].i]);
-      put(&q, &cc, 4);
-    }
-    for (size_t k = 0; k < n; ++k) {
-      double xh = p->x[ord[k].i];
-      double f = xh - floor(xh);
-      put(&q, &f, 8);
-    }
-    double* arrs[3] = {p->vx, p->vy, p->vz};
-    for (int a = 0; a < 3; ++a)
-      for (size_t k = 0; k < n; ++k) put(&q, &arrs[a][ord[k].i], 8);
-    for (size_t k = 0; k < n; ++k) put(&q, &p->id[ord[k].i], 8);
-    free(ord);
+  for (int sp = 0; sp < 2; ++sp)
+    if (put_species(&q, &s->sp[sp]) != ORC_OK) return ORC_ENOMEM;
+  if (s->cfg.neutrals) {
+    uint64_t nn = s->nt.n;
+    put(&q, &nn, 8);
+    put(&q, s->nt_recycled, 16);
+    put(&q, s->nt_lost, 16);
+    put(&q, &s->nt_ionized, 8);
+    put(&q, &s->nt_near, 8);
+    if (put_species(&q, &s->nt) != ORC_OK) return ORC_ENOMEM;
   }
   uint32_t crc = crc32_ieee((const unsigned char*)buf, (size_t)(q - (unsigned char*)buf));
   put(&q, &crc, 4);
@@ -973,11 +1250,20 @@ int orc_restore(orc_sim* s, const void* buf, size_t len) {
   get(&q, &ver, 4);
   get(&q, &zero, 4);
   get(&q, &h, 8);
-  if (ver != 1 || h != orc_config_hash(&s->cfg)) return ORC_ECORRUPT;
+  if (ver != (s->cfg.neutrals ? 2u : 1u) || h != orc_config_hash(&s->cfg)) return ORC_ECORRUPT;
   get(&q, &step, 8);
   get(&q, &n[0], 8);
   get(&q, &n[1], 8);
-  if (len != SNAP_HDR + 4 + 44 * (n[0] + n[1])) return ORC_ECORRUPT;
+  uint64_t nn = 0;
+  if (n[0] > len / 44 || n[1] > len / 44) return ORC_ECORRUPT;
+  size_t charged = SNAP_HDR + 44 * (n[0] + n[1]);
+  if (ver == 2) {
+    if (len < charged + SNAP_NT_HDR + 4) return ORC_ECORRUPT;
+    memcpy(&nn, b + charged, 8);
+    if (nn > len / 44 || len != charged + SNAP_NT_HDR + 44 * nn + 4) return ORC_ECORRUPT;
+  } else if (len != charged + 4) {
+    return ORC_ECORRUPT;
+  }
   get(&q, s->wall_hits, 32);
   get(&q, s->coll, 40);
   get(&q, s->near, 16);
@@ -989,16 +1275,29 @@ int orc_restore(orc_sim* s, const void* buf, size_t len) {
   get(&q, s->wall_energy, 16);
   s->step = step;
   s->particle_steps = 0;
-  for (int sp = 0; sp < 2; ++sp) {
-    orc_species* p = &s->sp[sp];
-    if (sp_reserve(p, n[sp]) != ORC_OK) return ORC_ENOMEM;
+  s->nt.n = 0;
+  memset(s->nt_recycled, 0, sizeof(s->nt_recycled));
+  memset(s->nt_lost, 0, sizeof(s->nt_lost));
+  s->nt_ionized = s->nt_near = s->nt_particle_steps = 0;
+  for (int sp = 0; sp < 3; ++sp) {
+    if (sp == 2) {
+      if (ver != 2) break;
+      get(&q, &nn, 8);
+      get(&q, s->nt_recycled, 16);
+      get(&q, s->nt_lost, 16);
+      get(&q, &s->nt_ionized, 8);
+      get(&q, &s->nt_near, 8);
+    }
+    orc_species* p = sp == 2 ? &s->nt : &s->sp[sp];
+    const size_t ns = sp == 2 ? (size_t)nn : (size_t)n[sp];
+    if (sp_reserve(p, ns) != ORC_OK) return ORC_ENOMEM;
     const unsigned char* cell = q;
-    const unsigned char* frac = cell + 4 * n[sp];
-    const unsigned char* vx = frac + 8 * n[sp];
-    const unsigned char* vy = vx + 8 * n[sp];
-    const unsigned char* vz = vy + 8 * n[sp];
-    const unsigned char* id = vz + 8 * n[sp];
-    for (size_t i = 0; i < n[sp]; ++i) {
+    const unsigned char* frac = cell + 4 * ns;
+    const unsigned char* vx = frac + 8 * ns;
+    const unsigned char* vy = vx + 8 * ns;
+    const unsigned char* vz = vy + 8 * ns;
+    const unsigned char* id = vz + 8 * ns;
+    for (size_t i = 0; i < ns; ++i) {
       int32_t cc;
       double f;
       memcpy(&cc, cell + 4 * i, 4);
@@ -1011,10 +1310,11 @@ int orc_restore(orc_sim* s, const void* buf, size_t len) {
       memcpy(&p->vz[i], vz + 8 * i, 8);
       memcpy(&p->id[i], id + 8 * i, 8);
     }
-    p->n = n[sp];
-    q = id + 8 * n[sp];
+    p->n = ns;
+    q = id + 8 * ns;
   }
   for (int sp = 0; sp < 2; ++sp) sort_species(&s->sp[sp], s->N);
+  sort_species(&s->nt, s->N);
   deposit_and_solve(s);
   return ORC_OK;
 }

@@ -55,6 +55,10 @@ extern "C" {
 #define ORC_CH_SCAT 3u
 #define ORC_CH_CHILD 4u
 #define ORC_CH_SOURCE 5u
+#define ORC_CH_RECYCLE 6u /* recycling of an absorbed ion into a neutral */
+#define ORC_CH_NIZ 7u     /* electron-impact ionization of a tracked neutral */
+
+#define ORC_MAX_SMOOTH 4 /* passes of the density filter */
 
 typedef struct {
   int32_t ncells;         /* number of cells N (>= 2); nodes 0..N */
@@ -86,6 +90,16 @@ typedef struct {
   double profile_scale;   /* EXP: scale length (dx units); QUIET_SINE: amplitude (dx units) */
   double source_x1;       /* source region [0, source_x1) (dx units) */
   uint64_t seed;          /* run seed: part of every Philox key and counter */
+  /* D+/e/D sheath physics (Table 3: ions recycled into neutrals at the walls; Sec. 2: density
+   * smoothing).  Zero: none of it. */
+  int32_t smooth_passes;  /* binomial passes over the charge density before the solve (0..4) */
+  uint32_t neutrals;      /* 1: species 2, tracked neutrals of the ion mass, charge 0 */
+  int32_t neutral_ppc;    /* initial neutrals per cell: uniform, Maxwellian at T_rec (0: none) */
+  uint32_t reserved;      /* 0 */
+  double recycle;         /* probability that an ion absorbed at a wall returns as a neutral */
+  double T_rec;           /* temperature of the recycled neutrals (flux half-Maxwellian) */
+  double K_iz;            /* rate coefficient of electron-impact ionization of a neutral */
+  double T_sec;           /* temperature of the electron a neutral's ionization creates */
 } orc_config;
 
 typedef struct {
@@ -105,6 +119,17 @@ typedef struct {
   double wall_energy[2];         /* sum over absorbed particles of 0.5 m v^2 w */
   uint64_t particle_steps;       /* sum over steps of the live particles at step start */
 } orc_diag_t;
+
+/* Tracked neutrals (species 2), cumulative since creation unless stated. */
+typedef struct {
+  uint64_t n;                 /* live neutrals */
+  uint64_t recycled[2];       /* neutrals created by recycling at [0 = left, 1 = right] wall */
+  uint64_t lost[2];           /* neutrals absorbed at [left, right] wall */
+  uint64_t ionized;           /* neutrals ionized (each became an ion and created an electron) */
+  uint64_t near_threshold;    /* ionization draws within 1e-5 relative of the probability */
+  uint64_t particle_steps;    /* sum over steps of the live neutrals at step start */
+  double ke;                  /* sum 0.5 m v^2 w over live neutrals */
+} orc_ndiag_t;
 
 typedef struct orc_sim orc_sim;
 
@@ -126,7 +151,8 @@ void orc_boris(double qm, double dt, const double E[3], const double B[3], doubl
 /* Null-collision bound per species (R8), already rounded to FP32. */
 void orc_nu_max(const orc_config* cfg, float nu_max[2], float p_null[2]);
 
-/* Initial state of particle i of species sp (x in dx units, v, id) as the load creates it. */
+/* Initial state of particle i of species sp (x in dx units, v, id) as the load creates it;
+ * sp = 2: initial neutral i. */
 void orc_load_particle(const orc_config* cfg, int sp, uint64_t i, double* x, double v[3], uint64_t* id);
 
 /* Simulation object. */
@@ -137,7 +163,11 @@ int orc_diag(orc_sim* s, orc_diag_t* out);
 /* R: 2 x (N+1) int64 fixed-point deposits, rho/phi/E: N+1 nodes each; any may be NULL. */
 int orc_fields(orc_sim* s, int64_t* R, double* rho, double* phi, double* E);
 uint64_t orc_count(orc_sim* s, int species);
-/* Copies the live particles of a species in storage order: x_hat (dx units), v (n x 3), id. */
+int orc_neutral_diag(orc_sim* s, orc_ndiag_t* out);
+/* The density filter of smooth_passes passes, in place on a node density rho (N + 1 nodes). */
+void orc_smooth(int32_t N, int32_t passes, double* rho);
+/* Copies the live particles of a species (2: the neutrals) in storage order: x_hat (dx units),
+ * v (n x 3), id. */
 int orc_particles(orc_sim* s, int species, double* x, double* v, uint64_t* id);
 /* Snapshot blob (format shared by specification with the GPU library, written separately). */
 int orc_snapshot(orc_sim* s, void* buf, size_t cap, size_t* needed);

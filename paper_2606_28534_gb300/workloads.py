@@ -101,6 +101,16 @@ def small_ensemble(n: int = 9, seed: int = SEED0 + 40) -> list:
     return runs
 
 
+#: D+/e/D sheath (Table 3: D+ ions recycled into D neutrals at the walls; Sec. 2: density
+#: smoothing), on config 3's grid, load and source: deuterium ions (m_D / m_e = 3670.483), every ion
+#: absorbed at a wall returns as a tracked neutral (flux half-Maxwellian at T_rec = 0.1), a uniform
+#: neutral background of 763 per cell at t = 0 (50 M neutrals), electron-impact ionization of the
+#: neutrals with K_iz n_e dt = 2e-4 per step at n_e = 1, two smoothing passes; 150 M particles.
+M_D = 3670.483
+C6 = variant(C3, mass=(1.0, M_D), m_gas=M_D, smooth_passes=2, neutrals=1, neutral_ppc=763, recycle=1.0,
+             T_rec=0.1, K_iz=0.002, T_sec=1.0, neutral_capacity=1.15, seed=SEED0 + 6)
+C6_STEPS = 100
+
 #: config 5: collisionless adjoint case, 1024 cells x 200 ppc, 200 steps.
 C5 = variant(BASE, ncells=1024, L=1024.0, ppc=(200, 200), coll_mask=0, seed=SEED0 + 5)
 C5_STEPS = 200
@@ -113,8 +123,16 @@ SMALL_C3 = variant(C3, ncells=512, L=512.0, ppc=(41, 41), profile_scale=64.0, so
 #: strongly collisional: every process fires often, to exercise the collision paths.
 SMALL_COLL = variant(SMALL_C2, n_gas=25.0, ncells=48, L=48.0, ppc=(61, 61))
 
+#: the D+/e/D sheath, small: uniform plasma and neutrals on 96 cells, walls biased, ionization of
+#: the neutrals fast enough to fire every step
+SMALL_C6 = variant(C6, ncells=96, L=96.0, ppc=(53, 53), neutral_ppc=31, load_profile=LOAD_UNIFORM,
+                   source_mode=SOURCE_NONE, K_iz=0.5)
+
 #: profiling case: config 3's physics and profile with 1/8 of the particles (12.5 M, 350 MB of
 #: particle data: larger than L2, small enough for multi-pass counter captures)
 C3_PROFILE = variant(C3, ppc=(96, 96))
 
-CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c5": C5, "c3p": C3_PROFILE}
+#: the D+/e/D sheath with 1/8 of the particles (profiling case)
+C6_PROFILE = variant(C6, ppc=(96, 96), neutral_ppc=96)
+
+CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c5": C5, "c3p": C3_PROFILE, "c6": C6, "c6p": C6_PROFILE}

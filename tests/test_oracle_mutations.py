@@ -16,6 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 PINS_MAIN = ["tests/test_oracle_pins_numerics.py", "tests/test_oracle_pins_physics.py"]
 PINS_ADJ = ["tests/test_oracle_pins_adjoint.py"]
+PINS_SHEATH = ["tests/test_oracle_pins_sheath.py"]
 
 # (name, file, text as written, text with the mistake, pin files expected to catch it)
 MUTATIONS = [
@@ -67,6 +68,42 @@ MUTATIONS = [
      "grad[1] = gT / c->T[0];", PINS_ADJ),
     ("adjoint: position update without 1/dx", "pic_adjoint.c", "lv[3 * p] += lx[p] * c->dt / m.dx;",
      "lv[3 * p] += lx[p] * c->dt;", PINS_ADJ),
+    ("smoothing: wall node weights", "pic_oracle.c", "rho[0] = (old[0] + old[1]) / 2.0;",
+     "rho[0] = (3.0 * old[0] + old[1]) / 4.0;", PINS_SHEATH),
+    ("smoothing: interior weights", "pic_oracle.c",
+     "rho[j] = (old[j - 1] + 2.0 * old[j] + old[j + 1]) / 4.0;",
+     "rho[j] = (old[j - 1] + old[j] + old[j + 1]) / 3.0;", PINS_SHEATH),
+    ("smoothing left out of the solve", "pic_oracle.c", "orc_smooth(N, s->cfg.smooth_passes, s->rho);",
+     "(void)0;", PINS_SHEATH),
+    ("recycled neutral leaves outward", "pic_oracle.c", "out->v[0] = side == 0 ? vx : -vx;",
+     "out->v[0] = side == 0 ? -vx : vx;", PINS_SHEATH),
+    ("recycled neutral not flux-weighted", "pic_oracle.c",
+     "double vx = vt * sqrt(-2.0 * log(1.0 - u01(w[1])));",
+     "double vx = vt * fabs(sqrt(-2.0 * log(1.0 - u01(w[1]))) * cos(2.0 * ORC_PI * u01(w[2])));",
+     PINS_SHEATH),
+    ("recycled neutral born a cell inside the right wall", "pic_oracle.c",
+     "(double)s->N - 1.0 / 16777216.0", "(double)s->N - 1.0", PINS_SHEATH),
+    ("recycling probability inverted", "pic_oracle.c", "if (!(u01(w[0]) < c->recycle)) return 0;",
+     "if (!(u01(w[0]) >= c->recycle)) return 0;", PINS_SHEATH),
+    ("neutral move without 1/dx", "pic_oracle.c", "double xh = p->x[i] + p->vx[i] * c->dt / s->dx;",
+     "double xh = p->x[i] + p->vx[i] * c->dt;", PINS_SHEATH),
+    ("neutral ionization without dt", "pic_oracle.c", "double P = 1.0 - exp(-c->K_iz * ne * c->dt);",
+     "double P = 1.0 - exp(-c->K_iz * ne);", PINS_SHEATH),
+    ("electron density without the half-cell wall volume", "pic_oracle.c",
+     "s->ne[j] = s->w[0] * ((double)s->R[0][j] / TWO32) / vol;",
+     "s->ne[j] = s->w[0] * ((double)s->R[0][j] / TWO32) / s->dx;", PINS_SHEATH),
+    ("ionized neutral kept", "pic_oracle.c", "cnt[t][2]++;\n        keep[i] = 0;",
+     "cnt[t][2]++;\n        keep[i] = 1;", PINS_SHEATH),
+    ("ion of an ionized neutral takes the new electron's velocity", "pic_oracle.c",
+     "plist_add(&nz_born[1][t], xh, v, p->id[i])", "plist_add(&nz_born[1][t], xh, e_new.v, p->id[i])",
+     PINS_SHEATH),
+    ("new electron at the ion mass", "pic_oracle.c", "double vt = sqrt(c->T_sec / c->mass[0]);",
+     "double vt = sqrt(c->T_sec / c->mass[1]);", PINS_SHEATH),
+    ("initial neutrals at the ion temperature", "pic_oracle.c",
+     "const double vt = sqrt(c->T_rec / c->mass[1]);\n    uint32_t w[4];",
+     "const double vt = sqrt(c->T[1] / c->mass[1]);\n    uint32_t w[4];", PINS_SHEATH),
+    ("snapshot restore drops the ionization count", "pic_oracle.c", "get(&q, &s->nt_ionized, 8);",
+     "q += 8;", PINS_SHEATH),
 ]
 
 
