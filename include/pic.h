@@ -5,7 +5,9 @@
  * deposition of charge to the grid, field solve, interpolation of the field back to the
  * particles, and Monte Carlo collisions, for the bounded high-density sheath model of Table 3
  * (a magnetised plasma between two absorbing walls with a neutral background), advanced by
- * BIT1-style "natural sorting" of particles per cell (Sec. 2).  Checkpoint/restart semantics
+ * BIT1-style "natural sorting" of particles per cell (Sec. 2).  Optionally the D+/e/D sheath
+ * physics of Table 3 and Sec. 2: ions recycled into tracked neutrals at the walls, electron-impact
+ * ionization of those neutrals, and smoothing of the charge density before the field solve.  Checkpoint/restart semantics
  * (per-species particle records from which the run resumes exactly) follow Sec. 4.1.
  *
  * Conventions for every call:
@@ -29,7 +31,7 @@
 extern "C" {
 #endif
 
-#define PIC_ABI_VERSION 1u
+#define PIC_ABI_VERSION 2u
 
 /* status codes */
 #define PIC_OK 0
@@ -68,7 +70,21 @@ extern "C" {
 
 /* Configuration.  Plain old data; abi_version must be PIC_ABI_VERSION.  Species 0 are the
  * electrons (the only species that ionize, excite and scatter elastically); species 1 are the
- * ions (charge exchange).  Weight of a macro-particle: w_s = dx / ppc_s (n0 = 1). */
+ * ions (charge exchange).  Weight of a macro-particle: w_s = dx / ppc_s (n0 = 1).
+ *
+ * Sheath physics (all zero: off).  neutrals = 1 adds species 2, tracked neutrals with the ion's
+ * mass and weight and no charge: neutral_ppc per cell at t = 0 (uniform in each cell, Maxwellian at
+ * T_rec; ids 3 << 61 | i); an ion absorbed at a wall returns with probability `recycle` as a
+ * neutral on that wall (x = 0, or the last FP32 fraction of the last cell), its v_x inward from the
+ * flux-weighted half-Maxwellian at T_rec and v_y, v_z Maxwellian; neutrals move in straight lines
+ * and are lost at either wall; a neutral inside ionizes with probability 1 - exp(-K_iz n_e(x) dt),
+ * n_e(x) the CIC interpolation of the node electron density of the last deposit (half-cell volume
+ * at the walls), becoming an ion (same position, velocity and id) beside a new electron, Maxwellian
+ * at T_sec.  smooth_passes > 0 replaces the charge density, before the field solve, smooth_passes
+ * times by (rho_{j-1} + 2 rho_j + rho_{j+1}) / 4 inside and (rho_0 + rho_1) / 2,
+ * (rho_{N-1} + rho_N) / 2 at the walls (total charge kept); pic_get_field then returns the smoothed
+ * rho and its phi.  Both need PIC_FP32 with integer charges |q| <= 64; neutrals need ion capacity
+ * below 2^31.  Not available in ensembles (pic_batch_*) or in the adjoint (pic_adj_*). */
 typedef struct pic_config {
   uint32_t abi_version;
   uint32_t precision;     /* PIC_FP32 or PIC_FP64_PLAIN */
@@ -102,6 +118,15 @@ typedef struct pic_config {
   double source_x1;       /* end of the source region (cells), 0 < source_x1 <= N */
   double capacity_factor; /* particle buffer capacity per species = factor * ppc * N (>= 1) */
   uint64_t seed;          /* run seed (enters every Philox key and counter) */
+  int32_t smooth_passes;  /* density smoothing passes before the field solve, 0 .. 4 */
+  uint32_t neutrals;      /* 1: tracked neutrals (species 2), recycling, their ionization */
+  int32_t neutral_ppc;    /* initial neutrals per cell (0 .. ; 0 when neutrals == 0) */
+  uint32_t reserved;      /* 0 */
+  double recycle;         /* probability that an absorbed ion returns as a neutral, [0, 1] */
+  double T_rec;           /* temperature of recycled and initial neutrals */
+  double K_iz;            /* rate coefficient of electron-impact ionization of a neutral */
+  double T_sec;           /* temperature of the electron a neutral's ionization creates */
+  double neutral_capacity; /* neutral buffer capacity = factor * max(neutral_ppc, ppc[1]) * N (>= 1) */
 } pic_config;
 
 /* Diagnostics (cumulative since pic_init unless stated). */
@@ -123,6 +148,18 @@ typedef struct pic_diag {
   uint64_t particle_steps;       /* sum over steps of the live particles at the start of each
                                     step, since pic_init / pic_restore (the throughput unit) */
 } pic_diag_t;
+
+/* Tracked neutrals (cumulative since pic_init unless stated). */
+typedef struct pic_neutral_diag {
+  uint64_t n;                 /* live neutrals (exact) */
+  uint64_t recycled[2];       /* neutrals created by recycling at [0 = left, 1 = right] wall */
+  uint64_t lost[2];           /* neutrals absorbed at [left, right] wall */
+  uint64_t ionized;           /* neutrals ionized (each became an ion beside a new electron) */
+  uint64_t near_threshold;    /* ionization draws within 1e-5 relative of the probability */
+  uint64_t particle_steps;    /* sum over steps of the live neutrals at the start of each step,
+                                 since pic_init / pic_restore */
+  double ke;                  /* sum of 0.5 m v^2 w over live neutrals */
+} pic_neutral_diag_t;
 
 typedef struct pic_handle pic_handle;
 
@@ -157,7 +194,9 @@ int pic_sync(pic_handle* h);
  * Version-1 blob, little-endian: "PICMCSN1", u32 version, u32 0, u64 config hash, u64 step,
  * u64 n[2], u64 counters[17], i64 wall_charge, f64 wall_energy[2], then per species
  * i32 cell[n], f64 frac[n], f64 vx[n], f64 vy[n], f64 vz[n], u64 id[n] in ascending id order,
- * then the CRC-32 (IEEE, as zlib) of all preceding bytes.  Synchronises the stream. */
+ * then the CRC-32 (IEEE, as zlib) of all preceding bytes.  With neutrals the blob is version 2:
+ * before the CRC come u64 n_neutral, u64 recycled[2], u64 lost[2], u64 ionized, u64 near and the
+ * neutrals' records in the same layout.  Synchronises the stream. */
 int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed);
 
 /* Replace the state by a blob from pic_snapshot (or any writer of the same format) made with
@@ -169,6 +208,10 @@ int pic_restore(pic_handle* h, const void* buf, size_t len);
 /* Diagnostics; reduces on the device, then one read of the control block and one wait on the
  * stream.  *out is filled only when the call returns PIC_OK (otherwise: the device-side error). */
 int pic_diag(pic_handle* h, pic_diag_t* out);
+
+/* Neutral diagnostics (PIC_EINVAL without neutrals); as pic_diag: one pass over the neutrals for
+ * their kinetic energy, one read of the control block, one wait. */
+int pic_neutral_diag(pic_handle* h, pic_neutral_diag_t* out);
 
 /* Bytes one pic_diag copies from the device to the host (the control block of counters and
  * partial sums): the device-to-host traffic of reading the diagnostics. */
@@ -182,7 +225,7 @@ int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E,
 /* Per-kernel device time via CUDA events on the handle's stream.  enable != 0 starts recording
  * (adds two event records per launch); pic_kernel_times synchronises and returns, for up to
  * nkinds kernel kinds, total milliseconds, launch counts and names. */
-#define PIC_KERNEL_KINDS 8
+#define PIC_KERNEL_KINDS 9
 int pic_profile(pic_handle* h, int enable);
 int pic_kernel_times(pic_handle* h, double* ms, uint64_t* launches, const char** names,
                      int32_t nkinds);
@@ -224,8 +267,9 @@ int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double
  * load (profile, T), the collision set and every collision parameter (n_gas, sigma_*, E_*, E_cap,
  * Tg, m_gas), the wall potentials, capacity_factor and the seed.  What they must share: dt, the
  * cell size L / ncells, B and its angle, the species masses and charges, frozen_mask, field_mode,
- * E_ext and sort_interval.  Every simulation must use PIC_FP32, PIC_SOURCE_NONE and integer
- * species charges (the integer-exact field solve); 1 <= nsims <= PIC_BATCH_MAX_SIMS; the
+ * E_ext and sort_interval.  Every simulation must use PIC_FP32, PIC_SOURCE_NONE, integer
+ * species charges (the integer-exact field solve) and none of the sheath physics (neutrals 0,
+ * smooth_passes 0); 1 <= nsims <= PIC_BATCH_MAX_SIMS; the
  * particle capacities of each species together below 2^31.  Anything else: PIC_EINVAL.
  *
  * Conventions are those of the single-simulation calls: the caller owns host buffers, work runs on
@@ -320,7 +364,8 @@ void pic_batch_free(pic_batch* b);
  * The adjoint stores the particle state every `checkpoint_every` steps and the node field of every
  * step during a recording forward, and recomputes each segment of checkpoint_every steps from its
  * checkpoint during the reverse sweep (memory: about (steps / checkpoint_every + checkpoint_every)
- * x 20 bytes per particle).  Configurations: coll_mask 0, PIC_SOURCE_NONE, T[0] > 0 (precision
+ * x 20 bytes per particle).  Configurations: coll_mask 0, PIC_SOURCE_NONE, T[0] > 0, no sheath
+ * physics (neutrals 0, smooth_passes 0) (precision
  * and sort_interval are ignored); 1 <= checkpoint_every <= steps.  Work runs on cuda_stream; the
  * forward and gradient calls synchronise it. */
 typedef struct pic_adj pic_adj;

@@ -15,7 +15,7 @@
 namespace picx {
 
 const char* const kKindNames[PIC_KERNEL_KINDS] = {"step", "source", "field", "sort", "load", "diag", "plan",
-                                                   "step_scatter"};
+                                                   "step_scatter", "neutral"};
 
 
 // ---------------------------------------------------------------------------------------------
@@ -39,12 +39,31 @@ bool valid(const pic_config* c) {
   const double n = (double)c->ppc[0] * c->ncells * c->capacity_factor;
   const double m = (double)c->ppc[1] * c->ncells * c->capacity_factor;
   if (n > 2.0e9 || m > 2.0e9) return false;  // u32 cell cursors
+  // sheath physics: FP32 path with the integer-exact field solve only
+  if (c->reserved != 0u || c->neutrals > 1u || c->smooth_passes < 0 || c->smooth_passes > PIC_MAX_SMOOTH)
+    return false;
+  if ((c->neutrals || c->smooth_passes) && (c->precision != PIC_FP32 || !exact_possible(*c))) return false;
+  if (c->neutrals) {
+    if (!(c->recycle >= 0.0 && c->recycle <= 1.0) || !(c->T_rec >= 0.0) || !(c->K_iz >= 0.0) ||
+        !(c->T_sec >= 0.0) || c->neutral_ppc < 0 || !(c->neutral_capacity >= 1.0) || !(c->neutral_capacity <= 64.0))
+      return false;
+    if ((double)std::max(c->neutral_ppc, c->ppc[1]) * c->ncells * c->neutral_capacity > 2.0e9) return false;
+  } else if (c->neutral_ppc != 0) {
+    return false;
+  }
   return true;
 }
 
 unsigned long long capacity(const pic_config* c, int s) {
   double n = std::ceil((double)c->ppc[s] * (double)c->ncells * c->capacity_factor);
   unsigned long long v = (unsigned long long)n + 4ull;
+  return (v + 1023ull) & ~1023ull;
+}
+
+unsigned long long neutral_capacity(const pic_config* c) {
+  if (!c->neutrals) return 0ull;
+  const double n = std::ceil((double)std::max(c->neutral_ppc, c->ppc[1]) * (double)c->ncells * c->neutral_capacity);
+  const unsigned long long v = (unsigned long long)n + 4ull;
   return (v + 1023ull) & ~1023ull;
 }
 
@@ -83,6 +102,19 @@ void layout(pic_handle* h, char* base, size_t* total) {
       h->cursor[s] = cv.take<unsigned int>(N);
     }
     h->E2 = cv.take<float2>(N);
+    if (h->cap_nt) {
+      for (int b = 0; b < 2; ++b) {
+        Species32& a = h->nt[b];
+        a.cell = cv.take<int>(h->cap_nt);
+        a.frac = cv.take<float>(h->cap_nt);
+        a.vx = cv.take<float>(h->cap_nt);
+        a.vy = cv.take<float>(h->cap_nt);
+        a.vz = cv.take<float>(h->cap_nt);
+        a.id = cv.take<unsigned long long>(h->cap_nt);
+      }
+      h->NE2 = cv.take<float2>(N);
+      h->wlog = cv.take<unsigned int>(h->cap[1]);
+    }
   } else {
     for (int s = 0; s < 2; ++s) {
       Species64& a = h->a64[s];
@@ -222,7 +254,28 @@ StepParams32 params32(pic_handle* h) {
     P.src[s] = P.sp[s];
     P.cursor[s] = h->cursor[s];
   }
+  P.wlog = (h->cap_nt && h->cfg.recycle > 0.0) ? h->wlog : nullptr;
   return P;
+}
+
+// The neutral step of a particle step with parameters P (its charged buffers and counters).
+NeutralParams neutral_params(pic_handle* h, const StepParams32& P) {
+  NeutralParams Q;
+  std::memset(&Q, 0, sizeof(Q));
+  const pic_config& c = h->cfg;
+  Q.P = P;
+  Q.src = h->nt[h->nt_buf];
+  Q.dst = h->nt[1 - h->nt_buf];
+  Q.cap = h->cap_nt;
+  Q.ion_id = P.src[1].id;
+  Q.NE2 = h->NE2;
+  Q.Kdt = (float)(c.K_iz * c.dt);
+  Q.vt_rec = (float)std::sqrt(c.T_rec / c.mass[1]);
+  Q.vt_sec = (float)std::sqrt(c.T_sec / c.mass[0]);
+  Q.mass = (float)c.mass[1];
+  Q.recycle_u24 = (unsigned)std::ceil(c.recycle * 16777216.0);
+  Q.ionize = c.K_iz > 0.0 ? 1 : 0;
+  return Q;
 }
 
 StepParams64 params64(pic_handle* h) {
@@ -267,8 +320,10 @@ void exact_coefficients(pic_handle* h, PoissonParams* F) {
   const int N = c.ncells;
   const double dx = c.L / N;
   const double kappa = dx * dx * 2.3283064365386963e-10 * (double)g / ((double)c.ppc[0] * (double)c.ppc[1]);
-  F->e_in = kappa / (2.0 * N * dx);
-  F->e_wall = kappa / ((double)N * dx);
+  // smoothing leaves the net charge in units of 2^-(2 passes + 1) of the deposit unit
+  const double unit = c.smooth_passes > 0 ? std::ldexp(1.0, -(2 * c.smooth_passes + 1)) : 1.0;
+  F->e_in = unit * kappa / (2.0 * N * dx);
+  F->e_wall = unit * kappa / ((double)N * dx);
   F->e_bias = (c.V_left - c.V_right) / ((double)N * dx);
   F->exact = 1;
 }
@@ -302,6 +357,10 @@ PoissonParams field_params(pic_handle* h, bool keep_counts, bool count_step) {
   F.E2 = h->E2;
   F.ctl = h->ctl;
   F.plain = h->plain ? 1 : 0;
+  F.smooth = h->cfg.smooth_passes;
+  F.NE2 = h->NE2;
+  F.ne_scale = (dx / h->cfg.ppc[0]) * 2.3283064365386963e-10 / dx;
+  F.nt_cap = h->cap_nt;
   return F;
 }
 
@@ -405,8 +464,30 @@ int load_initial(pic_handle* h) {
         }
       }
     }
+    if (rc == PIC_OK && h->cap_nt) {  // initial neutrals into buffer 0
+      h->nt_buf = 0;
+      const unsigned long long nn = (unsigned long long)c.neutral_ppc * (unsigned long long)c.ncells;
+      if (round_up4(nn) > h->cap_nt) {
+        rc = PIC_EOVERFLOW;
+      } else {
+        EvPair e;
+        prof_begin(h, K_LOAD, &e);
+        if (launch_nload32(h->nt[0], nn, c.neutral_ppc, c.ncells, c.seed, std::sqrt(c.T_rec / c.mass[1]), h->st) !=
+            cudaSuccess)
+          rc = PIC_ECUDA;
+        prof_end(h, &e);
+        const int dead[4] = {PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL};
+        if (rc == PIC_OK && round_up4(nn) > nn &&
+            cudaMemcpyAsync(h->nt[0].cell + nn, dead, 4 * (round_up4(nn) - nn), cudaMemcpyHostToDevice, h->st) !=
+                cudaSuccess)
+          rc = PIC_ECUDA;
+        c0.nt_cur = round_up4(nn);
+        c0.nt_live = nn;
+      }
+    }
     if (rc == PIC_OK && cudaMemcpyAsync(h->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
       rc = PIC_ECUDA;
+    if (rc == PIC_OK) rc = cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : PIC_ECUDA;  // c0 is on the stack
     if (rc == PIC_OK) rc = refresh_field(h);
     if (rc == PIC_OK) rc = check_errors(h);
   }
@@ -516,11 +597,12 @@ struct Fnv {
   }
 };
 
-// Canonical physics fields (precision, sort interval and capacity excluded): int32 ncells,
+// Canonical physics fields (precision, sort interval and capacities excluded): int32 ncells,
 // ppc[2], load_profile, profile_mode, source_mode; uint32 coll_mask, field_mode, frozen_mask;
 // f64 L, dt, mass[2], charge[2], T[2], Tg, m_gas, B, B_angle_deg, V_left, V_right, n_gas,
 // sigma_el, sigma_ex, E_ex, sigma_iz, E_iz, sigma_cx, E_cap, E_ext, profile_scale, source_x1;
-// u64 seed; all little-endian.
+// u64 seed; then, when smoothing or neutrals are on, int32 smooth_passes, neutrals, neutral_ppc;
+// f64 recycle, T_rec, K_iz, T_sec; all little-endian.
 uint64_t config_hash(const pic_config& c) {
   Fnv f;
   const int32_t iv[6] = {c.ncells, c.ppc[0], c.ppc[1], c.load_profile, c.profile_mode, c.source_mode};
@@ -533,10 +615,17 @@ uint64_t config_hash(const pic_config& c) {
   f.add(uv, sizeof(uv));
   f.add(dv, sizeof(dv));
   f.add(&c.seed, sizeof(c.seed));
+  if (c.smooth_passes || c.neutrals) {  // the sheath-physics fields, when any is in use
+    const int32_t iv2[3] = {c.smooth_passes, (int32_t)c.neutrals, c.neutral_ppc};
+    const double dv2[4] = {c.recycle, c.T_rec, c.K_iz, c.T_sec};
+    f.add(iv2, sizeof(iv2));
+    f.add(dv2, sizeof(dv2));
+  }
   return f.h;
 }
 
 const size_t kHdr = 8 + 4 + 4 + 8 + 8 + 16 + 17 * 8 + 8 + 16;
+const size_t kNtHdr = 8 + 6 * 8;  // version 2: u64 n_neutral, u64 recycled[2], lost[2], ionized, near
 
 struct HostParticles {
   std::vector<int32_t> cell;
@@ -608,6 +697,42 @@ int fetch_particles(pic_handle* h, HostParticles out[2], Ctl* ctl) {
   return PIC_OK;
 }
 
+// The live neutrals (FP32 buffer a, extent n) in ascending id order.
+int fetch_neutrals(pic_handle* h, const Species32& a, size_t n, HostParticles& o) {
+  std::vector<int32_t> cell(n);
+  std::vector<float> f(n), vx(n), vy(n), vz(n);
+  std::vector<uint64_t> id(n);
+  CK(cudaMemcpy(cell.data(), a.cell, n * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(f.data(), a.frac, n * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(vx.data(), a.vx, n * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(vy.data(), a.vy, n * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(vz.data(), a.vz, n * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(id.data(), a.id, n * 8, cudaMemcpyDeviceToHost));
+  (void)h;
+  std::vector<size_t> live;
+  live.reserve(n);
+  for (size_t i = 0; i < n; ++i)
+    if (cell[i] != PIC_DEAD_CELL) live.push_back(i);
+  std::sort(live.begin(), live.end(), [&](size_t x, size_t y) { return id[x] < id[y]; });
+  const size_t m = live.size();
+  o.cell.resize(m);
+  o.frac.resize(m);
+  o.vx.resize(m);
+  o.vy.resize(m);
+  o.vz.resize(m);
+  o.id.resize(m);
+  for (size_t k = 0; k < m; ++k) {
+    const size_t i = live[k];
+    o.cell[k] = cell[i];
+    o.frac[k] = f[i];
+    o.vx[k] = vx[i];
+    o.vy[k] = vy[i];
+    o.vz[k] = vz[i];
+    o.id[k] = id[i];
+  }
+  return PIC_OK;
+}
+
 template <class T>
 void put(std::vector<unsigned char>& b, const T& v) {
   const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
@@ -633,18 +758,29 @@ int check_blob(const pic_handle* h, const void* buf, size_t len) {
   std::memcpy(&hash, b + 16, 8);
   std::memcpy(&step, b + 24, 8);
   std::memcpy(n, b + 32, 16);
-  if (ver != 1 || hash != config_hash(h->cfg)) return PIC_ECORRUPT;
-  if (n[0] > (1ull << 40) || n[1] > (1ull << 40) || len != kHdr + 4 + 44 * (n[0] + n[1])) return PIC_ECORRUPT;
+  if (ver != (h->cap_nt ? 2u : 1u) || hash != config_hash(h->cfg)) return PIC_ECORRUPT;
+  if (n[0] > (1ull << 40) || n[1] > (1ull << 40)) return PIC_ECORRUPT;
+  const size_t charged = kHdr + 44 * (size_t)(n[0] + n[1]);
+  uint64_t nn = 0;
+  if (ver == 2) {  // the neutral block: u64 n, u64 counters[6], records
+    if (len < charged + kNtHdr + 4) return PIC_ECORRUPT;
+    std::memcpy(&nn, b + charged, 8);
+    if (nn > (1ull << 40) || len != charged + kNtHdr + 44 * nn + 4) return PIC_ECORRUPT;
+    if (round_up4(nn) > h->cap_nt) return PIC_EOVERFLOW;
+  } else if (len != charged + 4) {
+    return PIC_ECORRUPT;
+  }
   for (int s = 0; s < 2; ++s)
     if (round_up4(n[s]) > h->cap[s]) return PIC_EOVERFLOW;
   const int N = h->N;
   // range of every cell and fraction (host threads)
   {
-    size_t off = kHdr;
+    const size_t offs[3] = {kHdr, kHdr + 44 * (size_t)n[0], charged + kNtHdr};
+    const uint64_t counts[3] = {n[0], n[1], nn};
     bool bad = false;
-    for (int s = 0; s < 2; ++s) {
-      const size_t m = (size_t)n[s];
-      const unsigned char* cell = b + off;
+    for (int s = 0; s < 3; ++s) {
+      const size_t m = (size_t)counts[s];
+      const unsigned char* cell = b + offs[s];
       const unsigned char* frac = cell + 4 * m;
       const int T = host_threads(12 * m);
       std::vector<char> flag(T, 0);
@@ -667,7 +803,6 @@ int check_blob(const pic_handle* h, const void* buf, size_t len) {
       }
       for (auto& t : th) t.join();
       for (char f : flag) bad = bad || f;
-      off += 44 * m;
     }
     if (bad) return PIC_ECORRUPT;
   }
@@ -695,38 +830,43 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
   const double dx = h->cfg.L / N;
   size_t off = kHdr;
   h->cur = 0;
+  // FP32: a species' arrays (m records at blob offset o) go straight to device staging (the sort's
+  // second buffer, unused between sorts) and a kernel converts them into dst
+  auto upload32 = [&](size_t o, size_t m, const Species32& dstsp) -> int {
+    char* stage = h->stage;
+    const size_t stage_bytes = h->stage_bytes;
+    const size_t per = std::max<size_t>(4, (stage_bytes - 6 * 256) / 44 / 4 * 4);
+    const unsigned char* src[6] = {b + o, b + o + 4 * m, b + o + 12 * m, b + o + 20 * m, b + o + 28 * m,
+                                   b + o + 36 * m};
+    const size_t width[6] = {4, 8, 8, 8, 8, 8};
+    for (size_t done = 0; done < m; done += per) {
+      const size_t cnt_i = std::min(per, m - done);
+      char* dst[6];
+      size_t so = 0;
+      for (int a = 0; a < 6; ++a) {
+        dst[a] = stage + so;
+        so += (width[a] * cnt_i + 255) & ~size_t(255);
+        CK(cudaMemcpyAsync(dst[a], src[a] + width[a] * done, width[a] * cnt_i, cudaMemcpyHostToDevice, h->st));
+      }
+      CK(launch_restore32(reinterpret_cast<const int*>(dst[0]), reinterpret_cast<const double*>(dst[1]),
+                          reinterpret_cast<const double*>(dst[2]), reinterpret_cast<const double*>(dst[3]),
+                          reinterpret_cast<const double*>(dst[4]), reinterpret_cast<const unsigned long long*>(dst[5]),
+                          cnt_i, dstsp, done, N, h->st));
+    }
+    const size_t mp = (size_t)round_up4(m);
+    if (mp > m) {
+      const int dead[4] = {PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL};
+      CK(cudaMemcpyAsync(dstsp.cell + m, dead, 4 * (mp - m), cudaMemcpyHostToDevice, h->st));
+    }
+    CK(cudaStreamSynchronize(h->st));
+    return PIC_OK;
+  };
   for (int s = 0; s < 2; ++s) {
     const size_t m = (size_t)n[s];
     const size_t mp = (size_t)round_up4(m);
     if (!h->plain) {
-      // the blob's arrays go straight to device staging (the sort's second buffer, unused
-      // between sorts) and a kernel converts them into buffer 0
-      char* stage = h->stage;
-      const size_t stage_bytes = h->stage_bytes;
-      const size_t per = std::max<size_t>(4, (stage_bytes - 6 * 256) / 44 / 4 * 4);
-      const unsigned char* src[6] = {b + off, b + off + 4 * m, b + off + 12 * m, b + off + 20 * m,
-                                     b + off + 28 * m, b + off + 36 * m};
-      const size_t width[6] = {4, 8, 8, 8, 8, 8};
-      for (size_t done = 0; done < m; done += per) {
-        const size_t cnt_i = std::min(per, m - done);
-        char* dst[6];
-        size_t o = 0;
-        for (int a = 0; a < 6; ++a) {
-          dst[a] = stage + o;
-          o += (width[a] * cnt_i + 255) & ~size_t(255);
-          CK(cudaMemcpyAsync(dst[a], src[a] + width[a] * done, width[a] * cnt_i, cudaMemcpyHostToDevice, h->st));
-        }
-        CK(launch_restore32(reinterpret_cast<const int*>(dst[0]), reinterpret_cast<const double*>(dst[1]),
-                            reinterpret_cast<const double*>(dst[2]), reinterpret_cast<const double*>(dst[3]),
-                            reinterpret_cast<const double*>(dst[4]),
-                            reinterpret_cast<const unsigned long long*>(dst[5]), cnt_i, h->a32[0][s], done, N,
-                            h->st));
-      }
-      if (mp > m) {
-        const int dead[4] = {PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL, PIC_DEAD_CELL};
-        CK(cudaMemcpyAsync(h->a32[0][s].cell + m, dead, 4 * (mp - m), cudaMemcpyHostToDevice, h->st));
-        CK(cudaStreamSynchronize(h->st));
-      }
+      const int rc = upload32(off, m, h->a32[0][s]);
+      if (rc != PIC_OK) return rc;
     } else {
       std::vector<double> x(mp, -1.0), a1(mp, 0.0), a2(mp, 0.0), a3(mp, 0.0);
       std::vector<uint64_t> id2(mp, 0ull);
@@ -759,6 +899,22 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
   for (int s = 0; s < 2; ++s) {
     c.n_cur[s] = round_up4(n[s]);
     c.n_live[s] = n[s];
+  }
+  if (h->cap_nt) {  // version 2: the neutral block follows the charged records (off is past them)
+    uint64_t nn, nc[6];
+    std::memcpy(&nn, b + off, 8);
+    std::memcpy(nc, b + off + 8, sizeof(nc));
+    const int rc = upload32(off + kNtHdr, (size_t)nn, h->nt[0]);
+    if (rc != PIC_OK) return rc;
+    h->nt_buf = 0;
+    c.nt_cur = round_up4(nn);
+    c.nt_live = nn;
+    c.nt_recycled[0] = nc[0];
+    c.nt_recycled[1] = nc[1];
+    c.nt_lost[0] = nc[2];
+    c.nt_lost[1] = nc[3];
+    c.nt_ionized = nc[4];
+    c.nt_near = nc[5];
   }
   int k = 0;
   for (int s = 0; s < 2; ++s)
@@ -824,6 +980,7 @@ int pic_workspace_size(const pic_config* cfg, size_t* bytes) {
   tmp.N = cfg->ncells;
   tmp.plain = cfg->precision == PIC_FP64_PLAIN;
   for (int s = 0; s < 2; ++s) tmp.cap[s] = capacity(cfg, s);
+  tmp.cap_nt = neutral_capacity(cfg);
   layout(&tmp, nullptr, bytes);
   return PIC_OK;
 }
@@ -840,6 +997,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
   h->N = cfg->ncells;
   h->plain = cfg->precision == PIC_FP64_PLAIN;
   for (int s = 0; s < 2; ++s) h->cap[s] = capacity(cfg, s);
+  h->cap_nt = neutral_capacity(cfg);
   size_t need = 0;
   layout(h, nullptr, &need);
   if (workspace) {
@@ -866,6 +1024,7 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
   h->grid_scatter = h->plain ? 0 : sms * occupancy_step32(true);
   h->grid_sort = sms * 16;
   h->grid_diag = sms * 8;
+  h->grid_neutral = h->cap_nt ? sms * occupancy_neutral32() : 0;
   *out = h;
 
   int rc = PIC_OK;
@@ -902,6 +1061,11 @@ int pic_step(pic_handle* h, int32_t n) {
       prof_begin(h, scatter ? K_STEP_SCATTER : K_STEP, &e);
       CK(scatter ? launch_step32_scatter(P, h->grid_scatter, h->st) : launch_step32(P, h->grid_step, h->st));
       prof_end(h, &e);
+      if (h->cap_nt) {  // the neutrals alive at the step start, and the ions recycled in this step
+        prof_begin(h, K_NEUTRAL, &e);
+        CK(launch_neutral32(neutral_params(h, P), h->grid_neutral, h->st));
+        prof_end(h, &e);
+      }
       if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
         prof_begin(h, K_SOURCE, &e);
         CK(launch_source32(P, h->st));
@@ -925,8 +1089,10 @@ int pic_step(pic_handle* h, int32_t n) {
     prof_begin(h, K_FIELD, &e);
     PoissonParams F = field_params(h, sort_now, true);
     F.scatter_step = scatter ? 1 : 0;
+    if (h->cap_nt) F.nt_pad = h->nt[1 - h->nt_buf];  // the buffer the neutral step wrote
     CK(launch_field(F, h->st));
     prof_end(h, &e);
+    if (h->cap_nt) h->nt_buf = 1 - h->nt_buf;
     if (sort_now) {
       // the counting sort: cursors from this step's counts now; the particles move during the next
       // step (k_step32 in scatter mode), which saves a read and a write of every particle
@@ -1002,6 +1168,31 @@ int pic_diag(pic_handle* h, pic_diag_t* d) {
   return PIC_OK;
 }
 
+int pic_neutral_diag(pic_handle* h, pic_neutral_diag_t* d) {
+  if (!h || !d || !h->cap_nt) return PIC_EINVAL;
+  CK(cudaMemsetAsync(&h->ctl->nt_ke_fx, 0, sizeof(h->ctl->nt_ke_fx), h->st));
+  EvPair e;
+  prof_begin(h, K_DIAG, &e);
+  CK(launch_ndiag32(h->nt[h->nt_buf], h->ctl, (float)h->cfg.mass[1], h->grid_diag, h->st));
+  prof_end(h, &e);
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const int rc = status_of(c.error);
+  if (rc != PIC_OK) return rc;
+  std::memset(d, 0, sizeof(*d));
+  d->n = c.nt_live;
+  for (int k = 0; k < 2; ++k) {
+    d->recycled[k] = c.nt_recycled[k];
+    d->lost[k] = c.nt_lost[k];
+  }
+  d->ionized = c.nt_ionized;
+  d->near_threshold = c.nt_near;
+  d->particle_steps = c.nt_particle_steps;
+  d->ke = (double)c.nt_ke_fx * (1.0 / 16777216.0) * (h->cfg.L / h->N / h->cfg.ppc[1]);
+  return PIC_OK;
+}
+
 int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E, size_t nnodes) {
   if (!h || nnodes != (size_t)h->N + 1) return PIC_EINVAL;
   int rc = check_errors(h);
@@ -1027,18 +1218,23 @@ int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
   if (!h) return PIC_EINVAL;
   int rc = check_errors(h);
   if (rc != PIC_OK && rc != PIC_EOVERFLOW) return rc;
-  HostParticles P[2];
+  HostParticles P[2], NT;
   Ctl c;
   rc = fetch_particles(h, P, &c);
   if (rc != PIC_OK) return rc;
-  const size_t need = kHdr + 4 + 44 * (P[0].id.size() + P[1].id.size());
+  if (h->cap_nt) {
+    rc = fetch_neutrals(h, h->nt[h->nt_buf], (size_t)c.nt_cur, NT);
+    if (rc != PIC_OK) return rc;
+  }
+  const size_t need = kHdr + 4 + 44 * (P[0].id.size() + P[1].id.size()) +
+                      (h->cap_nt ? kNtHdr + 44 * NT.id.size() : 0);
   if (needed) *needed = need;
   if (!buf) return PIC_OK;
   if (cap < need) return PIC_EINVAL;
   std::vector<unsigned char> b;
   b.reserve(need);
   b.insert(b.end(), "PICMCSN1", "PICMCSN1" + 8);
-  put(b, (uint32_t)1);
+  put(b, (uint32_t)(h->cap_nt ? 2 : 1));
   put(b, (uint32_t)0);
   put(b, config_hash(h->cfg));
   put(b, (uint64_t)h->step);
@@ -1062,6 +1258,19 @@ int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
     put_arr(b, P[s].vy);
     put_arr(b, P[s].vz);
     put_arr(b, P[s].id);
+  }
+  if (h->cap_nt) {
+    put(b, (uint64_t)NT.id.size());
+    for (int k = 0; k < 2; ++k) put(b, (uint64_t)c.nt_recycled[k]);
+    for (int k = 0; k < 2; ++k) put(b, (uint64_t)c.nt_lost[k]);
+    put(b, (uint64_t)c.nt_ionized);
+    put(b, (uint64_t)c.nt_near);
+    put_arr(b, NT.cell);
+    put_arr(b, NT.frac);
+    put_arr(b, NT.vx);
+    put_arr(b, NT.vy);
+    put_arr(b, NT.vz);
+    put_arr(b, NT.id);
   }
   put(b, crc32_ieee(b.data(), b.size()));
   std::memcpy(buf, b.data(), b.size());

@@ -55,6 +55,7 @@ namespace {
 bool adj_valid(const pic_config* c, int32_t steps, int32_t K) {
   if (!valid(c)) return false;
   if (c->coll_mask != 0u || c->source_mode != PIC_SOURCE_NONE || !(c->T[0] > 0)) return false;
+  if (c->neutrals || c->smooth_passes) return false;  // the adjoint differentiates the plain step
   if (steps < 1 || K < 1 || K > steps) return false;
   const double np = (double)c->ncells * ((double)c->ppc[0] + (double)c->ppc[1]);
   return np < 2147483648.0;

@@ -89,6 +89,7 @@ bool batch_valid(const pic_config* c, int n) {
     const pic_config& a = c[k];
     if (!valid(&a)) return false;
     if (a.precision != PIC_FP32 || a.source_mode != PIC_SOURCE_NONE || !exact_possible(a)) return false;
+    if (a.neutrals || a.smooth_passes) return false;  // sheath physics: single runs only
     const pic_config& z = c[0];
     if (a.dt != z.dt || a.L / a.ncells != z.L / z.ncells || a.B != z.B || a.B_angle_deg != z.B_angle_deg ||
         a.frozen_mask != z.frozen_mask || a.field_mode != z.field_mode || a.E_ext != z.E_ext ||

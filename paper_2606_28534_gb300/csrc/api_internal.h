@@ -12,7 +12,7 @@ int occupancy_step64();
 
 namespace picx {
 
-enum Kind { K_STEP = 0, K_SOURCE, K_FIELD, K_SORT, K_LOAD, K_DIAG, K_PLAN, K_STEP_SCATTER, K_KINDS };
+enum Kind { K_STEP = 0, K_SOURCE, K_FIELD, K_SORT, K_LOAD, K_DIAG, K_PLAN, K_STEP_SCATTER, K_NEUTRAL, K_KINDS };
 extern const char* const kKindNames[PIC_KERNEL_KINDS];
 
 struct EvPair {
@@ -50,6 +50,13 @@ struct pic_handle {
   int ke_every = 0;       // the step sums the kinetic energy on every ke_every-th step (0: never)
   bool pending_scatter = false;  // a sort scan ran: the next step moves the particles to buffer 1 - cur
   bool ke_valid = false;  // the last completed step (or refresh) summed it (ke_last holds it)
+  // tracked neutrals (cfg.neutrals): two compacted buffers, the one the next step reads is nt_buf
+  unsigned long long cap_nt = 0;
+  Species32 nt[2];
+  int nt_buf = 0;
+  float2* NE2 = nullptr;       // node electron density pairs per cell
+  unsigned int* wlog = nullptr;  // ions absorbed at a wall in the current step (recycling)
+  int grid_neutral = 0;
   bool prof = false;
   std::vector<picx::EvPair> ev;
   double ms[PIC_KERNEL_KINDS] = {0};
@@ -60,6 +67,7 @@ namespace picx {
 
 bool valid(const pic_config* c);
 unsigned long long capacity(const pic_config* c, int s);
+unsigned long long neutral_capacity(const pic_config* c);
 void derive(pic_handle* h);
 void prof_begin(pic_handle* h, int kind, EvPair* e);
 void prof_end(pic_handle* h, EvPair* e);

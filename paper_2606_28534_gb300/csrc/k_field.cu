@@ -27,9 +27,19 @@
 //
 // k_field_fp64 (plain FP64 path, the pic_poisson operation, diagnostics, non-integer charges):
 // the Green's-function formula above in FP64 with two prefix scans.
+//
+// Density smoothing (Sec. 2, BIT1's smoothing operators): P.smooth passes of the binomial filter
+// rho' = (rho_{j-1} + 2 rho_j + rho_{j+1}) / 4 inside, (rho_0 + rho_1) / 2 and
+// (rho_{N-1} + rho_N) / 2 at the walls, applied to the charge before the solve.  In the exact
+// kernel it runs on t_j = r_j dx / vol_j (the wall charges doubled) in integers, each pass the
+// stencil times 4 (inside t_{j-1} + 2 t_j + t_{j+1}, at a wall 2 (t_0 + t_1)); r is then rebuilt in
+// units of 2^-(2 passes + 1) of the deposit unit and the E coefficients carry that factor.  Each
+// pass reads the neighbours of a thread's run of nodes (across CTAs through distributed shared
+// memory), waits for the cluster, and rewrites the run in place.
 #include <cooperative_groups.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "pic_internal.cuh"
 
@@ -105,6 +115,49 @@ __device__ void bookkeeping(const PoissonParams& P) {
     g->ke_acc[s] = 0ull;
   }
   g->src_K = 0ull;
+  g->wlog_n = 0ull;
+  if (P.nt_cap && P.nt_pad.cell) {  // after a neutral step: the buffer it wrote becomes the next extent
+    unsigned long long n = g->nt_out;
+    if (n > P.nt_cap) n = P.nt_cap;
+    const unsigned long long pad = round_up4(n);
+    for (unsigned long long i = n; i < pad; ++i) P.nt_pad.cell[i] = PIC_DEAD_CELL;
+    g->nt_cur = pad;
+    g->nt_out = 0ull;
+  }
+}
+
+// P.smooth passes of the density filter over this CTA's segment buf[0 .. len) of the nodes
+// [a, a + len), in the thread-run layout (thread tid owns buf[i0 .. i0 + items)).  Long long: the
+// integer stencil of the exact kernel on t (x 4 per pass); double: the filter on densities.
+template <class T>
+__device__ void smooth_segment(T* buf, int len, int a, int N, int seg, int i0, int items, int passes,
+                               cg::cluster_group& cluster, int rank) {
+  for (int pass = 0; pass < passes; ++pass) {
+    cluster.sync();  // every CTA's segment holds the previous pass
+    T left = T(0), right = T(0);
+    if (i0 < len) {
+      const int last = min(i0 + items, len) - 1;
+      if (a + i0 > 0) left = i0 > 0 ? buf[i0 - 1] : cluster.map_shared_rank(buf, rank - 1)[seg - 1];
+      if (a + last < N) right = last + 1 < len ? buf[last + 1] : cluster.map_shared_rank(buf, rank + 1)[0];
+    }
+    cluster.sync();  // every neighbour is read before any run is rewritten
+    T prev = left;
+    for (int k = 0; k < items; ++k) {
+      const int i = i0 + k;
+      if (i >= len) break;
+      const int j = a + i;
+      const T cur = buf[i];
+      const T next = (k + 1 < items && i + 1 < len) ? buf[i + 1] : right;
+      T v;
+      if constexpr (std::is_integral<T>::value) {
+        v = j == 0 ? T(2) * (cur + next) : (j == N ? T(2) * (prev + cur) : prev + T(2) * cur + next);
+      } else {
+        v = j == 0 ? (cur + next) * T(0.5) : (j == N ? (prev + cur) * T(0.5) : (prev + T(2) * cur + next) * T(0.25));
+      }
+      buf[i] = v;
+      prev = cur;
+    }
+  }
 }
 
 // =============================================================================================
@@ -128,22 +181,41 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   if (P.ctl && rank == 0 && tid == 0) bookkeeping(P);
 
   // ---- pass 1 (coalesced): node deposits, net integer charge ------------------------------------
+  // |r| bound that keeps the smoothed values (at most 4^(passes + 1) |r|) inside int64
+  const __int128 lim = (__int128)0x7FFFFFFFFFFFFFFFll >> (P.smooth ? 2 * P.smooth + 2 : 0);
   for (int i = tid; i < len; i += PIC_FIELD_TPB) {
     const int j = a + i;
     const long long R0 = node_R(P, 0, j), R1 = node_R(P, 1, j);
     P.R[0][j] = R0;
     P.R[1][j] = R1;
     const __int128 rn = (__int128)P.m[0] * R0 + (__int128)P.m[1] * R1;
-    if (rn > (__int128)0x7FFFFFFFFFFFFFFFll || rn < -(__int128)0x7FFFFFFFFFFFFFFFll) {
+    if (rn > lim || rn < -lim) {
       atomicOr(&P.ctl->error, ERR_DEVICE);  // net deposit beyond int64: report, never wrap silently
     }
     Rn[i] = (long long)rn;
+    if (P.NE2) {  // node electron density (neutral ionization)
+      const float ne = (float)((double)R0 * P.ne_scale * ((j == 0 || j == N) ? 2.0 : 1.0));
+      if (j < N) P.NE2[j].x = ne;
+      if (j > 0) P.NE2[j - 1].y = ne;
+    }
   }
   __syncthreads();
 
-  // ---- per-thread runs: Q (cumulative interior charge) and sum of k r_k -------------------------
   const int items = (len + PIC_FIELD_TPB - 1) / PIC_FIELD_TPB;
   const int i0 = tid * items;
+  if (P.smooth > 0) {
+    for (int k = 0; k < items; ++k) {  // t: wall charges doubled
+      const int i = i0 + k;
+      if (i < len && (a + i == 0 || a + i == N)) Rn[i] *= 2;
+    }
+    smooth_segment<long long>(Rn, len, a, N, seg, i0, items, P.smooth, cluster, rank);
+    for (int k = 0; k < items; ++k) {  // back to charges, in units of 2^-(2 passes + 1)
+      const int i = i0 + k;
+      if (i < len && a + i != 0 && a + i != N) Rn[i] *= 2;
+    }
+  }
+
+  // ---- per-thread runs: Q (cumulative interior charge) and sum of k r_k -------------------------
   __int128 oq = 0, op = 0;
   for (int k = 0; k < items; ++k) {
     const int i = i0 + k;
@@ -283,17 +355,30 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   if ((MODE == 0 || MODE == 1) && P.ctl && rank == 0 && tid == 0) bookkeeping(P);
 
   // ---- pass 1 (coalesced): node density -> shared f_j ---------------------------------------
-  for (int i = tid; i < len; i += PIC_FIELD_TPB) {
-    const int j = a + i;
-    const double r = node_rho<MODE>(P, j);
-    if (MODE != 2) P.rho[j] = r;
-    F[i] = (j >= 1 && j <= N - 1) ? dx2 * r : 0.0;
+  const int items = (len + PIC_FIELD_TPB - 1) / PIC_FIELD_TPB;
+  const int i0 = tid * items;
+  if (MODE == 3 && P.smooth > 0) {  // diagnostics of a smoothed run: the density the solve used
+    for (int i = tid; i < len; i += PIC_FIELD_TPB) F[i] = node_rho<MODE>(P, a + i);
+    __syncthreads();
+    smooth_segment<double>(F, len, a, N, seg, i0, items, P.smooth, cluster, rank);
+    for (int k = 0; k < items; ++k) {
+      const int i = i0 + k;
+      if (i >= len) break;
+      const int j = a + i;
+      P.rho[j] = F[i];
+      F[i] = (j >= 1 && j <= N - 1) ? dx2 * F[i] : 0.0;
+    }
+  } else {
+    for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+      const int j = a + i;
+      const double r = node_rho<MODE>(P, j);
+      if (MODE != 2) P.rho[j] = r;
+      F[i] = (j >= 1 && j <= N - 1) ? dx2 * r : 0.0;
+    }
   }
   __syncthreads();
 
   // ---- per-thread runs of consecutive nodes: sums of k f_k and (N - k) f_k ----------------------
-  const int items = (len + PIC_FIELD_TPB - 1) / PIC_FIELD_TPB;
-  const int i0 = tid * items;
   Pair own = {0.0, 0.0};
   for (int k = 0; k < items; ++k) {
     const int i = i0 + k;

@@ -190,6 +190,13 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
             const int side = cn < 0 ? 0 : 1;
             atomicAdd(&bc.hits[s][side], 1u);
             atomicAdd(&bc.lost[s], 1u);
+            if (s == 1 && P.wlog) {  // recycling: log the ion's index in the buffer read, and its wall
+              const unsigned long long e = atomicAdd(&P.ctl->wlog_n, 1ull);
+              if (e < P.cap[1])
+                P.wlog[e] = (i0 + (unsigned)k) | ((unsigned)side << 31);
+              else
+                atomicOr(&P.ctl->error, ERR_DEVICE);
+            }
             const float e = 0.5f * K.mass * (vx[k] * vx[k] + vy[k] * vy[k] + vz[k] * vz[k]);
             atomicAdd(&bc.efx[s], (unsigned long long)__double2ull_rn((double)e * 16777216.0));
             c[k] = PIC_DEAD_CELL;

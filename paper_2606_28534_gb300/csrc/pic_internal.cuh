@@ -35,6 +35,9 @@
 #define CH_SCAT 3u
 #define CH_CHILD 4u
 #define CH_SOURCE 5u
+#define CH_RECYCLE 6u
+#define CH_NIZ 7u
+#define PIC_MAX_SMOOTH 4
 
 // error bits of Ctl::error
 #define ERR_OVERFLOW 1u
@@ -68,6 +71,13 @@ struct Ctl {
   unsigned long long ke_last[2];         // ke_acc of the last completed step (read by pic_diag)
   long long netq;                        // diag scratch: sum_j sum_s sign(q_s) R_sj
   double fe_part[PIC_DIAG_BLOCKS];       // diag scratch: field energy per block of nodes
+  // tracked neutrals (species 2)
+  unsigned long long nt_cur;             // extent of the neutral buffer read by the next step
+  unsigned long long nt_out;             // neutrals written by the current step (next extent)
+  unsigned long long nt_live;
+  unsigned long long nt_recycled[2], nt_lost[2], nt_ionized, nt_near, nt_particle_steps;
+  unsigned long long nt_ke_fx;           // diag scratch: sum 0.5 m v^2 of the neutrals, 2^-24 units
+  unsigned long long wlog_n;             // ions absorbed at a wall in the current step (recycling log)
 };
 
 struct Species32 {
@@ -130,6 +140,24 @@ struct StepParams32 {
   unsigned int scatter;  // the step after a sort: read src, write each particle to its sorted slot in sp
   Species32 src[2];      // scatter: the buffer the sort step left (sp: the buffer being filled)
   unsigned int* cursor[2];  // scatter: per-cell write cursors of the sort scan
+  unsigned int* wlog;    // recycling: index of each ion absorbed at a wall in the buffer the step
+                         // reads, | side << 31 (null: no recycling)
+};
+
+// The neutral step (k_neutral.cu): the neutrals alive at the step start move, leave at the walls
+// or ionize; the ions the particle step logged at the walls return as neutrals.  Survivors and new
+// neutrals are written, compacted, into the other neutral buffer.
+struct NeutralParams {
+  StepParams32 P;                   // the particle step's parameters (births, deposits, counters)
+  Species32 src, dst;               // neutral buffers read / written
+  unsigned long long cap;           // neutral capacity
+  const unsigned long long* ion_id; // ion ids of the buffer the particle step read (log indices)
+  const float2* NE2;                // node electron density pairs (n_e,c, n_e,c+1) per cell
+  float Kdt;                        // K_iz dt
+  float vt_rec, vt_sec;             // sqrt(T_rec / m_ion), sqrt(T_sec / m_e)
+  float mass;                       // neutral (= ion) mass
+  unsigned recycle_u24;             // ceil(recycle 2^24): (w >> 8) < recycle_u24  <=>  u01(w) < recycle
+  int ionize;                       // K_iz > 0
 };
 
 struct StepParams64 {
@@ -255,6 +283,11 @@ struct PoissonParams {
   unsigned long long cap[2];
   int plain;
   int scatter_step;  // bookkeeping after a scattering step: the extent of the filled buffer is sort_new
+  int smooth;        // density smoothing passes (exact path and mode 3)
+  float2* NE2;       // out, may be null: node electron density pairs per cell (neutral ionization)
+  double ne_scale;   // n_e,j = R_0j ne_scale (x 2 at the wall nodes)
+  Species32 nt_pad;  // neutrals: the buffer the neutral step wrote (padded to a multiple of 4)
+  unsigned long long nt_cap;  // 0: no neutrals
 };
 
 struct SortParams {
@@ -397,6 +430,12 @@ cudaError_t launch_restore32(const int* cell, const double* frac, const double* 
                              unsigned long long base, int N, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                           cudaStream_t st);
+// tracked neutrals
+cudaError_t launch_neutral32(const NeutralParams& p, int grid, cudaStream_t st);
+int occupancy_neutral32();
+cudaError_t launch_nload32(const Species32& dst, unsigned long long n, int ppc, int N, unsigned long long seed,
+                           double vt, cudaStream_t st);
+cudaError_t launch_ndiag32(const Species32& a, Ctl* ctl, float mass, int grid, cudaStream_t st);
 
 // ensembles
 int bstep32_variants();

@@ -18,8 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpicgb.so")
 _lib = None
 
-PIC_ABI_VERSION = 1
-PIC_KERNEL_KINDS = 8
+PIC_ABI_VERSION = 2
+PIC_KERNEL_KINDS = 9
 STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_EOVERFLOW",
           5: "PIC_ECORRUPT", 6: "PIC_ETIMEOUT", 7: "PIC_EDEVICE"}
 
@@ -43,7 +43,16 @@ class PicConfig(C.Structure):
         ("E_ex", C.c_double), ("sigma_iz", C.c_double), ("E_iz", C.c_double),
         ("sigma_cx", C.c_double), ("E_cap", C.c_double), ("E_ext", C.c_double),
         ("profile_scale", C.c_double), ("source_x1", C.c_double), ("capacity_factor", C.c_double),
-        ("seed", C.c_uint64),
+        ("seed", C.c_uint64), ("smooth_passes", C.c_int32), ("neutrals", C.c_uint32),
+        ("neutral_ppc", C.c_int32), ("reserved", C.c_uint32), ("recycle", C.c_double), ("T_rec", C.c_double),
+        ("K_iz", C.c_double), ("T_sec", C.c_double), ("neutral_capacity", C.c_double),
+    ]
+
+
+class PicNeutralDiag(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint64), ("recycled", C.c_uint64 * 2), ("lost", C.c_uint64 * 2), ("ionized", C.c_uint64),
+        ("near_threshold", C.c_uint64), ("particle_steps", C.c_uint64), ("ke", C.c_double),
     ]
 
 
@@ -63,6 +72,7 @@ class PicDiag(C.Structure):
 SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapshot", "pic_restore",
            "pic_diag", "pic_get_field", "pic_profile", "pic_kernel_times", "pic_free",
            "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc", "pic_set_diag_interval", "pic_diag_bytes",
+           "pic_neutral_diag",
            "pic_batch_variant_count", "pic_batch_variant_name", "pic_batch_workspace_size",
            "pic_batch_init", "pic_batch_set_tuning", "pic_batch_set_diag_interval", "pic_batch_get_tuning", "pic_batch_step",
            "pic_batch_sync", "pic_batch_diag", "pic_batch_snapshot", "pic_batch_restore",
@@ -96,6 +106,7 @@ def lib():
         L.pic_snapshot.argtypes = [V, V, C.c_size_t, P(C.c_size_t)]
         L.pic_restore.argtypes = [V, V, C.c_size_t]
         L.pic_diag.argtypes = [V, P(PicDiag)]
+        L.pic_neutral_diag.argtypes = [V, P(PicNeutralDiag)]
         L.pic_get_field.argtypes = [V, P(C.c_int64), P(C.c_double), P(C.c_double), P(C.c_float),
                                     C.c_size_t]
         L.pic_profile.argtypes = [V, C.c_int]
@@ -235,6 +246,13 @@ class Simulation:
         d = PicDiag()
         _check(lib().pic_diag(self._h, C.byref(d)), "pic_diag")
         return _diag_dict(d)
+
+    def neutral_diag(self) -> dict:
+        """Tracked neutrals (configurations with ``neutrals=1``)."""
+        d = PicNeutralDiag()
+        _check(lib().pic_neutral_diag(self._h, C.byref(d)), "pic_neutral_diag")
+        return {"n": d.n, "recycled": list(d.recycled), "lost": list(d.lost), "ionized": d.ionized,
+                "near_threshold": d.near_threshold, "particle_steps": d.particle_steps, "ke": d.ke}
 
     def fields(self) -> dict:
         n1 = self.N + 1

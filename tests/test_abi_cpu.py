@@ -51,9 +51,28 @@ def test_workspace_size_validates_and_scales(L):
             pic.workspace_size(W.variant(W.SMALL_C2, **bad))
         assert e.value.status == 1
     c = pic.make_config(W.SMALL_C2)
-    c.abi_version = 2
+    c.abi_version = 1  # an older layout of pic_config
     n = C.c_size_t(0)
     assert L.pic_workspace_size(C.byref(c), C.byref(n)) == 1
+
+
+def test_sheath_physics_validates_and_adds_its_buffers(L):
+    base = pic.workspace_size(W.variant(W.SMALL_C6, neutrals=0, neutral_ppc=0, smooth_passes=0))
+    assert pic.workspace_size(W.variant(W.SMALL_C6, neutrals=0, neutral_ppc=0)) == base  # smoothing: no memory
+    with_nt = pic.workspace_size(W.SMALL_C6)
+    more_nt = pic.workspace_size(W.variant(W.SMALL_C6, neutral_ppc=400))
+    assert base < with_nt < more_nt
+    for bad in (dict(precision=W.PRECISION_FP64_PLAIN),          # FP32 path only
+                dict(charge=(-1.0, 1.5)),                         # integer charges (exact solve)
+                dict(smooth_passes=5), dict(smooth_passes=-1),
+                dict(recycle=1.5), dict(recycle=-0.1), dict(K_iz=-1.0), dict(T_rec=-1.0), dict(T_sec=-1.0),
+                dict(neutral_capacity=0.5), dict(neutral_ppc=-3), dict(neutrals=2),
+                dict(neutrals=0),                                 # initial neutrals need the species
+                dict(reserved=1)):
+        with pytest.raises(pic.PicError) as e:
+            pic.workspace_size(W.variant(W.SMALL_C6, **bad))
+        assert e.value.status == 1, bad
+    assert pic.workspace_size(W.variant(W.SMALL_C6, smooth_passes=4, recycle=0.0, K_iz=0.0)) > 0
 
 
 def test_init_rejects_bad_arguments_before_any_device_work(L):
@@ -99,6 +118,8 @@ def test_batch_workspace_is_the_sum_of_its_parts(L):
     dict(frozen_mask=2),
     dict(precision=W.PRECISION_FP64_PLAIN),  # the batch is the FP32 path
     dict(source_mode=W.SOURCE_PAIRS, source_x1=4.0),
+    dict(smooth_passes=1),  # the sheath physics runs in single simulations only
+    dict(neutrals=1, recycle=1.0, T_rec=0.1, neutral_capacity=1.5),
 ])
 def test_batch_rejects_configurations_that_cannot_share_a_launch(L, bad):
     runs = W.small_ensemble()
@@ -137,3 +158,11 @@ def test_batch_init_rejects_bad_arguments_before_any_device_work(L):
     assert L.pic_batch_reset(None) == 1
     assert L.pic_batch_set_tuning(None, None) == 1
     L.pic_batch_free(None)
+
+
+def test_adjoint_rejects_the_sheath_physics(L):
+    assert pic.adj_workspace_size(W.C5, 20, 5) > 0
+    for bad in (dict(smooth_passes=2), dict(neutrals=1, recycle=1.0, neutral_capacity=1.5)):
+        with pytest.raises(pic.PicError) as e:
+            pic.adj_workspace_size(W.variant(W.C5, **bad), 20, 5)
+        assert e.value.status == 1
