@@ -35,6 +35,9 @@ BYTES_SCATTER_EXTRA = 8  # the step after a sort writes each particle to a new s
 # dram__bytes_write.sum) of these kernels on the 12.6M-particle profiling case (c3p), scaled by
 # particles to a full launch: the ordinary step and the step after a sort
 TRAFFIC_STEP, TRAFFIC_SCATTER = 49.07, 57.06
+# the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
+# (8 B); on sort steps it writes each survivor, compacted, into the other buffer instead (28 B)
+BYTES_NEUTRAL_KERNEL, BYTES_NEUTRAL_COMPACT = 36, 56
 
 
 def _peaks():
@@ -165,6 +168,8 @@ W_DESC = {
           "B 0.5 @ 30 deg, 4 processes, sort every 10 steps",
     "c5": "collisionless, 1024 cells, 409,600 particles",
     "c3p": "non-uniform load profiling case, 65536 cells, 12,582,912 particles",
+    "c6": "D+/e/D sheath, 65536 cells, 100,007,936 charged + 50,003,968 neutral particles",
+    "c6p": "D+/e/D sheath profiling case, 65536 cells, 12,582,912 charged + 6,291,456 neutral particles",
 }
 
 
@@ -262,6 +267,85 @@ def batched(args, torch, pic, peak: float) -> dict:
         "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in kt.items()
                     if v["launches"]},
     }
+
+
+def sheath_section(args, torch, pic, peak: float) -> dict:
+    """The D+/e/D sheath on config 3's grid (deuterium ions recycled into tracked neutrals at the
+    walls, a neutral background of 50 M, their electron-impact ionization, two smoothing passes):
+    whole-step throughput over charged and neutral particles, the neutral kernel's roofline, and the
+    same plasma without the sheath physics for the cost of adding it."""
+    p = W.C6
+    K = args.sheath_steps
+    g = pic.Simulation(p)
+    g.step(args.warmup)
+    g.sync()
+    d0, n0 = g.diag(), g.neutral_diag()
+    ms = events_ms(torch, g.stream, lambda: g.step(K))
+    d1, n1 = g.diag(), g.neutral_diag()
+    charged = d1["particle_steps"] - d0["particle_steps"]
+    neutral = n1["particle_steps"] - n0["particle_steps"]
+    # kernel split over two sort cycles, launched with events
+    cyc = 2 * p["sort_interval"]
+    g.profile(True)
+    g.step(cyc)
+    kt = g.kernel_times()
+    g.profile(False)
+    n2 = g.neutral_diag()
+    nk = kt["neutral"]["launches"] + kt["neutral_compact"]["launches"]
+    nt_launch = (n2["particle_steps"] - n1["particle_steps"]) / max(1, nk)
+    nt_ms = kt["neutral"]["ms"] / max(1, kt["neutral"]["launches"])
+    nt_bytes = BYTES_NEUTRAL_KERNEL * nt_launch
+    achieved = nt_bytes / (nt_ms / 1000.0) / 1e9
+    nc_ms = kt["neutral_compact"]["ms"] / max(1, kt["neutral_compact"]["launches"])
+    nc_bytes = BYTES_NEUTRAL_COMPACT * nt_launch
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    # the same grid, load and deuterium plasma without neutrals or smoothing
+    q = W.variant(p, neutrals=0, neutral_ppc=0, smooth_passes=0, recycle=0.0, K_iz=0.0)
+    h = pic.Simulation(q)
+    h.step(args.warmup)
+    h.sync()
+    e0 = h.diag()["particle_steps"]
+    ms_q = events_ms(torch, h.stream, lambda: h.step(K))
+    ps_q = h.diag()["particle_steps"] - e0
+    h.close()
+    del h
+    torch.cuda.empty_cache()
+    out = {
+        "workload": "c6: D+/e/D sheath on config 3's grid: 65536 cells, 100,007,936 charged particles "
+                    "(exp(-x/(L/8)) load, pair source), 50,003,968 initial neutrals, every absorbed ion "
+                    "recycled, K_iz n_e dt = 2e-4, two smoothing passes",
+        "value": (charged + neutral) / (ms / 1000.0), "unit": "particle-steps/s (charged + neutral)",
+        "steps": K, "ms_per_step": ms / K, "charged_particle_steps": charged, "neutral_particle_steps": neutral,
+        "neutrals": {"n": n1["n"], "recycled": n1["recycled"], "lost": n1["lost"], "ionized": n1["ionized"]},
+        "without_sheath_physics": {"value": ps_q / (ms_q / 1000.0), "unit": "particle-steps/s",
+                                   "ms_per_step": ms_q / K},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "kernel": "k_neutral32 (in place)", "bytes_per_neutral": BYTES_NEUTRAL_KERNEL,
+                     "bytes_per_launch": nt_bytes, "avg_launch_ms": nt_ms, "traffic": None,
+                     "compacting_step": {"kernel": "k_neutral32 (compacting, sort steps)",
+                                         "bytes_per_neutral": BYTES_NEUTRAL_COMPACT, "avg_launch_ms": nc_ms,
+                                         "achieved": nc_bytes / (nc_ms / 1000.0) / 1e9 if nc_ms else None,
+                                         "frac": nc_bytes / (nc_ms / 1000.0) / 1e9 / peak if nc_ms else None}},
+        "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in kt.items() if v["launches"]},
+    }
+    if not args.no_cpu:
+        from oracle import oracle as O
+
+        cores = len(os.sched_getaffinity(0))
+        sample = W.variant(p, ppc=(max(1, p["ppc"][0] // 64), max(1, p["ppc"][1] // 64)),
+                           neutral_ppc=max(1, p["neutral_ppc"] // 64))
+        o = O.OracleSim(sample, threads=cores)
+        o.step(1)
+        c0, m0 = o.diag()["particle_steps"], o.neutral_diag()["particle_steps"]
+        t0 = time.perf_counter()
+        o.step(3)
+        dt = time.perf_counter() - t0
+        work = o.diag()["particle_steps"] - c0 + o.neutral_diag()["particle_steps"] - m0
+        out["cpu_baseline"] = {"value": work / dt, "unit": "particle-steps/s (charged + neutral)", "cores": cores,
+                               "kind": "oracle", "sample": f"ppc/64 of c6, 3 steps, {dt:.1f} s"}
+    return out
 
 
 def adjoint_section(args, torch, pic) -> dict:
@@ -456,6 +540,9 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
     adj = None
     if not args.no_adjoint:
         adj = adjoint_section(args, torch, pic)
+    sheath = None
+    if not args.no_sheath:
+        sheath = sheath_section(args, torch, pic, peak)
 
     if rank != 0:
         return
@@ -483,6 +570,7 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         "fp64_plain": plain,
         "batched": batch,
         "adjoint": adj,
+        "sheath": sheath,
         "e2e": e2e,
     }
     if world == 1 and not args.no_cpu:
@@ -509,6 +597,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adj-reps", type=int, default=5)
     ap.add_argument("--batch-steps", type=int, default=W.C4_STEPS)
+    ap.add_argument("--no-sheath", action="store_true")
+    ap.add_argument("--sheath-steps", type=int, default=W.C6_STEPS)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -225,7 +225,7 @@ int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E,
 /* Per-kernel device time via CUDA events on the handle's stream.  enable != 0 starts recording
  * (adds two event records per launch); pic_kernel_times synchronises and returns, for up to
  * nkinds kernel kinds, total milliseconds, launch counts and names. */
-#define PIC_KERNEL_KINDS 9
+#define PIC_KERNEL_KINDS 10
 int pic_profile(pic_handle* h, int enable);
 int pic_kernel_times(pic_handle* h, double* ms, uint64_t* launches, const char** names,
                      int32_t nkinds);

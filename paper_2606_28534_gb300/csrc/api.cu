@@ -15,7 +15,7 @@
 namespace picx {
 
 const char* const kKindNames[PIC_KERNEL_KINDS] = {"step", "source", "field", "sort", "load", "diag", "plan",
-                                                   "step_scatter", "neutral"};
+                                                   "step_scatter", "neutral", "neutral_compact"};
 
 
 // ---------------------------------------------------------------------------------------------
@@ -1061,9 +1061,12 @@ int pic_step(pic_handle* h, int32_t n) {
       prof_begin(h, scatter ? K_STEP_SCATTER : K_STEP, &e);
       CK(scatter ? launch_step32_scatter(P, h->grid_scatter, h->st) : launch_step32(P, h->grid_step, h->st));
       prof_end(h, &e);
-      if (h->cap_nt) {  // the neutrals alive at the step start, and the ions recycled in this step
-        prof_begin(h, K_NEUTRAL, &e);
-        CK(launch_neutral32(neutral_params(h, P), h->grid_neutral, h->st));
+      if (h->cap_nt) {  // the neutrals alive at the step start, and the ions recycled in this step:
+        // in place, or compacted into the other buffer on the steps that sort
+        NeutralParams Q = neutral_params(h, P);
+        if (!sort_now) Q.dst = Q.src;
+        prof_begin(h, sort_now ? K_NEUTRAL_COMPACT : K_NEUTRAL, &e);
+        CK(launch_neutral32(Q, sort_now, h->grid_neutral, h->st));
         prof_end(h, &e);
       }
       if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
@@ -1089,10 +1092,13 @@ int pic_step(pic_handle* h, int32_t n) {
     prof_begin(h, K_FIELD, &e);
     PoissonParams F = field_params(h, sort_now, true);
     F.scatter_step = scatter ? 1 : 0;
-    if (h->cap_nt) F.nt_pad = h->nt[1 - h->nt_buf];  // the buffer the neutral step wrote
+    if (h->cap_nt) {  // the buffer the neutral step wrote
+      F.nt_pad = h->nt[sort_now ? 1 - h->nt_buf : h->nt_buf];
+      F.nt_append = sort_now ? 0 : 1;
+    }
     CK(launch_field(F, h->st));
     prof_end(h, &e);
-    if (h->cap_nt) h->nt_buf = 1 - h->nt_buf;
+    if (h->cap_nt && sort_now) h->nt_buf = 1 - h->nt_buf;
     if (sort_now) {
       // the counting sort: cursors from this step's counts now; the particles move during the next
       // step (k_step32 in scatter mode), which saves a read and a write of every particle

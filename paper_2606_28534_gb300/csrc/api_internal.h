@@ -12,7 +12,7 @@ int occupancy_step64();
 
 namespace picx {
 
-enum Kind { K_STEP = 0, K_SOURCE, K_FIELD, K_SORT, K_LOAD, K_DIAG, K_PLAN, K_STEP_SCATTER, K_NEUTRAL, K_KINDS };
+enum Kind { K_STEP = 0, K_SOURCE, K_FIELD, K_SORT, K_LOAD, K_DIAG, K_PLAN, K_STEP_SCATTER, K_NEUTRAL, K_NEUTRAL_COMPACT, K_KINDS };
 extern const char* const kKindNames[PIC_KERNEL_KINDS];
 
 struct EvPair {

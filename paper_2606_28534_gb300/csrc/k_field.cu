@@ -116,8 +116,8 @@ __device__ void bookkeeping(const PoissonParams& P) {
   }
   g->src_K = 0ull;
   g->wlog_n = 0ull;
-  if (P.nt_cap && P.nt_pad.cell) {  // after a neutral step: the buffer it wrote becomes the next extent
-    unsigned long long n = g->nt_out;
+  if (P.nt_cap && P.nt_pad.cell) {  // after a neutral step: the extent of the buffer it wrote
+    unsigned long long n = (P.nt_append ? g->nt_cur : 0ull) + g->nt_out;
     if (n > P.nt_cap) n = P.nt_cap;
     const unsigned long long pad = round_up4(n);
     for (unsigned long long i = n; i < pad; ++i) P.nt_pad.cell[i] = PIC_DEAD_CELL;

@@ -15,15 +15,24 @@
 // velocity and (id, step, NIZ, 2) its id; (ion id, step, RECYCLE, 0) decides the recycling and gives
 // the velocity, (ion id, step, RECYCLE, 1) the neutral's id.
 //
-// Survivors and new neutrals are written, compacted, into the other neutral buffer: a warp claims
-// one contiguous range for all its lanes' outputs with one atomic, so the buffer never collects dead
-// slots and needs no sort.  Storage order is not reproducible between runs; nothing depends on it
-// (every draw is keyed by id, every deposit is an exact integer sum).
+// A warp takes chunks of 128 neutrals, lane l the entries l, l + 32, l + 64, l + 96 (every load
+// instruction reads 32 consecutive values).  A neutral's velocity and id never change, so an ordinary
+// step updates the buffer in place: it writes back the cell and fraction of each survivor and marks a
+// lost or ionized neutral dead (36 bytes per neutral in all); new neutrals are appended past the
+// extent.  On the steps that sort the charged species (COMPACT) the survivors and new neutrals are
+// instead written, compacted, into the other buffer (56 bytes per neutral), which drops the dead
+// slots: a warp claims one contiguous range for all its lanes' outputs with one atomic, and the
+// survivors of each of the four rounds fill a contiguous run of it.  Storage order is not
+// reproducible between runs; nothing depends on it (every draw is keyed by id, every deposit is an
+// exact integer sum).
 #include "step32_common.cuh"
 
 namespace {
 
 constexpr int NT_TPB = 256;
+#ifndef PIC_NEUTRAL_MINB
+#define PIC_NEUTRAL_MINB 3  // resident CTAs per SM the neutral step is compiled for (80 registers, no spills)
+#endif
 
 struct NCounters {
   unsigned int lost[2];
@@ -72,7 +81,68 @@ __device__ __forceinline__ void born_charged(const NeutralParams& Q, unsigned lo
   atomicAdd(&bc->ke[s], ke_fx32(v[0], v[1], v[2], P.ph.sp[s].mass));
 }
 
-__global__ void __launch_bounds__(NT_TPB) k_neutral32(const __grid_constant__ NeutralParams Q) {
+// An ionizing neutral (about one in several thousand per step): the ion it becomes and the electron
+// born beside it.  Kept out of line so that the streaming loop stays small.
+__device__ __noinline__ void ionize_one(const NeutralParams& Q, unsigned long long base0, unsigned long long base1,
+                                        int c, float f, float vx, float vy, float vz, unsigned long long id,
+                                        NCounters* bc) {
+  const Phys& ph = Q.P.ph;
+  const uint4 b = draw4(id, ph.seed, Q.P.step, CH_NIZ, 1u);
+  const uint4 kk = draw4(id, ph.seed, Q.P.step, CH_NIZ, 2u);
+  float n0, n1, n2, n3;
+  box_muller_f(b.x, b.y, n0, n1);
+  box_muller_f(b.z, b.w, n2, n3);
+  const float ve[3] = {Q.vt_sec * n0, Q.vt_sec * n1, Q.vt_sec * n2};
+  const float vi[3] = {vx, vy, vz};
+  born_charged<1>(Q, base1, c, f, vi, id, bc);
+  born_charged<0>(Q, base0, c, f, ve, (unsigned long long)kk.x | ((unsigned long long)kk.y << 32), bc);
+  atomicAdd(&bc->ionized, 1u);
+}
+
+// Writes the lanes' kept entries (bit r of keep: entry r) compacted, one claim per warp: entry r of
+// every lane lands in one contiguous run, so each store instruction covers consecutive addresses.
+template <int R>
+__device__ __forceinline__ void write_kept(const NeutralParams& Q, Ctl* g, unsigned long long off, unsigned keep,
+                                           const int* c, const float* f, const float* vx, const float* vy,
+                                           const float* vz, const unsigned long long* id) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  unsigned bal[R];
+  unsigned tot = 0u;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    bal[r] = __ballot_sync(0xFFFFFFFFu, (keep >> r) & 1u);
+    tot += __popc(bal[r]);
+  }
+  if (!tot) return;
+  unsigned long long base = 0ull;
+  if (lane == 0) base = atomicAdd(&g->nt_out, (unsigned long long)tot);
+  base = __shfl_sync(0xFFFFFFFFu, base, 0) + off;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if ((keep >> r) & 1u) {
+      const unsigned long long j = base + __popc(bal[r] & below);
+      if (j < Q.cap) {
+        Q.dst.cell[j] = c[r];
+        Q.dst.frac[j] = f[r];
+        Q.dst.vx[j] = vx[r];
+        Q.dst.vy[j] = vy[r];
+        Q.dst.vz[j] = vz[r];
+        Q.dst.id[j] = id[r];
+      } else {
+        atomicAdd(&g->dropped, 1ull);
+        atomicOr(&g->error, ERR_OVERFLOW);
+      }
+    }
+    base += __popc(bal[r]);
+  }
+}
+
+constexpr int NT_R = 4;                 // neutrals per lane per chunk
+constexpr int NT_CHUNK = 32 * NT_R;     // a warp's chunk: lane l holds entries l, l + 32, l + 64, l + 96
+
+template <bool COMPACT>
+__global__ void __launch_bounds__(NT_TPB, PIC_NEUTRAL_MINB) k_neutral32(const __grid_constant__ NeutralParams Q) {
   __shared__ NCounters bc;
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid < (int)(sizeof(NCounters) / 4)) reinterpret_cast<unsigned int*>(&bc)[tid] = 0u;
@@ -82,86 +152,94 @@ __global__ void __launch_bounds__(NT_TPB) k_neutral32(const __grid_constant__ Ne
   const Phys& ph = P.ph;
   const int N = ph.N;
   Ctl* const g = P.ctl;
-  const unsigned long long ngroups = g->nt_cur / 4;  // the extent is a multiple of 4
+  const unsigned long long ncur = g->nt_cur;
   const unsigned long long nlog = Q.P.wlog ? min(g->wlog_n, P.cap[1]) : 0ull;  // the log holds cap[1] entries
-  const unsigned long long items = ngroups + nlog;
   // births of the charged species go past the extent of the buffer the particle step filled
   const unsigned long long base0 = P.scatter ? g->sort_new[0] : g->n_cur[0];
   const unsigned long long base1 = P.scatter ? g->sort_new[1] : g->n_cur[1];
+  const unsigned long long gw = (unsigned long long)blockIdx.x * (NT_TPB / 32) + (tid >> 5);
   const unsigned long long nwarps = (unsigned long long)gridDim.x * (NT_TPB / 32);
   unsigned long long started = 0ull;
+  const unsigned long long append_at = COMPACT ? 0ull : ncur;  // new neutrals go past the extent in place
 
-  // a warp takes 32 consecutive items: groups of 4 neutrals (128-bit loads), then log entries
+  // ---- the neutrals alive at the step start: coalesced 4- and 8-byte loads, lane-interleaved --------
+  const unsigned long long nchunks = (ncur + NT_CHUNK - 1) / NT_CHUNK;
 #pragma unroll 1
-  for (unsigned long long w0 = ((unsigned long long)blockIdx.x * (NT_TPB / 32) + (tid >> 5)) * 32ull; w0 < items;
-       w0 += nwarps * 32ull) {
-    const unsigned long long it = w0 + lane;
-    int c[4];
-    float f[4], vx[4], vy[4], vz[4];
-    unsigned long long id[4];
-    unsigned keep = 0u;  // bit k: entry k of the arrays above is an output of this lane
-    if (it < ngroups) {
-      const unsigned long long i0 = it * 4ull;
-      const int4 c4 = *reinterpret_cast<const int4*>(Q.src.cell + i0);
-      const float4 f4 = *reinterpret_cast<const float4*>(Q.src.frac + i0);
-      const float4 x4 = *reinterpret_cast<const float4*>(Q.src.vx + i0);
-      const float4 y4 = *reinterpret_cast<const float4*>(Q.src.vy + i0);
-      const float4 z4 = *reinterpret_cast<const float4*>(Q.src.vz + i0);
-      const ulonglong2 ia = *reinterpret_cast<const ulonglong2*>(Q.src.id + i0);
-      const ulonglong2 ib = *reinterpret_cast<const ulonglong2*>(Q.src.id + i0 + 2);
-      const int ci[4] = {c4.x, c4.y, c4.z, c4.w};
-      const float fi[4] = {f4.x, f4.y, f4.z, f4.w}, xi[4] = {x4.x, x4.y, x4.z, x4.w},
-                  yi[4] = {y4.x, y4.y, y4.z, y4.w}, zi[4] = {z4.x, z4.y, z4.z, z4.w};
-      const unsigned long long ii[4] = {ia.x, ia.y, ib.x, ib.y};
+  for (unsigned long long ch = gw; ch < nchunks; ch += nwarps) {
+    const unsigned long long i0 = ch * NT_CHUNK + lane;
+    int c[NT_R];
+    float f[NT_R], vx[NT_R], vy[NT_R], vz[NT_R];
+    unsigned long long id[NT_R];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (ci[k] == PIC_DEAD_CELL) continue;
-        ++started;
-        float fk = fi[k];
-        const int cn = move_one(ph.dtdx, ci[k], fk, xi[k]);
-        if ((unsigned)cn >= (unsigned)N) {  // lost at a wall
-          atomicAdd(&bc.lost[cn < 0 ? 0 : 1], 1u);
+    for (int r = 0; r < NT_R; ++r) {
+      const unsigned long long i = i0 + 32ull * r;
+      c[r] = PIC_DEAD_CELL;
+      if (i < ncur) {
+        c[r] = Q.src.cell[i];
+        f[r] = Q.src.frac[i];
+        vx[r] = Q.src.vx[i];
+        vy[r] = Q.src.vy[i];
+        vz[r] = Q.src.vz[i];
+        id[r] = Q.src.id[i];
+      }
+    }
+    unsigned keep = 0u, live = 0u;
+#pragma unroll
+    for (int r = 0; r < NT_R; ++r) {
+      if (c[r] == PIC_DEAD_CELL) continue;
+      live |= 1u << r;
+      ++started;
+      const int cn = move_one(ph.dtdx, c[r], f[r], vx[r]);
+      if ((unsigned)cn >= (unsigned)N) {  // lost at a wall
+        atomicAdd(&bc.lost[cn < 0 ? 0 : 1], 1u);
+        continue;
+      }
+      c[r] = cn;
+      if (Q.ionize) {
+        const float2 ne2 = __ldg(Q.NE2 + cn);
+        const float ne = (1.f - f[r]) * ne2.x + f[r] * ne2.y;
+        const float Pz = -expm1f(-Q.Kdt * ne);
+        const float u = u01f(draw4(id[r], ph.seed, P.step, CH_NIZ, 0u).x);
+        if (fabsf(u - Pz) < 1e-5f * Pz) atomicAdd(&bc.near, 1u);
+        if (u < Pz) {  // the neutral becomes an ion beside a new electron
+          ionize_one(Q, base0, base1, cn, f[r], vx[r], vy[r], vz[r], id[r], &bc);
           continue;
         }
-        if (Q.ionize) {
-          const float2 ne2 = __ldg(Q.NE2 + cn);
-          const float ne = (1.f - fk) * ne2.x + fk * ne2.y;
-          const float Pz = -expm1f(-Q.Kdt * ne);
-          const uint4 w = draw4(ii[k], ph.seed, P.step, CH_NIZ, 0u);
-          const float u = u01f(w.x);
-          if (fabsf(u - Pz) < 1e-5f * Pz) atomicAdd(&bc.near, 1u);
-          if (u < Pz) {  // the neutral becomes an ion beside a new electron
-            const uint4 b = draw4(ii[k], ph.seed, P.step, CH_NIZ, 1u);
-            const uint4 kk = draw4(ii[k], ph.seed, P.step, CH_NIZ, 2u);
-            float n0, n1, n2, n3;
-            box_muller_f(b.x, b.y, n0, n1);
-            box_muller_f(b.z, b.w, n2, n3);
-            const float ve[3] = {Q.vt_sec * n0, Q.vt_sec * n1, Q.vt_sec * n2};
-            const float vi[3] = {xi[k], yi[k], zi[k]};
-            born_charged<1>(Q, base1, cn, fk, vi, ii[k], &bc);
-            born_charged<0>(Q, base0, cn, fk, ve, (unsigned long long)kk.x | ((unsigned long long)kk.y << 32), &bc);
-            atomicAdd(&bc.ionized, 1u);
-            continue;
-          }
-        }
-        c[k] = cn;
-        f[k] = fk;
-        vx[k] = xi[k];
-        vy[k] = yi[k];
-        vz[k] = zi[k];
-        id[k] = ii[k];
-        keep |= 1u << k;
       }
-    } else if (it < items) {  // an ion absorbed at a wall in this step
-      const unsigned e = Q.P.wlog[it - ngroups];
-      const int side = (int)(e >> 31);
-      const unsigned long long ion = Q.ion_id[e & 0x7FFFFFFFu];
-      const uint4 w = draw4(ion, ph.seed, P.step, CH_RECYCLE, 0u);
-      if ((w.x >> 8) < Q.recycle_u24) {
+      keep |= 1u << r;
+    }
+    if (COMPACT) {
+      write_kept<NT_R>(Q, g, 0ull, keep, c, f, vx, vy, vz, id);
+    } else {  // in place: position of each survivor, a dead mark for the others
+#pragma unroll
+      for (int r = 0; r < NT_R; ++r) {
+        if (!((live >> r) & 1u)) continue;
+        const unsigned long long i = i0 + 32ull * r;
+        const bool k = (keep >> r) & 1u;
+        Q.dst.cell[i] = k ? c[r] : PIC_DEAD_CELL;
+        if (k) Q.dst.frac[i] = f[r];
+      }
+    }
+  }
+
+  // ---- the ions the particle step absorbed: each returns as a neutral with probability recycle ------
+#pragma unroll 1
+  for (unsigned long long e0 = gw * 32ull; e0 < nlog; e0 += nwarps * 32ull) {
+    const unsigned long long e = e0 + lane;
+    int c[1];
+    float f[1], vx[1], vy[1], vz[1];
+    unsigned long long id[1];
+    unsigned keep = 0u;
+    if (e < nlog) {
+      const unsigned w = Q.P.wlog[e];
+      const int side = (int)(w >> 31);
+      const unsigned long long ion = Q.ion_id[w & 0x7FFFFFFFu];
+      const uint4 d = draw4(ion, ph.seed, P.step, CH_RECYCLE, 0u);
+      if ((d.x >> 8) < Q.recycle_u24) {
         const uint4 kk = draw4(ion, ph.seed, P.step, CH_RECYCLE, 1u);
-        const float a = Q.vt_rec * sqrtf(-2.f * logf(1.f - u01f(w.y)));  // flux half-Maxwellian
+        const float a = Q.vt_rec * sqrtf(-2.f * logf(1.f - u01f(d.y)));  // flux half-Maxwellian
         float n0, n1;
-        box_muller_f(w.z, w.w, n0, n1);
+        box_muller_f(d.z, d.w, n0, n1);
         c[0] = side ? N - 1 : 0;
         f[0] = side ? 0.99999994f : 0.f;
         vx[0] = side ? -a : a;
@@ -172,35 +250,9 @@ __global__ void __launch_bounds__(NT_TPB) k_neutral32(const __grid_constant__ Ne
         atomicAdd(&bc.recycled[side], 1u);
       }
     }
-    // one claim per warp for every output of its lanes
-    const int nout = __popc(keep);
-    int incl = nout;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    unsigned long long base = 0ull;
-    if (lane == 31 && total) base = atomicAdd(&g->nt_out, (unsigned long long)total);
-    unsigned long long j = __shfl_sync(0xFFFFFFFFu, base, 31) + (unsigned long long)(incl - nout);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (!((keep >> k) & 1u)) continue;
-      if (j >= Q.cap) {
-        atomicAdd(&g->dropped, 1ull);
-        atomicOr(&g->error, ERR_OVERFLOW);
-        continue;
-      }
-      Q.dst.cell[j] = c[k];
-      Q.dst.frac[j] = f[k];
-      Q.dst.vx[j] = vx[k];
-      Q.dst.vy[j] = vy[k];
-      Q.dst.vz[j] = vz[k];
-      Q.dst.id[j] = id[k];
-      ++j;
-    }
+    write_kept<1>(Q, g, append_at, keep, c, f, vx, vy, vz, id);
   }
+
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) started += __shfl_down_sync(0xFFFFFFFFu, started, o);
   if (lane == 0 && started) atomicAdd(&bc.started, started);
@@ -265,12 +317,15 @@ __global__ void __launch_bounds__(256) k_ndiag32(Species32 A, Ctl* ctl, float ma
 
 int occupancy_neutral32() {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_neutral32, NT_TPB, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_neutral32<false>, NT_TPB, 0);
   return b > 0 ? b : 1;
 }
 
-cudaError_t launch_neutral32(const NeutralParams& p, int grid, cudaStream_t st) {
-  k_neutral32<<<grid, NT_TPB, 0, st>>>(p);
+cudaError_t launch_neutral32(const NeutralParams& p, bool compact, int grid, cudaStream_t st) {
+  if (compact)
+    k_neutral32<true><<<grid, NT_TPB, 0, st>>>(p);
+  else
+    k_neutral32<false><<<grid, NT_TPB, 0, st>>>(p);
   return cudaGetLastError();
 }
 

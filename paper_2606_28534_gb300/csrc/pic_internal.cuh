@@ -145,8 +145,8 @@ struct StepParams32 {
 };
 
 // The neutral step (k_neutral.cu): the neutrals alive at the step start move, leave at the walls
-// or ionize; the ions the particle step logged at the walls return as neutrals.  Survivors and new
-// neutrals are written, compacted, into the other neutral buffer.
+// or ionize; the ions the particle step logged at the walls return as neutrals.  In place (dst ==
+// src, new neutrals appended), or compacted into the other buffer on the steps that sort.
 struct NeutralParams {
   StepParams32 P;                   // the particle step's parameters (births, deposits, counters)
   Species32 src, dst;               // neutral buffers read / written
@@ -288,6 +288,7 @@ struct PoissonParams {
   double ne_scale;   // n_e,j = R_0j ne_scale (x 2 at the wall nodes)
   Species32 nt_pad;  // neutrals: the buffer the neutral step wrote (padded to a multiple of 4)
   unsigned long long nt_cap;  // 0: no neutrals
+  int nt_append;     // the neutral step ran in place: its new neutrals follow the old extent
 };
 
 struct SortParams {
@@ -431,7 +432,8 @@ cudaError_t launch_restore32(const int* cell, const double* frac, const double* 
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                           cudaStream_t st);
 // tracked neutrals
-cudaError_t launch_neutral32(const NeutralParams& p, int grid, cudaStream_t st);
+// compact: write survivors and new neutrals compacted into p.dst (else p.dst == p.src, in place)
+cudaError_t launch_neutral32(const NeutralParams& p, bool compact, int grid, cudaStream_t st);
 int occupancy_neutral32();
 cudaError_t launch_nload32(const Species32& dst, unsigned long long n, int ppc, int N, unsigned long long seed,
                            double vt, cudaStream_t st);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpicgb.so")
 _lib = None
 
 PIC_ABI_VERSION = 2
-PIC_KERNEL_KINDS = 9
+PIC_KERNEL_KINDS = 10
 STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_EOVERFLOW",
           5: "PIC_ECORRUPT", 6: "PIC_ETIMEOUT", 7: "PIC_EDEVICE"}
 
