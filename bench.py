@@ -38,6 +38,10 @@ TRAFFIC_STEP, TRAFFIC_SCATTER = 49.07, 57.06
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
 # (8 B); on sort steps it writes each survivor, compacted, into the other buffer instead (28 B)
 BYTES_NEUTRAL_KERNEL, BYTES_NEUTRAL_COMPACT = 36, 56
+# DRAM bytes per neutral of one in-place neutral launch, from one ncu capture on the sheath profiling
+# case (c6p), scaled by neutrals to a full launch (writes still dirty in L2 at the launch's end are
+# not counted there)
+TRAFFIC_NEUTRAL = 32.80
 
 
 def _peaks():
@@ -323,7 +327,7 @@ def sheath_section(args, torch, pic, peak: float) -> dict:
                                    "ms_per_step": ms_q / K},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "kernel": "k_neutral32 (in place)", "bytes_per_neutral": BYTES_NEUTRAL_KERNEL,
-                     "bytes_per_launch": nt_bytes, "avg_launch_ms": nt_ms, "traffic": None,
+                     "bytes_per_launch": nt_bytes, "avg_launch_ms": nt_ms, "traffic": TRAFFIC_NEUTRAL * nt_launch,
                      "compacting_step": {"kernel": "k_neutral32 (compacting, sort steps)",
                                          "bytes_per_neutral": BYTES_NEUTRAL_COMPACT, "avg_launch_ms": nc_ms,
                                          "achieved": nc_bytes / (nc_ms / 1000.0) / 1e9 if nc_ms else None,

@@ -41,8 +41,9 @@ def _records(sp):
     return {"x": sp["cell"] + sp["frac"], "v": sp["v"], "id": sp["id"]}
 
 
-def _busy_blob(p, seed):
-    """The oracle's load of p plus ions leaving through both walls and neutrals near both walls."""
+def _busy_blob(p, seed, step=0):
+    """The oracle's load of p plus ions leaving through both walls and neutrals near both walls, at
+    step `step` (0: a sort step, the neutral step compacts; else in place unless step % interval = 0)."""
     rng = np.random.default_rng(seed)
     N = p["ncells"]
     d = snapfmt.parse(O.OracleSim(p).snapshot())
@@ -60,7 +61,7 @@ def _busy_blob(p, seed):
     vn[-200:, 0] = np.abs(vn[-200:, 0])
     nt = {"x": xn, "v": vn, "id": np.concatenate([nt["id"], (np.uint64(5) << np.uint64(60)) + np.arange(400, dtype=np.uint64)])}
     base = O.OracleSim(p).snapshot()
-    return snapfmt.round_to_fp32(snapfmt.with_particles(base, [el, io], neutrals=nt))
+    return snapfmt.round_to_fp32(snapfmt.with_particles(base, [el, io], step=step, neutrals=nt))
 
 
 def _both(p, blob):
@@ -155,14 +156,20 @@ def test_smoothed_field_matches_the_oracle(passes):
     assert np.abs(fg["E"] - fo["E"]).max() <= 2.0**-23 * sE + stepcheck.cond_tol(p["ncells"]) * sE
 
 
+@pytest.mark.parametrize("start", [0, 7], ids=["compacting", "in_place"])
 @pytest.mark.parametrize("case", ["load", "busy", "partial", "no_ionization"])
-def test_one_step_matches_the_oracle(case):
+def test_one_step_matches_the_oracle(case, start):
     p = W.variant(W.SMALL_C6, V_left=-2.0, **ROOMY)
     if case == "partial":
         p = W.variant(p, recycle=0.4)
     if case == "no_ionization":
         p = W.variant(p, K_iz=0.0)
-    blob = snapfmt.round_to_fp32(O.OracleSim(p).snapshot()) if case == "load" else _busy_blob(p, 11)
+    if case == "load":
+        d = snapfmt.parse(O.OracleSim(p).snapshot())
+        d["step"] = start
+        blob = snapfmt.round_to_fp32(snapfmt.build(d))
+    else:
+        blob = _busy_blob(p, 11, step=start)
     o, g = _both(p, blob)
     o.step(1)
     g.step(1)
@@ -203,6 +210,55 @@ def test_rerun_and_snapshot_continuation_are_bit_exact():
     sa, sb, sc = a.snapshot(), b.snapshot(), c.snapshot()
     assert sa == sb == sc  # storage order differs between runs; the state does not
     assert a.neutral_diag() == b.neutral_diag()
+
+
+def test_in_place_steps_then_a_compacting_step_match_the_oracle():
+    # steps 7, 8, 9 update the neutral buffer in place (dead slots accumulate, recycled neutrals are
+    # appended past the extent); step 10 compacts it
+    p = W.variant(W.SMALL_C6, V_left=-2.0, **ROOMY)
+    blob = _busy_blob(p, 15, step=7)
+    for k in range(4):
+        o, g = _both(p, blob)
+        o.step(1)
+        g.step(1)
+        _compare_one_step(p, blob, o, g)
+        blob = snapfmt.round_to_fp32(o.snapshot())
+
+
+def test_neutrals_over_a_frozen_plasma_match_the_oracle_for_twelve_steps():
+    # frozen charged species and no field: the neutrals' motion, wall losses and ionization (from a
+    # fixed electron density) follow the same trajectories in both codes step after step, through
+    # in-place steps (dead slots accumulate) and two compacting ones (steps 0 and 10)
+    p = W.variant(W.SMALL_C6, frozen_mask=3, field_mode=W.FIELD_ZERO, coll_mask=0, K_iz=0.3,
+                  source_mode=W.SOURCE_NONE, **ROOMY)
+    N = p["ncells"]
+    rng = np.random.default_rng(16)
+    d = snapfmt.parse(O.OracleSim(p).snapshot())
+    el, io = _records(d["species"][0]), _records(d["species"][1])
+    n = 4000
+    xn = np.concatenate([rng.uniform(0.0, N, n - 400), rng.uniform(0.0, 0.5, 200), N - rng.uniform(0.01, 0.5, 200)])
+    vn = rng.normal(size=(n, 3)) * 0.3
+    vn[-400:-200, 0] = -np.abs(vn[-400:-200, 0])
+    vn[-200:, 0] = np.abs(vn[-200:, 0])
+    ids = (np.uint64(5) << np.uint64(60)) + np.arange(n, dtype=np.uint64)
+    blob = snapfmt.round_to_fp32(snapfmt.with_particles(O.OracleSim(p).snapshot(), [el, io],
+                                                        neutrals={"x": xn, "v": vn, "id": ids}))
+    o, g = _both(p, blob)
+    steps = 12
+    o.step(steps)
+    g.step(steps)
+    no, ng = o.neutral_diag(), g.neutral_diag()
+    near = no["near_threshold"] + ng["near_threshold"]
+    a, b = stepcheck.by_id(snapfmt.parse(g.snapshot())["neutrals"]), stepcheck.by_id(snapfmt.parse(o.snapshot())["neutrals"])
+    common, ia, ib = np.intersect1d(a["id"], b["id"], return_indices=True)
+    x1 = xn + steps * vn[:, 0] * p["dt"] / (p["L"] / N)
+    edge = int(((np.abs(x1) < 1e-4) | (np.abs(x1 - N) < 1e-4)).sum())
+    assert len(a["id"]) + len(b["id"]) - 2 * len(common) <= 2 * near + edge
+    assert np.abs((a["cell"][ia] + a["frac"][ia]) - (b["cell"][ib] + b["frac"][ib])).max() <= steps * 2e-6
+    assert np.array_equal(a["v"][ia], np.float32(b["v"][ib]).astype(np.float64))  # velocities never change
+    assert abs(ng["ionized"] - no["ionized"]) <= near and ng["ionized"] > 0
+    assert abs(sum(ng["lost"]) - sum(no["lost"])) <= edge and sum(ng["lost"]) > 0
+    assert ng["particle_steps"] == no["particle_steps"] or near + edge > 0
 
 
 def test_accounting_is_exact_over_many_steps():
