@@ -217,6 +217,20 @@ int pic_neutral_diag(pic_handle* h, pic_neutral_diag_t* out);
  * partial sums): the device-to-host traffic of reading the diagnostics. */
 size_t pic_diag_bytes(void);
 
+/* Diagnostics without a wait: enqueue pic_diag's reductions (what = PIC_DIAG_ALL; none for
+ * PIC_DIAG_COUNTERS) and the copy of the control block into
+ * host_buf (pic_diag_bytes() bytes, owned by the caller; pinned memory keeps the copy asynchronous)
+ * on the handle's stream, and return.  Once the stream has passed that point (an event, a sync),
+ * pic_diag_decode turns the bytes into *out, as pic_diag would have at the call: the step count,
+ * counters and sums of the state after the steps enqueued before it, and the device-side error word
+ * (its status is returned, *out untouched, when an error was set).  Steps may be enqueued in between:
+ * reading step k's diagnostics while step k + 1 runs keeps the GPU busy. */
+#define PIC_DIAG_ALL 0u            /* every field of pic_diag_t */
+#define PIC_DIAG_COUNTERS 1u       /* counters, particle_steps and the error word only: no reduction
+                                      runs; ke, field_energy and net_charge_units read 0 */
+int pic_diag_async(pic_handle* h, void* host_buf, uint32_t what);
+int pic_diag_decode(const pic_handle* h, const void* host_buf, pic_diag_t* out);
+
 /* Copy the grid to host buffers of nnodes = N + 1 entries each (any may be NULL):
  * R: 2 x (N+1) int64 deposits (2^-32 particle units), rho, phi: FP64, E: FP32 node field as
  * seen by the particles.  Synchronises the stream. */

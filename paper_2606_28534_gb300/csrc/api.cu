@@ -1127,30 +1127,47 @@ int pic_sync(pic_handle* h) {
   return check_errors(h);
 }
 
-int pic_diag(pic_handle* h, pic_diag_t* d) {
-  if (!h || !d) return PIC_EINVAL;
-  CK(cudaMemsetAsync(h->ctl->ke_fx, 0, sizeof(h->ctl->ke_fx), h->st));
-  CK(cudaMemsetAsync(&h->ctl->netq, 0, sizeof(h->ctl->netq), h->st));
+int pic_diag_async(pic_handle* h, void* host_buf, uint32_t what) {
+  if (!h || !host_buf || what > PIC_DIAG_COUNTERS) return PIC_EINVAL;
   EvPair e;
   prof_begin(h, K_DIAG, &e);
-  // kinetic energy: summed by the last step (FP32 path, when it was asked to: ke_last), else one
+  CK(launch_store_u64(&h->ctl->diag_step, h->step, h->st));
+  CK(launch_store_u64(&h->ctl->diag_what, what, h->st));
+  if (what == PIC_DIAG_COUNTERS) {
+    prof_end(h, &e);
+    CK(cudaMemcpyAsync(host_buf, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
+    return PIC_OK;
+  }
+  CK(cudaMemsetAsync(&h->ctl->netq, 0, sizeof(h->ctl->netq), h->st));
+  // kinetic energy into ke_fx: the last step's sum when it made one (FP32 path, ke_last), else one
   // reduction pass here (same fixed point, same bits)
-  const bool ke_from_step = !h->plain && h->ke_valid;
-  if (h->plain) CK(launch_diag64(params64(h), h->grid_diag, h->st));
-  if (!h->plain && !ke_from_step) CK(launch_diag32(params32(h), h->grid_diag, h->st));
+  if (!h->plain && h->ke_valid) {
+    CK(cudaMemcpyAsync(h->ctl->ke_fx, h->ctl->ke_last, sizeof(h->ctl->ke_fx), cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    CK(cudaMemsetAsync(h->ctl->ke_fx, 0, sizeof(h->ctl->ke_fx), h->st));
+    if (h->plain)
+      CK(launch_diag64(params64(h), h->grid_diag, h->st));
+    else
+      CK(launch_diag32(params32(h), h->grid_diag, h->st));
+  }
   CK(launch_diag_grid(h->R[0], h->R[1], h->cfg.charge[0] > 0 ? 1 : -1, h->cfg.charge[1] > 0 ? 1 : -1, h->E, h->N,
                       h->cfg.L / h->N, h->ctl, h->st));
   prof_end(h, &e);
-  // one device-to-host read of the control block (its error word included) and one wait
+  CK(cudaMemcpyAsync(host_buf, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
+  return PIC_OK;
+}
+
+int pic_diag_decode(const pic_handle* h, const void* host_buf, pic_diag_t* d) {
+  if (!h || !host_buf || !d) return PIC_EINVAL;
   Ctl c;
-  CK(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
+  std::memcpy(&c, host_buf, sizeof(Ctl));
   const int rc = status_of(c.error);
   if (rc != PIC_OK) return rc;
   const int N = h->N;
   std::memset(d, 0, sizeof(*d));
   const double dx = h->cfg.L / N;
-  d->step = h->step;
+  const bool all = c.diag_what == PIC_DIAG_ALL;
+  d->step = c.diag_step;
   for (int s = 0; s < 2; ++s) {
     const double w = dx / h->cfg.ppc[s];
     d->n[s] = c.n_live[s];
@@ -1159,19 +1176,31 @@ int pic_diag(pic_handle* h, pic_diag_t* d) {
     d->near_threshold[s] = c.near_thr[s];
     d->nu_max_violations[s] = c.viol[s];
     d->births[s] = c.births[s];
-    d->ke[s] = (double)(ke_from_step ? c.ke_last[s] : c.ke_fx[s]) * (1.0 / 16777216.0) * w;
+    d->ke[s] = all ? (double)c.ke_fx[s] * (1.0 / 16777216.0) * w : 0.0;
     d->wall_energy[s] = (double)c.wall_energy_fx[s] * (1.0 / 16777216.0) * w;
   }
   for (int k = 0; k < 5; ++k) d->coll[k] = c.coll[k];
   d->source_pairs = c.source_pairs;
   d->dropped = c.dropped;
   d->wall_charge = c.wall_charge;
-  d->net_charge_units = c.netq;
-  double fe = 0.0;
-  for (int b = 0; b < PIC_DIAG_BLOCKS; ++b) fe += c.fe_part[b];
-  d->field_energy = fe;
   d->particle_steps = c.particle_steps;
+  if (all) {
+    d->net_charge_units = c.netq;
+    double fe = 0.0;
+    for (int b = 0; b < PIC_DIAG_BLOCKS; ++b) fe += c.fe_part[b];
+    d->field_energy = fe;
+  }
   return PIC_OK;
+}
+
+int pic_diag(pic_handle* h, pic_diag_t* d) {
+  if (!h || !d) return PIC_EINVAL;
+  // one device-to-host read of the control block (its error word included) and one wait
+  Ctl c;
+  int rc = pic_diag_async(h, &c, PIC_DIAG_ALL);
+  if (rc != PIC_OK) return rc;
+  CK(cudaStreamSynchronize(h->st));
+  return pic_diag_decode(h, &c, d);
 }
 
 int pic_neutral_diag(pic_handle* h, pic_neutral_diag_t* d) {

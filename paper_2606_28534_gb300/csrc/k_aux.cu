@@ -257,6 +257,15 @@ cudaError_t launch_restore32(const int* cell, const double* frac, const double* 
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_store_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+}  // namespace
+
+cudaError_t launch_store_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) {
+  k_store_u64<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   size_t blocks = (n + 255) / 256;

@@ -78,6 +78,8 @@ struct Ctl {
   unsigned long long nt_recycled[2], nt_lost[2], nt_ionized, nt_near, nt_particle_steps;
   unsigned long long nt_ke_fx;           // diag scratch: sum 0.5 m v^2 of the neutrals, 2^-24 units
   unsigned long long wlog_n;             // ions absorbed at a wall in the current step (recycling log)
+  unsigned long long diag_step;          // steps taken when the last diagnostics were enqueued
+  unsigned long long diag_what;          // PIC_DIAG_* of that request
 };
 
 struct Species32 {
@@ -431,6 +433,8 @@ cudaError_t launch_restore32(const int* cell, const double* frac, const double* 
                              unsigned long long base, int N, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                           cudaStream_t st);
+// *p = v, in stream order (v is taken at the call)
+cudaError_t launch_store_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 // tracked neutrals
 // compact: write survivors and new neutrals compacted into p.dst (else p.dst == p.src, in place)
 cudaError_t launch_neutral32(const NeutralParams& p, bool compact, int grid, cudaStream_t st);

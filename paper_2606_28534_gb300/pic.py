@@ -72,7 +72,7 @@ class PicDiag(C.Structure):
 SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapshot", "pic_restore",
            "pic_diag", "pic_get_field", "pic_profile", "pic_kernel_times", "pic_free",
            "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc", "pic_set_diag_interval", "pic_diag_bytes",
-           "pic_neutral_diag",
+           "pic_neutral_diag", "pic_diag_async", "pic_diag_decode",
            "pic_batch_variant_count", "pic_batch_variant_name", "pic_batch_workspace_size",
            "pic_batch_init", "pic_batch_set_tuning", "pic_batch_set_diag_interval", "pic_batch_get_tuning", "pic_batch_step",
            "pic_batch_sync", "pic_batch_diag", "pic_batch_snapshot", "pic_batch_restore",
@@ -107,6 +107,8 @@ def lib():
         L.pic_restore.argtypes = [V, V, C.c_size_t]
         L.pic_diag.argtypes = [V, P(PicDiag)]
         L.pic_neutral_diag.argtypes = [V, P(PicNeutralDiag)]
+        L.pic_diag_async.argtypes = [V, V, C.c_uint32]
+        L.pic_diag_decode.argtypes = [V, V, P(PicDiag)]
         L.pic_get_field.argtypes = [V, P(C.c_int64), P(C.c_double), P(C.c_double), P(C.c_float),
                                     C.c_size_t]
         L.pic_profile.argtypes = [V, C.c_int]
@@ -245,6 +247,19 @@ class Simulation:
     def diag(self) -> dict:
         d = PicDiag()
         _check(lib().pic_diag(self._h, C.byref(d)), "pic_diag")
+        return _diag_dict(d)
+
+    def diag_async(self, buf, counters_only: bool = False) -> None:
+        """Enqueue the diagnostics into ``buf`` (a pinned uint8 tensor of ``pic_diag_bytes()`` bytes)
+        without waiting; decode with ``diag_decode`` once the stream has passed this point.
+        ``counters_only``: no reduction (kinetic and field energy, net charge read 0)."""
+        if buf.numel() < lib().pic_diag_bytes():
+            raise ValueError("diagnostics buffer too small")
+        _check(lib().pic_diag_async(self._h, buf.data_ptr(), 1 if counters_only else 0), "pic_diag_async")
+
+    def diag_decode(self, buf) -> dict:
+        d = PicDiag()
+        _check(lib().pic_diag_decode(self._h, buf.data_ptr(), C.byref(d)), "pic_diag_decode")
         return _diag_dict(d)
 
     def neutral_diag(self) -> dict:

@@ -278,6 +278,43 @@ def test_diag_interval_changes_no_bit_of_the_diagnostics():
         g.close()
 
 
+def test_asynchronous_diagnostics_equal_the_synchronous_ones():
+    # pic_diag_async copies the control block as pic_diag would read it at that call; the host decodes
+    # it after later steps were enqueued, and gets the diagnostics of the earlier state
+    import torch
+
+    p = W.variant(W.SMALL_C3, V_left=-2.0)
+    a, b = pic.Simulation(p), pic.Simulation(p)
+    a.set_diag_interval(1)  # also the path where the step sums the kinetic energy
+    nb = pic.lib().pic_diag_bytes()
+    bufs = [torch.empty(nb, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    evs = [torch.cuda.Event() for _ in range(2)]
+    ref = []
+    for k in range(12):
+        b.step(1)
+        ref.append(b.diag())
+        a.step(1)
+        a.diag_async(bufs[k % 2])
+        evs[k % 2].record(a.stream)
+        if k:
+            evs[(k - 1) % 2].synchronize()
+            assert a.diag_decode(bufs[(k - 1) % 2]) == ref[k - 1]
+    evs[11 % 2].synchronize()
+    assert a.diag_decode(bufs[11 % 2]) == ref[11] == a.diag()
+    # counters only: no reduction runs; the energies and the net charge read 0, the rest is the same
+    a.diag_async(bufs[0], counters_only=True)
+    torch.cuda.synchronize()
+    c = a.diag_decode(bufs[0])
+    full = a.diag()
+    assert c["ke"] == [0.0, 0.0] and c["field_energy"] == 0.0 and c["net_charge_units"] == 0
+    for k in ("step", "n", "wall_hits", "coll", "births", "source_pairs", "particle_steps", "wall_energy"):
+        assert c[k] == full[k], k
+    with pytest.raises(ValueError):
+        a.diag_async(torch.empty(8, dtype=torch.uint8, pin_memory=True))
+    a.close()
+    b.close()
+
+
 def test_charge_and_accounting_invariants_every_step():
     p = W.variant(W.SMALL_C3, V_left=-2.0)
     g = pic.Simulation(p)
