@@ -310,3 +310,59 @@ def test_full_size_sheath_invariants():
 def test_batch_and_adjoint_refuse_the_sheath_physics():
     with pytest.raises(pic.PicError):
         pic.Batch([W.SMALL_C6])
+
+
+def test_smallest_grid_with_four_smoothing_passes_matches_the_oracle():
+    # N = 2: one interior node between the walls; the smoothing's wall rules act on every node
+    p = W.variant(W.SMALL_C6, ncells=2, L=2.0, ppc=(7, 7), neutral_ppc=5, smooth_passes=4, V_left=-1.0, **ROOMY)
+    blob = snapfmt.round_to_fp32(O.OracleSim(p).snapshot())
+    o, g = _both(p, blob)
+    fo, fg = o.fields(), g.fields()
+    assert np.array_equal(fo["R"], fg["R"])
+    assert np.abs(fg["rho"] - fo["rho"]).max() <= 1e-13 * np.abs(fo["rho"]).max()
+    assert np.abs(fg["E"] - fo["E"]).max() <= 2.0**-23 * np.abs(fo["E"]).max() + 1e-12
+    o.step(1)
+    g.step(1)
+    _compare_one_step(p, blob, o, g)
+
+
+def test_largest_grid_smoothing_crosses_every_cluster_boundary():
+    # 196607 cells: 24576 nodes per CTA of the field cluster; the stencil reads its neighbours across
+    # the seven CTA boundaries in each of the three passes
+    p = W.variant(W.SMALL_C6, ncells=196607, L=196607.0, ppc=(2, 2), neutral_ppc=1, smooth_passes=3,
+                  V_left=-2.0, load_profile=W.LOAD_EXP, profile_scale=20000.0, **ROOMY)
+    blob = snapfmt.round_to_fp32(O.OracleSim(p).snapshot())
+    o, g = _both(p, blob)
+    fo, fg = o.fields(), g.fields()
+    assert np.array_equal(fo["R"], fg["R"])
+    assert np.abs(fg["rho"] - fo["rho"]).max() <= 1e-13 * np.abs(fo["rho"]).max()
+    s = max(np.abs(fo["phi"]).max(), 1.0)
+    assert np.abs(fg["phi"] - fo["phi"]).max() <= stepcheck.cond_tol(p["ncells"]) * s
+    sE = np.abs(fo["E"]).max()
+    assert np.abs(fg["E"] - fo["E"]).max() <= 2.0**-23 * sE + stepcheck.cond_tol(p["ncells"]) * sE
+
+
+def test_a_full_neutral_buffer_reports_an_overflow_and_drops_the_rest():
+    # room for 6144 neutrals: 58 per cell at t = 0 and 400 more in the state leave 176 free slots;
+    # 600 ions recycle in the first step
+    p = W.variant(W.SMALL_C6, neutral_ppc=58, neutral_capacity=1.0, capacity_factor=2.0, K_iz=0.0)
+    g = pic.Simulation(p)
+    assert g.restore(_busy_blob(p, 17, step=3)) == 0  # an in-place step: recycled neutrals are appended
+    g.step(1)
+    with pytest.raises(pic.PicError) as e:
+        g.sync()
+    assert e.value.status == 4  # PIC_EOVERFLOW
+    g.close()
+
+
+def test_blobs_of_other_configurations_or_versions_are_refused():
+    p = W.variant(W.SMALL_C6, **ROOMY)
+    g = pic.Simulation(p)
+    good = g.snapshot()
+    assert snapfmt.parse(good)["version"] == 2
+    assert g.restore(good[:-9] + good[-4:]) == 5                   # truncated: PIC_ECORRUPT
+    other = pic.Simulation(W.variant(p, K_iz=0.25)).snapshot()     # other physics: other hash
+    assert g.restore(other) == 5
+    plain = pic.Simulation(W.variant(p, neutrals=0, neutral_ppc=0)).snapshot()
+    assert snapfmt.parse(plain)["version"] == 1 and g.restore(plain) == 5
+    assert g.restore(good) == 0
