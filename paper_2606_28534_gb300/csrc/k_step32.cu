@@ -144,10 +144,10 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         e2[k] = make_float2(0.f, 0.f);
         if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL) e2[k] = __ldg(P.E2 + c[k]);
       }
-      // scatter: claim each live particle's slot in its cell (four atomics in flight)
-      unsigned slot[PIC_PPT];
+      // scatter: claim each live particle's slot in its cell (four atomics in flight; their results
+      // are first needed at the stores, so the Philox work below covers their latency)
+      unsigned slot[PIC_PPT], peers[PIC_PPT], base[PIC_PPT];
       if (SCATTER) {
-        unsigned peers[PIC_PPT], base[PIC_PPT];
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
           const bool live = c[k] != PIC_DEAD_CELL;
@@ -155,9 +155,6 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
           base[k] = 0u;
           if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(P.cursor[s] + c[k], (unsigned)__popc(peers[k]));
         }
-#pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k)
-          slot[k] = __shfl_sync(0xFFFFFFFFu, base[k], __ffs(peers[k]) - 1) + (unsigned)__popc(peers[k] & below);
       }
       // the stage is read: refill it with the chunk NSTAGE steps ahead
       fence_proxy_async_smem();
@@ -206,6 +203,9 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         }
       }
       if (SCATTER) {
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k)
+          slot[k] = __shfl_sync(0xFFFFFFFFu, base[k], __ffs(peers[k]) - 1) + (unsigned)__popc(peers[k] & below);
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
           if (!((live0 >> k) & 1u)) continue;
