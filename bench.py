@@ -22,6 +22,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -271,6 +273,60 @@ def batched(args, torch, pic, peak: float) -> dict:
         "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in kt.items()
                     if v["launches"]},
     }
+
+
+DIAG_FIELDS = ("n", "wall_hits", "coll", "births", "near_threshold", "wall_charge", "net_charge_units",
+               "ke", "field_energy", "wall_energy")
+
+
+def _rel(a, b):
+    a, b = np.atleast_1d(np.asarray(a, np.float64)).ravel(), np.atleast_1d(np.asarray(b, np.float64)).ravel()
+    d = np.abs(a - b)
+    scale = np.maximum(np.abs(b), 1e-300)
+    return float((d / scale).max()) if d.any() else 0.0
+
+
+def precision_section(args, torch, pic) -> dict:
+    """The error of each diagnostic against the FP64 oracle: config 2 after 20 steps on the GPU, that
+    state given to the oracle, to the FP32 path and to the plain FP64 path, one step of each; the
+    relative difference of every pic_diag field (counts: the difference itself)."""
+    from oracle import oracle as O
+
+    p = W.C2
+    g = pic.Simulation(p)
+    g.step(20)
+    blob = g.snapshot()  # FP32 values: the same state for all three codes
+    g.close()
+    del g
+    cores = len(os.sched_getaffinity(0))
+    o = O.OracleSim(p, threads=cores)
+    assert o.restore(blob) == 0
+    o.step(1)
+    do = o.diag()
+    out = {"workload": "c2 (8,192,000 particles) after 20 steps, then one step from the same state",
+           "oracle_threads": cores, "fields": {}}
+    res = {}
+    for name, q in (("fp32", p), ("fp64_plain", W.variant(p, precision=W.PRECISION_FP64_PLAIN))):
+        h = pic.Simulation(q)
+        if h.restore(blob) != 0:
+            raise RuntimeError("restore failed")
+        h.step(1)
+        res[name] = h.diag()
+        h.close()
+        del h
+        torch.cuda.empty_cache()
+    for k in DIAG_FIELDS:
+        row = {}
+        for name, d in res.items():
+            if k in ("ke", "field_energy", "wall_energy"):
+                row[name] = _rel(d[k], do[k])
+            else:
+                row[name] = int(np.abs(np.asarray(d[k], np.int64) - np.asarray(do[k], np.int64)).max())
+        out["fields"][k] = row
+    out["what"] = ("ke, field_energy, wall_energy: max relative difference; the others: max absolute "
+                   "difference of counts (collision and near-threshold counts may differ by the "
+                   "near-threshold draws both codes count)")
+    return out
 
 
 def sheath_section(args, torch, pic, peak: float) -> dict:
@@ -559,6 +615,9 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
     sheath = None
     if not args.no_sheath:
         sheath = sheath_section(args, torch, pic, peak)
+    precision = None
+    if not args.no_cpu and not args.no_precision:
+        precision = precision_section(args, torch, pic)
 
     if rank != 0:
         return
@@ -587,6 +646,7 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         "batched": batch,
         "adjoint": adj,
         "sheath": sheath,
+        "precision": precision,
         "e2e": e2e,
     }
     if world == 1 and not args.no_cpu:
@@ -614,6 +674,7 @@ def main():
     ap.add_argument("--adj-reps", type=int, default=5)
     ap.add_argument("--batch-steps", type=int, default=W.C4_STEPS)
     ap.add_argument("--no-sheath", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--sheath-steps", type=int, default=W.C6_STEPS)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -190,6 +190,38 @@ def test_single_step_fp64_plain_matches_oracle(name):
     assert abs(dg["ke"][0] - do["ke"][0]) <= 1e-6 * do["ke"][0]
 
 
+def test_error_of_each_diagnostic_against_the_oracle():
+    # one step from the same state (the GPU's FP32 values) in the oracle, the FP32 path and the plain
+    # FP64 path: the energies within their arithmetic's rounding, the counts equal up to the
+    # near-threshold draws both codes count
+    p = W.variant(W.SMALL_C2, V_left=-2.0)
+    g = pic.Simulation(p)
+    g.step(20)
+    blob = g.snapshot()
+    o = O.OracleSim(p)
+    assert o.restore(blob) == 0
+    o.step(1)
+    do = o.diag()
+    # both GPU paths sum energies in 2^-24 fixed point per particle: up to n 2^-25 w of quantisation
+    w = np.array([p["L"] / p["ncells"] / p["ppc"][s] for s in range(2)])
+    quant = {"ke": np.array(do["n"]) * 2.0**-25 * w, "wall_energy": np.array(
+        [sum(do["wall_hits"][s]) for s in range(2)]) * 2.0**-25 * w, "field_energy": 0.0}
+    for prec, tol in ((W.PRECISION_FP32, {"ke": 1e-6, "wall_energy": 1e-6, "field_energy": 1e-3}),
+                      (W.PRECISION_FP64_PLAIN, {"ke": 1e-12, "wall_energy": 1e-12, "field_energy": 1e-9})):
+        h = pic.Simulation(W.variant(p, precision=prec))
+        assert h.restore(blob) == 0
+        h.step(1)
+        d = h.diag()
+        near = sum(d["near_threshold"]) + sum(do["near_threshold"]) - 2 * sum(snapfmt.parse(blob)["counters"][9:11])
+        for k, t in tol.items():
+            a, b = np.atleast_1d(d[k]), np.atleast_1d(do[k])
+            assert np.all(np.abs(a - b) <= t * np.abs(b) + quant[k] + 1e-300), (prec, k, a, b)
+        assert d["wall_hits"] == do["wall_hits"] and d["wall_charge"] == do["wall_charge"]
+        assert all(abs(x - y) <= near for x, y in zip(d["coll"], do["coll"]))
+        assert all(abs(x - y) <= 2 * near for x, y in zip(d["n"], do["n"]))
+        h.close()
+
+
 # ------------------------------------------------------------------------------------------------
 def test_rerun_and_snapshot_continuation_are_bit_exact():
     p = W.variant(W.SMALL_COLL, sort_interval=3)
