@@ -37,6 +37,8 @@ BYTES_SCATTER_EXTRA = 8  # the step after a sort writes each particle to a new s
 # dram__bytes_write.sum) of these kernels on the 12.6M-particle profiling case (c3p), scaled by
 # particles to a full launch: the ordinary step and the step after a sort
 TRAFFIC_STEP, TRAFFIC_SCATTER = 49.07, 57.06
+# the same for the ensemble's particle step (ncu on a 16-run ensemble of config 4's distribution)
+TRAFFIC_BSTEP = 49.28
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
 # (8 B); on sort steps it writes each survivor, compacted, into the other buffer instead (28 B)
 BYTES_NEUTRAL_KERNEL, BYTES_NEUTRAL_COMPACT = 36, 56
@@ -217,10 +219,13 @@ def batched(args, torch, pic, peak: float) -> dict:
     CUDA graphs), against the same runs advanced one at a time through the single-run API."""
     from paper_2606_28534_gb300 import autotune
 
-    runs = W.c4()
+    runs = W.c4() if args.batch_sims == W.C4_SIMS else W.ensemble(args.batch_sims)
     K = args.batch_steps
     b = pic.Batch(runs)
-    tune = autotune.tune(b, cache_path=os.path.join(tempfile.gettempdir(), "pic_gb300_tuning.json"))
+    if args.no_tune:
+        tune = {"tuning": {"variant": 0, "ctas_per_sm": 0, "use_graph": True}, "cached": False, "trials": []}
+    else:
+        tune = autotune.tune(b, cache_path=os.path.join(tempfile.gettempdir(), "pic_gb300_tuning.json"))
     b.step(args.warmup)
     b.sync()
 
@@ -269,7 +274,8 @@ def batched(args, torch, pic, peak: float) -> dict:
         "speedup_vs_one_at_a_time": value / one,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "kernel": "k_bstep32", "bytes_per_launch": bytes_per_launch,
-                     "avg_launch_ms": step_ms, "traffic": None},
+                     "avg_launch_ms": step_ms,
+                     "traffic": TRAFFIC_BSTEP * kps / max(1, kt["step"]["launches"])},
         "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in kt.items()
                     if v["launches"]},
     }
@@ -673,6 +679,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adj-reps", type=int, default=5)
     ap.add_argument("--batch-steps", type=int, default=W.C4_STEPS)
+    ap.add_argument("--batch-sims", type=int, default=W.C4_SIMS, help="runs of the ensemble (config 4: 256)")
+    ap.add_argument("--no-tune", action="store_true", help="default launch configuration of the batch")
     ap.add_argument("--no-sheath", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--sheath-steps", type=int, default=W.C6_STEPS)
