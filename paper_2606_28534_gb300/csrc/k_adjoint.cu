@@ -172,82 +172,55 @@ __global__ void __launch_bounds__(1024) k_adj_field_t(const double* __restrict__
   if (tid == 0) *gV += part[0] * (inv_dx / (double)N);
 }
 
-// One backward step of every particle alive after step n.  A warp takes 32 consecutive particles
-// (they stay close in cells: the load is in cell order); the mu contributions of the lanes that share
-// a cell are summed by the lowest of them (in lane order, through shared memory) and added to global
-// memory with one atomic pair per cell, instead of one pair per particle.
+// One backward step of every particle alive after step n.
 __global__ void __launch_bounds__(256) k_adj_reverse(const AdjRev P) {
-  __shared__ double sa0[8][32], sa1[8][32];
   const long long n = P.step;
   const int N = P.N;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (unsigned long long)(w * 32);
-       base < P.np; base += stride) {
-    const unsigned long long p = base + lane;
-    int key = -1;  // the cell whose two nodes receive this lane's mu contribution
-    double a0 = 0.0, a1 = 0.0;
-    if (p < P.np && P.absorb[p] > n) {  // alive after step n (otherwise nothing depends on its state)
-      const int s = p < P.n0 ? 0 : 1;
-      double lx = P.lx[p], lvx = P.lvx[p], lvy = P.lvy[p], lvz = P.lvz[p];
-      // deposit of x^{n+1}
-      const int c1 = P.s1.cell[p];
-      const float f1 = P.s1.frac[p];
-      const double g0 = c1 == 0 ? -P.mu[0] : P.dx * P.chi[c1];
-      const double g1 = c1 + 1 == N ? P.mu[N] : P.dx * P.chi[c1 + 1];
-      lx += P.qw[s] * (g1 - g0);
-      // J_flux at step n
-      if (s == 0 && P.flux_dtw != 0.0) {
-        const double d = (double)(c1 - (N - 1)) + (double)f1;
-        const double ad = fabs(d);
-        if (ad < 1.0) {
-          lx += P.flux_dtw * (double)P.s1.vx[p] * (d > 0.0 ? -1.0 : (d < 0.0 ? 1.0 : 0.0));
-          lvx += P.flux_dtw * (1.0 - ad);
-        }
+  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < P.np;
+       p += (unsigned long long)gridDim.x * blockDim.x) {
+    if (P.absorb[p] <= n) continue;  // not alive after step n: nothing depends on its state
+    const int s = p < P.n0 ? 0 : 1;
+    double lx = P.lx[p], lvx = P.lvx[p], lvy = P.lvy[p], lvz = P.lvz[p];
+    // deposit of x^{n+1}
+    const int c1 = P.s1.cell[p];
+    const float f1 = P.s1.frac[p];
+    const double g0 = c1 == 0 ? -P.mu[0] : P.dx * P.chi[c1];
+    const double g1 = c1 + 1 == N ? P.mu[N] : P.dx * P.chi[c1 + 1];
+    lx += P.qw[s] * (g1 - g0);
+    // J_flux at step n
+    if (s == 0 && P.flux_dtw != 0.0) {
+      const double d = (double)(c1 - (N - 1)) + (double)f1;
+      const double ad = fabs(d);
+      if (ad < 1.0) {
+        lx += P.flux_dtw * (double)P.s1.vx[p] * (d > 0.0 ? -1.0 : (d < 0.0 ? 1.0 : 0.0));
+        lvx += P.flux_dtw * (1.0 - ad);
       }
-      if (!((P.frozen_mask >> s) & 1u)) {
-        // x^{n+1} = x^n + v_x^{n+1} dt / dx
-        lvx += lx * P.dtdx;
-        // v^{n+1} = M v^n + (M + I) h e(x^n)
-        const double* M = P.M[s];  // row-major
-        if (P.field_mode == 0u) {
-          const double eb = P.h[s] * ((M[0] + 1.0) * lvx + M[3] * lvy + M[6] * lvz);
-          const int c0 = P.s0.cell[p];
-          const double f0 = (double)P.s0.frac[p];
-          const double E0 = (double)(float)P.E[c0], E1 = (double)(float)P.E[c0 + 1];
-          lx += eb * (E1 - E0);
-          key = c0;
-          a0 = eb * (1.0 - f0);
-          a1 = eb * f0;
-        }
-        const double ax = M[0] * lvx + M[3] * lvy + M[6] * lvz;
-        const double ay = M[1] * lvx + M[4] * lvy + M[7] * lvz;
-        const double az = M[2] * lvx + M[5] * lvy + M[8] * lvz;
-        lvx = ax;
-        lvy = ay;
-        lvz = az;
-      }
-      P.lx[p] = lx;
-      P.lvx[p] = lvx;
-      P.lvy[p] = lvy;
-      P.lvz[p] = lvz;
     }
-    // mu^n_c += e_bar (1 - f), mu^n_{c+1} += e_bar f, summed per cell over the warp
-    sa0[w][lane] = a0;
-    sa1[w][lane] = a1;
-    __syncwarp();
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
-    if (key >= 0 && lane == __ffs(peers) - 1) {
-      double s0 = 0.0, s1 = 0.0;
-      for (unsigned m = peers; m; m &= m - 1u) {
-        const int l = __ffs(m) - 1;
-        s0 += sa0[w][l];
-        s1 += sa1[w][l];
+    if (!((P.frozen_mask >> s) & 1u)) {
+      // x^{n+1} = x^n + v_x^{n+1} dt / dx
+      lvx += lx * P.dtdx;
+      // v^{n+1} = M v^n + (M + I) h e(x^n)
+      const double* M = P.M[s];  // row-major
+      if (P.field_mode == 0u) {
+        const double eb = P.h[s] * ((M[0] + 1.0) * lvx + M[3] * lvy + M[6] * lvz);
+        const int c0 = P.s0.cell[p];
+        const double f0 = (double)P.s0.frac[p];
+        const double E0 = (double)(float)P.E[c0], E1 = (double)(float)P.E[c0 + 1];
+        lx += eb * (E1 - E0);
+        atomicAdd(P.mu_next + c0, eb * (1.0 - f0));
+        atomicAdd(P.mu_next + c0 + 1, eb * f0);
       }
-      atomicAdd(P.mu_next + key, s0);
-      atomicAdd(P.mu_next + key + 1, s1);
+      const double ax = M[0] * lvx + M[3] * lvy + M[6] * lvz;
+      const double ay = M[1] * lvx + M[4] * lvy + M[7] * lvz;
+      const double az = M[2] * lvx + M[5] * lvy + M[8] * lvz;
+      lvx = ax;
+      lvy = ay;
+      lvz = az;
     }
-    __syncwarp();
+    P.lx[p] = lx;
+    P.lvx[p] = lvx;
+    P.lvy[p] = lvy;
+    P.lvz[p] = lvz;
   }
 }
 

@@ -9,11 +9,10 @@
 // and the node field is E_j = (phi_{j-1} - phi_{j+1}) / (2 dx) inside, Gauss's law over the half
 // cell at the walls: E_0 = (phi_0 - phi_1)/dx - rho_0 dx/2, E_N = (phi_{N-1} - phi_N)/dx + rho_N dx/2.
 //
-// Two implementations, each one thread-block cluster: PIC_FIELD_CTAS CTAs, or one CTA when the grid
-// has at most PIC_FIELD_SMALL nodes (no cluster barrier to wait for).  A CTA stages its contiguous
-// segment of the N + 1 nodes in shared memory with coalesced loads, each thread scans a run of
-// consecutive nodes, and CTA totals travel through distributed shared memory.  The CTA count is a
-// function of N, so every bit of the result is reproducible.
+// Two implementations, each one thread-block cluster of PIC_FIELD_CTAS CTAs; a CTA stages its
+// contiguous segment of the N + 1 nodes in shared memory with coalesced loads, each thread scans a
+// run of consecutive nodes, and CTA totals travel through distributed shared memory.  The CTA
+// count is fixed, so every bit of the result is reproducible.
 //
 // k_field_exact (FP32 path, integer species charges; the per-step solve).  FP64 runs at a small
 // fraction of the FP32/INT32 rate on this GPU, and the deposit is already exact int64, so the
@@ -41,7 +40,6 @@
 
 #include <cstring>
 #include <type_traits>
-#include <utility>
 
 #include "pic_internal.cuh"
 
@@ -165,19 +163,18 @@ __device__ void smooth_segment(T* buf, int len, int a, int N, int seg, int i0, i
 // =============================================================================================
 // BATCH: cluster k of the grid solves simulation k of an ensemble, with the parameters tab[k].
 template <bool BATCH>
-__global__ void __launch_bounds__(PIC_FIELD_TPB, 1)
+__global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIELD_TPB, 1)
     k_field_exact(const __grid_constant__ PoissonParams P0, const PoissonParams* __restrict__ tab) {
+  const PoissonParams& P = BATCH ? tab[blockIdx.x / PIC_FIELD_CTAS] : P0;
   extern __shared__ long long Rn[];  // r_j of this CTA's segment, then E_j (as double bits)
   __shared__ __int128 warp_q[PIC_FIELD_TPB / 32], warp_p[PIC_FIELD_TPB / 32];
   __shared__ __int128 cta_q, cta_p;  // read by the other CTAs of the cluster
   cg::cluster_group cluster = cg::this_cluster();
-  const int nct = (int)cluster.num_blocks();  // CTAs of the cluster (field_ctas)
-  const PoissonParams& P = BATCH ? tab[blockIdx.x / nct] : P0;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int rank = (int)cluster.block_rank();
   const int N = P.N;
   const int M = N + 1;
-  const int seg = (M + nct - 1) / nct;
+  const int seg = (M + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
   const int a = rank * seg;
   const int len = max(0, min(seg, M - a));
 
@@ -264,7 +261,8 @@ __global__ void __launch_bounds__(PIC_FIELD_TPB, 1)
   __int128 q = (w ? warp_q[w - 1] : (__int128)0) + iq - oq;  // exclusive prefix within the CTA
   cluster.sync();  // CTA totals visible; every input of pass 1 has been read
   __int128 Qtot = 0, Ptot = 0;
-  for (int r = 0; r < nct; ++r) {
+#pragma unroll
+  for (int r = 0; r < PIC_FIELD_CTAS; ++r) {
     const __int128 vq = *cluster.map_shared_rank(&cta_q, r);
     const __int128 vp = *cluster.map_shared_rank(&cta_p, r);
     if (r < rank) q += vq;
@@ -339,7 +337,8 @@ __device__ __forceinline__ double node_rho(const PoissonParams& P, int j) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(PIC_FIELD_TPB, 1) k_field_fp64(const __grid_constant__ PoissonParams P) {
+__global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIELD_TPB, 1)
+    k_field_fp64(const __grid_constant__ PoissonParams P) {
   extern __shared__ double F[];  // this CTA's segment: f_j = dx^2 rho_j, then phi_j
   __shared__ Pair warp_tot[PIC_FIELD_TPB / 32];
   __shared__ Pair cta_tot;  // read by the other CTAs of the cluster
@@ -348,8 +347,7 @@ __global__ void __launch_bounds__(PIC_FIELD_TPB, 1) k_field_fp64(const __grid_co
   const int rank = (int)cluster.block_rank();
   const int N = P.N;
   const int M = N + 1;
-  const int nct = (int)cluster.num_blocks();
-  const int seg = (M + nct - 1) / nct;
+  const int seg = (M + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
   const int a = rank * seg;
   const int len = max(0, min(seg, M - a));
   const double dx2 = P.dx * P.dx;
@@ -410,7 +408,8 @@ __global__ void __launch_bounds__(PIC_FIELD_TPB, 1) k_field_fp64(const __grid_co
   }
   cluster.sync();  // CTA totals visible; every input of pass 1 has been read
   Pair off = {0.0, 0.0}, tot = {0.0, 0.0};
-  for (int r = 0; r < nct; ++r) {
+#pragma unroll
+  for (int r = 0; r < PIC_FIELD_CTAS; ++r) {
     const Pair v = *cluster.map_shared_rank(&cta_tot, r);
     if (r < rank) {
       off.a += v.a;
@@ -509,59 +508,34 @@ static void field_attrs() {
   }
 }
 
-// CTAs of the cluster that solves N + 1 nodes: one for small grids (every node in one CTA's shared
-// memory, no cluster barriers), PIC_FIELD_CTAS otherwise.
-static int field_ctas(int N) { return N + 1 <= PIC_FIELD_SMALL ? 1 : PIC_FIELD_CTAS; }
-
-template <class... A, class... B>
-static cudaError_t launch_clustered(void (*kern)(A...), int grid, int nct, size_t smem, cudaStream_t st, B&&... args) {
-  cudaLaunchConfig_t cfg;
-  std::memset(&cfg, 0, sizeof(cfg));
-  cfg.gridDim = dim3(grid, 1, 1);
-  cfg.blockDim = dim3(PIC_FIELD_TPB, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = nct;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, std::forward<B>(args)...);
-}
-
 cudaError_t launch_field(const PoissonParams& p, cudaStream_t st) {
   if (p.N < 2 || p.N > PIC_MAX_CELLS_FP32) return cudaErrorInvalidValue;
-  const int nct = field_ctas(p.N);
-  const int seg = (p.N + 1 + nct - 1) / nct;
+  const int seg = (p.N + 1 + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
   const size_t smem = sizeof(double) * (size_t)seg;
   field_attrs();
-  const PoissonParams* none = nullptr;
-  cudaError_t e;
   switch (p.mode) {
     case 0:
-      e = p.exact ? launch_clustered(k_field_exact<false>, nct, nct, smem, st, p, none)
-                  : launch_clustered(k_field_fp64<0>, nct, nct, smem, st, p);
+      if (p.exact)
+        k_field_exact<false><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p, nullptr);
+      else
+        k_field_fp64<0><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p);
       break;
-    case 1: e = launch_clustered(k_field_fp64<1>, nct, nct, smem, st, p); break;
-    case 2: e = launch_clustered(k_field_fp64<2>, nct, nct, smem, st, p); break;
-    case 3: e = launch_clustered(k_field_fp64<3>, nct, nct, smem, st, p); break;
+    case 1: k_field_fp64<1><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
+    case 2: k_field_fp64<2><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
+    case 3: k_field_fp64<3><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return cudaGetLastError();
 }
 
-// Integer-exact field of every simulation of an ensemble: one cluster of PIC_FIELD_CTAS CTAs per
-// simulation, parameters tab[k] in device memory (their ctl, counts and arrays point into the
-// batch's arrays).
+// Integer-exact field of every simulation of an ensemble: one cluster per simulation, parameters
+// tab[k] in device memory (their ctl, counts and arrays point into the batch's arrays).
 cudaError_t launch_field_batch(const PoissonParams* tab, int nsims, int maxN, cudaStream_t st) {
   if (nsims < 1 || nsims > PIC_BATCH_MAX || maxN < 2 || maxN > PIC_MAX_CELLS_FP32) return cudaErrorInvalidValue;
   const int seg = (maxN + 1 + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
   field_attrs();
   PoissonParams unused;
   memset(&unused, 0, sizeof(unused));
-  const cudaError_t e = launch_clustered(k_field_exact<true>, nsims * PIC_FIELD_CTAS, PIC_FIELD_CTAS,
-                                         sizeof(double) * (size_t)seg, st, unused, tab);
-  return e != cudaSuccess ? e : cudaGetLastError();
+  k_field_exact<true><<<nsims * PIC_FIELD_CTAS, PIC_FIELD_TPB, sizeof(double) * (size_t)seg, st>>>(unused, tab);
+  return cudaGetLastError();
 }

@@ -28,7 +28,6 @@
 #define PIC_FIELD_TPB 1024
 #define PIC_FIELD_SEG_MAX 24576  // nodes per CTA of the field cluster (192 KB of shared memory)
 #define PIC_MAX_CELLS_FP32 (PIC_FIELD_CTAS * PIC_FIELD_SEG_MAX - 1)
-#define PIC_FIELD_SMALL 8192  // grids of at most this many nodes are solved by one CTA
 
 // Philox counter word 2: the stream of a draw
 #define CH_INIT 1u
