@@ -171,6 +171,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   __shared__ __int128 cta_q, cta_p;  // read by the other CTAs of the cluster
   cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int TPB = (int)blockDim.x, nw = TPB >> 5;  // a multiple of 32, at most PIC_FIELD_TPB
   const int rank = (int)cluster.block_rank();
   const int N = P.N;
   const int M = N + 1;
@@ -183,7 +184,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   // ---- pass 1 (coalesced): node deposits, net integer charge ------------------------------------
   // |r| bound that keeps the smoothed values (at most 4^(passes + 1) |r|) inside int64
   const __int128 lim = (__int128)0x7FFFFFFFFFFFFFFFll >> (P.smooth ? 2 * P.smooth + 2 : 0);
-  for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+  for (int i = tid; i < len; i += TPB) {
     const int j = a + i;
     const long long R0 = node_R(P, 0, j), R1 = node_R(P, 1, j);
     P.R[0][j] = R0;
@@ -201,7 +202,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   }
   __syncthreads();
 
-  const int items = (len + PIC_FIELD_TPB - 1) / PIC_FIELD_TPB;
+  const int items = (len + TPB - 1) / TPB;
   const int i0 = tid * items;
   if (P.smooth > 0) {
     for (int k = 0; k < items; ++k) {  // t: wall charges doubled
@@ -241,7 +242,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   }
   __syncthreads();
   if (tid < 32) {
-    __int128 vq = warp_q[tid], vp = warp_p[tid];
+    __int128 vq = tid < nw ? warp_q[tid] : (__int128)0, vp = tid < nw ? warp_p[tid] : (__int128)0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const __int128 uq = shfl_up_i128(vq, o), up = shfl_up_i128(vp, o);
@@ -270,7 +271,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
     Ptot += vp;
   }
   // clear the deposit accumulators for the next step (coalesced)
-  for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+  for (int i = tid; i < len; i += TPB) {
     const int j = a + i;
     if (j < N) {
       P.S[0][j] = 0ull;
@@ -302,7 +303,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
     Rn[i] = __double_as_longlong(E);
   }
   __syncthreads();
-  for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+  for (int i = tid; i < len; i += TPB) {
     const int j = a + i;
     const double E = __longlong_as_double(Rn[i]);
     P.E[j] = E;
@@ -344,6 +345,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   __shared__ Pair cta_tot;  // read by the other CTAs of the cluster
   cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x;
+  const int TPB = (int)blockDim.x, nw = TPB >> 5;  // a multiple of 32, at most PIC_FIELD_TPB
   const int rank = (int)cluster.block_rank();
   const int N = P.N;
   const int M = N + 1;
@@ -355,10 +357,10 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   if ((MODE == 0 || MODE == 1) && P.ctl && rank == 0 && tid == 0) bookkeeping(P);
 
   // ---- pass 1 (coalesced): node density -> shared f_j ---------------------------------------
-  const int items = (len + PIC_FIELD_TPB - 1) / PIC_FIELD_TPB;
+  const int items = (len + TPB - 1) / TPB;
   const int i0 = tid * items;
   if (MODE == 3 && P.smooth > 0) {  // diagnostics of a smoothed run: the density the solve used
-    for (int i = tid; i < len; i += PIC_FIELD_TPB) F[i] = node_rho<MODE>(P, a + i);
+    for (int i = tid; i < len; i += TPB) F[i] = node_rho<MODE>(P, a + i);
     __syncthreads();
     smooth_segment<double>(F, len, a, N, seg, i0, items, P.smooth, cluster, rank);
     for (int k = 0; k < items; ++k) {
@@ -369,7 +371,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
       F[i] = (j >= 1 && j <= N - 1) ? dx2 * F[i] : 0.0;
     }
   } else {
-    for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+    for (int i = tid; i < len; i += TPB) {
       const int j = a + i;
       const double r = node_rho<MODE>(P, j);
       if (MODE != 2) P.rho[j] = r;
@@ -392,7 +394,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   if ((tid & 31) == 31) warp_tot[tid >> 5] = incl;
   __syncthreads();
   if (tid < 32) {
-    Pair wi = warp_incl_scan(warp_tot[tid]);
+    Pair wi = warp_incl_scan(tid < nw ? warp_tot[tid] : Pair{0.0, 0.0});
     warp_tot[tid] = wi;  // inclusive over warps
     if (tid == 31) cta_tot = wi;
   }
@@ -420,7 +422,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   }
   // clear the accumulators of the deposit for the next step (coalesced)
   if (MODE == 0) {
-    for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+    for (int i = tid; i < len; i += TPB) {
       const int j = a + i;
       if (j < N) {
         P.S[0][j] = 0ull;
@@ -432,7 +434,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
       }
     }
   } else if (MODE == 1) {
-    for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+    for (int i = tid; i < len; i += TPB) {
       P.acc[0][a + i] = 0.0;
       P.acc[1][a + i] = 0.0;
     }
@@ -466,7 +468,7 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   // ---- pass 3 (coalesced): node field ------------------------------------------------------------
   if (P.E) {
     const double* rho = MODE == 2 ? P.rho_in : P.rho;
-    for (int i = tid; i < len; i += PIC_FIELD_TPB) {
+    for (int i = tid; i < len; i += TPB) {
       const int j = a + i;
       const double pm = j == 0 ? 0.0 : (i > 0 ? F[i - 1] : P.phi[j - 1]);
       const double pp = j == N ? 0.0 : (i + 1 < len ? F[i + 1] : P.phi[j + 1]);
@@ -508,21 +510,30 @@ static void field_attrs() {
   }
 }
 
+// Threads per CTA for a segment of seg nodes: about four nodes per thread (runs of consecutive
+// nodes), a multiple of 32 between 64 and PIC_FIELD_TPB.  Small grids get small CTAs: the scans'
+// FP64 and int128 work grows with the threads, not with the nodes.
+static int field_tpb(int seg) {
+  const int t = ((seg + 3) / 4 + 31) / 32 * 32;
+  return t < 64 ? 64 : (t > PIC_FIELD_TPB ? PIC_FIELD_TPB : t);
+}
+
 cudaError_t launch_field(const PoissonParams& p, cudaStream_t st) {
   if (p.N < 2 || p.N > PIC_MAX_CELLS_FP32) return cudaErrorInvalidValue;
   const int seg = (p.N + 1 + PIC_FIELD_CTAS - 1) / PIC_FIELD_CTAS;
   const size_t smem = sizeof(double) * (size_t)seg;
+  const int tpb = field_tpb(seg);
   field_attrs();
   switch (p.mode) {
     case 0:
       if (p.exact)
-        k_field_exact<false><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p, nullptr);
+        k_field_exact<false><<<PIC_FIELD_CTAS, tpb, smem, st>>>(p, nullptr);
       else
-        k_field_fp64<0><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p);
+        k_field_fp64<0><<<PIC_FIELD_CTAS, tpb, smem, st>>>(p);
       break;
-    case 1: k_field_fp64<1><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
-    case 2: k_field_fp64<2><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
-    case 3: k_field_fp64<3><<<PIC_FIELD_CTAS, PIC_FIELD_TPB, smem, st>>>(p); break;
+    case 1: k_field_fp64<1><<<PIC_FIELD_CTAS, tpb, smem, st>>>(p); break;
+    case 2: k_field_fp64<2><<<PIC_FIELD_CTAS, tpb, smem, st>>>(p); break;
+    case 3: k_field_fp64<3><<<PIC_FIELD_CTAS, tpb, smem, st>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -536,6 +547,6 @@ cudaError_t launch_field_batch(const PoissonParams* tab, int nsims, int maxN, cu
   field_attrs();
   PoissonParams unused;
   memset(&unused, 0, sizeof(unused));
-  k_field_exact<true><<<nsims * PIC_FIELD_CTAS, PIC_FIELD_TPB, sizeof(double) * (size_t)seg, st>>>(unused, tab);
+  k_field_exact<true><<<nsims * PIC_FIELD_CTAS, field_tpb(seg), sizeof(double) * (size_t)seg, st>>>(unused, tab);
   return cudaGetLastError();
 }
