@@ -74,11 +74,23 @@ __device__ __forceinline__ void adj_deposit(unsigned long long* R, int c, float 
 }
 
 // One forward step of every particle (mode 0: record, 1: replay, 2: recompute into the tape).
-__global__ void __launch_bounds__(256) k_adj_push(const AdjStep P) {
+// A CTA takes a contiguous range of particles (in load order, so a few neighbouring cells).  When
+// the grid is small (priv), its deposits go to a copy of both species' node arrays in shared memory
+// and only the nodes it touched are added to global memory: the integer sums are exact in any order,
+// and the same-address global atomics of neighbouring particles disappear.
+__global__ void __launch_bounds__(256) k_adj_push(const AdjStep P, int priv) {
+  extern __shared__ unsigned long long sR[];  // priv: R_0 then R_1 of this CTA, N + 1 nodes each
   double jf = 0.0;  // this thread's J_flux terms
   const long long n = P.step;
-  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < P.np;
-       p += (unsigned long long)gridDim.x * blockDim.x) {
+  const int M = P.N + 1;
+  const bool deposit = P.mode != 2;
+  if (priv && deposit) {
+    for (int j = threadIdx.x; j < 2 * M; j += blockDim.x) sR[j] = 0ull;
+    __syncthreads();
+  }
+  const unsigned long long per = ((P.np + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const unsigned long long p_end = min(P.np, (unsigned long long)(blockIdx.x + 1) * per);
+  for (unsigned long long p = (unsigned long long)blockIdx.x * per + threadIdx.x; p < p_end; p += blockDim.x) {
     const int ab = P.absorb[p];
     if (ab < n) continue;  // absorbed in an earlier step
     const int s = p < P.n0 ? 0 : 1;
@@ -112,7 +124,7 @@ __global__ void __launch_bounds__(256) k_adj_push(const AdjStep P) {
     P.dst.vy[p] = vy;
     P.dst.vz[p] = vz;
     if (!alive || P.mode == 2) continue;
-    adj_deposit(P.R[s], c, f);
+    adj_deposit(priv ? sR + (size_t)s * M : P.R[s], c, f);
     if (s == 0) {
       const double d = (double)(c - (P.N - 1)) + (double)f;
       const double ad = fabs(d);
@@ -120,6 +132,13 @@ __global__ void __launch_bounds__(256) k_adj_push(const AdjStep P) {
     }
   }
   if (P.mode == 2) return;
+  if (priv) {  // the nodes this CTA deposited to
+    __syncthreads();
+    for (int j = threadIdx.x; j < 2 * M; j += blockDim.x) {
+      const unsigned long long v = sR[j];
+      if (v) atomicAdd(P.R[j >= M ? 1 : 0] + (j >= M ? j - M : j), v);
+    }
+  }
   // J_flux: fixed-order warp sum, then an integer 2^-40 fixed-point reduction (order-free)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) jf += __shfl_down_sync(0xFFFFFFFFu, jf, o);
@@ -248,7 +267,10 @@ int grid_for(unsigned long long n, int cap) {
 }  // namespace
 
 cudaError_t launch_adj_push(const AdjStep& p, int max_grid, cudaStream_t st) {
-  k_adj_push<<<grid_for(p.np, max_grid), 256, 0, st>>>(p);
+  // both species' node arrays in shared memory when they fit in 32 KB
+  const size_t smem = 2 * sizeof(unsigned long long) * (size_t)(p.N + 1);
+  const int priv = p.mode != 2 && smem <= 32768 ? 1 : 0;
+  k_adj_push<<<grid_for(p.np, max_grid), 256, priv ? smem : 0, st>>>(p, priv);
   return cudaGetLastError();
 }
 
