@@ -191,13 +191,20 @@ __global__ void __launch_bounds__(1024) k_adj_field_t(const double* __restrict__
   if (tid == 0) *gV += part[0] * (inv_dx / (double)N);
 }
 
-// One backward step of every particle alive after step n.
+// One backward step of every particle alive after step n.  Particles stay near their load order
+// (cell order), so the lanes of a warp form runs of equal cells: the mu contributions are summed
+// over each run by a segmented warp scan and the run's last lane adds them with one atomic pair.
 __global__ void __launch_bounds__(256) k_adj_reverse(const AdjRev P) {
   const long long n = P.step;
   const int N = P.N;
-  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < P.np;
-       p += (unsigned long long)gridDim.x * blockDim.x) {
-    if (P.absorb[p] <= n) continue;  // not alive after step n: nothing depends on its state
+  const int lane = threadIdx.x & 31;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < P.np;
+       base += stride) {
+    const unsigned long long p = base + lane;
+    int key = -1;  // the cell whose two nodes receive this lane's mu contribution (-1: none)
+    double m0 = 0.0, m1 = 0.0;
+    if (p < P.np && P.absorb[p] > n) {  // alive after step n (otherwise nothing depends on its state)
     const int s = p < P.n0 ? 0 : 1;
     double lx = P.lx[p], lvx = P.lvx[p], lvy = P.lvy[p], lvz = P.lvz[p];
     // deposit of x^{n+1}
@@ -226,8 +233,9 @@ __global__ void __launch_bounds__(256) k_adj_reverse(const AdjRev P) {
         const double f0 = (double)P.s0.frac[p];
         const double E0 = (double)(float)P.E[c0], E1 = (double)(float)P.E[c0 + 1];
         lx += eb * (E1 - E0);
-        atomicAdd(P.mu_next + c0, eb * (1.0 - f0));
-        atomicAdd(P.mu_next + c0 + 1, eb * f0);
+        key = c0;
+        m0 = eb * (1.0 - f0);
+        m1 = eb * f0;
       }
       const double ax = M[0] * lvx + M[3] * lvy + M[6] * lvz;
       const double ay = M[1] * lvx + M[4] * lvy + M[7] * lvz;
@@ -240,6 +248,24 @@ __global__ void __launch_bounds__(256) k_adj_reverse(const AdjRev P) {
     P.lvx[p] = lvx;
     P.lvy[p] = lvy;
     P.lvz[p] = lvz;
+    }
+    // mu^n_c += e_bar (1 - f), mu^n_{c+1} += e_bar f: segmented sum over runs of equal cells
+    const int prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+    const unsigned heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || key != prev);
+    const int head = 31 - __clz(heads & (0xFFFFFFFFu >> (31 - lane)));  // first lane of my run
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t0 = __shfl_up_sync(0xFFFFFFFFu, m0, o), t1 = __shfl_up_sync(0xFFFFFFFFu, m1, o);
+      if (lane - o >= head) {
+        m0 += t0;
+        m1 += t1;
+      }
+    }
+    const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (last && key >= 0) {
+      atomicAdd(P.mu_next + key, m0);
+      atomicAdd(P.mu_next + key + 1, m1);
+    }
   }
 }
 
