@@ -249,6 +249,15 @@ void pic_free(pic_handle* h);
 
 const char* pic_strerror(int status);
 
+/* Self-test of the device-side wait limit (failure detection without a fault): launches one
+ * thread that waits on an mbarrier phase which can never complete (two arrivals expected, one
+ * made).  The wait gives up after its limit (about one second of wall time), records it and
+ * returns, leaving the context usable.  Returns PIC_ETIMEOUT when the limit worked as designed (the
+ * wait's duration in *seconds, may be NULL), PIC_ECUDA or PIC_ENOMEM on a runtime failure.  Every
+ * bounded wait of the particle kernels (the TMA stage barriers) uses the same limit and reports
+ * PIC_ETIMEOUT at the next synchronising call. */
+int pic_selftest_timeout(void* cuda_stream, double* seconds);
+
 /* ---- single operations, on caller-owned device buffers ------------------------------------ */
 
 /* Philox4x32-10 (Salmon et al., SC'11; the generator of the MC draws): out[4i..4i+3] =

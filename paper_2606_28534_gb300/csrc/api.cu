@@ -10,6 +10,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "api_internal.h"
 
 namespace picx {
@@ -209,6 +211,7 @@ void derive(pic_handle* h) {
 
 // ---------------------------------------------------------------------------------------------
 void prof_begin(pic_handle* h, int kind, EvPair* e) {
+  nvtxRangePushA(kKindNames[kind]);  // a named range per launch for timeline tools (no tool: a no-op)
   e->kind = kind;
   e->a = e->b = nullptr;
   if (!h->prof) return;
@@ -218,6 +221,7 @@ void prof_begin(pic_handle* h, int kind, EvPair* e) {
 }
 
 void prof_end(pic_handle* h, EvPair* e) {
+  nvtxRangePop();
   if (!h->prof || !e->a) return;
   cudaEventRecord(e->b, h->st);
   h->ev.push_back(*e);
@@ -1352,6 +1356,20 @@ void pic_free(pic_handle* h) {
   prof_harvest(h);
   if (h->owns_ws && h->ws) cudaFree(h->ws);
   delete h;
+}
+
+int pic_selftest_timeout(void* cuda_stream, double* seconds) {
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return PIC_ENOMEM;
+  unsigned long long out[2] = {0ull, 0ull};
+  cudaError_t e = launch_selftest_wait(d, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(out), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return PIC_ECUDA;
+  if (seconds) *seconds = (double)out[1] * 1e-9;
+  return status_of((unsigned)out[0]);
 }
 
 int pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n, void* cuda_stream) {

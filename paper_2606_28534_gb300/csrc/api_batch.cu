@@ -22,6 +22,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "api_internal.h"
 
 using namespace picx;
@@ -275,6 +277,7 @@ int upload_tables(pic_batch* b) {
 }
 
 void bprof_begin(pic_batch* b, int kind, EvPair* e, cudaStream_t st) {
+  nvtxRangePushA(kKindNames[kind]);  // a named range per launch for timeline tools (no tool: a no-op)
   e->kind = kind;
   e->a = e->b = nullptr;
   if (!b->prof) return;
@@ -284,6 +287,7 @@ void bprof_begin(pic_batch* b, int kind, EvPair* e, cudaStream_t st) {
 }
 
 void bprof_end(pic_batch* b, EvPair* e, cudaStream_t st) {
+  nvtxRangePop();
   if (!b->prof || !e->a) return;
   cudaEventRecord(e->b, st);
   b->ev.push_back(*e);

@@ -259,7 +259,27 @@ cudaError_t launch_restore32(const int* cell, const double* frac, const double* 
 
 namespace {
 __global__ void k_store_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+// Self-test of the bounded wait: an mbarrier that expects two arrivals and receives one never
+// completes its phase; the wait gives up after its time limit and the kernel records that.  No copy
+// is in flight and nothing else waits on this barrier.
+__global__ void k_selftest_wait(unsigned long long* out) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 2u);
+  mbar_init_fence();
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  const unsigned long long t0 = global_ns();
+  const bool done = mbar_wait_bounded(&bar, 0u);
+  out[1] = global_ns() - t0;
+  out[0] = done ? 0ull : (unsigned long long)ERR_TIMEOUT;
+}
 }  // namespace
+
+cudaError_t launch_selftest_wait(unsigned long long* out, cudaStream_t st) {
+  k_selftest_wait<<<1, 32, 0, st>>>(out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_store_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) {
   k_store_u64<<<1, 1, 0, st>>>(p, v);

@@ -237,10 +237,21 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0u;
 }
-// Wait for a phase with an iteration cap; false when the cap ran out (the caller reports it).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+#define PIC_WAIT_LIMIT_NS 1000000000ull  // a bounded wait gives up after about one second
+// Wait for a phase for at most PIC_WAIT_LIMIT_NS of wall time (and at most 2^22 polls); false when
+// the limit ran out (the caller reports it).  The first poll usually succeeds and costs no timer read.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-  for (int it = 0; it < (1 << 22); ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int it = 1; it < (1 << 22); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0 && global_ns() - t0 > PIC_WAIT_LIMIT_NS) return false;
+  }
   return false;
 }
 // Order this thread's earlier generic-proxy accesses of shared memory before later async-proxy
@@ -435,6 +446,8 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* ou
                           cudaStream_t st);
 // *p = v, in stream order (v is taken at the call)
 cudaError_t launch_store_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
+// self-test of the bounded wait: out[0] = error bits of a wait that cannot complete, out[1] = its ns
+cudaError_t launch_selftest_wait(unsigned long long* out, cudaStream_t st);
 // tracked neutrals
 // compact: write survivors and new neutrals compacted into p.dst (else p.dst == p.src, in place)
 cudaError_t launch_neutral32(const NeutralParams& p, bool compact, int grid, cudaStream_t st);

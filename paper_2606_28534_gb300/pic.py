@@ -72,7 +72,7 @@ class PicDiag(C.Structure):
 SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapshot", "pic_restore",
            "pic_diag", "pic_get_field", "pic_profile", "pic_kernel_times", "pic_free",
            "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc", "pic_set_diag_interval", "pic_diag_bytes",
-           "pic_neutral_diag", "pic_diag_async", "pic_diag_decode",
+           "pic_neutral_diag", "pic_diag_async", "pic_diag_decode", "pic_selftest_timeout",
            "pic_batch_variant_count", "pic_batch_variant_name", "pic_batch_workspace_size",
            "pic_batch_init", "pic_batch_set_tuning", "pic_batch_set_diag_interval", "pic_batch_get_tuning", "pic_batch_step",
            "pic_batch_sync", "pic_batch_diag", "pic_batch_snapshot", "pic_batch_restore",
@@ -109,6 +109,7 @@ def lib():
         L.pic_neutral_diag.argtypes = [V, P(PicNeutralDiag)]
         L.pic_diag_async.argtypes = [V, V, C.c_uint32]
         L.pic_diag_decode.argtypes = [V, V, P(PicDiag)]
+        L.pic_selftest_timeout.argtypes = [V, P(C.c_double)]
         L.pic_get_field.argtypes = [V, P(C.c_int64), P(C.c_double), P(C.c_double), P(C.c_float),
                                     C.c_size_t]
         L.pic_profile.argtypes = [V, C.c_int]
@@ -301,6 +302,16 @@ class Simulation:
         _check(lib().pic_kernel_times(self._h, ms, ln, names, PIC_KERNEL_KINDS), "pic_kernel_times")
         return {names[k].decode(): {"ms": ms[k], "launches": int(ln[k])}
                 for k in range(PIC_KERNEL_KINDS) if names[k] and names[k].decode()}
+
+
+def selftest_timeout(stream=None) -> tuple:
+    """Make a device-side bounded wait run out on purpose: returns (status, seconds); status
+    PIC_ETIMEOUT (6) means the limit worked and the context stays usable."""
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    sec = C.c_double(0.0)
+    rc = lib().pic_selftest_timeout(C.c_void_p(st.cuda_stream), C.byref(sec))
+    return int(rc), sec.value
 
 
 def batch_variants() -> list:

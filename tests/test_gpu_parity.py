@@ -486,3 +486,16 @@ def test_species_that_empty_out_keep_stepping():
     a, b = snapfmt.parse(g.snapshot()), snapfmt.parse(o.snapshot())
     assert np.array_equal(a["counters"], b["counters"]) and a["wall_charge"] == b["wall_charge"]
     assert all(len(sp["id"]) == 0 for sp in a["species"])
+
+
+def test_a_device_wait_that_cannot_complete_reports_a_timeout_and_the_context_survives():
+    # failure detection without a fault: the bounded wait used by the particle kernels gives up after
+    # its limit (about a second), the host reads PIC_ETIMEOUT, and the GPU keeps working
+    rc, sec = pic.selftest_timeout()
+    assert rc == 6, rc  # PIC_ETIMEOUT
+    assert 0.5 < sec < 5.0, sec
+    g = pic.Simulation(W.SMALL_C2)
+    g.step(3)
+    g.sync()
+    assert g.diag()["step"] == 3
+    g.close()
