@@ -1,7 +1,10 @@
 """Build the CUDA library ``libpicgb.so`` in-tree for sm_103a (GB300).
 
 Each ``csrc/*.cu`` is compiled by nvcc in parallel into ``_build/``, then linked into
-``paper_2606_28534_gb300/libpicgb.so``.  Rebuilds only what changed.
+``paper_2606_28534_gb300/libpicgb.so``.  Rebuilds only what changed.  ``build(checked=True)`` makes
+``libpicgb_checked.so`` (objects in ``_build_checked/``) with -DPIC_CHECKED: the particle kernels
+then validate every stored cell index before using it (an invalid one sets the device error word
+and the particle is treated as dead); load it with the environment variable PIC_LIB.
 """
 from __future__ import annotations
 
@@ -35,19 +38,22 @@ def _headers_mtime() -> float:
     return t
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD + "_checked" if checked else BUILD
+    lib = LIB[:-3] + "_checked.so" if checked else LIB
+    flags = FLAGS + (["-DPIC_CHECKED"] if checked else [])
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
     hdr_t = _headers_mtime()
     jobs = []
     objs = []
     for f in srcs:
         src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f[:-3] + ".o")
+        obj = os.path.join(build_dir, f[:-3] + ".o")
         objs.append(obj)
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_t):
-            jobs.append([nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj])
+            jobs.append([nvcc, *ARCH, *flags, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,12 +65,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if jobs or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
           id[k] = 0ull;
         }
       }
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k) c[k] = checked_cell(c[k], ws.N, &B.sims[kc].ctl->error);
       float2 e2[PIC_PPT];
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) {

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(NT_TPB, PIC_NEUTRAL_MINB) k_neutral32(const __
       const unsigned long long i = i0 + 32ull * r;
       c[r] = PIC_DEAD_CELL;
       if (i < ncur) {
-        c[r] = Q.src.cell[i];
+        c[r] = checked_cell(Q.src.cell[i], N, &g->error);
         f[r] = Q.src.frac[i];
         vx[r] = Q.src.vx[i];
         vy[r] = Q.src.vy[i];

@@ -136,6 +136,8 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
           id[k] = 0ull;
         }
       }
+#pragma unroll
+      for (int k = 0; k < PIC_PPT; ++k) c[k] = checked_cell(c[k], N, &P.ctl->error);
       // field node pairs of the four cells, requested first so that their latency overlaps the
       // Philox work below
       float2 e2[PIC_PPT];

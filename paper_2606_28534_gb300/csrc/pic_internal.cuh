@@ -199,6 +199,22 @@ __device__ __forceinline__ uint4 draw4(unsigned long long id, unsigned long long
                   make_uint2((unsigned)step, (unsigned)seed));
 }
 
+// Checked builds (-DPIC_CHECKED, build.py's checked library): a particle whose stored cell is
+// neither a cell of the grid nor the dead mark is reported (ERR_DEVICE) and treated as dead instead
+// of being used as an index.  Ordinary builds compile the test away.
+#ifdef PIC_CHECKED
+#define PIC_CHECKED_BUILD 1
+#else
+#define PIC_CHECKED_BUILD 0
+#endif
+__device__ __forceinline__ int checked_cell(int c, int N, unsigned int* error) {
+  if (PIC_CHECKED_BUILD && c != PIC_DEAD_CELL && (unsigned)c >= (unsigned)N) {
+    atomicOr(error, ERR_DEVICE);
+    return PIC_DEAD_CELL;
+  }
+  return c;
+}
+
 // 24-bit uniform in [0, 1): exact in FP32 and FP64
 __device__ __forceinline__ float u01f(unsigned w) { return (float)(w >> 8) * 5.9604644775390625e-08f; }
 __device__ __forceinline__ double u01d(unsigned w) { return (double)(w >> 8) * 5.9604644775390625e-08; }

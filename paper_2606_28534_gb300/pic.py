@@ -15,7 +15,8 @@ import numpy as np
 from . import workloads as W
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpicgb.so")
+# PIC_LIB names another build of the library (the checked build, libpicgb_checked.so)
+LIB_PATH = os.environ.get("PIC_LIB") or os.path.join(_HERE, "libpicgb.so")
 _lib = None
 
 PIC_ABI_VERSION = 2
