@@ -8,7 +8,7 @@ full PIC MC step (gather, push, walls, MCC, deposit, source, Poisson, and the so
 step).  Inputs (2.8 GB of particles) are larger than L2, so no flush is needed between steps.
 
 Lines printed (rank 0): one JSON object.  ``--impl reference`` times the plain FP64 CPU oracle
-(the reference of this build) on a bounded sample of the same workload instead.
+(the CPU reference of this library) on a bounded sample of the same workload instead.
 """
 from __future__ import annotations
 
