@@ -100,3 +100,28 @@ def test_energy_balance_of_a_collisionless_plasma_matches_the_oracle_spread():
     assert sum(d["wall_energy"]) > 0
     assert abs(drift) < 0.02
     assert abs(drift - drifts.mean()) <= 4 * drifts.std(ddof=1) + 1e-4, (drift, drifts.mean(), drifts.std(ddof=1))
+
+
+def test_exb_drift():
+    # uniform E along x, B along y: electrons starting at rest drift at E x B / B^2 (Boris keeps the
+    # drift exactly); the time average of v over 40 gyro-periods
+    E, B, dt = 0.05, 0.8, 0.1
+    p = W.variant(W.BASE, ncells=64, L=64.0, ppc=(4, 4), coll_mask=0, field_mode=W.FIELD_EXTERNAL, E_ext=E,
+                  frozen_mask=2, B=B, B_angle_deg=90.0, dt=dt, precision=W.PRECISION_FP32)
+    g = pic.Simulation(p)
+    d = snapfmt.parse(g.snapshot())
+    n = 16
+    ions = d["species"][1]
+    blob = snapfmt.round_to_fp32(snapfmt.with_particles(
+        g.snapshot(), [{"x": np.linspace(28.0, 36.0, n), "v": np.zeros((n, 3)), "id": np.arange(n, dtype=np.uint64)},
+                       {"x": ions["cell"] + ions["frac"], "v": ions["v"], "id": ions["id"]}]))
+    assert g.restore(blob) == 0
+    steps = int(round(40 * 2 * math.pi / (2 * math.atan(B * dt / 2))))
+    acc = np.zeros(3)
+    for _ in range(steps):
+        g.step(1)
+        acc += snapfmt.parse(g.snapshot())["species"][0]["v"].mean(axis=0)
+    mean = acc / steps
+    drift = np.cross([E, 0.0, 0.0], [0.0, B, 0.0]) / (B * B)
+    assert abs(mean[2] - drift[2]) / abs(drift[2]) < 2e-2, (mean, drift)
+    assert np.abs(mean - drift).max() < 2e-3 * np.linalg.norm(drift) + 1e-4 + 2e-2 * abs(drift[2])
