@@ -545,9 +545,12 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
     kernel_shares = {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in kt.values())), 4)
                      for k, v in kt.items() if v["launches"]}
 
+    # the single-GPU sections (plain path, ensemble, adjoint, sheath, precision) run only at N = 1:
+    # with replicas they would repeat the same work on every rank
+    single = world == 1
     # plain FP64 path on the same workload (the baseline the FP32 path is compared with)
     plain = None
-    if not args.no_plain:
+    if single and not args.no_plain:
         sim.close()
         del sim
         torch.cuda.empty_cache()
@@ -613,16 +616,16 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         sim2.close()
 
     batch = None
-    if not args.no_batch:
+    if single and not args.no_batch:
         batch = batched(args, torch, pic, peak)
     adj = None
-    if not args.no_adjoint:
+    if single and not args.no_adjoint:
         adj = adjoint_section(args, torch, pic)
     sheath = None
-    if not args.no_sheath:
+    if single and not args.no_sheath:
         sheath = sheath_section(args, torch, pic, peak)
     precision = None
-    if not args.no_cpu and not args.no_precision:
+    if single and not args.no_cpu and not args.no_precision:
         precision = precision_section(args, torch, pic)
 
     if rank != 0:
