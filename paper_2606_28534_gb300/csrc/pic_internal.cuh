@@ -176,13 +176,15 @@ struct StepParams64 {
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round forms the two
 // 32x32 -> 64-bit products of counter words 0 and 2 with the round multipliers and mixes their
 // halves with words 1, 3 and the key; the key advances by the two Weyl increments between rounds.
+// The high and low halves are separate 32-bit multiplies: a caller that uses only some output
+// words (the null-collision test reads word 0) lets the compiler drop the products of the last
+// two rounds that feed nothing (measured: 2.7% off the particle step against 64-bit products).
 __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
-    unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-    c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ k.x, (unsigned)p1, (unsigned)(p0 >> 32) ^ c.w ^ k.y,
-                   (unsigned)p0);
+    const unsigned h0 = __umulhi(0xD2511F53u, c.x), l0 = 0xD2511F53u * c.x;
+    const unsigned h1 = __umulhi(0xCD9E8D57u, c.z), l1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(h1 ^ c.y ^ k.x, l1, h0 ^ c.w ^ k.y, l0);
     k.x += 0x9E3779B9u;
     k.y += 0xBB67AE85u;
   }
