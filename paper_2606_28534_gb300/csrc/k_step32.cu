@@ -239,12 +239,18 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
           if (c[k] != PIC_DEAD_CELL && !((cand >> k) & 1u)) ke_lane += ke_fx32(vx[k], vy[k], vz[k], K.mass);
       }
       // queue the surviving candidates (their collision changes v only, not the deposit)
+      // (the ordinary step skips the four ballots when no lane of the warp has a candidate)
+      unsigned qmask = 0u;
 #pragma unroll
-      for (int k = 0; k < PIC_PPT; ++k) {
-        const bool qk = ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL;
-        const unsigned b = __ballot_sync(0xFFFFFFFFu, qk);
-        if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(SCATTER ? slot[k] : i0 + k);
-        qn += __popc(b);
+      for (int k = 0; k < PIC_PPT; ++k) qmask |= ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL ? 1u << k : 0u;
+      if (SCATTER || __any_sync(0xFFFFFFFFu, qmask != 0u)) {
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          const bool qk = SCATTER ? ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL : (qmask >> k) & 1u;
+          const unsigned b = __ballot_sync(0xFFFFFFFFu, qk);
+          if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(SCATTER ? slot[k] : i0 + k);
+          qn += __popc(b);
+        }
       }
 
       // ---- deposit: merge equal cells inside the thread, then across the warp -----------------
@@ -256,19 +262,38 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         rn[k] = live ? 1u : 0u;
         rsw[k] = live ? (unsigned long long)wr_of(f[k]) : 0ull;
       }
+      if (!SCATTER) {
+        // runs of equal cells inside the lane (the array is sorted up to the moves since the last
+        // sort), then particle 0 across the warp; particles 1..3 only where a lane still has one
 #pragma unroll
-      for (int k = 0; k < PIC_PPT; ++k) {
-#pragma unroll
-        for (int j = k + 1; j < PIC_PPT; ++j) {
-          if (rn[k] && rn[j] && c[j] == c[k]) {
-            rn[k] += rn[j];
-            rsw[k] += rsw[j];
-            rn[j] = 0u;
+        for (int k = PIC_PPT - 1; k > 0; --k) {
+          if (rn[k] && rn[k - 1] && c[k] == c[k - 1]) {
+            rn[k - 1] += rn[k];
+            rsw[k - 1] += rsw[k];
+            rn[k] = 0u;
           }
         }
-      }
+        warp_deposit(P.cnt[s], P.S[s], rn[0] ? c[0] : -1, rn[0], rsw[0]);
+        if (__any_sync(0xFFFFFFFFu, (rn[1] | rn[2] | rn[3]) != 0u)) {
 #pragma unroll
-      for (int k = 0; k < PIC_PPT; ++k) warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] : -1, rn[k], rsw[k]);
+          for (int k = 1; k < PIC_PPT; ++k) warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] : -1, rn[k], rsw[k]);
+        }
+      } else {
+        // every pair of the lane's particles (the step after a sort measured faster this way)
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+#pragma unroll
+          for (int j = k + 1; j < PIC_PPT; ++j) {
+            if (rn[k] && rn[j] && c[j] == c[k]) {
+              rn[k] += rn[j];
+              rsw[k] += rsw[j];
+              rn[j] = 0u;
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] : -1, rn[k], rsw[k]);
+      }
 
       if (qn > QFLUSH) {
         flush_queue(P, q, qn, nb0, nb1, &bc);
