@@ -36,7 +36,7 @@ BYTES_SCATTER_EXTRA = 8  # the step after a sort writes each particle to a new s
 # DRAM bytes per particle of one launch, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of these kernels on the 12.6M-particle profiling case (c3p), scaled by
 # particles to a full launch: the ordinary step and the step after a sort
-TRAFFIC_STEP, TRAFFIC_SCATTER = 49.09, 57.08
+TRAFFIC_STEP, TRAFFIC_SCATTER = 49.08, 57.14
 # the same for the ensemble's particle step (ncu on a 16-run ensemble of config 4's distribution)
 TRAFFIC_BSTEP = 49.28
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
