@@ -38,14 +38,14 @@ BYTES_SCATTER_EXTRA = 8  # the step after a sort writes each particle to a new s
 # particles to a full launch: the ordinary step and the step after a sort
 TRAFFIC_STEP, TRAFFIC_SCATTER = 49.08, 57.14
 # the same for the ensemble's particle step (ncu on a 16-run ensemble of config 4's distribution)
-TRAFFIC_BSTEP = 49.28
+TRAFFIC_BSTEP = 49.52
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
 # (8 B); on sort steps it writes each survivor, compacted, into the other buffer instead (28 B)
 BYTES_NEUTRAL_KERNEL, BYTES_NEUTRAL_COMPACT = 36, 56
 # DRAM bytes per neutral of one in-place neutral launch, from one ncu capture on the sheath profiling
 # case (c6p), scaled by neutrals to a full launch (writes still dirty in L2 at the launch's end are
 # not counted there)
-TRAFFIC_NEUTRAL = 32.80
+TRAFFIC_NEUTRAL = 32.58
 
 
 def _peaks():
@@ -405,12 +405,16 @@ def sheath_section(args, torch, pic, peak: float) -> dict:
         o = O.OracleSim(sample, threads=cores)
         o.step(1)
         c0, m0 = o.diag()["particle_steps"], o.neutral_diag()["particle_steps"]
+        # steps of the sample until about 3 s of host time have passed
         t0 = time.perf_counter()
-        o.step(3)
+        n = 0
+        while n < 400 and time.perf_counter() - t0 < 3.0:
+            o.step(5)
+            n += 5
         dt = time.perf_counter() - t0
         work = o.diag()["particle_steps"] - c0 + o.neutral_diag()["particle_steps"] - m0
         out["cpu_baseline"] = {"value": work / dt, "unit": "particle-steps/s (charged + neutral)", "cores": cores,
-                               "kind": "oracle", "sample": f"ppc/64 of c6, 3 steps, {dt:.1f} s"}
+                               "kind": "oracle", "sample": f"ppc/64 of c6, {n} steps, {dt:.2f} s"}
     return out
 
 
