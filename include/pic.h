@@ -249,6 +249,13 @@ void pic_free(pic_handle* h);
 
 const char* pic_strerror(int status);
 
+/* CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320, initial and final complement: zlib's
+ * crc32) of n bytes of host memory at p, the checksum that closes a snapshot blob (pic_snapshot,
+ * Sec. 4.1 checkpointing).  Writers of the blob format can use it for the last four bytes.  Pure
+ * host code on the calling thread and up to 64 helper threads; no device or handle is needed.
+ * p may be NULL only when n == 0 (the CRC of no bytes is 0). */
+uint32_t pic_blob_crc32(const void* p, size_t n);
+
 /* Self-test of the device-side wait limit (failure detection without a fault): launches one
  * thread that waits on an mbarrier phase which can never complete (two arrivals expected, one
  * made).  The wait gives up after its limit (about one second of wall time), records it and

@@ -989,6 +989,11 @@ using namespace picx;
 // =============================================================================================
 extern "C" {
 
+uint32_t pic_blob_crc32(const void* p, size_t n) {
+  if (!p || !n) return 0u;
+  return crc32_ieee(static_cast<const unsigned char*>(p), n);
+}
+
 const char* pic_strerror(int status) {
   switch (status) {
     case PIC_OK: return "ok";

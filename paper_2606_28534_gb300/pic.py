@@ -72,7 +72,7 @@ class PicDiag(C.Structure):
 #: every entry point of include/pic.h
 SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapshot", "pic_restore",
            "pic_diag", "pic_get_field", "pic_profile", "pic_kernel_times", "pic_free",
-           "pic_strerror", "pic_philox", "pic_poisson", "pic_field_noalloc", "pic_set_diag_interval", "pic_diag_bytes",
+           "pic_strerror", "pic_blob_crc32", "pic_philox", "pic_poisson", "pic_field_noalloc", "pic_set_diag_interval", "pic_diag_bytes",
            "pic_neutral_diag", "pic_diag_async", "pic_diag_decode", "pic_selftest_timeout",
            "pic_batch_variant_count", "pic_batch_variant_name", "pic_batch_workspace_size",
            "pic_batch_init", "pic_batch_set_tuning", "pic_batch_set_diag_interval", "pic_batch_get_tuning", "pic_batch_step",
@@ -119,6 +119,8 @@ def lib():
         L.pic_free.restype = None
         L.pic_strerror.argtypes = [C.c_int]
         L.pic_strerror.restype = C.c_char_p
+        L.pic_blob_crc32.argtypes = [V, C.c_size_t]
+        L.pic_blob_crc32.restype = C.c_uint32
         L.pic_philox.argtypes = [V, V, V, C.c_size_t, V]
         L.pic_poisson.argtypes = [V, C.c_int32, C.c_double, C.c_double, C.c_double, V, V, V]
         L.pic_field_noalloc.argtypes = [P(PicConfig), V, V, C.c_uint64, V, V, C.c_uint64, V, V, V]
@@ -303,6 +305,17 @@ class Simulation:
         _check(lib().pic_kernel_times(self._h, ms, ln, names, PIC_KERNEL_KINDS), "pic_kernel_times")
         return {names[k].decode(): {"ms": ms[k], "launches": int(ln[k])}
                 for k in range(PIC_KERNEL_KINDS) if names[k] and names[k].decode()}
+
+
+def blob_crc32(data) -> int:
+    """CRC-32 of a bytes-like object as the snapshot format computes it (zlib's crc32)."""
+    if isinstance(data, bytes):  # no copy: the pointer to the bytes object's own buffer
+        return int(lib().pic_blob_crc32(C.cast(C.c_char_p(data), C.c_void_p), len(data)))
+    mv = memoryview(data).cast("B")
+    if len(mv) == 0:
+        return 0
+    buf = (C.c_char * len(mv)).from_buffer_copy(mv) if mv.readonly else (C.c_char * len(mv)).from_buffer(mv)
+    return int(lib().pic_blob_crc32(C.addressof(buf), len(mv)))
 
 
 def selftest_timeout(stream=None) -> tuple:
@@ -547,4 +560,5 @@ def field_noalloc(params: dict, cell0, frac0, cell1, frac1, stream=None):
 
 
 __all__ = ["Simulation", "Batch", "Adjoint", "philox", "poisson", "make_config", "workspace_size",
-           "batch_workspace_size", "batch_variants", "adj_workspace_size", "lib", "PicError", "SYMBOLS", "W"]
+           "batch_workspace_size", "batch_variants", "adj_workspace_size", "blob_crc32", "lib", "PicError", "SYMBOLS",
+           "W"]

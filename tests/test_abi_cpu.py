@@ -166,3 +166,18 @@ def test_adjoint_rejects_the_sheath_physics(L):
         with pytest.raises(pic.PicError) as e:
             pic.adj_workspace_size(W.variant(W.C5, **bad), 20, 5)
         assert e.value.status == 1
+
+
+def test_blob_checksum_is_zlibs_crc32():
+    # the snapshot's closing checksum (pure host code: four interleaved registers per thread, the
+    # threads' parts joined in GF(2)); lengths around the split thresholds and one of 70 MB that
+    # the library spreads over several threads
+    import zlib
+
+    import numpy as np
+
+    rng = np.random.default_rng(11)
+    data = rng.integers(0, 256, size=(70 << 20) + 13, dtype=np.uint8).tobytes()
+    for n in (0, 1, 7, 8, 9, 255, 16383, 16384, 16391, 131079, 1 << 20, (33 << 20) + 5, len(data)):
+        assert pic.blob_crc32(data[:n]) == zlib.crc32(data[:n]), n
+    assert pic.blob_crc32(bytearray(data[:1000])) == zlib.crc32(data[:1000])
