@@ -31,7 +31,7 @@ namespace {
 
 constexpr int NT_TPB = 256;
 #ifndef PIC_NEUTRAL_MINB
-#define PIC_NEUTRAL_MINB 3  // resident CTAs per SM the neutral step is compiled for (80 registers, no spills)
+#define PIC_NEUTRAL_MINB 3  // resident CTAs per SM the neutral step is compiled for (80 registers; the in-place kernel spills 8 bytes)
 #endif
 
 struct NCounters {

@@ -36,7 +36,7 @@ constexpr size_t STEP_SMEM = (size_t)WARPS * (NSTAGE * STAGE_BYTES + QCAP * 8 + 
 // stay contiguous.  A particle absorbed in this step leaves a dead slot; births are appended past
 // the filled buffer's extent (sort_new).  This replaces the separate scatter pass of the sort.
 #ifndef PIC_SCATTER_MINB
-#define PIC_SCATTER_MINB 2  // resident CTAs per SM of the step after a sort (120 registers: no spills)
+#define PIC_SCATTER_MINB 2  // resident CTAs per SM of the step after a sort (under 128 registers: no spills)
 #endif
 
 template <bool SCATTER>
