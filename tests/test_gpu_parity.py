@@ -448,6 +448,31 @@ def test_full_size_sampled_load_and_invariants(name):
     assert d["coll"][4] > 0 and d["coll"][0] > 0
 
 
+
+def test_full_size_long_run_keeps_every_invariant():
+    # the 100M-particle workload over 1000 steps, the bench's timed run (100 sorts, the pair source
+    # balancing the ion losses, ionization births growing each species by about 8 %): charge,
+    # particle accounting and capacity hold at every check, and nothing is dropped
+    p = W.C3
+    g = pic.Simulation(p)
+    n0 = [p["ppc"][s] * p["ncells"] for s in range(2)]
+    cap = [int(p["capacity_factor"] * n) for n in n0]
+    for _ in range(4):
+        g.step(250)
+        d = g.diag()
+        assert d["dropped"] == 0
+        assert d["net_charge_units"] == 2**32 * (d["n"][1] - d["n"][0])
+        assert (d["n"][1] - d["n"][0]) + d["wall_charge"] == n0[1] - n0[0]
+        for s in range(2):
+            lost = d["wall_hits"][s][0] + d["wall_hits"][s][1]
+            assert d["n"][s] == n0[s] + d["births"][s] - lost + d["source_pairs"]
+            assert d["n"][s] <= cap[s]
+        assert all(math.isfinite(x) for x in d["ke"]) and math.isfinite(d["field_energy"])
+    assert d["step"] == 1000
+    # the source has replaced the ions lost at the walls, one pair each
+    assert d["source_pairs"] == d["wall_hits"][1][0] + d["wall_hits"][1][1]
+
+
 # ---- edge cases ---------------------------------------------------------------------------------
 def test_largest_grid_steps_and_matches_the_oracle():
     # the largest grid the FP32 path takes (8 CTAs of the field cluster x 24576 nodes, minus one)

@@ -307,6 +307,32 @@ def test_full_size_sheath_invariants():
     assert 0.3 * p["K_iz"] * p["dt"] < rate < 3.0 * p["K_iz"] * p["dt"]
 
 
+
+def test_full_size_sheath_long_run_keeps_every_invariant():
+    # the 150 M-particle sheath over 400 steps (40 compacting sorts of the neutrals; the two kinds
+    # of ionization grow each charged species by about a tenth, inside its capacity): the neutral
+    # and charged accounting, the charge identity and the capacities hold at every check
+    p = W.C6
+    g = pic.Simulation(p)
+    d0, n0 = g.diag(), g.neutral_diag()
+    ncap = int(p["neutral_capacity"] * max(p["neutral_ppc"], p["ppc"][1]) * p["ncells"])
+    for _ in range(4):
+        g.step(100)
+        d, nd = g.diag(), g.neutral_diag()
+        assert d["dropped"] == 0
+        assert nd["n"] == n0["n"] + sum(nd["recycled"]) - sum(nd["lost"]) - nd["ionized"]
+        assert nd["recycled"] == [d["wall_hits"][1][k] - d0["wall_hits"][1][k] for k in range(2)]
+        assert 0 < nd["n"] <= ncap
+        for s in range(2):
+            lost = sum(d["wall_hits"][s]) - sum(d0["wall_hits"][s])
+            born = d["births"][s] - d0["births"][s] + nd["ionized"] + (d["source_pairs"] - d0["source_pairs"])
+            assert d["n"][s] == d0["n"][s] + born - lost
+            assert d["n"][s] <= int(p["capacity_factor"] * p["ppc"][s] * p["ncells"])
+        assert d["net_charge_units"] == 2**32 * (d["n"][1] - d["n"][0])
+        assert math.isfinite(nd["ke"]) and math.isfinite(d["field_energy"])
+    assert d["step"] == 400
+
+
 def test_batch_and_adjoint_refuse_the_sheath_physics():
     with pytest.raises(pic.PicError):
         pic.Batch([W.SMALL_C6])
