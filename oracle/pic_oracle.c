@@ -717,6 +717,24 @@ static int ionize_neutral(const orc_sim* s, uint64_t id, uint64_t step, double x
 
 /* ------------------------------------------------------------------------------------------ */
 /* One full step (R2).                                                                         */
+/* The mover stages of one particle under the node field E: CIC gather (Sec. 2 "interpolating
+ * fields back"), Boris push and position update (Sec. 2 "particle mover").  xh is the position in
+ * cells. */
+static void move_particle(const orc_config* c, double qm, const double Bv[3], double dx, const double* E,
+                          double* xh, double v[3]) {
+  double Ex = 0.0;
+  if (c->field_mode == ORC_FIELD_SELF) {
+    int32_t cc = (int32_t)floor(*xh);
+    double f = *xh - (double)cc;
+    Ex = (1.0 - f) * E[cc] + f * E[cc + 1];
+  } else if (c->field_mode == ORC_FIELD_EXTERNAL) {
+    Ex = c->E_ext;
+  }
+  double Ev[3] = {Ex, 0.0, 0.0};
+  orc_boris(qm, c->dt, Ev, Bv, v);
+  *xh += v[0] * c->dt / dx;
+}
+
 static int step_once(orc_sim* s) {
   const orc_config* c = &s->cfg;
   const int32_t N = s->N;
@@ -757,20 +775,8 @@ static int step_once(orc_sim* s) {
 #endif
       orc_tcount* tc = &tcs[sp][t];
       double xh = p->x[i];
-      /* gather: CIC interpolation of the node field (Sec. 2 "interpolating fields back") */
-      double Ex = 0.0;
-      if (c->field_mode == ORC_FIELD_SELF) {
-        int32_t cc = (int32_t)floor(xh);
-        double f = xh - (double)cc;
-        Ex = (1.0 - f) * s->E[cc] + f * s->E[cc + 1];
-      } else if (c->field_mode == ORC_FIELD_EXTERNAL) {
-        Ex = c->E_ext;
-      }
-      /* push (Sec. 2 "particle mover") */
-      double Ev[3] = {Ex, 0.0, 0.0};
       double v[3] = {p->vx[i], p->vy[i], p->vz[i]};
-      orc_boris(s->qm[sp], c->dt, Ev, s->Bv, v);
-      xh += v[0] * c->dt / s->dx;
+      move_particle(c, s->qm[sp], s->Bv, s->dx, s->E, &xh, v);
       /* walls (Table 3: plasma absorbed at the walls) */
       if (xh < 0.0 || xh >= (double)N) {
         const int side = xh < 0.0 ? 0 : 1;
@@ -976,6 +982,53 @@ int orc_step(orc_sim* s, int32_t nsteps) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* One step of n given particles of species sp under a given node field E (N + 1 values): the
+ * mover, the wall test and the null-collision MC of orc_step, for parity checks that sample a state
+ * too large for the whole oracle step.  Positions in cells, velocities as (vx, vy, vz) triples.
+ * flags[k]: 1 absorbed at a wall, 2 collision candidate, 4 near-threshold draw, 8 ionization (the
+ * new pair itself is not returned).  Tracked neutrals and the pair source are not part of it. */
+int orc_step_sample(const orc_config* cfg, int sp, uint64_t step, const double* E, size_t n, const double* x,
+                    const double* v, const uint64_t* id, double* xo, double* vo, int32_t* flags) {
+  if (!cfg || !valid_config(cfg) || sp < 0 || sp > 1 || (n && (!x || !v || !id || !xo || !vo || !flags)))
+    return ORC_EINVAL;
+  if (cfg->field_mode == ORC_FIELD_SELF && !E) return ORC_EINVAL;
+  orc_sim t;
+  memset(&t, 0, sizeof(t));
+  t.cfg = *cfg;
+  derive(&t);
+  const int moves = !(cfg->frozen_mask & (1u << sp));
+  const int do_mcc = (sp == 0) ? ((cfg->coll_mask & (ORC_COLL_EL | ORC_COLL_EX | ORC_COLL_IZ)) != 0)
+                               : ((cfg->coll_mask & ORC_COLL_CX) != 0);
+  for (size_t k = 0; k < n; ++k) {
+    double xh = x[k];
+    double vv[3] = {v[3 * k], v[3 * k + 1], v[3 * k + 2]};
+    int32_t fl = 0;
+    if (moves) {
+      move_particle(cfg, t.qm[sp], t.Bv, t.dx, E, &xh, vv);
+      if (xh < 0.0 || xh >= (double)t.N) {
+        fl |= 1;
+      } else if (do_mcc) {
+        orc_tcount tc;
+        memset(&tc, 0, sizeof(tc));
+        if (sp == 0) {
+          orc_newp a, b;
+          if (collide_electron(&t, id[k], step, xh, vv, &tc, &a, &b)) fl |= 8;
+        } else {
+          collide_ion(&t, id[k], step, vv, &tc);
+        }
+        if (tc.coll[4]) fl |= 2;
+        if (tc.near) fl |= 4;
+      }
+    }
+    xo[k] = xh;
+    vo[3 * k] = vv[0];
+    vo[3 * k + 1] = vv[1];
+    vo[3 * k + 2] = vv[2];
+    flags[k] = fl;
+  }
+  return ORC_OK;
+}
+
 static int cmp_double(const void* a, const void* b) {
   double x = *(const double*)a, y = *(const double*)b;
   return (x > y) - (x < y);

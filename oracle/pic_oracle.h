@@ -159,6 +159,12 @@ void orc_load_particle(const orc_config* cfg, int sp, uint64_t i, double* x, dou
 orc_sim* orc_create(const orc_config* cfg, int* err);
 void orc_free(orc_sim* s);
 int orc_step(orc_sim* s, int32_t nsteps);
+/* One step of n given particles of species sp under the node field E (N + 1 values): mover, wall
+ * test and null-collision MC exactly as orc_step, for parity checks that sample a large state.
+ * x in cells, v as n (vx, vy, vz) triples; flags: 1 absorbed, 2 candidate, 4 near-threshold draw,
+ * 8 ionization.  Neutrals and the pair source are not included. */
+int orc_step_sample(const orc_config* cfg, int sp, uint64_t step, const double* E, size_t n, const double* x,
+                    const double* v, const uint64_t* id, double* xo, double* vo, int32_t* flags);
 int orc_diag(orc_sim* s, orc_diag_t* out);
 /* R: 2 x (N+1) int64 fixed-point deposits, rho/phi/E: N+1 nodes each; any may be NULL. */
 int orc_fields(orc_sim* s, int64_t* R, double* rho, double* phi, double* E);

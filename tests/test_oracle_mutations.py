@@ -38,8 +38,8 @@ MUTATIONS = [
      "R[c] += Wr;\n      R[c + 1] += Wl;", PINS_MAIN),
     ("wall half-cell volume dropped", "pic_oracle.c",
      "double vol = (j == 0 || j == N) ? 0.5 * s->dx : s->dx;", "double vol = s->dx;", PINS_MAIN),
-    ("gather weights swapped", "pic_oracle.c", "Ex = (1.0 - f) * s->E[cc] + f * s->E[cc + 1];",
-     "Ex = f * s->E[cc] + (1.0 - f) * s->E[cc + 1];", PINS_MAIN),
+    ("gather weights swapped", "pic_oracle.c", "Ex = (1.0 - f) * E[cc] + f * E[cc + 1];",
+     "Ex = f * E[cc] + (1.0 - f) * E[cc + 1];", PINS_MAIN),
     ("elastic angle term dropped", "pic_oracle.c", "sqrt(1.0 - 2.0 * m / c->m_gas * (1.0 - cchi))",
      "sqrt(1.0 - 2.0 * m / c->m_gas)", PINS_MAIN),
     ("excitation loss dropped", "pic_oracle.c", "double sp2 = sqrt(2.0 * (En - c->E_ex) / m);",

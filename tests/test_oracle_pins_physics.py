@@ -370,3 +370,52 @@ def test_restore_rejects_corrupt_or_foreign_blobs():
     b = _sim(W.variant(p, seed=p["seed"] + 1))
     assert b.restore(a.snapshot()) == 5
     assert a.restore(a.snapshot()[:-9]) == 5
+
+
+def test_step_sample_is_the_step_one_particle_at_a_time():
+    # orc_step_sample (the oracle step of given particles under a given field, for checks that
+    # sample a large state) against the whole oracle step from the same state: survivors bit for
+    # bit, the absorbed set, and the candidate, near-threshold and ionization counts
+    p = W.variant(W.SMALL_COLL, B=0.5, B_angle_deg=30.0, V_left=-2.0)
+    o = O.OracleSim(p)
+    o.step(3)
+    d0, E = o.diag(), o.fields()["E"]
+    before = [o.particles(s) for s in range(2)]
+    out = [O.step_sample(p, s, d0["step"], E, *before[s]) for s in range(2)]
+    o.step(1)
+    d1 = o.diag()
+    for s in range(2):
+        x0, v0, id0 = before[s]
+        xs, vs, fl = out[s]
+        x1, v1, id1 = o.particles(s)
+        absorbed = (fl & 1) != 0
+        assert int(absorbed.sum()) == sum(d1["wall_hits"][s]) - sum(d0["wall_hits"][s])
+        # every survivor, matched by id (births carry new ids; a sort may reorder)
+        keep = ~absorbed
+        o1 = np.argsort(id1)
+        pos = np.searchsorted(id1, id0[keep], sorter=o1)
+        j = o1[np.minimum(pos, len(id1) - 1)]
+        assert np.array_equal(id1[j], id0[keep])
+        assert np.array_equal(x1[j], xs[keep])
+        assert np.array_equal(v1[j], vs[keep])
+        assert not np.isin(id0[absorbed], id1).any()
+    assert sum(int(((f & 2) != 0).sum()) for _, _, f in out) == d1["coll"][4] - d0["coll"][4]
+    assert sum(int(((f & 4) != 0).sum()) for _, _, f in out) == sum(d1["near_threshold"]) - sum(d0["near_threshold"])
+    assert int(((out[0][2] & 8) != 0).sum()) == d1["births"][0] - d0["births"][0] > 0
+
+
+def test_step_sample_uniform_field_is_uniform_acceleration():
+    # B = 0, external uniform E, no collisions: v' = v + (q/m) E dt and x' = x + v' dt / dx
+    p = W.variant(W.SMALL_C1, field_mode=W.FIELD_EXTERNAL, E_ext=0.3, B=0.0, coll_mask=0)
+    rng = np.random.default_rng(5)
+    n = 200
+    x = rng.uniform(5.0, p["ncells"] - 5.0, n)
+    v = rng.normal(size=(n, 3)) * 0.1
+    for s in range(2):
+        xo, vo, fl = O.step_sample(p, s, 0, np.zeros(p["ncells"] + 1), x, v, np.arange(n, dtype=np.uint64))
+        a = p["charge"][s] / p["mass"][s] * p["E_ext"] * p["dt"]
+        dx = p["L"] / p["ncells"]
+        assert np.all(fl == 0)
+        assert np.allclose(vo[:, 0], v[:, 0] + a, rtol=0, atol=1e-14)
+        assert np.array_equal(vo[:, 1:], v[:, 1:])
+        assert np.allclose(xo, x + vo[:, 0] * p["dt"] / dx, rtol=0, atol=1e-12)
