@@ -663,65 +663,146 @@ struct HostParticles {
   std::vector<uint64_t> id;
 };
 
+// fn(lo, hi) over [0, n) split into contiguous ranges, one per host thread (sized by the bytes
+// the pass touches).
+template <class F>
+void host_parallel(size_t n, size_t bytes_per_item, F fn) {
+  const int T = host_threads(n * bytes_per_item);
+  if (T <= 1) {
+    fn((size_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  const size_t chunk = (n + T - 1) / T;
+  for (int k = 0; k < T; ++k) {
+    const size_t lo = std::min(n, (size_t)k * chunk), hi = std::min(n, lo + chunk);
+    th.emplace_back([lo, hi, &fn]() { fn(lo, hi); });
+  }
+  for (auto& t : th) t.join();
+}
+
+struct IdIdx {
+  uint64_t id, i;
+};
+
+// The live entries (cell != PIC_DEAD_CELL) of n as (id, index) pairs in ascending id order.  Ids
+// are unique, so the order is unique: each host thread collects and sorts the pairs of its range,
+// then neighbouring sorted runs are merged in parallel rounds.
+std::vector<IdIdx> live_by_id(const int32_t* cell, const uint64_t* id, size_t n) {
+  const int T = std::max(1, host_threads(12 * n));
+  const size_t chunk = (n + T - 1) / T;
+  std::vector<size_t> cnt(T + 1, 0);
+  {
+    std::vector<std::thread> th;
+    for (int k = 0; k < T; ++k)
+      th.emplace_back([&, k]() {
+        const size_t lo = std::min(n, (size_t)k * chunk), hi = std::min(n, lo + chunk);
+        size_t c = 0;
+        for (size_t i = lo; i < hi; ++i) c += cell[i] != PIC_DEAD_CELL;
+        cnt[k + 1] = c;
+      });
+    for (auto& t : th) t.join();
+  }
+  for (int k = 0; k < T; ++k) cnt[k + 1] += cnt[k];
+  std::vector<IdIdx> a(cnt[T]), b;
+  const auto by_id = [](const IdIdx& x, const IdIdx& y) { return x.id < y.id; };
+  {
+    std::vector<std::thread> th;
+    for (int k = 0; k < T; ++k)
+      th.emplace_back([&, k]() {
+        const size_t lo = std::min(n, (size_t)k * chunk), hi = std::min(n, lo + chunk);
+        size_t o = cnt[k];
+        for (size_t i = lo; i < hi; ++i)
+          if (cell[i] != PIC_DEAD_CELL) a[o++] = IdIdx{id[i], (uint64_t)i};
+        std::sort(a.begin() + (std::ptrdiff_t)cnt[k], a.begin() + (std::ptrdiff_t)cnt[k + 1], by_id);
+      });
+    for (auto& t : th) t.join();
+  }
+  std::vector<size_t> run(cnt.begin(), cnt.end());  // run r is [run[r], run[r + 1])
+  if (run.size() > 2) b.resize(a.size());
+  while (run.size() > 2) {
+    std::vector<size_t> next;
+    std::vector<std::thread> th;
+    for (size_t r = 0; r + 1 < run.size(); r += 2) {
+      next.push_back(run[r]);
+      const size_t lo = run[r], mid = run[r + 1], hi = r + 2 < run.size() ? run[r + 2] : run[r + 1];
+      th.emplace_back([&, lo, mid, hi]() {
+        std::merge(a.begin() + (std::ptrdiff_t)lo, a.begin() + (std::ptrdiff_t)mid, a.begin() + (std::ptrdiff_t)mid,
+                   a.begin() + (std::ptrdiff_t)hi, b.begin() + (std::ptrdiff_t)lo, by_id);
+      });
+    }
+    next.push_back(run.back());
+    for (auto& t : th) t.join();
+    a.swap(b);
+    run.swap(next);
+  }
+  return a;
+}
+
+// Gathers the live particles of one species in ascending id order (cell, fraction, v as read).
+template <class Frac, class Vel>
+void gather_by_id(const std::vector<IdIdx>& live, const int32_t* cell, const Frac* frac, const Vel* vx,
+                  const Vel* vy, const Vel* vz, HostParticles& o) {
+  const size_t m = live.size();
+  o.cell.resize(m);
+  o.frac.resize(m);
+  o.vx.resize(m);
+  o.vy.resize(m);
+  o.vz.resize(m);
+  o.id.resize(m);
+  host_parallel(m, 64, [&](size_t lo, size_t hi) {
+    for (size_t k = lo; k < hi; ++k) {
+      const size_t i = (size_t)live[k].i;
+      o.cell[k] = cell[i];
+      o.frac[k] = (double)frac[i];
+      o.vx[k] = (double)vx[i];
+      o.vy[k] = (double)vy[i];
+      o.vz[k] = (double)vz[i];
+      o.id[k] = live[k].id;
+    }
+  });
+}
+
 int fetch_particles(pic_handle* h, HostParticles out[2], Ctl* ctl) {
   CK(cudaStreamSynchronize(h->st));
   CK(cudaMemcpy(ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
   for (int s = 0; s < 2; ++s) {
     const size_t n = (size_t)ctl->n_cur[s];
-    HostParticles& o = out[s];
     std::vector<uint64_t> id(n);
-    std::vector<double> vx(n), vy(n), vz(n), x(n);
     std::vector<int32_t> cell(n);
-    std::vector<float> f32(n);
     if (!h->plain) {
       const Species32& a = h->a32[h->cur][s];
+      std::vector<float> f(n), vx(n), vy(n), vz(n);
       CK(cudaMemcpy(cell.data(), a.cell, n * 4, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(f32.data(), a.frac, n * 4, cudaMemcpyDeviceToHost));
-      for (size_t i = 0; i < n; ++i) x[i] = f32[i];
-      CK(cudaMemcpy(f32.data(), a.vx, n * 4, cudaMemcpyDeviceToHost));
-      for (size_t i = 0; i < n; ++i) vx[i] = f32[i];
-      CK(cudaMemcpy(f32.data(), a.vy, n * 4, cudaMemcpyDeviceToHost));
-      for (size_t i = 0; i < n; ++i) vy[i] = f32[i];
-      CK(cudaMemcpy(f32.data(), a.vz, n * 4, cudaMemcpyDeviceToHost));
-      for (size_t i = 0; i < n; ++i) vz[i] = f32[i];
+      CK(cudaMemcpy(f.data(), a.frac, n * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(vx.data(), a.vx, n * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(vy.data(), a.vy, n * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(vz.data(), a.vz, n * 4, cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(id.data(), a.id, n * 8, cudaMemcpyDeviceToHost));
+      gather_by_id(live_by_id(cell.data(), id.data(), n), cell.data(), f.data(), vx.data(), vy.data(), vz.data(),
+                   out[s]);
     } else {
       const Species64& a = h->a64[s];
+      std::vector<double> x(n), vx(n), vy(n), vz(n);
       CK(cudaMemcpy(x.data(), a.x, n * 8, cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(vx.data(), a.vx, n * 8, cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(vy.data(), a.vy, n * 8, cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(vz.data(), a.vz, n * 8, cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(id.data(), a.id, n * 8, cudaMemcpyDeviceToHost));
-      for (size_t i = 0; i < n; ++i) {
-        if (x[i] < 0.0) {
-          cell[i] = PIC_DEAD_CELL;
-          continue;
+      // absolute x -> (cell, fraction); absorbed particles carry x < 0
+      host_parallel(n, 12, [&](size_t lo, size_t hi) {
+        for (size_t i = lo; i < hi; ++i) {
+          if (x[i] < 0.0) {
+            cell[i] = PIC_DEAD_CELL;
+            continue;
+          }
+          const double c = std::floor(x[i]);
+          cell[i] = (int32_t)c;
+          x[i] = x[i] - c;
         }
-        double c = std::floor(x[i]);
-        cell[i] = (int32_t)c;
-        x[i] = x[i] - c;
-      }
-    }
-    std::vector<size_t> live;
-    live.reserve(n);
-    for (size_t i = 0; i < n; ++i)
-      if (cell[i] != PIC_DEAD_CELL) live.push_back(i);
-    std::sort(live.begin(), live.end(), [&](size_t a, size_t b) { return id[a] < id[b]; });
-    const size_t m = live.size();
-    o.cell.resize(m);
-    o.frac.resize(m);
-    o.vx.resize(m);
-    o.vy.resize(m);
-    o.vz.resize(m);
-    o.id.resize(m);
-    for (size_t k = 0; k < m; ++k) {
-      const size_t i = live[k];
-      o.cell[k] = cell[i];
-      o.frac[k] = x[i];
-      o.vx[k] = vx[i];
-      o.vy[k] = vy[i];
-      o.vz[k] = vz[i];
-      o.id[k] = id[i];
+      });
+      gather_by_id(live_by_id(cell.data(), id.data(), n), cell.data(), x.data(), vx.data(), vy.data(), vz.data(),
+                   out[s]);
     }
   }
   return PIC_OK;
@@ -739,27 +820,7 @@ int fetch_neutrals(pic_handle* h, const Species32& a, size_t n, HostParticles& o
   CK(cudaMemcpy(vz.data(), a.vz, n * 4, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(id.data(), a.id, n * 8, cudaMemcpyDeviceToHost));
   (void)h;
-  std::vector<size_t> live;
-  live.reserve(n);
-  for (size_t i = 0; i < n; ++i)
-    if (cell[i] != PIC_DEAD_CELL) live.push_back(i);
-  std::sort(live.begin(), live.end(), [&](size_t x, size_t y) { return id[x] < id[y]; });
-  const size_t m = live.size();
-  o.cell.resize(m);
-  o.frac.resize(m);
-  o.vx.resize(m);
-  o.vy.resize(m);
-  o.vz.resize(m);
-  o.id.resize(m);
-  for (size_t k = 0; k < m; ++k) {
-    const size_t i = live[k];
-    o.cell[k] = cell[i];
-    o.frac[k] = f[i];
-    o.vx[k] = vx[i];
-    o.vy[k] = vy[i];
-    o.vz[k] = vz[i];
-    o.id[k] = id[i];
-  }
+  gather_by_id(live_by_id(cell.data(), id.data(), n), cell.data(), f.data(), vx.data(), vy.data(), vz.data(), o);
   return PIC_OK;
 }
 
@@ -1288,62 +1349,82 @@ int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
   if (!h) return PIC_EINVAL;
   int rc = check_errors(h);
   if (rc != PIC_OK && rc != PIC_EOVERFLOW) return rc;
-  HostParticles P[2], NT;
+  // the size from the exact live counts of the control block (a size query moves no particles)
   Ctl c;
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const size_t need = kHdr + 4 + 44 * (size_t)(c.n_live[0] + c.n_live[1]) +
+                      (h->cap_nt ? kNtHdr + 44 * (size_t)c.nt_live : 0);
+  if (needed) *needed = need;
+  if (!buf) return PIC_OK;
+  if (cap < need) return PIC_EINVAL;
+  HostParticles P[2], NT;
   rc = fetch_particles(h, P, &c);
   if (rc != PIC_OK) return rc;
   if (h->cap_nt) {
     rc = fetch_neutrals(h, h->nt[h->nt_buf], (size_t)c.nt_cur, NT);
     if (rc != PIC_OK) return rc;
   }
-  const size_t need = kHdr + 4 + 44 * (P[0].id.size() + P[1].id.size()) +
-                      (h->cap_nt ? kNtHdr + 44 * NT.id.size() : 0);
-  if (needed) *needed = need;
-  if (!buf) return PIC_OK;
-  if (cap < need) return PIC_EINVAL;
-  std::vector<unsigned char> b;
-  b.reserve(need);
-  b.insert(b.end(), "PICMCSN1", "PICMCSN1" + 8);
-  put(b, (uint32_t)(h->cap_nt ? 2 : 1));
-  put(b, (uint32_t)0);
-  put(b, config_hash(h->cfg));
-  put(b, (uint64_t)h->step);
-  put(b, (uint64_t)P[0].id.size());
-  put(b, (uint64_t)P[1].id.size());
+  // the live entries found in the arrays must be the counted ones
+  if (P[0].id.size() != c.n_live[0] || P[1].id.size() != c.n_live[1] || (h->cap_nt && NT.id.size() != c.nt_live))
+    return PIC_EDEVICE;
+  // header, then each array copied straight into the caller's buffer (host threads for the
+  // large ones), then the CRC of everything before it
+  unsigned char* const out = static_cast<unsigned char*>(buf);
+  size_t at = 0;
+  const auto put_raw = [&](const void* src, size_t bytes) {
+    if (bytes >= (size_t)(64u << 20)) {
+      const unsigned char* p = static_cast<const unsigned char*>(src);
+      unsigned char* d = out + at;
+      host_parallel(bytes, 2, [&](size_t lo, size_t hi) { std::memcpy(d + lo, p + lo, hi - lo); });
+    } else if (bytes) {
+      std::memcpy(out + at, src, bytes);
+    }
+    at += bytes;
+  };
+  const auto put_u64 = [&](uint64_t v) { put_raw(&v, 8); };
+  put_raw("PICMCSN1", 8);
+  const uint32_t ver[2] = {(uint32_t)(h->cap_nt ? 2 : 1), 0u};
+  put_raw(ver, 8);
+  put_u64(config_hash(h->cfg));
+  put_u64((uint64_t)h->step);
+  put_u64((uint64_t)P[0].id.size());
+  put_u64((uint64_t)P[1].id.size());
   for (int s = 0; s < 2; ++s)
-    for (int k = 0; k < 2; ++k) put(b, (uint64_t)c.wall_hits[s][k]);
-  for (int k = 0; k < 5; ++k) put(b, (uint64_t)c.coll[k]);
-  for (int s = 0; s < 2; ++s) put(b, (uint64_t)c.near_thr[s]);
-  for (int s = 0; s < 2; ++s) put(b, (uint64_t)c.viol[s]);
-  for (int s = 0; s < 2; ++s) put(b, (uint64_t)c.births[s]);
-  put(b, (uint64_t)c.source_pairs);
-  put(b, (uint64_t)c.dropped);
-  put(b, (int64_t)c.wall_charge);
+    for (int k = 0; k < 2; ++k) put_u64((uint64_t)c.wall_hits[s][k]);
+  for (int k = 0; k < 5; ++k) put_u64((uint64_t)c.coll[k]);
+  for (int s = 0; s < 2; ++s) put_u64((uint64_t)c.near_thr[s]);
+  for (int s = 0; s < 2; ++s) put_u64((uint64_t)c.viol[s]);
+  for (int s = 0; s < 2; ++s) put_u64((uint64_t)c.births[s]);
+  put_u64((uint64_t)c.source_pairs);
+  put_u64((uint64_t)c.dropped);
+  const int64_t wall_charge = (int64_t)c.wall_charge;
+  put_raw(&wall_charge, 8);
   const double dx = h->cfg.L / h->N;
-  for (int s = 0; s < 2; ++s) put(b, (double)c.wall_energy_fx[s] * (1.0 / 16777216.0) * (dx / h->cfg.ppc[s]));
   for (int s = 0; s < 2; ++s) {
-    put_arr(b, P[s].cell);
-    put_arr(b, P[s].frac);
-    put_arr(b, P[s].vx);
-    put_arr(b, P[s].vy);
-    put_arr(b, P[s].vz);
-    put_arr(b, P[s].id);
+    const double e = (double)c.wall_energy_fx[s] * (1.0 / 16777216.0) * (dx / h->cfg.ppc[s]);
+    put_raw(&e, 8);
   }
+  const auto put_species = [&](const HostParticles& q) {
+    put_raw(q.cell.data(), 4 * q.cell.size());
+    put_raw(q.frac.data(), 8 * q.frac.size());
+    put_raw(q.vx.data(), 8 * q.vx.size());
+    put_raw(q.vy.data(), 8 * q.vy.size());
+    put_raw(q.vz.data(), 8 * q.vz.size());
+    put_raw(q.id.data(), 8 * q.id.size());
+  };
+  for (int s = 0; s < 2; ++s) put_species(P[s]);
   if (h->cap_nt) {
-    put(b, (uint64_t)NT.id.size());
-    for (int k = 0; k < 2; ++k) put(b, (uint64_t)c.nt_recycled[k]);
-    for (int k = 0; k < 2; ++k) put(b, (uint64_t)c.nt_lost[k]);
-    put(b, (uint64_t)c.nt_ionized);
-    put(b, (uint64_t)c.nt_near);
-    put_arr(b, NT.cell);
-    put_arr(b, NT.frac);
-    put_arr(b, NT.vx);
-    put_arr(b, NT.vy);
-    put_arr(b, NT.vz);
-    put_arr(b, NT.id);
+    put_u64((uint64_t)NT.id.size());
+    for (int k = 0; k < 2; ++k) put_u64((uint64_t)c.nt_recycled[k]);
+    for (int k = 0; k < 2; ++k) put_u64((uint64_t)c.nt_lost[k]);
+    put_u64((uint64_t)c.nt_ionized);
+    put_u64((uint64_t)c.nt_near);
+    put_species(NT);
   }
-  put(b, crc32_ieee(b.data(), b.size()));
-  std::memcpy(buf, b.data(), b.size());
+  if (at + 4 != need) return PIC_EDEVICE;
+  const uint32_t crc = crc32_ieee(out, at);
+  put_raw(&crc, 4);
   return PIC_OK;
 }
 

@@ -13,6 +13,7 @@ Tolerances:
   (plus the FP32 input rounding where the charge came from an FP32 step).
 """
 import math
+import struct
 
 import numpy as np
 import pytest
@@ -447,6 +448,64 @@ def test_full_size_sampled_load_and_invariants(name):
         assert d["n"][s] == n0[s] + d["births"][s] - lost + d["source_pairs"]
     assert d["coll"][4] > 0 and d["coll"][0] > 0
 
+
+
+
+def _species_views(blob: bytes) -> list:
+    """(cell, frac, v columns, id) of each charged species of a snapshot, as views into the blob."""
+    n = struct.unpack_from("<QQ", blob, 32)
+    off, out = snapfmt.HDR, []
+    for m in n:
+        cell = np.frombuffer(blob, np.int32, m, off)
+        frac = np.frombuffer(blob, np.float64, m, off + 4 * m)
+        v = [np.frombuffer(blob, np.float64, m, off + 12 * m + 8 * m * k) for k in range(3)]
+        ids = np.frombuffer(blob, np.uint64, m, off + 36 * m)
+        out.append((cell, frac, v, ids))
+        off += 44 * m
+    return out
+
+
+def test_full_size_sampled_step_matches_the_oracle_one_by_one():
+    # config 3 at full size (1e8 particles) in the bench's launch configuration: 2000 particles of
+    # each species, stepped one by one by the oracle (orc_step_sample: mover, walls, null-collision
+    # MC) under the GPU's own node field, against the GPU's step of the whole state; the tolerances
+    # of the single-step parity, absorption exact away from the walls, near-threshold draws counted
+    p = W.C3
+    g = pic.Simulation(p)
+    g.step(3)  # the step that follows is an ordinary one (sorts run at multiples of 10)
+    step = g.diag()["step"]
+    E = g.fields()["E"].astype(np.float64)
+    before = _species_views(g.snapshot())
+    g.step(1)
+    after = _species_views(g.snapshot())
+    rng = np.random.default_rng(17)
+    N = p["ncells"]
+    for s in range(2):
+        cell, frac, v, ids = before[s]
+        # 2000 anywhere, and up to 300 in the wall cells, where particles leave
+        edge = np.flatnonzero((cell == 0) | (cell == N - 1))
+        idx = np.union1d(rng.choice(len(ids), 2000, replace=False),
+                         rng.choice(edge, min(300, edge.size), replace=False))
+        x0 = cell[idx] + frac[idx]
+        v0 = np.stack([c[idx] for c in v], 1)
+        xo, vo, fl = O.step_sample(p, s, step, E, x0, v0, ids[idx])
+        cell1, frac1, v1, ids1 = after[s]
+        pos = np.minimum(np.searchsorted(ids1, ids[idx]), len(ids1) - 1)
+        found = ids1[pos] == ids[idx]
+        absorbed = (fl & 1) != 0
+        near = (fl & 4) != 0
+        at_wall = (np.abs(xo) < 1e-4) | (np.abs(xo - N) < 1e-4)
+        assert np.array_equal(found | near | at_wall, ~absorbed | near | at_wall)
+        ok = found & ~absorbed
+        xg = cell1[pos[ok]] + frac1[pos[ok]]
+        vg = np.stack([c[pos[ok]] for c in v1], 1)
+        vt = math.sqrt(p["T"][s] / p["mass"][s])
+        dv = np.abs(vg - vo[ok]).max(axis=1)
+        bad = (dv > 1e-5 * np.abs(vo[ok]).max(axis=1) + 1e-6 * vt) | (np.abs(xg - xo[ok]) > 2e-6)
+        assert int((bad & ~near[ok]).sum()) == 0, (s, int(bad.sum()))
+        if s == 0:  # electrons: some sampled ones leave, some are collision candidates (P_null 1 %)
+            assert int(absorbed.sum()) > 0
+            assert int(((fl & 2) != 0).sum()) > 0
 
 
 def test_full_size_long_run_keeps_every_invariant():
