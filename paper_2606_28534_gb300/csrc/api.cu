@@ -1052,94 +1052,109 @@ extern "C" {
 
 uint32_t pic_blob_crc32(const void* p, size_t n) {
   if (!p || !n) return 0u;
-  return crc32_ieee(static_cast<const unsigned char*>(p), n);
-}
-
-const char* pic_strerror(int status) {
-  switch (status) {
-    case PIC_OK: return "ok";
-    case PIC_EINVAL: return "invalid argument or configuration";
-    case PIC_ENOMEM: return "out of memory or workspace too small";
-    case PIC_ECUDA: return "CUDA runtime error";
-    case PIC_EOVERFLOW: return "particle capacity exceeded";
-    case PIC_ECORRUPT: return "corrupt or mismatched snapshot";
-    case PIC_ETIMEOUT: return "device wait timed out";
-    case PIC_EDEVICE: return "device-side check failed";
-    default: return "unknown status";
-  }
-}
-
-int pic_workspace_size(const pic_config* cfg, size_t* bytes) {
-  if (!valid(cfg) || !bytes) return PIC_EINVAL;
-  pic_handle tmp;
-  tmp.cfg = *cfg;
-  tmp.N = cfg->ncells;
-  tmp.plain = cfg->precision == PIC_FP64_PLAIN;
-  for (int s = 0; s < 2; ++s) tmp.cap[s] = capacity(cfg, s);
-  tmp.cap_nt = neutral_capacity(cfg);
-  layout(&tmp, nullptr, bytes);
-  return PIC_OK;
-}
-
-int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, void* cuda_stream, pic_handle** out) {
-  if (!out) return PIC_EINVAL;
-  *out = nullptr;
-  if (!valid(cfg)) return PIC_EINVAL;
-  if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return PIC_EINVAL;
-  pic_handle* h = new (std::nothrow) pic_handle();
-  if (!h) return PIC_ENOMEM;
-  h->cfg = *cfg;
-  h->st = static_cast<cudaStream_t>(cuda_stream);
-  h->N = cfg->ncells;
-  h->plain = cfg->precision == PIC_FP64_PLAIN;
-  for (int s = 0; s < 2; ++s) h->cap[s] = capacity(cfg, s);
-  h->cap_nt = neutral_capacity(cfg);
-  size_t need = 0;
-  layout(h, nullptr, &need);
-  if (workspace) {
-    if (workspace_bytes < need) {
-      delete h;
-      return PIC_ENOMEM;
+  try {
+      return crc32_ieee(static_cast<const unsigned char*>(p), n);
+    } catch (...) {  // no helper thread could start: the same CRC on this thread
+      return crc32_serial(static_cast<const unsigned char*>(p), n);
     }
-    h->ws = workspace;
-  } else {
-    if (cudaMalloc(&h->ws, need) != cudaSuccess) {
-      delete h;
-      return PIC_ENOMEM;
-    }
-    h->owns_ws = true;
   }
-  h->ws_bytes = need;
-  layout(h, static_cast<char*>(h->ws), &need);
-  derive(h);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sms <= 0) sms = 152;
-  h->grid_step = sms * (h->plain ? occupancy_step64() : occupancy_step32());
-  h->grid_scatter = h->plain ? 0 : sms * occupancy_step32(true);
-  h->grid_sort = sms * 16;
-  h->grid_diag = sms * 8;
-  h->grid_neutral = h->cap_nt ? sms * occupancy_neutral32() : 0;
-  *out = h;
 
-  int rc = PIC_OK;
-  // zero the grid arrays and the control block (particle arrays are written by the load)
-  const char* grid_begin = reinterpret_cast<const char*>(h->plain ? (void*)h->acc[0] : (void*)h->cnt[0]);
-  size_t grid_off = (size_t)(grid_begin - static_cast<char*>(h->ws));
-  if (cudaMemsetAsync(static_cast<char*>(h->ws) + grid_off, 0, need - 256 - grid_off, h->st) != cudaSuccess ||
-      cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st) != cudaSuccess) {
-    rc = PIC_ECUDA;
+  const char* pic_strerror(int status) {
+    switch (status) {
+      case PIC_OK: return "ok";
+      case PIC_EINVAL: return "invalid argument or configuration";
+      case PIC_ENOMEM: return "out of memory or workspace too small";
+      case PIC_ECUDA: return "CUDA runtime error";
+      case PIC_EOVERFLOW: return "particle capacity exceeded";
+      case PIC_ECORRUPT: return "corrupt or mismatched snapshot";
+      case PIC_ETIMEOUT: return "device wait timed out";
+      case PIC_EDEVICE: return "device-side check failed";
+      default: return "unknown status";
+    }
   }
-  if (rc == PIC_OK) rc = load_initial(h);
-  if (rc != PIC_OK) {
+
+  int pic_workspace_size(const pic_config* cfg, size_t* bytes) {
+    PIC_ENTRY_TRY
+    if (!valid(cfg) || !bytes) return PIC_EINVAL;
+    pic_handle tmp;
+    tmp.cfg = *cfg;
+    tmp.N = cfg->ncells;
+    tmp.plain = cfg->precision == PIC_FP64_PLAIN;
+    for (int s = 0; s < 2; ++s) tmp.cap[s] = capacity(cfg, s);
+    tmp.cap_nt = neutral_capacity(cfg);
+    layout(&tmp, nullptr, bytes);
+    return PIC_OK;
+    PIC_ENTRY_CATCH
+  }
+
+  int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, void* cuda_stream, pic_handle** out) {
+    PIC_ENTRY_TRY
+    if (!out) return PIC_EINVAL;
+    *out = nullptr;
+    if (!valid(cfg)) return PIC_EINVAL;
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return PIC_EINVAL;
+    pic_handle* h = new (std::nothrow) pic_handle();
+    if (!h) return PIC_ENOMEM;
+  try {
+    h->cfg = *cfg;
+    h->st = static_cast<cudaStream_t>(cuda_stream);
+    h->N = cfg->ncells;
+    h->plain = cfg->precision == PIC_FP64_PLAIN;
+    for (int s = 0; s < 2; ++s) h->cap[s] = capacity(cfg, s);
+    h->cap_nt = neutral_capacity(cfg);
+    size_t need = 0;
+    layout(h, nullptr, &need);
+    if (workspace) {
+      if (workspace_bytes < need) {
+        delete h;
+        return PIC_ENOMEM;
+      }
+      h->ws = workspace;
+    } else {
+      if (cudaMalloc(&h->ws, need) != cudaSuccess) {
+        delete h;
+        return PIC_ENOMEM;
+      }
+      h->owns_ws = true;
+    }
+    h->ws_bytes = need;
+    layout(h, static_cast<char*>(h->ws), &need);
+    derive(h);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+    h->grid_step = sms * (h->plain ? occupancy_step64() : occupancy_step32());
+    h->grid_scatter = h->plain ? 0 : sms * occupancy_step32(true);
+    h->grid_sort = sms * 16;
+    h->grid_diag = sms * 8;
+    h->grid_neutral = h->cap_nt ? sms * occupancy_neutral32() : 0;
+    *out = h;
+
+    int rc = PIC_OK;
+    // zero the grid arrays and the control block (particle arrays are written by the load)
+    const char* grid_begin = reinterpret_cast<const char*>(h->plain ? (void*)h->acc[0] : (void*)h->cnt[0]);
+    size_t grid_off = (size_t)(grid_begin - static_cast<char*>(h->ws));
+    if (cudaMemsetAsync(static_cast<char*>(h->ws) + grid_off, 0, need - 256 - grid_off, h->st) != cudaSuccess ||
+        cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st) != cudaSuccess) {
+      rc = PIC_ECUDA;
+    }
+    if (rc == PIC_OK) rc = load_initial(h);
+    if (rc != PIC_OK) {
+      pic_free(h);
+      *out = nullptr;
+    }
+    return rc;
+  } catch (...) {  // a host allocation or thread failed part way: release what was taken
     pic_free(h);
     *out = nullptr;
+    return PIC_ENOMEM;
   }
-  return rc;
+  PIC_ENTRY_CATCH
 }
 
 int pic_step(pic_handle* h, int32_t n) {
+  PIC_ENTRY_TRY
   if (!h || n < 0) return PIC_EINVAL;
   for (int32_t k = 0; k < n; ++k) {
     const bool sort_now = !h->plain && (h->step % (unsigned long long)h->cfg.sort_interval) == 0ull;
@@ -1208,22 +1223,28 @@ int pic_step(pic_handle* h, int32_t n) {
     h->step += 1;
   }
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 size_t pic_diag_bytes(void) { return sizeof(Ctl); }
 
 int pic_set_diag_interval(pic_handle* h, int32_t every) {
+  PIC_ENTRY_TRY
   if (!h || every < 0) return PIC_EINVAL;
   h->ke_every = every;
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_sync(pic_handle* h) {
+  PIC_ENTRY_TRY
   if (!h) return PIC_EINVAL;
   return check_errors(h);
+  PIC_ENTRY_CATCH
 }
 
 int pic_diag_async(pic_handle* h, void* host_buf, uint32_t what) {
+  PIC_ENTRY_TRY
   if (!h || !host_buf || what > PIC_DIAG_COUNTERS) return PIC_EINVAL;
   EvPair e;
   prof_begin(h, K_DIAG, &e);
@@ -1251,9 +1272,11 @@ int pic_diag_async(pic_handle* h, void* host_buf, uint32_t what) {
   prof_end(h, &e);
   CK(cudaMemcpyAsync(host_buf, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_diag_decode(const pic_handle* h, const void* host_buf, pic_diag_t* d) {
+  PIC_ENTRY_TRY
   if (!h || !host_buf || !d) return PIC_EINVAL;
   Ctl c;
   std::memcpy(&c, host_buf, sizeof(Ctl));
@@ -1287,9 +1310,11 @@ int pic_diag_decode(const pic_handle* h, const void* host_buf, pic_diag_t* d) {
     d->field_energy = fe;
   }
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_diag(pic_handle* h, pic_diag_t* d) {
+  PIC_ENTRY_TRY
   if (!h || !d) return PIC_EINVAL;
   // one device-to-host read of the control block (its error word included) and one wait
   Ctl c;
@@ -1297,9 +1322,11 @@ int pic_diag(pic_handle* h, pic_diag_t* d) {
   if (rc != PIC_OK) return rc;
   CK(cudaStreamSynchronize(h->st));
   return pic_diag_decode(h, &c, d);
+  PIC_ENTRY_CATCH
 }
 
 int pic_neutral_diag(pic_handle* h, pic_neutral_diag_t* d) {
+  PIC_ENTRY_TRY
   if (!h || !d || !h->cap_nt) return PIC_EINVAL;
   CK(cudaMemsetAsync(&h->ctl->nt_ke_fx, 0, sizeof(h->ctl->nt_ke_fx), h->st));
   EvPair e;
@@ -1322,9 +1349,11 @@ int pic_neutral_diag(pic_handle* h, pic_neutral_diag_t* d) {
   d->particle_steps = c.nt_particle_steps;
   d->ke = (double)c.nt_ke_fx * (1.0 / 16777216.0) * (h->cfg.L / h->N / h->cfg.ppc[1]);
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E, size_t nnodes) {
+  PIC_ENTRY_TRY
   if (!h || nnodes != (size_t)h->N + 1) return PIC_EINVAL;
   int rc = check_errors(h);
   if (rc != PIC_OK) return rc;
@@ -1343,9 +1372,11 @@ int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E,
     for (size_t j = 0; j < nnodes; ++j) E[j] = (float)e[j];
   }
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
+  PIC_ENTRY_TRY
   if (!h) return PIC_EINVAL;
   int rc = check_errors(h);
   if (rc != PIC_OK && rc != PIC_EOVERFLOW) return rc;
@@ -1426,17 +1457,21 @@ int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
   const uint32_t crc = crc32_ieee(out, at);
   put_raw(&crc, 4);
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_restore(pic_handle* h, const void* buf, size_t len) {
+  PIC_ENTRY_TRY
   int rc = restore_state(h, buf, len, false);
   if (rc != PIC_OK) return rc;
   rc = refresh_field(h);
   if (rc != PIC_OK) return rc;
   return check_errors(h);
+  PIC_ENTRY_CATCH
 }
 
 int pic_profile(pic_handle* h, int enable) {
+  PIC_ENTRY_TRY
   if (!h) return PIC_EINVAL;
   if (!enable && h->prof) {
     cudaStreamSynchronize(h->st);
@@ -1444,9 +1479,11 @@ int pic_profile(pic_handle* h, int enable) {
   }
   h->prof = enable != 0;
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_kernel_times(pic_handle* h, double* ms, uint64_t* launches, const char** names, int32_t nkinds) {
+  PIC_ENTRY_TRY
   if (!h || nkinds < 0) return PIC_EINVAL;
   CK(cudaStreamSynchronize(h->st));
   prof_harvest(h);
@@ -1460,6 +1497,7 @@ int pic_kernel_times(pic_handle* h, double* ms, uint64_t* launches, const char**
     h->launches[k] = 0;
   }
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 void pic_free(pic_handle* h) {
@@ -1471,6 +1509,7 @@ void pic_free(pic_handle* h) {
 }
 
 int pic_selftest_timeout(void* cuda_stream, double* seconds) {
+  PIC_ENTRY_TRY
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   unsigned long long* d = nullptr;
   if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return PIC_ENOMEM;
@@ -1482,18 +1521,22 @@ int pic_selftest_timeout(void* cuda_stream, double* seconds) {
   if (e != cudaSuccess) return PIC_ECUDA;
   if (seconds) *seconds = (double)out[1] * 1e-9;
   return status_of((unsigned)out[0]);
+  PIC_ENTRY_CATCH
 }
 
 int pic_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n, void* cuda_stream) {
+  PIC_ENTRY_TRY
   if (n && (!ctr || !key || !out)) return PIC_EINVAL;
   if ((reinterpret_cast<uintptr_t>(ctr) & 15u) || (reinterpret_cast<uintptr_t>(out) & 15u) ||
       (reinterpret_cast<uintptr_t>(key) & 7u))
     return PIC_EINVAL;
   return launch_philox(ctr, key, out, n, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  PIC_ENTRY_CATCH
 }
 
 int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double V_R, double* phi, double* E,
                 void* cuda_stream) {
+  PIC_ENTRY_TRY
   if (!rho || !phi || !E || ncells < 2 || ncells > PIC_MAX_CELLS_FP32 || !(dx > 0)) return PIC_EINVAL;
   PoissonParams F;
   std::memset(&F, 0, sizeof(F));
@@ -1507,6 +1550,7 @@ int pic_poisson(const double* rho, int32_t ncells, double dx, double V_L, double
   F.phi = phi;
   F.E = E;
   return launch_field(F, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  PIC_ENTRY_CATCH
 }
 
 }  // extern "C"

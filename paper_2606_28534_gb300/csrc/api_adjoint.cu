@@ -201,49 +201,60 @@ double field_energy_host(const std::vector<double>& E, int N, double dx) {
 extern "C" {
 
 int pic_adj_workspace_size(const pic_config* cfg, int32_t steps, int32_t checkpoint_every, size_t* bytes) {
+  PIC_ENTRY_TRY
   if (!bytes || !adj_valid(cfg, steps, checkpoint_every)) return PIC_EINVAL;
   pic_adj tmp;
   init_dims(&tmp, cfg, steps, checkpoint_every);
   layout(&tmp, nullptr, bytes);
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_adj_init(const pic_config* cfg, int32_t steps, int32_t checkpoint_every, void* workspace,
                  size_t workspace_bytes, void* cuda_stream, pic_adj** out) {
+  PIC_ENTRY_TRY
   if (!out) return PIC_EINVAL;
   *out = nullptr;
   if (!adj_valid(cfg, steps, checkpoint_every)) return PIC_EINVAL;
   if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return PIC_EINVAL;
   pic_adj* a = new (std::nothrow) pic_adj();
   if (!a) return PIC_ENOMEM;
-  init_dims(a, cfg, steps, checkpoint_every);
-  a->st = static_cast<cudaStream_t>(cuda_stream);
-  size_t need = 0;
-  layout(a, nullptr, &need);
-  if (workspace) {
-    if (workspace_bytes < need) {
-      delete a;
-      return PIC_ENOMEM;
+  try {
+    init_dims(a, cfg, steps, checkpoint_every);
+    a->st = static_cast<cudaStream_t>(cuda_stream);
+    size_t need = 0;
+    layout(a, nullptr, &need);
+    if (workspace) {
+      if (workspace_bytes < need) {
+        delete a;
+        return PIC_ENOMEM;
+      }
+      a->ws = workspace;
+    } else {
+      if (cudaMalloc(&a->ws, need) != cudaSuccess) {
+        delete a;
+        return PIC_ENOMEM;
+      }
+      a->owns_ws = true;
     }
-    a->ws = workspace;
-  } else {
-    if (cudaMalloc(&a->ws, need) != cudaSuccess) {
-      delete a;
-      return PIC_ENOMEM;
-    }
-    a->owns_ws = true;
+    a->ws_bytes = need;
+    layout(a, static_cast<char*>(a->ws), &need);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms > 0) a->max_grid = sms * 8;
+    *out = a;
+    return PIC_OK;
+  } catch (...) {  // a host allocation or thread failed part way: release what was taken
+    pic_adj_free(a);
+    *out = nullptr;
+    return PIC_ENOMEM;
   }
-  a->ws_bytes = need;
-  layout(a, static_cast<char*>(a->ws), &need);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sms > 0) a->max_grid = sms * 8;
-  *out = a;
-  return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_adj_forward(pic_adj* a, double V_left, double T_e, int32_t replay, double J[2]) {
+  PIC_ENTRY_TRY
   if (!a || !J || !(T_e > 0) || !std::isfinite(V_left)) return PIC_EINVAL;
   if (replay && !a->recorded) return PIC_EINVAL;
   pic_config c;
@@ -307,9 +318,11 @@ int pic_adj_forward(pic_adj* a, double V_left, double T_e, int32_t replay, doubl
     a->rec_Te = T_e;
   }
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_adj_gradient(pic_adj* a, const double w[2], double grad[2]) {
+  PIC_ENTRY_TRY
   if (!a || !w || !grad || !a->recorded) return PIC_EINVAL;
   pic_config c;
   const Phys ph = physics(a, a->rec_VL, a->rec_Te, &c);
@@ -417,20 +430,25 @@ int pic_adj_gradient(pic_adj* a, const double w[2], double grad[2]) {
   grad[0] = gV;
   grad[1] = gT / (2.0 * a->rec_Te);
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_adj_schedule(pic_adj* a, int32_t* absorb, size_t n) {
+  PIC_ENTRY_TRY
   if (!a || !absorb || n != (size_t)a->np || !a->recorded) return PIC_EINVAL;
   CKA(cudaStreamSynchronize(a->st));
   CKA(cudaMemcpy(absorb, a->absorb, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_adj_times(pic_adj* a, double* forward_ms, double* gradient_ms) {
+  PIC_ENTRY_TRY
   if (!a) return PIC_EINVAL;
   if (forward_ms) *forward_ms = a->ms_fwd;
   if (gradient_ms) *gradient_ms = a->ms_rev;
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 void pic_adj_free(pic_adj* a) {

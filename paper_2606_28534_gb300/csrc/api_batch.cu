@@ -462,77 +462,88 @@ int32_t pic_batch_variant_count(void) { return bstep32_variants(); }
 const char* pic_batch_variant_name(int32_t v) { return bstep32_variant_name(v); }
 
 int pic_batch_workspace_size(const pic_config* cfgs, int32_t nsims, size_t* bytes) {
+  PIC_ENTRY_TRY
   if (!bytes || !batch_valid(cfgs, nsims)) return PIC_EINVAL;
   pic_batch tmp;
   tmp.n = nsims;
   tmp.cfg.assign(cfgs, cfgs + nsims);
   layout(&tmp, nullptr, bytes);
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_init(const pic_config* cfgs, int32_t nsims, void* workspace, size_t workspace_bytes,
                    void* cuda_stream, pic_batch** out) {
+  PIC_ENTRY_TRY
   if (!out) return PIC_EINVAL;
   *out = nullptr;
   if (!batch_valid(cfgs, nsims)) return PIC_EINVAL;
   if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return PIC_EINVAL;
   pic_batch* b = new (std::nothrow) pic_batch();
   if (!b) return PIC_ENOMEM;
-  b->n = nsims;
-  b->cfg.assign(cfgs, cfgs + nsims);
-  b->st = static_cast<cudaStream_t>(cuda_stream);
-  b->sort_interval = cfgs[0].sort_interval;
-  size_t need = 0;
-  layout(b, nullptr, &need);
-  if (workspace) {
-    if (workspace_bytes < need) {
-      delete b;
-      return PIC_ENOMEM;
+  try {
+    b->n = nsims;
+    b->cfg.assign(cfgs, cfgs + nsims);
+    b->st = static_cast<cudaStream_t>(cuda_stream);
+    b->sort_interval = cfgs[0].sort_interval;
+    size_t need = 0;
+    layout(b, nullptr, &need);
+    if (workspace) {
+      if (workspace_bytes < need) {
+        delete b;
+        return PIC_ENOMEM;
+      }
+      b->ws = workspace;
+    } else {
+      if (cudaMalloc(&b->ws, need) != cudaSuccess) {
+        delete b;
+        return PIC_ENOMEM;
+      }
+      b->owns_ws = true;
     }
-    b->ws = workspace;
-  } else {
-    if (cudaMalloc(&b->ws, need) != cudaSuccess) {
-      delete b;
-      return PIC_ENOMEM;
+    b->ws_bytes = need;
+    layout(b, static_cast<char*>(b->ws), &need);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (b->sms <= 0) b->sms = 152;
+    *out = b;
+    int rc = PIC_OK;
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) rc = PIC_ECUDA;
+    b->views.assign(nsims, nullptr);
+    for (int k = 0; k < nsims && rc == PIC_OK; ++k) {
+      b->views[k] = new (std::nothrow) pic_handle();
+      if (!b->views[k]) {
+        rc = PIC_ENOMEM;
+        break;
+      }
+      make_view(b, k, b->views[k]);
     }
-    b->owns_ws = true;
-  }
-  b->ws_bytes = need;
-  layout(b, static_cast<char*>(b->ws), &need);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-  if (b->sms <= 0) b->sms = 152;
-  *out = b;
-  int rc = PIC_OK;
-  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) rc = PIC_ECUDA;
-  b->views.assign(nsims, nullptr);
-  for (int k = 0; k < nsims && rc == PIC_OK; ++k) {
-    b->views[k] = new (std::nothrow) pic_handle();
-    if (!b->views[k]) {
-      rc = PIC_ENOMEM;
-      break;
+    if (rc == PIC_OK) {
+      pic_batch_tuning t;
+      std::memset(&t, 0, sizeof(t));
+      t.use_graph = 1;
+      rc = pic_batch_set_tuning(b, &t);
     }
-    make_view(b, k, b->views[k]);
-  }
-  if (rc == PIC_OK) {
-    pic_batch_tuning t;
-    std::memset(&t, 0, sizeof(t));
-    t.use_graph = 1;
-    rc = pic_batch_set_tuning(b, &t);
-  }
-  if (rc == PIC_OK) rc = load_all(b);
-  if (rc == PIC_OK) rc = upload_tables(b);
-  if (rc == PIC_OK) rc = replan(b);
-  if (rc == PIC_OK) rc = sync_errors(b);
-  if (rc != PIC_OK) {
+    if (rc == PIC_OK) rc = load_all(b);
+    if (rc == PIC_OK) rc = upload_tables(b);
+    if (rc == PIC_OK) rc = replan(b);
+    if (rc == PIC_OK) rc = sync_errors(b);
+    if (rc != PIC_OK) {
+      pic_batch_free(b);
+      *out = nullptr;
+    }
+    return rc;
+  } catch (...) {  // a host allocation or thread failed part way: release what was taken
     pic_batch_free(b);
     *out = nullptr;
+    return PIC_ENOMEM;
   }
-  return rc;
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_set_tuning(pic_batch* b, const pic_batch_tuning* t) {
+  PIC_ENTRY_TRY
   if (!b || !t) return PIC_EINVAL;
   if (t->variant < 0 || t->variant >= bstep32_variants()) return PIC_EINVAL;
   const int occ = bstep32_occupancy(t->variant);
@@ -542,9 +553,11 @@ int pic_batch_set_tuning(pic_batch* b, const pic_batch_tuning* t) {
   b->tun = *t;
   b->grid_step = b->sms * (t->ctas_per_sm ? t->ctas_per_sm : occ);
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_set_diag_interval(pic_batch* b, int32_t every) {
+  PIC_ENTRY_TRY
   if (!b || every < 0 || every > 1) return PIC_EINVAL;
   if (every != b->ke_every) {
     cudaStreamSynchronize(b->st);
@@ -552,15 +565,19 @@ int pic_batch_set_diag_interval(pic_batch* b, int32_t every) {
   }
   b->ke_every = every;
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_get_tuning(pic_batch* b, pic_batch_tuning* t) {
+  PIC_ENTRY_TRY
   if (!b || !t) return PIC_EINVAL;
   *t = b->tun;
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_step(pic_batch* b, int32_t n) {
+  PIC_ENTRY_TRY
   if (!b || n < 0) return PIC_EINVAL;
   const unsigned long long cycle = 2ull * (unsigned long long)b->sort_interval;
   while (n > 0) {
@@ -583,28 +600,36 @@ int pic_batch_step(pic_batch* b, int32_t n) {
     }
   }
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_sync(pic_batch* b) {
+  PIC_ENTRY_TRY
   if (!b) return PIC_EINVAL;
   return sync_errors(b);
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_diag(pic_batch* b, pic_diag_t* out, int32_t nsims) {
+  PIC_ENTRY_TRY
   if (!b || !out || nsims < 0 || nsims > b->n) return PIC_EINVAL;
   for (int k = 0; k < nsims; ++k) {
     const int rc = pic_diag(view(b, k), out + k);
     if (rc != PIC_OK) return rc;
   }
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_snapshot(pic_batch* b, int32_t k, void* buf, size_t cap, size_t* needed) {
+  PIC_ENTRY_TRY
   if (!b || k < 0 || k >= b->n) return PIC_EINVAL;
   return pic_snapshot(view(b, k), buf, cap, needed);
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_restore(pic_batch* b, const void* const* blobs, const size_t* lens) {
+  PIC_ENTRY_TRY
   if (!b || !blobs || !lens) return PIC_EINVAL;
   unsigned long long step = 0;
   for (int k = 0; k < b->n; ++k) {
@@ -636,23 +661,29 @@ int pic_batch_restore(pic_batch* b, const void* const* blobs, const size_t* lens
   const int rc = replan(b);
   if (rc != PIC_OK) return rc;
   return sync_errors(b);
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_reset(pic_batch* b) {
+  PIC_ENTRY_TRY
   if (!b) return PIC_EINVAL;
   CKB(cudaStreamSynchronize(b->st));
   int rc = load_all(b);
   if (rc == PIC_OK) rc = replan(b);
   if (rc == PIC_OK) rc = sync_errors(b);
   return rc;
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_get_field(pic_batch* b, int32_t k, int64_t* R, double* rho, double* phi, float* E, size_t nnodes) {
+  PIC_ENTRY_TRY
   if (!b || k < 0 || k >= b->n) return PIC_EINVAL;
   return pic_get_field(view(b, k), R, rho, phi, E, nnodes);
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_profile(pic_batch* b, int enable) {
+  PIC_ENTRY_TRY
   if (!b) return PIC_EINVAL;
   if (!enable && b->prof) {
     cudaStreamSynchronize(b->st);
@@ -660,9 +691,11 @@ int pic_batch_profile(pic_batch* b, int enable) {
   }
   b->prof = enable != 0;
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 int pic_batch_kernel_times(pic_batch* b, double* ms, uint64_t* launches, const char** names, int32_t nkinds) {
+  PIC_ENTRY_TRY
   if (!b || nkinds < 0) return PIC_EINVAL;
   CKB(cudaStreamSynchronize(b->st));
   bprof_harvest(b);
@@ -676,6 +709,7 @@ int pic_batch_kernel_times(pic_batch* b, double* ms, uint64_t* launches, const c
     b->launches[k] = 0;
   }
   return PIC_OK;
+  PIC_ENTRY_CATCH
 }
 
 void pic_batch_free(pic_batch* b) {

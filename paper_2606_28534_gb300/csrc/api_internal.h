@@ -4,6 +4,15 @@
 #pragma once
 #include <vector>
 
+// Entry points catch what their host code may throw (a host allocation that fails, a host thread
+// that cannot start), so that no C++ exception crosses the C ABI: the call returns PIC_ENOMEM.
+#define PIC_ENTRY_TRY try {
+#define PIC_ENTRY_CATCH \
+  }                     \
+  catch (...) {         \
+    return PIC_ENOMEM;  \
+  }
+
 #include "../../include/pic.h"
 #include "pic_internal.cuh"
 
