@@ -11,7 +11,9 @@
  * (per-species particle records from which the run resumes exactly) follow Sec. 4.1.
  *
  * Conventions for every call:
- *  - Return value: PIC_OK (0) or one of the PIC_E* codes below; pic_strerror() names it.
+ *  - Return value: PIC_OK (0) or one of the PIC_E* codes below; pic_strerror() names it.  No
+ *    C++ exception leaves a call: a host allocation or host thread that fails inside one makes it
+ *    return PIC_ENOMEM (a failed pic_init / pic_batch_init / pic_adj_init releases what it took).
  *  - A handle owns all device state of one simulation.  The caller owns every host buffer it
  *    passes.  No call is thread-safe on one handle; distinct handles are independent.
  *  - Work is enqueued on the CUDA stream given to pic_init (NULL = the legacy default stream).
