@@ -144,6 +144,7 @@ PoissonParams field_from_R(const pic_adj* a, const pic_config& c, double* E) {
     F.qw[s] = c.charge[s] * (dx / c.ppc[s]);
   }
   F.mode = 3;
+  F.zero_R = 1;  // the next push deposits into R again
   F.N = c.ncells;
   F.dx = dx;
   F.inv_dx = 1.0 / dx;
@@ -293,7 +294,6 @@ int pic_adj_forward(pic_adj* a, double V_left, double T_e, int32_t replay, doubl
       const int rc = copy_state(a, a->ckpt[k / a->K], a->cur);
       if (rc != PIC_OK) return rc;
     }
-    for (int s = 0; s < 2; ++s) CKA(cudaMemsetAsync(a->R[s], 0, sizeof(unsigned long long) * nn, a->st));
     double* Eout = replay ? a->Escr[(k + 1) & 1] : a->Etape + (size_t)(k + 1) * nn;
     S.E = Ein;
     S.step = k;
@@ -401,9 +401,8 @@ int pic_adj_gradient(pic_adj* a, const double w[2], double grad[2]) {
       CKA(launch_adj_push(S, a->max_grid, a->st));
     }
     for (int k = n1 - 1; k >= n0; --k) {
-      CKA(launch_adj_field_t(mu, a->rhs, N, dx, a->gV, 1, a->st));
+      CKA(launch_adj_field_t(mu, a->rhs, N, dx, a->gV, 1, mu_next, a->st));
       CKA(launch_field(F, a->st));
-      CKA(cudaMemsetAsync(mu_next, 0, sizeof(double) * nn, a->st));
       R.s0 = a->tape[k - n0];
       R.s1 = a->tape[k + 1 - n0];
       R.E = a->Etape + (size_t)k * nn;
@@ -414,7 +413,7 @@ int pic_adj_gradient(pic_adj* a, const double w[2], double grad[2]) {
       std::swap(mu, mu_next);
     }
   }
-  CKA(launch_adj_field_t(mu, nullptr, N, dx, a->gV, 0, a->st));  // E^0's bias term
+  CKA(launch_adj_field_t(mu, nullptr, N, dx, a->gV, 0, nullptr, a->st));  // E^0's bias term
   CKA(launch_adj_tgrad(R, a->ckpt[0], a->partial, a->tblocks, a->st));
   cudaEventRecord(e1, a->st);
   double gV = 0.0;

@@ -164,13 +164,15 @@ __global__ void k_adj_fill(int* a, unsigned long long n, int v) {
 // runs at a small fraction of the FP32 rate on this GPU: the divisions are products with
 // reciprocals formed once on the host.
 __global__ void __launch_bounds__(1024) k_adj_field_t(const double* __restrict__ mu, double* __restrict__ rhs, int N,
-                                                    double inv_dx, double* gV, int with_rhs) {
+                                                    double inv_dx, double* gV, int with_rhs,
+                                                    double* __restrict__ zero_next) {
   __shared__ double part[1024];
   const int tid = threadIdx.x;
   const double half_inv_dx = 0.5 * inv_dx, inv_dx2 = inv_dx * inv_dx;
   double acc = 0.0;
   for (int j = tid; j <= N; j += 1024) {
     acc += mu[j];
+    if (zero_next) zero_next[j] = 0.0;
     if (with_rhs) {
       double a = 0.0;
       if (j >= 1 && j <= N - 1) {
@@ -312,8 +314,8 @@ cudaError_t launch_adj_fill(int* a, unsigned long long n, int v, cudaStream_t st
 }
 
 cudaError_t launch_adj_field_t(const double* mu, double* rhs, int N, double dx, double* gV, int with_rhs,
-                               cudaStream_t st) {
-  k_adj_field_t<<<1, 1024, 0, st>>>(mu, rhs, N, 1.0 / dx, gV, with_rhs);
+                               double* zero_next, cudaStream_t st) {
+  k_adj_field_t<<<1, 1024, 0, st>>>(mu, rhs, N, 1.0 / dx, gV, with_rhs, zero_next);
   return cudaGetLastError();
 }
 

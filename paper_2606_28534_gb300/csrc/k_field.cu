@@ -333,7 +333,12 @@ __device__ __forceinline__ double node_rho(const PoissonParams& P, int j) {
   } else if (MODE == 2) {
     return P.rho_in[j];
   } else {
-    return (P.qw[0] * (double)P.R[0][j] + P.qw[1] * (double)P.R[1][j]) * 2.3283064365386963e-10 * inv_vol;
+    const long long R0 = P.R[0][j], R1 = P.R[1][j];
+    if (P.zero_R) {  // each node is read by one thread
+      P.R[0][j] = 0;
+      P.R[1][j] = 0;
+    }
+    return (P.qw[0] * (double)R0 + P.qw[1] * (double)R1) * 2.3283064365386963e-10 * inv_vol;
   }
 }
 

@@ -299,6 +299,7 @@ struct PoissonParams {
   double inv_dx;
   int exact;        // mode 0: integer-exact field (integer charges)
   int mode;         // 0: fixed point, 1: FP64 accumulators, 2: plain rho, 3: from stored R
+  int zero_R;       // mode 3: R is zeroed once read (the adjoint forward's next deposit)
   int keep_counts;  // fixed point: leave cnt for the sort
   int N;
   double dx, V_L, V_R;
@@ -432,8 +433,9 @@ cudaError_t launch_adj_push(const AdjStep& p, int max_grid, cudaStream_t st);
 cudaError_t launch_adj_deposit0(const AdjState& s, unsigned long long n0, unsigned long long np,
                                 unsigned long long* R0, unsigned long long* R1, int max_grid, cudaStream_t st);
 cudaError_t launch_adj_fill(int* a, unsigned long long n, int v, cudaStream_t st);
+// zero_next (may be null): N + 1 values zeroed on the way (the next mu accumulator)
 cudaError_t launch_adj_field_t(const double* mu, double* rhs, int N, double dx, double* gV, int with_rhs,
-                               cudaStream_t st);
+                               double* zero_next, cudaStream_t st);
 cudaError_t launch_adj_reverse(const AdjRev& p, int max_grid, cudaStream_t st);
 cudaError_t launch_adj_tgrad(const AdjRev& p, const AdjState& s0, double* partial, int blocks, cudaStream_t st);
 
