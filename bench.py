@@ -9,6 +9,11 @@ step).  Inputs (2.8 GB of particles) are larger than L2, so no flush is needed b
 
 Lines printed (rank 0): one JSON object.  ``--impl reference`` times the plain FP64 CPU oracle
 (the CPU reference of this library) on a bounded sample of the same workload instead.
+
+With N > 1 processes (torchrun, one per GPU) every rank advances its own replica of the workload
+(its own seed, no data-path collective): the value is the particle-steps of all ranks over the
+slowest rank's time, and the end-to-end leg runs on every rank.  The single-GPU sections (plain
+FP64 path, ensemble, adjoint, sheath, precision, the CPU baseline) run at N = 1 only.
 """
 from __future__ import annotations
 
