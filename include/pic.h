@@ -192,7 +192,8 @@ int pic_set_diag_interval(pic_handle* h, int32_t every);
 /* Wait for the stream and report device-side errors (PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_EDEVICE). */
 int pic_sync(pic_handle* h);
 
-/* Serialise the state into buf (host memory, cap bytes).  buf == NULL: only *needed is set.
+/* Serialise the state into buf (host memory, cap bytes).  buf == NULL: only *needed is set, from
+ * the live counts (an upper bound after a neutral overflow); with buf, *needed = the bytes written.
  * Version-1 blob, little-endian: "PICMCSN1", u32 version, u32 0, u64 config hash, u64 step,
  * u64 n[2], u64 counters[17], i64 wall_charge, f64 wall_energy[2], then per species
  * i32 cell[n], f64 frac[n], f64 vx[n], f64 vy[n], f64 vz[n], u64 id[n] in ascending id order,

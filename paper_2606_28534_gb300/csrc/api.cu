@@ -1380,15 +1380,17 @@ int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
   if (!h) return PIC_EINVAL;
   int rc = check_errors(h);
   if (rc != PIC_OK && rc != PIC_EOVERFLOW) return rc;
-  // the size from the exact live counts of the control block (a size query moves no particles)
+  // a size query reads only the live counts of the control block and moves no particles (after
+  // a neutral overflow the count still includes the neutrals that found no slot: an upper bound)
   Ctl c;
   CK(cudaStreamSynchronize(h->st));
   CK(cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-  const size_t need = kHdr + 4 + 44 * (size_t)(c.n_live[0] + c.n_live[1]) +
-                      (h->cap_nt ? kNtHdr + 44 * (size_t)c.nt_live : 0);
-  if (needed) *needed = need;
-  if (!buf) return PIC_OK;
-  if (cap < need) return PIC_EINVAL;
+  if (!buf) {
+    if (needed)
+      *needed = kHdr + 4 + 44 * (size_t)(c.n_live[0] + c.n_live[1]) +
+                (h->cap_nt ? kNtHdr + 44 * (size_t)c.nt_live : 0);
+    return PIC_OK;
+  }
   HostParticles P[2], NT;
   rc = fetch_particles(h, P, &c);
   if (rc != PIC_OK) return rc;
@@ -1396,9 +1398,10 @@ int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
     rc = fetch_neutrals(h, h->nt[h->nt_buf], (size_t)c.nt_cur, NT);
     if (rc != PIC_OK) return rc;
   }
-  // the live entries found in the arrays must be the counted ones
-  if (P[0].id.size() != c.n_live[0] || P[1].id.size() != c.n_live[1] || (h->cap_nt && NT.id.size() != c.nt_live))
-    return PIC_EDEVICE;
+  // the blob holds the live entries found in the arrays
+  const size_t need = kHdr + 4 + 44 * (P[0].id.size() + P[1].id.size()) + (h->cap_nt ? kNtHdr + 44 * NT.id.size() : 0);
+  if (needed) *needed = need;
+  if (cap < need) return PIC_EINVAL;
   // header, then each array copied straight into the caller's buffer (host threads for the
   // large ones), then the CRC of everything before it
   unsigned char* const out = static_cast<unsigned char*>(buf);

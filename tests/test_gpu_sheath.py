@@ -378,6 +378,13 @@ def test_a_full_neutral_buffer_reports_an_overflow_and_drops_the_rest():
     with pytest.raises(pic.PicError) as e:
         g.sync()
     assert e.value.status == 4  # PIC_EOVERFLOW
+    # the state can still be saved: the blob holds the neutrals that found a slot
+    import zlib
+
+    blob = g.snapshot()
+    assert zlib.crc32(blob[:-4]) == int.from_bytes(blob[-4:], "little")
+    nt = snapfmt.parse(blob)["neutrals"]
+    assert 0 < len(nt["id"]) <= 6144 and len(np.unique(nt["id"])) == len(nt["id"])
     g.close()
 
 
