@@ -19,6 +19,8 @@
 
 namespace {
 
+static_assert(PIC_PPT == 4, "each lane moves four particles: one 128-bit access per array");
+
 // The simulation a warp is in, as the particle loop reads it (shared memory, one per warp: read
 // where used instead of held in registers through the loop).
 struct WarpSim {

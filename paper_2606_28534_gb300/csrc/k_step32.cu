@@ -21,6 +21,7 @@
 namespace {
 
 constexpr int NSTAGE = 2;   // chunks in flight per warp (TMA double buffer)
+static_assert(PIC_PPT == 4, "each lane moves four particles: one 128-bit access per array");
 constexpr int WARPS = PIC_TPB / 32;
 constexpr size_t STEP_SMEM = (size_t)WARPS * (NSTAGE * STAGE_BYTES + QCAP * 8 + NSTAGE * 8);
 
