@@ -165,20 +165,28 @@ typedef struct pic_neutral_diag {
 
 typedef struct pic_handle pic_handle;
 
-/* Bytes of device workspace that pic_init needs for cfg (capacity, sort buffers, grids). */
+/* Bytes of device workspace that pic_init needs for cfg (capacity, sort buffers, grids): the
+ * device-resident state of one run of the PIC MC cycle (Sec. 2), laid out as 1D contiguous
+ * per-species arrays (the 1D layout of Sec. 5.2). */
 int pic_workspace_size(const pic_config* cfg, size_t* bytes);
 
-/* Create a simulation: validate cfg, carve the caller's device workspace (256-byte aligned,
- * >= pic_workspace_size bytes; it must outlive the handle) or, when workspace is NULL, allocate
- * it with cudaMalloc (freed by pic_free).  Loads the particles (Philox keyed by particle id),
+/* Create a simulation (Sec. 2, "Background": the set-up before the PIC MC cycle -- particle
+ * load, first deposition, field solve and the "natural sorting" of particles per cell; Table 3:
+ * the bounded plasma between two absorbing walls).  Validates cfg (PIC_EINVAL), carves the
+ * caller's device workspace (256-byte aligned, >= pic_workspace_size bytes; it must outlive the
+ * handle; PIC_ENOMEM if smaller) or, when workspace is NULL, allocates it with cudaMalloc (freed
+ * by pic_free; PIC_ENOMEM on failure).  Loads the particles (Philox keyed by particle id),
  * deposits, solves the field and sorts.  cuda_stream is a cudaStream_t (NULL = default).
- * On success *out owns the state; on failure *out is NULL. */
+ * On success *out owns the state; on failure *out is NULL and nothing is left allocated. */
 int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, void* cuda_stream,
              pic_handle** out);
 
-/* Enqueue n >= 0 steps (gather, Boris push, walls, null-collision MC, deposit, source,
- * Poisson, and the per-cell counting sort + compaction on steps with step % sort_interval
- * == 0).  Asynchronous on the handle's stream. */
+/* Enqueue n >= 0 steps of the PIC MC cycle (Sec. 2, "Background": interpolation of the field to
+ * the particles, particle mover, absorption at the walls of Table 3, MC collisions, deposition to
+ * the grid, field solve; plus the per-cell counting sort and compaction -- BIT1's "natural
+ * sorting", Sec. 2, the arranger of Sec. 5.1 -- on steps with step % sort_interval == 0).
+ * Asynchronous on the handle's stream; PIC_EINVAL for n < 0 or a NULL handle, PIC_ECUDA if a
+ * launch fails.  Device-side errors surface at the next synchronising call. */
 int pic_step(pic_handle* h, int32_t n);
 
 /* Kinetic-energy diagnostics (pic_diag_t.ke).  every > 0: the FP32 step kernel sums the kinetic
@@ -189,11 +197,17 @@ int pic_step(pic_handle* h, int32_t n);
  * PIC_EINVAL for every < 0. */
 int pic_set_diag_interval(pic_handle* h, int32_t every);
 
-/* Wait for the stream and report device-side errors (PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_EDEVICE). */
+/* Wait for the stream and report device-side errors (PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_EDEVICE):
+ * the failure detection of this library (no counterpart in the paper beyond Sec. 4.1's
+ * checkpoint/restart, from which a failed run resumes). */
 int pic_sync(pic_handle* h);
 
-/* Serialise the state into buf (host memory, cap bytes).  buf == NULL: only *needed is set, from
- * the live counts (an upper bound after a neutral overflow); with buf, *needed = the bytes written.
+/* Checkpoint (Sec. 4.1, "Checkpoint/Restart": per-species particle records -- cell, position,
+ * velocity, id -- from which the run resumes; here an in-memory blob instead of an openPMD series).
+ * Serialises the state into buf (host memory, owned by the caller, cap bytes).  buf == NULL: only
+ * *needed is set, from the live counts (an upper bound after a neutral overflow); with buf,
+ * *needed = the bytes written (PIC_EINVAL if cap is too small).  Accepts a state after
+ * PIC_EOVERFLOW (it writes the particles that found a slot).
  * Version-1 blob, little-endian: "PICMCSN1", u32 version, u32 0, u64 config hash, u64 step,
  * u64 n[2], u64 counters[17], i64 wall_charge, f64 wall_energy[2], then per species
  * i32 cell[n], f64 frac[n], f64 vx[n], f64 vy[n], f64 vz[n], u64 id[n] in ascending id order,
@@ -202,14 +216,20 @@ int pic_sync(pic_handle* h);
  * neutrals' records in the same layout.  Synchronises the stream. */
 int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed);
 
-/* Replace the state by a blob from pic_snapshot (or any writer of the same format) made with
- * the same physics configuration (config hash), then redeposit and re-solve the field.
+/* Restart (Sec. 4.1, "Checkpoint/Restart": the restore of a checkpoint, after which the run
+ * continues; here bit-exactly, since every random draw is keyed by particle id and step).
+ * Replaces the state by a blob from pic_snapshot (or any writer of the same format) made with
+ * the same physics configuration (config hash), then redeposits, re-solves the field and sorts.
+ * The blob is host memory owned by the caller and is checked entirely before any state changes.
  * PIC_ECORRUPT on any format error; PIC_EOVERFLOW if a species exceeds the capacity.
  * Positions and velocities are rounded to FP32 under PIC_FP32.  Synchronises the stream. */
 int pic_restore(pic_handle* h, const void* buf, size_t len);
 
-/* Diagnostics; reduces on the device, then one read of the control block and one wait on the
- * stream.  *out is filled only when the call returns PIC_OK (otherwise: the device-side error). */
+/* Diagnostics of the run (Sec. 2 and Table 2: BIT1's diagnostics of particle numbers, wall
+ * fluxes and energies, taken every `datfile` steps there; here on request): particle counts,
+ * wall hits, collision counts, charge and energies (pic_diag_t).  Reduces on the device, then
+ * one read of the control block and one wait on the stream.  *out (host, caller-owned) is filled
+ * only when the call returns PIC_OK (otherwise: the device-side error, PIC_EINVAL for NULL). */
 int pic_diag(pic_handle* h, pic_diag_t* out);
 
 /* Neutral diagnostics (PIC_EINVAL without neutrals); as pic_diag: one pass over the neutrals for
@@ -234,10 +254,25 @@ size_t pic_diag_bytes(void);
 int pic_diag_async(pic_handle* h, void* host_buf, uint32_t what);
 int pic_diag_decode(const pic_handle* h, const void* host_buf, pic_diag_t* out);
 
-/* Copy the grid to host buffers of nnodes = N + 1 entries each (any may be NULL):
- * R: 2 x (N+1) int64 deposits (2^-32 particle units), rho, phi: FP64, E: FP32 node field as
- * seen by the particles.  Synchronises the stream. */
+/* The grid quantities of the PIC cycle (Sec. 2: "deposition to the grid" and the "field
+ * solver"): copies them to host buffers (caller-owned) of nnodes = N + 1 entries each (any may be
+ * NULL): R: 2 x (N+1) int64 deposits (species 0 then 1, 2^-32 particle units), rho, phi: FP64,
+ * E: FP32 node field as seen by the particles.  PIC_EINVAL if nnodes != N + 1.  Synchronises the
+ * stream and reports device-side errors first. */
 int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E, size_t nnodes);
+
+/* The storage order of one charged species (species 0 or 1): the arranger's output (Sec. 2,
+ * BIT1's "natural sorting"; the arranger of Sec. 5.1), for checking it.  Copies, for every slot of
+ * the particle buffer the next step reads, in storage order, the cell index (INT32_MIN marks a dead
+ * slot: a particle absorbed since the last sort, or padding) and, where ids != NULL, the particle
+ * id (meaningless in a dead slot) into host buffers of cap entries; *n = the buffer's extent (a
+ * multiple of 4, dead slots included).  cell == NULL and ids == NULL: only *n.  PIC_EINVAL for the
+ * plain FP64 path (it keeps no cell order) or a species outside {0, 1}; PIC_ENOMEM if cap < *n.
+ * After the full sort of pic_init / pic_restore the live slots come first, in non-decreasing cell
+ * order; after the step that follows a sort step, slot blocks follow the cells the particles held
+ * when that step began, with dead slots where particles were absorbed in it and that step's births
+ * after the blocks.  Synchronises the stream and reports device-side errors first. */
+int pic_storage_order(pic_handle* h, int32_t species, int32_t* cell, uint64_t* ids, size_t cap, size_t* n);
 
 /* Per-kernel device time via CUDA events on the handle's stream.  enable != 0 starts recording
  * (adds two event records per launch); pic_kernel_times synchronises and returns, for up to
@@ -368,6 +403,11 @@ int pic_batch_reset(pic_batch* b);
 int pic_batch_get_field(pic_batch* b, int32_t k, int64_t* R, double* rho, double* phi, float* E,
                         size_t nnodes);
 
+/* Storage order of species s of simulation k (as pic_storage_order; the arranger's output for
+ * that simulation, inside its segment of the batch's arrays). */
+int pic_batch_storage_order(pic_batch* b, int32_t k, int32_t species, int32_t* cell, uint64_t* ids,
+                            size_t cap, size_t* n);
+
 /* Per-kernel device time (as pic_profile / pic_kernel_times; kinds "step", "field", "sort",
  * "plan").  While profiling, steps are launched one by one (no graphs). */
 int pic_batch_profile(pic_batch* b, int enable);
@@ -422,6 +462,17 @@ int pic_adj_gradient(pic_adj* a, const double w[2], double grad[2]);
  * electrons then ions in load order; n must be the particle count. */
 int pic_adj_schedule(pic_adj* a, int32_t* absorb, size_t n);
 
+/* The tape of the last recording forward, for checking the reverse sweep against another
+ * implementation's on the same trajectory: the FP32 particle state after n steps (0 <= n <= steps;
+ * electrons then ions in load order, np = the particle count: cell, fraction, v; a particle absorbed
+ * before step n holds whatever state it was absorbed with) and E^n, the FP64 node field the push of
+ * step n uses (E^steps: the final field; nnodes = N + 1).  Any output may be NULL; host buffers owned
+ * by the caller.  The state is recomputed from its checkpoint with the recorded fields (the same
+ * kernel and inputs, hence the same bits as during the recording).  PIC_EINVAL before a recording
+ * forward, for n outside [0, steps] or wrong sizes.  Synchronises the stream. */
+int pic_adj_tape(pic_adj* a, int32_t n, int32_t* cell, float* frac, float* vx, float* vy, float* vz, double* E,
+                 size_t np, size_t nnodes);
+
 /* Device time of the last forward and the last gradient (CUDA events on the handle's stream). */
 int pic_adj_times(pic_adj* a, double* forward_ms, double* gradient_ms);
 
@@ -438,7 +489,9 @@ void pic_adj_free(pic_adj* a);
  * fixed array in device memory that every GPU which loads this library keeps until the process
  * exits; the first call on each device looks up that array's device address (make that first
  * call before any stream capture).  Limits: 2 <= cfg->ncells <= PIC_NOALLOC_MAX_CELLS (larger
- * grids return PIC_EINVAL), integer charges |q| <= 64, ppc ratio as in pic_init's exact solve.
+ * grids return PIC_EINVAL), integer charges |q| <= 64, ppc ratio as in pic_init's exact solve,
+ * 0 <= cfg->smooth_passes <= 4 (the density smoothing of the step's own solve is applied to E; R
+ * stays the unsmoothed deposit).
  * Inputs (device, caller-owned): per species s the cell indices (int32) and fractions (FP32) of
  * n_s particles; entries with a cell outside [0, N) or a fraction outside [0, 1) are skipped.
  * Outputs (device, caller-owned): R, 2 x (N+1) int64 node deposits (species 0 then 1, 2^-32

@@ -1375,6 +1375,23 @@ int pic_get_field(pic_handle* h, int64_t* R, double* rho, double* phi, float* E,
   PIC_ENTRY_CATCH
 }
 
+int pic_storage_order(pic_handle* h, int32_t species, int32_t* cell, uint64_t* ids, size_t cap, size_t* n) {
+  PIC_ENTRY_TRY
+  if (!h || !n || h->plain || species < 0 || species > 1) return PIC_EINVAL;
+  int rc = check_errors(h);
+  if (rc != PIC_OK) return rc;
+  unsigned long long ext = 0;
+  CK(cudaMemcpy(&ext, &h->ctl->n_cur[species], sizeof(ext), cudaMemcpyDeviceToHost));
+  *n = (size_t)ext;
+  if (!cell && !ids) return PIC_OK;
+  if (cap < (size_t)ext) return PIC_ENOMEM;
+  const Species32& a = h->a32[h->cur][species];
+  if (cell && ext) CK(cudaMemcpy(cell, a.cell, sizeof(int32_t) * ext, cudaMemcpyDeviceToHost));
+  if (ids && ext) CK(cudaMemcpy(ids, a.id, sizeof(uint64_t) * ext, cudaMemcpyDeviceToHost));
+  return PIC_OK;
+  PIC_ENTRY_CATCH
+}
+
 int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
   PIC_ENTRY_TRY
   if (!h) return PIC_EINVAL;

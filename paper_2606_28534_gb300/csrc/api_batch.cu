@@ -682,6 +682,14 @@ int pic_batch_get_field(pic_batch* b, int32_t k, int64_t* R, double* rho, double
   PIC_ENTRY_CATCH
 }
 
+int pic_batch_storage_order(pic_batch* b, int32_t k, int32_t species, int32_t* cell, uint64_t* ids, size_t cap,
+                            size_t* n) {
+  PIC_ENTRY_TRY
+  if (!b || k < 0 || k >= b->n) return PIC_EINVAL;
+  return pic_storage_order(view(b, k), species, cell, ids, cap, n);
+  PIC_ENTRY_CATCH
+}
+
 int pic_batch_profile(pic_batch* b, int enable) {
   PIC_ENTRY_TRY
   if (!b) return PIC_EINVAL;
