@@ -79,7 +79,8 @@ SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapsh
            "pic_batch_sync", "pic_batch_diag", "pic_batch_snapshot", "pic_batch_restore",
            "pic_batch_reset", "pic_batch_get_field", "pic_batch_profile", "pic_batch_kernel_times",
            "pic_batch_free", "pic_adj_workspace_size", "pic_adj_init", "pic_adj_forward",
-           "pic_adj_gradient", "pic_adj_schedule", "pic_adj_times", "pic_adj_free")
+           "pic_adj_gradient", "pic_adj_schedule", "pic_adj_times", "pic_adj_free",
+           "pic_storage_order", "pic_batch_storage_order", "pic_adj_tape")
 
 PIC_BATCH_MAX_SIMS = 4096
 
@@ -113,6 +114,10 @@ def lib():
         L.pic_selftest_timeout.argtypes = [V, P(C.c_double)]
         L.pic_get_field.argtypes = [V, P(C.c_int64), P(C.c_double), P(C.c_double), P(C.c_float),
                                     C.c_size_t]
+        L.pic_storage_order.argtypes = [V, C.c_int32, P(C.c_int32), P(C.c_uint64), C.c_size_t,
+                                        P(C.c_size_t)]
+        L.pic_batch_storage_order.argtypes = [V, C.c_int32, C.c_int32, P(C.c_int32), P(C.c_uint64),
+                                              C.c_size_t, P(C.c_size_t)]
         L.pic_profile.argtypes = [V, C.c_int]
         L.pic_kernel_times.argtypes = [V, P(C.c_double), P(C.c_uint64), P(C.c_char_p), C.c_int32]
         L.pic_free.argtypes = [V]
@@ -151,6 +156,8 @@ def lib():
         L.pic_adj_gradient.argtypes = [V, P(C.c_double), P(C.c_double)]
         L.pic_adj_schedule.argtypes = [V, P(C.c_int32), C.c_size_t]
         L.pic_adj_times.argtypes = [V, P(C.c_double), P(C.c_double)]
+        L.pic_adj_tape.argtypes = [V, C.c_int32, P(C.c_int32), P(C.c_float), P(C.c_float), P(C.c_float),
+                                   P(C.c_float), P(C.c_double), C.c_size_t, C.c_size_t]
         L.pic_adj_free.argtypes = [V]
         L.pic_adj_free.restype = None
         _lib = L
@@ -284,6 +291,11 @@ class Simulation:
                                    E.ctypes.data_as(C.POINTER(C.c_float)), n1), "pic_get_field")
         return {"R": R.reshape(2, n1), "rho": rho, "phi": phi, "E": E}
 
+    def storage_order(self, species: int):
+        """(cell, id) of every slot of the species' particle buffer in storage order (the arranger's
+        output); dead slots carry cell INT32_MIN."""
+        return _storage_order(lambda c, i, cap, n: lib().pic_storage_order(self._h, int(species), c, i, cap, n))
+
     def snapshot(self) -> bytes:
         need = C.c_size_t(0)
         _check(lib().pic_snapshot(self._h, None, 0, C.byref(need)), "pic_snapshot")
@@ -305,6 +317,16 @@ class Simulation:
         _check(lib().pic_kernel_times(self._h, ms, ln, names, PIC_KERNEL_KINDS), "pic_kernel_times")
         return {names[k].decode(): {"ms": ms[k], "launches": int(ln[k])}
                 for k in range(PIC_KERNEL_KINDS) if names[k] and names[k].decode()}
+
+
+def _storage_order(call):
+    n = C.c_size_t(0)
+    _check(call(None, None, 0, C.byref(n)), "storage order")
+    cell = np.empty(n.value, np.int32)
+    ids = np.empty(n.value, np.uint64)
+    _check(call(cell.ctypes.data_as(C.POINTER(C.c_int32)), ids.ctypes.data_as(C.POINTER(C.c_uint64)), n.value,
+                C.byref(n)), "storage order")
+    return cell, ids
 
 
 def blob_crc32(data) -> int:
@@ -435,6 +457,11 @@ class Batch:
                                          E.ctypes.data_as(C.POINTER(C.c_float)), n1), "pic_batch_get_field")
         return {"R": R.reshape(2, n1), "rho": rho, "phi": phi, "E": E}
 
+    def storage_order(self, k: int, species: int):
+        """(cell, id) in storage order of species ``species`` of run ``k`` (as Simulation.storage_order)."""
+        return _storage_order(lambda c, i, cap, n: lib().pic_batch_storage_order(self._h, int(k), int(species),
+                                                                                c, i, cap, n))
+
     def profile(self, enable: bool):
         _check(lib().pic_batch_profile(self._h, 1 if enable else 0), "pic_batch_profile")
 
@@ -509,6 +536,19 @@ class Adjoint:
         _check(lib().pic_adj_schedule(self._h, a.ctypes.data_as(C.POINTER(C.c_int32)), self.n), "pic_adj_schedule")
         return a
 
+    def tape(self, n: int):
+        """(cell, frac, v (np, 3), E^n) of the last recording forward after n steps (FP32 state as
+        recorded, FP64 node field)."""
+        N1 = int(self.params["ncells"]) + 1
+        cell = np.empty(self.n, np.int32)
+        fr, vx, vy, vz = (np.empty(self.n, np.float32) for _ in range(4))
+        E = np.empty(N1, np.float64)
+        f32 = C.POINTER(C.c_float)
+        _check(lib().pic_adj_tape(self._h, int(n), cell.ctypes.data_as(C.POINTER(C.c_int32)), fr.ctypes.data_as(f32),
+                                  vx.ctypes.data_as(f32), vy.ctypes.data_as(f32), vz.ctypes.data_as(f32),
+                                  E.ctypes.data_as(C.POINTER(C.c_double)), self.n, N1), "pic_adj_tape")
+        return cell, fr, np.stack([vx, vy, vz], 1), E
+
     def times(self):
         f, g = C.c_double(), C.c_double()
         _check(lib().pic_adj_times(self._h, C.byref(f), C.byref(g)), "pic_adj_times")
@@ -545,17 +585,32 @@ def field_noalloc(params: dict, cell0, frac0, cell1, frac1, stream=None):
     (R (2, N+1) int64, E (N+1,) float64).  The output tensors are allocated here by the caller
     side (torch); the library call itself allocates nothing.
     """
+    import torch
+
+    # the kernel reads frac_s[i] for every i < cell_s.numel(): refuse anything but matching,
+    # contiguous int32 / float32 tensors on one CUDA device before handing over raw pointers
+    pairs = ((cell0, frac0), (cell1, frac1))
+    if not all(isinstance(t, torch.Tensor) for pair in pairs for t in pair):
+        raise PicError(1, "pic_field_noalloc: cell_s and frac_s must be tensors")
+    if any(c.dim() != 1 or f.dim() != 1 or c.numel() != f.numel() for c, f in pairs):
+        raise PicError(1, "pic_field_noalloc: cell_s and frac_s must be 1-D and of equal length")
+    if any(c.dtype != torch.int32 or f.dtype != torch.float32 for c, f in pairs):
+        raise PicError(1, "pic_field_noalloc: cell_s must be int32 and frac_s float32")
+    dev = cell0.device
+    if any(not t.is_cuda or t.device != dev or not t.is_contiguous() for pair in pairs for t in pair):
+        raise PicError(1, "pic_field_noalloc: the inputs must be contiguous tensors on one CUDA device")
     torch = _torch()
     c = make_config(params)
     N = int(params["ncells"])
-    dev = cell0.device
     R = torch.empty((2, N + 1), dtype=torch.int64, device=dev)
     E = torch.empty(N + 1, dtype=torch.float64, device=dev)
     st = stream if stream is not None else torch.cuda.current_stream(dev)
-    _check(lib().pic_field_noalloc(C.byref(c), C.c_void_p(cell0.data_ptr()), C.c_void_p(frac0.data_ptr()),
-                                   cell0.numel(), C.c_void_p(cell1.data_ptr()), C.c_void_p(frac1.data_ptr()),
-                                   cell1.numel(), C.c_void_p(R.data_ptr()), C.c_void_p(E.data_ptr()),
-                                   C.c_void_p(st.cuda_stream)), "pic_field_noalloc")
+    # the library finds its fixed scratch on the current device: make it the tensors' device
+    with torch.cuda.device(dev):
+        _check(lib().pic_field_noalloc(C.byref(c), C.c_void_p(cell0.data_ptr()), C.c_void_p(frac0.data_ptr()),
+                                       cell0.numel(), C.c_void_p(cell1.data_ptr()), C.c_void_p(frac1.data_ptr()),
+                                       cell1.numel(), C.c_void_p(R.data_ptr()), C.c_void_p(E.data_ptr()),
+                                       C.c_void_p(st.cuda_stream)), "pic_field_noalloc")
     return R, E
 
 
