@@ -77,6 +77,7 @@ extern "C" int pic_field_noalloc(const pic_config* cfg, const int32_t* cell0, co
   if (cfg->ncells < 2 || cfg->ncells > kMaxCells) return PIC_EINVAL;  // beyond the fixed scratch
   if (!(cfg->L > 0) || cfg->ppc[0] < 1 || cfg->ppc[1] < 1) return PIC_EINVAL;
   if ((n0 && (!cell0 || !frac0)) || (n1 && (!cell1 || !frac1))) return PIC_EINVAL;
+  if (cfg->smooth_passes < 0 || cfg->smooth_passes > PIC_MAX_SMOOTH) return PIC_EINVAL;
   // integer-exact field only: small integer charges, as in the step's own solve
   PoissonParams F;
   std::memset(&F, 0, sizeof(F));
@@ -90,8 +91,12 @@ extern "C" int pic_field_noalloc(const pic_config* cfg, const int32_t* cell0, co
   const int N = cfg->ncells;
   const double dx = cfg->L / N;
   const double kappa = dx * dx * 2.3283064365386963e-10 * (double)g / ((double)cfg->ppc[0] * (double)cfg->ppc[1]);
-  F.e_in = kappa / (2.0 * N * dx);
-  F.e_wall = kappa / ((double)N * dx);
+  // smoothing leaves the net charge in units of 2^-(2 passes + 1) of the deposit unit, as in the
+  // step's own solve
+  const double unit = cfg->smooth_passes > 0 ? std::ldexp(1.0, -(2 * cfg->smooth_passes + 1)) : 1.0;
+  F.e_in = unit * kappa / (2.0 * N * dx);
+  F.e_wall = unit * kappa / ((double)N * dx);
+  F.smooth = cfg->smooth_passes;
   F.e_bias = (cfg->V_left - cfg->V_right) / ((double)N * dx);
   F.exact = 1;
   F.mode = 0;

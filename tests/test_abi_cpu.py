@@ -85,6 +85,33 @@ def test_init_rejects_bad_arguments_before_any_device_work(L):
     assert L.pic_poisson(None, 8, 1.0, 0.0, 0.0, None, None, None) == 1
 
 
+def test_no_alloc_entry_rejects_bad_arguments_before_any_device_work(L):
+    # the C entry point checks its configuration before it looks up its scratch or launches
+    R = C.c_void_p(16)
+    E = C.c_void_p(16)
+    for bad in (W.variant(W.SMALL_C2, ncells=65537, L=65537.0), W.variant(W.SMALL_C2, smooth_passes=5),
+                W.variant(W.SMALL_C2, charge=(-1.0, 1.5)), W.variant(W.SMALL_C2, ncells=1, L=1.0)):
+        c = pic.make_config(bad)
+        assert L.pic_field_noalloc(C.byref(c), None, None, 0, None, None, 0, R, E, None) == 1
+    c = pic.make_config(W.SMALL_C2)
+    assert L.pic_field_noalloc(C.byref(c), None, None, 4, None, None, 0, R, E, None) == 1  # n without arrays
+    assert L.pic_field_noalloc(C.byref(c), None, None, 0, None, None, 0, None, E, None) == 1
+
+
+def test_no_alloc_binding_refuses_mismatched_tensors_before_the_call():
+    # the binding hands raw pointers to a kernel that reads frac_s[i] for i < len(cell_s): a shorter
+    # frac tensor, other dtypes, views that are not contiguous or tensors off the GPU never reach it
+    import torch
+
+    c = torch.zeros(8, dtype=torch.int32)
+    f = torch.zeros(8, dtype=torch.float32)
+    for args in ((c, f[:4], c, f), (c, f, c[:4], f), (c.long(), f, c, f), (c, f.double(), c, f),
+                 (c.reshape(2, 4), f.reshape(2, 4), c, f), (c, f, c, f)):
+        with pytest.raises(pic.PicError) as e:
+            pic.field_noalloc(W.SMALL_C2, *args)
+        assert e.value.status == 1
+
+
 # ---- ensembles --------------------------------------------------------------------------------
 def test_batch_shapes_are_listed(L):
     names = pic.batch_variants()
