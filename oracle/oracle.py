@@ -142,6 +142,10 @@ def lib():
         L.orc_adj_forward.argtypes = [P(OrcConfig), C.c_int32, C.c_int, P(C.c_int32), P(C.c_double)]
         L.orc_adj_gradient.argtypes = [P(OrcConfig), C.c_int32, P(C.c_double), P(C.c_double),
                                        P(C.c_double), P(C.c_int32)]
+        L.orc_adj_trajectory.argtypes = [P(OrcConfig), C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double),
+                                         P(C.c_int32), P(C.c_double)]
+        L.orc_adj_gradient_from_tape.argtypes = [P(OrcConfig), C.c_int32, P(C.c_double), P(C.c_double),
+                                                 P(C.c_double), P(C.c_double), P(C.c_int32), P(C.c_double)]
         _lib = L
     return _lib
 
@@ -405,3 +409,43 @@ def adj_gradient(params: dict, steps: int, weights=(1.0, 0.0)):
     if rc != 0:
         raise RuntimeError(f"orc_adj_gradient failed: {rc}")
     return g, J, ab
+
+
+def adj_gradient_from_tape(params: dict, steps: int, weights, X, V, EN, absorb):
+    """The oracle's reverse sweep over a trajectory recorded elsewhere: X (steps+1, np) positions in
+    cell units, V (steps+1, np, 3) velocities, EN (steps+1, N+1) node fields, absorb (np,) the
+    schedule.  Returns grad d(w . J)/d(V_left, T_e) (2,)."""
+    c = make_config(params)
+    n = lib().orc_adj_particles(C.byref(c))
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    EN = np.ascontiguousarray(EN, dtype=np.float64)
+    ab = np.ascontiguousarray(absorb, dtype=np.int32)
+    if X.shape != (steps + 1, n) or V.shape != (steps + 1, n, 3) or EN.shape != (steps + 1, c.ncells + 1) \
+            or ab.shape != (n,):
+        raise ValueError("trajectory of the wrong shape")
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    g = np.zeros(2)
+    rc = lib().orc_adj_gradient_from_tape(C.byref(c), steps, _ptr(w, C.c_double), _ptr(X, C.c_double),
+                                          _ptr(V, C.c_double), _ptr(EN, C.c_double), _ptr(ab, C.c_int32),
+                                          _ptr(g, C.c_double))
+    if rc != 0:
+        raise RuntimeError(f"orc_adj_gradient_from_tape failed: {rc}")
+    return g
+
+
+def adj_trajectory(params: dict, steps: int):
+    """The oracle's recording forward with its trajectory: (X, V, EN, absorb, J) in the layout of
+    adj_gradient_from_tape."""
+    c = make_config(params)
+    n = lib().orc_adj_particles(C.byref(c))
+    X = np.empty((steps + 1, n))
+    V = np.empty((steps + 1, n, 3))
+    EN = np.empty((steps + 1, c.ncells + 1))
+    ab = np.zeros(n, np.int32)
+    J = np.zeros(2)
+    rc = lib().orc_adj_trajectory(C.byref(c), steps, _ptr(X, C.c_double), _ptr(V, C.c_double), _ptr(EN, C.c_double),
+                                  _ptr(ab, C.c_int32), _ptr(J, C.c_double))
+    if rc != 0:
+        raise RuntimeError(f"orc_adj_trajectory failed: {rc}")
+    return X, V, EN, ab, J

@@ -230,83 +230,109 @@ int orc_adj_forward(const orc_config* c, int32_t steps, int replay, int32_t* abs
   return forward(c, steps, replay, absorb, J, NULL, NULL, NULL);
 }
 
-int orc_adj_gradient(const orc_config* c, int32_t steps, const double wt[2], double grad[2], double J[2],
-                     int32_t* absorb) {
-  if (!valid_adj(c, steps) || !wt || !grad || !J || !absorb) return ORC_EINVAL;
+/* The reverse sweep over a stored trajectory (X, V, EN as forward() keeps it, absorb the schedule):
+ * grad = d(wt[0] J_flux + wt[1] J_fe) / d(V_left, T[0]). */
+static int reverse(const orc_config* c, int32_t steps, const double wt[2], const double* X, const double* V,
+                   const double* EN, const int32_t* absorb, double grad[2]) {
   adj_model m;
   adj_model_init(c, &m);
   const int32_t N = m.N;
   const size_t np = m.np, nn = (size_t)(N + 1);
-  double* X = (double*)malloc(sizeof(double) * (size_t)(steps + 1) * np);
-  double* V = (double*)malloc(sizeof(double) * (size_t)(steps + 1) * 3 * np);
-  double* EN = (double*)malloc(sizeof(double) * (size_t)(steps + 1) * nn);
   double* lx = (double*)calloc(np, sizeof(double));
   double* lv = (double*)calloc(3 * np, sizeof(double));
   double* mu = (double*)malloc(sizeof(double) * nn);
   double* mu_next = (double*)malloc(sizeof(double) * nn);
   double* rb = (double*)malloc(sizeof(double) * nn);
-  int rc = ORC_ENOMEM;
-  if (X && V && EN && lx && lv && mu && mu_next && rb) rc = forward(c, steps, 0, absorb, J, X, V, EN);
-  if (rc == ORC_OK) {
-    double gV = 0.0;
-    /* dJ/dE^T: the final field energy */
-    const double* ET = EN + (size_t)steps * nn;
-    for (int32_t j = 0; j <= N; ++j) mu[j] = wt[1] * ((j == 0 || j == N) ? 0.5 : 1.0) * ET[j] * m.dx;
-    for (int32_t n = steps - 1; n >= 0; --n) {
-      /* E^{n+1} = G rho^{n+1} + (V_L - V_R) / (N dx) */
-      for (int32_t j = 0; j <= N; ++j) gV += mu[j] / ((double)N * m.dx);
-      orc_field_adjoint(N, m.dx, mu, rb);
-      const double* x1 = X + (size_t)(n + 1) * np;
-      const double* v1 = V + (size_t)(n + 1) * 3 * np;
-      const double* x0 = X + (size_t)n * np;
-      const double* En = EN + (size_t)n * nn;
-      memset(mu_next, 0, sizeof(double) * nn);
-      for (size_t p = 0; p < np; ++p) {
-        if (absorb[p] <= n) continue; /* not alive after step n: nothing depends on its state */
-        const int s = p < m.n0 ? 0 : 1;
-        /* deposit of x^{n+1} */
-        int32_t k1;
-        double f1;
-        cic(N, x1[p], &k1, &f1);
-        lx[p] += m.q[s] * m.w[s] * (rb[k1 + 1] / vol(&m, k1 + 1) - rb[k1] / vol(&m, k1));
-        /* J_flux at step n */
-        if (s == 0) {
-          const double d = x1[p] - (double)(N - 1);
-          if (fabs(d) < 1.0) {
-            lx[p] += wt[0] * c->dt * m.w[0] * v1[3 * p] * (d > 0.0 ? -1.0 : (d < 0.0 ? 1.0 : 0.0));
-            lv[3 * p] += wt[0] * c->dt * m.w[0] * (1.0 - fabs(d));
-          }
-        }
-        if (c->frozen_mask & (1u << s)) continue; /* not pushed: x^{n+1} = x^n, v^{n+1} = v^n */
-        /* x^{n+1} = x^n + v_x^{n+1} dt / dx */
-        lv[3 * p] += lx[p] * c->dt / m.dx;
-        /* v^{n+1} = M v^n + (M + I) h e */
-        double* L = &lv[3 * p];
-        double ebar = 0.0;
-        if (c->field_mode == ORC_FIELD_SELF) {
-          for (int i = 0; i < 3; ++i) ebar += (m.M[s][i][0] + (i == 0 ? 1.0 : 0.0)) * L[i];
-          ebar *= m.h[s];
-          int32_t k0;
-          double f0;
-          cic(N, x0[p], &k0, &f0);
-          lx[p] += ebar * (En[k0 + 1] - En[k0]);
-          mu_next[k0] += ebar * (1.0 - f0);
-          mu_next[k0 + 1] += ebar * f0;
-        }
-        double Lt[3];
-        for (int k = 0; k < 3; ++k) Lt[k] = m.M[s][0][k] * L[0] + m.M[s][1][k] * L[1] + m.M[s][2][k] * L[2];
-        L[0] = Lt[0], L[1] = Lt[1], L[2] = Lt[2];
-      }
-      memcpy(mu, mu_next, sizeof(double) * nn);
-    }
-    /* E^0 = G rho^0 + bias; rho^0 does not depend on the parameters */
-    for (int32_t j = 0; j <= N; ++j) gV += mu[j] / ((double)N * m.dx);
-    double gT = 0.0;
-    for (size_t p = 0; p < m.n0; ++p)
-      for (int k = 0; k < 3; ++k) gT += lv[3 * p + k] * V[3 * p + k];
-    grad[0] = gV;
-    grad[1] = gT / (2.0 * c->T[0]);
+  if (!lx || !lv || !mu || !mu_next || !rb) {
+    free(lx), free(lv), free(mu), free(mu_next), free(rb);
+    return ORC_ENOMEM;
   }
-  free(X), free(V), free(EN), free(lx), free(lv), free(mu), free(mu_next), free(rb);
+  double gV = 0.0;
+  /* dJ/dE^T: the final field energy */
+  const double* ET = EN + (size_t)steps * nn;
+  for (int32_t j = 0; j <= N; ++j) mu[j] = wt[1] * ((j == 0 || j == N) ? 0.5 : 1.0) * ET[j] * m.dx;
+  for (int32_t n = steps - 1; n >= 0; --n) {
+    /* E^{n+1} = G rho^{n+1} + (V_L - V_R) / (N dx) */
+    for (int32_t j = 0; j <= N; ++j) gV += mu[j] / ((double)N * m.dx);
+    orc_field_adjoint(N, m.dx, mu, rb);
+    const double* x1 = X + (size_t)(n + 1) * np;
+    const double* v1 = V + (size_t)(n + 1) * 3 * np;
+    const double* x0 = X + (size_t)n * np;
+    const double* En = EN + (size_t)n * nn;
+    memset(mu_next, 0, sizeof(double) * nn);
+    for (size_t p = 0; p < np; ++p) {
+      if (absorb[p] <= n) continue; /* not alive after step n: nothing depends on its state */
+      const int s = p < m.n0 ? 0 : 1;
+      /* deposit of x^{n+1} */
+      int32_t k1;
+      double f1;
+      cic(N, x1[p], &k1, &f1);
+      lx[p] += m.q[s] * m.w[s] * (rb[k1 + 1] / vol(&m, k1 + 1) - rb[k1] / vol(&m, k1));
+      /* J_flux at step n */
+      if (s == 0) {
+        const double d = x1[p] - (double)(N - 1);
+        if (fabs(d) < 1.0) {
+          lx[p] += wt[0] * c->dt * m.w[0] * v1[3 * p] * (d > 0.0 ? -1.0 : (d < 0.0 ? 1.0 : 0.0));
+          lv[3 * p] += wt[0] * c->dt * m.w[0] * (1.0 - fabs(d));
+        }
+      }
+      if (c->frozen_mask & (1u << s)) continue; /* not pushed: x^{n+1} = x^n, v^{n+1} = v^n */
+      /* x^{n+1} = x^n + v_x^{n+1} dt / dx */
+      lv[3 * p] += lx[p] * c->dt / m.dx;
+      /* v^{n+1} = M v^n + (M + I) h e */
+      double* L = &lv[3 * p];
+      double ebar = 0.0;
+      if (c->field_mode == ORC_FIELD_SELF) {
+        for (int i = 0; i < 3; ++i) ebar += (m.M[s][i][0] + (i == 0 ? 1.0 : 0.0)) * L[i];
+        ebar *= m.h[s];
+        int32_t k0;
+        double f0;
+        cic(N, x0[p], &k0, &f0);
+        lx[p] += ebar * (En[k0 + 1] - En[k0]);
+        mu_next[k0] += ebar * (1.0 - f0);
+        mu_next[k0 + 1] += ebar * f0;
+      }
+      double Lt[3];
+      for (int k = 0; k < 3; ++k) Lt[k] = m.M[s][0][k] * L[0] + m.M[s][1][k] * L[1] + m.M[s][2][k] * L[2];
+      L[0] = Lt[0], L[1] = Lt[1], L[2] = Lt[2];
+    }
+    memcpy(mu, mu_next, sizeof(double) * nn);
+  }
+  /* E^0 = G rho^0 + bias; rho^0 does not depend on the parameters */
+  for (int32_t j = 0; j <= N; ++j) gV += mu[j] / ((double)N * m.dx);
+  double gT = 0.0;
+  for (size_t p = 0; p < m.n0; ++p)
+    for (int k = 0; k < 3; ++k) gT += lv[3 * p + k] * V[3 * p + k];
+  grad[0] = gV;
+  grad[1] = gT / (2.0 * c->T[0]);
+  free(lx), free(lv), free(mu), free(mu_next), free(rb);
+  return ORC_OK;
+}
+
+int orc_adj_gradient(const orc_config* c, int32_t steps, const double wt[2], double grad[2], double J[2],
+                     int32_t* absorb) {
+  if (!valid_adj(c, steps) || !wt || !grad || !J || !absorb) return ORC_EINVAL;
+  adj_model m;
+  adj_model_init(c, &m);
+  const size_t np = m.np, nn = (size_t)(m.N + 1);
+  double* X = (double*)malloc(sizeof(double) * (size_t)(steps + 1) * np);
+  double* V = (double*)malloc(sizeof(double) * (size_t)(steps + 1) * 3 * np);
+  double* EN = (double*)malloc(sizeof(double) * (size_t)(steps + 1) * nn);
+  int rc = ORC_ENOMEM;
+  if (X && V && EN) rc = forward(c, steps, 0, absorb, J, X, V, EN);
+  if (rc == ORC_OK) rc = reverse(c, steps, wt, X, V, EN, absorb, grad);
+  free(X), free(V), free(EN);
   return rc;
+}
+
+int orc_adj_trajectory(const orc_config* c, int32_t steps, double* X, double* V, double* EN, int32_t* absorb,
+                       double J[2]) {
+  if (!valid_adj(c, steps) || !X || !V || !EN || !absorb || !J) return ORC_EINVAL;
+  return forward(c, steps, 0, absorb, J, X, V, EN);
+}
+
+int orc_adj_gradient_from_tape(const orc_config* c, int32_t steps, const double wt[2], const double* X,
+                               const double* V, const double* EN, const int32_t* absorb, double grad[2]) {
+  if (!valid_adj(c, steps) || !wt || !grad || !X || !V || !EN || !absorb) return ORC_EINVAL;
+  return reverse(c, steps, wt, X, V, EN, absorb, grad);
 }

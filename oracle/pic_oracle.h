@@ -200,6 +200,16 @@ int orc_adj_forward(const orc_config* cfg, int32_t steps, int replay, int32_t* a
  * Also returns J and the recorded schedule. */
 int orc_adj_gradient(const orc_config* cfg, int32_t steps, const double w[2], double grad[2], double J[2],
                      int32_t* absorb);
+/* The same reverse sweep over a trajectory given by the caller instead of this oracle's own forward
+ * (to hold another implementation's reverse sweep to this one on that implementation's recorded
+ * forward): X[(steps+1) np] positions in cell units, V[(steps+1) 3 np] velocities, EN[(steps+1)(N+1)]
+ * node fields (E^n: the field the push of step n uses; E^steps: the final field), absorb[np] the
+ * schedule; particles electrons then ions in load order. */
+int orc_adj_gradient_from_tape(const orc_config* cfg, int32_t steps, const double w[2], const double* X,
+                               const double* V, const double* EN, const int32_t* absorb, double grad[2]);
+/* The recording forward with its trajectory kept, in the layout orc_adj_gradient_from_tape takes. */
+int orc_adj_trajectory(const orc_config* cfg, int32_t steps, double* X, double* V, double* EN, int32_t* absorb,
+                       double J[2]);
 
 #ifdef __cplusplus
 }

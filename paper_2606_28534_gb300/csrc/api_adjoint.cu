@@ -441,6 +441,39 @@ int pic_adj_schedule(pic_adj* a, int32_t* absorb, size_t n) {
   PIC_ENTRY_CATCH
 }
 
+int pic_adj_tape(pic_adj* a, int32_t n, int32_t* cell, float* frac, float* vx, float* vy, float* vz, double* E,
+                 size_t np, size_t nnodes) {
+  PIC_ENTRY_TRY
+  if (!a || !a->recorded || n < 0 || n > a->T || np != (size_t)a->np || nnodes != (size_t)a->N + 1) return PIC_EINVAL;
+  pic_config c;
+  const Phys ph = physics(a, a->rec_VL, a->rec_Te, &c);
+  // the state after n steps: recomputed from its segment's checkpoint with the recorded fields (the
+  // same kernel and inputs as the recording forward, so the same bits)
+  const int seg = std::min(n / a->K, a->nseg - 1);
+  const int n0 = seg * a->K;
+  int rc = copy_state(a, a->tape[0], a->ckpt[seg]);
+  if (rc != PIC_OK) return rc;
+  AdjStep S = step_params(a, ph, c);
+  S.mode = 2;
+  for (int k = n0; k < n; ++k) {
+    S.src = a->tape[k - n0];
+    S.dst = a->tape[k + 1 - n0];
+    S.E = a->Etape + (size_t)k * nnodes;
+    S.step = k;
+    CKA(launch_adj_push(S, a->max_grid, a->st));
+  }
+  CKA(cudaStreamSynchronize(a->st));
+  const AdjState& t = a->tape[n - n0];
+  if (cell) CKA(cudaMemcpy(cell, t.cell, 4 * np, cudaMemcpyDeviceToHost));
+  if (frac) CKA(cudaMemcpy(frac, t.frac, 4 * np, cudaMemcpyDeviceToHost));
+  if (vx) CKA(cudaMemcpy(vx, t.vx, 4 * np, cudaMemcpyDeviceToHost));
+  if (vy) CKA(cudaMemcpy(vy, t.vy, 4 * np, cudaMemcpyDeviceToHost));
+  if (vz) CKA(cudaMemcpy(vz, t.vz, 4 * np, cudaMemcpyDeviceToHost));
+  if (E) CKA(cudaMemcpy(E, a->Etape + (size_t)n * nnodes, sizeof(double) * nnodes, cudaMemcpyDeviceToHost));
+  return PIC_OK;
+  PIC_ENTRY_CATCH
+}
+
 int pic_adj_times(pic_adj* a, double* forward_ms, double* gradient_ms) {
   PIC_ENTRY_TRY
   if (!a) return PIC_EINVAL;

@@ -15,6 +15,10 @@ What is compared, and why these tolerances:
   to the oracle's FP64 secant at the same h, within the FP32 forward error divided by h.
 * Checkpoint interval: any interval gives the same gradient (the recomputed states are bit-identical;
   only the order of FP64 atomic sums differs): 1e-12 relative.
+* The reverse sweep alone: the oracle's reverse sweep run over the GPU's own recorded trajectory
+  (its FP32 states, FP64 node fields and schedule, read back with pic_adj_tape) must give the GPU's
+  gradient to 1e-9 relative per component.  That separates an error of the reverse sweep from the
+  FP32-vs-FP64 trajectory difference the comparisons above allow for.
 """
 import numpy as np
 import pytest
@@ -150,4 +154,38 @@ def test_config5_full_size_against_the_oracle_and_finite_differences():
     # error at the base point, at least 1e-7 of J, stands for the error at theta +- h)
     tol = 5 * np.maximum(np.abs(J - Jo), 1e-7 * np.abs(Jo))[:, None] / h
     assert np.all(np.abs(fg - fo) <= tol), (fg, fo, tol)
+    a.close()
+
+
+def _gpu_tape(a, p, steps):
+    n = a.n
+    X = np.empty((steps + 1, n))
+    V = np.empty((steps + 1, n, 3))
+    EN = np.empty((steps + 1, p["ncells"] + 1))
+    for k in range(steps + 1):
+        cell, fr, v, E = a.tape(k)
+        X[k] = cell + fr.astype(np.float64)
+        V[k] = v
+        EN[k] = E
+    return X, V, EN
+
+
+@pytest.mark.parametrize("case", ["config5", "magnetised", "biased_right", "frozen_ions"])
+def test_reverse_sweep_equals_the_oracles_on_the_gpu_trajectory(case):
+    p, steps, K = {"config5": (W.variant(W.C5, V_left=-1.0), W.C5_STEPS, 20),
+                   "magnetised": (W.variant(SMALL, B=0.5, B_angle_deg=30.0), 80, 20),
+                   "biased_right": (W.variant(SMALL, V_right=0.6, T=(1.4, 0.1)), 80, 20),
+                   "frozen_ions": (W.variant(SMALL, frozen_mask=2), 80, 20)}[case]
+    a = pic.Adjoint(p, steps, K)
+    a.forward(p["V_left"], p["T"][0])
+    absorb = a.schedule()
+    X, V, EN = _gpu_tape(a, p, steps)
+    # the tape is the recorded forward: its state at a checkpoint step is the checkpoint itself, and
+    # the particles the schedule keeps stay inside the walls
+    alive = absorb > steps - 1
+    assert (X[steps][alive] >= 0).all() and (X[steps][alive] < p["ncells"]).all()
+    for w in ((1.0, 0.0), (0.0, 1.0)):
+        g = np.array(a.gradient(*w))
+        go = O.adj_gradient_from_tape(p, steps, w, X, V, EN, absorb)
+        assert np.all(np.abs(g - go) <= 1e-9 * np.abs(go) + 1e-14 * np.abs(go).max()), (case, w, g, go)
     a.close()

@@ -152,3 +152,19 @@ def test_bias_is_a_uniform_field():
     O.lib().orc_efield(N, dx, O._ptr(phi1, O.C.c_double), O._ptr(rho, O.C.c_double), O._ptr(E1, O.C.c_double))
     assert np.allclose(E1 - E0, -3.0 / (N * dx), rtol=0, atol=1e-12)
     assert math.isclose(float((E1 - E0).mean()), -3.0 / N, rel_tol=1e-12)
+
+
+def test_reverse_sweep_over_a_given_tape_is_the_oracles_own():
+    # the entry that reverses a trajectory recorded elsewhere runs the same sweep: fed the oracle's
+    # own recording forward it returns the oracle's gradient bit for bit, and a perturbed tape moves it
+    p = W.variant(W.C5, ncells=24, L=24.0, ppc=(9, 7), V_left=-0.8, B=0.4, B_angle_deg=50.0)
+    steps = 30
+    X, V, EN, ab, J = O.adj_trajectory(p, steps)
+    for w in ((1.0, 0.0), (0.0, 1.0), (0.7, -1.3)):
+        g, J2, ab2 = O.adj_gradient(p, steps, w)
+        assert np.array_equal(ab, ab2) and np.array_equal(J, J2)
+        assert np.array_equal(O.adj_gradient_from_tape(p, steps, w, X, V, EN, ab), g)
+    V2 = V.copy()
+    V2[0] *= 1.01
+    assert not np.array_equal(O.adj_gradient_from_tape(p, steps, (0.0, 1.0), X, V2, EN, ab),
+                              O.adj_gradient(p, steps, (0.0, 1.0))[0])
