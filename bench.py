@@ -36,14 +36,19 @@ if ROOT not in sys.path:
 from paper_2606_28534_gb300 import workloads as W  # noqa: E402
 
 METRIC = "particle-steps/s & HBM roofline %, FP32/batched vs plain FP64 grid, 1 GB300"
-BYTES_STEP_KERNEL = 48  # algorithmic bytes per particle per step kernel: 28 read + 20 written
-BYTES_SCATTER_EXTRA = 8  # the step after a sort writes each particle to a new slot: + its 8-byte id
+# algorithmic bytes per particle of the ordinary step kernel: cell word, fraction and velocity
+# read (20 B) and written (20 B); the id is read only by the ~1 % of particles whose null-collision
+# countdown expires (from L2, just written), which is left out
+BYTES_STEP_KERNEL = 40
+# the step after a sort reads and writes each particle with its id, to its sorted slot: 28 + 28 B
+BYTES_SCATTER_KERNEL = 56
 # DRAM bytes per particle of one launch, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of these kernels on the 12.6M-particle profiling case (c3p), scaled by
-# particles to a full launch: the ordinary step and the step after a sort
-TRAFFIC_STEP, TRAFFIC_SCATTER = 49.08, 57.14
+# particles to a full launch: the ordinary step and the step after a sort (None: not captured for
+# the kernels as they stand)
+TRAFFIC_STEP, TRAFFIC_SCATTER = None, None
 # the same for the ensemble's particle step (ncu on a 16-run ensemble of config 4's distribution)
-TRAFFIC_BSTEP = 49.52
+TRAFFIC_BSTEP = None
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
 # (8 B); on sort steps it writes each survivor, compacted, into the other buffer instead (28 B)
 BYTES_NEUTRAL_KERNEL, BYTES_NEUTRAL_COMPACT = 36, 56
@@ -280,7 +285,7 @@ def batched(args, torch, pic, peak: float) -> dict:
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "kernel": "k_bstep32", "bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": step_ms,
-                     "traffic": TRAFFIC_BSTEP * kps / max(1, kt["step"]["launches"])},
+                     "traffic": TRAFFIC_BSTEP * kps / max(1, kt["step"]["launches"]) if TRAFFIC_BSTEP else None},
         "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in kt.items()
                     if v["launches"]},
     }
@@ -536,21 +541,22 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
     value, ms_max = whole_job(ps, ms, ranks)
 
     peak, peak_kind = _peaks()
-    # the dominant kernel: the ordinary step (48 B per particle); the step after each sort, which
-    # also moves every particle to its sorted slot (56 B per particle), is reported beside it
+    # the dominant kernel: the ordinary step (40 B per particle); the step after each sort, which
+    # also moves every particle with its id to its sorted slot (56 B per particle), is reported
+    # beside it
     n_launch = kt["step"]["launches"] + kt["step_scatter"]["launches"]
     per_launch_particles = ps / max(1, n_launch)
     step_ms = kt["step"]["ms"] / max(1, kt["step"]["launches"])
     bytes_per_launch = BYTES_STEP_KERNEL * per_launch_particles
-    traffic = TRAFFIC_STEP * per_launch_particles
+    traffic = TRAFFIC_STEP * per_launch_particles if TRAFFIC_STEP else None
     achieved = bytes_per_launch / (step_ms / 1000.0) / 1e9
     sc_ms = kt["step_scatter"]["ms"] / max(1, kt["step_scatter"]["launches"])
-    sc_bytes = (BYTES_STEP_KERNEL + BYTES_SCATTER_EXTRA) * per_launch_particles
+    sc_bytes = BYTES_SCATTER_KERNEL * per_launch_particles
     scatter_step = {"kernel": "k_step32 (scatter)", "launches": kt["step_scatter"]["launches"],
                     "avg_launch_ms": sc_ms, "bytes_per_launch": sc_bytes,
                     "achieved": sc_bytes / (sc_ms / 1000.0) / 1e9 if sc_ms else None,
                     "frac": sc_bytes / (sc_ms / 1000.0) / 1e9 / peak if sc_ms else None,
-                    "traffic": TRAFFIC_SCATTER * per_launch_particles}
+                    "traffic": TRAFFIC_SCATTER * per_launch_particles if TRAFFIC_SCATTER else None}
     kernel_shares = {k: round(v["ms"] / max(1e-9, sum(x["ms"] for x in kt.values())), 4)
                      for k, v in kt.items() if v["launches"]}
 

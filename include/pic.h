@@ -189,6 +189,47 @@ int pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, voi
  * launch fails.  Device-side errors surface at the next synchronising call. */
 int pic_step(pic_handle* h, int32_t n);
 
+/* ---- particle decomposition of one simulation ------------------------------------------------
+ *
+ * The paper runs one simulation over many GPUs by MPI domain decomposition with particle load
+ * balancing (Sec. 4.1, "Particle Load Balancing"; one rank per GPU).  These calls split one
+ * simulation by particles instead: every part holds a subset of the particles over the whole grid
+ * (its own handle, typically one per GPU), and the parts exchange one thing per step, their int64
+ * node deposits, whose sum is exact and independent of the order of summation -- so a decomposed
+ * run computes, particle for particle and bit for bit, what one handle holding every particle
+ * computes.  Each part then solves the same field from the same total.  Per step:
+ *     pic_step_begin(h, R_local);      // the particle phase; R_local = this part's node deposits
+ *     R_total = sum over parts of R_local   (caller: an all-reduce of 2 (N+1) int64, e.g. NCCL)
+ *     pic_step_end(h, R_total);        // field solve of R_total, bookkeeping, sort on sort steps
+ * Set-up: pic_init (or pic_restore) with the same configuration on every part, pic_keep_subset,
+ * then pic_local_deposit, the same all-reduce, and pic_solve_deposit.  Requirements: PIC_FP32,
+ * integer charges (the exact solve), no pair source and no tracked neutrals (their new particles'
+ * ids would not be unique across parts); else PIC_EINVAL.  R_local and R_total are device pointers
+ * (caller-owned, 2 (N+1) int64 each: species 0 then species 1, 2^-32 particle units), used on the
+ * handle's stream.  After a decomposed step the grid quantities (R, rho, phi, E, field energy, net
+ * charge) are the whole simulation's; particle counts, counters and kinetic energies are this
+ * part's (the parts' counters add up to the whole's).  Plain pic_step refuses a handle with an
+ * open step (PIC_EINVAL). */
+
+/* Keep the particles with id % nparts == part (0 <= part < nparts), drop the others, redeposit,
+ * re-solve (this part's own deposit until pic_solve_deposit) and sort.  Part 0 keeps the cumulative
+ * counters and sums; the other parts restart them from zero.  Synchronises the stream. */
+int pic_keep_subset(pic_handle* h, uint32_t part, uint32_t nparts);
+
+/* R_local = the node deposits of this part's particles as they stand (no step open). */
+int pic_local_deposit(pic_handle* h, int64_t* R_local);
+
+/* Replace the field by the solve of the deposits R_total (no step open); nothing else changes. */
+int pic_solve_deposit(pic_handle* h, const int64_t* R_total);
+
+/* The particle phase of one step (gather, push, walls, null-collision MC, deposit) and this part's
+ * node deposits into R_local; the step stays open until pic_step_end. */
+int pic_step_begin(pic_handle* h, int64_t* R_local);
+
+/* Close the open step with the total deposits R_total: field solve, bookkeeping, sort scan on sort
+ * steps; the step count advances.  PIC_EINVAL without an open step. */
+int pic_step_end(pic_handle* h, const int64_t* R_total);
+
 /* Kinetic-energy diagnostics (pic_diag_t.ke).  every > 0: the FP32 step kernel sums the kinetic
  * energy of the particles it leaves alive on every every-th step (counted from pic_init /
  * pic_restore), so that pic_diag right after such a step costs no extra pass; every == 0 (the

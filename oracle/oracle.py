@@ -113,8 +113,8 @@ def lib():
         L.orc_free.restype = None
         L.orc_step.argtypes = [C.c_void_p, C.c_int32]
         L.orc_step_sample.argtypes = [P(OrcConfig), C.c_int, C.c_uint64, P(C.c_double), C.c_size_t,
-                                      P(C.c_double), P(C.c_double), P(C.c_uint64), P(C.c_double),
-                                      P(C.c_double), P(C.c_int32)]
+                                      P(C.c_double), P(C.c_double), P(C.c_uint64), P(C.c_uint32),
+                                      P(C.c_double), P(C.c_double), P(C.c_uint32), P(C.c_int32)]
         L.orc_diag.argtypes = [C.c_void_p, P(OrcDiag)]
         L.orc_fields.argtypes = [C.c_void_p, P(C.c_int64), P(C.c_double), P(C.c_double),
                                  P(C.c_double)]
@@ -125,6 +125,7 @@ def lib():
         L.orc_count.restype = C.c_uint64
         L.orc_particles.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double),
                                     P(C.c_uint64)]
+        L.orc_countdown.argtypes = [C.c_void_p, C.c_int, P(C.c_uint32)]
         L.orc_snapshot.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, P(C.c_size_t)]
         L.orc_restore.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
         L.orc_config_hash.argtypes = [P(OrcConfig)]
@@ -207,30 +208,33 @@ def boris(qm: float, dt: float, E, B, v) -> np.ndarray:
     return v
 
 
-def step_sample(params: dict, species: int, step: int, E, x, v, ids) -> tuple:
+def step_sample(params: dict, species: int, step: int, E, x, v, ids, nk) -> tuple:
     """One step of the given particles under the node field E (N + 1 values), one by one: the
-    mover, the wall test and the null-collision MC of the step (orc_step_sample).  Returns the new
-    positions (cells), velocities (n x 3) and flags (1 absorbed, 2 candidate, 4 near-threshold,
+    mover, the wall test and the null-collision MC of the step (orc_step_sample).  nk: the
+    particles' null-collision countdown pairs (k | c << 12).  Returns the new positions (cells),
+    velocities (n x 3), countdown pairs and flags (1 absorbed, 2 candidate, 4 near-threshold,
     8 ionization)."""
     c = make_config(params)
     x = np.ascontiguousarray(x, dtype=np.float64)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
     ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    nk = np.ascontiguousarray(nk, dtype=np.uint32)
     E = np.ascontiguousarray(E, dtype=np.float64)
     n = x.size
-    if v.shape[0] != n or ids.size != n:
-        raise ValueError("x, v and ids describe different numbers of particles")
+    if v.shape[0] != n or ids.size != n or nk.size != n:
+        raise ValueError("x, v, ids and nk describe different numbers of particles")
     if E.size != params["ncells"] + 1:
         raise ValueError("E holds N + 1 node values")
     xo = np.empty(n)
     vo = np.empty((n, 3))
+    nko = np.empty(n, np.uint32)
     flags = np.empty(n, np.int32)
     rc = lib().orc_step_sample(C.byref(c), int(species), int(step), _ptr(E, C.c_double), n, _ptr(x, C.c_double),
-                               _ptr(v, C.c_double), _ptr(ids, C.c_uint64), _ptr(xo, C.c_double),
-                               _ptr(vo, C.c_double), _ptr(flags, C.c_int32))
+                               _ptr(v, C.c_double), _ptr(ids, C.c_uint64), _ptr(nk, C.c_uint32), _ptr(xo, C.c_double),
+                               _ptr(vo, C.c_double), _ptr(nko, C.c_uint32), _ptr(flags, C.c_int32))
     if rc != 0:
         raise ValueError(f"orc_step_sample failed ({rc})")
-    return xo, vo, flags
+    return xo, vo, nko, flags
 
 
 def nu_max(params: dict):
@@ -345,6 +349,12 @@ class OracleSim:
         lib().orc_particles(self._h, s, _ptr(x, C.c_double), _ptr(v, C.c_double),
                             _ptr(ids, C.c_uint64))
         return x, v, ids
+
+    def countdown(self, s: int) -> np.ndarray:
+        """The null-collision countdown pairs (k | c << 12) of species s, in storage order."""
+        nk = np.empty(self.count(s), np.uint32)
+        lib().orc_countdown(self._h, s, _ptr(nk, C.c_uint32))
+        return nk
 
     def snapshot(self) -> bytes:
         need = C.c_size_t(0)

@@ -23,6 +23,19 @@
  *   R11 child ids are Philox words of (parent id, step, CHILD channel).
  *   R12 CIC deposit in int64 fixed point: W_r = rint(f 2^32), W_l = 2^32 - W_r.
  *   R13 source: one (e, ion) pair per ion absorbed this step, uniform in [0, x1), Maxwellian.
+ *   R17 null-collision candidates by geometric countdown (replaces a Bernoulli(P_null) draw per
+ *       particle and step; the same process in law, since P_null is constant per species): a
+ *       particle of a species that takes the test (collisions on, not frozen, P_null > 0) carries
+ *       a countdown k in 1..4095 and a flag c.  G(w), from one Philox word w: u = (w >> 8) 2^-24,
+ *       r = log(1 - u) / log1p(-P_null) in FP64, K = 1 + floor(r); (k, c) = (K, 1) if K <= 4095,
+ *       else (4095, 0).  A particle created at step s (the load at s = 0, births, source pairs, the
+ *       products of a neutral's ionization) takes G(word 0 of Philox(id, s, INIT, 2)).  In each
+ *       step in which it is pushed and stays inside, k -= 1; at k = 0 it is a candidate when
+ *       c = 1, and in either case takes G(word 0 of Philox(id, step, COLL, 0)), whose words 1..3
+ *       the collision uses as before.  A draw with r within 1e-9 max(1, r) of an integer is
+ *       counted as near-threshold.  In a snapshot the pair rides in bits 18..30 of the cell word
+ *       (cell | k << 18 | c << 30; 0 there means "not drawn": the restore draws it as at creation
+ *       at the blob's step).
  *
  * The D+/e/D sheath physics (Table 3: D+ ions recycled into D neutrals at the walls; Sec. 2:
  * density smoothing), all off unless the configuration asks for it:
@@ -52,6 +65,9 @@
 #endif
 
 #define TWO32 4294967296.0
+#define NEXT_KMAX 4095u        /* largest countdown (R17) */
+#define NEXT_CAND (1u << 12)   /* flag: the expiry is a null-collision candidate */
+#define CELL_BITS 18           /* the snapshot's cell word: cell | next << CELL_BITS */
 #define ORC_PI 3.14159265358979323846
 #define MAX_THREADS 256
 
@@ -213,6 +229,7 @@ void orc_nu_max(const orc_config* c, float nu_max[2], float p_null[2]) {
 typedef struct {
   double *x, *vx, *vy, *vz;
   uint64_t* id;
+  uint32_t* nk; /* R17: countdown k | flag c << 12 (0: the species takes no null-collision test) */
   size_t n, cap;
 } orc_species;
 
@@ -238,6 +255,7 @@ struct orc_sim {
   int32_t N;
   double dx, w[2], qm[2], Bv[3];
   float nu_max[2], p_null[2];
+  int mcc[2]; /* species s takes the null-collision test (R17) */
   orc_species sp[2];
   orc_species nt; /* tracked neutrals (N1) */
   int64_t* R[2];
@@ -265,18 +283,21 @@ static int sp_reserve(orc_species* s, size_t cap) {
   if (c) s->vz = c;
   uint64_t* d = (uint64_t*)realloc(s->id, nc * sizeof(uint64_t));
   if (d) s->id = d;
-  if (!x || !a || !b || !c || !d) return ORC_ENOMEM;
+  uint32_t* e = (uint32_t*)realloc(s->nk, nc * sizeof(uint32_t));
+  if (e) s->nk = e;
+  if (!x || !a || !b || !c || !d || !e) return ORC_ENOMEM;
   s->cap = nc;
   return ORC_OK;
 }
 
-static int sp_push_back(orc_species* s, double x, const double v[3], uint64_t id) {
+static int sp_push_back(orc_species* s, double x, const double v[3], uint64_t id, uint32_t nk) {
   if (s->n == s->cap && sp_reserve(s, s->n + 1) != ORC_OK) return ORC_ENOMEM;
   s->x[s->n] = x;
   s->vx[s->n] = v[0];
   s->vy[s->n] = v[1];
   s->vz[s->n] = v[2];
   s->id[s->n] = id;
+  s->nk[s->n] = nk;
   s->n++;
   return ORC_OK;
 }
@@ -392,6 +413,9 @@ static int sort_species(orc_species* p, int32_t N) {
   }
   for (size_t k = 0; k < n; ++k) tid[k] = p->id[perm[k]];
   memcpy(p->id, tid, n * sizeof(uint64_t));
+  uint32_t* tk = (uint32_t*)tid; /* reuse: n 32-bit words fit in n 64-bit ones */
+  for (size_t k = 0; k < n; ++k) tk[k] = p->nk[perm[k]];
+  memcpy(p->nk, tk, n * sizeof(uint32_t));
   free(cnt);
   free(perm);
   free(tmp);
@@ -452,6 +476,25 @@ void orc_load_particle(const orc_config* c, int sp, uint64_t i, double* xo, doub
   *ido = id;
 }
 
+/* R17: the countdown pair G(w) drawn from one Philox word. */
+static uint32_t geometric_next(float p_null, uint32_t w, uint64_t* near) {
+  const double v = 1.0 - u01(w); /* (0, 1] */
+  const double r = log(v) / log1p(-(double)p_null);
+  const double fl = floor(r);
+  const double tol = 1e-9 * fmax(1.0, r);
+  if (near && r > 0.0 && (r - fl < tol || fl + 1.0 - r < tol)) (*near)++;
+  if (fl >= (double)NEXT_KMAX) return NEXT_KMAX; /* K > 4095: wait 4095 steps, then draw again */
+  return ((uint32_t)fl + 1u) | NEXT_CAND;
+}
+
+/* The countdown of a particle of species sp created in step `step` (R17). */
+static uint32_t creation_next(const orc_sim* s, int sp, uint64_t id, uint64_t step) {
+  if (!s->mcc[sp]) return 0u;
+  uint32_t w[4];
+  draw(id, s->cfg.seed, step, ORC_CH_INIT, 2, w);
+  return geometric_next(s->p_null[sp], w[0], NULL);
+}
+
 static int load(orc_sim* s) {
   const orc_config* c = &s->cfg;
   for (int sp = 0; sp < 2; ++sp) {
@@ -464,6 +507,7 @@ static int load(orc_sim* s) {
       p->vx[i] = v[0];
       p->vy[i] = v[1];
       p->vz[i] = v[2];
+      p->nk[i] = creation_next(s, sp, p->id[i], 0);
     }
     p->n = np;
   }
@@ -477,6 +521,7 @@ static int load(orc_sim* s) {
       p->vx[i] = v[0];
       p->vy[i] = v[1];
       p->vz[i] = v[2];
+      p->nk[i] = 0u;
     }
     p->n = np;
   }
@@ -496,6 +541,11 @@ static void derive(orc_sim* s) {
   s->Bv[1] = c->B * sin(th);
   s->Bv[2] = 0.0;
   orc_nu_max(c, s->nu_max, s->p_null);
+  for (int sp = 0; sp < 2; ++sp) {
+    const int on = (sp == 0) ? ((c->coll_mask & (ORC_COLL_EL | ORC_COLL_EX | ORC_COLL_IZ)) != 0)
+                             : ((c->coll_mask & ORC_COLL_CX) != 0);
+    s->mcc[sp] = on && !(c->frozen_mask & (1u << sp)) && s->p_null[sp] > 0.0f;
+  }
 }
 
 orc_sim* orc_create(const orc_config* cfg, int* err) {
@@ -543,6 +593,7 @@ void orc_free(orc_sim* s) {
     free(s->sp[sp].vy);
     free(s->sp[sp].vz);
     free(s->sp[sp].id);
+    free(s->sp[sp].nk);
     free(s->R[sp]);
   }
   free(s->nt.x);
@@ -550,6 +601,7 @@ void orc_free(orc_sim* s) {
   free(s->nt.vy);
   free(s->nt.vz);
   free(s->nt.id);
+  free(s->nt.nk);
   free(s->rho);
   free(s->phi);
   free(s->E);
@@ -560,12 +612,9 @@ void orc_free(orc_sim* s) {
 /* ------------------------------------------------------------------------------------------ */
 /* Monte Carlo collision of one electron (null-collision method; Sec. 2 "MC collision
  * handling").  Returns 1 when an ionization produced a pair (written to e_new / i_new).       */
-static int collide_electron(const orc_sim* s, uint64_t id, uint64_t step, double x, double v[3],
-                            orc_tcount* tc, orc_newp* e_new, orc_newp* i_new) {
+static int collide_electron(const orc_sim* s, uint64_t id, uint64_t step, const uint32_t w[4], double x,
+                            double v[3], orc_tcount* tc, orc_newp* e_new, orc_newp* i_new) {
   const orc_config* c = &s->cfg;
-  uint32_t w[4];
-  draw(id, c->seed, step, ORC_CH_COLL, 0, w);
-  if (!(u01(w[0]) < (double)s->p_null[0])) return 0;
   tc->coll[4]++;
   double m = c->mass[0];
   double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
@@ -639,12 +688,9 @@ static int collide_electron(const orc_sim* s, uint64_t id, uint64_t step, double
 }
 
 /* Charge exchange of one ion: the ion leaves with a Maxwellian velocity at T_g.               */
-static void collide_ion(const orc_sim* s, uint64_t id, uint64_t step, double v[3],
+static void collide_ion(const orc_sim* s, uint64_t id, uint64_t step, const uint32_t w[4], double v[3],
                         orc_tcount* tc) {
   const orc_config* c = &s->cfg;
-  uint32_t w[4];
-  draw(id, c->seed, step, ORC_CH_COLL, 0, w);
-  if (!(u01(w[0]) < (double)s->p_null[1])) return;
   tc->coll[4]++;
   double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
   double numax = (double)s->nu_max[1];
@@ -762,8 +808,7 @@ static int step_once(orc_sim* s) {
       free(eabs);
       return ORC_ENOMEM;
     }
-    int do_mcc = (sp == 0) ? ((c->coll_mask & (ORC_COLL_EL | ORC_COLL_EX | ORC_COLL_IZ)) != 0)
-                           : ((c->coll_mask & ORC_COLL_CX) != 0);
+    const int do_mcc = s->mcc[sp];
     long long n = (long long)p->n;
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(nth) schedule(static)
@@ -797,17 +842,25 @@ static int step_once(orc_sim* s) {
         continue;
       }
       alive[i] = 1;
-      /* Monte Carlo collisions on survivors */
+      /* Monte Carlo collisions on survivors: the countdown of R17 decides the candidates */
       if (do_mcc) {
-        if (sp == 0) {
-          orc_newp e_new, i_new;
-          if (collide_electron(s, p->id[i], step, xh, v, tc, &e_new, &i_new)) {
-            if (plist_add(&born[0][t], e_new.x, e_new.v, e_new.id) != ORC_OK ||
-                plist_add(&born[1][t], i_new.x, i_new.v, i_new.id) != ORC_OK)
-              err = ORC_ENOMEM;
+        const uint32_t k = (p->nk[i] & NEXT_KMAX) - 1u, cand = p->nk[i] & NEXT_CAND;
+        if (k == 0u) {
+          uint32_t w[4];
+          draw(p->id[i], c->seed, step, ORC_CH_COLL, 0, w);
+          if (cand && sp == 0) {
+            orc_newp e_new, i_new;
+            if (collide_electron(s, p->id[i], step, w, xh, v, tc, &e_new, &i_new)) {
+              if (plist_add(&born[0][t], e_new.x, e_new.v, e_new.id) != ORC_OK ||
+                  plist_add(&born[1][t], i_new.x, i_new.v, i_new.id) != ORC_OK)
+                err = ORC_ENOMEM;
+            }
+          } else if (cand) {
+            collide_ion(s, p->id[i], step, w, v, tc);
           }
+          p->nk[i] = geometric_next(s->p_null[sp], w[0], &tc->near);
         } else {
-          collide_ion(s, p->id[i], step, v, tc);
+          p->nk[i] = k | cand;
         }
       }
       p->x[i] = xh;
@@ -828,6 +881,7 @@ static int step_once(orc_sim* s) {
       p->vy[k] = p->vy[i];
       p->vz[k] = p->vz[i];
       p->id[k] = p->id[i];
+      p->nk[k] = p->nk[i];
       ++k;
     }
     p->n = k;
@@ -900,6 +954,7 @@ static int step_once(orc_sim* s) {
       p->vy[k] = p->vy[i];
       p->vz[k] = p->vz[i];
       p->id[k] = p->id[i];
+      p->nk[k] = p->nk[i];
       ++k;
     }
     p->n = k;
@@ -916,7 +971,9 @@ static int step_once(orc_sim* s) {
     for (int t = 0; t < MAX_THREADS; ++t) {
       orc_plist* l = &born[sp][t];
       for (size_t k = 0; k < l->n; ++k) {
-        if (sp_push_back(&s->sp[sp], l->p[k].x, l->p[k].v, l->p[k].id) != ORC_OK) err = ORC_ENOMEM;
+        if (sp_push_back(&s->sp[sp], l->p[k].x, l->p[k].v, l->p[k].id, creation_next(s, sp, l->p[k].id, step)) !=
+            ORC_OK)
+          err = ORC_ENOMEM;
       }
       s->births[sp] += l->n;
       free(l->p);
@@ -926,14 +983,16 @@ static int step_once(orc_sim* s) {
     for (int t = 0; t < MAX_THREADS; ++t) {
       orc_plist* l = &nz_born[sp][t];
       for (size_t k = 0; k < l->n; ++k)
-        if (sp_push_back(&s->sp[sp], l->p[k].x, l->p[k].v, l->p[k].id) != ORC_OK) err = ORC_ENOMEM;
+        if (sp_push_back(&s->sp[sp], l->p[k].x, l->p[k].v, l->p[k].id, creation_next(s, sp, l->p[k].id, step)) !=
+            ORC_OK)
+          err = ORC_ENOMEM;
       free(l->p);
     }
   }
   for (int t = 0; t < MAX_THREADS; ++t) {
     orc_plist* l = &recycled[t];
     for (size_t k = 0; k < l->n; ++k)
-      if (sp_push_back(&s->nt, l->p[k].x, l->p[k].v, l->p[k].id) != ORC_OK) err = ORC_ENOMEM;
+      if (sp_push_back(&s->nt, l->p[k].x, l->p[k].v, l->p[k].id, 0u) != ORC_OK) err = ORC_ENOMEM;
     free(l->p);
   }
   if (err != ORC_OK) return err;
@@ -953,7 +1012,7 @@ static int step_once(orc_sim* s) {
         box_muller(w[0], w[1], &n0, &n1);
         box_muller(w[2], w[3], &n2, &n3);
         double v[3] = {vt * n0, vt * n1, vt * n2};
-        if (sp_push_back(&s->sp[sp], x, v, id) != ORC_OK) return ORC_ENOMEM;
+        if (sp_push_back(&s->sp[sp], x, v, id, creation_next(s, sp, id, step)) != ORC_OK) return ORC_ENOMEM;
       }
     }
     s->source_pairs += ion_losses;
@@ -988,8 +1047,10 @@ int orc_step(orc_sim* s, int32_t nsteps) {
  * flags[k]: 1 absorbed at a wall, 2 collision candidate, 4 near-threshold draw, 8 ionization (the
  * new pair itself is not returned).  Tracked neutrals and the pair source are not part of it. */
 int orc_step_sample(const orc_config* cfg, int sp, uint64_t step, const double* E, size_t n, const double* x,
-                    const double* v, const uint64_t* id, double* xo, double* vo, int32_t* flags) {
-  if (!cfg || !valid_config(cfg) || sp < 0 || sp > 1 || (n && (!x || !v || !id || !xo || !vo || !flags)))
+                    const double* v, const uint64_t* id, const uint32_t* nk, double* xo, double* vo, uint32_t* nko,
+                    int32_t* flags) {
+  if (!cfg || !valid_config(cfg) || sp < 0 || sp > 1 ||
+      (n && (!x || !v || !id || !nk || !xo || !vo || !nko || !flags)))
     return ORC_EINVAL;
   if (cfg->field_mode == ORC_FIELD_SELF && !E) return ORC_EINVAL;
   orc_sim t;
@@ -997,24 +1058,31 @@ int orc_step_sample(const orc_config* cfg, int sp, uint64_t step, const double* 
   t.cfg = *cfg;
   derive(&t);
   const int moves = !(cfg->frozen_mask & (1u << sp));
-  const int do_mcc = (sp == 0) ? ((cfg->coll_mask & (ORC_COLL_EL | ORC_COLL_EX | ORC_COLL_IZ)) != 0)
-                               : ((cfg->coll_mask & ORC_COLL_CX) != 0);
   for (size_t k = 0; k < n; ++k) {
     double xh = x[k];
     double vv[3] = {v[3 * k], v[3 * k + 1], v[3 * k + 2]};
     int32_t fl = 0;
+    nko[k] = nk[k];
     if (moves) {
       move_particle(cfg, t.qm[sp], t.Bv, t.dx, E, &xh, vv);
       if (xh < 0.0 || xh >= (double)t.N) {
         fl |= 1;
-      } else if (do_mcc) {
+      } else if (t.mcc[sp]) {
         orc_tcount tc;
         memset(&tc, 0, sizeof(tc));
-        if (sp == 0) {
-          orc_newp a, b;
-          if (collide_electron(&t, id[k], step, xh, vv, &tc, &a, &b)) fl |= 8;
+        const uint32_t kk = (nk[k] & NEXT_KMAX) - 1u, cand = nk[k] & NEXT_CAND;
+        if (kk == 0u) {
+          uint32_t w[4];
+          draw(id[k], cfg->seed, step, ORC_CH_COLL, 0, w);
+          if (cand && sp == 0) {
+            orc_newp a, b;
+            if (collide_electron(&t, id[k], step, w, xh, vv, &tc, &a, &b)) fl |= 8;
+          } else if (cand) {
+            collide_ion(&t, id[k], step, w, vv, &tc);
+          }
+          nko[k] = geometric_next(t.p_null[sp], w[0], &tc.near);
         } else {
-          collide_ion(&t, id[k], step, vv, &tc);
+          nko[k] = kk | cand;
         }
         if (tc.coll[4]) fl |= 2;
         if (tc.near) fl |= 4;
@@ -1123,6 +1191,13 @@ int orc_neutral_diag(orc_sim* s, orc_ndiag_t* d) {
   return ORC_OK;
 }
 
+int orc_countdown(orc_sim* s, int species, uint32_t* nk) {
+  orc_species* p = species_of(s, species);
+  if (!p || !nk) return ORC_EINVAL;
+  for (size_t i = 0; i < p->n; ++i) nk[i] = p->nk[i];
+  return ORC_OK;
+}
+
 int orc_particles(orc_sim* s, int species, double* x, double* v, uint64_t* id) {
   orc_species* p = species_of(s, species);
   if (!p) return ORC_EINVAL;
@@ -1139,16 +1214,18 @@ int orc_particles(orc_sim* s, int species, double* x, double* v, uint64_t* id) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* Snapshot blob, version 1, little-endian, no padding:
+/* Snapshot blob, version 3, little-endian, no padding:
  *   "PICMCSN1" | u32 version | u32 0 | u64 config hash | u64 step | u64 n[2] |
  *   u64 wall_hits[2][2] | u64 coll[5] | u64 near[2] | u64 viol[2] | u64 births[2] |
  *   u64 source_pairs | u64 dropped | i64 wall_charge | f64 wall_energy[2] |
- *   per species: i32 cell[n] | f64 frac[n] | f64 vx[n] | f64 vy[n] | f64 vz[n] | u64 id[n] |
+ *   per species: u32 cell word[n] | f64 frac[n] | f64 vx[n] | f64 vy[n] | f64 vz[n] | u64 id[n] |
  *   u32 CRC-32 (IEEE 802.3, reflected, as zlib) of everything before it.
+ * The cell word is cell | k << 18 | c << 30 with the null-collision countdown (k, c) of R17 (0 in
+ * bits 18..31 for a species without the test).
  * Particles are written in ascending id order within a species (canonical order), so two runs
  * that hold the same particle set write the same bytes.  This mirrors the checkpoint semantics
  * of Sec. 4.1 (per-species particle records; restart rebuilds positions and velocities).
- * Version 2 (configurations with tracked neutrals) inserts before the CRC: u64 n_neutral |
+ * Version 4 (configurations with tracked neutrals) inserts before the CRC: u64 n_neutral |
  * u64 recycled[2] | u64 lost[2] | u64 ionized | u64 near | the neutral records as above.     */
 #define SNAP_MAGIC "PICMCSN1"
 #define SNAP_HDR (8 + 4 + 4 + 8 + 8 + 16 + 17 * 8 + 8 + 16)
@@ -1222,8 +1299,8 @@ static int put_species(unsigned char** q, const orc_species* p) {
   }
   qsort(ord, n, sizeof(idx_key), cmp_key);
   for (size_t k = 0; k < n; ++k) {
-    int32_t cc = (int32_t)floor(p->x[ord[k].i]);
-    put(q, &cc, 4);
+    const uint32_t cw = (uint32_t)floor(p->x[ord[k].i]) | (p->nk[ord[k].i] << CELL_BITS);
+    put(q, &cw, 4);
   }
   for (size_t k = 0; k < n; ++k) {
     double xh = p->x[ord[k].i];
@@ -1249,7 +1326,7 @@ int orc_snapshot(orc_sim* s, void* buf, size_t cap, size_t* needed) {
   if (!buf) return ORC_OK;
   if (cap < need) return ORC_EINVAL;
   unsigned char* q = (unsigned char*)buf;
-  uint32_t ver = s->cfg.neutrals ? 2 : 1, zero = 0;
+  uint32_t ver = s->cfg.neutrals ? 4 : 3, zero = 0;
   uint64_t h = orc_config_hash(&s->cfg), dropped = 0;
   put(&q, SNAP_MAGIC, 8);
   put(&q, &ver, 4);
@@ -1303,14 +1380,14 @@ int orc_restore(orc_sim* s, const void* buf, size_t len) {
   get(&q, &ver, 4);
   get(&q, &zero, 4);
   get(&q, &h, 8);
-  if (ver != (s->cfg.neutrals ? 2u : 1u) || h != orc_config_hash(&s->cfg)) return ORC_ECORRUPT;
+  if (ver != (s->cfg.neutrals ? 4u : 3u) || h != orc_config_hash(&s->cfg)) return ORC_ECORRUPT;
   get(&q, &step, 8);
   get(&q, &n[0], 8);
   get(&q, &n[1], 8);
   uint64_t nn = 0;
   if (n[0] > len / 44 || n[1] > len / 44) return ORC_ECORRUPT;
   size_t charged = SNAP_HDR + 44 * (n[0] + n[1]);
-  if (ver == 2) {
+  if (ver == 4) {
     if (len < charged + SNAP_NT_HDR + 4) return ORC_ECORRUPT;
     memcpy(&nn, b + charged, 8);
     if (nn > len / 44 || len != charged + SNAP_NT_HDR + 44 * nn + 4) return ORC_ECORRUPT;
@@ -1334,7 +1411,7 @@ int orc_restore(orc_sim* s, const void* buf, size_t len) {
   s->nt_ionized = s->nt_near = s->nt_particle_steps = 0;
   for (int sp = 0; sp < 3; ++sp) {
     if (sp == 2) {
-      if (ver != 2) break;
+      if (ver != 4) break;
       get(&q, &nn, 8);
       get(&q, s->nt_recycled, 16);
       get(&q, s->nt_lost, 16);
@@ -1351,11 +1428,22 @@ int orc_restore(orc_sim* s, const void* buf, size_t len) {
     const unsigned char* vz = vy + 8 * ns;
     const unsigned char* id = vz + 8 * ns;
     for (size_t i = 0; i < ns; ++i) {
-      int32_t cc;
+      uint32_t cw;
       double f;
-      memcpy(&cc, cell + 4 * i, 4);
+      memcpy(&cw, cell + 4 * i, 4);
       memcpy(&f, frac + 8 * i, 8);
-      if (cc < 0 || cc >= s->N || !(f >= 0.0 && f < 1.0)) return ORC_ECORRUPT;
+      const int32_t cc = (int32_t)(cw & ((1u << CELL_BITS) - 1u));
+      uint32_t nk = cw >> CELL_BITS;
+      if (cc >= s->N || !(f >= 0.0 && f < 1.0)) return ORC_ECORRUPT;
+      if (sp < 2 && s->mcc[sp]) { /* R17: a valid countdown pair, or 0 = not drawn */
+        if (nk > (NEXT_CAND | NEXT_KMAX)) return ORC_ECORRUPT;
+        memcpy(&p->id[i], id + 8 * i, 8);
+        if (nk == 0u) nk = creation_next(s, sp, p->id[i], step);
+        if ((nk & NEXT_KMAX) == 0u) return ORC_ECORRUPT;
+      } else if (nk != 0u) {
+        return ORC_ECORRUPT; /* no countdown for species without the null-collision test */
+      }
+      p->nk[i] = nk;
       p->x[i] = (double)cc + f;
       if (p->x[i] >= (double)cc + 1.0) p->x[i] = nextafter((double)cc + 1.0, 0.0);
       memcpy(&p->vx[i], vx + 8 * i, 8);

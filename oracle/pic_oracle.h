@@ -161,10 +161,12 @@ void orc_free(orc_sim* s);
 int orc_step(orc_sim* s, int32_t nsteps);
 /* One step of n given particles of species sp under the node field E (N + 1 values): mover, wall
  * test and null-collision MC exactly as orc_step, for parity checks that sample a large state.
- * x in cells, v as n (vx, vy, vz) triples; flags: 1 absorbed, 2 candidate, 4 near-threshold draw,
- * 8 ionization.  Neutrals and the pair source are not included. */
+ * x in cells, v as n (vx, vy, vz) triples, nk the null-collision countdown pairs (k | c << 12, as a
+ * snapshot's cell word carries them in bits 18..30), nko the pairs after the step; flags: 1 absorbed,
+ * 2 candidate, 4 near-threshold draw, 8 ionization.  Neutrals and the pair source are not included. */
 int orc_step_sample(const orc_config* cfg, int sp, uint64_t step, const double* E, size_t n, const double* x,
-                    const double* v, const uint64_t* id, double* xo, double* vo, int32_t* flags);
+                    const double* v, const uint64_t* id, const uint32_t* nk, double* xo, double* vo, uint32_t* nko,
+                    int32_t* flags);
 int orc_diag(orc_sim* s, orc_diag_t* out);
 /* R: 2 x (N+1) int64 fixed-point deposits, rho/phi/E: N+1 nodes each; any may be NULL. */
 int orc_fields(orc_sim* s, int64_t* R, double* rho, double* phi, double* E);
@@ -175,6 +177,9 @@ void orc_smooth(int32_t N, int32_t passes, double* rho);
 /* Copies the live particles of a species (2: the neutrals) in storage order: x_hat (dx units),
  * v (n x 3), id. */
 int orc_particles(orc_sim* s, int species, double* x, double* v, uint64_t* id);
+/* The null-collision countdown pairs (k | c << 12, R17; 0 for a species without the test) of the
+ * live particles of a species, in the storage order of orc_particles. */
+int orc_countdown(orc_sim* s, int species, uint32_t* nk);
 /* Snapshot blob (format shared by specification with the GPU library, written separately). */
 int orc_snapshot(orc_sim* s, void* buf, size_t cap, size_t* needed);
 int orc_restore(orc_sim* s, const void* buf, size_t len);

@@ -125,6 +125,7 @@ void layout(pic_handle* h, char* base, size_t* total) {
       a.vy = cv.take<double>(h->cap[s]);
       a.vz = cv.take<double>(h->cap[s]);
       a.id = cv.take<unsigned long long>(h->cap[s]);
+      a.nk = cv.take<unsigned>(h->cap[s]);
     }
     for (int s = 0; s < 2; ++s) h->acc[s] = cv.take<double>(N + 1);
   }
@@ -176,6 +177,8 @@ void derive(pic_handle* h) {
     k.nu_max = (float)(c.n_gas * smax[s] * vcap);
     k.p_null = (float)(1.0 - std::exp(-(double)k.nu_max * c.dt));
     k.p_null_u24 = (unsigned)std::ceil((double)k.p_null * 16777216.0);
+    k.lnq_d = std::log1p(-(double)k.p_null);  // the countdown's geometric parameter
+    k.lnq = (float)k.lnq_d;
   }
   p.dtdx_d = c.dt / dx;
   p.dtdx = (float)p.dtdx_d;
@@ -205,6 +208,12 @@ void derive(pic_handle* h) {
   p.field_mode = c.field_mode;
   p.push_mask = 3u & ~c.frozen_mask;
   p.has_B = c.B != 0.0 ? 1u : 0u;
+  p.mcc_mask = 0u;
+  for (int s = 0; s < 2; ++s) {  // species that take the null-collision test (and carry a countdown)
+    const bool on = s == 0 ? (c.coll_mask & (PIC_COLL_EL | PIC_COLL_EX | PIC_COLL_IZ)) != 0u
+                           : (c.coll_mask & PIC_COLL_CX) != 0u;
+    if (on && ((p.push_mask >> s) & 1u) && p.sp[s].p_null > 0.f) p.mcc_mask |= 1u << s;
+  }
   p.N = c.ncells;
   p.seed = c.seed;
 }
@@ -789,15 +798,17 @@ int fetch_particles(pic_handle* h, HostParticles out[2], Ctl* ctl) {
       CK(cudaMemcpy(vy.data(), a.vy, n * 8, cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(vz.data(), a.vz, n * 8, cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(id.data(), a.id, n * 8, cudaMemcpyDeviceToHost));
-      // absolute x -> (cell, fraction); absorbed particles carry x < 0
-      host_parallel(n, 12, [&](size_t lo, size_t hi) {
+      std::vector<unsigned> nk(n);
+      CK(cudaMemcpy(nk.data(), a.nk, n * 4, cudaMemcpyDeviceToHost));
+      // absolute x -> (cell word, fraction); absorbed particles carry x < 0
+      host_parallel(n, 16, [&](size_t lo, size_t hi) {
         for (size_t i = lo; i < hi; ++i) {
           if (x[i] < 0.0) {
             cell[i] = PIC_DEAD_CELL;
             continue;
           }
           const double c = std::floor(x[i]);
-          cell[i] = (int32_t)c;
+          cell[i] = (int32_t)((uint32_t)c | (nk[i] << PIC_CELL_BITS));
           x[i] = x[i] - c;
         }
       });
@@ -849,11 +860,11 @@ int check_blob(const pic_handle* h, const void* buf, size_t len) {
   std::memcpy(&hash, b + 16, 8);
   std::memcpy(&step, b + 24, 8);
   std::memcpy(n, b + 32, 16);
-  if (ver != (h->cap_nt ? 2u : 1u) || hash != config_hash(h->cfg)) return PIC_ECORRUPT;
+  if (ver != (h->cap_nt ? 4u : 3u) || hash != config_hash(h->cfg)) return PIC_ECORRUPT;
   if (n[0] > (1ull << 40) || n[1] > (1ull << 40)) return PIC_ECORRUPT;
   const size_t charged = kHdr + 44 * (size_t)(n[0] + n[1]);
   uint64_t nn = 0;
-  if (ver == 2) {  // the neutral block: u64 n, u64 counters[6], records
+  if (ver == 4) {  // the neutral block: u64 n, u64 counters[6], records
     if (len < charged + kNtHdr + 4) return PIC_ECORRUPT;
     std::memcpy(&nn, b + charged, 8);
     if (nn > (1ull << 40) || len != charged + kNtHdr + 44 * nn + 4) return PIC_ECORRUPT;
@@ -864,12 +875,16 @@ int check_blob(const pic_handle* h, const void* buf, size_t len) {
   for (int s = 0; s < 2; ++s)
     if (round_up4(n[s]) > h->cap[s]) return PIC_EOVERFLOW;
   const int N = h->N;
-  // range of every cell and fraction (host threads)
+  // range of every cell, countdown and fraction (host threads).  The cell word is
+  // cell | k << 18 | c << 30; a species with the null-collision test may leave the countdown pair
+  // (k | c << 12) at 0 ("not drawn": the restore draws it), else 1 <= k <= 4095; every other
+  // species (the neutrals included) carries 0 there.
   {
     const size_t offs[3] = {kHdr, kHdr + 44 * (size_t)n[0], charged + kNtHdr};
     const uint64_t counts[3] = {n[0], n[1], nn};
     bool bad = false;
     for (int s = 0; s < 3; ++s) {
+      const bool mcc = s < 2 && ((h->ph.mcc_mask >> s) & 1u);
       const size_t m = (size_t)counts[s];
       const unsigned char* cell = b + offs[s];
       const unsigned char* frac = cell + 4 * m;
@@ -881,11 +896,15 @@ int check_blob(const pic_handle* h, const void* buf, size_t len) {
         th.emplace_back([&, k]() {
           const size_t i0 = std::min(m, (size_t)k * chunk), i1 = std::min(m, i0 + chunk);
           for (size_t i = i0; i < i1; ++i) {
-            int32_t c;
+            uint32_t w;
             double f;
-            std::memcpy(&c, cell + 4 * i, 4);
+            std::memcpy(&w, cell + 4 * i, 4);
             std::memcpy(&f, frac + 8 * i, 8);
-            if (c < 0 || c >= N || !(f >= 0.0 && f < 1.0)) {
+            const uint32_t pair = w >> PIC_CELL_BITS;
+            const bool pair_ok = mcc ? (pair == 0u || (pair <= (PIC_NEXT_CAND | PIC_NEXT_KMAX) &&
+                                                       (pair & PIC_NEXT_KMAX) != 0u))
+                                     : pair == 0u;
+            if ((int)(w & PIC_CELL_MASK) >= N || !pair_ok || !(f >= 0.0 && f < 1.0)) {
               flag[k] = 1;
               break;
             }
@@ -923,7 +942,7 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
   h->cur = 0;
   // FP32: a species' arrays (m records at blob offset o) go straight to device staging (the sort's
   // second buffer, unused between sorts) and a kernel converts them into dst
-  auto upload32 = [&](size_t o, size_t m, const Species32& dstsp) -> int {
+  auto upload32 = [&](size_t o, size_t m, const Species32& dstsp, int species) -> int {
     char* stage = h->stage;
     const size_t stage_bytes = h->stage_bytes;
     const size_t per = std::max<size_t>(4, (stage_bytes - 6 * 256) / 44 / 4 * 4);
@@ -942,7 +961,7 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
       CK(launch_restore32(reinterpret_cast<const int*>(dst[0]), reinterpret_cast<const double*>(dst[1]),
                           reinterpret_cast<const double*>(dst[2]), reinterpret_cast<const double*>(dst[3]),
                           reinterpret_cast<const double*>(dst[4]), reinterpret_cast<const unsigned long long*>(dst[5]),
-                          cnt_i, dstsp, done, N, h->st));
+                          cnt_i, dstsp, done, h->ph, species, step, h->st));
     }
     const size_t mp = (size_t)round_up4(m);
     if (mp > m) {
@@ -956,17 +975,20 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
     const size_t m = (size_t)n[s];
     const size_t mp = (size_t)round_up4(m);
     if (!h->plain) {
-      const int rc = upload32(off, m, h->a32[0][s]);
+      const int rc = upload32(off, m, h->a32[0][s], s);
       if (rc != PIC_OK) return rc;
     } else {
       std::vector<double> x(mp, -1.0), a1(mp, 0.0), a2(mp, 0.0), a3(mp, 0.0);
       std::vector<uint64_t> id2(mp, 0ull);
+      std::vector<unsigned> nk(mp, 0u);
       const unsigned char* cell = b + off;
       for (size_t i = 0; i < m; ++i) {
-        int32_t c;
+        uint32_t w;
         double f;
-        std::memcpy(&c, cell + 4 * i, 4);
+        std::memcpy(&w, cell + 4 * i, 4);
         std::memcpy(&f, cell + 4 * m + 8 * i, 8);
+        const int32_t c = (int32_t)(w & PIC_CELL_MASK);
+        nk[i] = w >> PIC_CELL_BITS;
         double xx = (double)c + f;
         if (xx >= (double)c + 1.0) xx = std::nextafter((double)c + 1.0, 0.0);
         x[i] = xx;
@@ -981,6 +1003,8 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
       CK(cudaMemcpy(a.vy, a2.data(), 8 * mp, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(a.vz, a3.data(), 8 * mp, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(a.id, id2.data(), 8 * mp, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(a.nk, nk.data(), 4 * mp, cudaMemcpyHostToDevice));
+      CK(launch_fill_pairs64(a.nk, a.id, m, h->ph, s, step, h->st));  // pairs the blob left undrawn
     }
     off += 44 * m;
   }
@@ -995,7 +1019,7 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
     uint64_t nn, nc[6];
     std::memcpy(&nn, b + off, 8);
     std::memcpy(nc, b + off + 8, sizeof(nc));
-    const int rc = upload32(off + kNtHdr, (size_t)nn, h->nt[0]);
+    const int rc = upload32(off + kNtHdr, (size_t)nn, h->nt[0], 2);
     if (rc != PIC_OK) return rc;
     h->nt_buf = 0;
     c.nt_cur = round_up4(nn);
@@ -1033,6 +1057,94 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
   }
   h->step = step;
   return PIC_OK;
+}
+
+// The particle phase of one step: the particle, neutral and source kernels (the deposit goes into
+// the per-cell counts); records in h whether the step sorts and whether it moved the particles.
+int step_particles(pic_handle* h) {
+  const bool sort_now = !h->plain && (h->step % (unsigned long long)h->cfg.sort_interval) == 0ull;
+  const bool scatter = !h->plain && h->pending_scatter;
+  EvPair e;
+  if (!h->plain) {
+    StepParams32 P = params32(h);
+    const bool sum_ke = h->ke_every > 0 && ((h->step + 1) % (unsigned long long)h->ke_every) == 0ull;
+    P.sum_ke = sum_ke ? 1u : 0u;
+    h->ke_valid = sum_ke;
+    if (scatter) {  // the step after a sort: read buffer cur, fill buffer 1 - cur in sorted order
+      for (int s = 0; s < 2; ++s) P.sp[s] = h->a32[1 - h->cur][s];
+      P.scatter = 1u;
+    }
+    prof_begin(h, scatter ? K_STEP_SCATTER : K_STEP, &e);
+    CK(scatter ? launch_step32_scatter(P, h->grid_scatter, h->st) : launch_step32(P, h->grid_step, h->st));
+    prof_end(h, &e);
+    if (h->cap_nt) {  // the neutrals alive at the step start, and the ions recycled in this step:
+      // in place, or compacted into the other buffer on the steps that sort
+      NeutralParams Q = neutral_params(h, P);
+      if (!sort_now) Q.dst = Q.src;
+      prof_begin(h, sort_now ? K_NEUTRAL_COMPACT : K_NEUTRAL, &e);
+      CK(launch_neutral32(Q, sort_now, h->grid_neutral, h->st));
+      prof_end(h, &e);
+    }
+    if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
+      prof_begin(h, K_SOURCE, &e);
+      CK(launch_source32(P, h->st));
+      prof_end(h, &e);
+    }
+    if (scatter) {
+      h->cur = 1 - h->cur;
+      h->pending_scatter = false;
+    }
+  } else {
+    const StepParams64 P = params64(h);
+    prof_begin(h, K_STEP, &e);
+    CK(launch_step64(P, h->grid_step, h->st));
+    prof_end(h, &e);
+    if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
+      prof_begin(h, K_SOURCE, &e);
+      CK(launch_source64(P, h->st));
+      prof_end(h, &e);
+    }
+  }
+  h->open_sort = sort_now;
+  h->open_scatter = scatter;
+  return PIC_OK;
+}
+
+// The rest of the step: field solve (of this handle's deposits, or of the deposits R_total of a
+// decomposed simulation), bookkeeping, and the sort scan on sort steps; the step count advances.
+int step_close(pic_handle* h, const long long* R_total) {
+  EvPair e;
+  const bool sort_now = h->open_sort, scatter = h->open_scatter;
+  prof_begin(h, K_FIELD, &e);
+  PoissonParams F = field_params(h, sort_now, true);
+  F.scatter_step = scatter ? 1 : 0;
+  F.R_in = R_total;
+  if (h->cap_nt) {  // the buffer the neutral step wrote
+    F.nt_pad = h->nt[sort_now ? 1 - h->nt_buf : h->nt_buf];
+    F.nt_append = sort_now ? 0 : 1;
+  }
+  CK(launch_field(F, h->st));
+  prof_end(h, &e);
+  if (h->cap_nt && sort_now) h->nt_buf = 1 - h->nt_buf;
+  if (sort_now) {
+    // the counting sort: cursors from this step's counts now; the particles move during the next
+    // step (k_step32 in scatter mode), which saves a read and a write of every particle
+    prof_begin(h, K_SORT, &e);
+    Species32 src[2] = {h->a32[h->cur][0], h->a32[h->cur][1]};
+    Species32 dst[2] = {h->a32[1 - h->cur][0], h->a32[1 - h->cur][1]};
+    CK(launch_sort_scan32(src, dst, h->cnt, h->cursor, h->cap, h->ctl, h->N, h->st));
+    prof_end(h, &e);
+    h->pending_scatter = true;
+  }
+  h->step += 1;
+  return PIC_OK;
+}
+
+// Particle decomposition needs the FP32 path and the integer-exact field (an exact sum of the
+// parts' deposits), and none of the per-step inputs a part could not draw alone (pair source ids,
+// tracked neutrals).
+bool split_ok(const pic_handle* h) {
+  return !h->plain && exact_possible(h->cfg) && h->cfg.source_mode == PIC_SOURCE_NONE && !h->cap_nt;
 }
 
 bool blob_step(const void* buf, size_t len, unsigned long long* step) {
@@ -1155,72 +1267,11 @@ uint32_t pic_blob_crc32(const void* p, size_t n) {
 
 int pic_step(pic_handle* h, int32_t n) {
   PIC_ENTRY_TRY
-  if (!h || n < 0) return PIC_EINVAL;
+  if (!h || n < 0 || h->split_open) return PIC_EINVAL;
   for (int32_t k = 0; k < n; ++k) {
-    const bool sort_now = !h->plain && (h->step % (unsigned long long)h->cfg.sort_interval) == 0ull;
-    const bool scatter = !h->plain && h->pending_scatter;
-    EvPair e;
-    if (!h->plain) {
-      StepParams32 P = params32(h);
-      const bool sum_ke = h->ke_every > 0 && ((h->step + 1) % (unsigned long long)h->ke_every) == 0ull;
-      P.sum_ke = sum_ke ? 1u : 0u;
-      h->ke_valid = sum_ke;
-      if (scatter) {  // the step after a sort: read buffer cur, fill buffer 1 - cur in sorted order
-        for (int s = 0; s < 2; ++s) P.sp[s] = h->a32[1 - h->cur][s];
-        P.scatter = 1u;
-      }
-      prof_begin(h, scatter ? K_STEP_SCATTER : K_STEP, &e);
-      CK(scatter ? launch_step32_scatter(P, h->grid_scatter, h->st) : launch_step32(P, h->grid_step, h->st));
-      prof_end(h, &e);
-      if (h->cap_nt) {  // the neutrals alive at the step start, and the ions recycled in this step:
-        // in place, or compacted into the other buffer on the steps that sort
-        NeutralParams Q = neutral_params(h, P);
-        if (!sort_now) Q.dst = Q.src;
-        prof_begin(h, sort_now ? K_NEUTRAL_COMPACT : K_NEUTRAL, &e);
-        CK(launch_neutral32(Q, sort_now, h->grid_neutral, h->st));
-        prof_end(h, &e);
-      }
-      if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
-        prof_begin(h, K_SOURCE, &e);
-        CK(launch_source32(P, h->st));
-        prof_end(h, &e);
-      }
-      if (scatter) {
-        h->cur = 1 - h->cur;
-        h->pending_scatter = false;
-      }
-    } else {
-      const StepParams64 P = params64(h);
-      prof_begin(h, K_STEP, &e);
-      CK(launch_step64(P, h->grid_step, h->st));
-      prof_end(h, &e);
-      if (h->cfg.source_mode == PIC_SOURCE_PAIRS) {
-        prof_begin(h, K_SOURCE, &e);
-        CK(launch_source64(P, h->st));
-        prof_end(h, &e);
-      }
-    }
-    prof_begin(h, K_FIELD, &e);
-    PoissonParams F = field_params(h, sort_now, true);
-    F.scatter_step = scatter ? 1 : 0;
-    if (h->cap_nt) {  // the buffer the neutral step wrote
-      F.nt_pad = h->nt[sort_now ? 1 - h->nt_buf : h->nt_buf];
-      F.nt_append = sort_now ? 0 : 1;
-    }
-    CK(launch_field(F, h->st));
-    prof_end(h, &e);
-    if (h->cap_nt && sort_now) h->nt_buf = 1 - h->nt_buf;
-    if (sort_now) {
-      // the counting sort: cursors from this step's counts now; the particles move during the next
-      // step (k_step32 in scatter mode), which saves a read and a write of every particle
-      prof_begin(h, K_SORT, &e);
-      Species32 src[2] = {h->a32[h->cur][0], h->a32[h->cur][1]};
-      Species32 dst[2] = {h->a32[1 - h->cur][0], h->a32[1 - h->cur][1]};
-      CK(launch_sort_scan32(src, dst, h->cnt, h->cursor, h->cap, h->ctl, h->N, h->st));
-      prof_end(h, &e);
-      h->pending_scatter = true;
-    }
-    h->step += 1;
+    int rc = step_particles(h);
+    if (rc == PIC_OK) rc = step_close(h, nullptr);
+    if (rc != PIC_OK) return rc;
   }
   return PIC_OK;
   PIC_ENTRY_CATCH
@@ -1233,6 +1284,86 @@ int pic_set_diag_interval(pic_handle* h, int32_t every) {
   if (!h || every < 0) return PIC_EINVAL;
   h->ke_every = every;
   return PIC_OK;
+  PIC_ENTRY_CATCH
+}
+
+int pic_keep_subset(pic_handle* h, uint32_t part, uint32_t nparts) {
+  PIC_ENTRY_TRY
+  if (!h || !split_ok(h) || h->split_open || nparts < 1 || part >= nparts) return PIC_EINVAL;
+  int rc = check_errors(h);
+  if (rc != PIC_OK) return rc;
+  CK(launch_keep_subset(h->a32[h->cur][0], h->a32[h->cur][1], h->ctl, part, nparts, h->st));
+  rc = refresh_field(h);  // deposit of the part's particles, its own field, full sort + compaction
+  if (rc == PIC_OK) rc = check_errors(h);
+  if (rc != PIC_OK) return rc;
+  if (part != 0) {  // cumulative counters and sums stay with part 0, so that the parts add up
+    Ctl c;
+    CK(cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    std::memset(c.wall_hits, 0, sizeof(c.wall_hits));
+    std::memset(c.coll, 0, sizeof(c.coll));
+    std::memset(c.near_thr, 0, sizeof(c.near_thr));
+    std::memset(c.viol, 0, sizeof(c.viol));
+    std::memset(c.births, 0, sizeof(c.births));
+    std::memset(c.wall_energy_fx, 0, sizeof(c.wall_energy_fx));
+    c.source_pairs = c.dropped = 0ull;
+    c.wall_charge = 0;
+    c.particle_steps = 0ull;
+    CK(cudaMemcpy(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
+  }
+  return PIC_OK;
+  PIC_ENTRY_CATCH
+}
+
+int pic_local_deposit(pic_handle* h, int64_t* R_local) {
+  PIC_ENTRY_TRY
+  if (!h || !R_local || !split_ok(h) || h->split_open) return PIC_EINVAL;
+  // a deposit pass over the particles as they stand (no push, no collision), the node deposits,
+  // then the per-cell accumulators cleared again
+  Phys saved = h->ph;
+  h->ph.push_mask = 0u;
+  h->ph.coll_mask = 0u;
+  h->ph.mcc_mask = 0u;
+  StepParams32 P = params32(h);
+  h->ph = saved;
+  CK(launch_step32(P, h->grid_step, h->st));
+  const PoissonParams F = field_params(h, false, false);
+  CK(launch_node_deposit(F, reinterpret_cast<long long*>(R_local), h->st));
+  for (int s = 0; s < 2; ++s) {
+    CK(cudaMemsetAsync(h->cnt[s], 0, sizeof(unsigned int) * h->N, h->st));
+    CK(cudaMemsetAsync(h->S[s], 0, sizeof(unsigned long long) * h->N, h->st));
+  }
+  return PIC_OK;
+  PIC_ENTRY_CATCH
+}
+
+int pic_solve_deposit(pic_handle* h, const int64_t* R_total) {
+  PIC_ENTRY_TRY
+  if (!h || !R_total || !split_ok(h) || h->split_open) return PIC_EINVAL;
+  PoissonParams F = field_params(h, true, false);
+  F.R_in = reinterpret_cast<const long long*>(R_total);
+  F.no_book = 1;
+  CK(launch_field(F, h->st));
+  return PIC_OK;
+  PIC_ENTRY_CATCH
+}
+
+int pic_step_begin(pic_handle* h, int64_t* R_local) {
+  PIC_ENTRY_TRY
+  if (!h || !R_local || !split_ok(h) || h->split_open) return PIC_EINVAL;
+  int rc = step_particles(h);
+  if (rc != PIC_OK) return rc;
+  const PoissonParams F = field_params(h, false, false);
+  CK(launch_node_deposit(F, reinterpret_cast<long long*>(R_local), h->st));
+  h->split_open = true;
+  return PIC_OK;
+  PIC_ENTRY_CATCH
+}
+
+int pic_step_end(pic_handle* h, const int64_t* R_total) {
+  PIC_ENTRY_TRY
+  if (!h || !R_total || !h->split_open) return PIC_EINVAL;
+  h->split_open = false;
+  return step_close(h, reinterpret_cast<const long long*>(R_total));
   PIC_ENTRY_CATCH
 }
 
@@ -1386,7 +1517,11 @@ int pic_storage_order(pic_handle* h, int32_t species, int32_t* cell, uint64_t* i
   if (!cell && !ids) return PIC_OK;
   if (cap < (size_t)ext) return PIC_ENOMEM;
   const Species32& a = h->a32[h->cur][species];
-  if (cell && ext) CK(cudaMemcpy(cell, a.cell, sizeof(int32_t) * ext, cudaMemcpyDeviceToHost));
+  if (cell && ext) {
+    CK(cudaMemcpy(cell, a.cell, sizeof(int32_t) * ext, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < (size_t)ext; ++i)  // the cell alone (the word also carries the countdown)
+      if (cell[i] != PIC_DEAD_CELL) cell[i] &= PIC_CELL_MASK;
+  }
   if (ids && ext) CK(cudaMemcpy(ids, a.id, sizeof(uint64_t) * ext, cudaMemcpyDeviceToHost));
   return PIC_OK;
   PIC_ENTRY_CATCH
@@ -1435,7 +1570,7 @@ int pic_snapshot(pic_handle* h, void* buf, size_t cap, size_t* needed) {
   };
   const auto put_u64 = [&](uint64_t v) { put_raw(&v, 8); };
   put_raw("PICMCSN1", 8);
-  const uint32_t ver[2] = {(uint32_t)(h->cap_nt ? 2 : 1), 0u};
+  const uint32_t ver[2] = {(uint32_t)(h->cap_nt ? 4 : 3), 0u};
   put_raw(ver, 8);
   put_u64(config_hash(h->cfg));
   put_u64((uint64_t)h->step);

@@ -264,12 +264,11 @@ int upload_tables(pic_batch* b) {
     std::memset(&x, 0, sizeof(x));
     for (int s = 0; s < 2; ++s) {
       x.seg[s] = (unsigned)b->seg[s][k];
-      x.p_null_u24[s] = h->ph.sp[s].p_null_u24;
     }
     x.cbase = (int)b->cbase[k];
     x.N = h->N;
     x.seed = h->ph.seed;
-    x.collides = ((h->ph.coll_mask & 7u) ? 1u : 0u) | ((h->ph.coll_mask & 8u) ? 2u : 0u);
+    x.collides = h->ph.mcc_mask;
     for (int s = 0; s < 2; ++s) x.cap[s] = (unsigned)b->cap_s[s][k];
   }
   CKB(cudaMemcpy(b->d_hot, hot.data(), sizeof(BSim) * n, cudaMemcpyHostToDevice));

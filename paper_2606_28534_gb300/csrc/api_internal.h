@@ -58,6 +58,8 @@ struct pic_handle {
   int grid_step = 0, grid_sort = 0, grid_diag = 0, grid_scatter = 0;
   int ke_every = 0;       // the step sums the kinetic energy on every ke_every-th step (0: never)
   bool pending_scatter = false;  // a sort scan ran: the next step moves the particles to buffer 1 - cur
+  bool open_sort = false, open_scatter = false;  // the step in progress sorts / moved the particles
+  bool split_open = false;  // pic_step_begin ran; pic_step_end closes the step
   bool ke_valid = false;  // the last completed step (or refresh) summed it (ke_last holds it)
   // tracked neutrals (cfg.neutrals): two compacted buffers, the one the next step reads is nt_buf
   unsigned long long cap_nt = 0;
@@ -86,6 +88,10 @@ bool exact_possible(const pic_config& c);
 PoissonParams field_params(pic_handle* h, bool keep_counts, bool count_step);
 int refresh_field(pic_handle* h);
 int check_errors(pic_handle* h);
+// The two halves of pic_step's step: the particle phase, and the field solve (of R_total when not
+// null), bookkeeping and sort scan that close it.
+int step_particles(pic_handle* h);
+int step_close(pic_handle* h, const long long* R_total);
 int status_of(unsigned int err_bits);
 // Initial particles of h (the grid arrays and the control block are already zero): load,
 // padding, control block, deposit + field + sort, error check.

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) k_load32(const StepParams32 P, const Load
       }
     }
     const Species32 A = s ? P.sp[1] : P.sp[0];
-    A.cell[i] = c;
+    A.cell[i] = created_word(P.ph, s, c, id, 0ull);  // with the particle's collision countdown
     A.frac[i] = f;
     A.vx[i] = (float)v[0];
     A.vy[i] = (float)v[1];
@@ -91,7 +91,18 @@ __global__ void __launch_bounds__(256) k_load64(const StepParams64 P, const Load
     A.vy[i] = v[1];
     A.vz[i] = v[2];
     A.id[i] = id;
+    A.nk[i] = created_pair<true>(P.ph, s, id, 0ull);
   }
+}
+
+// Plain path: countdown pairs a snapshot left undrawn (0) for a species with the null-collision
+// test: drawn as at creation, at the snapshot's step.
+__global__ void __launch_bounds__(256) k_fill_pairs64(unsigned* __restrict__ nk, const unsigned long long* __restrict__ id,
+                                                      unsigned long long n, const Phys ph, int s,
+                                                      unsigned long long step) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    if (nk[i] == 0u) nk[i] = created_pair<true>(ph, s, id[i], step);
 }
 
 // Plain path: sum of 0.5 m v^2 over live particles in 2^-24 fixed point (exact integer sums,
@@ -173,17 +184,23 @@ __global__ void __launch_bounds__(256) k_diag_grid(const long long* __restrict__
   }
 }
 
-// Restore: one chunk of a snapshot's per-species arrays (uploaded as they are in the blob: int32
-// cells, FP64 fractions and velocities, u64 ids) converted to the FP32 layout.  The host has
-// already checked cells and fractions; a fraction that rounds up to 1 moves to the next cell.
+// Restore: one chunk of a snapshot's per-species arrays (uploaded as they are in the blob: cell
+// words, FP64 fractions and velocities, u64 ids) converted to the FP32 layout.  The host has
+// already checked cells, countdowns and fractions; a fraction that rounds up to 1 moves to the next
+// cell; a countdown the blob left undrawn (0) for a species with the test is drawn as at creation,
+// at the snapshot's step (species 2, the neutrals, carry none).
 __global__ void __launch_bounds__(256) k_restore32(const int* __restrict__ cell, const double* __restrict__ frac,
                                                    const double* __restrict__ vx, const double* __restrict__ vy,
                                                    const double* __restrict__ vz,
                                                    const unsigned long long* __restrict__ id, unsigned long long n,
-                                                   Species32 dst, unsigned long long base, int N) {
+                                                   Species32 dst, unsigned long long base, const Phys ph, int s,
+                                                   unsigned long long step) {
+  const int N = ph.N;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    int c = cell[i];
+    int c = cell[i] & PIC_CELL_MASK;
+    unsigned pair = (unsigned)cell[i] >> PIC_CELL_BITS;
+    if (pair == 0u && s < 2) pair = created_pair(ph, s, id[i], step);
     float f = (float)frac[i];
     if (f >= 1.f) {
       f = 0.f;
@@ -194,12 +211,35 @@ __global__ void __launch_bounds__(256) k_restore32(const int* __restrict__ cell,
       }
     }
     const unsigned long long k = base + i;
-    dst.cell[k] = c;
+    dst.cell[k] = c | (int)(pair << PIC_CELL_BITS);
     dst.frac[k] = f;
     dst.vx[k] = (float)vx[i];
     dst.vy[k] = (float)vy[i];
     dst.vz[k] = (float)vz[i];
     dst.id[k] = id[i];
+  }
+}
+
+// Particle decomposition: the live particles whose id % nparts != part leave this part (marked dead;
+// the next full sort compacts them away); the live counts drop by as many.
+__global__ void __launch_bounds__(256) k_keep_subset(const Species32 a0, const Species32 a1, Ctl* ctl, unsigned part,
+                                                     unsigned nparts) {
+  const unsigned long long n0 = ctl->n_cur[0], n1 = ctl->n_cur[1];
+  unsigned long long gone[2] = {0ull, 0ull};
+  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < n0 + n1;
+       g += (unsigned long long)gridDim.x * blockDim.x) {
+    const int s = g < n0 ? 0 : 1;
+    const unsigned long long i = s ? g - n0 : g;
+    const Species32& A = s ? a1 : a0;
+    if (A.cell[i] == PIC_DEAD_CELL || A.id[i] % nparts == part) continue;
+    A.cell[i] = PIC_DEAD_CELL;
+    gone[s] += 1ull;
+  }
+  for (int s = 0; s < 2; ++s) {
+    unsigned long long t = gone[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, o);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(&ctl->n_live[s], (unsigned long long)(-(long long)t));
   }
 }
 
@@ -249,11 +289,21 @@ cudaError_t launch_diag_grid(const long long* R0, const long long* R1, int sign0
 
 cudaError_t launch_restore32(const int* cell, const double* frac, const double* vx, const double* vy, const double* vz,
                              const unsigned long long* id, unsigned long long n, const Species32& dst,
-                             unsigned long long base, int N, cudaStream_t st) {
+                             unsigned long long base, const Phys& ph, int species, unsigned long long step,
+                             cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const unsigned long long blocks = (n + 255) / 256;
   const int grid = (int)(blocks < 152ull * 16 ? blocks : 152ull * 16);
-  k_restore32<<<grid, 256, 0, st>>>(cell, frac, vx, vy, vz, id, n, dst, base, N);
+  k_restore32<<<grid, 256, 0, st>>>(cell, frac, vx, vy, vz, id, n, dst, base, ph, species, step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_pairs64(unsigned* nk, const unsigned long long* id, unsigned long long n, const Phys& ph,
+                                int species, unsigned long long step, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned long long blocks = (n + 255) / 256;
+  const int grid = (int)(blocks < 152ull * 16 ? blocks : 152ull * 16);
+  k_fill_pairs64<<<grid, 256, 0, st>>>(nk, id, n, ph, species, step);
   return cudaGetLastError();
 }
 
@@ -283,6 +333,12 @@ cudaError_t launch_selftest_wait(unsigned long long* out, cudaStream_t st) {
 
 cudaError_t launch_store_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) {
   k_store_u64<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keep_subset(const Species32& a0, const Species32& a1, Ctl* ctl, unsigned part, unsigned nparts,
+                               cudaStream_t st) {
+  k_keep_subset<<<152 * 8, 256, 0, st>>>(a0, a1, ctl, part, nparts);
   return cudaGetLastError();
 }
 

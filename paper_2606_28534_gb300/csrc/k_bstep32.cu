@@ -6,7 +6,7 @@
 // whole ensemble (chunks of 32 x PIC_PPT consecutive particles of its segment; pre_s is written by
 // k_bplan from the extents after the previous step).  Warp w of the grid takes the contiguous run
 // [w per, (w+1) per) of the list, so that a warp meets one or two simulations per species: it keeps
-// the simulation's constants (segment, cells, seed, P_null) in registers, its collision queue and
+// the simulation's constants (segment, cells, seed, countdown) in shared memory, its collision queue and
 // its counters, and hands the counters to the simulation's control block when it moves on.
 // Per particle the arithmetic is the single-run kernel's (k_step32.cu), with the simulation's cell
 // offset added for the field gather and the deposit; constants every simulation shares (push,
@@ -26,7 +26,7 @@ static_assert(PIC_PPT == 4, "each lane moves four particles: one 128-bit access 
 struct WarpSim {
   unsigned seg;    // first slot of the species segment
   unsigned nk;     // extent of the species segment
-  unsigned pnull;  // null-collision probability, 0: no draw
+  unsigned mcc;    // 1: the species takes the null-collision countdown in this simulation
   int cbase;       // first cell
   int N;           // cells
   unsigned cap;    // capacity of the species segment
@@ -53,12 +53,13 @@ __device__ __forceinline__ int owner(const unsigned* __restrict__ pre, int nsims
 }
 
 // Lane 0: bulk copies of local chunk lt of species s of simulation k (arrays A) into a stage buffer.
+// The ids only in the step after a sort (it moves them); the ordinary step needs none.
 __device__ __forceinline__ void issue_chunk(const BatchStep32& B, const Species32& A, int s, int k, unsigned lt,
-                                            unsigned char* buf, unsigned long long* bar) {
+                                            unsigned char* buf, unsigned long long* bar, bool with_id) {
   const unsigned nk = B.ncur[s][k];
   const unsigned i0 = lt * CHUNK;
   const unsigned n = min((unsigned)CHUNK, nk - i0);  // multiple of 4
-  stage_issue_span(A, B.hot[k].seg[s] + i0, n, buf, bar);
+  stage_issue_span(A, B.hot[k].seg[s] + i0, n, buf, bar, with_id);
 }
 
 // Where births of simulation k go in species s: past the extent of the buffer being written (after
@@ -111,7 +112,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
   const unsigned below = (1u << lane) - 1u;
   const Phys& ph = B.ph;
   const int nsims = B.nsims;
-  const unsigned long long step = B.dev->step;
   const unsigned gw = blockIdx.x * WARPS + wib;
   const unsigned nw = gridDim.x * WARPS;
   int qn = 0;            // warp-uniform
@@ -141,12 +141,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         const unsigned t = t0 + st;
         if (t < t1) {
           while (pre[ki + 1] <= t) ++ki;
-          issue_chunk(B, Asrc, s, ki, t - pre[ki], stage + st * STAGE_BYTES, bar + st);
+          issue_chunk(B, Asrc, s, ki, t - pre[ki], stage + st * STAGE_BYTES, bar + st, SCATTER);
         }
       }
     }
     // the simulation being processed (warp-uniform); kend == 0 until the first one is entered.
-    // pnull == 0: the species does not collide in this simulation (no draw is made).
+    // mcc == 0: the species takes no null-collision countdown in this simulation.
     int kc = kfirst;
     unsigned kbeg = 0u, kend = 0u;
     WarpSim& ws = wsm[wib];
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
           const BSim& h = B.hot[kc];
           ws.seg = h.seg[s];
           ws.nk = B.ncur[s][kc];
-          ws.pnull = moves && ((h.collides >> s) & 1u) ? h.p_null_u24[s] : 0u;
+          ws.mcc = (h.collides >> s) & 1u;
           ws.cbase = h.cbase;
           ws.N = h.N;
           ws.cap = h.cap[s];
@@ -192,21 +192,22 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         const float4 x4 = reinterpret_cast<const float4*>(buf + CHUNK * 8)[lane];
         const float4 y4 = reinterpret_cast<const float4*>(buf + CHUNK * 12)[lane];
         const float4 z4 = reinterpret_cast<const float4*>(buf + CHUNK * 16)[lane];
-        const ulonglong2 id01 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane];
-        const ulonglong2 id23 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane + 1];
         c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
         f[0] = f4.x; f[1] = f4.y; f[2] = f4.z; f[3] = f4.w;
         vx[0] = x4.x; vx[1] = x4.y; vx[2] = x4.z; vx[3] = x4.w;
         vy[0] = y4.x; vy[1] = y4.y; vy[2] = y4.z; vy[3] = y4.w;
         vz[0] = z4.x; vz[1] = z4.y; vz[2] = z4.z; vz[3] = z4.w;
-        id[0] = id01.x; id[1] = id01.y; id[2] = id23.x; id[3] = id23.y;
+        if (SCATTER) {
+          const ulonglong2 id01 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane];
+          const ulonglong2 id23 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane + 1];
+          id[0] = id01.x; id[1] = id01.y; id[2] = id23.x; id[3] = id23.y;
+        } else {
+          id[0] = id[1] = id[2] = id[3] = 0ull;
+        }
       }
       if (!have) {
 #pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k) {
-          c[k] = PIC_DEAD_CELL;
-          id[k] = 0ull;
-        }
+        for (int k = 0; k < PIC_PPT; ++k) c[k] = PIC_DEAD_CELL;
       }
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) c[k] = checked_cell(c[k], ws.N, &B.sims[kc].ctl->error);
@@ -214,7 +215,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) {
         e2[k] = make_float2(0.f, 0.f);
-        if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL) e2[k] = __ldg(B.E2 + (ws.cbase + c[k]));
+        if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL)
+          e2[k] = __ldg(B.E2 + (ws.cbase + (c[k] & PIC_CELL_MASK)));
       }
       // the step after a sort: claim each live particle's slot in its cell (four atomics in flight)
       unsigned slot[PIC_PPT];
@@ -224,10 +226,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
           const bool live = c[k] != PIC_DEAD_CELL;
-          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cb + c[k] : -1);
+          const int cell = cb + (c[k] & PIC_CELL_MASK);
+          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cell : -1);
           base[k] = 0u;
           if (live && lane == __ffs(peers[k]) - 1)
-            base[k] = atomicAdd(B.cursor[s] + cb + c[k], (unsigned)__popc(peers[k]));
+            base[k] = atomicAdd(B.cursor[s] + cell, (unsigned)__popc(peers[k]));
         }
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k)
@@ -244,27 +247,22 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         if (tn < t1) {
           int ki = kc;  // owner of chunk tn: this simulation or a later one
           while (pre[ki + 1] <= tn) ++ki;
-          issue_chunk(B, Asrc, s, ki, tn - pre[ki], stage + st * STAGE_BYTES, bar + st);
+          issue_chunk(B, Asrc, s, ki, tn - pre[ki], stage + st * STAGE_BYTES, bar + st, SCATTER);
         }
       }
       st = st + 1 == NST ? 0 : st + 1;
 
-      unsigned cand = 0u;
-      const unsigned pnull = ws.pnull;
-      if (pnull) {
-        const unsigned long long seed = ws.seed;
-#pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k) {
-          const uint4 w = draw4(id[k], seed, step, CH_COLL, 0u);
-          if ((w.x >> 8) < pnull) cand |= 1u << k;
-        }
-      }
+      unsigned cand = 0u;  // the null-collision countdown expired in this step (queued)
+      const bool collides = ws.mcc != 0u;
       const int N = ws.N;
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) {
         if (c[k] == PIC_DEAD_CELL) continue;
         if (moves) {
-          const int cn = push_one(ph, K, e2[k], c[k], f[k], vx[k], vy[k], vz[k]);
+          // the cell moves by dc; a survivor's word takes dc directly (its cell stays in [0, N), so
+          // nothing borrows from the countdown bits)
+          const int dc = push_one(ph, K, e2[k], 0, f[k], vx[k], vy[k], vz[k]);
+          const int cn = (c[k] & PIC_CELL_MASK) + dc;
           if ((unsigned)cn >= (unsigned)N) {  // absorbed at a wall
             const int side = cn < 0 ? 0 : 1;
             atomicAdd(&wc.hits[s][side], 1u);
@@ -274,7 +272,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
             c[k] = PIC_DEAD_CELL;
             continue;
           }
-          c[k] = cn;
+          c[k] += dc;
+          if (collides) {  // one step less to the next null-collision draw; queued when it expires
+            c[k] -= 1 << PIC_CELL_BITS;
+            if ((((unsigned)c[k] >> PIC_CELL_BITS) & PIC_NEXT_KMAX) == 0u) cand |= 1u << k;
+          }
         }
       }
       if (SCATTER) {
@@ -337,24 +339,24 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         // only where a lane still has one
 #pragma unroll
         for (int k = PIC_PPT - 1; k > 0; --k) {
-          if (rn[k] && rn[k - 1] && c[k] == c[k - 1]) {
+          if (rn[k] && rn[k - 1] && ((c[k] ^ c[k - 1]) & PIC_CELL_MASK) == 0) {
             rn[k - 1] += rn[k];
             rsw[k - 1] += rsw[k];
             rn[k] = 0u;
           }
         }
-        warp_deposit(B.cnt[s], B.S[s], rn[0] ? cbase + c[0] : -1, rn[0], rsw[0]);
+        warp_deposit(B.cnt[s], B.S[s], rn[0] ? cbase + (c[0] & PIC_CELL_MASK) : -1, rn[0], rsw[0]);
         if (__any_sync(0xFFFFFFFFu, (rn[1] | rn[2] | rn[3]) != 0u)) {
 #pragma unroll
           for (int k = 1; k < PIC_PPT; ++k)
-            warp_deposit(B.cnt[s], B.S[s], rn[k] ? cbase + c[k] : -1, rn[k], rsw[k]);
+            warp_deposit(B.cnt[s], B.S[s], rn[k] ? cbase + (c[k] & PIC_CELL_MASK) : -1, rn[k], rsw[k]);
         }
       } else {
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
 #pragma unroll
           for (int j = k + 1; j < PIC_PPT; ++j) {
-            if (rn[k] && rn[j] && c[j] == c[k]) {
+            if (rn[k] && rn[j] && ((c[j] ^ c[k]) & PIC_CELL_MASK) == 0) {
               rn[k] += rn[j];
               rsw[k] += rsw[j];
               rn[j] = 0u;
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         }
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k)
-          warp_deposit(B.cnt[s], B.S[s], rn[k] ? cbase + c[k] : -1, rn[k], rsw[k]);
+          warp_deposit(B.cnt[s], B.S[s], rn[k] ? cbase + (c[k] & PIC_CELL_MASK) : -1, rn[k], rsw[k]);
       }
 
       if (qn > QFLUSH) {

@@ -179,14 +179,15 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
   const int a = rank * seg;
   const int len = max(0, min(seg, M - a));
 
-  if (P.ctl && rank == 0 && tid == 0) bookkeeping(P);
+  if (P.ctl && !P.no_book && rank == 0 && tid == 0) bookkeeping(P);
 
   // ---- pass 1 (coalesced): node deposits, net integer charge ------------------------------------
   // |r| bound that keeps the smoothed values (at most 4^(passes + 1) |r|) inside int64
   const __int128 lim = (__int128)0x7FFFFFFFFFFFFFFFll >> (P.smooth ? 2 * P.smooth + 2 : 0);
   for (int i = tid; i < len; i += TPB) {
     const int j = a + i;
-    const long long R0 = node_R(P, 0, j), R1 = node_R(P, 1, j);
+    // a decomposed simulation solves the total of every part's deposits (exact integer sums)
+    const long long R0 = P.R_in ? P.R_in[j] : node_R(P, 0, j), R1 = P.R_in ? P.R_in[M + j] : node_R(P, 1, j);
     P.R[0][j] = R0;
     P.R[1][j] = R1;
     const __int128 rn = (__int128)P.m[0] * R0 + (__int128)P.m[1] * R1;
@@ -541,6 +542,25 @@ cudaError_t launch_field(const PoissonParams& p, cudaStream_t st) {
     case 3: k_field_fp64<3><<<PIC_FIELD_CTAS, tpb, smem, st>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+namespace {
+// This handle's node deposits R_sj = 2^32 cnt_j - S_j + S_{j-1} (the counts stay for the field
+// kernel that closes the step).
+__global__ void __launch_bounds__(256) k_node_deposit(const PoissonParams P, long long* __restrict__ out) {
+  const int M = P.N + 1;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    out[j] = node_R(P, 0, j);
+    out[M + j] = node_R(P, 1, j);
+  }
+}
+}  // namespace
+
+cudaError_t launch_node_deposit(const PoissonParams& p, long long* out, cudaStream_t st) {
+  const int M = p.N + 1;
+  const int grid = (M + 255) / 256 < 1024 ? (M + 255) / 256 : 1024;
+  k_node_deposit<<<grid, 256, 0, st>>>(p, out);
   return cudaGetLastError();
 }
 

@@ -69,7 +69,7 @@ __device__ __forceinline__ void born_charged(const NeutralParams& Q, unsigned lo
     return;
   }
   const Species32& a = P.sp[s];
-  a.cell[slot] = c;
+  a.cell[slot] = created_word(P.ph, s, c, id, P.step);  // with the new particle's collision countdown
   a.frac[slot] = f;
   a.vx[slot] = v[0];
   a.vy[slot] = v[1];

@@ -150,9 +150,10 @@ __device__ __forceinline__ void scatter_tile(const SortParams& P, unsigned long 
 #pragma unroll
   for (int k = 0; k < PIC_PPT; ++k) {
     const bool live = c[k] != PIC_DEAD_CELL;
-    peers[k] = __match_any_sync(0xFFFFFFFFu, live ? c[k] : -1);
+    const int cell = c[k] & PIC_CELL_MASK;  // the word also carries the null-collision countdown
+    peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cell : -1);
     base[k] = 0u;
-    if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(cur + c[k], (unsigned)__popc(peers[k]));
+    if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(cur + cell, (unsigned)__popc(peers[k]));
   }
 #pragma unroll
   for (int k = 0; k < PIC_PPT; ++k) {

@@ -8,10 +8,12 @@
 //   gather   E_p = (1-f) E_c + f E_{c+1} from the float2 node-pair array (one 8-byte load)
 //   push     Boris rotation with uniform B; cell-local position update (FP32 fraction)
 //   walls    absorbed when the new cell leaves [0, N)
-//   MCC      null-collision test with one Philox4x32-10 block of (particle id, step, COLL);
-//            candidates are queued per warp and then select elastic / excitation / ionization
-//            (electrons) or charge exchange (ions); ionization appends an (e, ion) pair past the
-//            array end
+//   MCC      null collisions by geometric countdown: the particle's countdown (bits 18..30 of its
+//            cell word) steps down; when it expires the particle is queued per warp, draws one
+//            Philox4x32-10 block of (particle id, step, COLL), collides if the expiry is a
+//            candidate -- elastic / excitation / ionization (electrons) or charge exchange
+//            (ions); ionization appends an (e, ion) pair past the array end -- and takes its next
+//            countdown from the same block
 //   deposit  CIC in int64 fixed point: W_r = rint(f 2^32); per cell a particle count and a sum of
 //            W_r, aggregated over the lanes of a warp that share a cell (redux.sync) and added
 //            to global memory with one reduction per (warp, cell).  Node deposits follow as
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
     const Species32& Asrc = SCATTER ? P.src[s] : P.sp[s];  // read
     const SpConst& K = ph.sp[s];
     const bool moves = (ph.push_mask >> s) & 1u;
-    const bool collides = moves && (s == 0 ? (ph.coll_mask & 7u) != 0u : (ph.coll_mask & 8u) != 0u);
+    const bool collides = (ph.mcc_mask >> s) & 1u;  // takes the null-collision countdown
     const unsigned long long tag = (unsigned long long)s << 63;
     // Chunk schedule.  An ordinary step gives each warp a contiguous run of chunks: concurrent warps
     // then work in different cells, so that the deposit's reductions from different warps rarely
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
 #pragma unroll
       for (int st = 0; st < NSTAGE; ++st) {
         const unsigned t = t_first + st * t_inc;
-        if (t < t_end) stage_issue(Asrc, t, ncur, stage + st * STAGE_BYTES, bar + st);
+        if (t < t_end) stage_issue(Asrc, t, ncur, stage + st * STAGE_BYTES, bar + st, SCATTER);
       }
     }
     int st = 0;
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
       const unsigned i0 = t * CHUNK + lane * PIC_PPT;
       int c[PIC_PPT];
       float f[PIC_PPT], vx[PIC_PPT], vy[PIC_PPT], vz[PIC_PPT];
-      unsigned long long id[PIC_PPT];
+      unsigned long long id[PIC_PPT];  // the step after a sort moves the ids; the ordinary step needs none
       const bool have = i0 < ncur;
       {
         const int4 c4 = reinterpret_cast<const int4*>(buf)[lane];
@@ -121,31 +123,32 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         const float4 x4 = reinterpret_cast<const float4*>(buf + CHUNK * 8)[lane];
         const float4 y4 = reinterpret_cast<const float4*>(buf + CHUNK * 12)[lane];
         const float4 z4 = reinterpret_cast<const float4*>(buf + CHUNK * 16)[lane];
-        const ulonglong2 id01 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane];
-        const ulonglong2 id23 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane + 1];
         c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
         f[0] = f4.x; f[1] = f4.y; f[2] = f4.z; f[3] = f4.w;
         vx[0] = x4.x; vx[1] = x4.y; vx[2] = x4.z; vx[3] = x4.w;
         vy[0] = y4.x; vy[1] = y4.y; vy[2] = y4.z; vy[3] = y4.w;
         vz[0] = z4.x; vz[1] = z4.y; vz[2] = z4.z; vz[3] = z4.w;
-        id[0] = id01.x; id[1] = id01.y; id[2] = id23.x; id[3] = id23.y;
+        if (SCATTER) {
+          const ulonglong2 id01 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane];
+          const ulonglong2 id23 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane + 1];
+          id[0] = id01.x; id[1] = id01.y; id[2] = id23.x; id[3] = id23.y;
+        } else {
+          id[0] = id[1] = id[2] = id[3] = 0ull;
+        }
       }
       if (!have) {
 #pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k) {
-          c[k] = PIC_DEAD_CELL;
-          id[k] = 0ull;
-        }
+        for (int k = 0; k < PIC_PPT; ++k) c[k] = PIC_DEAD_CELL;
       }
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) c[k] = checked_cell(c[k], N, &P.ctl->error);
       // field node pairs of the four cells, requested first so that their latency overlaps the
-      // Philox work below
+      // slot claims and the push below
       float2 e2[PIC_PPT];
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) {
         e2[k] = make_float2(0.f, 0.f);
-        if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL) e2[k] = __ldg(P.E2 + c[k]);
+        if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL) e2[k] = __ldg(P.E2 + (c[k] & PIC_CELL_MASK));
       }
       // scatter: claim each live particle's slot in its cell (four atomics in flight; their results
       // are first needed at the stores, so the Philox work below covers their latency)
@@ -154,9 +157,10 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
           const bool live = c[k] != PIC_DEAD_CELL;
-          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? c[k] : -1);
+          const int cell = c[k] & PIC_CELL_MASK;
+          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cell : -1);
           base[k] = 0u;
-          if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(P.cursor[s] + c[k], (unsigned)__popc(peers[k]));
+          if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(P.cursor[s] + cell, (unsigned)__popc(peers[k]));
         }
       }
       // the stage is read: refill it with the chunk NSTAGE steps ahead
@@ -164,28 +168,22 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
       __syncwarp();
       if (lane == 0) {
         const unsigned tn = t + NSTAGE * t_inc;
-        if (tn < t_end) stage_issue(Asrc, tn, ncur, stage + st * STAGE_BYTES, bar + st);
+        if (tn < t_end) stage_issue(Asrc, tn, ncur, stage + st * STAGE_BYTES, bar + st, SCATTER);
       }
       st = st + 1 == NSTAGE ? 0 : st + 1;
 
-      // null-collision candidates: the draw depends only on (id, step), so the four Philox
-      // blocks are independent instruction streams
       unsigned live0 = 0u;  // live at the start of the step (scatter: owns a slot)
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) live0 |= c[k] != PIC_DEAD_CELL ? (1u << k) : 0u;
-      unsigned cand = 0u;
-      if (collides) {
-#pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k) {
-          const uint4 w = draw4(id[k], ph.seed, P.step, CH_COLL, 0u);
-          if ((w.x >> 8) < K.p_null_u24) cand |= 1u << k;
-        }
-      }
+      unsigned cand = 0u;  // the null-collision countdown expired in this step (queued)
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) {
         if (c[k] == PIC_DEAD_CELL) continue;
         if (moves) {
-          const int cn = push_one(ph, K, e2[k], c[k], f[k], vx[k], vy[k], vz[k]);
+          // the cell moves by dc; a survivor's word takes dc directly (its cell stays in [0, N), so
+          // nothing borrows from the countdown bits)
+          const int dc = push_one(ph, K, e2[k], 0, f[k], vx[k], vy[k], vz[k]);
+          const int cn = (c[k] & PIC_CELL_MASK) + dc;
           if ((unsigned)cn >= (unsigned)N) {  // absorbed at a wall
             const int side = cn < 0 ? 0 : 1;
             atomicAdd(&bc.hits[s][side], 1u);
@@ -202,7 +200,11 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
             c[k] = PIC_DEAD_CELL;
             continue;
           }
-          c[k] = cn;
+          c[k] += dc;
+          if (collides) {  // one step less to the next null-collision draw; queued when it expires
+            c[k] -= 1 << PIC_CELL_BITS;
+            if ((((unsigned)c[k] >> PIC_CELL_BITS) & PIC_NEXT_KMAX) == 0u) cand |= 1u << k;
+          }
         }
       }
       if (SCATTER) {
@@ -233,13 +235,13 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         *reinterpret_cast<float4*>(A.vy + i0) = make_float4(vy[0], vy[1], vy[2], vy[3]);
         *reinterpret_cast<float4*>(A.vz + i0) = make_float4(vz[0], vz[1], vz[2], vz[3]);
       }
-      // kinetic energy after the push (steps that sum it); a candidate's is added after its collision
+      // kinetic energy after the push (steps that sum it); a queued particle's is added after its draw
       if (P.sum_ke) {
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k)
           if (c[k] != PIC_DEAD_CELL && !((cand >> k) & 1u)) ke_lane += ke_fx32(vx[k], vy[k], vz[k], K.mass);
       }
-      // queue the surviving candidates (their collision changes v only, not the deposit)
+      // queue the particles whose countdown expired (a collision changes v only, not the deposit)
       // (the ordinary step skips the four ballots when no lane of the warp has a candidate)
       unsigned qmask = 0u;
 #pragma unroll
@@ -268,16 +270,17 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         // sort), then particle 0 across the warp; particles 1..3 only where a lane still has one
 #pragma unroll
         for (int k = PIC_PPT - 1; k > 0; --k) {
-          if (rn[k] && rn[k - 1] && c[k] == c[k - 1]) {
+          if (rn[k] && rn[k - 1] && ((c[k] ^ c[k - 1]) & PIC_CELL_MASK) == 0) {
             rn[k - 1] += rn[k];
             rsw[k - 1] += rsw[k];
             rn[k] = 0u;
           }
         }
-        warp_deposit(P.cnt[s], P.S[s], rn[0] ? c[0] : -1, rn[0], rsw[0]);
+        warp_deposit(P.cnt[s], P.S[s], rn[0] ? c[0] & PIC_CELL_MASK : -1, rn[0], rsw[0]);
         if (__any_sync(0xFFFFFFFFu, (rn[1] | rn[2] | rn[3]) != 0u)) {
 #pragma unroll
-          for (int k = 1; k < PIC_PPT; ++k) warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] : -1, rn[k], rsw[k]);
+          for (int k = 1; k < PIC_PPT; ++k)
+            warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] & PIC_CELL_MASK : -1, rn[k], rsw[k]);
         }
       } else {
         // every pair of the lane's particles (the step after a sort measured faster this way)
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         for (int k = 0; k < PIC_PPT; ++k) {
 #pragma unroll
           for (int j = k + 1; j < PIC_PPT; ++j) {
-            if (rn[k] && rn[j] && c[j] == c[k]) {
+            if (rn[k] && rn[j] && ((c[j] ^ c[k]) & PIC_CELL_MASK) == 0) {
               rn[k] += rn[j];
               rsw[k] += rsw[j];
               rn[j] = 0u;
@@ -293,7 +296,8 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
           }
         }
 #pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k) warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] : -1, rn[k], rsw[k]);
+        for (int k = 0; k < PIC_PPT; ++k)
+          warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] & PIC_CELL_MASK : -1, rn[k], rsw[k]);
       }
 
       if (qn > QFLUSH) {
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(256) k_source32(const StepParams32 P) {
       box_muller_f(u.x, u.y, a0, a1);
       box_muller_f(u.z, u.w, a2, a3);
       float v[3] = {ph.sp[0].vt * a0, ph.sp[0].vt * a1, ph.sp[0].vt * a2};
-      if (append32<0>(P, n0, c, f, v, ide)) {
+      if (append32<0>(P, n0, created_word(ph, 0, c, ide, P.step), f, v, ide)) {
         atomicAdd(P.cnt[0] + c, 1u);
         atomicAdd(P.S[0] + c, (unsigned long long)wr);
         atomicAdd(&added[0], 1u);
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(256) k_source32(const StepParams32 P) {
       box_muller_f(u.x, u.y, a0, a1);
       box_muller_f(u.z, u.w, a2, a3);
       float v[3] = {ph.sp[1].vt * a0, ph.sp[1].vt * a1, ph.sp[1].vt * a2};
-      if (append32<1>(P, n1, c, f, v, ide + 1ull)) {
+      if (append32<1>(P, n1, created_word(ph, 1, c, ide + 1ull, P.step), f, v, ide + 1ull)) {
         atomicAdd(P.cnt[1] + c, 1u);
         atomicAdd(P.S[1] + c, (unsigned long long)wr);
         atomicAdd(&added[1], 1u);

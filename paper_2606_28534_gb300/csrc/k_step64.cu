@@ -3,7 +3,8 @@
 // Same method and the same random draws as the FP32 step (paper Sec. 2: interpolation, mover,
 // MC collisions, deposition), written the plain way: one thread per particle over an unsorted
 // array, absolute positions in cell units (FP64), the node field read from global memory, and
-// the CIC deposit done with FP64 atomic adds of (1 - f) and f into per-node accumulators.
+// the CIC deposit done with FP64 atomic adds of (1 - f) and f into per-node accumulators.  The
+// null-collision countdown pair of each particle lives in its own array (nk).
 #include "pic_internal.cuh"
 
 namespace {
@@ -38,7 +39,7 @@ __device__ __forceinline__ void box_muller_d(unsigned wa, unsigned wb, double& n
 
 template <int s>
 __device__ __forceinline__ bool append64(const StepParams64& P, unsigned long long ncur, double x,
-                                         const double* v, unsigned long long id) {
+                                         const double* v, unsigned long long id) {  // created in this step
   unsigned long long slot = ncur + atomicAdd(&P.ctl->n_born[s], 1ull);
   if (slot >= P.cap[s]) {
     atomicAdd(&P.ctl->dropped, 1ull);
@@ -51,6 +52,7 @@ __device__ __forceinline__ bool append64(const StepParams64& P, unsigned long lo
   a.vy[slot] = v[1];
   a.vz[slot] = v[2];
   a.id[slot] = id;
+  a.nk[slot] = created_pair<true>(P.ph, s, id, P.step);
   return true;
 }
 
@@ -105,10 +107,17 @@ __device__ void particle64(const StepParams64& P, unsigned long long i, unsigned
       A.x[i] = -1.0;
       return;
     }
-    const bool collides = s == 0 ? (ph.coll_mask & 7u) != 0u : (ph.coll_mask & 8u) != 0u;
-    if (collides) {
-      uint4 w = draw4(A.id[i], ph.seed, P.step, CH_COLL, 0u);
-      if (u01d(w.x) < (double)K.p_null) {
+    unsigned pair = A.nk[i];
+    bool expired = false;
+    if ((ph.mcc_mask >> s) & 1u) {  // the null-collision countdown
+      const unsigned kk = (pair & PIC_NEXT_KMAX) - 1u;
+      expired = kk == 0u;
+      pair = kk | (pair & PIC_NEXT_CAND);
+    }
+    if (expired) {
+      const uint4 w = draw4(A.id[i], ph.seed, P.step, CH_COLL, 0u);
+      A.nk[i] = countdown_draw_d(K, w.x, &bc->near_thr[s]);
+      if (pair & PIC_NEXT_CAND) {
         atomicAdd(&bc->coll[4], 1u);
         const double numax = (double)K.nu_max;
         const double r = u01d(w.y) * numax;
@@ -190,6 +199,8 @@ __device__ void particle64(const StepParams64& P, unsigned long long i, unsigned
           }
         }
       }
+    } else if ((ph.mcc_mask >> s) & 1u) {
+      A.nk[i] = pair;
     }
     A.x[i] = x;
     A.vx[i] = v[0];

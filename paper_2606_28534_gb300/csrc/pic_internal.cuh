@@ -10,6 +10,10 @@
 //   control block Ctl (counters and array extents), 256-byte aligned.
 // Extents n_cur are kept a multiple of 4 so that every particle load/store is a 128-bit access;
 // slots past the last particle carry cell = DEAD_CELL.
+// The cell word of a live particle is cell | k << 18 | c << 30: the cell (N < 2^18) and the
+// particle's null-collision countdown (k, c) (the geometric countdown reading; k in 1..4095, c set
+// when its expiry is a candidate; both 0 for species without the test).  DEAD_CELL has bit 31 set,
+// which no live word has.  The plain FP64 path keeps the pair (k | c << 12) in its own array.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -24,6 +28,10 @@
 #define PIC_TILE (PIC_TPB * PIC_PPT)
 #define PIC_WCAP 2048
 #define PIC_DEAD_CELL ((int)0x80000000)
+#define PIC_CELL_BITS 18
+#define PIC_CELL_MASK ((1 << PIC_CELL_BITS) - 1)
+#define PIC_NEXT_KMAX 4095u       // largest countdown
+#define PIC_NEXT_CAND (1u << 12)  // in a countdown pair k | c << 12: the expiry is a candidate
 #define PIC_FIELD_CTAS 8
 #define PIC_FIELD_TPB 1024
 #define PIC_FIELD_SEG_MAX 24576  // nodes per CTA of the field cluster (192 KB of shared memory)
@@ -97,6 +105,7 @@ struct Species64 {
   double* vy;
   double* vz;
   unsigned long long* id;
+  unsigned* nk;  // null-collision countdown pair k | c << 12 (0: no test)
 };
 
 // Physics constants of one species, rounded once on the host.
@@ -105,6 +114,8 @@ struct SpConst {
   float t[3], s[3]; // Boris rotation vectors
   float p_null;     // 1 - exp(-nu_max dt), FP32
   unsigned p_null_u24;  // ceil(p_null 2^24): (w >> 8) < p_null_u24  <=>  u01(w) < p_null
+  float lnq;        // log1p(-p_null) rounded to FP32 (the countdown's fast path)
+  double lnq_d;     // log1p(-p_null) in FP64
   float nu_max;     // FP32
   float mass;
   float vt;         // sqrt(T/m) (source, load)
@@ -125,6 +136,7 @@ struct Phys {
   double dtdx_d, ngs_el_d, ngs_ex_d, ngs_iz_d, ngs_cx_d, E_ex_d, E_iz_d, two_m_over_M_d,
       vt_gas_d, E_ext_d, src_x1_d;
   unsigned int coll_mask, field_mode, push_mask, has_B;
+  unsigned int mcc_mask;  // bit s: species s takes the null-collision test (processes on, pushed, p_null > 0)
   int N;
   unsigned long long seed;
 };
@@ -210,7 +222,7 @@ __device__ __forceinline__ uint4 draw4(unsigned long long id, unsigned long long
 #define PIC_CHECKED_BUILD 0
 #endif
 __device__ __forceinline__ int checked_cell(int c, int N, unsigned int* error) {
-  if (PIC_CHECKED_BUILD && c != PIC_DEAD_CELL && (unsigned)c >= (unsigned)N) {
+  if (PIC_CHECKED_BUILD && c != PIC_DEAD_CELL && (c < 0 || (c & PIC_CELL_MASK) >= N)) {
     atomicOr(error, ERR_DEVICE);
     return PIC_DEAD_CELL;
   }
@@ -220,6 +232,57 @@ __device__ __forceinline__ int checked_cell(int c, int N, unsigned int* error) {
 // 24-bit uniform in [0, 1): exact in FP32 and FP64
 __device__ __forceinline__ float u01f(unsigned w) { return (float)(w >> 8) * 5.9604644775390625e-08f; }
 __device__ __forceinline__ double u01d(unsigned w) { return (double)(w >> 8) * 5.9604644775390625e-08; }
+
+// The countdown pair G(w) (k | c << 12) from one Philox word w: u = (w >> 8) 2^-24,
+// r = log(1 - u) / log1p(-p_null), K = 1 + floor(r); (K, candidate) if K <= 4095, else (4095, not a
+// candidate: the particle waits 4095 steps and draws again).  The FP32 quotient (logf and the
+// division within 1 ulp and 0.5 ulp, log1p(-p_null) rounded once: relative error below 2.5e-7)
+// decides the floor unless it lies within 1e-6 r (at least 1e-6) of an integer; then the quotient is
+// taken in FP64 (log within 1 ulp).  A draw whose FP64 quotient lies within 1e-9 max(1, r) of an
+// integer is counted as near-threshold.
+__device__ __forceinline__ unsigned countdown_draw(const SpConst& K, unsigned w, unsigned* near) {
+  const float v = 1.0f - u01f(w);  // (0, 1], exact
+  const float r = logf(v) / K.lnq;
+  float fl = floorf(r);
+  if (!(fminf(r - fl, fl + 1.0f - r) > 1e-6f * fmaxf(r, 1.0f))) {
+    const double rd = log((double)v) / K.lnq_d;
+    const double fd = floor(rd);
+    const double tol = 1e-9 * fmax(1.0, rd);
+    if (near && rd > 0.0 && (rd - fd < tol || fd + 1.0 - rd < tol)) atomicAdd(near, 1u);
+    if (fd >= (double)PIC_NEXT_KMAX) return PIC_NEXT_KMAX;
+    return ((unsigned)fd + 1u) | PIC_NEXT_CAND;
+  }
+  if (fl >= (float)PIC_NEXT_KMAX) return PIC_NEXT_KMAX;
+  return ((unsigned)fl + 1u) | PIC_NEXT_CAND;
+}
+
+// The same pair with the quotient in FP64 throughout (the plain FP64 path).
+__device__ __forceinline__ unsigned countdown_draw_d(const SpConst& K, unsigned w, unsigned* near) {
+  const double rd = log(1.0 - u01d(w)) / K.lnq_d;
+  const double fd = floor(rd);
+  const double tol = 1e-9 * fmax(1.0, rd);
+  if (near && rd > 0.0 && (rd - fd < tol || fd + 1.0 - rd < tol)) atomicAdd(near, 1u);
+  if (fd >= (double)PIC_NEXT_KMAX) return PIC_NEXT_KMAX;
+  return ((unsigned)fd + 1u) | PIC_NEXT_CAND;
+}
+
+// The countdown pair of a particle of species s created in step `step` (the load: step 0; births,
+// source pairs, the products of a neutral's ionization): from word 0 of Philox(id, step, INIT, 2);
+// 0 for a species without the null-collision test.
+template <bool FP64 = false>
+__device__ __forceinline__ unsigned created_pair(const Phys& ph, int s, unsigned long long id,
+                                                 unsigned long long step) {
+  if (!((ph.mcc_mask >> s) & 1u)) return 0u;
+  const uint4 w = draw4(id, ph.seed, step, CH_INIT, 2u);
+  return FP64 ? countdown_draw_d(ph.sp[s], w.x, nullptr) : countdown_draw(ph.sp[s], w.x, nullptr);
+}
+
+// The cell word of such a particle in cell c.
+__device__ __forceinline__ int created_word(const Phys& ph, int s, int c, unsigned long long id,
+                                            unsigned long long step) {
+  return c | (int)(created_pair(ph, s, id, step) << PIC_CELL_BITS);
+}
+
 
 __host__ __device__ inline unsigned long long round_up4(unsigned long long n) { return (n + 3ull) & ~3ull; }
 
@@ -321,6 +384,9 @@ struct PoissonParams {
   Species32 nt_pad;  // neutrals: the buffer the neutral step wrote (padded to a multiple of 4)
   unsigned long long nt_cap;  // 0: no neutrals
   int nt_append;     // the neutral step ran in place: its new neutrals follow the old extent
+  const long long* R_in;  // exact path: the node deposits to solve (2 (N+1): species 0, then 1) in
+                          // place of this handle's own counts (a decomposed simulation's total)
+  int no_book;       // skip the per-step bookkeeping (a re-solve outside a step)
 };
 
 struct SortParams {
@@ -347,8 +413,7 @@ struct BSim {
   int cbase;                // first cell in the batch cell arrays
   int N;                    // cells
   unsigned long long seed;  // run seed
-  unsigned p_null_u24[2];   // null-collision probability (see SpConst)
-  unsigned collides;        // bit s: species s takes the null-collision test
+  unsigned collides;        // bit s: species s takes the null-collision test (its mcc_mask)
   unsigned cap[2];          // capacity of each species segment
   unsigned pad;
 };
@@ -440,6 +505,11 @@ cudaError_t launch_adj_reverse(const AdjRev& p, int max_grid, cudaStream_t st);
 cudaError_t launch_adj_tgrad(const AdjRev& p, const AdjState& s0, double* partial, int blocks, cudaStream_t st);
 
 cudaError_t launch_field(const PoissonParams& p, cudaStream_t st);
+// out[s (N+1) + j] = this handle's node deposit R_sj from its per-cell counts and weight sums
+cudaError_t launch_node_deposit(const PoissonParams& p, long long* out, cudaStream_t st);
+// particle decomposition: drop (mark dead) the live particles whose id % nparts != part
+cudaError_t launch_keep_subset(const Species32& a0, const Species32& a1, Ctl* ctl, unsigned part, unsigned nparts,
+                               cudaStream_t st);
 cudaError_t launch_step32(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_step64(const StepParams64& p, int grid, cudaStream_t st);
 cudaError_t launch_source32(const StepParams32& p, cudaStream_t st);
@@ -459,9 +529,14 @@ cudaError_t launch_diag64(const StepParams64& p, int grid, cudaStream_t st);
 cudaError_t launch_diag32(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_diag_grid(const long long* R0, const long long* R1, int sign0, int sign1, const double* E, int N,
                              double dx, Ctl* ctl, cudaStream_t st);
+// species: 0, 1 (charged: undrawn countdowns are drawn at `step`) or 2 (neutrals: plain cells)
 cudaError_t launch_restore32(const int* cell, const double* frac, const double* vx, const double* vy, const double* vz,
                              const unsigned long long* id, unsigned long long n, const Species32& dst,
-                             unsigned long long base, int N, cudaStream_t st);
+                             unsigned long long base, const Phys& ph, int species, unsigned long long step,
+                             cudaStream_t st);
+// plain path: the countdown pairs a snapshot left undrawn
+cudaError_t launch_fill_pairs64(unsigned* nk, const unsigned long long* id, unsigned long long n, const Phys& ph,
+                                int species, unsigned long long step, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                           cudaStream_t st);
 // *p = v, in stream order (v is taken at the call)

@@ -77,9 +77,10 @@ __device__ __forceinline__ unsigned wr_of(float f) {
   return __float2uint_rn(f * 4294967296.0f);
 }
 
-// Append one particle past the end of species s; returns false (and counts a drop) when full.
+// Append one particle past the end of species s (cw: its cell word); returns false (and counts a
+// drop) when full.
 template <int s>
-__device__ __forceinline__ bool append32(const StepParams32& P, unsigned long long ncur, int c, float f,
+__device__ __forceinline__ bool append32(const StepParams32& P, unsigned long long ncur, int cw, float f,
                                          const float* v, unsigned long long id) {
   unsigned long long slot = ncur + atomicAdd(&P.ctl->n_born[s], 1ull);
   if (slot >= P.cap[s]) {
@@ -88,7 +89,7 @@ __device__ __forceinline__ bool append32(const StepParams32& P, unsigned long lo
     return false;
   }
   const Species32& a = P.sp[s];
-  a.cell[slot] = c;
+  a.cell[slot] = cw;
   a.frac[slot] = f;
   a.vx[slot] = v[0];
   a.vy[slot] = v[1];
@@ -97,16 +98,15 @@ __device__ __forceinline__ bool append32(const StepParams32& P, unsigned long lo
   return true;
 }
 
-// Collision of a null-collision candidate electron (P_null test already passed): selects elastic,
-// excitation, ionization or null against u1 nu_max; ionization appends the new (e, ion) pair at
-// the parent's position and deposits it.  Returns the new velocity.
+// Collision of a null-collision candidate electron (its countdown expired; w: the draw (id, step,
+// COLL, 0)): selects elastic, excitation, ionization or null against u1 nu_max; ionization appends
+// the new (e, ion) pair at the parent's position and deposits it.  Returns the new velocity.
 __device__ __forceinline__ float4 collide_electron(const StepParams32& P, unsigned long long ncur0,
-                                                unsigned long long ncur1, unsigned long long id, int c,
+                                                unsigned long long ncur1, unsigned long long id, uint4 w, int c,
                                                 float f, float vx, float vy, float vz, BlockCounters* bc) {
   const Phys& ph = P.ph;
   const SpConst& k = ph.sp[0];
   const unsigned long long step = P.step;
-  uint4 w = draw4(id, ph.seed, step, CH_COLL, 0u);
   atomicAdd(&bc->coll[4], 1u);
   float v2 = vx * vx + vy * vy + vz * vz;
   float speed = sqrtf(v2);
@@ -154,13 +154,15 @@ __device__ __forceinline__ float4 collide_electron(const StepParams32& P, unsign
   float ci[3] = {ph.vt_gas * n0, ph.vt_gas * n1, ph.vt_gas * n2};
   atomicAdd(&bc->coll[2], 1u);
   const unsigned long long wr = wr_of(f);
-  if (append32<0>(P, ncur0, c, f, ce, (unsigned long long)kk.x | ((unsigned long long)kk.y << 32))) {
+  const unsigned long long ide = (unsigned long long)kk.x | ((unsigned long long)kk.y << 32);
+  const unsigned long long idi = (unsigned long long)kk.z | ((unsigned long long)kk.w << 32);
+  if (append32<0>(P, ncur0, created_word(ph, 0, c, ide, step), f, ce, ide)) {
     atomicAdd(P.cnt[0] + c, 1u);
     atomicAdd(P.S[0] + c, wr);
     atomicAdd(&bc->born[0], 1u);
     atomicAdd(&bc->ke[0], ke_fx32(ce[0], ce[1], ce[2], ph.sp[0].mass));
   }
-  if (append32<1>(P, ncur1, c, f, ci, (unsigned long long)kk.z | ((unsigned long long)kk.w << 32))) {
+  if (append32<1>(P, ncur1, created_word(ph, 1, c, idi, step), f, ci, idi)) {
     atomicAdd(P.cnt[1] + c, 1u);
     atomicAdd(P.S[1] + c, wr);
     atomicAdd(&bc->born[1], 1u);
@@ -169,11 +171,11 @@ __device__ __forceinline__ float4 collide_electron(const StepParams32& P, unsign
   return make_float4(spp * dx, spp * dy, spp * dz, 1.f);
 }
 
-// Charge exchange of a candidate ion: the ion leaves with a Maxwellian velocity at T_g.
+// Charge exchange of a candidate ion (w: the draw (id, step, COLL, 0)): the ion leaves with a
+// Maxwellian velocity at T_g.
 __device__ __forceinline__ float4 collide_ion(const Phys& ph, unsigned long long id, unsigned long long step,
-                                           float vx, float vy, float vz, BlockCounters* bc) {
+                                           uint4 w, float vx, float vy, float vz, BlockCounters* bc) {
   const SpConst& k = ph.sp[1];
-  uint4 w = draw4(id, ph.seed, step, CH_COLL, 0u);
   atomicAdd(&bc->coll[4], 1u);
   float speed = sqrtf(vx * vx + vy * vy + vz * vz);
   float b1 = ph.ngs_cx * speed;
@@ -228,11 +230,13 @@ constexpr int CHUNK = 32 * PIC_PPT;
 // stage buffer of one chunk: cell | frac | vx | vy | vz (4 B each) | id (8 B)
 constexpr int STAGE_BYTES = CHUNK * (5 * 4 + 8);
 
-// Collisions of the queued candidates, one per lane: each lane reloads its particle (just written
-// by this warp, so from L2), applies the collision and stores the new velocity.  About one
-// particle in a hundred is a candidate, so this runs every few dozen chunks and keeps the rare
-// code out of the streaming loop.
-__device__ __noinline__ void flush_queue(const StepParams32& P, const unsigned long long* q, int qn,
+// The queued particles whose null-collision countdown expired in this step, one per lane: each lane
+// reloads its particle (just written by this warp, so from L2), draws (id, step, COLL, 0), applies
+// the collision when the expiry is a candidate, stores the new velocity and the next countdown
+// (from word 0 of the same draw) in the cell word.  About one particle in a hundred expires per
+// step, so this runs every few dozen chunks, out of the streaming loop's path.  Inlined: as a
+// called function its register needs made the caller save registers around every call.
+__device__ __forceinline__ void flush_queue(const StepParams32& P, const unsigned long long* q, int qn,
                                          unsigned long long ncur0, unsigned long long ncur1, BlockCounters* bc) {
   __syncwarp();
   const int lane = threadIdx.x & 31;
@@ -243,38 +247,45 @@ __device__ __noinline__ void flush_queue(const StepParams32& P, const unsigned l
     const int s = (int)(rec >> 63);
     const unsigned long long i = rec & 0x7FFFFFFFFFFFFFFFull;
     const Species32 A = s ? P.sp[1] : P.sp[0];
-    const int c = A.cell[i];
+    const int cw = A.cell[i];
+    const int c = cw & PIC_CELL_MASK;
     const float f = A.frac[i];
     const unsigned long long id = A.id[i];
     const float vx = A.vx[i], vy = A.vy[i], vz = A.vz[i];
-    const float4 r = s == 0 ? collide_electron(P, ncur0, ncur1, id, c, f, vx, vy, vz, bc)
-                            : collide_ion(P.ph, id, P.step, vx, vy, vz, bc);
-    A.vx[i] = r.x;
-    A.vy[i] = r.y;
-    A.vz[i] = r.z;
+    const uint4 w = draw4(id, P.ph.seed, P.step, CH_COLL, 0u);
+    float4 r = make_float4(vx, vy, vz, 0.f);
+    if ((unsigned)cw >> (PIC_CELL_BITS + 12)) {  // the expiry is a candidate
+      r = s == 0 ? collide_electron(P, ncur0, ncur1, id, w, c, f, vx, vy, vz, bc)
+                 : collide_ion(P.ph, id, P.step, w, vx, vy, vz, bc);
+      A.vx[i] = r.x;
+      A.vy[i] = r.y;
+      A.vz[i] = r.z;
+    }
+    A.cell[i] = c | (int)(countdown_draw(P.ph.sp[s], w.x, &bc->near_thr[s]) << PIC_CELL_BITS);
     atomicAdd(&bc->ke[s], ke_fx32(r.x, r.y, r.z, P.ph.sp[s].mass));
   }
   __syncwarp();
 }
 
 // Lane 0 starts the bulk copies of the n particles [i0, i0 + n) (n <= CHUNK, a multiple of 4, i0
-// a multiple of 4) into a stage buffer.
+// a multiple of 4) into a stage buffer; the ids only when with_id (a step that moves particles to
+// new slots: the ordinary step needs no id, a particle whose countdown expires reloads its own).
 __device__ __forceinline__ void stage_issue_span(const Species32& A, unsigned i0, unsigned n, unsigned char* buf,
-                                                 unsigned long long* bar) {
-  mbar_expect_tx(bar, n * 28u);
+                                                 unsigned long long* bar, bool with_id) {
+  mbar_expect_tx(bar, n * (with_id ? 28u : 20u));
   tma_load_1d(buf, A.cell + i0, n * 4u, bar);
   tma_load_1d(buf + CHUNK * 4, A.frac + i0, n * 4u, bar);
   tma_load_1d(buf + CHUNK * 8, A.vx + i0, n * 4u, bar);
   tma_load_1d(buf + CHUNK * 12, A.vy + i0, n * 4u, bar);
   tma_load_1d(buf + CHUNK * 16, A.vz + i0, n * 4u, bar);
-  tma_load_1d(buf + CHUNK * 20, A.id + i0, n * 8u, bar);
+  if (with_id) tma_load_1d(buf + CHUNK * 20, A.id + i0, n * 8u, bar);
 }
 
 // Lane 0 starts the bulk copies of chunk t (ncur particles in the species) into a stage buffer.
 __device__ __forceinline__ void stage_issue(const Species32& A, unsigned t, unsigned ncur, unsigned char* buf,
-                                            unsigned long long* bar) {
+                                            unsigned long long* bar, bool with_id) {
   const unsigned i0 = t * CHUNK;
-  stage_issue_span(A, i0, min((unsigned)CHUNK, ncur - i0), buf, bar);
+  stage_issue_span(A, i0, min((unsigned)CHUNK, ncur - i0), buf, bar, with_id);
 }
 
 // Adds item idx (0 <= idx < 16) of a set of counters to a simulation's control block.

@@ -80,7 +80,8 @@ SYMBOLS = ("pic_workspace_size", "pic_init", "pic_step", "pic_sync", "pic_snapsh
            "pic_batch_reset", "pic_batch_get_field", "pic_batch_profile", "pic_batch_kernel_times",
            "pic_batch_free", "pic_adj_workspace_size", "pic_adj_init", "pic_adj_forward",
            "pic_adj_gradient", "pic_adj_schedule", "pic_adj_times", "pic_adj_free",
-           "pic_storage_order", "pic_batch_storage_order", "pic_adj_tape")
+           "pic_storage_order", "pic_batch_storage_order", "pic_adj_tape", "pic_keep_subset",
+           "pic_local_deposit", "pic_solve_deposit", "pic_step_begin", "pic_step_end")
 
 PIC_BATCH_MAX_SIMS = 4096
 
@@ -114,6 +115,11 @@ def lib():
         L.pic_selftest_timeout.argtypes = [V, P(C.c_double)]
         L.pic_get_field.argtypes = [V, P(C.c_int64), P(C.c_double), P(C.c_double), P(C.c_float),
                                     C.c_size_t]
+        L.pic_keep_subset.argtypes = [V, C.c_uint32, C.c_uint32]
+        L.pic_local_deposit.argtypes = [V, V]
+        L.pic_solve_deposit.argtypes = [V, V]
+        L.pic_step_begin.argtypes = [V, V]
+        L.pic_step_end.argtypes = [V, V]
         L.pic_storage_order.argtypes = [V, C.c_int32, P(C.c_int32), P(C.c_uint64), C.c_size_t,
                                         P(C.c_size_t)]
         L.pic_batch_storage_order.argtypes = [V, C.c_int32, C.c_int32, P(C.c_int32), P(C.c_uint64),
@@ -290,6 +296,30 @@ class Simulation:
                                    phi.ctypes.data_as(C.POINTER(C.c_double)),
                                    E.ctypes.data_as(C.POINTER(C.c_float)), n1), "pic_get_field")
         return {"R": R.reshape(2, n1), "rho": rho, "phi": phi, "E": E}
+
+    # ---- particle decomposition (the deposit tensors: int64 CUDA tensors of 2 (N + 1) values) ----
+    def _dep(self, R):
+        torch = _torch()
+        if not (isinstance(R, torch.Tensor) and R.dtype == torch.int64 and R.is_cuda and R.is_contiguous()
+                and R.numel() == 2 * (self.N + 1)):
+            raise PicError(1, "deposit tensor: a contiguous int64 CUDA tensor of 2 (N + 1) values")
+        return C.c_void_p(R.data_ptr())
+
+    def keep_subset(self, part: int, nparts: int):
+        """Keep the particles with id % nparts == part (this part of a decomposed simulation)."""
+        _check(lib().pic_keep_subset(self._h, int(part), int(nparts)), "pic_keep_subset")
+
+    def local_deposit(self, R):
+        _check(lib().pic_local_deposit(self._h, self._dep(R)), "pic_local_deposit")
+
+    def solve_deposit(self, R):
+        _check(lib().pic_solve_deposit(self._h, self._dep(R)), "pic_solve_deposit")
+
+    def step_begin(self, R):
+        _check(lib().pic_step_begin(self._h, self._dep(R)), "pic_step_begin")
+
+    def step_end(self, R):
+        _check(lib().pic_step_end(self._h, self._dep(R)), "pic_step_end")
 
     def storage_order(self, species: int):
         """(cell, id) of every slot of the species' particle buffer in storage order (the arranger's

@@ -1,7 +1,8 @@
 """One FP32 step of the GPU path against one FP64 step of the oracle from the same state.
 
 Tolerances (see the header of test_gpu_parity.py): |dv| <= 1e-5 |v| + 1e-6 v_th and |dx| <= 2e-6
-cells per particle matched by id; every other disagreement is a near-threshold collision draw,
+cells per particle matched by id, the null-collision countdown equal; every other disagreement is a
+near-threshold collision draw,
 counted by both codes; wall hits and candidate counts exact; the net deposit exactly 2^32 times
 the net particle charge; the field and deposit within the FP32 position error.
 """
@@ -40,7 +41,8 @@ def assert_one_step(p, blob, do, so_blob, fo, dg, sg_blob, fg):
         dv = np.abs(a["v"][ia] - b["v"][ib]).max(axis=1) if len(common) else np.zeros(0)
         okv = dv <= 1e-5 * np.abs(b["v"][ib]).max(axis=1) + 1e-6 * vt if len(common) else np.zeros(0, bool)
         okx = np.abs(xa - xb) <= 2e-6
-        bad = ~(okv & okx)
+        okn = a["next"][ia] == b["next"][ib]
+        bad = ~(okv & okx & okn)
         mismatched += int(bad.sum()) + only
     # every disagreement is a near-threshold collision draw (each can add a particle pair)
     assert mismatched <= 4 * near, (mismatched, near)

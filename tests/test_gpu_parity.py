@@ -455,15 +455,16 @@ def test_full_size_sampled_load_and_invariants(name):
 
 
 def _species_views(blob: bytes) -> list:
-    """(cell, frac, v columns, id) of each charged species of a snapshot, as views into the blob."""
+    """(cell, frac, v columns, id, countdown pair) of each charged species of a snapshot, as views
+    into the blob (cell and pair split from the cell word)."""
     n = struct.unpack_from("<QQ", blob, 32)
     off, out = snapfmt.HDR, []
     for m in n:
-        cell = np.frombuffer(blob, np.int32, m, off)
+        word = np.frombuffer(blob, np.uint32, m, off)
         frac = np.frombuffer(blob, np.float64, m, off + 4 * m)
         v = [np.frombuffer(blob, np.float64, m, off + 12 * m + 8 * m * k) for k in range(3)]
         ids = np.frombuffer(blob, np.uint64, m, off + 36 * m)
-        out.append((cell, frac, v, ids))
+        out.append(((word & snapfmt.CELL_MASK).astype(np.int32), frac, v, ids, word >> snapfmt.CELL_BITS))
         off += 44 * m
     return out
 
@@ -484,15 +485,15 @@ def test_full_size_sampled_step_matches_the_oracle_one_by_one():
     rng = np.random.default_rng(17)
     N = p["ncells"]
     for s in range(2):
-        cell, frac, v, ids = before[s]
+        cell, frac, v, ids, nk = before[s]
         # 2000 anywhere, and up to 300 in the wall cells, where particles leave
         edge = np.flatnonzero((cell == 0) | (cell == N - 1))
         idx = np.union1d(rng.choice(len(ids), 2000, replace=False),
                          rng.choice(edge, min(300, edge.size), replace=False))
         x0 = cell[idx] + frac[idx]
         v0 = np.stack([c[idx] for c in v], 1)
-        xo, vo, fl = O.step_sample(p, s, step, E, x0, v0, ids[idx])
-        cell1, frac1, v1, ids1 = after[s]
+        xo, vo, nko, fl = O.step_sample(p, s, step, E, x0, v0, ids[idx], nk[idx])
+        cell1, frac1, v1, ids1, nk1 = after[s]
         pos = np.minimum(np.searchsorted(ids1, ids[idx]), len(ids1) - 1)
         found = ids1[pos] == ids[idx]
         absorbed = (fl & 1) != 0
@@ -505,6 +506,7 @@ def test_full_size_sampled_step_matches_the_oracle_one_by_one():
         vt = math.sqrt(p["T"][s] / p["mass"][s])
         dv = np.abs(vg - vo[ok]).max(axis=1)
         bad = (dv > 1e-5 * np.abs(vo[ok]).max(axis=1) + 1e-6 * vt) | (np.abs(xg - xo[ok]) > 2e-6)
+        bad |= nk1[pos[ok]] != nko[ok]  # the null-collision countdown: exact
         assert int((bad & ~near[ok]).sum()) == 0, (s, int(bad.sum()))
         if s == 0:  # electrons: some sampled ones leave, some are collision candidates (P_null 1 %)
             assert int(absorbed.sum()) > 0

@@ -392,10 +392,10 @@ def test_blobs_of_other_configurations_or_versions_are_refused():
     p = W.variant(W.SMALL_C6, **ROOMY)
     g = pic.Simulation(p)
     good = g.snapshot()
-    assert snapfmt.parse(good)["version"] == 2
+    assert snapfmt.parse(good)["version"] == 4
     assert g.restore(good[:-9] + good[-4:]) == 5                   # truncated: PIC_ECORRUPT
     other = pic.Simulation(W.variant(p, K_iz=0.25)).snapshot()     # other physics: other hash
     assert g.restore(other) == 5
     plain = pic.Simulation(W.variant(p, neutrals=0, neutral_ppc=0)).snapshot()
-    assert snapfmt.parse(plain)["version"] == 1 and g.restore(plain) == 5
+    assert snapfmt.parse(plain)["version"] == 3 and g.restore(plain) == 5
     assert g.restore(good) == 0

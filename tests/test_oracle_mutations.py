@@ -62,8 +62,8 @@ MUTATIONS = [
     ("adjoint: field transpose wall sign", "pic_adjoint.c", "if (k == 1) a -= mu[0] / dx;",
      "if (k == 1) a += mu[0] / dx;", PINS_ADJ),
     ("adjoint: initial field's bias term dropped", "pic_adjoint.c",
-     "    for (int32_t j = 0; j <= N; ++j) gV += mu[j] / ((double)N * m.dx);\n    double gT",
-     "    double gT", PINS_ADJ),
+     "  for (int32_t j = 0; j <= N; ++j) gV += mu[j] / ((double)N * m.dx);\n  double gT",
+     "  double gT", PINS_ADJ),
     ("adjoint: temperature chain factor", "pic_adjoint.c", "grad[1] = gT / (2.0 * c->T[0]);",
      "grad[1] = gT / c->T[0];", PINS_ADJ),
     ("adjoint: position update without 1/dx", "pic_adjoint.c", "lv[3 * p] += lx[p] * c->dt / m.dx;",
@@ -104,6 +104,13 @@ MUTATIONS = [
      "const double vt = sqrt(c->T[1] / c->mass[1]);\n    uint32_t w[4];", PINS_SHEATH),
     ("snapshot restore drops the ionization count", "pic_oracle.c", "get(&q, &s->nt_ionized, 8);",
      "q += 8;", PINS_SHEATH),
+    ("countdown: the cap's expiry taken as a candidate", "pic_oracle.c",
+     "if (fl >= (double)NEXT_KMAX) return NEXT_KMAX;", "if (fl >= (double)NEXT_KMAX) return NEXT_KMAX | NEXT_CAND;",
+     PINS_MAIN),
+    ("countdown: one step too long", "pic_oracle.c", "return ((uint32_t)fl + 1u) | NEXT_CAND;",
+     "return ((uint32_t)fl + 2u) | NEXT_CAND;", PINS_MAIN),
+    ("countdown: geometric parameter linearised", "pic_oracle.c", "log(v) / log1p(-(double)p_null)",
+     "log(v) / (-(double)p_null)", PINS_MAIN),
 ]
 
 

@@ -381,13 +381,15 @@ def test_step_sample_is_the_step_one_particle_at_a_time():
     o.step(3)
     d0, E = o.diag(), o.fields()["E"]
     before = [o.particles(s) for s in range(2)]
-    out = [O.step_sample(p, s, d0["step"], E, *before[s]) for s in range(2)]
+    nk0 = [o.countdown(s) for s in range(2)]
+    out = [O.step_sample(p, s, d0["step"], E, *before[s], nk0[s]) for s in range(2)]
     o.step(1)
     d1 = o.diag()
     for s in range(2):
         x0, v0, id0 = before[s]
-        xs, vs, fl = out[s]
+        xs, vs, nks, fl = out[s]
         x1, v1, id1 = o.particles(s)
+        nk1 = o.countdown(s)
         absorbed = (fl & 1) != 0
         assert int(absorbed.sum()) == sum(d1["wall_hits"][s]) - sum(d0["wall_hits"][s])
         # every survivor, matched by id (births carry new ids; a sort may reorder)
@@ -398,10 +400,11 @@ def test_step_sample_is_the_step_one_particle_at_a_time():
         assert np.array_equal(id1[j], id0[keep])
         assert np.array_equal(x1[j], xs[keep])
         assert np.array_equal(v1[j], vs[keep])
+        assert np.array_equal(nk1[j], nks[keep])
         assert not np.isin(id0[absorbed], id1).any()
-    assert sum(int(((f & 2) != 0).sum()) for _, _, f in out) == d1["coll"][4] - d0["coll"][4]
-    assert sum(int(((f & 4) != 0).sum()) for _, _, f in out) == sum(d1["near_threshold"]) - sum(d0["near_threshold"])
-    assert int(((out[0][2] & 8) != 0).sum()) == d1["births"][0] - d0["births"][0] > 0
+    assert sum(int(((f & 2) != 0).sum()) for *_, f in out) == d1["coll"][4] - d0["coll"][4]
+    assert sum(int(((f & 4) != 0).sum()) for *_, f in out) == sum(d1["near_threshold"]) - sum(d0["near_threshold"])
+    assert int(((out[0][3] & 8) != 0).sum()) == d1["births"][0] - d0["births"][0] > 0
 
 
 def test_step_sample_uniform_field_is_uniform_acceleration():
@@ -412,10 +415,70 @@ def test_step_sample_uniform_field_is_uniform_acceleration():
     x = rng.uniform(5.0, p["ncells"] - 5.0, n)
     v = rng.normal(size=(n, 3)) * 0.1
     for s in range(2):
-        xo, vo, fl = O.step_sample(p, s, 0, np.zeros(p["ncells"] + 1), x, v, np.arange(n, dtype=np.uint64))
+        xo, vo, nko, fl = O.step_sample(p, s, 0, np.zeros(p["ncells"] + 1), x, v, np.arange(n, dtype=np.uint64),
+                                        np.zeros(n, np.uint32))
+        assert np.all(nko == 0)  # no null-collision test: no countdown
         a = p["charge"][s] / p["mass"][s] * p["E_ext"] * p["dt"]
         dx = p["L"] / p["ncells"]
         assert np.all(fl == 0)
         assert np.allclose(vo[:, 0], v[:, 0] + a, rtol=0, atol=1e-14)
         assert np.array_equal(vo[:, 1:], v[:, 1:])
         assert np.allclose(xo, x + vo[:, 0] * p["dt"] / dx, rtol=0, atol=1e-12)
+
+
+def _candidate_flags(p, s, n, steps):
+    """Candidate flags (steps x n) of n nearly cold particles of species s under no field: their
+    process frequencies vanish, so every candidate is a null collision and nothing else changes."""
+    o = O.OracleSim(W.variant(p, ncells=64, L=64.0, ppc=(max(1, n // 64), max(1, n // 64))))
+    x, _v, ids = o.particles(s)
+    nk = o.countdown(s)
+    x, ids, nk = x[:n], ids[:n], nk[:n]
+    v = np.full((len(x), 3), 1e-9)
+    E = np.zeros(p["ncells"] + 1)
+    flags = np.empty((steps, len(x)), bool)
+    for t in range(steps):
+        x, v, nk, fl = O.step_sample(p, s, t, E, x, v, ids, nk)
+        assert not (fl & 1).any()
+        flags[t] = (fl & 2) != 0
+    return flags
+
+
+@pytest.mark.parametrize("p_target", [0.04, 6e-4])
+def test_countdown_candidates_are_bernoulli_per_step(p_target):
+    # R17 replaces the per-step Bernoulli(P_null) test by a geometric countdown; in law the candidate
+    # process must be the same: i.i.d. Bernoulli(P_null) per particle and step.  Checked: the rate
+    # (binomial, 5 sigma), the spread of the per-step counts (binomial dispersion), and the waiting
+    # times to a particle's next candidate (geometric, chi-square over a fixed window; a wait longer
+    # than the window counts in the last bin).  The small P_null also exercises the countdown cap
+    # (K > 4095 waits 4095 steps and draws again): a bin isolates waits of exactly 4095 steps.
+    base = W.variant(W.SMALL_C1, field_mode=W.FIELD_ZERO, coll_mask=W.COLL_EL, E_cap=0.5, n_gas=1.0)
+    # nu_max dt = n_gas sigma_el v_cap dt with v_cap = 1 (E_cap = 0.5, m = 1): pick sigma_el
+    p = W.variant(base, sigma_el=-np.log1p(-p_target) / base["dt"])
+    pn = float(O.nu_max(p)[1][0])
+    q = 1.0 - pn
+    n, steps = (3000, 600) if p_target > 0.01 else (1500, 9000)
+    f = _candidate_flags(p, 0, n, steps)
+    tot, trials = int(f.sum()), f.size
+    assert abs(tot - trials * pn) <= 5 * np.sqrt(trials * pn * (1 - pn)), (tot, trials * pn)
+    per_step = f.sum(axis=1)
+    disp = per_step.var(ddof=1) / (f.shape[1] * pn * (1 - pn))
+    assert abs(disp - 1.0) <= 6 * np.sqrt(1.0 / (f.shape[1] * pn * steps) + 2.0 / (steps - 1)), disp
+    # waits from each start (the beginning, or a candidate) early enough to see a full window
+    L = steps // 2
+    waits = []
+    for j in range(f.shape[1]):
+        t = np.flatnonzero(f[:, j])
+        for t0 in np.concatenate([[-1], t]):
+            if t0 + L >= steps:
+                break
+            nxt = t[t > t0]
+            waits.append(nxt[0] - t0 if len(nxt) and nxt[0] - t0 <= L else L + 1)  # L + 1: longer than L
+    waits = np.array(waits)
+    sf = lambda k: q ** (k - 1)  # P(wait >= k)
+    edges = np.unique(np.concatenate([[1], 1 + np.ceil(np.log(np.linspace(1, 0.03, 12)[1:]) / np.log(q)),
+                                      [4095, 4096, 4097] if L > 4097 else [], [L + 1]]).astype(int))
+    edges = edges[edges <= L + 1]
+    obs = [((waits >= a) & (waits < b)).sum() for a, b in zip(edges[:-1], edges[1:])] + [(waits >= edges[-1]).sum()]
+    exp = [len(waits) * (sf(a) - sf(b)) for a, b in zip(edges[:-1], edges[1:])] + [len(waits) * sf(edges[-1])]
+    chi2 = sum((o_ - e_) ** 2 / max(e_, 1.0) for o_, e_ in zip(obs, exp))
+    assert chi2 < 45, (chi2, list(zip(edges.tolist(), obs, np.round(exp, 1))))

@@ -296,7 +296,7 @@ def test_snapshot_continuation_and_thread_count_give_the_same_bytes():
     O.set_threads(1)
     a.step(2)
     mid = a.snapshot()
-    assert snapfmt.parse(mid)["version"] == 2
+    assert snapfmt.parse(mid)["version"] == 4
     b = _sim_from(p, mid)
     c = _sim_from(p, blob, threads=4)
     O.set_threads(1)
@@ -306,7 +306,7 @@ def test_snapshot_continuation_and_thread_count_give_the_same_bytes():
     c.step(6)
     O.set_threads(1)
     assert a.snapshot() == b.snapshot() == c.snapshot()
-    # the sheath fields are part of the configuration hash; a version-1 reader refuses the blob
+    # the sheath fields are part of the configuration hash; a version-3 reader refuses the blob
     assert O.config_hash(p) != O.config_hash(W.variant(p, K_iz=0.25))
     assert O.config_hash(W.C3) == O.config_hash(W.variant(W.C3, recycle=0.5, T_rec=2.0))
     assert O.OracleSim(W.variant(p, neutrals=0, neutral_ppc=0)).restore(mid) != 0
