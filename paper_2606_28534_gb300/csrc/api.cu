@@ -1238,6 +1238,14 @@ uint32_t pic_blob_crc32(const void* p, size_t n) {
     if (sms <= 0) sms = 152;
     h->grid_step = sms * (h->plain ? occupancy_step64() : occupancy_step32());
     h->grid_scatter = h->plain ? 0 : sms * occupancy_step32(true);
+    {  // small runs: no more CTAs than the particle capacity can keep busy (a warp per chunk of
+       // 128 particles, a thread per particle on the plain path); large runs fill every SM
+      const unsigned long long room = h->cap[0] + h->cap[1];
+      const unsigned long long need = h->plain ? (room + 255) / 256 : (room + PIC_TILE - 1) / PIC_TILE;
+      const int cap_grid = (int)std::max<unsigned long long>(1ull, std::min<unsigned long long>(need, 1ull << 20));
+      h->grid_step = std::min(h->grid_step, cap_grid);
+      if (!h->plain) h->grid_scatter = std::min(h->grid_scatter, cap_grid);
+    }
     h->grid_sort = sms * 16;
     h->grid_diag = sms * 8;
     h->grid_neutral = h->cap_nt ? sms * occupancy_neutral32() : 0;

@@ -22,10 +22,18 @@
 
 namespace {
 
-constexpr int NSTAGE = 2;   // chunks in flight per warp (TMA double buffer)
 static_assert(PIC_PPT == 4, "each lane moves four particles: one 128-bit access per array");
 constexpr int WARPS = PIC_TPB / 32;
-constexpr size_t STEP_SMEM = (size_t)WARPS * (NSTAGE * STAGE_BYTES + QCAP * 8 + NSTAGE * 8);
+#ifndef PIC_STEP_NSTAGE
+#define PIC_STEP_NSTAGE 2  // chunks in flight per warp in the ordinary step (3 measured slower)
+#endif
+// Per variant: TMA stages per warp and the bytes of one stage (the ordinary step stages no ids).
+template <bool SCATTER>
+struct StepShape {
+  static constexpr int NSTAGE = SCATTER ? 2 : PIC_STEP_NSTAGE;
+  static constexpr int SB = SCATTER ? STAGE_BYTES : CHUNK * 20;
+  static constexpr size_t SMEM = (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + NSTAGE * 8);
+};
 
 // One warp handles chunks of 32 x PIC_PPT consecutive particles of one species (a contiguous run
 // of chunks per warp; strided over the warps of the grid in the step after a sort); the warp's next
@@ -47,14 +55,16 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
     k_step32(const __grid_constant__ StepParams32 P) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ BlockCounters bc;
+  constexpr int NSTAGE = StepShape<SCATTER>::NSTAGE;
+  constexpr int SB = StepShape<SCATTER>::SB;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, wib = tid >> 5;
-  unsigned char* const stage = dsm + (size_t)wib * NSTAGE * STAGE_BYTES;
+  unsigned char* const stage = dsm + (size_t)wib * NSTAGE * SB;
   unsigned long long* const q =
-      reinterpret_cast<unsigned long long*>(dsm + (size_t)WARPS * NSTAGE * STAGE_BYTES) + (size_t)wib * QCAP;
+      reinterpret_cast<unsigned long long*>(dsm + (size_t)WARPS * NSTAGE * SB) + (size_t)wib * QCAP;
   unsigned long long* const bar = reinterpret_cast<unsigned long long*>(
-                                      dsm + (size_t)WARPS * (NSTAGE * STAGE_BYTES + QCAP * 8)) + wib * NSTAGE;
+                                      dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8)) + wib * NSTAGE;
   if (tid < (int)(sizeof(BlockCounters) / 4)) reinterpret_cast<unsigned int*>(&bc)[tid] = 0u;
   if (lane < NSTAGE) mbar_init(bar + lane, 1u);
   mbar_init_fence();
@@ -100,7 +110,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
 #pragma unroll
       for (int st = 0; st < NSTAGE; ++st) {
         const unsigned t = t_first + st * t_inc;
-        if (t < t_end) stage_issue(Asrc, t, ncur, stage + st * STAGE_BYTES, bar + st, SCATTER);
+        if (t < t_end) stage_issue(Asrc, t, ncur, stage + st * SB, bar + st, SCATTER);
       }
     }
     int st = 0;
@@ -111,7 +121,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         break;
       }
       parity ^= 1u << st;
-      const unsigned char* const buf = stage + st * STAGE_BYTES;
+      const unsigned char* const buf = stage + st * SB;
       const unsigned i0 = t * CHUNK + lane * PIC_PPT;
       int c[PIC_PPT];
       float f[PIC_PPT], vx[PIC_PPT], vy[PIC_PPT], vz[PIC_PPT];
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
       __syncwarp();
       if (lane == 0) {
         const unsigned tn = t + NSTAGE * t_inc;
-        if (tn < t_end) stage_issue(Asrc, tn, ncur, stage + st * STAGE_BYTES, bar + st, SCATTER);
+        if (tn < t_end) stage_issue(Asrc, tn, ncur, stage + st * SB, bar + st, SCATTER);
       }
       st = st + 1 == NSTAGE ? 0 : st + 1;
 
@@ -384,7 +394,8 @@ int occupancy_step32(bool scatter) {
   step32_attrs();
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, scatter ? k_step32<true> : k_step32<false>, PIC_TPB,
-                                                    STEP_SMEM) != cudaSuccess ||
+                                                    scatter ? StepShape<true>::SMEM : StepShape<false>::SMEM) !=
+                                                        cudaSuccess ||
       b < 1)
     b = 1;
   return b;
@@ -393,21 +404,21 @@ int occupancy_step32(bool scatter) {
 static void step32_attrs() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_step32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STEP_SMEM);
-    cudaFuncSetAttribute(k_step32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STEP_SMEM);
+    cudaFuncSetAttribute(k_step32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StepShape<false>::SMEM);
+    cudaFuncSetAttribute(k_step32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StepShape<true>::SMEM);
     done = true;
   }
 }
 
 cudaError_t launch_step32(const StepParams32& p, int grid, cudaStream_t st) {
   step32_attrs();
-  k_step32<false><<<grid, PIC_TPB, STEP_SMEM, st>>>(p);
+  k_step32<false><<<grid, PIC_TPB, StepShape<false>::SMEM, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step32_scatter(const StepParams32& p, int grid, cudaStream_t st) {
   step32_attrs();
-  k_step32<true><<<grid, PIC_TPB, STEP_SMEM, st>>>(p);
+  k_step32<true><<<grid, PIC_TPB, StepShape<true>::SMEM, st>>>(p);
   return cudaGetLastError();
 }
 
