@@ -125,7 +125,6 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
       const unsigned i0 = t * CHUNK + lane * PIC_PPT;
       int c[PIC_PPT];
       float f[PIC_PPT], vx[PIC_PPT], vy[PIC_PPT], vz[PIC_PPT];
-      unsigned long long id[PIC_PPT];  // the step after a sort moves the ids; the ordinary step needs none
       const bool have = i0 < ncur;
       {
         const int4 c4 = reinterpret_cast<const int4*>(buf)[lane];
@@ -138,13 +137,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         vx[0] = x4.x; vx[1] = x4.y; vx[2] = x4.z; vx[3] = x4.w;
         vy[0] = y4.x; vy[1] = y4.y; vy[2] = y4.z; vy[3] = y4.w;
         vz[0] = z4.x; vz[1] = z4.y; vz[2] = z4.z; vz[3] = z4.w;
-        if (SCATTER) {
-          const ulonglong2 id01 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane];
-          const ulonglong2 id23 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane + 1];
-          id[0] = id01.x; id[1] = id01.y; id[2] = id23.x; id[3] = id23.y;
-        } else {
-          id[0] = id[1] = id[2] = id[3] = 0ull;
-        }
+
       }
       if (!have) {
 #pragma unroll
@@ -160,27 +153,19 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         e2[k] = make_float2(0.f, 0.f);
         if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL) e2[k] = __ldg(P.E2 + (c[k] & PIC_CELL_MASK));
       }
-      // scatter: claim each live particle's slot in its cell (four atomics in flight; their results
-      // are first needed at the stores, so the Philox work below covers their latency)
-      unsigned slot[PIC_PPT], peers[PIC_PPT], base[PIC_PPT];
-      if (SCATTER) {
-#pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k) {
-          const bool live = c[k] != PIC_DEAD_CELL;
-          const int cell = c[k] & PIC_CELL_MASK;
-          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cell : -1);
-          base[k] = 0u;
-          if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(P.cursor[s] + cell, (unsigned)__popc(peers[k]));
+      // the ordinary step has read its stage: refill it with the chunk NSTAGE steps ahead (the step
+      // after a sort reads the start-of-step cells and the ids from it again at its stores, and
+      // refills it after them)
+      unsigned char* const sbuf = stage + st * SB;
+      if (!SCATTER) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          const unsigned tn = t + NSTAGE * t_inc;
+          if (tn < t_end) stage_issue(Asrc, tn, ncur, sbuf, bar + st, false);
         }
+        st = st + 1 == NSTAGE ? 0 : st + 1;
       }
-      // the stage is read: refill it with the chunk NSTAGE steps ahead
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        const unsigned tn = t + NSTAGE * t_inc;
-        if (tn < t_end) stage_issue(Asrc, tn, ncur, stage + st * SB, bar + st, SCATTER);
-      }
-      st = st + 1 == NSTAGE ? 0 : st + 1;
 
       unsigned live0 = 0u;  // live at the start of the step (scatter: owns a slot)
 #pragma unroll
@@ -217,10 +202,25 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
           }
         }
       }
+      unsigned slot[PIC_PPT];
       if (SCATTER) {
+        // claim each particle's slot in the cell it held at the start of the step (one atomic per
+        // (warp, cell) group and particle index; the start-of-step cells are still in the stage)
+        const int4 c4 = reinterpret_cast<const int4*>(sbuf)[lane];
+        const int c0[PIC_PPT] = {c4.x, c4.y, c4.z, c4.w};
+        unsigned peers[PIC_PPT], base[PIC_PPT];
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          const bool live = (live0 >> k) & 1u;
+          const int cell = c0[k] & PIC_CELL_MASK;
+          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cell : -1);
+          base[k] = 0u;
+          if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(P.cursor[s] + cell, (unsigned)__popc(peers[k]));
+        }
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k)
           slot[k] = __shfl_sync(0xFFFFFFFFu, base[k], __ffs(peers[k]) - 1) + (unsigned)__popc(peers[k] & below);
+        const unsigned long long* const sid = reinterpret_cast<const unsigned long long*>(sbuf + CHUNK * 20);
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
           if (!((live0 >> k) & 1u)) continue;
@@ -236,8 +236,16 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
           A.vx[j] = vx[k];
           A.vy[j] = vy[k];
           A.vz[j] = vz[k];
-          A.id[j] = id[k];
+          A.id[j] = sid[lane * PIC_PPT + k];
         }
+        // the stage is read: refill it with the chunk NSTAGE steps ahead
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          const unsigned tn = t + NSTAGE * t_inc;
+          if (tn < t_end) stage_issue(Asrc, tn, ncur, sbuf, bar + st, true);
+        }
+        st = st + 1 == NSTAGE ? 0 : st + 1;
       } else if (have && moves) {
         *reinterpret_cast<int4*>(A.cell + i0) = make_int4(c[0], c[1], c[2], c[3]);
         *reinterpret_cast<float4*>(A.frac + i0) = make_float4(f[0], f[1], f[2], f[3]);
