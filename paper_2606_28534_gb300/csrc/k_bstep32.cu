@@ -33,10 +33,13 @@ struct WarpSim {
   unsigned long long seed;
 };
 
-template <int TPB, int NST>
+// Shared memory of a shape: per warp NST stage buffers (the ordinary step stages no ids), the
+// collision queue and the stage barriers.
+template <int TPB, int NST, bool SCATTER>
 struct BShape {
   static constexpr int WARPS = TPB / 32;
-  static constexpr size_t SMEM = (size_t)WARPS * (NST * STAGE_BYTES + QCAP * 8 + NST * 8);
+  static constexpr int SB = SCATTER ? STAGE_BYTES : CHUNK * 20;
+  static constexpr size_t SMEM = (size_t)WARPS * (NST * SB + QCAP * 8 + NST * 8);
 };
 
 // Last k < nsims with pre[k] <= t, for t < pre[nsims]: the simulation that owns chunk t.
@@ -91,6 +94,7 @@ __device__ __forceinline__ void leave_sim(const BatchStep32& B, int k, int s, co
 template <int TPB, int MINB, int NST, bool SCATTER>
 __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ BatchStep32 B) {
   constexpr int WARPS = TPB / 32;
+  constexpr int SB = BShape<TPB, NST, SCATTER>::SB;
   static_assert(sizeof(BlockCounters) / 4 <= 32, "one word of the counters per lane");
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ BlockCounters wcs[WARPS];
@@ -98,11 +102,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, wib = tid >> 5;
-  unsigned char* const stage = dsm + (size_t)wib * NST * STAGE_BYTES;
+  unsigned char* const stage = dsm + (size_t)wib * NST * SB;
   unsigned long long* const q =
-      reinterpret_cast<unsigned long long*>(dsm + (size_t)WARPS * NST * STAGE_BYTES) + (size_t)wib * QCAP;
+      reinterpret_cast<unsigned long long*>(dsm + (size_t)WARPS * NST * SB) + (size_t)wib * QCAP;
   unsigned long long* const bar = reinterpret_cast<unsigned long long*>(
-                                      dsm + (size_t)WARPS * (NST * STAGE_BYTES + QCAP * 8)) + wib * NST;
+                                      dsm + (size_t)WARPS * (NST * SB + QCAP * 8)) + wib * NST;
   BlockCounters& wc = wcs[wib];
   if (lane < (int)(sizeof(BlockCounters) / 4)) reinterpret_cast<unsigned int*>(&wc)[lane] = 0u;
   if (lane < NST) mbar_init(bar + lane, 1u);
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         const unsigned t = t0 + st;
         if (t < t1) {
           while (pre[ki + 1] <= t) ++ki;
-          issue_chunk(B, Asrc, s, ki, t - pre[ki], stage + st * STAGE_BYTES, bar + st, SCATTER);
+          issue_chunk(B, Asrc, s, ki, t - pre[ki], stage + st * SB, bar + st, SCATTER);
         }
       }
     }
@@ -180,11 +184,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         break;
       }
       parity ^= 1u << st;
-      const unsigned char* const buf = stage + st * STAGE_BYTES;
+      const unsigned char* const buf = stage + st * SB;
       const unsigned i0 = (t - kbeg) * CHUNK + lane * PIC_PPT;  // index in the simulation's segment
       int c[PIC_PPT];
       float f[PIC_PPT], vx[PIC_PPT], vy[PIC_PPT], vz[PIC_PPT];
-      unsigned long long id[PIC_PPT];
       const bool have = i0 < ws.nk;
       {
         const int4 c4 = reinterpret_cast<const int4*>(buf)[lane];
@@ -197,13 +200,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         vx[0] = x4.x; vx[1] = x4.y; vx[2] = x4.z; vx[3] = x4.w;
         vy[0] = y4.x; vy[1] = y4.y; vy[2] = y4.z; vy[3] = y4.w;
         vz[0] = z4.x; vz[1] = z4.y; vz[2] = z4.z; vz[3] = z4.w;
-        if (SCATTER) {
-          const ulonglong2 id01 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane];
-          const ulonglong2 id23 = reinterpret_cast<const ulonglong2*>(buf + CHUNK * 20)[2 * lane + 1];
-          id[0] = id01.x; id[1] = id01.y; id[2] = id23.x; id[3] = id23.y;
-        } else {
-          id[0] = id[1] = id[2] = id[3] = 0ull;
-        }
       }
       if (!have) {
 #pragma unroll
@@ -218,39 +214,27 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL)
           e2[k] = __ldg(B.E2 + (ws.cbase + (c[k] & PIC_CELL_MASK)));
       }
-      // the step after a sort: claim each live particle's slot in its cell (four atomics in flight)
-      unsigned slot[PIC_PPT];
-      if (SCATTER) {
-        const int cb = ws.cbase;
-        unsigned peers[PIC_PPT], base[PIC_PPT];
-#pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k) {
-          const bool live = c[k] != PIC_DEAD_CELL;
-          const int cell = cb + (c[k] & PIC_CELL_MASK);
-          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cell : -1);
-          base[k] = 0u;
-          if (live && lane == __ffs(peers[k]) - 1)
-            base[k] = atomicAdd(B.cursor[s] + cell, (unsigned)__popc(peers[k]));
-        }
-#pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k)
-          slot[k] = __shfl_sync(0xFFFFFFFFu, base[k], __ffs(peers[k]) - 1) + (unsigned)__popc(peers[k] & below);
-      }
       unsigned live0 = 0u;  // live at the start of the step (the step after a sort: owns a slot)
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) live0 |= c[k] != PIC_DEAD_CELL ? (1u << k) : 0u;
-      // the stage is read: refill it with the chunk NST steps ahead
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        const unsigned tn = t + NST;
-        if (tn < t1) {
-          int ki = kc;  // owner of chunk tn: this simulation or a later one
-          while (pre[ki + 1] <= tn) ++ki;
-          issue_chunk(B, Asrc, s, ki, tn - pre[ki], stage + st * STAGE_BYTES, bar + st, SCATTER);
+      // the ordinary step has read its stage: refill it with the chunk NST steps ahead (the step
+      // after a sort reads the start-of-step cells and the ids from it again at its stores, and
+      // refills it after them)
+      unsigned char* const sbuf = stage + st * SB;
+      const auto refill = [&](bool with_id) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          const unsigned tn = t + NST;
+          if (tn < t1) {
+            int ki = kc;  // owner of chunk tn: this simulation or a later one
+            while (pre[ki + 1] <= tn) ++ki;
+            issue_chunk(B, Asrc, s, ki, tn - pre[ki], sbuf, bar + st, with_id);
+          }
         }
-      }
-      st = st + 1 == NST ? 0 : st + 1;
+        st = st + 1 == NST ? 0 : st + 1;
+      };
+      if (!SCATTER) refill(false);
 
       unsigned cand = 0u;  // the null-collision countdown expired in this step (queued)
       const bool collides = ws.mcc != 0u;
@@ -279,7 +263,27 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
           }
         }
       }
+      unsigned slot[PIC_PPT];
       if (SCATTER) {
+        // claim each particle's slot in the cell it held at the start of the step (one atomic per
+        // (warp, cell) group and particle index; the start-of-step cells are still in the stage)
+        const int cb = ws.cbase;
+        const int4 c4 = reinterpret_cast<const int4*>(sbuf)[lane];
+        const int c0[PIC_PPT] = {c4.x, c4.y, c4.z, c4.w};
+        unsigned peers[PIC_PPT], base[PIC_PPT];
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          const bool live = (live0 >> k) & 1u;
+          const int cell = cb + (c0[k] & PIC_CELL_MASK);
+          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cell : -1);
+          base[k] = 0u;
+          if (live && lane == __ffs(peers[k]) - 1)
+            base[k] = atomicAdd(B.cursor[s] + cell, (unsigned)__popc(peers[k]));
+        }
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k)
+          slot[k] = __shfl_sync(0xFFFFFFFFu, base[k], __ffs(peers[k]) - 1) + (unsigned)__popc(peers[k] & below);
+        const unsigned long long* const sid = reinterpret_cast<const unsigned long long*>(sbuf + CHUNK * 20);
         const unsigned seg = ws.seg, cap = ws.cap;
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
@@ -296,8 +300,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
           A.vx[j] = vx[k];
           A.vy[j] = vy[k];
           A.vz[j] = vz[k];
-          A.id[j] = id[k];
+          A.id[j] = sid[lane * PIC_PPT + k];
         }
+        refill(true);
       } else if (have && moves) {
         const unsigned g = ws.seg + i0;
         *reinterpret_cast<int4*>(A.cell + g) = make_int4(c[0], c[1], c[2], c[3]);
@@ -475,7 +480,7 @@ __global__ void __launch_bounds__(PLAN_TPB) k_bplan(const BatchPlan P) {
 
 template <int TPB, int MINB, int NST, bool SCATTER>
 cudaError_t launch_variant(const BatchStep32& p, int grid, cudaStream_t st) {
-  constexpr size_t smem = BShape<TPB, NST>::SMEM;
+  constexpr size_t smem = BShape<TPB, NST, SCATTER>::SMEM;
   static bool done = false;
   if (!done) {
     cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST, SCATTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -488,12 +493,12 @@ cudaError_t launch_variant(const BatchStep32& p, int grid, cudaStream_t st) {
 
 template <int TPB, int MINB, int NST>
 int occupancy_variant() {
-  constexpr size_t smem = BShape<TPB, NST>::SMEM;
+  constexpr size_t smem0 = BShape<TPB, NST, false>::SMEM, smem1 = BShape<TPB, NST, true>::SMEM;
   int occ[2] = {0, 0};
-  cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_bstep32<TPB, MINB, NST, false>, TPB, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_bstep32<TPB, MINB, NST, true>, TPB, smem);
+  cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0);
+  cudaFuncSetAttribute(k_bstep32<TPB, MINB, NST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_bstep32<TPB, MINB, NST, false>, TPB, smem0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_bstep32<TPB, MINB, NST, true>, TPB, smem1);
   const int b = occ[0] < occ[1] ? occ[0] : occ[1];
   return b < 1 ? 1 : b;
 }
