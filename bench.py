@@ -44,11 +44,10 @@ BYTES_STEP_KERNEL = 40
 BYTES_SCATTER_KERNEL = 56
 # DRAM bytes per particle of one launch, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of these kernels on the 12.6M-particle profiling case (c3p), scaled by
-# particles to a full launch: the ordinary step and the step after a sort (None: not captured for
-# the kernels as they stand)
-TRAFFIC_STEP, TRAFFIC_SCATTER = None, None
+# particles to a full launch: the ordinary step and the step after a sort
+TRAFFIC_STEP, TRAFFIC_SCATTER = 41.51, 57.38
 # the same for the ensemble's particle step (ncu on a 16-run ensemble of config 4's distribution)
-TRAFFIC_BSTEP = None
+TRAFFIC_BSTEP = 41.49
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
 # (8 B); on sort steps it writes each survivor, compacted, into the other buffer instead (28 B)
 BYTES_NEUTRAL_KERNEL, BYTES_NEUTRAL_COMPACT = 36, 56
