@@ -82,8 +82,9 @@ __device__ __forceinline__ void born_charged(const NeutralParams& Q, unsigned lo
 }
 
 // An ionizing neutral (about one in several thousand per step): the ion it becomes and the electron
-// born beside it.  Kept out of line so that the streaming loop stays small.
-__device__ __noinline__ void ionize_one(const NeutralParams& Q, unsigned long long base0, unsigned long long base1,
+// born beside it.  Inlined: as a called function its register needs made the caller save registers
+// around every call.
+__device__ __forceinline__ void ionize_one(const NeutralParams& Q, unsigned long long base0, unsigned long long base1,
                                         int c, float f, float vx, float vy, float vz, unsigned long long id,
                                         NCounters* bc) {
   const Phys& ph = Q.P.ph;
