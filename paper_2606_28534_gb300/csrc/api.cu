@@ -104,6 +104,7 @@ void layout(pic_handle* h, char* base, size_t* total) {
       h->cursor[s] = cv.take<unsigned int>(N);
     }
     h->E2 = cv.take<float2>(N);
+    h->fgrid = cv.take<FieldGrid>(1);
     if (h->cap_nt) {
       for (int b = 0; b < 2; ++b) {
         Species32& a = h->nt[b];
@@ -374,6 +375,8 @@ PoissonParams field_params(pic_handle* h, bool keep_counts, bool count_step) {
   F.NE2 = h->NE2;
   F.ne_scale = (dx / h->cfg.ppc[0]) * 2.3283064365386963e-10 / dx;
   F.nt_cap = h->cap_nt;
+  F.grid = h->field_ctas > 0 ? h->fgrid : nullptr;
+  F.grid_ctas = h->field_ctas;
   return F;
 }
 
@@ -1245,6 +1248,10 @@ uint32_t pic_blob_crc32(const void* p, size_t n) {
       const int cap_grid = (int)std::max<unsigned long long>(1ull, std::min<unsigned long long>(need, 1ull << 20));
       h->grid_step = std::min(h->grid_step, cap_grid);
       if (!h->plain) h->grid_scatter = std::min(h->grid_scatter, cap_grid);
+    }
+    if (!h->plain && h->fgrid) {  // the grid-wide field solve: a CTA per 256 nodes, at most one per SM
+      const int want = (h->N + 1 + 255) / 256;
+      h->field_ctas = std::max(1, std::min(std::min(want, sms), PIC_FIELD_GRID_MAX));
     }
     h->grid_sort = sms * 16;
     h->grid_diag = sms * 8;

@@ -43,6 +43,8 @@ struct pic_handle {
   Species32 a32[2][2];  // [buffer][species]
   int cur = 0;
   Species64 a64[2];
+  FieldGrid* fgrid = nullptr;  // scratch of the grid-wide field solve (FP32 path)
+  int field_ctas = 0;          // its CTAs (0: the one-cluster solve)
   unsigned int* cnt[2] = {nullptr, nullptr};
   unsigned long long* S[2] = {nullptr, nullptr};
   unsigned int* cursor[2] = {nullptr, nullptr};

@@ -315,6 +315,251 @@ __global__ void __cluster_dims__(PIC_FIELD_CTAS, 1, 1) __launch_bounds__(PIC_FIE
 }
 
 // =============================================================================================
+// The same integer-exact solve over many CTAs (one simulation; k_field_exact's formulas and
+// roundings, so the two give identical bits).  On one 8-CTA cluster the solve of a 65537-node
+// grid is bound by the FP64 rate of eight SMs; here each of up to one CTA per SM takes a contiguous
+// segment of nodes, and the CTAs exchange only their segment totals (interior charge and first
+// moment) through global memory and one grid barrier.  The launch is cooperative, so every CTA is
+// resident while the others wait.  Smoothing reads a halo of one node per pass on each side of
+// the segment (recomputed from the deposits), so it needs no exchange.
+constexpr int FG_TPB = 256;
+constexpr size_t FG_SMEM_MAX = 96 * 1024;  // shared memory of one CTA: two buffers of its segment
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Sum of an int128 over the CTA (every thread gets it); red: FG_TPB / 32 entries of shared memory.
+__device__ __forceinline__ __int128 block_sum_i128(__int128 v, __int128* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long lo = __shfl_xor_sync(0xFFFFFFFFu, (long long)(unsigned long long)v, o);
+    const long long hi = __shfl_xor_sync(0xFFFFFFFFu, (long long)(v >> 64), o);
+    v += ((__int128)hi << 64) | (__int128)(unsigned long long)lo;
+  }
+  __syncthreads();  // red is free
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  __int128 t = 0;
+#pragma unroll
+  for (int k = 0; k < FG_TPB / 32; ++k) t += red[k];
+  return t;
+}
+
+__global__ void __launch_bounds__(FG_TPB) k_field_grid(const __grid_constant__ PoissonParams P) {
+  extern __shared__ long long fg[];  // two buffers of the extended segment (t, then E as bits)
+  __shared__ __int128 warp_q[FG_TPB / 32], warp_p[FG_TPB / 32], red[FG_TPB / 32];
+  __shared__ __int128 cta_q, cta_p;
+  __shared__ int ok;
+  FieldGrid* const G = P.grid;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  constexpr int nw = FG_TPB / 32;
+  const int N = P.N, M = N + 1;
+  const int nb = (int)gridDim.x, rank = (int)blockIdx.x;
+  const int seg = (M + nb - 1) / nb;
+  const int a = rank * seg;
+  const int len = max(0, min(seg, M - a));
+  const int h = P.smooth;                                  // halo: one node per pass
+  const int xa = max(0, a - h), xb = min(M, a + len + h);  // extended segment [xa, xb)
+  const int xl = max(0, xb - xa);
+  long long* buf = fg;
+  long long* alt = fg + (seg + 2 * h);
+
+  if (P.ctl && !P.no_book && rank == 0 && tid == 0) bookkeeping(P);
+
+  // ---- node deposits, net integer charge (own nodes stored, the halo only read) -------------------
+  const __int128 lim = (__int128)0x7FFFFFFFFFFFFFFFll >> (h ? 2 * h + 2 : 0);
+  for (int e = tid; e < xl; e += FG_TPB) {
+    const int j = xa + e;
+    const bool own = j >= a && j < a + len;
+    const long long R0 = P.R_in ? P.R_in[j] : node_R(P, 0, j), R1 = P.R_in ? P.R_in[M + j] : node_R(P, 1, j);
+    const __int128 rn = (__int128)P.m[0] * R0 + (__int128)P.m[1] * R1;
+    if (own) {
+      P.R[0][j] = R0;
+      P.R[1][j] = R1;
+      if (rn > lim || rn < -lim) atomicOr(&P.ctl->error, ERR_DEVICE);  // never wrap silently
+      if (P.NE2) {
+        const float ne = (float)((double)R0 * P.ne_scale * ((j == 0 || j == N) ? 2.0 : 1.0));
+        if (j < N) P.NE2[j].x = ne;
+        if (j > 0) P.NE2[j - 1].y = ne;
+      }
+    }
+    buf[e] = (long long)rn;
+  }
+  __syncthreads();
+  if (h > 0) {  // the integer filter of k_field_exact: t (wall charges doubled), x 4 per pass
+    for (int e = tid; e < xl; e += FG_TPB) {
+      const int j = xa + e;
+      if (j == 0 || j == N) buf[e] *= 2;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < h; ++pass) {
+      for (int e = tid; e < xl; e += FG_TPB) {
+        const int j = xa + e;
+        const long long cur = buf[e];
+        long long v;
+        if (j == 0)
+          v = 2 * (cur + buf[e + 1]);
+        else if (j == N)
+          v = 2 * (buf[e - 1] + cur);
+        else if (e == 0 || e == xl - 1)
+          v = cur;  // the halo's edge: stale from here on, one node further each pass
+        else
+          v = buf[e - 1] + 2 * cur + buf[e + 1];
+        alt[e] = v;
+      }
+      __syncthreads();
+      long long* const t = buf;
+      buf = alt;
+      alt = t;
+    }
+    for (int e = tid; e < xl; e += FG_TPB) {  // back to charges, in units of 2^-(2 passes + 1)
+      const int j = xa + e;
+      if (j != 0 && j != N) buf[e] *= 2;
+    }
+    __syncthreads();
+  }
+  long long* const own_r = buf + (a - xa);
+
+  // ---- per-thread runs of the own segment: Q (cumulative interior charge) and sum of k r_k -------
+  const int items = (len + FG_TPB - 1) / FG_TPB;
+  const int i0 = tid * items;
+  __int128 oq = 0, op = 0;
+  for (int k = 0; k < items; ++k) {
+    const int i = i0 + k;
+    if (i >= len) break;
+    const int j = a + i;
+    if (j >= 1 && j <= N - 1) {
+      oq += (__int128)own_r[i];
+      op += (__int128)own_r[i] * j;
+    }
+  }
+  __int128 iq = oq, ip = op;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const __int128 uq = shfl_up_i128(iq, o), up = shfl_up_i128(ip, o);
+    if (lane >= o) {
+      iq += uq;
+      ip += up;
+    }
+  }
+  if (lane == 31) {
+    warp_q[w] = iq;
+    warp_p[w] = ip;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    __int128 vq = tid < nw ? warp_q[tid] : (__int128)0, vp = tid < nw ? warp_p[tid] : (__int128)0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const __int128 uq = shfl_up_i128(vq, o), up = shfl_up_i128(vp, o);
+      if (lane >= o) {
+        vq += uq;
+        vp += up;
+      }
+    }
+    if (tid < nw) {
+      warp_q[tid] = vq;
+      warp_p[tid] = vp;
+    }
+    if (tid == 31) {
+      cta_q = vq;
+      cta_p = vp;
+    }
+  }
+  __syncthreads();
+  __int128 q = (w ? warp_q[w - 1] : (__int128)0) + iq - oq;  // exclusive prefix within the CTA
+
+  // ---- grid barrier: publish the CTA totals, wait for every CTA's ----------------------------------
+  if (tid == 0) {
+    G->tot[rank][0] = cta_q;
+    G->tot[rank][1] = cta_p;
+    const unsigned g0 = ld_acquire_u32(&G->gen);  // read before arriving: it cannot move until then
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(&G->count, 1u) == (unsigned)nb - 1u) {  // last to arrive: reset, release the rest
+      G->count = 0u;
+      __threadfence();
+      atomicAdd(&G->gen, 1u);
+    } else {
+      good = 0;
+      const unsigned long long t0 = global_ns();
+      for (int it = 0; it < (1 << 22); ++it) {
+        if (ld_acquire_u32(&G->gen) != g0) {
+          good = 1;
+          break;
+        }
+        if ((it & 63) == 63 && global_ns() - t0 > PIC_WAIT_LIMIT_NS) break;
+      }
+      if (!good) atomicOr(&P.ctl->error, ERR_TIMEOUT);
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  if (!ok) return;  // reported; the field is left as it was
+
+  // the prefix of the CTAs before this one and the grid totals (read past L1)
+  __int128 pq = 0, tq = 0, tp = 0;
+  for (int r = tid; r < nb; r += FG_TPB) {
+    const long long* const t = reinterpret_cast<const long long*>(&G->tot[r][0]);
+    const __int128 vq = ((__int128)__ldcg(t + 1) << 64) | (__int128)(unsigned long long)__ldcg(t);
+    const __int128 vp = ((__int128)__ldcg(t + 3) << 64) | (__int128)(unsigned long long)__ldcg(t + 2);
+    if (r < rank) pq += vq;
+    tq += vq;
+    tp += vp;
+  }
+  q += block_sum_i128(pq, red);
+  const __int128 Qtot = block_sum_i128(tq, red);
+  const __int128 Ptot = block_sum_i128(tp, red);
+
+  // clear the deposit accumulators of the own segment for the next step (every CTA has read its
+  // halo before the barrier)
+  for (int i = tid; i < len; i += FG_TPB) {
+    const int j = a + i;
+    if (j < N) {
+      P.S[0][j] = 0ull;
+      P.S[1][j] = 0ull;
+      if (!P.keep_counts) {
+        const_cast<unsigned int*>(P.cnt[0])[j] = 0u;
+        const_cast<unsigned int*>(P.cnt[1])[j] = 0u;
+      }
+    }
+  }
+
+  // ---- node field in place -------------------------------------------------------------------------
+  const __int128 T = (__int128)N * Qtot - Ptot;
+  for (int k = 0; k < items; ++k) {
+    const int i = i0 + k;
+    if (i >= len) break;
+    const int j = a + i;
+    const __int128 r = own_r[i];
+    double E;
+    if (j == 0) {
+      E = -P.e_wall * i128_to_double(T + (__int128)N * r) + P.e_bias;
+    } else if (j == N) {
+      E = P.e_wall * i128_to_double(Ptot + (__int128)N * r) + P.e_bias;
+    } else {
+      const __int128 qprev = q;
+      q += r;
+      E = P.e_in * i128_to_double((__int128)N * (q + qprev) - 2 * T) + P.e_bias;
+    }
+    own_r[i] = __double_as_longlong(E);
+  }
+  __syncthreads();
+  for (int i = tid; i < len; i += FG_TPB) {
+    const int j = a + i;
+    const double E = __longlong_as_double(own_r[i]);
+    P.E[j] = E;
+    if (j < N) P.E2[j].x = (float)E;
+    if (j > 0) P.E2[j - 1].y = (float)E;
+  }
+}
+
+// =============================================================================================
 // FP64 Green's function.  MODE 0: from the per-cell counts (non-integer charges), 1: from the
 // FP64 accumulators of the plain path, 2: from a given rho (pic_poisson), 3: from the stored R
 // (diagnostics: rho and phi, and E only when asked for).
@@ -532,6 +777,20 @@ cudaError_t launch_field(const PoissonParams& p, cudaStream_t st) {
   field_attrs();
   switch (p.mode) {
     case 0:
+      if (p.exact && p.grid && p.grid_ctas > 0) {
+        const int nb = p.grid_ctas > PIC_FIELD_GRID_MAX ? PIC_FIELD_GRID_MAX : p.grid_ctas;
+        const int gseg = (p.N + 1 + nb - 1) / nb;
+        const size_t gsmem = sizeof(long long) * 2 * (size_t)(gseg + 2 * p.smooth);
+        if (gsmem <= FG_SMEM_MAX) {  // else (very few SMs) the one-cluster solve below
+          static bool grid_attr = false;
+          if (!grid_attr) {
+            set_smem(k_field_grid, (int)FG_SMEM_MAX);
+            grid_attr = true;
+          }
+          void* args[] = {const_cast<PoissonParams*>(&p)};
+          return cudaLaunchCooperativeKernel((const void*)k_field_grid, dim3(nb), dim3(FG_TPB), args, gsmem, st);
+        }
+      }
       if (p.exact)
         k_field_exact<false><<<PIC_FIELD_CTAS, tpb, smem, st>>>(p, nullptr);
       else

@@ -16,8 +16,9 @@
 //            countdown from the same block
 //   deposit  CIC in int64 fixed point: W_r = rint(f 2^32); per cell a particle count and a sum of
 //            W_r, aggregated over the lanes of a warp that share a cell (redux.sync) and added
-//            to global memory with one reduction per (warp, cell).  Node deposits follow as
-//            R_j = 2^32 cnt_j - S_j + S_{j-1} in the field kernel.
+//            to global memory with one reduction per (warp, cell); in the step after a sort
+//            through lane slots in shared memory for a window of cells (window_deposit).  Node
+//            deposits follow as R_j = 2^32 cnt_j - S_j + S_{j-1} in the field kernel.
 #include "step32_common.cuh"
 
 namespace {
@@ -32,7 +33,8 @@ template <bool SCATTER>
 struct StepShape {
   static constexpr int NSTAGE = SCATTER ? 2 : PIC_STEP_NSTAGE;
   static constexpr int SB = SCATTER ? STAGE_BYTES : CHUNK * 20;
-  static constexpr size_t SMEM = (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + NSTAGE * 8);
+  static constexpr int WB = SCATTER ? DW_BYTES : 0;  // deposit window slots (the step after a sort)
+  static constexpr size_t SMEM = (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + WB + NSTAGE * 8);
 };
 
 // One warp handles chunks of 32 x PIC_PPT consecutive particles of one species (a contiguous run
@@ -63,10 +65,13 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
   unsigned char* const stage = dsm + (size_t)wib * NSTAGE * SB;
   unsigned long long* const q =
       reinterpret_cast<unsigned long long*>(dsm + (size_t)WARPS * NSTAGE * SB) + (size_t)wib * QCAP;
+  constexpr int WB = StepShape<SCATTER>::WB;
+  const unsigned wslots = smem_u32(dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8) + (size_t)wib * WB) + lane * 8u;
   unsigned long long* const bar = reinterpret_cast<unsigned long long*>(
-                                      dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8)) + wib * NSTAGE;
+                                      dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + WB)) + wib * NSTAGE;
   if (tid < (int)(sizeof(BlockCounters) / 4)) reinterpret_cast<unsigned int*>(&bc)[tid] = 0u;
   if (lane < NSTAGE) mbar_init(bar + lane, 1u);
+  if (SCATTER) window_zero(wslots);
   mbar_init_fence();
   __syncthreads();
 
@@ -301,21 +306,16 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
             warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] & PIC_CELL_MASK : -1, rn[k], rsw[k]);
         }
       } else {
-        // every pair of the lane's particles (the step after a sort measured faster this way)
+        // chunks on a grid stride, ten steps of drift since they were ordered: through the warp's
+        // window of cells
+        int cc[PIC_PPT];
+        unsigned wr[PIC_PPT];
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
-#pragma unroll
-          for (int j = k + 1; j < PIC_PPT; ++j) {
-            if (rn[k] && rn[j] && ((c[j] ^ c[k]) & PIC_CELL_MASK) == 0) {
-              rn[k] += rn[j];
-              rsw[k] += rsw[j];
-              rn[j] = 0u;
-            }
-          }
+          cc[k] = rn[k] ? c[k] & PIC_CELL_MASK : -1;
+          wr[k] = (unsigned)rsw[k];
         }
-#pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k)
-          warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] & PIC_CELL_MASK : -1, rn[k], rsw[k]);
+        window_deposit(wslots, cc, wr, 0, P.cnt[s], P.S[s]);
       }
 
       if (qn > QFLUSH) {
@@ -343,55 +343,90 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
 
 // Pair source (one pair per ion absorbed in this step), uniform in [0, x1), Maxwellian at T_s.
 // Ids: 2^63 | (step & 0x7FFFFFFF) << 32 | (2k + s); positions drawn from the electron's key.
+// Lane k of a warp makes pair k of the warp's span; the warp claims the slots of its new particles
+// with one atomic per species, and sums the live counts and kinetic energies before adding them.
+constexpr int SOURCE_CTAS = 32;
+
+// The warp's new particles of species s (this lane's when mine): slots past base, deposit, counts.
+template <int s>
+__device__ __forceinline__ void source_append(const StepParams32& P, unsigned long long base, bool mine, int c,
+                                              float f, unsigned wr, const float* v, unsigned long long id,
+                                              unsigned& added, unsigned long long& ke) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
+  unsigned long long first = 0ull;
+  if (lane == 0 && m) first = atomicAdd(&P.ctl->n_born[s], (unsigned long long)__popc(m));
+  first = __shfl_sync(0xFFFFFFFFu, first, 0);
+  if (!mine) return;
+  const unsigned long long slot = base + first + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+  if (slot >= P.cap[s]) {
+    atomicAdd(&P.ctl->dropped, 1ull);
+    atomicOr(&P.ctl->error, ERR_OVERFLOW);
+    return;
+  }
+  const Species32& a = P.sp[s];
+  a.cell[slot] = created_word(P.ph, s, c, id, P.step);
+  a.frac[slot] = f;
+  a.vx[slot] = v[0];
+  a.vy[slot] = v[1];
+  a.vz[slot] = v[2];
+  a.id[slot] = id;
+  atomicAdd(P.cnt[s] + c, 1u);
+  atomicAdd(P.S[s] + c, (unsigned long long)wr);
+  ++added;
+  ke += ke_fx32(v[0], v[1], v[2], P.ph.sp[s].mass);
+}
+
 __global__ void __launch_bounds__(256) k_source32(const StepParams32 P) {
   const Phys& ph = P.ph;
   const unsigned long long K = P.ctl->src_K;
   // births go past the extent of the buffer the step filled
   const unsigned long long n0 = P.scatter ? P.ctl->sort_new[0] : P.ctl->n_cur[0];
   const unsigned long long n1 = P.scatter ? P.ctl->sort_new[1] : P.ctl->n_cur[1];
-  __shared__ unsigned int added[2];
-  if (threadIdx.x < 2) added[threadIdx.x] = 0u;
-  __syncthreads();
-  for (unsigned long long k = threadIdx.x; k < K; k += blockDim.x) {
-    unsigned long long ide = (1ull << 63) | ((P.step & 0x7FFFFFFFull) << 32) | (2ull * k);
-    uint4 w = draw4(ide, ph.seed, P.step, CH_SOURCE, 0u);
-    float x = ph.src_x1 * u01f(w.x);
-    float fl = floorf(x);
-    int c = (int)fl;
-    float f = x - fl;
-    if (f >= 1.f) { f = 0.f; c += 1; }
-    if (c >= ph.N) { c = ph.N - 1; f = 0.99999994f; }
-    unsigned wr = wr_of(f);
-    {
-      uint4 u = draw4(ide, ph.seed, P.step, CH_SOURCE, 1u);
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned added[2] = {0u, 0u};
+  unsigned long long ke[2] = {0ull, 0ull};
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long kw = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; kw < K; kw += stride) {
+    const unsigned long long k = kw + lane;
+    const bool mine = k < K;
+    const unsigned long long ide = (1ull << 63) | ((P.step & 0x7FFFFFFFull) << 32) | (2ull * k);
+    int c = 0;
+    float f = 0.f, ve[3] = {0.f, 0.f, 0.f}, vi[3] = {0.f, 0.f, 0.f};
+    if (mine) {
+      const uint4 w = draw4(ide, ph.seed, P.step, CH_SOURCE, 0u);
+      const float x = ph.src_x1 * u01f(w.x);
+      const float fl = floorf(x);
+      c = (int)fl;
+      f = x - fl;
+      if (f >= 1.f) { f = 0.f; c += 1; }
+      if (c >= ph.N) { c = ph.N - 1; f = 0.99999994f; }
       float a0, a1, a2, a3;
+      const uint4 u = draw4(ide, ph.seed, P.step, CH_SOURCE, 1u);
       box_muller_f(u.x, u.y, a0, a1);
       box_muller_f(u.z, u.w, a2, a3);
-      float v[3] = {ph.sp[0].vt * a0, ph.sp[0].vt * a1, ph.sp[0].vt * a2};
-      if (append32<0>(P, n0, created_word(ph, 0, c, ide, P.step), f, v, ide)) {
-        atomicAdd(P.cnt[0] + c, 1u);
-        atomicAdd(P.S[0] + c, (unsigned long long)wr);
-        atomicAdd(&added[0], 1u);
-        atomicAdd(&P.ctl->ke_acc[0], ke_fx32(v[0], v[1], v[2], ph.sp[0].mass));
-      }
+      ve[0] = ph.sp[0].vt * a0; ve[1] = ph.sp[0].vt * a1; ve[2] = ph.sp[0].vt * a2;
+      const uint4 u2 = draw4(ide + 1ull, ph.seed, P.step, CH_SOURCE, 1u);
+      box_muller_f(u2.x, u2.y, a0, a1);
+      box_muller_f(u2.z, u2.w, a2, a3);
+      vi[0] = ph.sp[1].vt * a0; vi[1] = ph.sp[1].vt * a1; vi[2] = ph.sp[1].vt * a2;
     }
-    {
-      uint4 u = draw4(ide + 1ull, ph.seed, P.step, CH_SOURCE, 1u);
-      float a0, a1, a2, a3;
-      box_muller_f(u.x, u.y, a0, a1);
-      box_muller_f(u.z, u.w, a2, a3);
-      float v[3] = {ph.sp[1].vt * a0, ph.sp[1].vt * a1, ph.sp[1].vt * a2};
-      if (append32<1>(P, n1, created_word(ph, 1, c, ide + 1ull, P.step), f, v, ide + 1ull)) {
-        atomicAdd(P.cnt[1] + c, 1u);
-        atomicAdd(P.S[1] + c, (unsigned long long)wr);
-        atomicAdd(&added[1], 1u);
-        atomicAdd(&P.ctl->ke_acc[1], ke_fx32(v[0], v[1], v[2], ph.sp[1].mass));
-      }
+    const unsigned wr = wr_of(f);
+    source_append<0>(P, n0, mine, c, f, wr, ve, ide, added[0], ke[0]);
+    source_append<1>(P, n1, mine, c, f, wr, vi, ide + 1ull, added[1], ke[1]);
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const unsigned a = __reduce_add_sync(0xFFFFFFFFu, added[s]);
+    unsigned long long e = ke[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xFFFFFFFFu, e, o);
+    if (lane == 0) {
+      if (a) atomicAdd(&P.ctl->n_live[s], (unsigned long long)a);
+      if (e) atomicAdd(&P.ctl->ke_acc[s], e);
     }
   }
-  __syncthreads();
-  if (threadIdx.x < 2 && added[threadIdx.x]) atomicAdd(&P.ctl->n_live[threadIdx.x], (unsigned long long)added[threadIdx.x]);
-  if (threadIdx.x == 0) P.ctl->source_pairs += K;
+  if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl->source_pairs += K;
 }
 
 }  // namespace
@@ -431,6 +466,6 @@ cudaError_t launch_step32_scatter(const StepParams32& p, int grid, cudaStream_t 
 }
 
 cudaError_t launch_source32(const StepParams32& p, cudaStream_t st) {
-  k_source32<<<1, 256, 0, st>>>(p);
+  k_source32<<<SOURCE_CTAS, 256, 0, st>>>(p);
   return cudaGetLastError();
 }

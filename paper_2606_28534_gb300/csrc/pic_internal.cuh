@@ -350,6 +350,17 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned
 }
 
 // launchers (each file owns its kernels)
+// Scratch of the grid-wide integer-exact field solve of one simulation (k_field_grid): the
+// arrival count and generation of its grid barrier, and the per-CTA totals it exchanges
+// (interior charge, first moment).  Zero-initialised with the workspace.
+constexpr int PIC_FIELD_GRID_MAX = 1024;  // CTAs of the grid-wide solve
+struct FieldGrid {
+  unsigned int count;
+  unsigned int gen;
+  unsigned int pad[2];
+  __int128 tot[PIC_FIELD_GRID_MAX][2];
+};
+
 struct PoissonParams {
   // input: either fixed-point counts (cnt/S) or FP64 accumulators (acc) or a plain rho
   const unsigned int* cnt[2];
@@ -387,6 +398,8 @@ struct PoissonParams {
   const long long* R_in;  // exact path: the node deposits to solve (2 (N+1): species 0, then 1) in
                           // place of this handle's own counts (a decomposed simulation's total)
   int no_book;       // skip the per-step bookkeeping (a re-solve outside a step)
+  FieldGrid* grid;   // exact path: solve over grid_ctas co-resident CTAs (null: one cluster)
+  int grid_ctas;
 };
 
 struct SortParams {

@@ -223,6 +223,75 @@ __device__ __forceinline__ void warp_deposit(unsigned int* __restrict__ gcnt, un
   }
 }
 
+// ---- deposit of a chunk through a window of cells (the step after a sort) -------------------
+// The step after a sort reads its chunks on a grid stride from the buffer the sort step left, ten
+// steps after that buffer was ordered: the electrons of a chunk are spread over a few neighbouring
+// cells in no order, and many warps work in one dense cell at a time, so per-lane global atomics
+// and cell-by-cell warp reductions meet on the same addresses.  Instead each lane adds its
+// particles to its own shared-memory slots for the DW cells that end at the chunk's highest cell,
+// and each touched cell is reduced across the warp once, into one global reduction per array.
+// Particles below the window go straight to global memory.  Integer sums: exact in any order.
+constexpr int DW = 8;                  // cells in the window (a power of two)
+constexpr int DW_BYTES = DW * 32 * 8;  // one warp's slots: column j of lane l at 256 j + 8 l
+
+// A lane's slot holds two words for its (at most four) particles of one cell:
+//   h = count << 23 + sum of (W_r >> 16),   l = sum of (W_r & 0xFFFF).
+// Over a warp (at most 128 particles) the sums of h stay below 2^23 in the low field and the counts
+// below 2^8, so one 32-bit warp reduction per word is exact.
+__device__ __forceinline__ void red_shared_u32(unsigned a, unsigned v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// Zeroes this lane's slots (once per kernel; the flush re-zeroes what it reads).
+__device__ __forceinline__ void window_zero(unsigned slots) {
+#pragma unroll
+  for (int j = 0; j < DW; ++j) asm volatile("st.shared.u64 [%0], %1;" ::"r"(slots + 256u * j), "l"(0ull) : "memory");
+}
+
+// Deposits the live particles of a chunk (c[k]: cell index, -1 dead; wr[k]: right weights).
+// slots: shared address of this lane's column 0.  cell_off is added to the global cell index.
+__device__ __forceinline__ void window_deposit(unsigned slots, const int (&c)[PIC_PPT], const unsigned (&wr)[PIC_PPT],
+                                               int cell_off, unsigned int* __restrict__ gcnt,
+                                               unsigned long long* __restrict__ gS) {
+  int lmax = -1;
+#pragma unroll
+  for (int k = 0; k < PIC_PPT; ++k) lmax = max(lmax, c[k]);
+  const int mx = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)(lmax + 1)) - 1;
+  if (mx < 0) return;
+  const int base = mx - DW + 1;
+  unsigned touched = 0u;
+#pragma unroll
+  for (int k = 0; k < PIC_PPT; ++k) {
+    if (c[k] < 0) continue;
+    if (c[k] >= base) {
+      const unsigned col = (unsigned)c[k] & (DW - 1);
+      const unsigned a = slots + 256u * col;
+      red_shared_u32(a, (1u << 23) + (wr[k] >> 16));
+      red_shared_u32(a + 4u, wr[k] & 0xFFFFu);
+      touched |= 1u << col;
+    } else {
+      atomicAdd(gcnt + cell_off + c[k], 1u);
+      atomicAdd(gS + cell_off + c[k], (unsigned long long)wr[k]);
+    }
+  }
+  unsigned cols = __reduce_or_sync(0xFFFFFFFFu, touched);
+  while (cols) {
+    const int col = __ffs(cols) - 1;
+    cols &= cols - 1u;
+    const unsigned a = slots + 256u * (unsigned)col;
+    unsigned h, l;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(h), "=r"(l) : "r"(a) : "memory");
+    asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(0ull) : "memory");
+    const unsigned hs = __reduce_add_sync(0xFFFFFFFFu, h);
+    const unsigned ls = __reduce_add_sync(0xFFFFFFFFu, l);
+    if ((threadIdx.x & 31) == 0) {
+      const int cell = cell_off + base + ((col - base) & (DW - 1));
+      atomicAdd(gcnt + cell, hs >> 23);
+      atomicAdd(gS + cell, ((unsigned long long)(hs & 0x7FFFFFu) << 16) + (unsigned long long)ls);
+    }
+  }
+}
+
 constexpr int QCAP = 160;   // per-warp queue of collision candidates
 constexpr int QFLUSH = 32;  // the warp processes its queue once it holds more than this (a
                             // chunk adds at most 32 * PIC_PPT = 128 entries)
