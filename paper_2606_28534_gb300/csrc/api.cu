@@ -850,13 +850,19 @@ void put_arr(std::vector<unsigned char>& b, const std::vector<T>& v) {
   b.insert(b.end(), p, p + sizeof(T) * v.size());
 }
 
-int check_blob(const pic_handle* h, const void* buf, size_t len) {
-  if (!h || !buf) return PIC_EINVAL;
-  const unsigned char* b = static_cast<const unsigned char*>(buf);
+// The blob's record groups (charged species 0 and 1, the neutrals): byte offsets and counts; over:
+// more records than the handle's capacity (reported as PIC_EOVERFLOW once the blob has passed the
+// checks of its contents, so that a damaged blob is always PIC_ECORRUPT).
+struct BlobGroups {
+  size_t off[3];
+  uint64_t n[3];
+  bool over;
+};
+
+// Every check of a blob that reads only its header: magic, version, configuration hash, counts and
+// length; fills the record groups.
+int check_header(const pic_handle* h, const unsigned char* b, size_t len, BlobGroups* g) {
   if (len < kHdr + 4 || std::memcmp(b, "PICMCSN1", 8) != 0) return PIC_ECORRUPT;
-  uint32_t crc;
-  std::memcpy(&crc, b + len - 4, 4);
-  if (crc != crc32_ieee(b, len - 4)) return PIC_ECORRUPT;
   uint32_t ver;
   uint64_t hash, step, n[2];
   std::memcpy(&ver, b + 8, 4);
@@ -871,20 +877,32 @@ int check_blob(const pic_handle* h, const void* buf, size_t len) {
     if (len < charged + kNtHdr + 4) return PIC_ECORRUPT;
     std::memcpy(&nn, b + charged, 8);
     if (nn > (1ull << 40) || len != charged + kNtHdr + 44 * nn + 4) return PIC_ECORRUPT;
-    if (round_up4(nn) > h->cap_nt) return PIC_EOVERFLOW;
   } else if (len != charged + 4) {
     return PIC_ECORRUPT;
   }
-  for (int s = 0; s < 2; ++s)
-    if (round_up4(n[s]) > h->cap[s]) return PIC_EOVERFLOW;
+  g->over = round_up4(nn) > h->cap_nt;
+  for (int s = 0; s < 2; ++s) g->over = g->over || round_up4(n[s]) > h->cap[s];
+  g->off[0] = kHdr;
+  g->off[1] = kHdr + 44 * (size_t)n[0];
+  g->off[2] = charged + kNtHdr;
+  g->n[0] = n[0];
+  g->n[1] = n[1];
+  g->n[2] = nn;
+  return PIC_OK;
+}
+
+// The checks that read the whole blob, on host threads: the CRC, and the range of every cell,
+// countdown and fraction.  The cell word is cell | k << 18 | c << 30; a species with the
+// null-collision test may leave the countdown pair (k | c << 12) at 0 ("not drawn": the restore
+// draws it), else 1 <= k <= 4095; every other species (the neutrals included) carries 0 there.
+int check_body(const pic_handle* h, const unsigned char* b, size_t len, const BlobGroups& g) {
+  uint32_t crc;
+  std::memcpy(&crc, b + len - 4, 4);
+  if (crc != crc32_ieee(b, len - 4)) return PIC_ECORRUPT;
   const int N = h->N;
-  // range of every cell, countdown and fraction (host threads).  The cell word is
-  // cell | k << 18 | c << 30; a species with the null-collision test may leave the countdown pair
-  // (k | c << 12) at 0 ("not drawn": the restore draws it), else 1 <= k <= 4095; every other
-  // species (the neutrals included) carries 0 there.
   {
-    const size_t offs[3] = {kHdr, kHdr + 44 * (size_t)n[0], charged + kNtHdr};
-    const uint64_t counts[3] = {n[0], n[1], nn};
+    const size_t* offs = g.off;
+    const uint64_t* counts = g.n;
     bool bad = false;
     for (int s = 0; s < 3; ++s) {
       const bool mcc = s < 2 && ((h->ph.mcc_mask >> s) & 1u);
@@ -922,13 +940,104 @@ int check_blob(const pic_handle* h, const void* buf, size_t len) {
   return PIC_OK;
 }
 
+int check_blob(const pic_handle* h, const void* buf, size_t len) {
+  if (!h || !buf) return PIC_EINVAL;
+  const unsigned char* b = static_cast<const unsigned char*>(buf);
+  BlobGroups g;
+  int rc = check_header(h, b, len, &g);
+  if (rc == PIC_OK) rc = check_body(h, b, len, g);
+  return rc != PIC_OK ? rc : (g.over ? PIC_EOVERFLOW : PIC_OK);
+}
+
+// The same checks as check_body on the device, for a large blob of the FP32 path: the blob is
+// copied once into a temporary device buffer (cudaMallocAsync), where k_blob_crc checksums its
+// 64 KB blocks and k_blob_ranges checks the records; the host joins the block checksums (the
+// operator Z^65536 as four byte tables) and finishes the tail.  On success *dev holds the copy,
+// from which the restore then reads; PIC_ECORRUPT frees it.  Returns -1 (nothing allocated)
+// when the device path does not apply or the allocation fails: the caller checks on the host.
+int check_body_device(pic_handle* h, const unsigned char* b, size_t len, const BlobGroups& g, unsigned char** dev) {
+  *dev = nullptr;
+  if (h->plain || len < (size_t(16) << 20)) return -1;
+  const size_t n = len - 4;
+  const size_t nblk = n / 65536;
+  const size_t alen = (len + 255) & ~size_t(255);
+  const size_t blen = (4 * nblk + 255) & ~size_t(255);
+  std::vector<uint32_t> hb(nblk);  // (before the allocation: a failure here frees nothing)
+  unsigned char* d = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&d), alen + blen + 256, h->st) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  uint32_t* blk = reinterpret_cast<uint32_t*>(d + alen);
+  unsigned int* bad = reinterpret_cast<unsigned int*>(d + alen + blen);
+  // operators: one zero byte, then squared up to 2^16 zero bytes
+  Gf2 z;
+  z.m[0] = 0xEDB88320u;
+  for (int i = 1; i < 32; ++i) z.m[i] = 1u << (i - 1);
+  z = gf2_square(gf2_square(gf2_square(z)));
+  BlobCrcOps ops;
+  for (int k = 0; k < 11; ++k) z = gf2_square(z);  // 2048 bytes
+  for (int k = 0; k < 5; ++k) {
+    std::memcpy(ops.z[k], z.m, sizeof(z.m));
+    z = gf2_square(z);
+  }  // z: 65536 bytes
+  unsigned int hbad = 0;
+  cudaError_t e = cudaMemsetAsync(bad, 0, 4, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, b, len, cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = launch_blob_crc(d, nblk, ops, blk, h->st);
+  for (int s = 0; s < 3 && e == cudaSuccess; ++s)
+    e = launch_blob_ranges(d + g.off[s], d + g.off[s] + 4 * g.n[s], g.n[s], h->N,
+                           s < 2 && ((h->ph.mcc_mask >> s) & 1u) ? 1 : 0, bad, h->st);
+  if (e == cudaSuccess && nblk) e = cudaMemcpyAsync(hb.data(), blk, 4 * nblk, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(d, h->st);
+    return PIC_ECUDA;
+  }
+  uint32_t tab[4][256];
+  for (int j = 0; j < 4; ++j)
+    for (uint32_t x = 0; x < 256; ++x) tab[j][x] = gf2_apply(z, x << (8 * j));
+  uint32_t reg = 0xFFFFFFFFu;
+  for (size_t i = 0; i < nblk; ++i)
+    reg = (tab[0][reg & 0xFFu] ^ tab[1][(reg >> 8) & 0xFFu] ^ tab[2][(reg >> 16) & 0xFFu] ^ tab[3][reg >> 24]) ^ hb[i];
+  reg = crc_raw(crc_tables(), reg, b + 65536 * nblk, n - 65536 * nblk);
+  uint32_t crc;
+  std::memcpy(&crc, b + n, 4);
+  if ((reg ^ 0xFFFFFFFFu) != crc || hbad) {
+    cudaFreeAsync(d, h->st);
+    return PIC_ECORRUPT;
+  }
+  *dev = d;
+  return PIC_OK;
+}
+
 int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
   if (!h || !buf) return PIC_EINVAL;
-  if (!checked) {
-    const int rc = check_blob(h, buf, len);
-    if (rc != PIC_OK) return rc;
-  }
   const unsigned char* b = static_cast<const unsigned char*>(buf);
+  unsigned char* dev = nullptr;  // a device copy of the blob (large FP32 blobs): uploads read it
+  if (!checked) {
+    BlobGroups g;
+    int rc = check_header(h, b, len, &g);
+    if (rc != PIC_OK) return rc;
+    if (!g.over) rc = check_body_device(h, b, len, g, &dev);
+    if (g.over || rc < 0) rc = check_body(h, b, len, g);
+    if (rc == PIC_OK && g.over) rc = PIC_EOVERFLOW;
+    if (rc != PIC_OK) {
+      if (dev) cudaFreeAsync(dev, h->st);
+      return rc;
+    }
+  }
+  struct DevFree {  // the device copy is released however the restore ends
+    unsigned char* p;
+    cudaStream_t st;
+    ~DevFree() {
+      if (p) {
+        cudaStreamSynchronize(st);
+        cudaFreeAsync(p, st);
+      }
+    }
+  } dev_free{dev, h->st};
   uint64_t step, n[2];
   std::memcpy(&step, b + 24, 8);
   std::memcpy(n, b + 32, 16);
@@ -949,8 +1058,10 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
     char* stage = h->stage;
     const size_t stage_bytes = h->stage_bytes;
     const size_t per = std::max<size_t>(4, (stage_bytes - 6 * 256) / 44 / 4 * 4);
-    const unsigned char* src[6] = {b + o, b + o + 4 * m, b + o + 12 * m, b + o + 20 * m, b + o + 28 * m,
-                                   b + o + 36 * m};
+    const unsigned char* sb = dev ? dev : b;  // the device copy when there is one
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const unsigned char* src[6] = {sb + o, sb + o + 4 * m, sb + o + 12 * m, sb + o + 20 * m, sb + o + 28 * m,
+                                   sb + o + 36 * m};
     const size_t width[6] = {4, 8, 8, 8, 8, 8};
     for (size_t done = 0; done < m; done += per) {
       const size_t cnt_i = std::min(per, m - done);
@@ -959,7 +1070,7 @@ int restore_state(pic_handle* h, const void* buf, size_t len, bool checked) {
       for (int a = 0; a < 6; ++a) {
         dst[a] = stage + so;
         so += (width[a] * cnt_i + 255) & ~size_t(255);
-        CK(cudaMemcpyAsync(dst[a], src[a] + width[a] * done, width[a] * cnt_i, cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(dst[a], src[a] + width[a] * done, width[a] * cnt_i, kind, h->st));
       }
       CK(launch_restore32(reinterpret_cast<const int*>(dst[0]), reinterpret_cast<const double*>(dst[1]),
                           reinterpret_cast<const double*>(dst[2]), reinterpret_cast<const double*>(dst[3]),

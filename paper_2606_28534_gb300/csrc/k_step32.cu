@@ -15,9 +15,9 @@
 //            (ions); ionization appends an (e, ion) pair past the array end -- and takes its next
 //            countdown from the same block
 //   deposit  CIC in int64 fixed point: W_r = rint(f 2^32); per cell a particle count and a sum of
-//            W_r, aggregated over the lanes of a warp that share a cell (redux.sync) and added
-//            to global memory with one reduction per (warp, cell); in the step after a sort
-//            through lane slots in shared memory for a window of cells (window_deposit).  Node
+//            W_r.  Each lane adds its particles to its own shared-memory slots for the window of
+//            cells that ends at the chunk's highest cell; each touched cell is then reduced across
+//            the warp (redux.sync) into one global reduction per array (window_deposit).  Node
 //            deposits follow as R_j = 2^32 cnt_j - S_j + S_{j-1} in the field kernel.
 #include "step32_common.cuh"
 
@@ -33,8 +33,7 @@ template <bool SCATTER>
 struct StepShape {
   static constexpr int NSTAGE = SCATTER ? 2 : PIC_STEP_NSTAGE;
   static constexpr int SB = SCATTER ? STAGE_BYTES : CHUNK * 20;
-  static constexpr int WB = SCATTER ? DW_BYTES : 0;  // deposit window slots (the step after a sort)
-  static constexpr size_t SMEM = (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + WB + NSTAGE * 8);
+  static constexpr size_t SMEM = (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + DW_BYTES + NSTAGE * 8);
 };
 
 // One warp handles chunks of 32 x PIC_PPT consecutive particles of one species (a contiguous run
@@ -65,13 +64,13 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
   unsigned char* const stage = dsm + (size_t)wib * NSTAGE * SB;
   unsigned long long* const q =
       reinterpret_cast<unsigned long long*>(dsm + (size_t)WARPS * NSTAGE * SB) + (size_t)wib * QCAP;
-  constexpr int WB = StepShape<SCATTER>::WB;
-  const unsigned wslots = smem_u32(dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8) + (size_t)wib * WB) + lane * 8u;
+  const unsigned wslots =  // this lane's deposit window slots
+      smem_u32(dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8) + (size_t)wib * DW_BYTES) + lane * 8u;
   unsigned long long* const bar = reinterpret_cast<unsigned long long*>(
-                                      dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + WB)) + wib * NSTAGE;
+                                      dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + DW_BYTES)) + wib * NSTAGE;
   if (tid < (int)(sizeof(BlockCounters) / 4)) reinterpret_cast<unsigned int*>(&bc)[tid] = 0u;
   if (lane < NSTAGE) mbar_init(bar + lane, 1u);
-  if (SCATTER) window_zero(wslots);
+  window_zero(wslots);
   mbar_init_fence();
   __syncthreads();
 
@@ -279,41 +278,14 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         }
       }
 
-      // ---- deposit: merge equal cells inside the thread, then across the warp -----------------
-      unsigned rn[PIC_PPT];
-      unsigned long long rsw[PIC_PPT];
-#pragma unroll
-      for (int k = 0; k < PIC_PPT; ++k) {
-        const bool live = c[k] != PIC_DEAD_CELL;
-        rn[k] = live ? 1u : 0u;
-        rsw[k] = live ? (unsigned long long)wr_of(f[k]) : 0ull;
-      }
-      if (!SCATTER) {
-        // runs of equal cells inside the lane (the array is sorted up to the moves since the last
-        // sort), then particle 0 across the warp; particles 1..3 only where a lane still has one
-#pragma unroll
-        for (int k = PIC_PPT - 1; k > 0; --k) {
-          if (rn[k] && rn[k - 1] && ((c[k] ^ c[k - 1]) & PIC_CELL_MASK) == 0) {
-            rn[k - 1] += rn[k];
-            rsw[k - 1] += rsw[k];
-            rn[k] = 0u;
-          }
-        }
-        warp_deposit(P.cnt[s], P.S[s], rn[0] ? c[0] & PIC_CELL_MASK : -1, rn[0], rsw[0]);
-        if (__any_sync(0xFFFFFFFFu, (rn[1] | rn[2] | rn[3]) != 0u)) {
-#pragma unroll
-          for (int k = 1; k < PIC_PPT; ++k)
-            warp_deposit(P.cnt[s], P.S[s], rn[k] ? c[k] & PIC_CELL_MASK : -1, rn[k], rsw[k]);
-        }
-      } else {
-        // chunks on a grid stride, ten steps of drift since they were ordered: through the warp's
-        // window of cells
+      // ---- deposit through the warp's window of cells ------------------------------------------
+      {
         int cc[PIC_PPT];
         unsigned wr[PIC_PPT];
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
-          cc[k] = rn[k] ? c[k] & PIC_CELL_MASK : -1;
-          wr[k] = (unsigned)rsw[k];
+          cc[k] = c[k] != PIC_DEAD_CELL ? c[k] & PIC_CELL_MASK : -1;
+          wr[k] = wr_of(f[k]);
         }
         window_deposit(wslots, cc, wr, 0, P.cnt[s], P.S[s]);
       }

@@ -543,6 +543,16 @@ cudaError_t launch_diag32(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_diag_grid(const long long* R0, const long long* R1, int sign0, int sign1, const double* E, int N,
                              double dx, Ctl* ctl, cudaStream_t st);
 // species: 0, 1 (charged: undrawn countdowns are drawn at `step`) or 2 (neutrals: plain cells)
+// Device checks of a checkpoint blob (k_blob.cu): the CRC-32 register of each full 64 KB block
+// from a zero register; z[k] = the register update by 2048 * 2^k zero bytes (column i: image of
+// bit i).  Range checks of one species' cell words and fractions.
+struct BlobCrcOps {
+  uint32_t z[5][32];
+};
+cudaError_t launch_blob_crc(const unsigned char* p, unsigned long long nblocks, const BlobCrcOps& ops, uint32_t* out,
+                            cudaStream_t st);
+cudaError_t launch_blob_ranges(const unsigned char* cells, const unsigned char* fracs, unsigned long long m, int N,
+                               int mcc, unsigned int* bad, cudaStream_t st);
 cudaError_t launch_restore32(const int* cell, const double* frac, const double* vx, const double* vy, const double* vz,
                              const unsigned long long* id, unsigned long long n, const Species32& dst,
                              unsigned long long base, const Phys& ph, int species, unsigned long long step,

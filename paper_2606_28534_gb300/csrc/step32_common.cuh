@@ -223,14 +223,15 @@ __device__ __forceinline__ void warp_deposit(unsigned int* __restrict__ gcnt, un
   }
 }
 
-// ---- deposit of a chunk through a window of cells (the step after a sort) -------------------
-// The step after a sort reads its chunks on a grid stride from the buffer the sort step left, ten
-// steps after that buffer was ordered: the electrons of a chunk are spread over a few neighbouring
-// cells in no order, and many warps work in one dense cell at a time, so per-lane global atomics
-// and cell-by-cell warp reductions meet on the same addresses.  Instead each lane adds its
-// particles to its own shared-memory slots for the DW cells that end at the chunk's highest cell,
-// and each touched cell is reduced across the warp once, into one global reduction per array.
-// Particles below the window go straight to global memory.  Integer sums: exact in any order.
+// ---- deposit of a chunk through a window of cells ---------------------------------------------
+// Between sorts the electrons drift: a few steps after a sort a third to three fifths of
+// consecutive electrons are in different cells, so a 128-particle chunk spreads over a few
+// neighbouring cells in no order, and reducing it across the warp cell by cell takes several
+// rounds and leaves many single-lane global atomics (which, in the step after a sort, many warps
+// aim at one dense cell at a time).  Instead each lane adds its particles to its own shared-memory
+// slots for the DW cells that end at the chunk's highest cell, and each touched cell is reduced
+// across the warp once, into one global reduction per array.  Particles below the window go
+// straight to global memory.  Integer sums: exact in any order.
 constexpr int DW = 8;                  // cells in the window (a power of two)
 constexpr int DW_BYTES = DW * 32 * 8;  // one warp's slots: column j of lane l at 256 j + 8 l
 

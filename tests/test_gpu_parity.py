@@ -382,6 +382,52 @@ def test_restore_error_codes():
     assert g.restore(snapfmt.with_particles(o.snapshot(), big)) == 4
 
 
+def test_large_blob_restore_checks_on_the_device():
+    # A blob of 16 MB or more (FP32 path) is checked on the device: the CRC of its 64 KB blocks,
+    # joined on the host with the tail past the last full block, and every record's range.  Damage
+    # anywhere -- inside a block, in the tail, in the stored CRC -- or a record out of range under a
+    # valid CRC is PIC_ECORRUPT with the state untouched; the intact blob restores bit for bit.
+    import zlib
+
+    p = W.variant(W.SMALL_C3, ppc=(500, 500))
+    g = pic.Simulation(p)
+    g.step(4)
+    blob = g.snapshot()
+    g.close()
+    assert len(blob) >= 16 << 20
+    h = pic.Simulation(p)
+    h.step(1)
+    before = h.snapshot()
+    n = len(blob) - 4
+    for pos in (n // 2 + 12345, n - 100, n + 1):
+        bad = bytearray(blob)
+        bad[pos] ^= 0x04
+        assert h.restore(bytes(bad)) == 5, pos
+        assert h.snapshot() == before
+
+    def with_crc(b):
+        b[-4:] = (zlib.crc32(bytes(b[:-4])) & 0xFFFFFFFF).to_bytes(4, "little")
+        return bytes(b)
+
+    hdr = 208  # header bytes before species 0's cell words
+    m0 = int.from_bytes(blob[32:40], "little")
+    bad = bytearray(blob)
+    w = int.from_bytes(bad[hdr + 4 * 7: hdr + 4 * 8], "little")
+    bad[hdr + 4 * 7: hdr + 4 * 8] = ((w & ~0x3FFFF) | p["ncells"]).to_bytes(4, "little")  # cell N
+    assert h.restore(with_crc(bad)) == 5
+    bad = bytearray(blob)
+    bad[hdr + 4 * m0 + 8 * 11: hdr + 4 * m0 + 8 * 12] = struct.pack("<d", 1.0)  # fraction 1
+    assert h.restore(with_crc(bad)) == 5
+    bad = bytearray(blob)
+    w = int.from_bytes(bad[hdr + 4 * 3: hdr + 4 * 4], "little")
+    bad[hdr + 4 * 3: hdr + 4 * 4] = ((w & 0x3FFFF) | (0x1000 << 18)).to_bytes(4, "little")  # countdown 0, flag 1
+    assert h.restore(with_crc(bad)) == 5
+    assert h.snapshot() == before
+    assert h.restore(blob) == 0
+    assert h.snapshot() == blob
+    h.close()
+
+
 @pytest.mark.parametrize("precision", [W.PRECISION_FP32, W.PRECISION_FP64_PLAIN])
 def test_config1_long_run_moments_match_the_oracle_statistically(precision):
     # Config 1 (256 cells, 100 ppc per species, 1000 steps; R16: parity of long runs is statistical):
