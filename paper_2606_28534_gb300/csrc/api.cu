@@ -225,8 +225,20 @@ void prof_begin(pic_handle* h, int kind, EvPair* e) {
   e->kind = kind;
   e->a = e->b = nullptr;
   if (!h->prof) return;
-  cudaEventCreate(&e->a);
-  cudaEventCreate(&e->b);
+  for (cudaEvent_t* x : {&e->a, &e->b}) {
+    if (!h->ev_free.empty()) {
+      *x = h->ev_free.back();
+      h->ev_free.pop_back();
+    } else if (cudaEventCreate(x) != cudaSuccess) {
+      *x = nullptr;
+    }
+  }
+  if (!e->a || !e->b) {  // no event: this launch goes untimed
+    if (e->a) h->ev_free.push_back(e->a);
+    if (e->b) h->ev_free.push_back(e->b);
+    e->a = e->b = nullptr;
+    return;
+  }
   cudaEventRecord(e->a, h->st);
 }
 
@@ -244,8 +256,8 @@ void prof_harvest(pic_handle* h) {
       h->ms[e.kind] += ms;
       h->launches[e.kind] += 1;
     }
-    cudaEventDestroy(e.a);
-    cudaEventDestroy(e.b);
+    h->ev_free.push_back(e.a);
+    h->ev_free.push_back(e.b);
   }
   h->ev.clear();
 }
@@ -1785,6 +1797,7 @@ void pic_free(pic_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
   prof_harvest(h);
+  for (cudaEvent_t x : h->ev_free) cudaEventDestroy(x);
   if (h->owns_ws && h->ws) cudaFree(h->ws);
   delete h;
 }

@@ -72,6 +72,7 @@ struct pic_handle {
   int grid_neutral = 0;
   bool prof = false;
   std::vector<picx::EvPair> ev;
+  std::vector<cudaEvent_t> ev_free;  // harvested events, reused (creating one costs host time)
   double ms[PIC_KERNEL_KINDS] = {0};
   uint64_t launches[PIC_KERNEL_KINDS] = {0};
 };

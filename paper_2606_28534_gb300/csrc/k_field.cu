@@ -788,7 +788,10 @@ cudaError_t launch_field(const PoissonParams& p, cudaStream_t st) {
             grid_attr = true;
           }
           void* args[] = {const_cast<PoissonParams*>(&p)};
-          return cudaLaunchCooperativeKernel((const void*)k_field_grid, dim3(nb), dim3(FG_TPB), args, gsmem, st);
+          const cudaError_t e =
+              cudaLaunchCooperativeKernel((const void*)k_field_grid, dim3(nb), dim3(FG_TPB), args, gsmem, st);
+          if (e != cudaErrorCooperativeLaunchTooLarge) return e;
+          cudaGetLastError();  // fewer SMs free than CTAs (a shared device): the one-cluster solve
         }
       }
       if (p.exact)
