@@ -57,7 +57,7 @@ BYTES_NEUTRAL_KERNEL, BYTES_NEUTRAL_COMPACT = 36, 56
 # DRAM bytes per neutral of one in-place neutral launch, from one ncu capture on the sheath profiling
 # case (c6p), scaled by neutrals to a full launch (writes still dirty in L2 at the launch's end are
 # not counted there)
-TRAFFIC_NEUTRAL = 32.58
+TRAFFIC_NEUTRAL = 32.33
 
 
 def _peaks():

@@ -262,6 +262,58 @@ void prof_harvest(pic_handle* h) {
   h->ev.clear();
 }
 
+// The tensor maps of the particle step's stage loads (StepMaps), made once per handle: per buffer
+// and species, the five 4-byte arrays as a 2-D tensor of 32-bit elements, cap[s] wide and 5 rows,
+// the rows as far apart as the workspace layout places the arrays (cap[s] elements in a single
+// run; the whole batch's capacity in a run of an ensemble), read in boxes of 128 x 5.  The encoder
+// is the driver's cuTensorMapEncodeTiled, reached through the runtime.  Until the maps exist
+// (maps_ok) no particle step is launched for the handle.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+int make_step_maps(pic_handle* h) {
+  h->maps_ok = false;
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return PIC_ECUDA;
+  for (int b = 0; b < 2; ++b)
+    for (int s = 0; s < 2; ++s) {
+      const Species32& a = h->a32[b][s];
+      const unsigned long long cap = h->cap[s];
+      const char* const rows[5] = {reinterpret_cast<const char*>(a.cell), reinterpret_cast<const char*>(a.frac),
+                                   reinterpret_cast<const char*>(a.vx), reinterpret_cast<const char*>(a.vy),
+                                   reinterpret_cast<const char*>(a.vz)};
+      const long long pitch = rows[1] - rows[0];
+      bool ok = pitch >= (long long)(cap * 4) && pitch % 16 == 0 && (reinterpret_cast<uintptr_t>(rows[0]) & 15u) == 0;
+      for (int r = 2; r < 5; ++r) ok = ok && rows[r] - rows[r - 1] == pitch;
+      if (!ok) return PIC_ECUDA;  // not a layout the maps can describe
+      const cuuint64_t dims[2] = {cap, 5};
+      const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+      const cuuint32_t box[2] = {32 * PIC_PPT, 5};
+      const cuuint32_t estr[2] = {1, 1};
+      if (enc(&h->maps[b].tmap[s], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, a.cell, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return PIC_ECUDA;
+    }
+  h->maps_ok = true;
+  return PIC_OK;
+}
+
 StepParams32 params32(pic_handle* h) {
   StepParams32 P;
   for (int s = 0; s < 2; ++s) {
@@ -408,7 +460,8 @@ int refresh_field(pic_handle* h) {
   StepParams32 P32 = params32(h);
   P32.sum_ke = 1u;
   cudaError_t err = h->plain ? launch_step64(params64(h), h->grid_step, h->st)
-                             : launch_step32(P32, h->grid_step, h->st);
+                             : (h->maps_ok ? launch_step32(P32, h->maps[h->cur], h->grid_step, h->st)
+                                           : cudaErrorInvalidValue);
   prof_end(h, &e);
   h->ph = saved;
   h->ke_valid = !h->plain;
@@ -1201,7 +1254,10 @@ int step_particles(pic_handle* h) {
       P.scatter = 1u;
     }
     prof_begin(h, scatter ? K_STEP_SCATTER : K_STEP, &e);
-    CK(scatter ? launch_step32_scatter(P, h->grid_scatter, h->st) : launch_step32(P, h->grid_step, h->st));
+    // both read buffer cur
+    if (!h->maps_ok) return PIC_ECUDA;
+    CK(scatter ? launch_step32_scatter(P, h->maps[h->cur], h->grid_scatter, h->st)
+               : launch_step32(P, h->maps[h->cur], h->grid_step, h->st));
     prof_end(h, &e);
     if (h->cap_nt) {  // the neutrals alive at the step start, and the ions recycled in this step:
       // in place, or compacted into the other buffer on the steps that sort
@@ -1358,6 +1414,11 @@ uint32_t pic_blob_crc32(const void* p, size_t n) {
     h->ws_bytes = need;
     layout(h, static_cast<char*>(h->ws), &need);
     derive(h);
+    if (!h->plain && make_step_maps(h) != PIC_OK) {
+      if (h->owns_ws) cudaFree(h->ws);
+      delete h;
+      return PIC_ECUDA;
+    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1463,7 +1524,8 @@ int pic_local_deposit(pic_handle* h, int64_t* R_local) {
   h->ph.mcc_mask = 0u;
   StepParams32 P = params32(h);
   h->ph = saved;
-  CK(launch_step32(P, h->grid_step, h->st));
+  if (!h->maps_ok) return PIC_ECUDA;
+  CK(launch_step32(P, h->maps[h->cur], h->grid_step, h->st));
   const PoissonParams F = field_params(h, false, false);
   CK(launch_node_deposit(F, reinterpret_cast<long long*>(R_local), h->st));
   for (int s = 0; s < 2; ++s) {

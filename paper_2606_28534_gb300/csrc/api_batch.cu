@@ -517,6 +517,7 @@ int pic_batch_init(const pic_config* cfgs, int32_t nsims, void* workspace, size_
         break;
       }
       make_view(b, k, b->views[k]);
+      if (make_step_maps(b->views[k]) != PIC_OK) rc = PIC_ECUDA;  // the single-run steps of a view
     }
     if (rc == PIC_OK) {
       pic_batch_tuning t;

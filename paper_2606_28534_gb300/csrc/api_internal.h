@@ -43,6 +43,8 @@ struct pic_handle {
   Species32 a32[2][2];  // [buffer][species]
   int cur = 0;
   Species64 a64[2];
+  StepMaps maps[2];             // the particle step's stage tensor maps, per buffer (FP32 path)
+  bool maps_ok = false;         // maps made (make_step_maps): particle steps may be launched
   FieldGrid* fgrid = nullptr;  // scratch of the grid-wide field solve (FP32 path)
   int field_ctas = 0;          // its CTAs (0: the one-cluster solve)
   unsigned int* cnt[2] = {nullptr, nullptr};
@@ -102,6 +104,8 @@ int load_initial(pic_handle* h);
 // Every check pic_restore makes of a blob before it changes any state: format, checksum,
 // configuration hash, sizes, capacity, the range of every cell and fraction.
 int check_blob(const pic_handle* h, const void* buf, size_t len);
+// The particle step's stage tensor maps of a handle (api.cu); PIC_ECUDA if they cannot be made.
+int make_step_maps(pic_handle* h);
 // Everything pic_restore does before the redeposit: (unless checked) check_blob, particles into
 // buffer 0 (FP32: through h->stage), control block, cleared accumulators, h->step.  Leaves
 // h->cur = 0.

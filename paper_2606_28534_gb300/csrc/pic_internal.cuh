@@ -15,6 +15,7 @@
 // when its expiry is a candidate; both 0 for species without the test).  DEAD_CELL has bit 31 set,
 // which no live word has.  The plain FP64 path keeps the pair (k | c << 12) in its own array.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the descriptor type only; no driver call is linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -156,6 +157,13 @@ struct StepParams32 {
   unsigned int* cursor[2];  // scatter: per-cell write cursors of the sort scan
   unsigned int* wlog;    // recycling: index of each ion absorbed at a wall in the buffer the step
                          // reads, | side << 31 (null: no recycling)
+};
+
+// The particle step's stage loads (a kernel parameter of its own): per species, a 2-D tensor map
+// over the five 4-byte arrays of the buffer the step reads (rows cell, frac, vx, vy, vz, each
+// cap[s] elements apart), so that a chunk's stage is one tensor copy of a 128 x 5 box.
+struct StepMaps {
+  CUtensorMap tmap[2];
 };
 
 // The neutral step (k_neutral.cu): the neutrals alive at the step start move, leave at the walls
@@ -340,6 +348,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// Global -> shared tiled tensor copy of the box at (x, y) of a 2-D tensor map (in kernel parameter
+// space); completes the box's bytes on the mbarrier.  x times the element size a multiple of 16.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
 // Global -> shared bulk copy; completes tx bytes on the mbarrier.  Both addresses 16-byte aligned,
 // size a multiple of 16.
 __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
@@ -523,7 +540,7 @@ cudaError_t launch_node_deposit(const PoissonParams& p, long long* out, cudaStre
 // particle decomposition: drop (mark dead) the live particles whose id % nparts != part
 cudaError_t launch_keep_subset(const Species32& a0, const Species32& a1, Ctl* ctl, unsigned part, unsigned nparts,
                                cudaStream_t st);
-cudaError_t launch_step32(const StepParams32& p, int grid, cudaStream_t st);
+cudaError_t launch_step32(const StepParams32& p, const StepMaps& m, int grid, cudaStream_t st);
 cudaError_t launch_step64(const StepParams64& p, int grid, cudaStream_t st);
 cudaError_t launch_source32(const StepParams32& p, cudaStream_t st);
 cudaError_t launch_source64(const StepParams64& p, cudaStream_t st);
@@ -537,7 +554,7 @@ cudaError_t launch_sort32(Species32 src[2], Species32 dst[2], unsigned int* cnt[
 // the scan alone, deferred: the next step kernel (scatter mode) moves the particles
 cudaError_t launch_sort_scan32(Species32 src[2], Species32 dst[2], unsigned int* cnt[2], unsigned int* cursor[2],
                                const unsigned long long cap[2], Ctl* ctl, int N, cudaStream_t st);
-cudaError_t launch_step32_scatter(const StepParams32& p, int grid, cudaStream_t st);
+cudaError_t launch_step32_scatter(const StepParams32& p, const StepMaps& m, int grid, cudaStream_t st);
 cudaError_t launch_diag64(const StepParams64& p, int grid, cudaStream_t st);
 cudaError_t launch_diag32(const StepParams32& p, int grid, cudaStream_t st);
 cudaError_t launch_diag_grid(const long long* R0, const long long* R1, int sign0, int sign1, const double* E, int N,

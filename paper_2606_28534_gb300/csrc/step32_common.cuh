@@ -358,6 +358,19 @@ __device__ __forceinline__ void stage_issue(const Species32& A, unsigned t, unsi
   stage_issue_span(A, i0, min((unsigned)CHUNK, ncur - i0), buf, bar, with_id);
 }
 
+// The same with one 2-D tensor copy of the chunk's five 4-byte arrays (the box: 128 particles x 5
+// rows, the stage's layout); the ids, when asked for, by a 1-D bulk copy.  The box always arrives
+// whole: past the species' capacity TMA fills zeros, and slots past ncur are never used.
+__device__ __forceinline__ void stage_issue_tmap(const CUtensorMap* map, const Species32& A, unsigned t,
+                                                 unsigned ncur, unsigned char* buf, unsigned long long* bar,
+                                                 bool with_id) {
+  const unsigned i0 = t * CHUNK;
+  const unsigned n = min((unsigned)CHUNK, ncur - i0);
+  mbar_expect_tx(bar, CHUNK * 20u + (with_id ? n * 8u : 0u));
+  tma_load_2d(buf, map, (int)i0, 0, bar);
+  if (with_id) tma_load_1d(buf + CHUNK * 20, A.id + i0, n * 8u, bar);
+}
+
 // Adds item idx (0 <= idx < 16) of a set of counters to a simulation's control block.
 __device__ __forceinline__ void counters_to_ctl(Ctl* g, const Phys& ph, const BlockCounters& bc, int idx) {
   if (idx < 4) {
