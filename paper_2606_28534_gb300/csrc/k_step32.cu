@@ -38,7 +38,7 @@ struct StepShape {
 
 // One warp handles chunks of 32 x PIC_PPT consecutive particles of one species (a contiguous run
 // of chunks per warp; strided over the warps of the grid in the step after a sort); the warp's next
-// chunk is already streaming into shared memory (TMA bulk copy
+// chunk is already streaming into shared memory (a TMA tensor copy
 // completing on an mbarrier) while it computes the current one.  No block-wide barrier inside the
 // particle loop.
 // SCATTER: the step after a sort step.  The sort scan has turned the per-cell counts of the
