@@ -286,30 +286,35 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-int make_step_maps(pic_handle* h) {
-  h->maps_ok = false;
+int encode_step_maps(const Species32* a, const unsigned long long* cap, StepMaps* out) {
   const EncodeTiledFn enc = encode_tiled();
   if (!enc) return PIC_ECUDA;
-  for (int b = 0; b < 2; ++b)
-    for (int s = 0; s < 2; ++s) {
-      const Species32& a = h->a32[b][s];
-      const unsigned long long cap = h->cap[s];
-      const char* const rows[5] = {reinterpret_cast<const char*>(a.cell), reinterpret_cast<const char*>(a.frac),
-                                   reinterpret_cast<const char*>(a.vx), reinterpret_cast<const char*>(a.vy),
-                                   reinterpret_cast<const char*>(a.vz)};
-      const long long pitch = rows[1] - rows[0];
-      bool ok = pitch >= (long long)(cap * 4) && pitch % 16 == 0 && (reinterpret_cast<uintptr_t>(rows[0]) & 15u) == 0;
-      for (int r = 2; r < 5; ++r) ok = ok && rows[r] - rows[r - 1] == pitch;
-      if (!ok) return PIC_ECUDA;  // not a layout the maps can describe
-      const cuuint64_t dims[2] = {cap, 5};
-      const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-      const cuuint32_t box[2] = {32 * PIC_PPT, 5};
-      const cuuint32_t estr[2] = {1, 1};
-      if (enc(&h->maps[b].tmap[s], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, a.cell, dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return PIC_ECUDA;
-    }
+  for (int s = 0; s < 2; ++s) {
+    const char* const rows[5] = {reinterpret_cast<const char*>(a[s].cell), reinterpret_cast<const char*>(a[s].frac),
+                                 reinterpret_cast<const char*>(a[s].vx), reinterpret_cast<const char*>(a[s].vy),
+                                 reinterpret_cast<const char*>(a[s].vz)};
+    const long long pitch = rows[1] - rows[0];
+    bool ok = pitch >= (long long)(cap[s] * 4) && pitch % 16 == 0 && (reinterpret_cast<uintptr_t>(rows[0]) & 15u) == 0;
+    for (int r = 2; r < 5; ++r) ok = ok && rows[r] - rows[r - 1] == pitch;
+    if (!ok) return PIC_ECUDA;  // not a layout the maps can describe
+    const cuuint64_t dims[2] = {cap[s], 5};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {32 * PIC_PPT, 5};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&out->tmap[s], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, a[s].cell, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return PIC_ECUDA;
+  }
+  return PIC_OK;
+}
+
+int make_step_maps(pic_handle* h) {
+  h->maps_ok = false;
+  for (int b = 0; b < 2; ++b) {
+    const int rc = encode_step_maps(h->a32[b], h->cap, &h->maps[b]);
+    if (rc != PIC_OK) return rc;
+  }
   h->maps_ok = true;
   return PIC_OK;
 }

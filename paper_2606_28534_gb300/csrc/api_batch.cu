@@ -42,6 +42,7 @@ struct pic_batch {
   BatchDev* dev = nullptr;
   Ctl* ctl = nullptr;
   Species32 arr[2][2];  // [buffer][species]
+  StepMaps maps[2];     // the step's stage tensor maps over arr[buffer] (both species)
   unsigned int* cnt[2] = {nullptr, nullptr};
   unsigned long long* S[2] = {nullptr, nullptr};
   unsigned int* cursor[2] = {nullptr, nullptr};
@@ -348,7 +349,7 @@ int enqueue_step(pic_batch* b, cudaStream_t st) {
   const bool scatter = b->pending;
   EvPair e;
   bprof_begin(b, scatter ? K_STEP_SCATTER : K_STEP, &e, st);
-  CKB(launch_bstep32(b->tun.variant, step_params(b, scatter), b->grid_step, scatter, st));
+  CKB(launch_bstep32(b->tun.variant, step_params(b, scatter), b->maps[b->cur], b->grid_step, scatter, st));
   bprof_end(b, &e, st);
   if (scatter) {
     b->cur = 1 - b->cur;
@@ -519,6 +520,8 @@ int pic_batch_init(const pic_config* cfgs, int32_t nsims, void* workspace, size_
       make_view(b, k, b->views[k]);
       if (make_step_maps(b->views[k]) != PIC_OK) rc = PIC_ECUDA;  // the single-run steps of a view
     }
+    for (int p = 0; p < 2 && rc == PIC_OK; ++p)
+      if (encode_step_maps(b->arr[p], b->total_cap, &b->maps[p]) != PIC_OK) rc = PIC_ECUDA;
     if (rc == PIC_OK) {
       pic_batch_tuning t;
       std::memset(&t, 0, sizeof(t));

@@ -106,6 +106,8 @@ int load_initial(pic_handle* h);
 int check_blob(const pic_handle* h, const void* buf, size_t len);
 // The particle step's stage tensor maps of a handle (api.cu); PIC_ECUDA if they cannot be made.
 int make_step_maps(pic_handle* h);
+// The same for species arrays a[2] of capacities cap[2] (an ensemble's batch-wide arrays).
+int encode_step_maps(const Species32* a, const unsigned long long* cap, StepMaps* out);
 // Everything pic_restore does before the redeposit: (unless checked) check_blob, particles into
 // buffer 0 (FP32: through h->stage), control block, cleared accumulators, h->step.  Leaves
 // h->cur = 0.

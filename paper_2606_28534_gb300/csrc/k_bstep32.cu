@@ -57,12 +57,19 @@ __device__ __forceinline__ int owner(const unsigned* __restrict__ pre, int nsims
 
 // Lane 0: bulk copies of local chunk lt of species s of simulation k (arrays A) into a stage buffer.
 // The ids only in the step after a sort (it moves them); the ordinary step needs none.
-__device__ __forceinline__ void issue_chunk(const BatchStep32& B, const Species32& A, int s, int k, unsigned lt,
-                                            unsigned char* buf, unsigned long long* bar, bool with_id) {
+// One 2-D tensor copy of the chunk's five 4-byte arrays (map: the batch-wide arrays of species s
+// in the buffer read), at x = the chunk's first slot in the batch (a multiple of 128: segments are
+// multiples of 1024 slots, so the box stays inside the simulation's segment).
+__device__ __forceinline__ void issue_chunk(const BatchStep32& B, const CUtensorMap* map, const Species32& A, int s,
+                                            int k, unsigned lt, unsigned char* buf, unsigned long long* bar,
+                                            bool with_id) {
   const unsigned nk = B.ncur[s][k];
   const unsigned i0 = lt * CHUNK;
   const unsigned n = min((unsigned)CHUNK, nk - i0);  // multiple of 4
-  stage_issue_span(A, B.hot[k].seg[s] + i0, n, buf, bar, with_id);
+  const unsigned g = B.hot[k].seg[s] + i0;
+  mbar_expect_tx(bar, CHUNK * 20u + (with_id ? n * 8u : 0u));
+  tma_load_2d(buf, map, (int)g, 0, bar);
+  if (with_id) tma_load_1d(buf + CHUNK * 20, A.id + g, n * 8u, bar);
 }
 
 // Where births of simulation k go in species s: past the extent of the buffer being written (after
@@ -92,7 +99,8 @@ __device__ __forceinline__ void leave_sim(const BatchStep32& B, int k, int s, co
 // sorted slot of its simulation's segment in B.sp (cursors: the sort scan's, at the simulation's
 // cell offset); B.sims then addresses the written buffer, for the collision queue and births.
 template <int TPB, int MINB, int NST, bool SCATTER>
-__global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ BatchStep32 B) {
+__global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ BatchStep32 B,
+                                                              const __grid_constant__ StepMaps M) {
   constexpr int WARPS = TPB / 32;
   constexpr int SB = BShape<TPB, NST, SCATTER>::SB;
   static_assert(sizeof(BlockCounters) / 4 <= 32, "one word of the counters per lane");
@@ -145,7 +153,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         const unsigned t = t0 + st;
         if (t < t1) {
           while (pre[ki + 1] <= t) ++ki;
-          issue_chunk(B, Asrc, s, ki, t - pre[ki], stage + st * SB, bar + st, SCATTER);
+          issue_chunk(B, s ? &M.tmap[1] : &M.tmap[0], Asrc, s, ki, t - pre[ki], stage + st * SB, bar + st, SCATTER);
         }
       }
     }
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
           if (tn < t1) {
             int ki = kc;  // owner of chunk tn: this simulation or a later one
             while (pre[ki + 1] <= tn) ++ki;
-            issue_chunk(B, Asrc, s, ki, tn - pre[ki], sbuf, bar + st, with_id);
+            issue_chunk(B, s ? &M.tmap[1] : &M.tmap[0], Asrc, s, ki, tn - pre[ki], sbuf, bar + st, with_id);
           }
         }
         st = st + 1 == NST ? 0 : st + 1;
@@ -479,7 +487,7 @@ __global__ void __launch_bounds__(PLAN_TPB) k_bplan(const BatchPlan P) {
 }
 
 template <int TPB, int MINB, int NST, bool SCATTER>
-cudaError_t launch_variant(const BatchStep32& p, int grid, cudaStream_t st) {
+cudaError_t launch_variant(const BatchStep32& p, const StepMaps& m, int grid, cudaStream_t st) {
   constexpr size_t smem = BShape<TPB, NST, SCATTER>::SMEM;
   static bool done = false;
   if (!done) {
@@ -487,7 +495,7 @@ cudaError_t launch_variant(const BatchStep32& p, int grid, cudaStream_t st) {
                          (int)smem);
     done = true;
   }
-  k_bstep32<TPB, MINB, NST, SCATTER><<<grid, TPB, smem, st>>>(p);
+  k_bstep32<TPB, MINB, NST, SCATTER><<<grid, TPB, smem, st>>>(p, m);
   return cudaGetLastError();
 }
 
@@ -505,8 +513,8 @@ int occupancy_variant() {
 
 struct Variant {
   const char* name;
-  cudaError_t (*launch)(const BatchStep32&, int, cudaStream_t);
-  cudaError_t (*launch_scatter)(const BatchStep32&, int, cudaStream_t);
+  cudaError_t (*launch)(const BatchStep32&, const StepMaps&, int, cudaStream_t);
+  cudaError_t (*launch_scatter)(const BatchStep32&, const StepMaps&, int, cudaStream_t);
   int (*occupancy)();
 };
 
@@ -531,9 +539,9 @@ const char* bstep32_variant_name(int v) { return v >= 0 && v < kNumVariants ? kV
 
 int bstep32_occupancy(int v) { return v >= 0 && v < kNumVariants ? kVariants[v].occupancy() : 0; }
 
-cudaError_t launch_bstep32(int v, const BatchStep32& p, int grid, bool scatter, cudaStream_t st) {
+cudaError_t launch_bstep32(int v, const BatchStep32& p, const StepMaps& m, int grid, bool scatter, cudaStream_t st) {
   if (v < 0 || v >= kNumVariants || grid < 1) return cudaErrorInvalidValue;
-  return scatter ? kVariants[v].launch_scatter(p, grid, st) : kVariants[v].launch(p, grid, st);
+  return scatter ? kVariants[v].launch_scatter(p, m, grid, st) : kVariants[v].launch(p, m, grid, st);
 }
 
 cudaError_t launch_bplan(const BatchPlan& p, cudaStream_t st) {

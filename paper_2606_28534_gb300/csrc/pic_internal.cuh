@@ -595,7 +595,7 @@ cudaError_t launch_ndiag32(const Species32& a, Ctl* ctl, float mass, int grid, c
 int bstep32_variants();
 const char* bstep32_variant_name(int v);
 int bstep32_occupancy(int v);
-cudaError_t launch_bstep32(int v, const BatchStep32& p, int grid, bool scatter, cudaStream_t st);
+cudaError_t launch_bstep32(int v, const BatchStep32& p, const StepMaps& m, int grid, bool scatter, cudaStream_t st);
 cudaError_t launch_bplan(const BatchPlan& p, cudaStream_t st);
 cudaError_t launch_field_batch(const PoissonParams* tab, int nsims, int maxN, cudaStream_t st);
 // the sort scans of an ensemble (tables with defer = 1: the next step moves the particles)
