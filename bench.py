@@ -50,7 +50,7 @@ BYTES_SCATTER_KERNEL = 56
 # particles to a full launch: the ordinary step and the step after a sort
 TRAFFIC_STEP, TRAFFIC_SCATTER = 41.40, 57.41
 # the same for the ensemble's particle step (ncu on a 16-run ensemble of config 4's distribution)
-TRAFFIC_BSTEP = 41.49
+TRAFFIC_BSTEP = 41.50
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
 # (8 B); on sort steps it writes each survivor, compacted, into the other buffer instead (28 B)
 BYTES_NEUTRAL_KERNEL, BYTES_NEUTRAL_COMPACT = 36, 56
