@@ -630,11 +630,17 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         dsum = sim2.diag_decode(bufs[(ek - 1) % 2])["particle_steps"]
         torch.cuda.synchronize()
         t2 = time.perf_counter()
+        # the same restore once more, outside the metric: it separates first-call costs of the
+        # process (the temporary device buffer's first allocation, module loads) from the copy
+        ta = time.perf_counter()
+        rc = pic.lib().pic_restore(sim2._h, pinned.data_ptr(), pinned.numel())
+        restore_again = time.perf_counter() - ta if rc == 0 else None
         ranks.barrier()
         e2e = {"value": whole_job(dsum, 1e3 * (t2 - t0), ranks)[0], "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(pinned.numel() / ek),
                "d2h_bytes_per_step": int(pic.lib().pic_diag_bytes()),
-               "steps": ek, "restore_s": round(t1 - t0, 4), "ms_per_step": round(1e3 * (t2 - t1) / ek, 4),
+               "steps": ek, "restore_s": round(t1 - t0, 4),
+               "restore_again_s": round(restore_again, 4) if restore_again is not None else None, "ms_per_step": round(1e3 * (t2 - t1) / ek, 4),
                "what": "pic_restore from a checkpoint blob in pinned host memory, then per step "
                        "pic_step(1) and pic_diag_async(PIC_DIAG_COUNTERS) (device-to-host copy of the "
                        "control block: counters, particle-steps, error word; no energy reduction) into "
