@@ -39,7 +39,7 @@ template <int TPB, int NST, bool SCATTER>
 struct BShape {
   static constexpr int WARPS = TPB / 32;
   static constexpr int SB = SCATTER ? STAGE_BYTES : CHUNK * 20;
-  static constexpr size_t SMEM = (size_t)WARPS * (NST * SB + QCAP * 8 + NST * 8);
+  static constexpr size_t SMEM = (size_t)WARPS * (NST * SB + QCAP * 4 + NST * 8);
 };
 
 // Last k < nsims with pre[k] <= t, for t < pre[nsims]: the simulation that owns chunk t.
@@ -80,7 +80,7 @@ __device__ __forceinline__ unsigned long long birth_base(const BatchStep32& B, i
 
 // The warp leaves simulation k: its queued collisions, the kinetic energy of its particles of
 // species s and its counters go to the simulation; the counters restart from zero.
-__device__ __forceinline__ void leave_sim(const BatchStep32& B, int k, int s, const unsigned long long* q, int qn,
+__device__ __forceinline__ void leave_sim(const BatchStep32& B, int k, int s, const unsigned* q, int qn,
                                           BlockCounters& wc, unsigned long long ke, bool run_queue, bool scatter) {
   const int lane = threadIdx.x & 31;
   if (run_queue && qn)
@@ -111,10 +111,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
   const int tid = threadIdx.x;
   const int lane = tid & 31, wib = tid >> 5;
   unsigned char* const stage = dsm + (size_t)wib * NST * SB;
-  unsigned long long* const q =
-      reinterpret_cast<unsigned long long*>(dsm + (size_t)WARPS * NST * SB) + (size_t)wib * QCAP;
+  unsigned* const q = reinterpret_cast<unsigned*>(dsm + (size_t)WARPS * NST * SB) + (size_t)wib * QCAP;
   unsigned long long* const bar = reinterpret_cast<unsigned long long*>(
-                                      dsm + (size_t)WARPS * (NST * SB + QCAP * 8)) + wib * NST;
+                                      dsm + (size_t)WARPS * (NST * SB + QCAP * 4)) + wib * NST;
   BlockCounters& wc = wcs[wib];
   if (lane < (int)(sizeof(BlockCounters) / 4)) reinterpret_cast<unsigned int*>(&wc)[lane] = 0u;
   if (lane < NST) mbar_init(bar + lane, 1u);
@@ -142,7 +141,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
     const Species32& Asrc = SCATTER ? B.src[s] : B.sp[s];  // read
     const SpConst& K = ph.sp[s];
     const bool moves = (ph.push_mask >> s) & 1u;
-    const unsigned long long tag = (unsigned long long)s << 63;
+    const unsigned tag = (unsigned)s << 31;
     const int kfirst = owner(pre, nsims, t0);
 
     // prologue: the warp's first NST chunks
@@ -333,7 +332,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         for (int k = 0; k < PIC_PPT; ++k) {
           const bool qk = SCATTER ? ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL : (qmask >> k) & 1u;
           const unsigned b = __ballot_sync(0xFFFFFFFFu, qk);
-          if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(SCATTER ? slot[k] : i0 + k);
+          if (qk) q[qn + __popc(b & below)] = tag | (SCATTER ? slot[k] : i0 + k);
           qn += __popc(b);
         }
       }

@@ -33,7 +33,12 @@ template <bool SCATTER>
 struct StepShape {
   static constexpr int NSTAGE = SCATTER ? 2 : PIC_STEP_NSTAGE;
   static constexpr int SB = SCATTER ? STAGE_BYTES : CHUNK * 20;
-  static constexpr size_t SMEM = (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + DW_BYTES + NSTAGE * 8);
+  // cells of the deposit window: 4 in the ordinary step, so that three CTAs per SM leave the larger
+  // L1 split of the SM's memory (the field gathers hit it; 0.91 -> 0.89 ms), 8 after a sort (its
+  // chunks, ten steps of drift from their order, spread wider)
+  static constexpr int W = SCATTER ? 8 : 4;
+  static constexpr int WB = window_bytes<W>();
+  static constexpr size_t SMEM = (size_t)WARPS * (NSTAGE * SB + QCAP * 4 + WB + NSTAGE * 8);
 };
 
 // One warp handles chunks of 32 x PIC_PPT consecutive particles of one species (a contiguous run
@@ -62,15 +67,14 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
   const int tid = threadIdx.x;
   const int lane = tid & 31, wib = tid >> 5;
   unsigned char* const stage = dsm + (size_t)wib * NSTAGE * SB;
-  unsigned long long* const q =
-      reinterpret_cast<unsigned long long*>(dsm + (size_t)WARPS * NSTAGE * SB) + (size_t)wib * QCAP;
+  unsigned* const q = reinterpret_cast<unsigned*>(dsm + (size_t)WARPS * NSTAGE * SB) + (size_t)wib * QCAP;
   const unsigned wslots =  // this lane's deposit window slots
-      smem_u32(dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8) + (size_t)wib * DW_BYTES) + lane * 8u;
+      smem_u32(dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 4) + (size_t)wib * StepShape<SCATTER>::WB) + lane * 8u;
   unsigned long long* const bar = reinterpret_cast<unsigned long long*>(
-                                      dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 8 + DW_BYTES)) + wib * NSTAGE;
+                                      dsm + (size_t)WARPS * (NSTAGE * SB + QCAP * 4 + StepShape<SCATTER>::WB)) + wib * NSTAGE;
   if (tid < (int)(sizeof(BlockCounters) / 4)) reinterpret_cast<unsigned int*>(&bc)[tid] = 0u;
   if (lane < NSTAGE) mbar_init(bar + lane, 1u);
-  window_zero(wslots);
+  window_zero<StepShape<SCATTER>::W>(wslots);
   mbar_init_fence();
   __syncthreads();
 
@@ -107,7 +111,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
     const SpConst& K = Kh;
     const bool moves = (ph.push_mask >> s) & 1u;
     const bool collides = (ph.mcc_mask >> s) & 1u;  // takes the null-collision countdown
-    const unsigned long long tag = (unsigned long long)s << 63;
+    const unsigned tag = (unsigned)s << 31;
     // Chunk schedule.  An ordinary step gives each warp a contiguous run of chunks: concurrent warps
     // then work in different cells, so that the deposit's reductions from different warps rarely
     // meet on one address (on the grid stride ~50 warps deposit into one dense cell at a time).  The
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         for (int k = 0; k < PIC_PPT; ++k) {
           const bool qk = SCATTER ? ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL : (qmask >> k) & 1u;
           const unsigned b = __ballot_sync(0xFFFFFFFFu, qk);
-          if (qk) q[qn + __popc(b & below)] = tag | (unsigned long long)(SCATTER ? slot[k] : i0 + k);
+          if (qk) q[qn + __popc(b & below)] = tag | (SCATTER ? slot[k] : i0 + k);
           qn += __popc(b);
         }
       }
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
           cc[k] = c[k] != PIC_DEAD_CELL ? c[k] & PIC_CELL_MASK : -1;
           wr[k] = wr_of(f[k]);
         }
-        window_deposit(wslots, cc, wr, 0, P.cnt[s], P.S[s]);
+        window_deposit<StepShape<SCATTER>::W>(wslots, cc, wr, 0, P.cnt[s], P.S[s]);
       }
 
       if (qn > QFLUSH) {

@@ -232,8 +232,12 @@ __device__ __forceinline__ void warp_deposit(unsigned int* __restrict__ gcnt, un
 // slots for the DW cells that end at the chunk's highest cell, and each touched cell is reduced
 // across the warp once, into one global reduction per array.  Particles below the window go
 // straight to global memory.  Integer sums: exact in any order.
-constexpr int DW = 8;                  // cells in the window (a power of two)
-constexpr int DW_BYTES = DW * 32 * 8;  // one warp's slots: column j of lane l at 256 j + 8 l
+// A window of W cells (a power of two) takes W * 256 bytes per warp: column j of lane l at
+// 256 j + 8 l.
+template <int W>
+constexpr int window_bytes() {
+  return W * 32 * 8;
+}
 
 // A lane's slot holds two words for its (at most four) particles of one cell:
 //   h = count << 23 + sum of (W_r >> 16),   l = sum of (W_r & 0xFFFF).
@@ -244,13 +248,16 @@ __device__ __forceinline__ void red_shared_u32(unsigned a, unsigned v) {
 }
 
 // Zeroes this lane's slots (once per kernel; the flush re-zeroes what it reads).
+template <int DW>
 __device__ __forceinline__ void window_zero(unsigned slots) {
 #pragma unroll
   for (int j = 0; j < DW; ++j) asm volatile("st.shared.u64 [%0], %1;" ::"r"(slots + 256u * j), "l"(0ull) : "memory");
 }
 
-// Deposits the live particles of a chunk (c[k]: cell index, -1 dead; wr[k]: right weights).
-// slots: shared address of this lane's column 0.  cell_off is added to the global cell index.
+// Deposits the live particles of a chunk (c[k]: cell index, -1 dead; wr[k]: right weights) through
+// a window of DW cells.  slots: shared address of this lane's column 0.  cell_off is added to the
+// global cell index.
+template <int DW>
 __device__ __forceinline__ void window_deposit(unsigned slots, const int (&c)[PIC_PPT], const unsigned (&wr)[PIC_PPT],
                                                int cell_off, unsigned int* __restrict__ gcnt,
                                                unsigned long long* __restrict__ gS) {
@@ -293,7 +300,8 @@ __device__ __forceinline__ void window_deposit(unsigned slots, const int (&c)[PI
   }
 }
 
-constexpr int QCAP = 160;   // per-warp queue of collision candidates
+constexpr int QCAP = 160;   // per-warp queue of collision candidates: species << 31 | slot (the
+                            // configuration check keeps capacities below 2^31)
 constexpr int QFLUSH = 32;  // the warp processes its queue once it holds more than this (a
                             // chunk adds at most 32 * PIC_PPT = 128 entries)
 constexpr int CHUNK = 32 * PIC_PPT;
@@ -306,16 +314,16 @@ constexpr int STAGE_BYTES = CHUNK * (5 * 4 + 8);
 // (from word 0 of the same draw) in the cell word.  About one particle in a hundred expires per
 // step, so this runs every few dozen chunks, out of the streaming loop's path.  Inlined: as a
 // called function its register needs made the caller save registers around every call.
-__device__ __forceinline__ void flush_queue(const StepParams32& P, const unsigned long long* q, int qn,
+__device__ __forceinline__ void flush_queue(const StepParams32& P, const unsigned* q, int qn,
                                          unsigned long long ncur0, unsigned long long ncur1, BlockCounters* bc) {
   __syncwarp();
   const int lane = threadIdx.x & 31;
   for (int base = 0; base < qn; base += 32) {
     const int e = base + lane;
     if (e >= qn) break;
-    const unsigned long long rec = q[e];
-    const int s = (int)(rec >> 63);
-    const unsigned long long i = rec & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned rec = q[e];
+    const int s = (int)(rec >> 31);
+    const unsigned long long i = rec & 0x7FFFFFFFu;
     const Species32 A = s ? P.sp[1] : P.sp[0];
     const int cw = A.cell[i];
     const int c = cw & PIC_CELL_MASK;
