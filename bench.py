@@ -48,7 +48,7 @@ BYTES_SCATTER_KERNEL = 56
 # DRAM bytes per particle of one launch, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of these kernels on the 12.6M-particle profiling case (c3p), scaled by
 # particles to a full launch: the ordinary step and the step after a sort
-TRAFFIC_STEP, TRAFFIC_SCATTER = 41.40, 57.41
+TRAFFIC_STEP, TRAFFIC_SCATTER = 41.37, 57.45
 # the same for the ensemble's particle step (ncu on a 16-run ensemble of config 4's distribution)
 TRAFFIC_BSTEP = 41.50
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
