@@ -46,9 +46,10 @@ BYTES_STEP64_KERNEL = 72
 # the step after a sort reads and writes each particle with its id, to its sorted slot: 28 + 28 B
 BYTES_SCATTER_KERNEL = 56
 # DRAM bytes per particle of one launch, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of these kernels on the 12.6M-particle profiling case (c3p), scaled by
-# particles to a full launch: the ordinary step and the step after a sort
-TRAFFIC_STEP, TRAFFIC_SCATTER = 41.37, 57.45
+# dram__bytes_write.sum) of these kernels on the 50.3M-particle profiling case (c3h, large enough
+# for the ordinary step's claimed chunk segments), scaled by particles to a full launch: the
+# ordinary step and the step after a sort
+TRAFFIC_STEP, TRAFFIC_SCATTER = 42.75, 58.80
 # the same for the ensemble's particle step (ncu on a 16-run ensemble of config 4's distribution)
 TRAFFIC_BSTEP = 41.50
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
@@ -188,6 +189,7 @@ W_DESC = {
           "B 0.5 @ 30 deg, 4 processes, sort every 10 steps",
     "c5": "collisionless, 1024 cells, 409,600 particles",
     "c3p": "non-uniform load profiling case, 65536 cells, 12,582,912 particles",
+    "c3h": "non-uniform load profiling case, 65536 cells, 50,331,648 particles",
     "c6": "D+/e/D sheath, 65536 cells, 100,007,936 charged + 50,003,968 neutral particles",
     "c6p": "D+/e/D sheath profiling case, 65536 cells, 12,582,912 charged + 6,291,456 neutral particles",
 }
@@ -635,17 +637,27 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         ta = time.perf_counter()
         rc = pic.lib().pic_restore(sim2._h, pinned.data_ptr(), pinned.numel())
         restore_again = time.perf_counter() - ta if rc == 0 else None
+        sim2.close()
+        # also outside the metric, after the restores (a first copy out of a freshly written pinned
+        # buffer can be slower than later ones): the plain copy rate of this buffer to the device
+        probe = torch.empty(pinned.numel(), dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        tp = time.perf_counter()
+        probe.copy_(pinned, non_blocking=True)
+        torch.cuda.synchronize()
+        blob_h2d_gbs = pinned.numel() / (time.perf_counter() - tp) / 1e9
+        del probe
         ranks.barrier()
         e2e = {"value": whole_job(dsum, 1e3 * (t2 - t0), ranks)[0], "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(pinned.numel() / ek),
                "d2h_bytes_per_step": int(pic.lib().pic_diag_bytes()),
                "steps": ek, "restore_s": round(t1 - t0, 4),
-               "restore_again_s": round(restore_again, 4) if restore_again is not None else None, "ms_per_step": round(1e3 * (t2 - t1) / ek, 4),
+               "restore_again_s": round(restore_again, 4) if restore_again is not None else None,
+               "blob_h2d_gbs": round(blob_h2d_gbs, 1), "ms_per_step": round(1e3 * (t2 - t1) / ek, 4),
                "what": "pic_restore from a checkpoint blob in pinned host memory, then per step "
                        "pic_step(1) and pic_diag_async(PIC_DIAG_COUNTERS) (device-to-host copy of the "
                        "control block: counters, particle-steps, error word; no energy reduction) into "
                        "pinned memory, each step's copy decoded on the host while the next step runs"}
-        sim2.close()
 
     batch = None
     if single and not args.no_batch:

@@ -24,13 +24,17 @@
 namespace {
 
 static_assert(PIC_PPT == 4, "each lane moves four particles: one 128-bit access per array");
-constexpr int WARPS = PIC_TPB / 32;
 #ifndef PIC_STEP_NSTAGE
 #define PIC_STEP_NSTAGE 2  // chunks in flight per warp in the ordinary step (3 measured slower)
 #endif
 // Per variant: TMA stages per warp and the bytes of one stage (the ordinary step stages no ids).
 template <bool SCATTER>
 struct StepShape {
+  static constexpr int TPB = PIC_TPB;
+  static constexpr int WARPS = TPB / 32;
+  // the ordinary step may claim chunk segments (below); after a sort, claimed segments made that
+  // step 1 % faster but left an order that made the next nine steps 3 % slower
+  static constexpr bool DYN = !SCATTER;
   static constexpr int NSTAGE = SCATTER ? 2 : PIC_STEP_NSTAGE;
   static constexpr int SB = SCATTER ? STAGE_BYTES : CHUNK * 20;
   // cells of the deposit window: 4 in the ordinary step, so that three CTAs per SM leave the larger
@@ -41,8 +45,9 @@ struct StepShape {
   static constexpr size_t SMEM = (size_t)WARPS * (NSTAGE * SB + QCAP * 4 + WB + NSTAGE * 8);
 };
 
-// One warp handles chunks of 32 x PIC_PPT consecutive particles of one species (a contiguous run
-// of chunks per warp; strided over the warps of the grid in the step after a sort); the warp's next
+// One warp handles chunks of 32 x PIC_PPT consecutive particles of one species (segments of
+// consecutive chunks claimed from a grid-wide counter, or a contiguous run of chunks per warp for a
+// small species; strided over the warps of the grid in the step after a sort); the warp's next
 // chunk is already streaming into shared memory (a TMA tensor copy
 // completing on an mbarrier) while it computes the current one.  No block-wide barrier inside the
 // particle loop.
@@ -57,11 +62,14 @@ struct StepShape {
 #endif
 
 template <bool SCATTER>
-__global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP_MINB)
+__global__ void __launch_bounds__(StepShape<SCATTER>::TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP_MINB)
     k_step32(const __grid_constant__ StepParams32 P, const __grid_constant__ StepMaps M) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ BlockCounters bc;
+  constexpr int WARPS = StepShape<SCATTER>::WARPS;
+  constexpr bool DYN = StepShape<SCATTER>::DYN;
   constexpr int NSTAGE = StepShape<SCATTER>::NSTAGE;
+  __shared__ unsigned stage_t[WARPS][NSTAGE];  // claimed segments: the chunk in each stage
   constexpr int SB = StepShape<SCATTER>::SB;
 
   const int tid = threadIdx.x;
@@ -117,10 +125,33 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
     // meet on one address (on the grid stride ~50 warps deposit into one dense cell at a time).  The
     // step after a sort keeps the grid stride: its cursor claims return values, and many warps in
     // one cell overlap their latencies.
-    const unsigned per = SCATTER ? 0u : (chunks + nw - 1) / nw;
-    const unsigned t_first = SCATTER ? gw : min(chunks, gw * per);
-    const unsigned t_end = SCATTER ? chunks : min(chunks, t_first + per);
+    //
+    // A large species (at least 48 chunks per warp) is instead claimed in segments of seg
+    // consecutive chunks from a grid-wide counter, the next segment one segment ahead (its
+    // atomic's round trip overlaps the current segment), so that every warp works until the species
+    // runs out: with a static run per warp the warps' end times spread over a third of the launch
+    // (SMs run at different speeds, and chunks in sparse regions cost more), and the last warps
+    // ran with their SMs nearly empty.  seg = chunks per warp / 5 within [12, 24]: shorter
+    // segments make the counter's single address a hot spot, longer ones leave a longer tail.
+    const bool dyn = DYN && chunks >= 48u * nw;
+    const unsigned seg = min(24u, max(12u, chunks / (5u * nw)));
+    const unsigned per = (SCATTER || dyn) ? 0u : (chunks + nw - 1) / nw;
+    const unsigned t_first = dyn ? 0u : SCATTER ? gw : min(chunks, gw * per);
+    const unsigned t_end = (SCATTER || dyn) ? chunks : min(chunks, t_first + per);
     const unsigned t_inc = SCATTER ? nw : 1u;
+    unsigned seg_cur = 0u, seg_end = 0u, seg_nxt = 0u;  // lane 0, claimed segments
+    // lane 0, claimed segments: the chunk for the stage stg (the next one of the segments, recorded
+    // in the stage's slot for the warp's lanes; 0xFFFFFFFF when the species is done)
+    const auto next = [&](int stg) -> unsigned {
+      if (seg_cur >= seg_end) {
+        seg_cur = seg_nxt;
+        seg_end = min(seg_nxt + seg, chunks);
+        seg_nxt = atomicAdd(&P.ctl->chunk_claim[s], seg);
+      }
+      const unsigned tn = seg_cur < seg_end ? seg_cur++ : 0xFFFFFFFFu;
+      stage_t[wib][stg] = tn;
+      return tn;
+    };
     unsigned long long ke_lane = 0ull;  // kinetic energy of this lane's particles that stay live
 
     // lane 0: the copies of chunk t into a stage buffer: one 2-D tensor copy of its five 4-byte
@@ -130,15 +161,18 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
     };
     // prologue: the warp's first NSTAGE chunks
     if (lane == 0) {
+      if (dyn) seg_nxt = atomicAdd(&P.ctl->chunk_claim[s], seg);
+      unsigned t = dyn ? next(0) : t_first;
 #pragma unroll
       for (int st = 0; st < NSTAGE; ++st) {
-        const unsigned t = t_first + st * t_inc;
         if (t < t_end) issue(t, stage + st * SB, bar + st);
+        if (st + 1 < NSTAGE) t = dyn ? next(st + 1) : t + t_inc;
       }
     }
+    __syncwarp();
     int st = 0;
 #pragma unroll 1
-    for (unsigned t = t_first; t < t_end; t += t_inc) {
+    for (unsigned t = dyn ? stage_t[wib][0] : t_first; t < t_end; t = dyn ? stage_t[wib][st] : t + t_inc) {
       if (!__all_sync(0xFFFFFFFFu, mbar_wait_bounded(bar + st, (parity >> st) & 1u))) {
         failed = true;
         break;
@@ -177,22 +211,36 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         if (moves && ph.field_mode == 0u && c[k] != PIC_DEAD_CELL) e2[k] = __ldg(P.E2 + (c[k] & PIC_CELL_MASK));
       }
       // the ordinary step has read its stage: refill it with the chunk NSTAGE steps ahead (the step
-      // after a sort reads the start-of-step cells and the ids from it again at its stores, and
-      // refills it after them)
+      // after a sort reads the ids from it at its stores, and refills it after them)
       unsigned char* const sbuf = stage + st * SB;
       if (!SCATTER) {
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-          const unsigned tn = t + NSTAGE * t_inc;
+          const unsigned tn = dyn ? next(st) : t + NSTAGE * t_inc;
           if (tn < t_end) issue(tn, sbuf, bar + st);
         }
+        if (dyn) __syncwarp();  // the claimed chunk is read by every lane at the loop's end
         st = st + 1 == NSTAGE ? 0 : st + 1;
       }
 
       unsigned live0 = 0u;  // live at the start of the step (scatter: owns a slot)
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) live0 |= c[k] != PIC_DEAD_CELL ? (1u << k) : 0u;
+      // the step after a sort claims each particle's slot in the cell it holds at the start of the
+      // step (one atomic per (warp, cell) group and particle index) before the push, so that the
+      // claims' round trips overlap the push; the slots are resolved at the stores
+      unsigned peers[PIC_PPT], base[PIC_PPT];
+      if (SCATTER) {
+#pragma unroll
+        for (int k = 0; k < PIC_PPT; ++k) {
+          const bool live = (live0 >> k) & 1u;
+          const int cell = c[k] & PIC_CELL_MASK;
+          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cell : -1);
+          base[k] = 0u;
+          if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(P.cursor[s] + cell, (unsigned)__popc(peers[k]));
+        }
+      }
       unsigned cand = 0u;  // the null-collision countdown expired in this step (queued)
 #pragma unroll
       for (int k = 0; k < PIC_PPT; ++k) {
@@ -227,19 +275,7 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
       }
       unsigned slot[PIC_PPT];
       if (SCATTER) {
-        // claim each particle's slot in the cell it held at the start of the step (one atomic per
-        // (warp, cell) group and particle index; the start-of-step cells are still in the stage)
-        const int4 c4 = reinterpret_cast<const int4*>(sbuf)[lane];
-        const int c0[PIC_PPT] = {c4.x, c4.y, c4.z, c4.w};
-        unsigned peers[PIC_PPT], base[PIC_PPT];
-#pragma unroll
-        for (int k = 0; k < PIC_PPT; ++k) {
-          const bool live = (live0 >> k) & 1u;
-          const int cell = c0[k] & PIC_CELL_MASK;
-          peers[k] = __match_any_sync(0xFFFFFFFFu, live ? cell : -1);
-          base[k] = 0u;
-          if (live && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(P.cursor[s] + cell, (unsigned)__popc(peers[k]));
-        }
+        // each particle's slot: its group's claimed base plus its rank in the group
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k)
           slot[k] = __shfl_sync(0xFFFFFFFFu, base[k], __ffs(peers[k]) - 1) + (unsigned)__popc(peers[k] & below);
@@ -265,9 +301,10 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-          const unsigned tn = t + NSTAGE * t_inc;
+          const unsigned tn = dyn ? next(st) : t + NSTAGE * t_inc;
           if (tn < t_end) issue(tn, sbuf, bar + st);
         }
+        if (dyn) __syncwarp();
         st = st + 1 == NSTAGE ? 0 : st + 1;
       } else if (have && moves) {
         *reinterpret_cast<int4*>(A.cell + i0) = make_int4(c[0], c[1], c[2], c[3]);
@@ -284,13 +321,18 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
       }
       // queue the particles whose countdown expired (a collision changes v only, not the deposit)
       // (the ordinary step skips the four ballots when no lane of the warp has a candidate)
-      unsigned qmask = 0u;
+      // the ordinary step sets cand only for particles that survived the push and stay live; after a
+      // sort a failed slot claim can still kill one
+      unsigned qmask = cand;
+      if (SCATTER) {
+        qmask = 0u;
 #pragma unroll
-      for (int k = 0; k < PIC_PPT; ++k) qmask |= ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL ? 1u << k : 0u;
+        for (int k = 0; k < PIC_PPT; ++k) qmask |= ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL ? 1u << k : 0u;
+      }
       if (SCATTER || __any_sync(0xFFFFFFFFu, qmask != 0u)) {
 #pragma unroll
         for (int k = 0; k < PIC_PPT; ++k) {
-          const bool qk = SCATTER ? ((cand >> k) & 1u) && c[k] != PIC_DEAD_CELL : (qmask >> k) & 1u;
+          const bool qk = (qmask >> k) & 1u;
           const unsigned b = __ballot_sync(0xFFFFFFFFu, qk);
           if (qk) q[qn + __popc(b & below)] = tag | (SCATTER ? slot[k] : i0 + k);
           qn += __popc(b);
@@ -330,6 +372,14 @@ __global__ void __launch_bounds__(PIC_TPB, SCATTER ? PIC_SCATTER_MINB : PIC_STEP
 // ---- flush the block counters ----------------------------------------------------------------
   __syncthreads();
   if (tid < 16) counters_to_ctl(P.ctl, ph, bc, tid);
+  if (DYN && tid == 0) {  // every claim of this CTA is done; the last CTA resets the counters
+    __threadfence();
+    if (atomicAdd(&P.ctl->chunk_done, 1u) == gridDim.x - 1u) {
+      atomicExch(&P.ctl->chunk_claim[0], 0u);
+      atomicExch(&P.ctl->chunk_claim[1], 0u);
+      atomicExch(&P.ctl->chunk_done, 0u);
+    }
+  }
 }
 
 // Pair source (one pair per ion absorbed in this step), uniform in [0, x1), Maxwellian at T_s.
@@ -427,7 +477,8 @@ static void step32_attrs();
 int occupancy_step32(bool scatter) {
   step32_attrs();
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, scatter ? k_step32<true> : k_step32<false>, PIC_TPB,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, scatter ? k_step32<true> : k_step32<false>,
+                                                    scatter ? StepShape<true>::TPB : StepShape<false>::TPB,
                                                     scatter ? StepShape<true>::SMEM : StepShape<false>::SMEM) !=
                                                         cudaSuccess ||
       b < 1)
@@ -446,13 +497,13 @@ static void step32_attrs() {
 
 cudaError_t launch_step32(const StepParams32& p, const StepMaps& m, int grid, cudaStream_t st) {
   step32_attrs();
-  k_step32<false><<<grid, PIC_TPB, StepShape<false>::SMEM, st>>>(p, m);
+  k_step32<false><<<grid, StepShape<false>::TPB, StepShape<false>::SMEM, st>>>(p, m);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step32_scatter(const StepParams32& p, const StepMaps& m, int grid, cudaStream_t st) {
   step32_attrs();
-  k_step32<true><<<grid, PIC_TPB, StepShape<true>::SMEM, st>>>(p, m);
+  k_step32<true><<<grid, StepShape<true>::TPB, StepShape<true>::SMEM, st>>>(p, m);
   return cudaGetLastError();
 }
 

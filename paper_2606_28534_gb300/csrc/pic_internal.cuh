@@ -89,6 +89,11 @@ struct Ctl {
   unsigned long long wlog_n;             // ions absorbed at a wall in the current step (recycling log)
   unsigned long long diag_step;          // steps taken when the last diagnostics were enqueued
   unsigned long long diag_what;          // PIC_DIAG_* of that request
+  // the ordinary particle step's chunk schedule: chunks claimed per species, CTAs done (the last
+  // CTA of a launch zeroes all three for the next launch)
+  unsigned int chunk_claim[2];
+  unsigned int chunk_done;
+  unsigned int chunk_pad;
 };
 
 struct Species32 {

@@ -131,8 +131,12 @@ SMALL_C6 = variant(C6, ncells=96, L=96.0, ppc=(53, 53), neutral_ppc=31, load_pro
 #: profiling case: config 3's physics and profile with 1/8 of the particles (12.5 M, 350 MB of
 #: particle data: larger than L2, small enough for multi-pass counter captures)
 C3_PROFILE = variant(C3, ppc=(96, 96))
+#: config 3 with half of its particles (profiling case of the step's claimed chunk segments, which a
+#: species takes from 48 chunks per warp on: 25 M particles per species)
+C3_HALF = variant(C3, ppc=(384, 384))
 
 #: the D+/e/D sheath with 1/8 of the particles (profiling case)
 C6_PROFILE = variant(C6, ppc=(96, 96), neutral_ppc=96)
 
-CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c5": C5, "c3p": C3_PROFILE, "c6": C6, "c6p": C6_PROFILE}
+CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c5": C5, "c3p": C3_PROFILE, "c3h": C3_HALF, "c6": C6,
+           "c6p": C6_PROFILE}

@@ -530,6 +530,16 @@ def test_full_size_sampled_step_matches_the_oracle_one_by_one():
     after = _species_views(g.snapshot())
     rng = np.random.default_rng(17)
     N = p["ncells"]
+    # every particle of the stepped state deposited exactly once (at this size the step claims its
+    # chunks in segments from a grid-wide counter): the node deposits equal the CIC deposit of the
+    # stored particles, W_r = rint(f 2^32) (ties to even), summed here exactly (integers below 2^53)
+    R = g.fields()["R"]
+    for s in range(2):
+        cell1, frac1 = after[s][0], after[s][1]
+        wr = np.rint(frac1 * 2.0**32)
+        Rh = (np.bincount(cell1, weights=2.0**32 - wr, minlength=N + 1)
+              + np.bincount(cell1 + 1, weights=wr, minlength=N + 1))
+        assert np.array_equal(Rh.astype(np.int64), R[s]), s
     for s in range(2):
         cell, frac, v, ids, nk = before[s]
         # 2000 anywhere, and up to 300 in the wall cells, where particles leave
