@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ BlockCounters wcs[WARPS];
   __shared__ WarpSim wsm[WARPS];
+  __shared__ unsigned stage_t[WARPS][NST];  // claimed segments: the chunk in each stage
+  constexpr bool DYN = !SCATTER;           // the ordinary step may claim chunk segments
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, wib = tid >> 5;
@@ -133,9 +135,39 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
   for (int s = 0; s < 2 && !failed; ++s) {
     const unsigned* __restrict__ pre = B.pre[s];
     const unsigned total = pre[nsims];
-    const unsigned per = (total + nw - 1) / nw;
-    const unsigned t0 = min(total, gw * per);
-    const unsigned t1 = min(total, t0 + per);
+    // Work list schedule: a contiguous run of chunks per warp, or, from 48 chunks per warp on,
+    // segments of cseg consecutive chunks claimed from a counter of the batch (the next one a
+    // segment ahead), so that every warp works until the species runs out (the single-run step's
+    // schedule; a static run per warp ends with SMs nearly empty).
+    const bool dyn = DYN && total >= 48u * nw;
+    const unsigned cseg = min(24u, max(12u, total / (5u * nw)));
+    unsigned seg_cur = 0u, seg_end = 0u, seg_nxt = 0u;  // lane 0, claimed segments
+    // lane 0, claimed segments: the chunk for the stage stg, recorded in the stage's slot for the
+    // warp's lanes (0xFFFFFFFF when the species is done)
+    const auto next = [&](int stg) -> unsigned {
+      if (seg_cur >= seg_end) {
+        seg_cur = seg_nxt;
+        seg_end = min(seg_nxt + cseg, total);
+        seg_nxt = atomicAdd(&B.dev->claim[s], cseg);
+      }
+      const unsigned tn = seg_cur < seg_end ? seg_cur++ : 0xFFFFFFFFu;
+      stage_t[wib][stg] = tn;
+      return tn;
+    };
+    unsigned t0, t1;
+    if (dyn) {
+      if (lane == 0) {
+        seg_nxt = atomicAdd(&B.dev->claim[s], cseg);
+        next(0);
+      }
+      __syncwarp();
+      t0 = stage_t[wib][0];
+      t1 = total;
+    } else {
+      const unsigned per = (total + nw - 1) / nw;
+      t0 = min(total, gw * per);
+      t1 = min(total, t0 + per);
+    }
     if (t0 >= t1) continue;
     const Species32& A = B.sp[s];                          // written
     const Species32& Asrc = SCATTER ? B.src[s] : B.sp[s];  // read
@@ -149,7 +181,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
       int ki = kfirst;
 #pragma unroll
       for (int st = 0; st < NST; ++st) {
-        const unsigned t = t0 + st;
+        const unsigned t = st == 0 ? t0 : dyn ? next(st) : t0 + st;
         if (t < t1) {
           while (pre[ki + 1] <= t) ++ki;
           issue_chunk(B, s ? &M.tmap[1] : &M.tmap[0], Asrc, s, ki, t - pre[ki], stage + st * SB, bar + st, SCATTER);
@@ -163,8 +195,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
     WarpSim& ws = wsm[wib];
     unsigned long long ke_lane = 0ull;  // kinetic energy of this lane's particles that stay live
     int st = 0;
+    __syncwarp();
 #pragma unroll 1
-    for (unsigned t = t0; t < t1; ++t) {
+    for (unsigned t = t0; t < t1; t = dyn ? stage_t[wib][st] : t + 1u) {
       if (t >= kend) {  // first chunk of another simulation
         if (kend) {
           leave_sim(B, kc, s, q, qn, wc, ke_lane, true, SCATTER);
@@ -232,13 +265,14 @@ __global__ void __launch_bounds__(TPB, MINB) k_bstep32(const __grid_constant__ B
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-          const unsigned tn = t + NST;
+          const unsigned tn = dyn ? next(st) : t + NST;
           if (tn < t1) {
             int ki = kc;  // owner of chunk tn: this simulation or a later one
             while (pre[ki + 1] <= tn) ++ki;
             issue_chunk(B, s ? &M.tmap[1] : &M.tmap[0], Asrc, s, ki, tn - pre[ki], sbuf, bar + st, with_id);
           }
         }
+        if (dyn) __syncwarp();  // the claimed chunk is read by every lane at the loop's end
         st = st + 1 == NST ? 0 : st + 1;
       };
       if (!SCATTER) refill(false);
@@ -482,6 +516,8 @@ __global__ void __launch_bounds__(PLAN_TPB) k_bplan(const BatchPlan P) {
   if (tid == 0) {
     P.dev->step = step_s;
     if (err_s) P.dev->error |= err_s;
+    P.dev->claim[0] = 0u;  // the next particle step claims its chunks from zero
+    P.dev->claim[1] = 0u;
   }
 }
 

@@ -458,6 +458,7 @@ struct BatchDev {
   unsigned long long step;  // step the next particle step advances
   unsigned int error;       // OR of the simulations' error bits (refreshed by the plan kernel)
   unsigned int pad;
+  unsigned int claim[2];    // per species: chunks claimed in the step (zeroed by the plan kernel)
 };
 
 struct BatchStep32 {
