@@ -50,8 +50,9 @@ BYTES_SCATTER_KERNEL = 56
 # for the ordinary step's claimed chunk segments), scaled by particles to a full launch: the
 # ordinary step and the step after a sort
 TRAFFIC_STEP, TRAFFIC_SCATTER = 42.75, 58.80
-# the same for the ensemble's particle step (ncu on a 16-run ensemble of config 4's distribution)
-TRAFFIC_BSTEP = 41.50
+# the same for the ensemble's particle step (ncu on a 20-run ensemble of config 4's distribution,
+# large enough for its claimed chunk segments)
+TRAFFIC_BSTEP = 41.56
 # the neutral step reads each neutral (cell, frac, v, id: 28 B) and writes back its cell and fraction
 # (8 B); on sort steps it writes each survivor, compacted, into the other buffer instead (28 B)
 BYTES_NEUTRAL_KERNEL, BYTES_NEUTRAL_COMPACT = 36, 56
