@@ -32,8 +32,9 @@ template <bool SCATTER>
 struct StepShape {
   static constexpr int TPB = PIC_TPB;
   static constexpr int WARPS = TPB / 32;
-  // the ordinary step may claim chunk segments (below); after a sort, claimed segments made that
-  // step 1 % faster but left an order that made the next nine steps 3 % slower
+  // the ordinary step may claim chunk segments (below); after a sort, claimed segments of 12-24
+  // chunks made that step 1 % faster but left an order that made the next nine steps 3 % slower,
+  // and claims of one or two chunks at a time made it 20-36 % slower
   static constexpr bool DYN = !SCATTER;
   static constexpr int NSTAGE = SCATTER ? 2 : PIC_STEP_NSTAGE;
   static constexpr int SB = SCATTER ? STAGE_BYTES : CHUNK * 20;

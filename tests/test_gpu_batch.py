@@ -9,8 +9,9 @@ configuration computes alone.
   produce byte-identical snapshots, identical diagnostics and identical fields over many steps and
   several sorts, for every compiled shape of the batch step kernel, with and without CUDA graphs.
 * The C4 ensemble at full size (256 runs, 5.7e8 particles): sampled initial particles against the
-  oracle's loader, charge and particle accounting of every run after 20 steps, and one run
-  against the same configuration run alone.
+  oracle's loader, charge and particle accounting of every run after 20 steps, the node deposits of
+  three runs against an exact integer sum over their stored particles, and one run against the same
+  configuration run alone.
 """
 import math
 
@@ -249,6 +250,19 @@ def test_c4_full_size():
             lost = d["wall_hits"][s][0] + d["wall_hits"][s][1]
             assert d["n"][s] == n0[s] + d["births"][s] - lost
         assert d["coll"][4] > 0
+    # every particle deposited exactly once (at this size the ensemble's step claims its chunks in
+    # segments from a counter of the batch): the node deposits of the smallest, a middle and the
+    # largest run equal the CIC deposit of their stored particles, W_r = rint(f 2^32), summed here
+    # exactly (integers below 2^53)
+    for k in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        N = runs[k]["ncells"]
+        sp = snapfmt.parse(b.snapshot(k))["species"]
+        R = b.fields(k)["R"]
+        for s in range(2):
+            cell, wr = sp[s]["cell"].astype(np.int64), np.rint(sp[s]["frac"] * 2.0**32)
+            Rh = (np.bincount(cell, weights=2.0**32 - wr, minlength=N + 1)
+                  + np.bincount(cell + 1, weights=wr, minlength=N + 1))
+            assert np.array_equal(Rh.astype(np.int64), R[s]), (k, s)
     # one mid-size run against the same configuration alone (byte-identical state)
     k = int(order[len(order) // 2])
     g = pic.Simulation(runs[k])
