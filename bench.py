@@ -616,21 +616,25 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
         if rc != 0:
             raise RuntimeError(f"pic_restore failed: {rc}")
         t1 = time.perf_counter()
-        # every step's diagnostics are read back; step k + 1 is enqueued before step k's copy is
-        # decoded, so the GPU does not wait for the host
+        # every step's diagnostics are read back into a ring of DEPTH pinned buffers; step k's copy
+        # is decoded once step k + DEPTH - 1 is enqueued, so that a host stall shorter than a few
+        # steps does not leave the GPU idle
+        DEPTH = 4
         nb = int(pic.lib().pic_diag_bytes())
-        bufs = [torch.empty(nb, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-        evs = [torch.cuda.Event() for _ in range(2)]
+        bufs = [torch.empty(nb, dtype=torch.uint8, pin_memory=True) for _ in range(DEPTH)]
+        evs = [torch.cuda.Event() for _ in range(DEPTH)]
         dsum = 0
         for k in range(ek):
             sim2.step(1)
-            sim2.diag_async(bufs[k % 2], counters_only=True)
-            evs[k % 2].record(sim2.stream)
-            if k:
-                evs[(k - 1) % 2].synchronize()
-                dsum = sim2.diag_decode(bufs[(k - 1) % 2])["particle_steps"]
-        evs[(ek - 1) % 2].synchronize()
-        dsum = sim2.diag_decode(bufs[(ek - 1) % 2])["particle_steps"]
+            sim2.diag_async(bufs[k % DEPTH], counters_only=True)
+            evs[k % DEPTH].record(sim2.stream)
+            j = k - (DEPTH - 1)
+            if j >= 0:
+                evs[j % DEPTH].synchronize()
+                dsum = sim2.diag_decode(bufs[j % DEPTH])["particle_steps"]
+        for j in range(max(0, ek - (DEPTH - 1)), ek):
+            evs[j % DEPTH].synchronize()
+            dsum = sim2.diag_decode(bufs[j % DEPTH])["particle_steps"]
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         # the same restore once more, outside the metric: it separates first-call costs of the
@@ -658,7 +662,7 @@ def run_ours(args, rank: int, world: int, local: int) -> None:
                "what": "pic_restore from a checkpoint blob in pinned host memory, then per step "
                        "pic_step(1) and pic_diag_async(PIC_DIAG_COUNTERS) (device-to-host copy of the "
                        "control block: counters, particle-steps, error word; no energy reduction) into "
-                       "pinned memory, each step's copy decoded on the host while the next step runs"}
+                       "a ring of 4 pinned buffers, each step's copy decoded on the host three steps later"}
 
     batch = None
     if single and not args.no_batch:
