@@ -374,8 +374,9 @@ __global__ void __launch_bounds__(StepShape<SCATTER>::TPB, SCATTER ? PIC_SCATTER
   __syncthreads();
   if (tid < 16) counters_to_ctl(P.ctl, ph, bc, tid);
   if (DYN && tid == 0) {  // every claim of this CTA is done; the last CTA resets the counters
-    __threadfence();
+    __threadfence();  // this CTA's claims (ordered here by the barrier) before its count
     if (atomicAdd(&P.ctl->chunk_done, 1u) == gridDim.x - 1u) {
+      __threadfence();  // every CTA's claims before the reset
       atomicExch(&P.ctl->chunk_claim[0], 0u);
       atomicExch(&P.ctl->chunk_claim[1], 0u);
       atomicExch(&P.ctl->chunk_done, 0u);
